@@ -1,0 +1,253 @@
+"""CPU oracle for the tensor-product multigrid preconditioned-CG path.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference leg of ``bench.py`` may import this package.  The
+product path (the CUDA library and its binding) never imports it, and this
+package imports nothing from the product path.
+
+The arithmetic lives in ``tpmg_oracle.c`` (plain single-threaded FP64 C,
+compiled with ``-ffp-contract=off``); this module only compiles it and marshals
+numpy arrays through ctypes.  Every function of the C file cites the passage of
+Dedner, Mueller & Scheichl (arXiv:1408.2981) it follows.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tpmg_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle_tpmg.so")
+_lock = threading.Lock()
+_lib = None
+
+_D = ctypes.c_double
+_I = ctypes.c_int
+_P = ctypes.c_void_p
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/liboracle_tpmg.so`` (gcc, C99, -O2)."""
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    return compile_source(_SRC, _LIB_PATH)
+
+
+_libs: dict = {}
+
+
+def compile_source(src: str, out_path: str) -> str:
+    """Compile one oracle C source into a shared library at ``out_path``."""
+    tmp = out_path + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           src, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out_path)
+    return out_path
+
+
+def _load(path: str | None = None):
+    """ctypes handle of the oracle library (the built default, or ``path``)."""
+    global _lib
+    with _lock:
+        key = path or _LIB_PATH
+        if key in _libs:
+            return _libs[key]
+        lib = ctypes.CDLL(path if path else build())
+        lib.oracle_create.restype = _P
+        lib.oracle_create.argtypes = [_I, _I, _I, _D, _D, _D, _D, _I, _I, _I, _I, _D, _I]
+        lib.oracle_destroy.argtypes = [_P]
+        lib.oracle_info.argtypes = [_P, _P, _P]
+        lib.oracle_grid_sizes.argtypes = [_P, _I, _P]
+        lib.oracle_export_grid.argtypes = [_P, _I, _P, _P, _P, _P, _P, _P]
+        lib.oracle_export_vertical.argtypes = [_P, _P, _P, _P]
+        lib.oracle_level_cells.argtypes = [_P, _I]
+        lib.oracle_apply.argtypes = [_P, _I, _P, _P]
+        lib.oracle_column_blocks.argtypes = [_P, _I, _P, _P, _P]
+        lib.oracle_smooth.argtypes = [_P, _I, _P, _P, _I, _I]
+        lib.oracle_restrict.argtypes = [_P, _I, _P, _P]
+        lib.oracle_prolong_add.argtypes = [_P, _I, _P, _P]
+        lib.oracle_vcycle.argtypes = [_P, _P, _P]
+        lib.oracle_pcg.argtypes = [_P, _P, _P, _D, _I, _P, _P, _P, _P]
+        lib.oracle_richardson.argtypes = [_P, _P, _P, _I, _P]
+        lib.oracle_thomas.argtypes = [_I, _P, _P, _P, _P, _P]
+        _libs[key] = lib
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def _ptr(a: np.ndarray | None):
+    if a is None:
+        return None
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def thomas(a, b, c, d, lib_path: str | None = None) -> np.ndarray:
+    """Solve tridiag(a, b, c) x = d (a[0], c[-1] unused) with the oracle's Thomas algorithm."""
+    a, b, c, d = (_f64(v) for v in (a, b, c, d))
+    n = d.shape[0]
+    x = np.empty(n)
+    if _load(lib_path).oracle_thomas(n, _ptr(a), _ptr(b), _ptr(c), _ptr(d), _ptr(x)) != 0:
+        raise ValueError("oracle_thomas failed")
+    return x
+
+
+class Oracle:
+    """One oracle problem instance: icosahedral grid hierarchy, vertical grid,
+    operator, smoother, V-cycle and PCG, all in FP64 on the host.
+
+    Multigrid level 0 is the coarsest; level ``n_levels - 1`` is the finest
+    (refinement ``refinement``).  Field vectors are ``[n_cells * n_r]`` with
+    the vertical index fastest.
+    """
+
+    SMOOTH_MCSOR = 0
+    SMOOTH_JACOBI = 1
+    CENTRE_CIRCUM = 0
+    CENTRE_VERTEX_MEAN = 1
+
+    def __init__(self, refinement: int, n_levels: int, n_r: int, H: float = 10.0 / 6371.0,
+                 grading: float = 1.0, omega2: float = 0.0, courant_c: float = 8.0,
+                 nu_pre: int = 2, nu_post: int = 2, nu_coarse: int = 1,
+                 smoother: int = 0, relax: float = 1.0, centre_kind: int = 0,
+                 lib_path: str | None = None):
+        lib = _load(lib_path)
+        self._lib = lib
+        self._h = lib.oracle_create(refinement, n_levels, n_r, H, grading, omega2, courant_c,
+                                    nu_pre, nu_post, nu_coarse, smoother, relax, centre_kind)
+        if not self._h:
+            raise ValueError("oracle_create rejected the parameters")
+        sc = np.zeros(4)
+        it = np.zeros(3, dtype=np.int32)
+        lib.oracle_info(self._h, _ptr(sc), _ptr(it))
+        self.omega2, self.h_min, self.H, self.grading = (float(v) for v in sc)
+        self.refinement, self.n_levels, self.n_r = (int(v) for v in it)
+        self.nu_pre, self.nu_post, self.nu_coarse = nu_pre, nu_post, nu_coarse
+        self.smoother, self.relax, self.centre_kind = smoother, relax, centre_kind
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._lib.oracle_destroy(h)
+            self._h = None
+
+    # ------------------------------------------------------------- geometry
+    def grid_sizes(self, ref: int) -> dict:
+        out = np.zeros(4, dtype=np.int32)
+        if self._lib.oracle_grid_sizes(self._h, ref, _ptr(out)) != 0:
+            raise ValueError("bad refinement level")
+        return dict(n_cells=int(out[0]), n_verts=int(out[1]), n_edges=int(out[2]), n_colours=int(out[3]))
+
+    def grid(self, ref: int) -> dict:
+        n = self.grid_sizes(ref)["n_cells"]
+        out = dict(centre=np.zeros((n, 3)), area=np.zeros(n), nbr=np.zeros((n, 3), dtype=np.int32),
+                   g=np.zeros((n, 3)), colour=np.zeros(n, dtype=np.int32), corners=np.zeros((n, 3, 3)))
+        self._lib.oracle_export_grid(self._h, ref, _ptr(out["centre"]), _ptr(out["area"]), _ptr(out["nbr"]),
+                                     _ptr(out["g"]), _ptr(out["colour"]), _ptr(out["corners"]))
+        return out
+
+    def level_ref(self, level: int) -> int:
+        return self.refinement - (self.n_levels - 1 - level)
+
+    def level_cells(self, level: int) -> int:
+        n = self._lib.oracle_level_cells(self._h, level)
+        if n < 0:
+            raise ValueError("bad multigrid level")
+        return n
+
+    def vertical(self) -> dict:
+        r = np.zeros(self.n_r + 1)
+        dr = np.zeros(self.n_r)
+        vol = np.zeros(self.n_r)
+        self._lib.oracle_export_vertical(self._h, _ptr(r), _ptr(dr), _ptr(vol))
+        return dict(r=r, dr=dr, vol=vol)
+
+    def size(self, level: int | None = None) -> int:
+        level = self.n_levels - 1 if level is None else level
+        return self.level_cells(level) * self.n_r
+
+    # ------------------------------------------------------------- operators
+    def apply(self, x, level: int | None = None) -> np.ndarray:
+        level = self.n_levels - 1 if level is None else level
+        x = _f64(x).reshape(-1)
+        assert x.shape[0] == self.size(level)
+        y = np.empty_like(x)
+        self._lib.oracle_apply(self._h, level, _ptr(x), _ptr(y))
+        return y
+
+    def column_blocks(self, level: int | None = None):
+        level = self.n_levels - 1 if level is None else level
+        n = self.level_cells(level)
+        sub, diag, sup = (np.zeros((n, self.n_r)) for _ in range(3))
+        self._lib.oracle_column_blocks(self._h, level, _ptr(sub), _ptr(diag), _ptr(sup))
+        return sub, diag, sup
+
+    def smooth(self, f, u, sweeps: int = 1, direction: int = 1, level: int | None = None) -> np.ndarray:
+        level = self.n_levels - 1 if level is None else level
+        f = _f64(f).reshape(-1)
+        u = _f64(u).reshape(-1).copy()
+        self._lib.oracle_smooth(self._h, level, _ptr(f), _ptr(u), sweeps, direction)
+        return u
+
+    def restrict(self, r_fine, level_fine: int) -> np.ndarray:
+        r_fine = _f64(r_fine).reshape(-1)
+        out = np.zeros(self.size(level_fine - 1))
+        if self._lib.oracle_restrict(self._h, level_fine, _ptr(r_fine), _ptr(out)) != 0:
+            raise ValueError("bad level")
+        return out
+
+    def prolong_add(self, u_coarse, u_fine, level_fine: int) -> np.ndarray:
+        u_coarse = _f64(u_coarse).reshape(-1)
+        out = _f64(u_fine).reshape(-1).copy()
+        if self._lib.oracle_prolong_add(self._h, level_fine, _ptr(u_coarse), _ptr(out)) != 0:
+            raise ValueError("bad level")
+        return out
+
+    def vcycle(self, r) -> np.ndarray:
+        r = _f64(r).reshape(-1)
+        z = np.empty_like(r)
+        self._lib.oracle_vcycle(self._h, _ptr(r), _ptr(z))
+        return z
+
+    def pcg(self, f, u0=None, rtol: float = 1e-5, max_iter: int = 100) -> dict:
+        f = _f64(f).reshape(-1)
+        u = np.zeros_like(f) if u0 is None else _f64(u0).reshape(-1).copy()
+        iters = ctypes.c_int(0)
+        rel = ctypes.c_double(0.0)
+        true_rel = ctypes.c_double(0.0)
+        hist = np.zeros(max_iter + 1)
+        status = self._lib.oracle_pcg(self._h, _ptr(f), _ptr(u), rtol, max_iter, ctypes.byref(iters),
+                                      ctypes.byref(rel), _ptr(hist), ctypes.byref(true_rel))
+        return dict(u=u, iters=iters.value, rel_resid=rel.value, true_rel=true_rel.value,
+                    hist=hist[:iters.value + 1].copy(), status=status)
+
+    def richardson(self, f, u0, n_iter: int) -> tuple[np.ndarray, np.ndarray]:
+        f = _f64(f).reshape(-1)
+        u = _f64(u0).reshape(-1).copy()
+        hist = np.zeros(n_iter + 1)
+        self._lib.oracle_richardson(self._h, _ptr(f), _ptr(u), n_iter, _ptr(hist))
+        return u, hist
+
+    def dense_operator(self, level: int | None = None) -> np.ndarray:
+        """Assemble A column by column from the matrix-free apply (tiny grids only)."""
+        n = self.size(level)
+        if n > 6000:
+            raise ValueError("dense assembly is for tiny grids")
+        A = np.zeros((n, n))
+        e = np.zeros(n)
+        for j in range(n):
+            e[j] = 1.0
+            A[:, j] = self.apply(e, level)
+            e[j] = 0.0
+        return A

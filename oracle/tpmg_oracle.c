@@ -1,0 +1,795 @@
+/*
+ * tpmg_oracle.c -- TEST INFRASTRUCTURE ONLY (not part of the product path).
+ *
+ * A plain, slow, single-threaded FP64 CPU statement of what the tensor-product
+ * multigrid (TPMG) preconditioned conjugate-gradient path computes, written from
+ * Dedner, Mueller & Scheichl, "Efficient multigrid preconditioners for
+ * atmospheric flow simulations at high aspect ratio" (arXiv:1408.2981).
+ * Only the tests, the smoke check and the CPU-baseline leg of the benchmark may
+ * load this file.  It shares no code, header, table or helper with the CUDA
+ * library and includes nothing from it.
+ *
+ * Problem (Sec. 2, eq. HelmholtzVector with constant profiles
+ * alpha_r = alpha_S = beta = 1, xi_r = 0):
+ *     -omega^2 div grad u + u = f   in the shell  S^2 x [1, 1+H],
+ * homogeneous Neumann conditions at r = 1 and r = 1+H (Appendix A).
+ *
+ * Everything is plain loops in the order the paper states the method:
+ *   grid (Sec. 4.1, Sec. 4.2) -> finite-volume hat coefficients (Appendix A,
+ *   eq. hatFunctionsNonFac) -> column equation (eq. ColumnEquation,
+ *   TridiagonalSystem) -> Thomas algorithm -> block relaxation (eq. BlockJacobi)
+ *   -> V-cycle (Algorithm 1) -> preconditioned CG.
+ *
+ * Readings taken where the paper is silent, ambiguous or garbled are marked
+ * "Reading Cn" and listed in the design notes of the repository.
+ *
+ * Build: plain C99, compiled with -O2 -ffp-contract=off so that every
+ * operation is one IEEE-754 double rounding on every host.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------- */
+/* 3-vectors                                                                  */
+/* ------------------------------------------------------------------------- */
+typedef struct { double x, y, z; } vec3;
+
+static vec3 v_make(double x, double y, double z) { vec3 v = {x, y, z}; return v; }
+static vec3 v_add(vec3 a, vec3 b) { return v_make(a.x + b.x, a.y + b.y, a.z + b.z); }
+static vec3 v_sub(vec3 a, vec3 b) { return v_make(a.x - b.x, a.y - b.y, a.z - b.z); }
+static vec3 v_scale(vec3 a, double s) { return v_make(a.x * s, a.y * s, a.z * s); }
+static double v_dot(vec3 a, vec3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+static vec3 v_cross(vec3 a, vec3 b)
+{
+    return v_make(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+static double v_norm(vec3 a) { return sqrt(v_dot(a, a)); }
+static vec3 v_unit(vec3 a) { return v_scale(a, 1.0 / v_norm(a)); }
+
+/* ------------------------------------------------------------------------- */
+/* Horizontal grid: icosahedron refined by edge bisection, vertices projected */
+/* onto the unit sphere (Sec. 4.1: each coarse triangle holds four fine ones; */
+/* Sec. 4.2: icosahedral grid with points projected onto the sphere).         */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int ref;            /* refinement level: 20 * 4^ref cells               */
+    int n_cells, n_verts, n_edges;
+    vec3 *vert;         /* [n_verts] vertex positions on the unit sphere    */
+    int *cv;            /* [n_cells][3] vertex ids, counter-clockwise seen from outside */
+    int *nbr;           /* [n_cells][3] cell across edge e = (v_e, v_{(e+1)%3}) */
+    int *edge;          /* [n_cells][3] id of the unique edge in slot e     */
+    vec3 *centre;       /* [n_cells] cell centre r_T                        */
+    double *area;       /* [n_cells] |T|                                    */
+    double *g;          /* [n_cells][3] |S_TT'| n.(r_T'-r_T)/|r_T'-r_T|^2  */
+    int *colour;        /* [n_cells] greedy colour of the neighbour graph   */
+    int n_colours;
+} ogrid;
+
+static void grid_free(ogrid *G)
+{
+    free(G->vert); free(G->cv); free(G->nbr); free(G->edge);
+    free(G->centre); free(G->area); free(G->g); free(G->colour);
+    memset(G, 0, sizeof(*G));
+}
+
+static int grid_alloc(ogrid *G, int ref, int n_cells, int n_verts)
+{
+    G->ref = ref;
+    G->n_cells = n_cells;
+    G->n_verts = n_verts;
+    G->vert = (vec3 *)calloc((size_t)n_verts, sizeof(vec3));
+    G->cv = (int *)calloc((size_t)n_cells * 3, sizeof(int));
+    G->nbr = (int *)calloc((size_t)n_cells * 3, sizeof(int));
+    G->edge = (int *)calloc((size_t)n_cells * 3, sizeof(int));
+    G->centre = (vec3 *)calloc((size_t)n_cells, sizeof(vec3));
+    G->area = (double *)calloc((size_t)n_cells, sizeof(double));
+    G->g = (double *)calloc((size_t)n_cells * 3, sizeof(double));
+    G->colour = (int *)calloc((size_t)n_cells, sizeof(int));
+    if (!G->vert || !G->cv || !G->nbr || !G->edge || !G->centre || !G->area || !G->g || !G->colour)
+        return -1;
+    return 0;
+}
+
+/* Level 0.  Vertices: the 12 cyclic permutations of (0, +-1, +-phi), taken in
+ * the order  index = 4*p + 2*[s1 > 0] + [s2 > 0]  for the cyclic shift p of
+ * (0, s1, s2*phi), then normalised.  Faces: every triple of pairwise adjacent
+ * vertices, listed as (i, j, k) with i the smallest id and (i, j, k)
+ * counter-clockwise seen from outside; faces sorted lexicographically. */
+static int build_icosahedron(ogrid *G)
+{
+    const double phi = 0.5 * (1.0 + sqrt(5.0));
+    vec3 raw[12];
+    int p, s1, s2, i, j, k, nf = 0;
+    if (grid_alloc(G, 0, 20, 12)) return -1;
+    for (p = 0; p < 3; ++p)
+        for (s1 = 0; s1 < 2; ++s1)
+            for (s2 = 0; s2 < 2; ++s2) {
+                double a = 0.0, b = s1 ? 1.0 : -1.0, c = s2 ? phi : -phi;
+                vec3 v;
+                if (p == 0) v = v_make(a, b, c);
+                else if (p == 1) v = v_make(c, a, b);
+                else v = v_make(b, c, a);
+                raw[4 * p + 2 * s1 + s2] = v;
+            }
+    for (i = 0; i < 12; ++i) G->vert[i] = v_unit(raw[i]);
+    /* adjacent vertices of the unnormalised icosahedron are at distance 2 */
+    for (i = 0; i < 12; ++i)
+        for (j = i + 1; j < 12; ++j)
+            for (k = j + 1; k < 12; ++k) {
+                vec3 dij = v_sub(raw[i], raw[j]), djk = v_sub(raw[j], raw[k]), dki = v_sub(raw[k], raw[i]);
+                if (fabs(v_dot(dij, dij) - 4.0) > 1e-9 || fabs(v_dot(djk, djk) - 4.0) > 1e-9 ||
+                    fabs(v_dot(dki, dki) - 4.0) > 1e-9)
+                    continue;
+                {
+                    vec3 nrm = v_cross(v_sub(raw[j], raw[i]), v_sub(raw[k], raw[i]));
+                    vec3 mid = v_add(v_add(raw[i], raw[j]), raw[k]);
+                    if (nf >= 20) return -1;
+                    G->cv[3 * nf + 0] = i;
+                    if (v_dot(nrm, mid) > 0.0) { G->cv[3 * nf + 1] = j; G->cv[3 * nf + 2] = k; }
+                    else { G->cv[3 * nf + 1] = k; G->cv[3 * nf + 2] = j; }
+                    ++nf;
+                }
+            }
+    if (nf != 20) return -1;
+    /* lexicographic sort of the (i, j, k) rows (insertion sort, 20 rows) */
+    for (i = 1; i < 20; ++i) {
+        int row[3] = {G->cv[3 * i], G->cv[3 * i + 1], G->cv[3 * i + 2]};
+        j = i - 1;
+        while (j >= 0 && (G->cv[3 * j] > row[0] ||
+                          (G->cv[3 * j] == row[0] && (G->cv[3 * j + 1] > row[1] ||
+                                                      (G->cv[3 * j + 1] == row[1] && G->cv[3 * j + 2] > row[2]))))) {
+            memcpy(&G->cv[3 * (j + 1)], &G->cv[3 * j], 3 * sizeof(int));
+            --j;
+        }
+        memcpy(&G->cv[3 * (j + 1)], row, 3 * sizeof(int));
+    }
+    return 0;
+}
+
+/* Neighbours: every edge of the closed surface is shared by exactly two cells.
+ * Sort all (cell, slot) half-edges by their unordered vertex pair and pair them. */
+typedef struct { int lo, hi, cell, slot; } half_edge;
+
+static int cmp_half_edge(const void *pa, const void *pb)
+{
+    const half_edge *a = (const half_edge *)pa, *b = (const half_edge *)pb;
+    if (a->lo != b->lo) return a->lo < b->lo ? -1 : 1;
+    if (a->hi != b->hi) return a->hi < b->hi ? -1 : 1;
+    if (a->cell != b->cell) return a->cell < b->cell ? -1 : 1;
+    return a->slot - b->slot;
+}
+
+static int match_edges(ogrid *G)
+{
+    int n = 3 * G->n_cells, i;
+    half_edge *h = (half_edge *)malloc((size_t)n * sizeof(half_edge));
+    if (!h) return -1;
+    for (i = 0; i < n; ++i) {
+        int T = i / 3, e = i % 3;
+        int a = G->cv[3 * T + e], b = G->cv[3 * T + (e + 1) % 3];
+        h[i].lo = a < b ? a : b;
+        h[i].hi = a < b ? b : a;
+        h[i].cell = T;
+        h[i].slot = e;
+    }
+    qsort(h, (size_t)n, sizeof(half_edge), cmp_half_edge);
+    if (n % 2) { free(h); return -1; }
+    for (i = 0; i < n; i += 2) {
+        const half_edge *a = &h[i], *b = &h[i + 1];
+        if (a->lo != b->lo || a->hi != b->hi || a->cell == b->cell ||
+            (i + 2 < n && h[i + 2].lo == a->lo && h[i + 2].hi == a->hi)) {
+            free(h);
+            return -1; /* not a closed two-manifold */
+        }
+        G->nbr[3 * a->cell + a->slot] = b->cell;
+        G->nbr[3 * b->cell + b->slot] = a->cell;
+        G->edge[3 * a->cell + a->slot] = i / 2;
+        G->edge[3 * b->cell + b->slot] = i / 2;
+    }
+    G->n_edges = n / 2;
+    free(h);
+    return 0;
+}
+
+/* One bisection step.  With m_ab = normalize(v_a + v_b), child j of parent
+ * (v0, v1, v2) is cell 4*parent + j:
+ *   j = 0: (m01, m12, m20)   j = 1: (v0, m01, m20)
+ *   j = 2: (m01, v1, m12)    j = 3: (m20, m12, v2) */
+static int refine(const ogrid *P, ogrid *C)
+{
+    int T, i;
+    if (grid_alloc(C, P->ref + 1, 4 * P->n_cells, P->n_verts + P->n_edges)) return -1;
+    for (i = 0; i < P->n_verts; ++i) C->vert[i] = P->vert[i];
+    for (T = 0; T < P->n_cells; ++T) {
+        int v0 = P->cv[3 * T], v1 = P->cv[3 * T + 1], v2 = P->cv[3 * T + 2];
+        int m01 = P->n_verts + P->edge[3 * T + 0];
+        int m12 = P->n_verts + P->edge[3 * T + 1];
+        int m20 = P->n_verts + P->edge[3 * T + 2];
+        int *c = &C->cv[12 * T];
+        C->vert[m01] = v_unit(v_add(P->vert[v0], P->vert[v1]));
+        C->vert[m12] = v_unit(v_add(P->vert[v1], P->vert[v2]));
+        C->vert[m20] = v_unit(v_add(P->vert[v2], P->vert[v0]));
+        c[0] = m01; c[1] = m12; c[2] = m20;
+        c[3] = v0;  c[4] = m01; c[5] = m20;
+        c[6] = m01; c[7] = v1;  c[8] = m12;
+        c[9] = m20; c[10] = m12; c[11] = v2;
+    }
+    return 0;
+}
+
+/* Geometry (Appendix A).  Reading C3: |T| is the spherical area and |S| the
+ * great-circle arc length.  The cell centre r_T is the spherical circumcentre
+ * (centre_kind 0): then r_T' - r_T is orthogonal to the shared edge, the
+ * condition under which the two-point flux of Appendix A is consistent.  The
+ * normalised vertex mean (centre_kind 1) is kept as an option. */
+static void compute_geometry(ogrid *G, int centre_kind)
+{
+    int T, e;
+    for (T = 0; T < G->n_cells; ++T) {
+        vec3 a = G->vert[G->cv[3 * T]], b = G->vert[G->cv[3 * T + 1]], c = G->vert[G->cv[3 * T + 2]];
+        /* spherical excess, Van Oosterom & Strackee: tan(E/2) = |a.(b x c)| / (1 + a.b + b.c + c.a);
+         * a.(b x c) is evaluated as a.((b - a) x (c - a)), equal in exact arithmetic,
+         * which keeps full relative precision for small cells. */
+        double num = fabs(v_dot(a, v_cross(v_sub(b, a), v_sub(c, a))));
+        double den = 1.0 + v_dot(a, b) + v_dot(b, c) + v_dot(c, a);
+        G->area[T] = 2.0 * atan2(num, den);
+        if (centre_kind == 0)
+            G->centre[T] = v_unit(v_cross(v_sub(b, a), v_sub(c, a)));  /* equidistant from a, b, c */
+        else
+            G->centre[T] = v_unit(v_add(v_add(a, b), c));
+    }
+    /* two-point flux factor g_TT' = |S_TT'| n_TT'.(r_T' - r_T) / |r_T' - r_T|^2,
+     * evaluated once per edge (from the cell with the smaller id) so that
+     * g_TT' == g_T'T exactly. */
+    for (T = 0; T < G->n_cells; ++T)
+        for (e = 0; e < 3; ++e) {
+            int Tp = G->nbr[3 * T + e], ep;
+            vec3 p, q, m, n, d;
+            double len, gval;
+            if (Tp < T) continue;
+            p = G->vert[G->cv[3 * T + e]];
+            q = G->vert[G->cv[3 * T + (e + 1) % 3]];
+            len = atan2(v_norm(v_cross(p, v_sub(q, p))), v_dot(p, q));   /* |p x q| = |p x (q - p)| */
+            m = v_unit(v_add(p, q));                 /* edge midpoint */
+            n = v_unit(v_cross(v_sub(q, p), m));     /* tangent to the sphere, normal to the edge */
+            d = v_sub(G->centre[Tp], G->centre[T]);
+            if (v_dot(n, d) < 0.0) n = v_scale(n, -1.0);
+            gval = len * v_dot(n, d) / v_dot(d, d);
+            G->g[3 * T + e] = gval;
+            for (ep = 0; ep < 3; ++ep)
+                if (G->nbr[3 * Tp + ep] == T) G->g[3 * Tp + ep] = gval;
+        }
+}
+
+/* Greedy colouring in cell-index order: smallest colour not taken by an
+ * already-coloured neighbour (Reading C4: multicolour block-SOR). */
+static void greedy_colour(ogrid *G)
+{
+    int T, e, c;
+    G->n_colours = 0;
+    for (T = 0; T < G->n_cells; ++T) {
+        int used[4] = {0, 0, 0, 0};
+        for (e = 0; e < 3; ++e) {
+            int Tp = G->nbr[3 * T + e];
+            if (Tp < T) used[G->colour[Tp]] = 1;
+        }
+        for (c = 0; c < 4 && used[c]; ++c) {}
+        G->colour[T] = c; /* a cubic graph never needs a fifth colour */
+        if (c + 1 > G->n_colours) G->n_colours = c + 1;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Oracle context                                                              */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int L, n_levels, n_r;
+    double H, grading, omega2, h_min;
+    int nu_pre, nu_post, nu_coarse, smoother; /* smoother: 0 multicolour block-SOR, 1 block-Jacobi */
+    int centre_kind;                          /* 0 circumcentre, 1 normalised vertex mean */
+    double relax;
+    ogrid *grid;          /* [L+1] refinement levels 0..L                     */
+    /* vertical grid (Appendix A), faces k = 0..n_r                           */
+    double *zeta;         /* [n_r+1] height r_k - 1                           */
+    double *r;            /* [n_r+1] r_k                                      */
+    double *dr;           /* [n_r]   r_{k+1} - r_k                            */
+    double *vol;          /* [n_r]   v_k = (r_{k+1}^3 - r_k^3)/3              */
+    double *arv;          /* [n_r+1] sigma_k 2 r_k^2 / (r_{k+1} - r_{k-1})    */
+    /* multigrid work arrays per multigrid level (0 = coarsest)               */
+    double **mg_f, **mg_u, **mg_r;
+    double *col_a, *col_b, *col_c, *col_d, *col_x, *col_cp, *col_dp;
+} octx;
+
+static const ogrid *mg_grid(const octx *o, int l) { return &o->grid[o->L - (o->n_levels - 1 - l)]; }
+
+/* Hat coefficients for unit profiles (eq. hatFunctionsNonFac).
+ * beta_hat_{T,k}        = |T| v_k
+ * alphaS_hat_{TT',k}    = omega^2 (r_{k+1} - r_k) g_TT'
+ * alphar_hat_{T,k}      = omega^2 sigma_k |T| 2 r_k^2 / (r_{k+1} - r_{k-1})   (face k)
+ * Reading C2: a single factor omega^2 in the horizontal term. */
+static double beta_hat(const octx *o, const ogrid *G, int T, int k) { return G->area[T] * o->vol[k]; }
+static double alphaS_hat(const octx *o, const ogrid *G, int T, int e, int k)
+{
+    return o->omega2 * o->dr[k] * G->g[3 * T + e];
+}
+static double alphar_hat(const octx *o, const ogrid *G, int T, int face)
+{
+    return o->omega2 * G->area[T] * o->arv[face];
+}
+
+/* Column T of the operator (eq. ColumnEquation, TridiagonalSystem; Reading C2):
+ *   (A u)_{T,k} = a_{T,k} u_{T,k} + b_{T,k} u_{T,k+1} + c_{T,k-1} u_{T,k-1}
+ *                 + sum_T' d_{TT',k} u_{T',k}
+ * with off-diagonals b_{T,k} = c_{T,k} = -alphar_hat_{T,k+1} (face k+1 couples
+ * levels k and k+1), d_{TT',k} = -alphaS_hat_{TT',k}, and diagonal
+ * a_{T,k} = beta_hat_{T,k} minus the sum of all off-diagonals of the row. */
+static void column_matrix(const octx *o, const ogrid *G, int T, double *sub, double *diag, double *sup)
+{
+    int k, e, n = o->n_r;
+    for (k = 0; k < n; ++k) {
+        double lo = alphar_hat(o, G, T, k), up = alphar_hat(o, G, T, k + 1), hs = 0.0;
+        for (e = 0; e < 3; ++e) hs += alphaS_hat(o, G, T, e, k);
+        sub[k] = -lo;
+        sup[k] = -up;
+        diag[k] = beta_hat(o, G, T, k) + lo + up + hs;
+    }
+}
+
+static void apply_level(octx *o, int l, const double *u, double *y)
+{
+    const ogrid *G = mg_grid(o, l);
+    int n = o->n_r, T, k, e;
+    for (T = 0; T < G->n_cells; ++T) {
+        column_matrix(o, G, T, o->col_a, o->col_b, o->col_c);
+        for (k = 0; k < n; ++k) {
+            double s = o->col_b[k] * u[(size_t)T * n + k];
+            if (k > 0) s += o->col_a[k] * u[(size_t)T * n + k - 1];
+            if (k < n - 1) s += o->col_c[k] * u[(size_t)T * n + k + 1];
+            for (e = 0; e < 3; ++e)
+                s -= alphaS_hat(o, G, T, e, k) * u[(size_t)G->nbr[3 * T + e] * n + k];
+            y[(size_t)T * n + k] = s;
+        }
+    }
+}
+
+/* Thomas algorithm for tridiag(a, b, c) x = d, no pivoting: forward
+ * elimination then back substitution.  a[0] and c[n-1] are not used. */
+int oracle_thomas(int n, const double *a, const double *b, const double *c, const double *d, double *x)
+{
+    double *cp, *dp;
+    int i;
+    if (n < 1) return -1;
+    cp = (double *)malloc((size_t)n * sizeof(double));
+    dp = (double *)malloc((size_t)n * sizeof(double));
+    if (!cp || !dp) { free(cp); free(dp); return -2; }
+    cp[0] = (n > 1) ? c[0] / b[0] : 0.0;
+    dp[0] = d[0] / b[0];
+    for (i = 1; i < n; ++i) {
+        double den = b[i] - a[i] * cp[i - 1];
+        cp[i] = (i < n - 1) ? c[i] / den : 0.0;
+        dp[i] = (d[i] - a[i] * dp[i - 1]) / den;
+    }
+    x[n - 1] = dp[n - 1];
+    for (i = n - 2; i >= 0; --i) x[i] = dp[i] - cp[i] * x[i + 1];
+    free(cp);
+    free(dp);
+    return 0;
+}
+
+/* Block relaxation of column T (eq. BlockJacobi):
+ *   u_T <- u_T + rho * A_T^{-1} (f_T - (A u)_T),
+ * A_T the tridiagonal diagonal block of the column. */
+static void relax_column(octx *o, int l, int T, const double *f, const double *u_in, double *u_out)
+{
+    const ogrid *G = mg_grid(o, l);
+    int n = o->n_r, k, e;
+    column_matrix(o, G, T, o->col_a, o->col_b, o->col_c);
+    for (k = 0; k < n; ++k) {
+        double s = o->col_b[k] * u_in[(size_t)T * n + k];
+        if (k > 0) s += o->col_a[k] * u_in[(size_t)T * n + k - 1];
+        if (k < n - 1) s += o->col_c[k] * u_in[(size_t)T * n + k + 1];
+        for (e = 0; e < 3; ++e)
+            s -= alphaS_hat(o, G, T, e, k) * u_in[(size_t)G->nbr[3 * T + e] * n + k];
+        o->col_d[k] = f[(size_t)T * n + k] - s;
+    }
+    oracle_thomas(n, o->col_a, o->col_b, o->col_c, o->col_d, o->col_x);
+    for (k = 0; k < n; ++k) u_out[(size_t)T * n + k] = u_in[(size_t)T * n + k] + o->relax * o->col_x[k];
+}
+
+/* Multicolour block-SOR: columns of one colour do not touch each other, so a
+ * sequential in-place sweep over the cells of colour c (index order) is the
+ * colour pass.  Reading C4: colour order 0..C-1 (forward) or C-1..0. */
+static void colour_pass(octx *o, int l, int c, const double *f, double *u)
+{
+    const ogrid *G = mg_grid(o, l);
+    int T;
+    for (T = 0; T < G->n_cells; ++T)
+        if (G->colour[T] == c) relax_column(o, l, T, f, u, u);
+}
+
+static void jacobi_sweep(octx *o, int l, const double *f, double *u)
+{
+    const ogrid *G = mg_grid(o, l);
+    size_t N = (size_t)G->n_cells * o->n_r;
+    double *old = (double *)malloc(N * sizeof(double));
+    int T;
+    memcpy(old, u, N * sizeof(double));
+    for (T = 0; T < G->n_cells; ++T) relax_column(o, l, T, f, old, u);
+    free(old);
+}
+
+/* dir = +1 forward colours, -1 reverse colours, 0 symmetric (forward then the
+ * reverse order without repeating the last colour). */
+static void smooth(octx *o, int l, const double *f, double *u, int sweeps, int dir)
+{
+    const ogrid *G = mg_grid(o, l);
+    int s, c;
+    for (s = 0; s < sweeps; ++s) {
+        if (o->smoother == 1) { jacobi_sweep(o, l, f, u); continue; }
+        if (dir >= 0)
+            for (c = 0; c < G->n_colours; ++c) colour_pass(o, l, c, f, u);
+        if (dir < 0)
+            for (c = G->n_colours - 1; c >= 0; --c) colour_pass(o, l, c, f, u);
+        if (dir == 0)
+            for (c = G->n_colours - 2; c >= 0; --c) colour_pass(o, l, c, f, u);
+    }
+}
+
+/* Restriction (Sec. 5: sum of the four fine cells of a coarse cell) and the
+ * prolongation P = R^T (Reading C5: piecewise-constant injection). */
+static void restrict_sum(const octx *o, int l_fine, const double *rf, double *fc)
+{
+    const ogrid *Gc = mg_grid(o, l_fine - 1);
+    int n = o->n_r, T, j, k;
+    for (T = 0; T < Gc->n_cells; ++T)
+        for (k = 0; k < n; ++k) {
+            double s = 0.0;
+            for (j = 0; j < 4; ++j) s += rf[(size_t)(4 * T + j) * n + k];
+            fc[(size_t)T * n + k] = s;
+        }
+}
+
+static void prolong_add(const octx *o, int l_fine, const double *uc, double *uf)
+{
+    const ogrid *Gc = mg_grid(o, l_fine - 1);
+    int n = o->n_r, T, j, k;
+    for (T = 0; T < Gc->n_cells; ++T)
+        for (j = 0; j < 4; ++j)
+            for (k = 0; k < n; ++k) uf[(size_t)(4 * T + j) * n + k] += uc[(size_t)T * n + k];
+}
+
+/* Algorithm 1 on multigrid level l with RHS f and initial guess u (in/out).
+ * Coarsest level: nu_coarse smoother sweeps (symmetric for block-SOR). */
+static void vcycle_level(octx *o, int l, const double *f, double *u)
+{
+    const ogrid *G = mg_grid(o, l);
+    size_t N = (size_t)G->n_cells * o->n_r, i;
+    if (l == 0) {
+        smooth(o, l, f, u, o->nu_coarse, 0);
+        return;
+    }
+    smooth(o, l, f, u, o->nu_pre, +1);                       /* pre-smoothing    */
+    apply_level(o, l, u, o->mg_r[l]);                        /* residual         */
+    for (i = 0; i < N; ++i) o->mg_r[l][i] = f[i] - o->mg_r[l][i];
+    restrict_sum(o, l, o->mg_r[l], o->mg_f[l - 1]);          /* f_{l-1} = R r_l  */
+    memset(o->mg_u[l - 1], 0, (size_t)mg_grid(o, l - 1)->n_cells * o->n_r * sizeof(double));
+    vcycle_level(o, l - 1, o->mg_f[l - 1], o->mg_u[l - 1]);  /* recursion        */
+    prolong_add(o, l, o->mg_u[l - 1], u);                    /* correction       */
+    smooth(o, l, f, u, o->nu_post, -1);                      /* post-smoothing   */
+}
+
+/* ------------------------------------------------------------------------- */
+/* Exported API (ctypes)                                                       */
+/* ------------------------------------------------------------------------- */
+void oracle_destroy(void *h)
+{
+    octx *o = (octx *)h;
+    int l;
+    if (!o) return;
+    if (o->grid)
+        for (l = 0; l <= o->L; ++l) grid_free(&o->grid[l]);
+    free(o->grid);
+    free(o->zeta); free(o->r); free(o->dr); free(o->vol); free(o->arv);
+    if (o->mg_f)
+        for (l = 0; l < o->n_levels; ++l) { free(o->mg_f[l]); free(o->mg_u[l]); free(o->mg_r[l]); }
+    free(o->mg_f); free(o->mg_u); free(o->mg_r);
+    free(o->col_a); free(o->col_b); free(o->col_c); free(o->col_d); free(o->col_x);
+    free(o->col_cp); free(o->col_dp);
+    free(o);
+}
+
+/* omega2 > 0 is used as given; otherwise omega^2 = courant_c * h_min^2 with
+ * h_min the smallest distance between neighbouring fine-level centres
+ * (Sec. 2: the Courant number omega/h uses the smallest spacing; Reading C1). */
+void *oracle_create(int refinement, int n_levels, int n_r, double H, double grading, double omega2,
+                    double courant_c, int nu_pre, int nu_post, int nu_coarse, int smoother, double relax,
+                    int centre_kind)
+{
+    octx *o;
+    int l, k, T, e;
+    if (refinement < 0 || refinement > 10 || n_levels < 1 || n_levels > refinement + 1 || n_r < 1 ||
+        !(H > 0.0) || !(grading > 0.0) || nu_pre < 0 || nu_post < 0 || nu_coarse < 0 ||
+        (smoother != 0 && smoother != 1) || (centre_kind != 0 && centre_kind != 1))
+        return NULL;
+    o = (octx *)calloc(1, sizeof(octx));
+    if (!o) return NULL;
+    o->L = refinement; o->n_levels = n_levels; o->n_r = n_r; o->H = H; o->grading = grading;
+    o->nu_pre = nu_pre; o->nu_post = nu_post; o->nu_coarse = nu_coarse;
+    o->smoother = smoother; o->relax = relax; o->centre_kind = centre_kind;
+    o->grid = (ogrid *)calloc((size_t)refinement + 1, sizeof(ogrid));
+    if (!o->grid || build_icosahedron(&o->grid[0]) || match_edges(&o->grid[0])) goto fail;
+    for (l = 1; l <= refinement; ++l)
+        if (refine(&o->grid[l - 1], &o->grid[l]) || match_edges(&o->grid[l])) goto fail;
+    for (l = 0; l <= refinement; ++l) {
+        compute_geometry(&o->grid[l], centre_kind);
+        greedy_colour(&o->grid[l]);
+    }
+    /* smallest centre distance on the finest level */
+    {
+        const ogrid *G = &o->grid[refinement];
+        o->h_min = HUGE_VAL;
+        for (T = 0; T < G->n_cells; ++T)
+            for (e = 0; e < 3; ++e) {
+                double d = v_norm(v_sub(G->centre[G->nbr[3 * T + e]], G->centre[T]));
+                if (d < o->h_min) o->h_min = d;
+            }
+    }
+    o->omega2 = omega2 > 0.0 ? omega2 : courant_c * o->h_min * o->h_min;
+    if (!(o->omega2 > 0.0)) goto fail;
+
+    /* Vertical grid (Appendix A; Reading C7: geometric grading, finest at the
+     * ground).  Heights zeta_k = r_k - 1 carry full relative precision. */
+    o->zeta = (double *)calloc((size_t)n_r + 1, sizeof(double));
+    o->r = (double *)calloc((size_t)n_r + 1, sizeof(double));
+    o->dr = (double *)calloc((size_t)n_r, sizeof(double));
+    o->vol = (double *)calloc((size_t)n_r, sizeof(double));
+    o->arv = (double *)calloc((size_t)n_r + 1, sizeof(double));
+    if (!o->zeta || !o->r || !o->dr || !o->vol || !o->arv) goto fail;
+    for (k = 0; k <= n_r; ++k) {
+        if (grading == 1.0) o->zeta[k] = H * (double)k / (double)n_r;
+        else o->zeta[k] = H * (pow(grading, (double)k) - 1.0) / (pow(grading, (double)n_r) - 1.0);
+    }
+    o->zeta[0] = 0.0;
+    o->zeta[n_r] = H;
+    for (k = 0; k <= n_r; ++k) o->r[k] = 1.0 + o->zeta[k];
+    for (k = 0; k < n_r; ++k) {
+        o->dr[k] = o->zeta[k + 1] - o->zeta[k];
+        /* v_k = (r_{k+1}^3 - r_k^3)/3 in factored form (Reading C8) */
+        o->vol[k] = o->dr[k] * (o->r[k + 1] * o->r[k + 1] + o->r[k + 1] * o->r[k] + o->r[k] * o->r[k]) / 3.0;
+    }
+    /* Neumann: sigma_0 = sigma_{n_r} = 0 (eq. VerticalDiffusion) */
+    for (k = 0; k <= n_r; ++k)
+        o->arv[k] = (k == 0 || k == n_r) ? 0.0 : 2.0 * o->r[k] * o->r[k] / (o->zeta[k + 1] - o->zeta[k - 1]);
+
+    o->mg_f = (double **)calloc((size_t)n_levels, sizeof(double *));
+    o->mg_u = (double **)calloc((size_t)n_levels, sizeof(double *));
+    o->mg_r = (double **)calloc((size_t)n_levels, sizeof(double *));
+    if (!o->mg_f || !o->mg_u || !o->mg_r) goto fail;
+    for (l = 0; l < n_levels; ++l) {
+        size_t N = (size_t)mg_grid(o, l)->n_cells * n_r;
+        o->mg_f[l] = (double *)calloc(N, sizeof(double));
+        o->mg_u[l] = (double *)calloc(N, sizeof(double));
+        o->mg_r[l] = (double *)calloc(N, sizeof(double));
+        if (!o->mg_f[l] || !o->mg_u[l] || !o->mg_r[l]) goto fail;
+    }
+    o->col_a = (double *)calloc((size_t)n_r, sizeof(double));
+    o->col_b = (double *)calloc((size_t)n_r, sizeof(double));
+    o->col_c = (double *)calloc((size_t)n_r, sizeof(double));
+    o->col_d = (double *)calloc((size_t)n_r, sizeof(double));
+    o->col_x = (double *)calloc((size_t)n_r, sizeof(double));
+    o->col_cp = (double *)calloc((size_t)n_r, sizeof(double));
+    o->col_dp = (double *)calloc((size_t)n_r, sizeof(double));
+    if (!o->col_a || !o->col_b || !o->col_c || !o->col_d || !o->col_x || !o->col_cp || !o->col_dp) goto fail;
+    return o;
+fail:
+    oracle_destroy(o);
+    return NULL;
+}
+
+/* scalars: [omega2, h_min, H, grading]; ints: [L, n_levels, n_r] */
+void oracle_info(const void *h, double *scalars, int *ints)
+{
+    const octx *o = (const octx *)h;
+    scalars[0] = o->omega2; scalars[1] = o->h_min; scalars[2] = o->H; scalars[3] = o->grading;
+    ints[0] = o->L; ints[1] = o->n_levels; ints[2] = o->n_r;
+}
+
+/* Per refinement level: n_cells, n_verts, n_edges, n_colours. */
+int oracle_grid_sizes(const void *h, int ref, int *out4)
+{
+    const octx *o = (const octx *)h;
+    if (ref < 0 || ref > o->L) return -1;
+    out4[0] = o->grid[ref].n_cells; out4[1] = o->grid[ref].n_verts;
+    out4[2] = o->grid[ref].n_edges; out4[3] = o->grid[ref].n_colours;
+    return 0;
+}
+
+/* Any output pointer may be NULL.  centre [n][3], area [n], nbr [n][3],
+ * g [n][3], colour [n], corners [n][3][3] (vertex positions of each cell). */
+int oracle_export_grid(const void *h, int ref, double *centre, double *area, int *nbr, double *g, int *colour,
+                       double *corners)
+{
+    const octx *o = (const octx *)h;
+    const ogrid *G;
+    int T, e;
+    if (ref < 0 || ref > o->L) return -1;
+    G = &o->grid[ref];
+    for (T = 0; T < G->n_cells; ++T) {
+        if (centre) { centre[3 * T] = G->centre[T].x; centre[3 * T + 1] = G->centre[T].y; centre[3 * T + 2] = G->centre[T].z; }
+        if (area) area[T] = G->area[T];
+        if (colour) colour[T] = G->colour[T];
+        for (e = 0; e < 3; ++e) {
+            if (nbr) nbr[3 * T + e] = G->nbr[3 * T + e];
+            if (g) g[3 * T + e] = G->g[3 * T + e];
+            if (corners) {
+                vec3 v = G->vert[G->cv[3 * T + e]];
+                corners[9 * T + 3 * e] = v.x; corners[9 * T + 3 * e + 1] = v.y; corners[9 * T + 3 * e + 2] = v.z;
+            }
+        }
+    }
+    return 0;
+}
+
+/* r_faces [n_r+1], dr [n_r], vol [n_r]; any may be NULL. */
+void oracle_export_vertical(const void *h, double *r_faces, double *dr, double *vol)
+{
+    const octx *o = (const octx *)h;
+    int k;
+    for (k = 0; k <= o->n_r; ++k) if (r_faces) r_faces[k] = o->r[k];
+    for (k = 0; k < o->n_r; ++k) { if (dr) dr[k] = o->dr[k]; if (vol) vol[k] = o->vol[k]; }
+}
+
+/* Multigrid level l (0 = coarsest) -> number of cells, or -1. */
+int oracle_level_cells(const void *h, int l)
+{
+    const octx *o = (const octx *)h;
+    if (l < 0 || l >= o->n_levels) return -1;
+    return mg_grid(o, l)->n_cells;
+}
+
+int oracle_apply(void *h, int l, const double *x, double *y)
+{
+    octx *o = (octx *)h;
+    if (l < 0 || l >= o->n_levels) return -1;
+    apply_level(o, l, x, y);
+    return 0;
+}
+
+/* Diagonal blocks of the column equation on level l: sub, diag, sup [n_cells][n_r]. */
+int oracle_column_blocks(void *h, int l, double *sub, double *diag, double *sup)
+{
+    octx *o = (octx *)h;
+    const ogrid *G;
+    int T;
+    if (l < 0 || l >= o->n_levels) return -1;
+    G = mg_grid(o, l);
+    for (T = 0; T < G->n_cells; ++T)
+        column_matrix(o, G, T, sub + (size_t)T * o->n_r, diag + (size_t)T * o->n_r, sup + (size_t)T * o->n_r);
+    return 0;
+}
+
+/* sweeps of the smoother on level l; dir = +1, -1 or 0 (symmetric). */
+int oracle_smooth(void *h, int l, const double *f, double *u, int sweeps, int dir)
+{
+    octx *o = (octx *)h;
+    if (l < 0 || l >= o->n_levels) return -1;
+    smooth(o, l, f, u, sweeps, dir);
+    return 0;
+}
+
+int oracle_restrict(void *h, int l_fine, const double *rf, double *fc)
+{
+    octx *o = (octx *)h;
+    if (l_fine < 1 || l_fine >= o->n_levels) return -1;
+    restrict_sum(o, l_fine, rf, fc);
+    return 0;
+}
+
+int oracle_prolong_add(void *h, int l_fine, const double *uc, double *uf)
+{
+    octx *o = (octx *)h;
+    if (l_fine < 1 || l_fine >= o->n_levels) return -1;
+    prolong_add(o, l_fine, uc, uf);
+    return 0;
+}
+
+/* One V-cycle on the finest level from a zero initial guess: z = B r. */
+int oracle_vcycle(void *h, const double *r, double *z)
+{
+    octx *o = (octx *)h;
+    int l = o->n_levels - 1;
+    memset(z, 0, (size_t)mg_grid(o, l)->n_cells * o->n_r * sizeof(double));
+    vcycle_level(o, l, r, z);
+    return 0;
+}
+
+static double dot(size_t N, const double *a, const double *b)
+{
+    double s = 0.0;
+    size_t i;
+    for (i = 0; i < N; ++i) s += a[i] * b[i];
+    return s;
+}
+
+/* Preconditioned conjugate gradients (the outer solver for the symmetric
+ * positive definite constant-profile operator), preconditioner B = one
+ * V-cycle.  u holds the initial guess on entry.  Stops when
+ * ||r_k||_2 <= rtol ||r_0||_2 on the recursively updated residual (Sec. 5:
+ * residual reduced by five orders of magnitude for rtol = 1e-5).
+ * iters = number of operator products q = A p.  hist (nullable, max_iter+1)
+ * receives ||r_k|| / ||r_0||.  true_rel (nullable) receives ||f - A u|| / ||r_0||.
+ * Returns 0 converged, 1 not converged, -3 breakdown (p.Ap <= 0 or non-finite). */
+int oracle_pcg(void *h, const double *f, double *u, double rtol, int max_iter, int *iters, double *rel_resid,
+               double *hist, double *true_rel)
+{
+    octx *o = (octx *)h;
+    int lf = o->n_levels - 1, it, status = 1;
+    size_t N = (size_t)mg_grid(o, lf)->n_cells * o->n_r, i;
+    double *r = (double *)malloc(N * sizeof(double));
+    double *z = (double *)malloc(N * sizeof(double));
+    double *p = (double *)malloc(N * sizeof(double));
+    double *q = (double *)malloc(N * sizeof(double));
+    double rz, rnorm0, rnorm;
+    if (!r || !z || !p || !q) { free(r); free(z); free(p); free(q); return -2; }
+    apply_level(o, lf, u, q);
+    for (i = 0; i < N; ++i) r[i] = f[i] - q[i];
+    rnorm0 = sqrt(dot(N, r, r));
+    *iters = 0;
+    *rel_resid = 1.0;
+    if (hist) hist[0] = 1.0;
+    if (!isfinite(rnorm0)) { status = -3; goto done; }
+    if (rnorm0 == 0.0) { *rel_resid = 0.0; status = 0; goto done; }
+    oracle_vcycle(h, r, z);
+    memcpy(p, z, N * sizeof(double));
+    rz = dot(N, r, z);
+    for (it = 0; it < max_iter; ++it) {
+        double pq, alpha, rz_new, beta;
+        apply_level(o, lf, p, q);
+        pq = dot(N, p, q);
+        if (!(pq > 0.0) || !isfinite(pq)) { status = -3; break; }
+        alpha = rz / pq;
+        for (i = 0; i < N; ++i) { u[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
+        rnorm = sqrt(dot(N, r, r));
+        *iters = it + 1;
+        *rel_resid = rnorm / rnorm0;
+        if (hist) hist[it + 1] = *rel_resid;
+        if (rnorm <= rtol * rnorm0) { status = 0; break; }
+        oracle_vcycle(h, r, z);
+        rz_new = dot(N, r, z);
+        beta = rz_new / rz;
+        rz = rz_new;
+        for (i = 0; i < N; ++i) p[i] = z[i] + beta * p[i];
+    }
+done:
+    if (true_rel) {
+        apply_level(o, lf, u, q);
+        for (i = 0; i < N; ++i) q[i] = f[i] - q[i];
+        *true_rel = rnorm0 > 0.0 ? sqrt(dot(N, q, q)) / rnorm0 : 0.0;
+    }
+    free(r); free(z); free(p); free(q);
+    return status;
+}
+
+/* Preconditioned Richardson iteration u <- u + B (f - A u), n_iter steps
+ * (Sec. 3.3).  hist (nullable, n_iter+1) receives ||f - A u_k||_2. */
+int oracle_richardson(void *h, const double *f, double *u, int n_iter, double *hist)
+{
+    octx *o = (octx *)h;
+    int lf = o->n_levels - 1, it;
+    size_t N = (size_t)mg_grid(o, lf)->n_cells * o->n_r, i;
+    double *r = (double *)malloc(N * sizeof(double));
+    double *z = (double *)malloc(N * sizeof(double));
+    if (!r || !z) { free(r); free(z); return -2; }
+    for (it = 0; it <= n_iter; ++it) {
+        apply_level(o, lf, u, r);
+        for (i = 0; i < N; ++i) r[i] = f[i] - r[i];
+        if (hist) hist[it] = sqrt(dot(N, r, r));
+        if (it == n_iter) break;
+        oracle_vcycle(h, r, z);
+        for (i = 0; i < N; ++i) u[i] += z[i];
+    }
+    free(r); free(z);
+    return 0;
+}

@@ -1,0 +1,147 @@
+"""Seeded synthetic inputs shared by the CUDA path and the CPU oracle.
+
+This module holds none of the solver's arithmetic: it only turns a seed into
+numbers.  Both sides of every parity check receive the identical bytes it
+produces.  Numpy only; no torch, no CUDA.
+
+* ``splitmix64`` -- Steele, Lea & Flood's SplitMix64 generator (counter-based:
+  output i is mix(seed + (i+1) * 0x9E3779B97F4A7C15)).
+* ``uniform_pm1`` -- 53-bit doubles in [-1, 1).
+* ``real_sph_harm`` -- orthonormal real spherical harmonics evaluated at points
+  of the unit sphere, from the three-term recurrence of the associated Legendre
+  functions.
+* ``manufactured_solution`` -- a sum of low-order spherical harmonics times
+  vertical cosines (the cosines satisfy the zero-flux vertical conditions).
+* ``smooth_field`` -- a random band-limited field on the shell.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+SEED_UNIFORM_SMALL = 2981001   # 1280 cells x 16 uniform levels, RHS uniform[-1, 1]
+SEED_MANUFACTURED = 2981002    # 81920 cells x 64 graded levels, manufactured solution
+SEED_MIXED = 2981003           # 327680 cells x 128 graded levels, RHS uniform[-1, 1]
+SEED_BATCH = 2981004           # batch of uneven problems
+SEED_LEARNED = 2981005         # learned coarse solve / warm start data
+SEED_SWEEP = 2981010           # n_r sweep
+
+
+def splitmix64(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """Outputs ``offset .. offset+n-1`` of the SplitMix64 stream for ``seed``."""
+    with np.errstate(over="ignore"):
+        i = np.arange(offset + 1, offset + n + 1, dtype=np.uint64)
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + i * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform01(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """53-bit doubles in [0, 1)."""
+    return (splitmix64(seed, n, offset) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def uniform_pm1(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """53-bit doubles in [-1, 1)."""
+    return 2.0 * uniform01(seed, n, offset) - 1.0
+
+
+def randint(seed: int, n: int, lo: int, hi: int, offset: int = 0) -> np.ndarray:
+    """Integers uniform in [lo, hi] (inclusive)."""
+    u = uniform01(seed, n, offset)
+    return lo + np.minimum(np.floor(u * (hi - lo + 1)), hi - lo).astype(np.int64)
+
+
+def real_sph_harm(l: int, m: int, xyz: np.ndarray) -> np.ndarray:
+    """Orthonormal real spherical harmonic Y_lm at unit vectors ``xyz`` [n, 3].
+
+    m > 0 uses cos(m phi), m < 0 uses sin(|m| phi); no Condon-Shortley phase.
+    """
+    if l < 0 or abs(m) > l:
+        raise ValueError("need 0 <= |m| <= l")
+    xyz = np.asarray(xyz, dtype=np.float64)
+    x, y, z = xyz[:, 0], xyz[:, 1], xyz[:, 2]
+    ct = np.clip(z, -1.0, 1.0)
+    st = np.sqrt(np.maximum(0.0, 1.0 - ct * ct))
+    phi = np.arctan2(y, x)
+    am = abs(m)
+    # P_am^am = (2am-1)!! st^am, then the upward recurrence in l
+    pmm = np.ones_like(ct)
+    for i in range(1, am + 1):
+        pmm = pmm * (2 * i - 1) * st
+    if l == am:
+        plm = pmm
+    else:
+        pm1 = ct * (2 * am + 1) * pmm
+        if l == am + 1:
+            plm = pm1
+        else:
+            p_prev, p_cur = pmm, pm1
+            for ll in range(am + 2, l + 1):
+                p_next = ((2 * ll - 1) * ct * p_cur - (ll + am - 1) * p_prev) / (ll - am)
+                p_prev, p_cur = p_cur, p_next
+            plm = p_cur
+    norm = math.sqrt((2 * l + 1) / (4 * math.pi) * math.factorial(l - am) / math.factorial(l + am))
+    if m == 0:
+        return norm * plm
+    if m > 0:
+        return math.sqrt(2.0) * norm * plm * np.cos(am * phi)
+    return math.sqrt(2.0) * norm * plm * np.sin(am * phi)
+
+
+def manufactured_params(seed: int, n_terms: int = 8, l_max: int = 4, n_max: int = 3) -> list[tuple]:
+    """(a_i, l_i, m_i, n_i) for the manufactured solution, all drawn from ``seed``."""
+    u = uniform01(seed, 4 * n_terms)
+    out = []
+    for i in range(n_terms):
+        l = int(min(math.floor(u[4 * i] * (l_max + 1)), l_max))
+        m = int(min(math.floor(u[4 * i + 1] * (2 * l + 1)), 2 * l)) - l
+        n = int(min(math.floor(u[4 * i + 2] * (n_max + 1)), n_max))
+        a = 2.0 * float(u[4 * i + 3]) - 1.0
+        out.append((a, l, m, n))
+    return out
+
+
+def manufactured_solution(centres: np.ndarray, r_faces: np.ndarray, seed: int,
+                          n_terms: int = 8, l_max: int = 4, n_max: int = 3) -> np.ndarray:
+    """u*[T, k] = sum_i a_i Y_{l_i m_i}(c_T) cos(n_i pi (r_{k+1/2} - 1) / H), flattened [T][k].
+
+    ``centres`` [n_cells, 3] unit vectors, ``r_faces`` [n_r + 1] radii of the
+    level faces, ``H = r_faces[-1] - r_faces[0]``.
+    """
+    centres = np.asarray(centres, dtype=np.float64)
+    r_faces = np.asarray(r_faces, dtype=np.float64)
+    H = r_faces[-1] - r_faces[0]
+    zmid = 0.5 * (r_faces[:-1] + r_faces[1:]) - r_faces[0]
+    u = np.zeros((centres.shape[0], zmid.shape[0]))
+    for a, l, m, n in manufactured_params(seed, n_terms, l_max, n_max):
+        u += a * np.outer(real_sph_harm(l, m, centres), np.cos(n * math.pi * zmid / H))
+    return u.reshape(-1)
+
+
+def smooth_field(centres: np.ndarray, r_faces: np.ndarray, seed: int, l_max: int = 16,
+                 n_max: int = 3, decay: float = 1.0) -> np.ndarray:
+    """Random band-limited field: sum over l <= l_max, |m| <= l, n <= n_max of
+    c_{lmn} Y_lm(c_T) cos(n pi z / H), c uniform[-1, 1] / (1 + l)^decay."""
+    centres = np.asarray(centres, dtype=np.float64)
+    r_faces = np.asarray(r_faces, dtype=np.float64)
+    H = r_faces[-1] - r_faces[0]
+    zmid = 0.5 * (r_faces[:-1] + r_faces[1:]) - r_faces[0]
+    n_coef = (l_max + 1) ** 2 * (n_max + 1)
+    c = uniform_pm1(seed, n_coef)
+    out = np.zeros((centres.shape[0], zmid.shape[0]))
+    idx = 0
+    for l in range(l_max + 1):
+        for m in range(-l, l + 1):
+            y = real_sph_harm(l, m, centres) / (1.0 + l) ** decay
+            for n in range(n_max + 1):
+                out += c[idx] * np.outer(y, np.cos(n * math.pi * zmid / H))
+                idx += 1
+    return out.reshape(-1)

@@ -1,0 +1,504 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each ``pin_*`` function takes a namespace ``ns`` with ``ns.Oracle`` (the oracle
+class, or a variant bound to another build of the oracle) and ``ns.thomas``, and
+raises ``AssertionError`` when the oracle disagrees with the fixed fact.  The
+pins are used twice: on the real oracle (``test_oracle_pins.py``) and on
+copies of the oracle with a planted mistake (``test_oracle_mutants.py``), which
+must each fail at least one pin.
+
+Citations are to Dedner, Mueller & Scheichl, arXiv:1408.2981.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.linalg as sla
+
+from paper_1408_2981_gb300 import inputs
+
+EPS = np.finfo(np.float64).eps
+FOUR_PI = 4.0 * math.pi
+
+
+# ----------------------------------------------------------------------------- grid
+def pin_mesh_counts(ns, max_ref: int = 4):
+    """Sec. 4.1: each coarse triangle holds four fine ones.  A closed triangulated
+    sphere refined by bisection has F = 20*4^L, E = 30*4^L, V = 10*4^L + 2 (Euler V-E+F = 2)."""
+    o = ns.Oracle(refinement=max_ref, n_levels=1, n_r=1)
+    for ref in range(max_ref + 1):
+        s = o.grid_sizes(ref)
+        assert s["n_cells"] == 20 * 4 ** ref
+        assert s["n_edges"] == 30 * 4 ** ref
+        assert s["n_verts"] == 10 * 4 ** ref + 2
+        assert s["n_verts"] - s["n_edges"] + s["n_cells"] == 2
+
+
+def pin_mesh_areas(ns, max_ref: int = 5):
+    """Spherical areas tile the unit sphere (sum 4 pi); the four children of a cell
+    tile it exactly; the 20 faces of the icosahedron are congruent (4 pi / 20)."""
+    o = ns.Oracle(refinement=max_ref, n_levels=1, n_r=1)
+    prev = None
+    for ref in range(max_ref + 1):
+        a = o.grid(ref)["area"]
+        assert abs(a.sum() - FOUR_PI) <= 64 * EPS * FOUR_PI
+        if ref == 0:
+            np.testing.assert_allclose(a, FOUR_PI / 20.0, rtol=16 * EPS, atol=0)
+        if prev is not None:
+            np.testing.assert_allclose(a.reshape(-1, 4).sum(axis=1), prev, rtol=32 * EPS * 2 ** ref, atol=0)
+        prev = a
+
+
+def pin_level0_closed_forms(ns):
+    """Regular icosahedron: adjacent vertices subtend arccos(1/sqrt5); adjacent face
+    centres subtend pi - dihedral = arccos(sqrt5/3); by symmetry the centre chord is
+    normal to the shared edge, so g = |S| / |r_T' - r_T| for every edge (Appendix A)."""
+    S = math.acos(1.0 / math.sqrt(5.0))
+    theta = math.acos(math.sqrt(5.0) / 3.0)
+    d = 2.0 * math.sin(0.5 * theta)
+    for ck in (0, 1):
+        o = ns.Oracle(refinement=0, n_levels=1, n_r=1, centre_kind=ck)
+        g = o.grid(0)
+        np.testing.assert_allclose(g["g"], S / d, rtol=64 * EPS, atol=0)
+        c = g["centre"]
+        for T in range(20):
+            for e in range(3):
+                Tp = g["nbr"][T, e]
+                np.testing.assert_allclose(np.linalg.norm(c[Tp] - c[T]), d, rtol=64 * EPS)
+        corners = g["corners"]
+        dots = np.einsum("tij,tj->ti", corners, c)
+        np.testing.assert_allclose(dots, dots[0, 0], rtol=64 * EPS)
+
+
+def pin_mesh_topology(ns, max_ref: int = 4):
+    """Neighbour relation symmetric, cells counter-clockwise seen from outside,
+    the centre child 4T of a refined cell borders exactly its three siblings,
+    colouring valid with <= 4 colours, g_TT' > 0 and g_TT' = g_T'T, vertices and
+    centres on the unit sphere, circumcentres equidistant from the corners."""
+    for ck in (0, 1):
+        o = ns.Oracle(refinement=max_ref, n_levels=1, n_r=1, centre_kind=ck)
+        for ref in range(max_ref + 1):
+            g = o.grid(ref)
+            n = g["area"].shape[0]
+            nbr, gg, col, cen, cor = g["nbr"], g["g"], g["colour"], g["centre"], g["corners"]
+            assert np.all((nbr >= 0) & (nbr < n))
+            for T in range(n):
+                for e in range(3):
+                    Tp = nbr[T, e]
+                    assert Tp != T
+                    back = np.where(nbr[Tp] == T)[0]
+                    assert back.shape[0] == 1
+                    assert gg[Tp, back[0]] == gg[T, e]
+                    assert col[Tp] != col[T]
+                    # the shared edge is (v_e, v_e+1) of T and appears reversed in T'
+                    p, q = cor[T, e], cor[T, (e + 1) % 3]
+                    ep = back[0]
+                    np.testing.assert_array_equal(cor[Tp, ep], q)
+                    np.testing.assert_array_equal(cor[Tp, (ep + 1) % 3], p)
+            assert col.max() <= 3 and col.min() >= 0
+            assert np.all(gg > 0)
+            np.testing.assert_allclose(np.linalg.norm(cor, axis=2), 1.0, rtol=4 * EPS)
+            np.testing.assert_allclose(np.linalg.norm(cen, axis=1), 1.0, rtol=4 * EPS)
+            orient = np.einsum("ti,ti->t", np.cross(cor[:, 1] - cor[:, 0], cor[:, 2] - cor[:, 0]), cen)
+            assert np.all(orient > 0)
+            if ck == 0:
+                dd = np.einsum("tij,tj->ti", cor, cen)
+                np.testing.assert_allclose(dd, dd[:, :1] * np.ones((1, 3)), rtol=64 * EPS)
+            if ref > 0:
+                for T in range(n // 4):
+                    assert sorted(nbr[4 * T].tolist()) == [4 * T + 1, 4 * T + 2, 4 * T + 3]
+                # children lie inside the parent: corners of child j=1..3 include a parent corner
+                gp = o.grid(ref - 1)["corners"]
+                for T in range(n // 4):
+                    np.testing.assert_array_equal(cor[4 * T + 1, 0], gp[T, 0])
+                    np.testing.assert_array_equal(cor[4 * T + 2, 1], gp[T, 1])
+                    np.testing.assert_array_equal(cor[4 * T + 3, 2], gp[T, 2])
+
+
+def pin_vertical(ns):
+    """Appendix A: 1 = r_0 < ... < r_nr = 1 + H; v_k = (r_{k+1}^3 - r_k^3)/3, so the
+    v_k telescope to ((1+H)^3 - 1)/3 and equal dr (r_mid^2 + dr^2/12) exactly;
+    geometric grading has a constant ratio dr_{k+1}/dr_k."""
+    for n_r, gr, H in [(16, 1.0, 10.0 / 6371.0), (64, 1.05, 10.0 / 6371.0), (7, 1.3, 0.5), (1, 1.0, 0.25)]:
+        o = ns.Oracle(refinement=0, n_levels=1, n_r=n_r, H=H, grading=gr)
+        v = o.vertical()
+        r, dr, vol = v["r"], v["dr"], v["vol"]
+        assert r[0] == 1.0 and abs(r[-1] - (1.0 + H)) <= EPS
+        assert np.all(dr > 0)
+        assert abs(dr.sum() - H) <= 8 * n_r * EPS * H
+        exact = H * (3.0 + 3.0 * H + H * H) / 3.0
+        assert abs(vol.sum() - exact) <= 8 * n_r * EPS * exact
+        rm = 0.5 * (r[:-1] + r[1:])
+        np.testing.assert_allclose(vol, dr * (rm * rm + dr * dr / 12.0), rtol=16 * EPS)
+        if gr == 1.0:
+            np.testing.assert_allclose(dr, H / n_r, rtol=1e-10)
+        else:
+            np.testing.assert_allclose(dr[1:] / dr[:-1], gr, rtol=1e-9)
+
+
+# ----------------------------------------------------------------------------- operator
+SMALL_CASES = [
+    dict(refinement=1, n_levels=2, n_r=5, grading=1.2, H=0.05, courant_c=8.0),
+    dict(refinement=2, n_levels=3, n_r=3, grading=1.0, courant_c=80.0),
+    dict(refinement=0, n_levels=1, n_r=9, grading=1.05, courant_c=8.0, centre_kind=1),
+]
+
+
+def _vertical_matrix(o):
+    """The vertical factor K = diag(v) + omega^2 V^r of the Kronecker form
+    (Sec. 3.3, A = (omega^2 A^r + B^r) (x) M^S + omega^2 M^r (x) A^S), from the
+    exported vertical grid: face coupling 2 r_k^2 / (r_{k+1} - r_{k-1}) (eq. VerticalDiffusion)."""
+    v = o.vertical()
+    r, vol = v["r"], v["vol"]
+    n_r = o.n_r
+    z = r - 1.0
+    a = np.zeros(n_r + 1)
+    if n_r > 1:
+        a[1:n_r] = 2.0 * r[1:n_r] ** 2 / (z[2:] - z[:-2])
+    Vr = np.diag(a[:-1] + a[1:]) - np.diag(a[1:-1], 1) - np.diag(a[1:-1], -1)
+    return np.diag(vol) + o.omega2 * Vr, np.diag(v["dr"])
+
+
+def _horizontal_laplacian(g):
+    n = g["area"].shape[0]
+    Lh = np.zeros((n, n))
+    for T in range(n):
+        for e in range(3):
+            Lh[T, T] += g["g"][T, e]
+            Lh[T, g["nbr"][T, e]] -= g["g"][T, e]
+    return Lh
+
+
+def pin_constants_in_kernel(ns):
+    """The diffusion terms are flux differences that vanish on constants
+    (Appendix A), so A 1 = beta_hat = |T| v_k on every level."""
+    for kw in SMALL_CASES + [dict(refinement=4, n_levels=3, n_r=16, grading=1.05, courant_c=80.0)]:
+        o = ns.Oracle(**kw)
+        v = o.vertical()
+        for level in range(o.n_levels):
+            g = o.grid(o.level_ref(level))
+            y = o.apply(np.ones(o.size(level)), level)
+            beta = np.outer(g["area"], v["vol"]).reshape(-1)
+            sub, diag, sup = o.column_blocks(level)
+            bound = 16 * EPS * 2.0 * diag.reshape(-1)
+            assert np.all(np.abs(y - beta) <= bound), np.max(np.abs(y - beta) / bound)
+
+
+def pin_symmetric_spd(ns):
+    """With xi = 0 and constant profiles the operator is symmetric positive
+    definite (Sec. 3.3); the two-point fluxes also make it an M-matrix: positive
+    diagonal, non-positive off-diagonals, strict diagonal dominance (beta_hat > 0)."""
+    for kw in SMALL_CASES:
+        o = ns.Oracle(**kw)
+        for level in range(o.n_levels):
+            A = o.dense_operator(level)
+            assert np.array_equal(A, A.T)
+            np.linalg.cholesky(A)
+            off = A - np.diag(np.diag(A))
+            assert np.all(off <= 0)
+            assert np.all(np.diag(A) > -off.sum(axis=1))
+
+
+def pin_kronecker(ns):
+    """Sec. 3.3: for factorising profiles A = diag|T| (x) (diag v + omega^2 V^r)
+    + omega^2 L^S (x) diag(dr), assembled here from small matrices and compared
+    entry by entry with the matrix-free operator."""
+    for kw in SMALL_CASES:
+        o = ns.Oracle(**kw)
+        K, M = _vertical_matrix(o)
+        for level in range(o.n_levels):
+            g = o.grid(o.level_ref(level))
+            Ak = np.kron(np.diag(g["area"]), K) + o.omega2 * np.kron(_horizontal_laplacian(g), M)
+            A = o.dense_operator(level)
+            # 1e-11: the heights are rebuilt here as r - 1, which costs ~1e-14 relative
+            assert np.all(np.abs(A - Ak) <= 1e-11 * np.abs(Ak) + 1e-300), np.max(np.abs(A - Ak) / np.abs(Ak))
+
+
+def pin_horizontal_consistency(ns):
+    """Spherical harmonics are eigenfunctions of the Laplace-Beltrami operator
+    (eigenvalue -l(l+1)).  With n_r = 1 the horizontal part of A divided by
+    omega^2 dr is a two-point-flux Laplacian L^S; its Rayleigh quotient on Y_lm
+    relative to the area-weighted mass must converge to l(l+1) at second order."""
+    o = ns.Oracle(refinement=5, n_levels=1, n_r=1, omega2=1.0)
+    v = o.vertical()
+    for l, m in [(1, 0), (2, 1), (3, -2), (4, 3)]:
+        errs = []
+        for ref in (3, 4, 5):
+            oo = ns.Oracle(refinement=ref, n_levels=1, n_r=1, omega2=1.0)
+            g = oo.grid(ref)
+            u = inputs.real_sph_harm(l, m, g["centre"])
+            hor = (oo.apply(u) - g["area"] * v["vol"][0] * u) / (oo.omega2 * v["dr"][0])
+            rq = (u @ hor) / (u @ (g["area"] * u))
+            errs.append(abs(rq - l * (l + 1)))
+        assert errs[-1] < 2e-3 * l * (l + 1), errs
+        assert errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.5, errs
+
+
+def pin_vertical_consistency(ns):
+    """Vertical part: for u = cos(n pi (r - 1)/H), constant on the sphere, the
+    horizontal fluxes vanish and (A u)_k / (|T| v_k) must approach the continuous
+    u - omega^2 r^-2 d/dr (r^2 du/dr) at the cell centres, at second order on a
+    uniform grid (Appendix A, eq. VerticalDiffusion).  H = 0.5 makes the r^2
+    metric terms visible."""
+    H, n = 0.5, 2
+    errs = []
+    for n_r in (16, 32, 64):
+        o = ns.Oracle(refinement=0, n_levels=1, n_r=n_r, H=H, omega2=0.01)
+        g, v = o.grid(0), o.vertical()
+        r = v["r"]
+        zc = 0.5 * (r[:-1] + r[1:]) - 1.0
+        # cell averages of cos(kz) over each cell, weighted by r^2 (finite-volume unknowns)
+        kk = n * math.pi / H
+        u_col = np.cos(kk * zc)
+        u = np.tile(u_col, 20)
+        y = o.apply(u).reshape(20, n_r) / np.outer(g["area"], v["vol"])
+        rc = 1.0 + zc
+        lu = u_col + o.omega2 * (kk * kk * np.cos(kk * zc) + (2.0 / rc) * kk * np.sin(kk * zc))
+        interior = slice(1, n_r - 1)
+        errs.append(np.max(np.abs(y[0, interior] - lu[interior])) / np.max(np.abs(lu)))
+        assert np.allclose(y, y[0:1, :], rtol=1e-12, atol=1e-12 * np.max(np.abs(y)))
+    assert errs[0] / errs[1] > 3.0 and errs[1] / errs[2] > 3.0, errs
+
+
+# ----------------------------------------------------------------------------- Thomas
+def pin_thomas(ns):
+    """Thomas algorithm (Sec. 4.1) against dense LU with partial pivoting on random
+    diagonally dominant systems, n = 1..16, and on actual column blocks A_T."""
+    rng = np.random.default_rng(5)
+    for n in range(1, 17):
+        for _ in range(5):
+            a = rng.uniform(-1, 1, n)
+            c = rng.uniform(-1, 1, n)
+            b = np.abs(a) + np.abs(c) + rng.uniform(0.1, 2.0, n)
+            d = rng.uniform(-1, 1, n)
+            Ad = np.diag(b) + np.diag(a[1:], -1) + np.diag(c[:-1], 1)
+            x = ns.thomas(a, b, c, d)
+            xd = np.linalg.solve(Ad, d)
+            np.testing.assert_allclose(x, xd, rtol=1e-13, atol=1e-13 * np.max(np.abs(xd)))
+    o = ns.Oracle(refinement=2, n_levels=1, n_r=16, grading=1.05, courant_c=80.0)
+    sub, diag, sup = o.column_blocks()
+    A = o.dense_operator() if o.size() <= 6000 else None
+    for T in (0, 7, 100, 319):
+        d = rng.uniform(-1, 1, o.n_r)
+        x = ns.thomas(sub[T], diag[T], sup[T], d)
+        blk = A[T * o.n_r:(T + 1) * o.n_r, T * o.n_r:(T + 1) * o.n_r]
+        xd = np.linalg.solve(blk, d)
+        np.testing.assert_allclose(x, xd, rtol=1e-10, atol=1e-12 * np.max(np.abs(xd)))
+
+
+# ----------------------------------------------------------------------------- transfers
+def pin_transfers(ns):
+    """Restriction sums the four children (Sec. 5); prolongation is its transpose
+    (P = R^T): <R x, y> = <x, P y>.  Restricting the fine cell areas (times any
+    vertical profile) gives the coarse areas, because the children tile the parent."""
+    o = ns.Oracle(refinement=3, n_levels=3, n_r=4)
+    rng = np.random.default_rng(11)
+    for lf in (1, 2):
+        gf, gc = o.grid(o.level_ref(lf)), o.grid(o.level_ref(lf - 1))
+        x = rng.uniform(-1, 1, o.size(lf))
+        y = rng.uniform(-1, 1, o.size(lf - 1))
+        Rx = o.restrict(x, lf)
+        Py = o.prolong_add(y, np.zeros(o.size(lf)), lf)
+        assert abs(Rx @ y - x @ Py) <= 1e-13 * (np.abs(Rx) @ np.abs(y))
+        prof = np.arange(1.0, o.n_r + 1.0)
+        ra = o.restrict(np.outer(gf["area"], prof).reshape(-1), lf)
+        np.testing.assert_allclose(ra, np.outer(gc["area"], prof).reshape(-1), rtol=1e-13)
+        base = rng.uniform(-1, 1, o.size(lf))
+        np.testing.assert_allclose(o.prolong_add(y, base, lf) - base, Py, rtol=1e-14, atol=1e-15)
+
+
+# ----------------------------------------------------------------------------- smoother / V-cycle
+def dense_vcycle(o, r):
+    """Algorithm 1 written with dense matrices (tiny grids): smoother
+    u <- u + rho A_T^{-1}(f - A u)_T column by column (eq. BlockJacobi) grouped by
+    colour (forward colours before, reverse colours after the coarse-grid
+    correction, forward-then-reverse on the coarsest level), or all columns at
+    once (block Jacobi); R sums children, P = R^T."""
+    n_r = o.n_r
+    As = [o.dense_operator(l) for l in range(o.n_levels)]
+    cols = [o.grid(o.level_ref(l))["colour"] for l in range(o.n_levels)]
+
+    def relax(l, f, u, cells):
+        res = f - As[l] @ u
+        u = u.copy()
+        for T in cells:
+            s = slice(T * n_r, (T + 1) * n_r)
+            u[s] += o.relax * np.linalg.solve(As[l][s, s], res[s])
+        return u
+
+    def sweep(l, f, u, order):
+        if o.smoother == 1:
+            return relax(l, f, u, range(cols[l].shape[0]))
+        for c in order:
+            u = relax(l, f, u, np.where(cols[l] == c)[0])
+        return u
+
+    def R(l, x):
+        return x.reshape(-1, 4, n_r).sum(axis=1).reshape(-1)
+
+    def P(l, x):
+        return np.repeat(x.reshape(-1, 1, n_r), 4, axis=1).reshape(-1)
+
+    def cycle(l, f, u):
+        nc = int(cols[l].max()) + 1
+        fwd, rev = list(range(nc)), list(range(nc - 1, -1, -1))
+        if l == 0:
+            for _ in range(o.nu_coarse):
+                u = sweep(l, f, u, fwd + list(range(nc - 2, -1, -1)))
+            return u
+        for _ in range(o.nu_pre):
+            u = sweep(l, f, u, fwd)
+        rc = R(l, f - As[l] @ u)
+        uc = cycle(l - 1, rc, np.zeros(rc.shape[0]))
+        u = u + P(l, uc)
+        for _ in range(o.nu_post):
+            u = sweep(l, f, u, rev)
+        return u
+
+    return cycle(o.n_levels - 1, r, np.zeros_like(r))
+
+
+VCYCLE_CASES = [
+    dict(refinement=2, n_levels=3, n_r=4, grading=1.1, courant_c=8.0, nu_pre=1, nu_post=1, nu_coarse=1),
+    dict(refinement=2, n_levels=2, n_r=3, courant_c=80.0, nu_pre=2, nu_post=2, nu_coarse=2),
+    dict(refinement=2, n_levels=3, n_r=4, courant_c=8.0, nu_pre=2, nu_post=2, nu_coarse=1, smoother=1, relax=0.5),
+    dict(refinement=1, n_levels=2, n_r=6, courant_c=30.0, nu_pre=1, nu_post=1, nu_coarse=1, relax=0.8),
+]
+
+
+def pin_vcycle_dense(ns):
+    """The matrix-free V-cycle equals Algorithm 1 written with dense matrices."""
+    rng = np.random.default_rng(3)
+    for kw in VCYCLE_CASES:
+        o = ns.Oracle(**kw)
+        r = rng.uniform(-1, 1, o.size())
+        z = o.vcycle(r)
+        zd = dense_vcycle(o, r)
+        # the column blocks have condition numbers up to ~1e7 (vertical coupling over
+        # mass term ~ omega^2/dr^2), so two exact-in-theory solves agree to ~1e-9
+        np.testing.assert_allclose(z, zd, rtol=1e-8, atol=1e-10 * np.max(np.abs(zd)))
+
+
+def pin_preconditioner_symmetric(ns):
+    """Symmetric smoothing (reverse colour order after the correction, symmetric
+    coarsest sweep, nu_pre = nu_post) and P = R^T make the V-cycle B symmetric;
+    positive definite because it converges.  CG needs both."""
+    rng = np.random.default_rng(4)
+    for kw in VCYCLE_CASES + [dict(refinement=3, n_levels=4, n_r=16, courant_c=8.0, nu_pre=1, nu_post=1)]:
+        o = ns.Oracle(**kw)
+        for _ in range(3):
+            x = rng.uniform(-1, 1, o.size())
+            y = rng.uniform(-1, 1, o.size())
+            bx, by = o.vcycle(x), o.vcycle(y)
+            # rounding in the column solves is amplified by their condition number (~1e7)
+            assert abs(bx @ y - x @ by) <= 1e-10 * np.linalg.norm(bx) * np.linalg.norm(y)
+            assert bx @ x > 0
+
+
+def pin_invariant_subspaces(ns):
+    """Sec. 3.3 (reduction to two dimensions): with (omega^2 A^r + B^r) e_j =
+    lambda_j M^r e_j, A maps e_j (x) V^S into M^r e_j (x) V^S, the block smoother
+    keeps e_j (x) V^S invariant, and the V-cycle maps M^r e_j (x) V^S into
+    e_j (x) V^S; components along the other e_i stay at rounding level."""
+    rng = np.random.default_rng(9)
+    for kw in [dict(refinement=2, n_levels=3, n_r=6, grading=1.2, H=0.05, courant_c=8.0, nu_pre=1, nu_post=1),
+               dict(refinement=2, n_levels=2, n_r=5, H=0.05, courant_c=20.0, smoother=1, relax=0.5)]:
+        o = ns.Oracle(**kw)
+        K, M = _vertical_matrix(o)
+        lam, E = sla.eigh(K, M)           # E^T M E = I
+        nc = o.level_cells(o.n_levels - 1)
+        for j in (0, o.n_r // 2, o.n_r - 1):
+            w = rng.uniform(-1, 1, nc)
+            others = [i for i in range(o.n_r) if i != j]
+            u = np.outer(w, E[:, j]).reshape(-1)
+            Au = o.apply(u).reshape(nc, o.n_r) @ E           # coefficients along M e_i
+            assert np.max(np.abs(Au[:, others])) <= 1e-9 * np.max(np.abs(Au[:, j]))
+            Su = o.smooth(np.zeros_like(u), u, 1, 1).reshape(nc, o.n_r) @ (M @ E)
+            assert np.max(np.abs(Su[:, others])) <= 1e-9 * np.max(np.abs(Su[:, j]))
+            x = np.outer(w, M @ E[:, j]).reshape(-1)
+            Bx = o.vcycle(x).reshape(nc, o.n_r) @ (M @ E)
+            assert np.max(np.abs(Bx[:, others])) <= 1e-9 * np.max(np.abs(Bx[:, j]))
+
+
+# ----------------------------------------------------------------------------- solver
+def pin_pcg_dense(ns):
+    """PCG to rtol 1e-13 reproduces the dense direct solution A^{-1} f.
+
+    On shells of moderate aspect ratio (H = 0.1, cond(A) <= ~1e6) the match is
+    required to 1e-10 in the 2-norm.  At the atmospheric aspect ratio
+    (H = 10/6371) cond(A) reaches ~1e9 through the barely damped vertically
+    constant mode, and two backward-stable direct solvers (Cholesky, LU) already
+    disagree by ~1e-9; there PCG must agree with Cholesky in the energy norm to
+    within 10x that disagreement (floor 1e-12)."""
+    cases = [dict(refinement=0, n_levels=1, n_r=8, grading=1.1, H=0.1, courant_c=8.0),
+             dict(refinement=1, n_levels=2, n_r=8, H=0.1, courant_c=80.0, nu_pre=1, nu_post=1),
+             dict(refinement=2, n_levels=3, n_r=8, grading=1.05, H=0.1, courant_c=8.0),
+             dict(refinement=2, n_levels=2, n_r=4, H=0.1, courant_c=20.0, smoother=1, relax=0.5)]
+    for kw in cases:
+        o = ns.Oracle(**kw)
+        f = inputs.uniform_pm1(inputs.SEED_UNIFORM_SMALL, o.size())
+        res = o.pcg(f, rtol=1e-13, max_iter=300)
+        assert res["status"] == 0
+        A = o.dense_operator()
+        ud = sla.cho_solve(sla.cho_factor(A), f)
+        assert np.linalg.norm(res["u"] - ud) <= 1e-10 * np.linalg.norm(ud)
+    for kw in [dict(refinement=1, n_levels=2, n_r=8, courant_c=80.0, nu_pre=1, nu_post=1),
+               dict(refinement=2, n_levels=3, n_r=8, grading=1.05, courant_c=8.0)]:
+        o = ns.Oracle(**kw)
+        f = inputs.uniform_pm1(inputs.SEED_UNIFORM_SMALL, o.size())
+        res = o.pcg(f, rtol=1e-13, max_iter=300)
+        assert res["status"] == 0
+        A = o.dense_operator()
+        ud = sla.cho_solve(sla.cho_factor(A), f)
+        ul = sla.lu_solve(sla.lu_factor(A), f)
+
+        def anorm(e):
+            return math.sqrt(max(e @ A @ e, 0.0))
+
+        floor = max(10.0 * anorm(ul - ud), 1e-12 * anorm(ud))
+        assert anorm(res["u"] - ud) <= floor, (anorm(res["u"] - ud) / anorm(ud), floor / anorm(ud))
+
+
+def pin_manufactured(ns):
+    """Manufactured solution: f = A u*, solve to rtol 1e-12, recover u* in the
+    energy norm to 1e-9 (a residual drop of 1e-12 bounds the error by cond-weighted 1e-12)."""
+    o = ns.Oracle(refinement=3, n_levels=3, n_r=16, grading=1.05, courant_c=80.0)
+    g, v = o.grid(o.refinement), o.vertical()
+    ustar = inputs.manufactured_solution(g["centre"], v["r"], inputs.SEED_MANUFACTURED)
+    f = o.apply(ustar)
+    res = o.pcg(f, rtol=1e-12, max_iter=200)
+    assert res["status"] == 0
+    e = res["u"] - ustar
+    assert math.sqrt(e @ o.apply(e)) <= 1e-9 * math.sqrt(ustar @ f)
+
+
+def convergence_factor(o, n_iter: int = 8, seed: int = 77) -> float:
+    """Asymptotic residual reduction per Richardson step u <- u + B(f - A u), f = 0."""
+    u0 = inputs.uniform_pm1(seed, o.size())
+    _, hist = o.richardson(np.zeros(o.size()), u0, n_iter)
+    return float((hist[-1] / hist[-4]) ** (1.0 / 3.0))
+
+
+def pin_robust_convergence(ns):
+    """Theorem (Sec. 3.3): the TPMG V-cycle factor is bounded away from 1
+    independently of h and of the vertical aspect ratio.  Measured over grids and
+    anisotropies: every factor < 0.5 and their spread (max/min) <= 2."""
+    rhos = []
+    for ref in (3, 4):
+        for n_r in (16, 64):
+            for gr in (1.0, 1.05):
+                for C in (8.0, 80.0):
+                    o = ns.Oracle(refinement=ref, n_levels=4, n_r=n_r, grading=gr, courant_c=C,
+                                  nu_pre=2, nu_post=2, nu_coarse=1)
+                    rhos.append(convergence_factor(o))
+    assert max(rhos) < 0.5, rhos
+    assert max(rhos) / min(rhos) <= 2.0, rhos
+
+
+ALL_PINS = [
+    pin_mesh_counts, pin_mesh_areas, pin_level0_closed_forms, pin_mesh_topology, pin_vertical,
+    pin_constants_in_kernel, pin_symmetric_spd, pin_kronecker, pin_horizontal_consistency,
+    pin_vertical_consistency, pin_thomas, pin_transfers, pin_vcycle_dense, pin_preconditioner_symmetric,
+    pin_invariant_subspaces, pin_pcg_dense, pin_manufactured, pin_robust_convergence,
+]

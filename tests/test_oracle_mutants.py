@@ -1,0 +1,94 @@
+"""Planted mistakes: every plausible one-line error in the oracle must fail a pin.
+
+Each mutant is the oracle source with one textual change (a dropped term, a
+wrong sign, index, operand or loop order), compiled into a temporary library
+and run against all pins of ``pins.py`` in a child process.  The test passes
+when some pin rejects the mutant.  The mistakes are planted in the CPU oracle
+only; nothing here touches a GPU.
+"""
+import os
+import subprocess
+import sys
+import textwrap
+
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+TESTS = os.path.join(ROOT, "tests")
+
+MUTANTS = {
+    "drop_horizontal_flux": (
+        "                s -= alphaS_hat(o, G, T, e, k) * u[(size_t)G->nbr[3 * T + e] * n + k];\n"
+        "            y[(size_t)T * n + k] = s;",
+        "                s -= 0.0 * u[(size_t)G->nbr[3 * T + e] * n + k];\n"
+        "            y[(size_t)T * n + k] = s;"),
+    "vertical_offdiag_sign": ("sub[k] = -lo;", "sub[k] = lo;"),
+    "upper_face_index": ("up = alphar_hat(o, G, T, k + 1)", "up = alphar_hat(o, G, T, k)"),
+    "neighbour_slot_shift": (
+        "u[(size_t)G->nbr[3 * T + e] * n + k];\n            y[",
+        "u[(size_t)G->nbr[3 * T + (e + 1) % 3] * n + k];\n            y["),
+    "thomas_forward_index": ("dp[i] = (d[i] - a[i] * dp[i - 1]) / den;", "dp[i] = (d[i] - a[i - 1] * dp[i - 1]) / den;"),
+    "thomas_backward_index": ("x[i] = dp[i] - cp[i] * x[i + 1];", "x[i] = dp[i] - cp[i + 1] * x[i + 1];"),
+    "restrict_child_index": ("s += rf[(size_t)(4 * T + j) * n + k];", "s += rf[(size_t)(4 * T) * n + k];"),
+    "post_smooth_order": ("smooth(o, l, f, u, o->nu_post, -1);", "smooth(o, l, f, u, o->nu_post, +1);"),
+    "volume_factor": ("o->r[k + 1] * o->r[k + 1] + o->r[k + 1] * o->r[k] + o->r[k] * o->r[k]",
+                      "o->r[k + 1] * o->r[k + 1] + o->r[k + 1] * o->r[k + 1] + o->r[k] * o->r[k]"),
+    "area_half_excess": ("G->area[T] = 2.0 * atan2(num, den);", "G->area[T] = atan2(num, den);"),
+    "g_without_edge_length": ("gval = len * v_dot(n, d) / v_dot(d, d);", "gval = v_dot(n, d) / v_dot(d, d);"),
+    "g_distance_power": ("gval = len * v_dot(n, d) / v_dot(d, d);", "gval = len * v_dot(n, d) / sqrt(v_dot(d, d));"),
+    "pcg_beta_inverted": ("beta = rz_new / rz;", "beta = rz / rz_new;"),
+    "prolong_half": ("uf[(size_t)(4 * T + j) * n + k] += uc[(size_t)T * n + k];",
+                     "uf[(size_t)(4 * T + j) * n + k] += 0.5 * uc[(size_t)T * n + k];"),
+    "correction_sign": ("uf[(size_t)(4 * T + j) * n + k] += uc[(size_t)T * n + k];",
+                        "uf[(size_t)(4 * T + j) * n + k] -= uc[(size_t)T * n + k];"),
+    "horizontal_uses_volume": ("return o->omega2 * o->dr[k] * G->g[3 * T + e];",
+                               "return o->omega2 * o->vol[k] * G->g[3 * T + e];"),
+    "vertical_missing_r2": ("2.0 * o->r[k] * o->r[k] / (o->zeta[k + 1] - o->zeta[k - 1])",
+                            "2.0 / (o->zeta[k + 1] - o->zeta[k - 1])"),
+    "vertical_distance": ("2.0 * o->r[k] * o->r[k] / (o->zeta[k + 1] - o->zeta[k - 1])",
+                          "2.0 * o->r[k] * o->r[k] / (o->zeta[k + 1] - o->zeta[k])"),
+    "skip_last_colour": ("for (c = 0; c < G->n_colours; ++c) colour_pass(o, l, c, f, u);",
+                         "for (c = 0; c < G->n_colours - 1; ++c) colour_pass(o, l, c, f, u);"),
+    "child_orientation": ("c[3] = v0;  c[4] = m01; c[5] = m20;", "c[3] = v0;  c[4] = m20; c[5] = m01;"),
+    "residual_sign": ("o->mg_r[l][i] = f[i] - o->mg_r[l][i];", "o->mg_r[l][i] = o->mg_r[l][i] - f[i];"),
+    "vertex_mean_centre": ("G->centre[T] = v_unit(v_add(v_add(a, b), c));", "G->centre[T] = v_unit(v_add(a, b));"),
+    "colouring_looks_ahead": ("if (Tp < T) used[G->colour[Tp]] = 1;", "if (Tp > T) used[G->colour[Tp]] = 1;"),
+    "grading_exponent": ("pow(grading, (double)k)", "pow(grading, (double)(k + 1))"),
+    "relaxation_ignored": ("u_in[(size_t)T * n + k] + o->relax * o->col_x[k];", "u_in[(size_t)T * n + k] + o->col_x[k];"),
+    "diag_misses_mass": ("diag[k] = beta_hat(o, G, T, k) + lo + up + hs;", "diag[k] = lo + up + hs;"),
+    "pcg_alpha_inverted": ("alpha = rz / pq;", "alpha = pq / rz;"),
+    "coarse_sweep_one_way": ("smooth(o, l, f, u, o->nu_coarse, 0);", "smooth(o, l, f, u, o->nu_coarse, +1);"),
+}
+
+DRIVER = textwrap.dedent("""
+    import functools, sys, types
+    sys.path[:0] = [{root!r}, {tests!r}]
+    import oracle, pins
+    lib = sys.argv[1]
+    ns = types.SimpleNamespace(Oracle=functools.partial(oracle.Oracle, lib_path=lib),
+                               thomas=functools.partial(oracle.thomas, lib_path=lib))
+    for p in pins.ALL_PINS:
+        try:
+            p(ns)
+        except Exception as exc:
+            print("REJECTED_BY", p.__name__, type(exc).__name__)
+            sys.exit(0)
+    print("ALL_PINS_PASSED")
+    sys.exit(3)
+""")
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_fails_a_pin(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(oracle._SRC).read()
+    assert src.count(old) >= 1, f"mutation site for {name} not found"
+    mutated = src.replace(old, new, 1)
+    c_path = tmp_path / "mutant.c"
+    c_path.write_text(mutated)
+    lib = oracle.compile_source(str(c_path), str(tmp_path / "libmutant.so"))
+    proc = subprocess.run([sys.executable, "-c", DRIVER.format(root=ROOT, tests=TESTS), lib],
+                          capture_output=True, text=True, timeout=600)
+    assert proc.returncode == 0 and "REJECTED_BY" in proc.stdout, (proc.returncode, proc.stdout, proc.stderr[-2000:])

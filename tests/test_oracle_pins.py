@@ -1,0 +1,16 @@
+"""The CPU oracle against what the paper and the mathematics fix (no GPU)."""
+import types
+
+import pytest
+
+import pins
+
+
+@pytest.fixture(scope="module")
+def ns(oracle_ns):
+    return types.SimpleNamespace(Oracle=oracle_ns.Oracle, thomas=oracle_ns.thomas)
+
+
+@pytest.mark.parametrize("pin", pins.ALL_PINS, ids=lambda p: p.__name__)
+def test_pin(ns, pin):
+    pin(ns)
