@@ -1,0 +1,360 @@
+#!/usr/bin/env python3
+"""Throughput of TPMG-preconditioned CG on one GB300 (or N independent replicas).
+
+A step is one full solve, from a zero initial guess to a 1e-5 reduction of the
+residual 2-norm, of the pressure-correction system -omega^2 div grad u + u = f
+on the thin spherical shell, with the inputs resident in HBM.  The metric is
+unknowns per second (unknowns x steps / device time).
+
+Default workload: icosahedral refinement 6 (81,920 triangles) x 64 vertical
+levels graded 1.05 over a 10 km shell (5,242,880 unknowns), omega^2/h^2 = 80,
+manufactured solution u* = sum of 8 seeded low-order spherical harmonics x
+vertical cosines, f = A u*; 6 multigrid levels, 2/2 line-SOR sweeps, 1 coarse
+sweep; FP64 throughout.
+
+Flags: --gpus N --steps K --warmup W [--impl tpmg|reference] [--workload NAME]
+Under torchrun (N > 1) every rank solves its own replica (no data exchange:
+the path shards only through independent problems on this pool).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "unknowns/sec to 1e-5 residual reduction (TPMG-PCG) at 1 GB300; HBM GB/s vs peak"
+
+WORKLOADS = {
+    "81920x64": dict(
+        params=dict(refinement=6, n_levels=6, n_r=64, grading=1.05, courant_c=80.0, nu_pre=2, nu_post=2, nu_coarse=1),
+        rhs="manufactured", seed=2981002,
+        text="icosahedral refinement 6 (81920 triangles) x 64 levels graded 1.05 over 10 km, omega^2/h^2=80, "
+             "manufactured spherical-harmonic x cosine solution, f = A u*, 6 MG levels, nu 2/2/1, rtol 1e-5"),
+    "1280x16": dict(
+        params=dict(refinement=3, n_levels=4, n_r=16, grading=1.0, courant_c=8.0, nu_pre=1, nu_post=1, nu_coarse=1),
+        rhs="uniform", seed=2981001,
+        text="icosahedral refinement 3 (1280 triangles) x 16 uniform levels over 10 km, omega^2/h^2=8, "
+             "RHS uniform[-1,1], 4 MG levels, nu 1/1/1, rtol 1e-5"),
+}
+
+# FP64 flops per unknown of each kernel class as written (FMA = 2 flops), and
+# algorithmic HBM bytes per unknown (each array streamed once).
+FLOPS_PER_UNIT = {"relax": 12.0, "apply": 17.0, "restrict": 16.0, "residual": 17.0, "axpy": 6.0,
+                  "dot": 2.0, "xpby": 2.0, "prolong": 1.0}
+BYTES_PER_UNIT = {"relax": 48.0, "apply": 24.0, "restrict": 18.0, "residual": 24.0, "axpy": 48.0,
+                  "dot": 16.0, "xpby": 24.0, "prolong": 20.0}
+SM_COUNT_GB300 = 152
+FP64_FMA_PER_CLK_PER_SM = 2     # GB300: 1.25 TFLOP/s dense FP64 at 2.07 GHz over 152 SMs
+
+
+def load_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return dict(hbm_gbs=float(d.get("hbm_gbs", 6800.0)), sm_max_mhz=float(d.get("sm_max_mhz", 2070.0)),
+                    source="measured")
+    return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, source="fallback")
+
+
+def fp64_peak_tflops(sm_count: int, mhz: float) -> float:
+    return sm_count * FP64_FMA_PER_CLK_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- distributed helpers
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    """Max of a per-rank number over all ranks (identity for one rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def aggregate_value(units_per_step: float, steps: int, world: int, local_ms: float) -> tuple[float, float]:
+    """Whole-job throughput: units all ranks processed / the slowest rank's time."""
+    t_ms = max_over_ranks(local_ms, world)
+    return units_per_step * steps * world / (t_ms / 1e3), t_ms
+
+
+# ----------------------------------------------------------------------------- oracle timing
+def oracle_inputs(wl: dict):
+    import oracle
+    from paper_1408_2981_gb300 import inputs
+
+    o = oracle.Oracle(**wl["params"])
+    if wl["rhs"] == "manufactured":
+        g, v = o.grid(o.refinement), o.vertical()
+        ustar = inputs.manufactured_solution(g["centre"], v["r"], wl["seed"])
+        f = o.apply(ustar)
+    else:
+        f = inputs.uniform_pm1(wl["seed"], o.size())
+    return o, f
+
+
+def time_oracle(wl: dict, min_seconds: float, max_solves: int, rtol: float):
+    o, f = oracle_inputs(wl)
+    times, iters = [], None
+    while len(times) < max_solves and (sum(times) < min_seconds or not times):
+        t0 = time.perf_counter()
+        res = o.pcg(f, rtol=rtol, max_iter=200)
+        times.append(time.perf_counter() - t0)
+        iters = res["iters"]
+    return o.size(), times, iters
+
+
+# ----------------------------------------------------------------------------- arms
+def run_reference(args, wl):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    o, f = oracle_inputs(wl)
+    N = o.size()
+    for _ in range(min(args.warmup, 1)):
+        o.pcg(f, rtol=args.rtol, max_iter=200)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        res = o.pcg(f, rtol=args.rtol, max_iter=200)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = N * len(times) / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world,
+            "steps": len(times), "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["text"], "n_unknowns": N},
+            "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{len(times)} full oracle solves of the workload (setup excluded), "
+                                       f"{res['iters']} PCG iterations each"},
+            "e2e": {"value": value, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "iters": res["iters"], "rel_resid": res["rel_resid"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_tpmg(args, wl):
+    import numpy as np
+    import torch
+
+    from paper_1408_2981_gb300 import binding, build as _build, inputs
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    _build.build()
+    stream = torch.cuda.current_stream()
+    s = binding.Solver(stream=stream, **wl["params"])
+    N = s.N
+    m = s.export_mesh()
+    if wl["rhs"] == "manufactured":
+        ustar = torch.from_numpy(inputs.manufactured_solution(m["centres"], m["r_faces"], wl["seed"])).cuda()
+        f = torch.empty(N, dtype=torch.float64, device="cuda")
+        s.apply_operator(ustar, f)
+    else:
+        f = torch.from_numpy(inputs.uniform_pm1(wl["seed"], N)).cuda()
+    u = torch.zeros(N, dtype=torch.float64, device="cuda")
+    l2 = torch.cuda.get_device_properties(local).L2_cache_size
+    flush = torch.empty(max(2 * l2, 256 << 20) // 4, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+
+    # warm-up; the last warm-up solve times every kernel class to find the dominant one
+    for w in range(args.warmup):
+        if w == args.warmup - 1:
+            s.profile(classes=tuple(c for c in binding.KERNEL_CLASSES if c != "copy"))
+        u.zero_()
+        st, it, rel, _ = s.solve(f, u, rtol=args.rtol, max_iter=200)
+    prof_all = s.profile_read()
+    shares = {k: v["ms"] for k, v in prof_all.items() if v["ms"] > 0}
+    dominant = max(shares, key=shares.get) if shares else "relax"
+
+    # timed region: K solves, L2 flushed between steps, only the dominant class event-timed
+    s.profile(classes=(dominant,))
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    iters = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        evs[k][0].record(stream)
+        u.zero_()
+        st, it, rel, _ = s.solve(f, u, rtol=args.rtol, max_iter=200)
+        evs[k][1].record(stream)
+        iters.append(it)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    local_ms = sum(a.elapsed_time(b) for a, b in evs)
+    value, t_ms = aggregate_value(N, args.steps, world, local_ms)
+    prof = s.profile_read()
+    gpu_launches = int(sum(v["launches"] for c, v in prof.items() if c != "copy"))
+
+    # end to end through the C ABI with host buffers (copies inside the timed call)
+    f_host = torch.empty(N, dtype=torch.float64, pin_memory=True)
+    f_host.copy_(f)
+    u_host = torch.zeros(N, dtype=torch.float64, pin_memory=True)
+    fh, uh = f_host.numpy(), u_host.numpy()
+    e2e_steps = max(1, min(args.steps, 10))
+    barrier(world)
+    e2e_s = 0.0
+    for _ in range(e2e_steps):
+        uh[:] = 0.0
+        t0 = time.perf_counter()
+        s.solve_host(fh, uh, rtol=args.rtol, max_iter=200)
+        e2e_s += time.perf_counter() - t0
+    e2e_ms = max_over_ranks(1e3 * e2e_s, world)
+    e2e_value = N * e2e_steps * world / (e2e_ms / 1e3)
+
+    # roofline of the dominant kernel class, from the event-timed launches of the timed region
+    peaks = load_peaks()
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    d = prof[dominant]
+    roof = None
+    if d["ms"] > 0 and d["launches"] > 0:
+        flops = FLOPS_PER_UNIT.get(dominant, 0.0) * d["units"]
+        nbytes = BYTES_PER_UNIT.get(dominant, 0.0) * d["units"]
+        achieved = flops / (d["ms"] / 1e3) / 1e12
+        peak = fp64_peak_tflops(sm_count, peaks["sm_max_mhz"])
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": f"{dominant} (FP64)",
+                "peak_source": f"FP64 pipe: {sm_count} SMs x {FP64_FMA_PER_CLK_PER_SM} DFMA/clk x 2 x "
+                               f"{peaks['sm_max_mhz']:.0f} MHz",
+                "launches_per_step": d["launches"] / args.steps,
+                "avg_launch_us": 1e3 * d["ms"] / d["launches"],
+                "hbm_gbs_algorithmic": nbytes / (d["ms"] / 1e3) / 1e9,
+                "hbm_frac_of_measured": nbytes / (d["ms"] / 1e3) / 1e9 / peaks["hbm_gbs"],
+                "share_of_step": d["ms"] / local_ms}
+    # aggregate algorithmic HBM rate of the whole solve
+    tot_bytes = sum(BYTES_PER_UNIT.get(c, 0.0) * v["units"] for c, v in prof.items())
+    hbm = {"achieved_gbs": tot_bytes / (local_ms / 1e3) / 1e9, "peak_gbs": peaks["hbm_gbs"],
+           "frac": tot_bytes / (local_ms / 1e3) / 1e9 / peaks["hbm_gbs"], "source": peaks["source"]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n_o, times, o_iters = time_oracle(wl, min_seconds=10.0, max_solves=3, rtol=args.rtol)
+        cpu = {"value": n_o * len(times) / sum(times), "unit": "unknowns/s", "cores": 1, "kind": "oracle",
+               "sample": f"{len(times)} full oracle solve(s) of the same workload, setup excluded, "
+                         f"{o_iters} PCG iterations, single thread"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": wl["text"], "n_unknowns": N, "parallelism": f"replicas{world}",
+                           "l2": "flushed between steps (write of 2x L2 outside the timed events)"},
+                "e2e": {"value": e2e_value, "unit": "unknowns/s", "h2d_bytes_per_step": 2 * 8 * N,
+                        "d2h_bytes_per_step": 8 * N},
+                "gpu_launches": gpu_launches, "roofline": roof, "hbm": hbm, "cpu_baseline": cpu,
+                "clocks": clk, "iters": iters[-1], "rel_resid": rel,
+                "kernel_ms_per_step": {c: v["ms"] / 1.0 for c, v in prof_all.items() if v["ms"] > 0}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["tpmg", "reference"], default="tpmg")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="81920x64")
+    ap.add_argument("--rtol", type=float, default=1e-5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 1 and args.impl == "tpmg":
+        ap.error("--warmup must be >= 1")
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl)
+    return run_tpmg(args, wl)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

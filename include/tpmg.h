@@ -1,0 +1,193 @@
+/*
+ * tpmg.h -- C ABI of the GB300 tensor-product multigrid (TPMG) library.
+ *
+ * Solves the pressure-correction equation of Dedner, Mueller & Scheichl,
+ * "Efficient multigrid preconditioners for atmospheric flow simulations at
+ * high aspect ratio" (arXiv:1408.2981), Sec. 2 eq. HelmholtzVector with
+ * constant profiles (alpha_r = alpha_S = beta = 1, xi_r = 0):
+ *
+ *     -omega^2 div grad u + u = f      in  S^2 x [1, 1+H],
+ *     du/dr = 0 at r = 1 and r = 1 + H,
+ *
+ * discretised by the cell-centred finite volumes of Appendix A on an
+ * icosahedral grid (Sec. 4.1-4.2) times a graded vertical column, with
+ * preconditioned conjugate gradients whose preconditioner is one TPMG V-cycle
+ * (Algorithm 1): vertical line (column tridiagonal) relaxation, eq. BlockJacobi,
+ * and horizontal-only coarsening.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Field vectors are double arrays of length n_cells * n_r in the library's
+ * cell order (cell T of refinement level L, children of a coarse cell T are
+ * 4T..4T+3) with the vertical index k fastest: element (T, k) at T*n_r + k.
+ * A right-hand side holds cell integrals (Sec. 5), i.e. the finite-volume
+ * discretisation of the source times the cell volume |T| v_k.
+ *
+ * Pointers named d_* are DEVICE pointers on the current CUDA device (for
+ * example the data pointer of a float64 torch tensor); h_* are HOST pointers.
+ * The caller owns every buffer it passes and keeps it alive until the work
+ * on the context's stream that uses it has completed; the library never
+ * frees caller memory.  The library owns every internal workspace: all of it
+ * is allocated by tpmg_setup and released by tpmg_destroy.
+ *
+ * All device work is ordered on the stream given to tpmg_setup.
+ * tpmg_apply_operator and tpmg_vcycle are asynchronous; tpmg_solve and
+ * tpmg_solve_host return after the solve has finished.
+ *
+ * Errors are returned as tpmg_status values; no C++ exception crosses this
+ * interface.  A context is not thread-safe: one thread at a time per context.
+ * tpmg_last_error gives a human-readable message for the last failed call.
+ */
+#ifndef TPMG_H
+#define TPMG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tpmg_ctx tpmg_ctx;
+
+typedef enum {
+    TPMG_OK = 0,
+    TPMG_ERR_INVALID_ARG = 1,   /* a parameter or pointer was rejected; nothing was launched */
+    TPMG_ERR_CUDA = 2,          /* a CUDA runtime call failed; see tpmg_last_error */
+    TPMG_ERR_OOM = 3,           /* device memory allocation failed in tpmg_setup */
+    TPMG_ERR_NOT_CONVERGED = 4, /* tpmg_solve used max_iter iterations without reaching rtol */
+    TPMG_ERR_BREAKDOWN = 5      /* p.Ap <= 0 or a non-finite residual (not SPD, or NaN/Inf input) */
+} tpmg_status;
+
+/* Block relaxation of eq. BlockJacobi: u_T <- u_T + relax A_T^{-1} (f - A u)_T. */
+enum { TPMG_SMOOTH_MCSOR = 0,   /* multicolour block-SOR: forward colours before, reverse after the correction */
+       TPMG_SMOOTH_JACOBI = 1 }; /* weighted block-Jacobi */
+
+/* Storage of the stencil (Sec. 3.2): recomputed on the fly from O(n_r + n_cells)
+ * factorised data (TPMG^otimes), or stored per unknown (TPMG^full). */
+enum { TPMG_COEFF_FACTORISED = 0, TPMG_COEFF_FULL = 1 };
+
+/* Cell centre used by the two-point flux of Appendix A. */
+enum { TPMG_CENTRE_CIRCUM = 0,      /* spherical circumcentre (centre chord normal to the edge) */
+       TPMG_CENTRE_VERTEX_MEAN = 1 };
+
+/* Arithmetic of the V-cycle.  FP64: everything in double.  MIXED: the V-cycle
+ * (operator, line smoother, transfers) in FP32 with BF16-stored stencil
+ * factors; the outer Krylov vectors, residual and dot products in FP64. */
+enum { TPMG_PREC_FP64 = 0, TPMG_PREC_MIXED = 1 };
+
+typedef struct {
+    int    refinement;   /* fine icosahedral level L >= 0: n_cells = 20 * 4^L (L <= 9) */
+    int    n_levels;     /* multigrid levels, 1 .. L+1 (level 0 coarsest = refinement L-n_levels+1) */
+    int    n_r;          /* vertical cells, 1 .. 1024 */
+    double H;            /* shell depth over the sphere radius, e.g. 10/6371 (> 0) */
+    double grading;      /* geometric ratio dr_{k+1}/dr_k, finest at k = 0; 1.0 = uniform (> 0) */
+    double omega2;       /* omega^2 in unit-sphere units; if <= 0, omega^2 = courant_c * h_min^2,
+                            h_min = smallest distance between neighbouring fine-level centres */
+    double courant_c;    /* Courant-type ratio omega^2 / h_min^2 used when omega2 <= 0 */
+    int    nu_pre;       /* pre-smoothing sweeps on levels > 0 (>= 0) */
+    int    nu_post;      /* post-smoothing sweeps on levels > 0 (>= 0; = nu_pre for a symmetric B) */
+    int    nu_coarse;    /* symmetric sweeps on the coarsest level (>= 0) */
+    int    smoother;     /* TPMG_SMOOTH_* */
+    double relax;        /* relaxation factor rho_relax (0 < relax < 2) */
+    int    coeff_storage;/* TPMG_COEFF_* */
+    int    centre;       /* TPMG_CENTRE_* */
+    int    precision;    /* TPMG_PREC_* */
+} tpmg_params;
+
+/* Fills *p with the defaults: refinement 3, n_levels 4, n_r 16, H = 10/6371,
+ * grading 1, omega2 0 with courant_c 8, nu 2/2/1, block-SOR with relax 1,
+ * factorised storage, circumcentres, FP64.  Returns TPMG_ERR_INVALID_ARG if p is NULL. */
+tpmg_status tpmg_default_params(tpmg_params *p);
+
+/* Builds the grid hierarchy, geometry, colouring and coefficients on the host
+ * (Sec. 4.1-4.2, Appendix A), uploads them, and allocates all workspaces on the
+ * current device.  cuda_stream is a cudaStream_t (NULL = legacy default
+ * stream).  On success *out owns everything and must be released with
+ * tpmg_destroy.  Errors: INVALID_ARG (bad parameter, *out untouched),
+ * OOM, CUDA. */
+tpmg_status tpmg_setup(const tpmg_params *p, void *cuda_stream, tpmg_ctx **out);
+
+/* y = A x on the finest level (eq. ColumnEquation: matrix-free finite-volume
+ * operator).  d_x, d_y: device, n_cells*n_r doubles, must not overlap.
+ * Asynchronous on the context stream.  Errors: INVALID_ARG (NULL pointer), CUDA. */
+tpmg_status tpmg_apply_operator(tpmg_ctx *ctx, const double *d_x, double *d_y);
+
+/* z = B r: one V-cycle (Algorithm 1) on the finest level from a zero initial
+ * guess; B is the preconditioner used inside tpmg_solve.  d_r, d_z: device,
+ * n_cells*n_r doubles, must not overlap; d_r is not modified.  Asynchronous.
+ * Errors: INVALID_ARG, CUDA. */
+tpmg_status tpmg_vcycle(tpmg_ctx *ctx, const double *d_r, double *d_z);
+
+/* Preconditioned CG for A u = f with B = one V-cycle.  d_u holds the initial
+ * guess on entry and the solution on return.  Stops when ||r_k||_2 <=
+ * rtol * ||r_0||_2 (recursively updated residual; Sec. 5 uses rtol = 1e-5).
+ * *iters = number of products q = A p; *rel_resid = ||r_k|| / ||r_0||.
+ * resid_hist (host, nullable, max_iter+1 doubles) receives ||r_k|| / ||r_0||
+ * for k = 0..*iters.  Synchronises the context stream before returning.
+ * Returns OK, NOT_CONVERGED (iters = max_iter), BREAKDOWN (p.Ap <= 0 or a
+ * non-finite norm; the solution holds the last finite iterate), INVALID_ARG, CUDA. */
+tpmg_status tpmg_solve(tpmg_ctx *ctx, const double *d_f, double *d_u, double rtol, int max_iter,
+                       int *iters, double *rel_resid, double *resid_hist);
+
+/* tpmg_solve with HOST buffers: copies h_f and the initial guess h_u to the
+ * device, solves, and copies the solution back into h_u, all inside the call
+ * (pinned host memory gives full copy bandwidth; pageable memory works).
+ * Same arguments and returns as tpmg_solve. */
+tpmg_status tpmg_solve_host(tpmg_ctx *ctx, const double *h_f, double *h_u, double rtol, int max_iter,
+                            int *iters, double *rel_resid, double *resid_hist);
+
+/* Sizes of multigrid level `level` (0 = coarsest, n_levels-1 = finest):
+ * cells, vertical cells, omega^2 actually used, number of colours.  Any output
+ * may be NULL.  Errors: INVALID_ARG. */
+tpmg_status tpmg_query(const tpmg_ctx *ctx, int level, int *n_cells, int *n_r, double *omega2, int *n_colours);
+
+/* Host copies of the grid of multigrid level `level`: centres [n][3] (unit
+ * vectors), areas [n] (spherical), nbrs [n][3] (cell across edge e of the
+ * counter-clockwise corners (v_e, v_{e+1})), g [n][3] (two-point flux factor
+ * |S| n.(c'-c)/|c'-c|^2), colour [n], r_faces [n_r+1] (1 = r_0 < ... < r_nr = 1+H).
+ * Any output may be NULL.  Errors: INVALID_ARG. */
+tpmg_status tpmg_export_mesh(const tpmg_ctx *ctx, int level, double *centres, double *areas, int *nbrs,
+                             double *g, int *colour, double *r_faces);
+
+/* Tracing: kernel classes of the library, for launch counts and timings. */
+enum { TPMG_K_APPLY = 0,      /* y = A x (with the fused dot of CG) */
+       TPMG_K_RESIDUAL = 1,   /* r = f - A u (initial residual of CG) */
+       TPMG_K_RESTRICT = 2,   /* fused residual + restriction of Algorithm 1 */
+       TPMG_K_RELAX = 3,      /* one colour pass / one Jacobi sweep of the line relaxation */
+       TPMG_K_PROLONG = 4,    /* u += P u_c when no post-smoothing follows */
+       TPMG_K_DOT = 5,        /* <r, z> block partials */
+       TPMG_K_AXPY = 6,       /* u += alpha p, r -= alpha q, ||r||^2 partials */
+       TPMG_K_XPBY = 7,       /* p = z + beta p */
+       TPMG_K_FINISH = 8,     /* deterministic reduction of partials + CG scalar step */
+       TPMG_K_COPY = 9,       /* device-to-device copies and clears issued by the library */
+       TPMG_K_COUNT = 10 };
+
+/* Resets the tracing counters of ctx and times (with a CUDA event pair on the
+ * context stream around each launch) the kernel classes whose bit is set in
+ * class_mask (bit i = class i; 0 = count launches only).  Launch counts and
+ * processed unknowns are always accumulated.  Errors: INVALID_ARG, CUDA. */
+tpmg_status tpmg_profile(tpmg_ctx *ctx, unsigned class_mask);
+
+/* Reads the counters of one kernel class since the last tpmg_profile call:
+ * launches, total device time in ms of the timed launches (0 if the class is
+ * not timed), and units = number of (cell, level) unknowns the launches
+ * processed (for the algorithmic bytes / flops per launch).  Synchronises the
+ * context stream.  Any output may be NULL.  Errors: INVALID_ARG, CUDA. */
+tpmg_status tpmg_profile_read(tpmg_ctx *ctx, int kernel_class, long long *launches, double *total_ms,
+                              double *units);
+
+/* Static description of a status value. */
+const char *tpmg_status_string(tpmg_status s);
+
+/* Message of the last failed call on ctx ("" if none); valid until the next call. */
+const char *tpmg_last_error(const tpmg_ctx *ctx);
+
+/* Releases every device and host resource of ctx (after synchronising its
+ * stream).  NULL is ignored. */
+void tpmg_destroy(tpmg_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TPMG_H */

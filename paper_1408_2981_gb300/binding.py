@@ -1,0 +1,238 @@
+"""Thin ctypes binding of ``libtpmg.so`` (C ABI declared in ``include/tpmg.h``).
+
+Functions keep the C names (``tpmg_setup``, ``tpmg_apply_operator``,
+``tpmg_vcycle``, ``tpmg_solve``, ...).  ``Solver`` wraps a context for torch
+float64 CUDA tensors: it only checks shapes/dtypes and passes data pointers
+and the current CUDA stream.  Every step of the solve runs in the library's
+CUDA kernels; there is no CPU fallback -- if the library is missing or fails
+to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libtpmg.so")
+
+TPMG_OK = 0
+TPMG_ERR_INVALID_ARG = 1
+TPMG_ERR_CUDA = 2
+TPMG_ERR_OOM = 3
+TPMG_ERR_NOT_CONVERGED = 4
+TPMG_ERR_BREAKDOWN = 5
+
+TPMG_SMOOTH_MCSOR = 0
+TPMG_SMOOTH_JACOBI = 1
+TPMG_COEFF_FACTORISED = 0
+TPMG_COEFF_FULL = 1
+TPMG_CENTRE_CIRCUM = 0
+TPMG_CENTRE_VERTEX_MEAN = 1
+TPMG_PREC_FP64 = 0
+TPMG_PREC_MIXED = 1
+
+# every entry point declared in include/tpmg.h
+EXPORTS = ["tpmg_default_params", "tpmg_setup", "tpmg_apply_operator", "tpmg_vcycle", "tpmg_solve",
+           "tpmg_solve_host", "tpmg_query", "tpmg_export_mesh", "tpmg_profile", "tpmg_profile_read",
+           "tpmg_status_string", "tpmg_last_error", "tpmg_destroy"]
+
+KERNEL_CLASSES = ["apply", "residual", "restrict", "relax", "prolong", "dot", "axpy", "xpby", "finish", "copy"]
+
+
+class tpmg_params(ctypes.Structure):
+    _fields_ = [("refinement", ctypes.c_int), ("n_levels", ctypes.c_int), ("n_r", ctypes.c_int),
+                ("H", ctypes.c_double), ("grading", ctypes.c_double), ("omega2", ctypes.c_double),
+                ("courant_c", ctypes.c_double), ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int),
+                ("nu_coarse", ctypes.c_int), ("smoother", ctypes.c_int), ("relax", ctypes.c_double),
+                ("coeff_storage", ctypes.c_int), ("centre", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class TPMGError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{status_name(status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libtpmg.so and declare its prototypes.  Raises if it is missing."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is not built: run paper_1408_2981_gb300.build.build() "
+                           "(the CUDA library is required; there is no CPU fallback)")
+    lib = ctypes.CDLL(p)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.tpmg_default_params.argtypes = [ctypes.POINTER(tpmg_params)]
+    lib.tpmg_setup.argtypes = [ctypes.POINTER(tpmg_params), P, ctypes.POINTER(P)]
+    lib.tpmg_apply_operator.argtypes = [P, P, P]
+    lib.tpmg_vcycle.argtypes = [P, P, P]
+    lib.tpmg_solve.argtypes = [P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D), P]
+    lib.tpmg_solve_host.argtypes = [P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D), P]
+    lib.tpmg_query.argtypes = [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(I)]
+    lib.tpmg_export_mesh.argtypes = [P, I, P, P, P, P, P, P]
+    lib.tpmg_profile.argtypes = [P, ctypes.c_uint]
+    lib.tpmg_profile_read.argtypes = [P, I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(D), ctypes.POINTER(D)]
+    lib.tpmg_status_string.argtypes = [I]
+    lib.tpmg_status_string.restype = ctypes.c_char_p
+    lib.tpmg_last_error.argtypes = [P]
+    lib.tpmg_last_error.restype = ctypes.c_char_p
+    lib.tpmg_destroy.argtypes = [P]
+    lib.tpmg_destroy.restype = None
+    for name in EXPORTS:
+        if name not in ("tpmg_destroy", "tpmg_status_string", "tpmg_last_error"):
+            getattr(lib, name).restype = I
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def status_name(status: int) -> str:
+    try:
+        return load().tpmg_status_string(status).decode()
+    except Exception:
+        return f"status {status}"
+
+
+def default_params(**overrides) -> tpmg_params:
+    p = tpmg_params()
+    st = load().tpmg_default_params(ctypes.byref(p))
+    if st != TPMG_OK:
+        raise TPMGError(st, "tpmg_default_params")
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(t) -> int:
+    return t.data_ptr()
+
+
+class Solver:
+    """A tpmg context bound to the current CUDA device and stream.
+
+    Keyword arguments are the fields of ``tpmg_params``.  Vectors are torch
+    float64 CUDA tensors with ``n_cells * n_r`` elements ([cell][k], k fastest).
+    """
+
+    def __init__(self, stream=None, **params):
+        import torch
+
+        self._torch = torch
+        self._lib = load()
+        self.params = default_params(**params)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        st = self._lib.tpmg_setup(ctypes.byref(self.params), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h))
+        if st != TPMG_OK:
+            raise TPMGError(st, "tpmg_setup rejected the parameters or failed")
+        self._h = h
+        self.n_levels = self.params.n_levels
+        self.n_r = self.params.n_r
+        self.n_cells, _, self.omega2, self.n_colours = self.query(self.n_levels - 1)
+        self.N = self.n_cells * self.n_r
+
+    # --------------------------------------------------------------- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.tpmg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int, what: str):
+        if st != TPMG_OK:
+            raise TPMGError(st, f"{what}: {self._lib.tpmg_last_error(self._h).decode()}")
+
+    def _vec(self, t, name: str):
+        torch = self._torch
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda:
+            raise TypeError(f"{name} must be a float64 CUDA tensor")
+        if t.numel() != self.N or not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous with {self.N} elements")
+        return _ptr(t)
+
+    # --------------------------------------------------------------- queries
+    def query(self, level: int):
+        n, nr, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        w = ctypes.c_double()
+        st = self._lib.tpmg_query(self._h, level, ctypes.byref(n), ctypes.byref(nr), ctypes.byref(w), ctypes.byref(c))
+        if st != TPMG_OK:
+            raise TPMGError(st, "tpmg_query")
+        return n.value, nr.value, w.value, c.value
+
+    def export_mesh(self, level: int | None = None) -> dict:
+        level = self.n_levels - 1 if level is None else level
+        n = self.query(level)[0]
+        out = dict(centres=np.zeros((n, 3)), areas=np.zeros(n), nbrs=np.zeros((n, 3), dtype=np.int32),
+                   g=np.zeros((n, 3)), colour=np.zeros(n, dtype=np.int32), r_faces=np.zeros(self.n_r + 1))
+        st = self._lib.tpmg_export_mesh(self._h, level, *(out[k].ctypes.data for k in
+                                                           ("centres", "areas", "nbrs", "g", "colour", "r_faces")))
+        if st != TPMG_OK:
+            raise TPMGError(st, "tpmg_export_mesh")
+        return out
+
+    # --------------------------------------------------------------- tracing
+    def profile(self, classes=()):
+        """Reset the counters; time the named kernel classes (see KERNEL_CLASSES)."""
+        mask = 0
+        for c in classes:
+            mask |= 1 << KERNEL_CLASSES.index(c)
+        self._check(self._lib.tpmg_profile(self._h, mask), "tpmg_profile")
+
+    def profile_read(self) -> dict:
+        out = {}
+        for i, name in enumerate(KERNEL_CLASSES):
+            n, ms, units = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
+            self._check(self._lib.tpmg_profile_read(self._h, i, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(units)),
+                        "tpmg_profile_read")
+            out[name] = dict(launches=n.value, ms=ms.value, units=units.value)
+        return out
+
+    # --------------------------------------------------------------- compute
+    def apply_operator(self, x, y):
+        self._check(self._lib.tpmg_apply_operator(self._h, self._vec(x, "x"), self._vec(y, "y")), "tpmg_apply_operator")
+
+    def vcycle(self, r, z):
+        self._check(self._lib.tpmg_vcycle(self._h, self._vec(r, "r"), self._vec(z, "z")), "tpmg_vcycle")
+
+    def solve(self, f, u, rtol: float = 1e-5, max_iter: int = 100, history: bool = False, raise_on_fail: bool = True):
+        """PCG; u holds the initial guess and receives the solution.
+        Returns (status, iters, rel_resid, hist)."""
+        it = ctypes.c_int(0)
+        rel = ctypes.c_double(0.0)
+        hist = np.zeros(max_iter + 1) if history else None
+        st = self._lib.tpmg_solve(self._h, self._vec(f, "f"), self._vec(u, "u"), rtol, max_iter, ctypes.byref(it),
+                                  ctypes.byref(rel), hist.ctypes.data if history else None)
+        if raise_on_fail and st not in (TPMG_OK,):
+            self._check(st, "tpmg_solve")
+        return st, it.value, rel.value, (hist[:it.value + 1] if history else None)
+
+    def solve_host(self, f: np.ndarray, u: np.ndarray, rtol: float = 1e-5, max_iter: int = 100,
+                   raise_on_fail: bool = True):
+        """PCG on host buffers (copies inside the call).  u is updated in place."""
+        for a, name in ((f, "f"), (u, "u")):
+            if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+                    and a.size == self.N):
+                raise ValueError(f"{name} must be a contiguous float64 array of {self.N} elements")
+        it = ctypes.c_int(0)
+        rel = ctypes.c_double(0.0)
+        st = self._lib.tpmg_solve_host(self._h, f.ctypes.data, u.ctypes.data, rtol, max_iter, ctypes.byref(it),
+                                       ctypes.byref(rel), None)
+        if raise_on_fail and st != TPMG_OK:
+            self._check(st, "tpmg_solve_host")
+        return st, it.value, rel.value

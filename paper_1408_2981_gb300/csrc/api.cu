@@ -1,0 +1,534 @@
+// C ABI of the TPMG library: context set-up, V-cycle orchestration (Algorithm 1
+// of Dedner, Mueller & Scheichl, arXiv:1408.2981) and preconditioned CG.
+// Every step of the solve runs in the kernels of kernels.cu on the context's
+// stream; the host only sequences launches and reads one scalar per iteration.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "tpmg_internal.h"
+
+using namespace tpmg;
+
+// Launch counters (always on) and optional CUDA-event timing per kernel class.
+struct Tracer {
+    unsigned mask = 0;
+    long long launches[TPMG_K_COUNT] = {};
+    double units[TPMG_K_COUNT] = {};
+    std::vector<cudaEvent_t> ev;   // pairs: ev[2i] before, ev[2i+1] after launch i
+    std::vector<int> cls;          // class of timed launch i
+    size_t used = 0;
+};
+
+struct tpmg_ctx {
+    tpmg_params p{};
+    Tracer tr;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int sm_count = 0;
+    HostGrid host;
+    std::vector<LevelDev> lv;     // multigrid levels, 0 = coarsest
+    VertDev vert{};
+    double *d_vert = nullptr;     // backing store of vert (dv | w | hr)
+    long N = 0;                   // fine-level unknowns
+    // PCG vectors (fine level)
+    double *r = nullptr, *z = nullptr, *pv = nullptr, *q = nullptr;
+    double *hf = nullptr, *hu = nullptr;   // device staging for tpmg_solve_host
+    double *partials = nullptr;
+    int n_part = 0;
+    Scalars *sc = nullptr;        // device
+    Scalars *h_sc = nullptr;      // pinned host mirror
+    std::vector<void *> allocs;   // every device allocation, freed by tpmg_destroy
+    std::string err;
+};
+
+namespace {
+
+const char *kStatus[] = {"TPMG_OK", "TPMG_ERR_INVALID_ARG", "TPMG_ERR_CUDA", "TPMG_ERR_OOM",
+                         "TPMG_ERR_NOT_CONVERGED", "TPMG_ERR_BREAKDOWN"};
+
+tpmg_status fail(tpmg_ctx *c, tpmg_status s, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return s;
+}
+
+#define CU(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? TPMG_ERR_OOM : TPMG_ERR_CUDA,      \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                      \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(tpmg_ctx *ctx, T **ptr, size_t count)
+{
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) return e;
+    ctx->allocs.push_back(p);
+    *ptr = static_cast<T *>(p);
+    return cudaMemsetAsync(p, 0, std::max<size_t>(count, 1) * sizeof(T), ctx->stream);
+}
+
+bool validate(const tpmg_params *p, std::string &msg)
+{
+    if (!p) { msg = "params is NULL"; return false; }
+    if (p->refinement < 0 || p->refinement > 9) { msg = "refinement must be in 0..9"; return false; }
+    if (p->n_levels < 1 || p->n_levels > p->refinement + 1) { msg = "n_levels must be in 1..refinement+1"; return false; }
+    if (p->n_r < 1 || p->n_r > 1024) { msg = "n_r must be in 1..1024"; return false; }
+    const double N = 20.0 * std::pow(4.0, p->refinement) * p->n_r;
+    if (N > 2147483647.0) { msg = "n_cells * n_r must fit in a 32-bit index"; return false; }
+    if (!(p->H > 0.0) || !std::isfinite(p->H)) { msg = "H must be positive"; return false; }
+    if (!(p->grading > 0.0) || !std::isfinite(p->grading)) { msg = "grading must be positive"; return false; }
+    if (!(p->omega2 > 0.0) && !(p->courant_c > 0.0)) { msg = "omega2 or courant_c must be positive"; return false; }
+    if (p->nu_pre < 0 || p->nu_post < 0 || p->nu_coarse < 0 || p->nu_pre > 64 || p->nu_post > 64 || p->nu_coarse > 64) {
+        msg = "smoothing counts must be in 0..64"; return false;
+    }
+    if (p->smoother != TPMG_SMOOTH_MCSOR && p->smoother != TPMG_SMOOTH_JACOBI) { msg = "unknown smoother"; return false; }
+    if (!(p->relax > 0.0 && p->relax < 2.0)) { msg = "relax must be in (0, 2)"; return false; }
+    if (p->coeff_storage != TPMG_COEFF_FACTORISED) { msg = "only factorised coefficient storage is built"; return false; }
+    if (p->centre != TPMG_CENTRE_CIRCUM && p->centre != TPMG_CENTRE_VERTEX_MEAN) { msg = "unknown centre kind"; return false; }
+    if (p->precision != TPMG_PREC_FP64) { msg = "only FP64 precision is built"; return false; }
+    return true;
+}
+
+Launch launch_of(const tpmg_ctx *ctx) { return Launch{ctx->stream, ctx->p.n_r, ctx->sm_count}; }
+
+cudaError_t grow_events(Tracer &t, size_t pairs)
+{
+    while (t.ev.size() < 2 * pairs) {
+        cudaEvent_t e;
+        cudaError_t err = cudaEventCreate(&e);
+        if (err != cudaSuccess) return err;
+        t.ev.push_back(e);
+    }
+    if (t.cls.size() < pairs) t.cls.resize(pairs);
+    return cudaSuccess;
+}
+
+// Every device operation of the library goes through run(): it counts the
+// launch and the unknowns it processes, and brackets it with an event pair on
+// the context stream when its class is being timed.
+template <class F>
+cudaError_t run(tpmg_ctx *ctx, int kclass, double units, F &&launch)
+{
+    Tracer &t = ctx->tr;
+    t.launches[kclass] += 1;
+    t.units[kclass] += units;
+    const bool timed = (t.mask >> kclass) & 1u;
+    if (timed) {
+        if (2 * t.used + 2 > t.ev.size()) {
+            cudaError_t e = grow_events(t, t.used + 1024);
+            if (e != cudaSuccess) return e;
+        }
+        cudaError_t e = cudaEventRecord(t.ev[2 * t.used], ctx->stream);
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = launch();
+    if (timed && e == cudaSuccess) {
+        e = cudaEventRecord(t.ev[2 * t.used + 1], ctx->stream);
+        t.cls[t.used] = kclass;
+        ++t.used;
+    }
+    return e;
+}
+
+#define LCHK(call)                                                                                \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) return fail(ctx, TPMG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+cudaError_t relax_pass(tpmg_ctx *ctx, const LevelDev &lv, int c, int mode, const double *f, double *u,
+                       const double *uc)
+{
+    const double units = (double)(lv.colour_off[c + 1] - lv.colour_off[c]) * ctx->p.n_r;
+    return run(ctx, TPMG_K_RELAX, units,
+               [&] { return launch_mcsor_pass(launch_of(ctx), lv, ctx->vert, c, mode, ctx->p.relax, f, u, uc); });
+}
+
+// Algorithm 1 on multigrid level l: u = V-cycle(f) from a zero initial guess.
+// `scratch` is a second vector of the level size (block Jacobi ping-pong).
+tpmg_status vcycle_level(tpmg_ctx *ctx, int l, const double *f, double *u, double *scratch)
+{
+    const Launch L = launch_of(ctx);
+    const tpmg_params &p = ctx->p;
+    const LevelDev &lv = ctx->lv[l];
+    const int C = lv.n_colours;
+    const bool jac = p.smoother == TPMG_SMOOTH_JACOBI;
+    double *cur = u, *oth = scratch;   // Jacobi: current iterate / other buffer
+    auto jacobi = [&](int mode, const double *uc) -> cudaError_t {
+        cudaError_t e = run(ctx, TPMG_K_RELAX, (double)lv.n * p.n_r,
+                            [&] { return launch_jacobi(L, lv, ctx->vert, mode, p.relax, f, cur, oth, uc); });
+        std::swap(cur, oth);
+        return e;
+    };
+    auto finish_in_u = [&]() -> tpmg_status {
+        if (cur != u) LCHK(run(ctx, TPMG_K_COPY, (double)lv.n * p.n_r, [&] { return cudaMemcpyAsync(u, cur, sizeof(double) * lv.n * p.n_r, cudaMemcpyDeviceToDevice, ctx->stream); }));
+        cur = u; oth = scratch;
+        return TPMG_OK;
+    };
+    if (l == 0) {
+        if (p.nu_coarse == 0) {
+            LCHK(run(ctx, TPMG_K_COPY, (double)lv.n * p.n_r, [&] { return cudaMemsetAsync(u, 0, sizeof(double) * lv.n * p.n_r, ctx->stream); }));
+            return TPMG_OK;
+        }
+        for (int s = 0; s < p.nu_coarse; ++s) {
+            if (jac) {
+                LCHK(jacobi(s == 0 ? PASS_ZERO : PASS_NORMAL, nullptr));
+                continue;
+            }
+            for (int c = 0; c < C; ++c)
+                LCHK(relax_pass(ctx, lv, c, s == 0 ? PASS_ZERO : PASS_NORMAL, f, u, nullptr));
+            for (int c = C - 2; c >= 0; --c)
+                LCHK(relax_pass(ctx, lv, c, PASS_NORMAL, f, u, nullptr));
+        }
+        return jac ? finish_in_u() : TPMG_OK;
+    }
+    // pre-smoothing (forward colour order)
+    if (p.nu_pre == 0) {
+        LCHK(run(ctx, TPMG_K_COPY, (double)lv.n * p.n_r, [&] { return cudaMemsetAsync(u, 0, sizeof(double) * lv.n * p.n_r, ctx->stream); }));
+    } else {
+        for (int s = 0; s < p.nu_pre; ++s) {
+            if (jac) {
+                LCHK(jacobi(s == 0 ? PASS_ZERO : PASS_NORMAL, nullptr));
+                continue;
+            }
+            for (int c = 0; c < C; ++c)
+                LCHK(relax_pass(ctx, lv, c, s == 0 ? PASS_ZERO : PASS_NORMAL, f, u, nullptr));
+        }
+        if (jac) { tpmg_status st = finish_in_u(); if (st != TPMG_OK) return st; }
+    }
+    // residual, restriction, recursion with zero guess
+    LevelDev &co = ctx->lv[l - 1];
+    LCHK(run(ctx, TPMG_K_RESTRICT, (double)lv.n * p.n_r,
+             [&] { return launch_resid_restrict(L, lv, co, ctx->vert, f, u, co.f); }));
+    tpmg_status st = vcycle_level(ctx, l - 1, co.f, co.u, co.u2);
+    if (st != TPMG_OK) return st;
+    // coarse-grid correction fused into the first post-smoothing sweep (reverse colours)
+    if (p.nu_post == 0) {
+        LCHK(run(ctx, TPMG_K_PROLONG, (double)lv.n * p.n_r, [&] { return launch_prolong_add(L, lv, co.u, u); }));
+        return TPMG_OK;
+    }
+    for (int s = 0; s < p.nu_post; ++s) {
+        const int mode = s == 0 ? PASS_PROLONG : PASS_NORMAL;
+        if (jac) {
+            LCHK(jacobi(mode, co.u));
+            continue;
+        }
+        for (int c = C - 1; c >= 0; --c)
+            LCHK(relax_pass(ctx, lv, c, mode, f, u, co.u));
+    }
+    return jac ? finish_in_u() : TPMG_OK;
+}
+
+tpmg_status vcycle_fine(tpmg_ctx *ctx, const double *r, double *z)
+{
+    const int l = ctx->p.n_levels - 1;
+    return vcycle_level(ctx, l, r, z, ctx->lv[l].u2);
+}
+
+tpmg_status read_scalars(tpmg_ctx *ctx)
+{
+    CU(cudaMemcpyAsync(ctx->h_sc, ctx->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return TPMG_OK;
+}
+
+tpmg_status pcg(tpmg_ctx *ctx, const double *f, double *u, double rtol, int max_iter, int *iters, double *rel,
+                double *hist)
+{
+    const Launch L = launch_of(ctx);
+    LevelDev &fl = ctx->lv[ctx->p.n_levels - 1];
+    const long N = ctx->N;
+    const int np = ctx->n_part;
+    *iters = 0;
+    *rel = 1.0;
+    LCHK(run(ctx, TPMG_K_RESIDUAL, (double)N, [&] { return launch_residual(L, fl, ctx->vert, f, u, ctx->r, ctx->partials, np); }));
+    LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_RR0, ctx->partials, np, ctx->sc); }));
+    tpmg_status st = read_scalars(ctx);
+    if (st != TPMG_OK) return st;
+    const double rr0 = ctx->h_sc->rr0;
+    if (hist) hist[0] = 1.0;
+    if (!std::isfinite(rr0)) return fail(ctx, TPMG_ERR_BREAKDOWN, "initial residual is not finite");
+    if (rr0 == 0.0) { *rel = 0.0; return TPMG_OK; }
+    if ((st = vcycle_fine(ctx, ctx->r, ctx->z)) != TPMG_OK) return st;
+    LCHK(run(ctx, TPMG_K_DOT, (double)N, [&] { return launch_dot(L, N, ctx->r, ctx->z, ctx->partials, np); }));
+    LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_RZ0, ctx->partials, np, ctx->sc); }));
+    LCHK(run(ctx, TPMG_K_COPY, (double)N, [&] { return cudaMemcpyAsync(ctx->pv, ctx->z, sizeof(double) * N, cudaMemcpyDeviceToDevice, ctx->stream); }));
+    for (int it = 0; it < max_iter; ++it) {
+        LCHK(run(ctx, TPMG_K_APPLY, (double)N, [&] { return launch_apply(L, fl, ctx->vert, ctx->pv, ctx->q, ctx->partials, np); }));
+        LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_ALPHA, ctx->partials, np, ctx->sc); }));
+        LCHK(run(ctx, TPMG_K_AXPY, (double)N, [&] { return launch_axpy_pair(L, N, ctx->sc, ctx->pv, ctx->q, u, ctx->r, ctx->partials, np); }));
+        LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_RR, ctx->partials, np, ctx->sc); }));
+        if ((st = read_scalars(ctx)) != TPMG_OK) return st;
+        const Scalars &s = *ctx->h_sc;
+        if (s.flag & 1) return fail(ctx, TPMG_ERR_BREAKDOWN, "p.Ap <= 0: operator or preconditioner not SPD");
+        if (s.flag & 2) return fail(ctx, TPMG_ERR_BREAKDOWN, "non-finite residual");
+        *iters = it + 1;
+        *rel = std::sqrt(s.rr / rr0);
+        if (hist) hist[it + 1] = *rel;
+        if (*rel <= rtol) return TPMG_OK;
+        if (it + 1 == max_iter) break;
+        if ((st = vcycle_fine(ctx, ctx->r, ctx->z)) != TPMG_OK) return st;
+        LCHK(run(ctx, TPMG_K_DOT, (double)N, [&] { return launch_dot(L, N, ctx->r, ctx->z, ctx->partials, np); }));
+        LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_BETA, ctx->partials, np, ctx->sc); }));
+        LCHK(run(ctx, TPMG_K_XPBY, (double)N, [&] { return launch_xpby(L, N, ctx->sc, ctx->z, ctx->pv); }));
+    }
+    return fail(ctx, TPMG_ERR_NOT_CONVERGED, "max_iter reached before rtol");
+}
+
+tpmg_status upload_level(tpmg_ctx *ctx, int l)
+{
+    const tpmg_params &p = ctx->p;
+    const HostLevel &H = ctx->host.lev[p.refinement - (p.n_levels - 1 - l)];
+    LevelDev &D = ctx->lv[l];
+    D.n = H.n;
+    D.ref = H.ref;
+    D.n_colours = H.n_colours;
+    std::vector<int4> nb(H.n);
+    std::vector<dbl4> g(H.n);
+    for (int T = 0; T < H.n; ++T) {
+        int mask = 0;
+        for (int e = 0; e < 3; ++e)
+            if (H.colour[H.nbr[3 * T + e]] < H.colour[T]) mask |= 1 << e;
+        nb[T] = make_int4(H.nbr[3 * T], H.nbr[3 * T + 1], H.nbr[3 * T + 2], mask);
+        const double g0 = H.g[3 * T], g1 = H.g[3 * T + 1], g2 = H.g[3 * T + 2];
+        g[T] = dbl4{g0, g1, g2, (g0 + g1) + g2};
+    }
+    std::vector<int> cells;
+    D.colour_off.assign(H.n_colours + 1, 0);
+    for (int c = 0; c < H.n_colours; ++c) {
+        D.colour_off[c] = (int)cells.size();
+        for (int T = 0; T < H.n; ++T)
+            if (H.colour[T] == c) cells.push_back(T);
+    }
+    D.colour_off[H.n_colours] = (int)cells.size();
+    const size_t n = H.n, nn = (size_t)H.n * p.n_r;
+    CU(dalloc(ctx, &D.nbr, n));
+    CU(dalloc(ctx, &D.g, n));
+    CU(dalloc(ctx, &D.area, n));
+    CU(dalloc(ctx, &D.cells_by_colour, n));
+    CU(dalloc(ctx, &D.inv, nn));
+    CU(dalloc(ctx, &D.ef, nn));
+    CU(dalloc(ctx, &D.cpf, nn));
+    CU(dalloc(ctx, &D.u2, nn));
+    if (l < p.n_levels - 1) {
+        CU(dalloc(ctx, &D.f, nn));
+        CU(dalloc(ctx, &D.u, nn));
+    }
+    CU(cudaMemcpyAsync(D.nbr, nb.data(), n * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(D.g, g.data(), n * sizeof(dbl4), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(D.area, H.area.data(), n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(D.cells_by_colour, cells.data(), n * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    CU(launch_thomas_factors(launch_of(ctx), D, ctx->vert));
+    // the host vectors above must outlive the asynchronous copies
+    CU(cudaStreamSynchronize(ctx->stream));
+    return TPMG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tpmg_status tpmg_default_params(tpmg_params *p)
+{
+    if (!p) return TPMG_ERR_INVALID_ARG;
+    std::memset(p, 0, sizeof(*p));
+    p->refinement = 3;
+    p->n_levels = 4;
+    p->n_r = 16;
+    p->H = 10.0 / 6371.0;
+    p->grading = 1.0;
+    p->omega2 = 0.0;
+    p->courant_c = 8.0;
+    p->nu_pre = 2;
+    p->nu_post = 2;
+    p->nu_coarse = 1;
+    p->smoother = TPMG_SMOOTH_MCSOR;
+    p->relax = 1.0;
+    p->coeff_storage = TPMG_COEFF_FACTORISED;
+    p->centre = TPMG_CENTRE_CIRCUM;
+    p->precision = TPMG_PREC_FP64;
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_setup(const tpmg_params *params, void *cuda_stream, tpmg_ctx **out)
+{
+    std::string msg;
+    if (!out) return TPMG_ERR_INVALID_ARG;
+    if (!validate(params, msg)) return TPMG_ERR_INVALID_ARG;
+    tpmg_ctx *ctx = new (std::nothrow) tpmg_ctx();
+    if (!ctx) return TPMG_ERR_OOM;
+    auto bail = [&](tpmg_status s) {
+        tpmg_destroy(ctx);
+        return s;
+    };
+    ctx->p = *params;
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (cudaGetDevice(&ctx->device) != cudaSuccess) return bail(TPMG_ERR_CUDA);
+    if (cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess)
+        return bail(TPMG_ERR_CUDA);
+    if (!build_host_grid(ctx->p, ctx->host, msg)) return bail(TPMG_ERR_INVALID_ARG);
+    const int n_r = ctx->p.n_r;
+    // vertical factors: dv | w | hr
+    {
+        const HostGrid &G = ctx->host;
+        std::vector<double> hv(3 * n_r + 1);
+        double *dv = hv.data(), *w = dv + n_r, *hr = w + n_r + 1;
+        for (int k = 0; k <= n_r; ++k) w[k] = G.omega2 * G.face[k];
+        for (int k = 0; k < n_r; ++k) {
+            dv[k] = (G.vol[k] + w[k]) + w[k + 1];
+            hr[k] = G.omega2 * G.dr[k];
+        }
+        tpmg_status st = TPMG_OK;
+        if (dalloc(ctx, &ctx->d_vert, hv.size()) != cudaSuccess) return bail(TPMG_ERR_OOM);
+        if (cudaMemcpyAsync(ctx->d_vert, hv.data(), hv.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+            st = TPMG_ERR_CUDA;
+        if (st != TPMG_OK) return bail(st);
+        ctx->vert.dv = ctx->d_vert;
+        ctx->vert.w = ctx->d_vert + n_r;
+        ctx->vert.hr = ctx->d_vert + 2 * n_r + 1;
+    }
+    ctx->lv.assign(ctx->p.n_levels, LevelDev());
+    for (int l = 0; l < ctx->p.n_levels; ++l) {
+        tpmg_status st = upload_level(ctx, l);
+        if (st != TPMG_OK) return bail(st);
+    }
+    ctx->N = (long)ctx->lv.back().n * n_r;
+    ctx->n_part = 2 * ctx->sm_count;
+    if (dalloc(ctx, &ctx->r, ctx->N) != cudaSuccess || dalloc(ctx, &ctx->z, ctx->N) != cudaSuccess ||
+        dalloc(ctx, &ctx->pv, ctx->N) != cudaSuccess || dalloc(ctx, &ctx->q, ctx->N) != cudaSuccess ||
+        dalloc(ctx, &ctx->hf, ctx->N) != cudaSuccess || dalloc(ctx, &ctx->hu, ctx->N) != cudaSuccess ||
+        dalloc(ctx, &ctx->partials, ctx->n_part) != cudaSuccess || dalloc(ctx, &ctx->sc, 1) != cudaSuccess)
+        return bail(TPMG_ERR_OOM);
+    if (cudaMallocHost(&ctx->h_sc, sizeof(Scalars)) != cudaSuccess) return bail(TPMG_ERR_OOM);
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return bail(TPMG_ERR_CUDA);
+    *out = ctx;
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_apply_operator(tpmg_ctx *ctx, const double *d_x, double *d_y)
+{
+    if (!ctx || !d_x || !d_y) return fail(ctx, TPMG_ERR_INVALID_ARG, "NULL argument");
+    if (d_x == d_y) return fail(ctx, TPMG_ERR_INVALID_ARG, "x and y must not overlap");
+    LCHK(run(ctx, TPMG_K_APPLY, (double)ctx->N,
+             [&] { return launch_apply(launch_of(ctx), ctx->lv.back(), ctx->vert, d_x, d_y, nullptr, 0); }));
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_vcycle(tpmg_ctx *ctx, const double *d_r, double *d_z)
+{
+    if (!ctx || !d_r || !d_z) return fail(ctx, TPMG_ERR_INVALID_ARG, "NULL argument");
+    if (d_r == d_z) return fail(ctx, TPMG_ERR_INVALID_ARG, "r and z must not overlap");
+    return vcycle_fine(ctx, d_r, d_z);
+}
+
+tpmg_status tpmg_solve(tpmg_ctx *ctx, const double *d_f, double *d_u, double rtol, int max_iter, int *iters,
+                       double *rel_resid, double *resid_hist)
+{
+    if (!ctx || !d_f || !d_u || !iters || !rel_resid) return fail(ctx, TPMG_ERR_INVALID_ARG, "NULL argument");
+    if (!(rtol >= 0.0) || max_iter < 0) return fail(ctx, TPMG_ERR_INVALID_ARG, "rtol must be >= 0, max_iter >= 0");
+    if (d_f == d_u) return fail(ctx, TPMG_ERR_INVALID_ARG, "f and u must not overlap");
+    return pcg(ctx, d_f, d_u, rtol, max_iter, iters, rel_resid, resid_hist);
+}
+
+tpmg_status tpmg_solve_host(tpmg_ctx *ctx, const double *h_f, double *h_u, double rtol, int max_iter, int *iters,
+                            double *rel_resid, double *resid_hist)
+{
+    if (!ctx || !h_f || !h_u || !iters || !rel_resid) return fail(ctx, TPMG_ERR_INVALID_ARG, "NULL argument");
+    if (!(rtol >= 0.0) || max_iter < 0) return fail(ctx, TPMG_ERR_INVALID_ARG, "rtol must be >= 0, max_iter >= 0");
+    const size_t bytes = sizeof(double) * ctx->N;
+    CU(cudaMemcpyAsync(ctx->hf, h_f, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->hu, h_u, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    tpmg_status st = pcg(ctx, ctx->hf, ctx->hu, rtol, max_iter, iters, rel_resid, resid_hist);
+    CU(cudaMemcpyAsync(h_u, ctx->hu, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return st;
+}
+
+tpmg_status tpmg_query(const tpmg_ctx *ctx, int level, int *n_cells, int *n_r, double *omega2, int *n_colours)
+{
+    if (!ctx || level < 0 || level >= ctx->p.n_levels) return TPMG_ERR_INVALID_ARG;
+    if (n_cells) *n_cells = ctx->lv[level].n;
+    if (n_r) *n_r = ctx->p.n_r;
+    if (omega2) *omega2 = ctx->host.omega2;
+    if (n_colours) *n_colours = ctx->lv[level].n_colours;
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_export_mesh(const tpmg_ctx *ctx, int level, double *centres, double *areas, int *nbrs, double *g,
+                             int *colour, double *r_faces)
+{
+    if (!ctx || level < 0 || level >= ctx->p.n_levels) return TPMG_ERR_INVALID_ARG;
+    const HostLevel &H = ctx->host.lev[ctx->p.refinement - (ctx->p.n_levels - 1 - level)];
+    if (centres) std::memcpy(centres, H.centre.data(), H.centre.size() * sizeof(double));
+    if (areas) std::memcpy(areas, H.area.data(), H.area.size() * sizeof(double));
+    if (nbrs) std::memcpy(nbrs, H.nbr.data(), H.nbr.size() * sizeof(int));
+    if (g) std::memcpy(g, H.g.data(), H.g.size() * sizeof(double));
+    if (colour) std::memcpy(colour, H.colour.data(), H.colour.size() * sizeof(int));
+    if (r_faces) std::memcpy(r_faces, ctx->host.r.data(), ctx->host.r.size() * sizeof(double));
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_profile(tpmg_ctx *ctx, unsigned class_mask)
+{
+    if (!ctx) return TPMG_ERR_INVALID_ARG;
+    if (class_mask >> TPMG_K_COUNT) return fail(ctx, TPMG_ERR_INVALID_ARG, "unknown kernel class in mask");
+    CU(cudaStreamSynchronize(ctx->stream));
+    Tracer &t = ctx->tr;
+    t.mask = class_mask;
+    std::fill(t.launches, t.launches + TPMG_K_COUNT, 0LL);
+    std::fill(t.units, t.units + TPMG_K_COUNT, 0.0);
+    t.used = 0;
+    if (class_mask) CU(grow_events(t, 8192));   // created here, outside any timed region
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_profile_read(tpmg_ctx *ctx, int kernel_class, long long *launches, double *total_ms, double *units)
+{
+    if (!ctx || kernel_class < 0 || kernel_class >= TPMG_K_COUNT) return fail(ctx, TPMG_ERR_INVALID_ARG, "bad class");
+    CU(cudaStreamSynchronize(ctx->stream));
+    const Tracer &t = ctx->tr;
+    double ms = 0.0;
+    for (size_t i = 0; i < t.used; ++i) {
+        if (t.cls[i] != kernel_class) continue;
+        float m = 0.f;
+        CU(cudaEventElapsedTime(&m, t.ev[2 * i], t.ev[2 * i + 1]));
+        ms += m;
+    }
+    if (launches) *launches = t.launches[kernel_class];
+    if (total_ms) *total_ms = ms;
+    if (units) *units = t.units[kernel_class];
+    return TPMG_OK;
+}
+
+const char *tpmg_status_string(tpmg_status s)
+{
+    const int i = (int)s;
+    return (i >= 0 && i < (int)(sizeof(kStatus) / sizeof(kStatus[0]))) ? kStatus[i] : "TPMG_UNKNOWN_STATUS";
+}
+
+const char *tpmg_last_error(const tpmg_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+void tpmg_destroy(tpmg_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (void *p : ctx->allocs) cudaFree(p);
+    if (ctx->h_sc) cudaFreeHost(ctx->h_sc);
+    for (cudaEvent_t e : ctx->tr.ev) cudaEventDestroy(e);
+    delete ctx;
+}
+
+}  // extern "C"
