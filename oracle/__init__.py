@@ -76,6 +76,8 @@ def _load(path: str | None = None):
         lib.oracle_pcg.argtypes = [_P, _P, _P, _D, _I, _P, _P, _P, _P]
         lib.oracle_richardson.argtypes = [_P, _P, _P, _I, _P]
         lib.oracle_thomas.argtypes = [_I, _P, _P, _P, _P, _P]
+        lib.oracle_column_solve.argtypes = [_I, _P, _P, _P, _P]
+        lib.oracle_column_couplings.argtypes = [_P, _I, _P, _P]
         _libs[key] = lib
         if path is None:
             _lib = lib
@@ -100,6 +102,17 @@ def thomas(a, b, c, d, lib_path: str | None = None) -> np.ndarray:
     x = np.empty(n)
     if _load(lib_path).oracle_thomas(n, _ptr(a), _ptr(b), _ptr(c), _ptr(d), _ptr(x)) != 0:
         raise ValueError("oracle_thomas failed")
+    return x
+
+
+def column_solve(c, m, d, lib_path: str | None = None) -> np.ndarray:
+    """Solve the column block with couplings c[1..n-1] (c[0] unused) and diagonal
+    excess m (diagonal = m_k + c_k + c_{k+1}) for right-hand side d."""
+    c, m, d = (_f64(v) for v in (c, m, d))
+    n = d.shape[0]
+    x = np.empty(n)
+    if _load(lib_path).oracle_column_solve(n, _ptr(c), _ptr(m), _ptr(d), _ptr(x)) != 0:
+        raise ValueError("oracle_column_solve failed")
     return x
 
 
@@ -192,6 +205,14 @@ class Oracle:
         sub, diag, sup = (np.zeros((n, self.n_r)) for _ in range(3))
         self._lib.oracle_column_blocks(self._h, level, _ptr(sub), _ptr(diag), _ptr(sup))
         return sub, diag, sup
+
+    def column_couplings(self, level: int | None = None):
+        """(c, m) [n_cells, n_r]: coupling to the level below and diagonal excess per row."""
+        level = self.n_levels - 1 if level is None else level
+        n = self.level_cells(level)
+        c, m = np.zeros((n, self.n_r)), np.zeros((n, self.n_r))
+        self._lib.oracle_column_couplings(self._h, level, _ptr(c), _ptr(m))
+        return c, m
 
     def smooth(self, f, u, sweeps: int = 1, direction: int = 1, level: int | None = None) -> np.ndarray:
         level = self.n_levels - 1 if level is None else level

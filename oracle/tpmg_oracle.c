@@ -319,12 +319,11 @@ static double alphar_hat(const octx *o, const ogrid *G, int T, int face)
     return o->omega2 * G->area[T] * o->arv[face];
 }
 
-/* Column T of the operator (eq. ColumnEquation, TridiagonalSystem; Reading C2):
- *   (A u)_{T,k} = a_{T,k} u_{T,k} + b_{T,k} u_{T,k+1} + c_{T,k-1} u_{T,k-1}
- *                 + sum_T' d_{TT',k} u_{T',k}
- * with off-diagonals b_{T,k} = c_{T,k} = -alphar_hat_{T,k+1} (face k+1 couples
- * levels k and k+1), d_{TT',k} = -alphaS_hat_{TT',k}, and diagonal
- * a_{T,k} = beta_hat_{T,k} minus the sum of all off-diagonals of the row. */
+/* Column T of the operator as a tridiagonal matrix (eq. ColumnEquation,
+ * TridiagonalSystem; Reading C2): off-diagonals -alphar_hat_{T,k} (face k couples
+ * levels k-1 and k), d_{TT',k} = -alphaS_hat_{TT',k}, and diagonal a_{T,k} =
+ * beta_hat_{T,k} minus the sum of all off-diagonals of the row.  Exported for
+ * the tests; the solver itself works with the flux form below. */
 static void column_matrix(const octx *o, const ogrid *G, int T, double *sub, double *diag, double *sup)
 {
     int k, e, n = o->n_r;
@@ -337,25 +336,37 @@ static void column_matrix(const octx *o, const ogrid *G, int T, double *sub, dou
     }
 }
 
+/* (A u)_{T,k} in the flux form in which Appendix A derives it: the mass term
+ * plus the vertical fluxes through faces k and k+1 (eq. VerticalDiffusion) and
+ * the horizontal two-point fluxes through the edges of T, each a coupling times
+ * a difference of neighbouring values:
+ *   beta_hat u_{T,k} + alphar_hat_{T,k} (u_{T,k} - u_{T,k-1})
+ *     + alphar_hat_{T,k+1} (u_{T,k} - u_{T,k+1}) + sum_T' alphaS_hat_{TT',k} (u_{T,k} - u_{T',k}).
+ * Reading C2 fixes the signs (a conservative flux difference).  Summing the
+ * tridiagonal entries first would round the large diagonal and perturb the
+ * nearly singular vertically constant mode of the column by eps * cond. */
+static double apply_row(const octx *o, const ogrid *G, const double *u, int T, int k)
+{
+    int n = o->n_r, e;
+    size_t i = (size_t)T * n + k;
+    double s = beta_hat(o, G, T, k) * u[i];
+    if (k > 0) s += alphar_hat(o, G, T, k) * (u[i] - u[i - 1]);
+    if (k < n - 1) s += alphar_hat(o, G, T, k + 1) * (u[i] - u[i + 1]);
+    for (e = 0; e < 3; ++e) s += alphaS_hat(o, G, T, e, k) * (u[i] - u[(size_t)G->nbr[3 * T + e] * n + k]);
+    return s;
+}
+
 static void apply_level(octx *o, int l, const double *u, double *y)
 {
     const ogrid *G = mg_grid(o, l);
-    int n = o->n_r, T, k, e;
-    for (T = 0; T < G->n_cells; ++T) {
-        column_matrix(o, G, T, o->col_a, o->col_b, o->col_c);
-        for (k = 0; k < n; ++k) {
-            double s = o->col_b[k] * u[(size_t)T * n + k];
-            if (k > 0) s += o->col_a[k] * u[(size_t)T * n + k - 1];
-            if (k < n - 1) s += o->col_c[k] * u[(size_t)T * n + k + 1];
-            for (e = 0; e < 3; ++e)
-                s -= alphaS_hat(o, G, T, e, k) * u[(size_t)G->nbr[3 * T + e] * n + k];
-            y[(size_t)T * n + k] = s;
-        }
-    }
+    int n = o->n_r, T, k;
+    for (T = 0; T < G->n_cells; ++T)
+        for (k = 0; k < n; ++k) y[(size_t)T * n + k] = apply_row(o, G, u, T, k);
 }
 
-/* Thomas algorithm for tridiag(a, b, c) x = d, no pivoting: forward
- * elimination then back substitution.  a[0] and c[n-1] are not used. */
+/* Textbook Thomas algorithm for a general tridiag(a, b, c) x = d, no pivoting:
+ * forward elimination then back substitution.  a[0] and c[n-1] are not used.
+ * (Exported for the tests; the smoother uses oracle_column_solve.) */
 int oracle_thomas(int n, const double *a, const double *b, const double *c, const double *d, double *x)
 {
     double *cp, *dp;
@@ -378,6 +389,43 @@ int oracle_thomas(int n, const double *a, const double *b, const double *c, cons
     return 0;
 }
 
+/* Thomas algorithm for the column block A_T, given -- as it arises in the flux
+ * form -- by its vertical couplings c_k >= 0 between levels k-1 and k
+ * (k = 1..n-1; A_T has -c_k off the diagonal) and the excess m_k > 0 of each
+ * diagonal entry over the couplings of its row (diagonal = m_k + c_k + c_{k+1},
+ * here m_k = beta_hat + sum_T' alphaS_hat).  Forward elimination and back
+ * substitution as in the textbook algorithm; the pivots are carried through
+ * their excess e_k = pivot_k - c_{k+1}, which obeys
+ *     e_0 = m_0,   e_k = m_k + c_k e_{k-1} / pivot_{k-1},
+ * a sum of non-negative terms.  (Eliminating row k-1 from row k subtracts
+ * c_k^2 / pivot_{k-1} = c_k - c_k e_{k-1} / pivot_{k-1} from the diagonal.)
+ * The textbook pivot b_k - c_k^2 / pivot_{k-1} cancels catastrophically when the
+ * couplings dwarf the mass term, as they do in a thin shell. */
+int oracle_column_solve(int n, const double *c, const double *m, const double *d, double *x)
+{
+    double *piv, *y;
+    int k;
+    if (n < 1) return -1;
+    piv = (double *)malloc((size_t)n * sizeof(double));
+    y = (double *)malloc((size_t)n * sizeof(double));
+    if (!piv || !y) { free(piv); free(y); return -2; }
+    {
+        double e = m[0];
+        piv[0] = e + (n > 1 ? c[1] : 0.0);
+        y[0] = d[0] / piv[0];
+        for (k = 1; k < n; ++k) {
+            e = m[k] + c[k] * e / piv[k - 1];
+            piv[k] = e + (k < n - 1 ? c[k + 1] : 0.0);
+            y[k] = (d[k] + c[k] * y[k - 1]) / piv[k];
+        }
+    }
+    x[n - 1] = y[n - 1];
+    for (k = n - 2; k >= 0; --k) x[k] = y[k] + c[k + 1] / piv[k] * x[k + 1];
+    free(piv);
+    free(y);
+    return 0;
+}
+
 /* Block relaxation of column T (eq. BlockJacobi):
  *   u_T <- u_T + rho * A_T^{-1} (f_T - (A u)_T),
  * A_T the tridiagonal diagonal block of the column. */
@@ -385,16 +433,14 @@ static void relax_column(octx *o, int l, int T, const double *f, const double *u
 {
     const ogrid *G = mg_grid(o, l);
     int n = o->n_r, k, e;
-    column_matrix(o, G, T, o->col_a, o->col_b, o->col_c);
     for (k = 0; k < n; ++k) {
-        double s = o->col_b[k] * u_in[(size_t)T * n + k];
-        if (k > 0) s += o->col_a[k] * u_in[(size_t)T * n + k - 1];
-        if (k < n - 1) s += o->col_c[k] * u_in[(size_t)T * n + k + 1];
-        for (e = 0; e < 3; ++e)
-            s -= alphaS_hat(o, G, T, e, k) * u_in[(size_t)G->nbr[3 * T + e] * n + k];
-        o->col_d[k] = f[(size_t)T * n + k] - s;
+        double hs = 0.0;
+        for (e = 0; e < 3; ++e) hs += alphaS_hat(o, G, T, e, k);
+        o->col_a[k] = alphar_hat(o, G, T, k);          /* coupling to level k-1 (face k) */
+        o->col_b[k] = beta_hat(o, G, T, k) + hs;        /* excess of the diagonal */
+        o->col_d[k] = f[(size_t)T * n + k] - apply_row(o, G, u_in, T, k);
     }
-    oracle_thomas(n, o->col_a, o->col_b, o->col_c, o->col_d, o->col_x);
+    oracle_column_solve(n, o->col_a, o->col_b, o->col_d, o->col_x);
     for (k = 0; k < n; ++k) u_out[(size_t)T * n + k] = u_in[(size_t)T * n + k] + o->relax * o->col_x[k];
 }
 
@@ -667,6 +713,26 @@ int oracle_column_blocks(void *h, int l, double *sub, double *diag, double *sup)
     G = mg_grid(o, l);
     for (T = 0; T < G->n_cells; ++T)
         column_matrix(o, G, T, sub + (size_t)T * o->n_r, diag + (size_t)T * o->n_r, sup + (size_t)T * o->n_r);
+    return 0;
+}
+
+/* Column data of the flux form on level l, [n_cells][n_r]: coupling c to the
+ * level below (face k; c[.][0] = 0) and diagonal excess m = beta_hat + sum alphaS_hat. */
+int oracle_column_couplings(void *h, int l, double *c, double *m)
+{
+    octx *o = (octx *)h;
+    const ogrid *G;
+    int T, k, e, n;
+    if (l < 0 || l >= o->n_levels) return -1;
+    G = mg_grid(o, l);
+    n = o->n_r;
+    for (T = 0; T < G->n_cells; ++T)
+        for (k = 0; k < n; ++k) {
+            double hs = 0.0;
+            for (e = 0; e < 3; ++e) hs += alphaS_hat(o, G, T, e, k);
+            c[(size_t)T * n + k] = alphar_hat(o, G, T, k);
+            m[(size_t)T * n + k] = beta_hat(o, G, T, k) + hs;
+        }
     return 0;
 }
 

@@ -35,7 +35,7 @@ struct tpmg_ctx {
     HostGrid host;
     std::vector<LevelDev> lv;     // multigrid levels, 0 = coarsest
     VertDev vert{};
-    double *d_vert = nullptr;     // backing store of vert (dv | w | hr)
+    double *d_vert = nullptr;     // backing store of vert (vol | w | hr)
     long N = 0;                   // fine-level unknowns
     // PCG vectors (fine level)
     double *r = nullptr, *z = nullptr, *pv = nullptr, *q = nullptr;
@@ -379,14 +379,14 @@ tpmg_status tpmg_setup(const tpmg_params *params, void *cuda_stream, tpmg_ctx **
         return bail(TPMG_ERR_CUDA);
     if (!build_host_grid(ctx->p, ctx->host, msg)) return bail(TPMG_ERR_INVALID_ARG);
     const int n_r = ctx->p.n_r;
-    // vertical factors: dv | w | hr
+    // vertical factors: vol | w | hr
     {
         const HostGrid &G = ctx->host;
         std::vector<double> hv(3 * n_r + 1);
-        double *dv = hv.data(), *w = dv + n_r, *hr = w + n_r + 1;
+        double *vol = hv.data(), *w = vol + n_r, *hr = w + n_r + 1;
         for (int k = 0; k <= n_r; ++k) w[k] = G.omega2 * G.face[k];
         for (int k = 0; k < n_r; ++k) {
-            dv[k] = (G.vol[k] + w[k]) + w[k + 1];
+            vol[k] = G.vol[k];
             hr[k] = G.omega2 * G.dr[k];
         }
         tpmg_status st = TPMG_OK;
@@ -396,7 +396,7 @@ tpmg_status tpmg_setup(const tpmg_params *params, void *cuda_stream, tpmg_ctx **
             cudaStreamSynchronize(ctx->stream) != cudaSuccess)
             st = TPMG_ERR_CUDA;
         if (st != TPMG_OK) return bail(st);
-        ctx->vert.dv = ctx->d_vert;
+        ctx->vert.vol = ctx->d_vert;
         ctx->vert.w = ctx->d_vert + n_r;
         ctx->vert.hr = ctx->d_vert + 2 * n_r + 1;
     }

@@ -6,16 +6,20 @@
 // colour; double4 {g0, g1, g2, g0+g1+g2}; area |T|.  Vertical factors are
 // shared by all levels (no vertical coarsening, Sec. 3.3).
 //
-// The operator in Kronecker form (Sec. 3.3, constant profiles):
-//   (A x)_{T,k} = |T| (dv_k x_k - w_k x_{k-1} - w_{k+1} x_{k+1})
-//               + hr_k (G_T x_k - sum_e g_e x_{T_e,k}),
-// dv_k = v_k + w_k + w_{k+1}, w_k = omega^2 sigma_k 2 r_k^2/(r_{k+1}-r_{k-1}),
-// hr_k = omega^2 (r_{k+1}-r_k), G_T = sum_e g_e (Appendix A, eq. hatFunctionsFac).
+// The operator in the flux form of Appendix A (constant profiles, factorised
+// storage: per-level vertical vectors times per-cell scalars, Sec. 3.2):
+//   (A x)_{T,k} = |T| (v_k x_k + w_k (x_k - x_{k-1}) + w_{k+1} (x_k - x_{k+1}))
+//               + hr_k sum_e g_e (x_k - x_{T_e,k}),
+// w_k = omega^2 sigma_k 2 r_k^2/(r_{k+1}-r_{k-1}), hr_k = omega^2 (r_{k+1}-r_k).
+// Every coupling multiplies a difference, so the large vertical couplings never
+// round the nearly singular vertically constant mode of a column.
 //
-// On GB300 the FP64 pipe, not HBM, bounds this arithmetic, so every kernel
-// counts its FP64 instructions: address arithmetic is 32-bit integer, the
-// Thomas pivots are precomputed once per level, and the line relaxation with
-// rho = 1 forms u_T = A_T^{-1} (f_T - sum_T' A_TT' u_T') directly (no residual).
+// On GB300 the FP64 pipe, not HBM, bounds this arithmetic (a warp-wide FP64
+// instruction holds an SM sub-partition's FP64 unit for ~64 cycles whatever
+// the number of active lanes), so every kernel counts its FP64 instructions:
+// address arithmetic is 32-bit integer, the Thomas pivots are precomputed once
+// per level, and the line relaxation forms u_T = A_T^{-1} (f_T - sum_T' A_TT'
+// u_T') directly (no residual, no cancellation).
 #include <cuda_runtime.h>
 
 #include "tpmg_internal.h"
@@ -48,7 +52,7 @@ struct OpView {
     const int4 *__restrict__ nbr;
     const dbl4 *__restrict__ g;
     const double *__restrict__ area;
-    const double *__restrict__ dv;
+    const double *__restrict__ vol;
     const double *__restrict__ w;
     const double *__restrict__ hr;
     int n_r;
@@ -56,21 +60,21 @@ struct OpView {
 
 inline OpView make_view(const LevelDev &lv, const VertDev &v, int n_r)
 {
-    return OpView{lv.nbr, lv.g, lv.area, v.dv, v.w, v.hr, n_r};
+    return OpView{lv.nbr, lv.g, lv.area, v.vol, v.w, v.hr, n_r};
 }
 
-// (A x)_{T,k}: 9 FP64 instructions.
+// (A x)_{T,k} in flux form: 13 FP64 instructions.
 __device__ __forceinline__ double apply_at(const OpView &o, const double *__restrict__ x, int T, int k, int i)
 {
     const int n_r = o.n_r;
     const int4 nb = __ldg(&o.nbr[T]);
     const dbl4 g = o.g[T];
     const double xc = x[i];
-    const double xm = k > 0 ? x[i - 1] : 0.0;
-    const double xp = k < n_r - 1 ? x[i + 1] : 0.0;
-    const double kx = fma(-__ldg(&o.w[k + 1]), xp, fma(-__ldg(&o.w[k]), xm, __ldg(&o.dv[k]) * xc));
-    const double h = fma(-g.z, x[nb.z * n_r + k], fma(-g.y, x[nb.y * n_r + k], fma(-g.x, x[nb.x * n_r + k], g.w * xc)));
-    return fma(__ldg(&o.area[T]), kx, __ldg(&o.hr[k]) * h);
+    const double dm = k > 0 ? xc - x[i - 1] : 0.0;
+    const double dp = k < n_r - 1 ? xc - x[i + 1] : 0.0;
+    const double vert = fma(__ldg(&o.w[k + 1]), dp, fma(__ldg(&o.w[k]), dm, __ldg(&o.vol[k]) * xc));
+    const double hor = fma(g.z, xc - x[nb.z * n_r + k], fma(g.y, xc - x[nb.y * n_r + k], g.x * (xc - x[nb.x * n_r + k])));
+    return fma(__ldg(&o.area[T]), vert, __ldg(&o.hr[k]) * hor);
 }
 
 template <int NT>
@@ -133,9 +137,13 @@ __global__ void __launch_bounds__(NT) k_prolong_add(const double *__restrict__ u
     }
 }
 
-// Thomas pivots of the column block A_T = |T| K + hr G_T (one thread per column):
-// pivot_k = b_k - (|T| w_k)^2 / pivot_{k-1};  inv = 1/pivot, ef = |T| w_k inv_k,
-// cpf = |T| w_{k+1} inv_k, so that the solve is
+// Thomas pivots of the column block A_T (one thread per column).  A_T has
+// couplings c_k = |T| w_k to the level below, c_{k+1} above, and diagonal
+// c_k + c_{k+1} + m_k with excess m_k = |T| v_k + hr_k G_T.  The pivots are
+// carried through their excess, e_0 = m_0, e_k = m_k + c_k e_{k-1} / p_{k-1},
+// p_k = e_k + c_{k+1}: only sums of non-negative terms, so they keep full
+// relative precision although c_k / m_k reaches 1e6-1e9 in a thin shell.
+// Stored: inv = 1/p_k, ef = c_k/p_k, cpf = c_{k+1}/p_k, so that the solve is
 //   y_k = rhs_k inv_k + ef_k y_{k-1};   x_k = y_k + cpf_k x_{k+1}.
 __global__ void k_factors(int n, OpView o, double *__restrict__ inv, double *__restrict__ ef, double *__restrict__ cpf)
 {
@@ -143,15 +151,16 @@ __global__ void k_factors(int n, OpView o, double *__restrict__ inv, double *__r
     if (T >= n) return;
     const int n_r = o.n_r;
     const double A = o.area[T], Gs = o.g[T].w;
-    double prev = 0.0;
+    double e = 0.0, p = 1.0;
     for (int k = 0; k < n_r; ++k) {
-        const double b = A * o.dv[k] + o.hr[k] * Gs;
-        const double sub = A * o.w[k];
-        const double iv = 1.0 / (b - sub * sub * prev);
+        const double m = A * o.vol[k] + o.hr[k] * Gs;
+        const double c = A * o.w[k], cu = A * o.w[k + 1];
+        e = k == 0 ? m : m + c * e / p;
+        p = e + cu;
+        const double iv = 1.0 / p;
         inv[T * n_r + k] = iv;
-        ef[T * n_r + k] = sub * iv;
-        cpf[T * n_r + k] = A * o.w[k + 1] * iv;
-        prev = iv;
+        ef[T * n_r + k] = c * iv;
+        cpf[T * n_r + k] = cu * iv;
     }
 }
 

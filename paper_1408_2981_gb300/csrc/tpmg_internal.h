@@ -46,10 +46,10 @@ struct alignas(32) dbl4 {   // four doubles, one 32-byte load
     double x, y, z, w;
 };
 struct VertDev {            // vertical factors shared by every level (no vertical coarsening)
-    const double *dv;       // [n_r]   v_k + w_k + w_{k+1}
+    const double *vol;      // [n_r]   v_k = (r_{k+1}^3 - r_k^3)/3
     const double *w;        // [n_r+1] omega^2 sigma_k 2 r_k^2 / (r_{k+1} - r_{k-1})
     const double *hr;       // [n_r]   omega^2 (r_{k+1} - r_k)
-    const float *dv32, *w32, *hr32;   // FP32 copies for the mixed-precision V-cycle
+    const float *vol32, *w32, *hr32;  // FP32 copies for the mixed-precision V-cycle
 };
 
 struct LevelDev {

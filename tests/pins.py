@@ -172,17 +172,15 @@ def _horizontal_laplacian(g):
 
 def pin_constants_in_kernel(ns):
     """The diffusion terms are flux differences that vanish on constants
-    (Appendix A), so A 1 = beta_hat = |T| v_k on every level."""
+    (Appendix A), so A 1 = beta_hat = |T| v_k on every level -- exactly, since
+    every flux multiplies a difference 1 - 1 = 0."""
     for kw in SMALL_CASES + [dict(refinement=4, n_levels=3, n_r=16, grading=1.05, courant_c=80.0)]:
         o = ns.Oracle(**kw)
         v = o.vertical()
         for level in range(o.n_levels):
             g = o.grid(o.level_ref(level))
             y = o.apply(np.ones(o.size(level)), level)
-            beta = np.outer(g["area"], v["vol"]).reshape(-1)
-            sub, diag, sup = o.column_blocks(level)
-            bound = 16 * EPS * 2.0 * diag.reshape(-1)
-            assert np.all(np.abs(y - beta) <= bound), np.max(np.abs(y - beta) / bound)
+            np.testing.assert_array_equal(y, np.outer(g["area"], v["vol"]).reshape(-1))
 
 
 def pin_symmetric_spd(ns):
@@ -264,7 +262,8 @@ def pin_vertical_consistency(ns):
 # ----------------------------------------------------------------------------- Thomas
 def pin_thomas(ns):
     """Thomas algorithm (Sec. 4.1) against dense LU with partial pivoting on random
-    diagonally dominant systems, n = 1..16, and on actual column blocks A_T."""
+    diagonally dominant systems, n = 1..16, and on actual column blocks A_T; the
+    same for the column solve that takes A_T as couplings + diagonal excess."""
     rng = np.random.default_rng(5)
     for n in range(1, 17):
         for _ in range(5):
@@ -276,15 +275,63 @@ def pin_thomas(ns):
             x = ns.thomas(a, b, c, d)
             xd = np.linalg.solve(Ad, d)
             np.testing.assert_allclose(x, xd, rtol=1e-13, atol=1e-13 * np.max(np.abs(xd)))
-    o = ns.Oracle(refinement=2, n_levels=1, n_r=16, grading=1.05, courant_c=80.0)
+            cc = rng.uniform(0.0, 2.0, n)
+            cc[0] = 0.0
+            m = rng.uniform(0.1, 2.0, n)
+            nxt = np.append(cc[1:], 0.0)
+            Am = np.diag(m + cc + nxt) - np.diag(cc[1:], -1) - np.diag(cc[1:], 1)
+            xm = ns.column_solve(cc, m, d)
+            xmd = np.linalg.solve(Am, d)
+            np.testing.assert_allclose(xm, xmd, rtol=1e-13, atol=1e-13 * np.max(np.abs(xmd)))
+    o = ns.Oracle(refinement=2, n_levels=1, n_r=16, grading=1.05, H=0.05, courant_c=80.0)
     sub, diag, sup = o.column_blocks()
-    A = o.dense_operator() if o.size() <= 6000 else None
+    cpl, exc = o.column_couplings()
+    A = o.dense_operator()
     for T in (0, 7, 100, 319):
         d = rng.uniform(-1, 1, o.n_r)
-        x = ns.thomas(sub[T], diag[T], sup[T], d)
         blk = A[T * o.n_r:(T + 1) * o.n_r, T * o.n_r:(T + 1) * o.n_r]
         xd = np.linalg.solve(blk, d)
-        np.testing.assert_allclose(x, xd, rtol=1e-10, atol=1e-12 * np.max(np.abs(xd)))
+        np.testing.assert_allclose(ns.thomas(sub[T], diag[T], sup[T], d), xd, rtol=1e-10,
+                                   atol=1e-12 * np.max(np.abs(xd)))
+        np.testing.assert_allclose(ns.column_solve(cpl[T], exc[T], d), xd, rtol=1e-10,
+                                   atol=1e-12 * np.max(np.abs(xd)))
+
+
+def _exact_column_solve(c, m, d):
+    """Gaussian elimination in exact rational arithmetic on the matrix whose
+    entries are the given doubles: diagonal m_k + c_k + c_{k+1}, off-diagonal -c."""
+    from fractions import Fraction as Fr
+
+    n = len(d)
+    c = [Fr(float(v)) for v in c] + [Fr(0)]
+    c[0] = Fr(0)
+    diag = [Fr(float(m[k])) + c[k] + c[k + 1] for k in range(n)]
+    rhs = [Fr(float(v)) for v in d]
+    for k in range(1, n):
+        f = c[k] / diag[k - 1]
+        diag[k] -= f * c[k]
+        rhs[k] += f * rhs[k - 1]
+    x = [Fr(0)] * n
+    x[n - 1] = rhs[n - 1] / diag[n - 1]
+    for k in range(n - 2, -1, -1):
+        x[k] = (rhs[k] + c[k + 1] * x[k + 1]) / diag[k]
+    return np.array([float(v) for v in x])
+
+
+def pin_column_solve_exact(ns):
+    """On thin-shell columns (H = 10/6371, omega^2/h^2 = 80, graded: the vertical
+    couplings exceed the diagonal excess by ~1e6, cond(A_T) ~ 1e7) the column
+    solve equals the exact rational solution of the same matrix to a few ulp:
+    no step of the elimination may subtract nearly equal numbers."""
+    rng = np.random.default_rng(12)
+    o = ns.Oracle(refinement=3, n_levels=1, n_r=24, grading=1.05, courant_c=80.0)
+    cpl, exc = o.column_couplings()
+    assert cpl[:, 1:].max() / exc.min() > 1e6       # the regime that defeats textbook pivots
+    for T in (0, 77, 1279):
+        d = rng.uniform(-1, 1, o.n_r)
+        x = ns.column_solve(cpl[T], exc[T], d)
+        xe = _exact_column_solve(cpl[T], exc[T], d)
+        np.testing.assert_allclose(x, xe, rtol=64 * EPS * o.n_r, atol=0)
 
 
 # ----------------------------------------------------------------------------- transfers
@@ -499,6 +546,6 @@ def pin_robust_convergence(ns):
 ALL_PINS = [
     pin_mesh_counts, pin_mesh_areas, pin_level0_closed_forms, pin_mesh_topology, pin_vertical,
     pin_constants_in_kernel, pin_symmetric_spd, pin_kronecker, pin_horizontal_consistency,
-    pin_vertical_consistency, pin_thomas, pin_transfers, pin_vcycle_dense, pin_preconditioner_symmetric,
+    pin_vertical_consistency, pin_thomas, pin_column_solve_exact, pin_transfers, pin_vcycle_dense, pin_preconditioner_symmetric,
     pin_invariant_subspaces, pin_pcg_dense, pin_manufactured, pin_robust_convergence,
 ]

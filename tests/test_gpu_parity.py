@@ -4,9 +4,11 @@ Tolerances (derivations in the design notes):
 * grid: cell order, neighbours and colours bit-exact; centres to a few ulp;
   areas / flux factors to 1e-12 relative (different but equivalent formulas).
 * operator: 64 eps times |A| |x| per element (9 rounded operations per row).
-* V-cycle: 1e-9 relative in the 2-norm -- the column blocks have condition
-  numbers ~1e7 (vertical coupling over mass term), so two equivalent orderings
-  of the line solve differ by up to ~1e-16 * 1e7 per relaxation.
+* V-cycle: 1e-11 relative in the energy norm ||.||_A (and 1e-7 in the
+  2-norm).  The column blocks have condition numbers 1e6-1e9 (vertical
+  coupling over the mass term), so two equivalent orderings of the line solve
+  differ by ~eps * cond in the 2-norm, but that difference lies in the nearly
+  null vertically constant mode, whose energy is ~1/cond of a typical mode.
 * PCG: 1e-10 relative solution error (the accuracy target of the path).
 """
 import numpy as np
@@ -101,7 +103,10 @@ def test_vcycle_parity(name):
     s.vcycle(cuda(r), z)
     zg, zo = host(z), o.vcycle(r)
     assert np.all(np.isfinite(zg))
-    assert np.linalg.norm(zg - zo) <= 1e-9 * np.linalg.norm(zo), np.linalg.norm(zg - zo) / np.linalg.norm(zo)
+    e = zg - zo
+    rel_a = np.sqrt(e @ o.apply(e)) / np.sqrt(zo @ o.apply(zo))
+    assert rel_a <= 1e-11, rel_a
+    assert np.linalg.norm(e) <= 1e-7 * np.linalg.norm(zo), np.linalg.norm(e) / np.linalg.norm(zo)
 
 
 def solve_pair(s, o, f, rtol, max_iter=200):

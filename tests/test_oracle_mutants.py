@@ -19,16 +19,17 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 TESTS = os.path.join(ROOT, "tests")
 
 MUTANTS = {
-    "drop_horizontal_flux": (
-        "                s -= alphaS_hat(o, G, T, e, k) * u[(size_t)G->nbr[3 * T + e] * n + k];\n"
-        "            y[(size_t)T * n + k] = s;",
-        "                s -= 0.0 * u[(size_t)G->nbr[3 * T + e] * n + k];\n"
-        "            y[(size_t)T * n + k] = s;"),
-    "vertical_offdiag_sign": ("sub[k] = -lo;", "sub[k] = lo;"),
-    "upper_face_index": ("up = alphar_hat(o, G, T, k + 1)", "up = alphar_hat(o, G, T, k)"),
-    "neighbour_slot_shift": (
-        "u[(size_t)G->nbr[3 * T + e] * n + k];\n            y[",
-        "u[(size_t)G->nbr[3 * T + (e + 1) % 3] * n + k];\n            y["),
+    "drop_horizontal_flux": ("for (e = 0; e < 3; ++e) s += alphaS_hat(o, G, T, e, k) * (u[i] - u[",
+                             "for (e = 0; e < 3; ++e) s += 0.0 * alphaS_hat(o, G, T, e, k) * (u[i] - u["),
+    "vertical_flux_sign": ("s += alphar_hat(o, G, T, k) * (u[i] - u[i - 1]);",
+                           "s += alphar_hat(o, G, T, k) * (u[i] + u[i - 1]);"),
+    "upper_face_index": ("s += alphar_hat(o, G, T, k + 1) * (u[i] - u[i + 1]);",
+                         "s += alphar_hat(o, G, T, k) * (u[i] - u[i + 1]);"),
+    "neighbour_slot_shift": ("(u[i] - u[(size_t)G->nbr[3 * T + e] * n + k]);",
+                             "(u[i] - u[(size_t)G->nbr[3 * T + (e + 1) % 3] * n + k]);"),
+    "column_solve_excess": ("e = m[k] + c[k] * e / piv[k - 1];", "e = m[k] + c[k] / piv[k - 1];"),
+    "column_solve_back": ("x[k] = y[k] + c[k + 1] / piv[k] * x[k + 1];", "x[k] = y[k] + c[k] / piv[k] * x[k + 1];"),
+    "column_solve_forward": ("y[k] = (d[k] + c[k] * y[k - 1]) / piv[k];", "y[k] = (d[k] - c[k] * y[k - 1]) / piv[k];"),
     "thomas_forward_index": ("dp[i] = (d[i] - a[i] * dp[i - 1]) / den;", "dp[i] = (d[i] - a[i - 1] * dp[i - 1]) / den;"),
     "thomas_backward_index": ("x[i] = dp[i] - cp[i] * x[i + 1];", "x[i] = dp[i] - cp[i + 1] * x[i + 1];"),
     "restrict_child_index": ("s += rf[(size_t)(4 * T + j) * n + k];", "s += rf[(size_t)(4 * T) * n + k];"),
@@ -57,7 +58,7 @@ MUTANTS = {
     "colouring_looks_ahead": ("if (Tp < T) used[G->colour[Tp]] = 1;", "if (Tp > T) used[G->colour[Tp]] = 1;"),
     "grading_exponent": ("pow(grading, (double)k)", "pow(grading, (double)(k + 1))"),
     "relaxation_ignored": ("u_in[(size_t)T * n + k] + o->relax * o->col_x[k];", "u_in[(size_t)T * n + k] + o->col_x[k];"),
-    "diag_misses_mass": ("diag[k] = beta_hat(o, G, T, k) + lo + up + hs;", "diag[k] = lo + up + hs;"),
+    "diag_misses_mass": ("o->col_b[k] = beta_hat(o, G, T, k) + hs;", "o->col_b[k] = hs;"),
     "pcg_alpha_inverted": ("alpha = rz / pq;", "alpha = pq / rz;"),
     "coarse_sweep_one_way": ("smooth(o, l, f, u, o->nu_coarse, 0);", "smooth(o, l, f, u, o->nu_coarse, +1);"),
 }
@@ -68,7 +69,8 @@ DRIVER = textwrap.dedent("""
     import oracle, pins
     lib = sys.argv[1]
     ns = types.SimpleNamespace(Oracle=functools.partial(oracle.Oracle, lib_path=lib),
-                               thomas=functools.partial(oracle.thomas, lib_path=lib))
+                               thomas=functools.partial(oracle.thomas, lib_path=lib),
+                               column_solve=functools.partial(oracle.column_solve, lib_path=lib))
     for p in pins.ALL_PINS:
         try:
             p(ns)

@@ -8,7 +8,8 @@ import pins
 
 @pytest.fixture(scope="module")
 def ns(oracle_ns):
-    return types.SimpleNamespace(Oracle=oracle_ns.Oracle, thomas=oracle_ns.thomas)
+    return types.SimpleNamespace(Oracle=oracle_ns.Oracle, thomas=oracle_ns.thomas,
+                                 column_solve=oracle_ns.column_solve)
 
 
 @pytest.mark.parametrize("pin", pins.ALL_PINS, ids=lambda p: p.__name__)
