@@ -118,6 +118,37 @@ tpmg_status tpmg_apply_operator(tpmg_ctx *ctx, const double *d_x, double *d_y);
  * Errors: INVALID_ARG, CUDA. */
 tpmg_status tpmg_vcycle(tpmg_ctx *ctx, const double *d_r, double *d_z);
 
+/* Capacity, in doubles, of the fixed scratch array of tpmg_vcycle_noalloc
+ * (2^21 doubles = 16 MiB). */
+#define TPMG_VCYCLE_NOALLOC_MAX_DOUBLES (1u << 21)
+
+/* z = B r exactly as tpmg_vcycle computes it, for callers that must not let
+ * the library allocate device memory on their behalf: a host model that owns
+ * the device memory through its own pool and forbids other allocations once
+ * its time loop runs, or code for which the device synchronisation that
+ * cudaMalloc / cudaFree can cause is not acceptable.  This call allocates
+ * nothing: the work vectors of the coarse levels (and the second buffer of the
+ * block-Jacobi smoother) come from one fixed device array built into the
+ * library, of TPMG_VCYCLE_NOALLOC_MAX_DOUBLES doubles, which every GPU that
+ * loads the library holds until the process exits.  The context itself still
+ * comes from tpmg_setup, and this call neither reads nor writes the context's
+ * own work vectors.  The paper has no counterpart: this is an interface
+ * convenience, not part of the method.
+ *
+ * d_r, d_z: device, n_cells*n_r doubles, must not overlap; d_r is not modified.
+ * The context's device must be current.  Scratch needed: 2 * sum over the
+ * coarse levels of n_cells_l * n_r doubles for block-SOR, plus sum over all
+ * levels of n_cells_l * n_r for block Jacobi (each part rounded up to 32
+ * doubles); a larger problem is rejected with INVALID_ARG before anything is
+ * launched.  The first call on a device looks up the array's device address
+ * (once per device, with that device current); make that first call before
+ * any stream capture.  Every call on a device shares the one array and leaves
+ * the last call's values in it; no element is read before the call has written
+ * it, so nothing needs clearing.  Calls whose work overlaps on the GPU (other
+ * streams, other contexts, other threads) race on the array: order them.
+ * Asynchronous on the context stream.  Errors: INVALID_ARG, CUDA. */
+tpmg_status tpmg_vcycle_noalloc(tpmg_ctx *ctx, const double *d_r, double *d_z);
+
 /* Preconditioned CG for A u = f with B = one V-cycle.  d_u holds the initial
  * guess on entry and the solution on return.  Stops when ||r_k||_2 <=
  * rtol * ||r_0||_2 (recursively updated residual; Sec. 5 uses rtol = 1e-5).

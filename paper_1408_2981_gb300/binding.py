@@ -34,7 +34,8 @@ TPMG_PREC_FP64 = 0
 TPMG_PREC_MIXED = 1
 
 # every entry point declared in include/tpmg.h
-EXPORTS = ["tpmg_default_params", "tpmg_setup", "tpmg_apply_operator", "tpmg_vcycle", "tpmg_solve",
+EXPORTS = ["tpmg_default_params", "tpmg_setup", "tpmg_apply_operator", "tpmg_vcycle", "tpmg_vcycle_noalloc",
+           "tpmg_solve",
            "tpmg_solve_host", "tpmg_query", "tpmg_export_mesh", "tpmg_profile", "tpmg_profile_read",
            "tpmg_status_string", "tpmg_last_error", "tpmg_destroy"]
 
@@ -73,6 +74,7 @@ def load(path: str | None = None):
     lib.tpmg_setup.argtypes = [ctypes.POINTER(tpmg_params), P, ctypes.POINTER(P)]
     lib.tpmg_apply_operator.argtypes = [P, P, P]
     lib.tpmg_vcycle.argtypes = [P, P, P]
+    lib.tpmg_vcycle_noalloc.argtypes = [P, P, P]
     lib.tpmg_solve.argtypes = [P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D), P]
     lib.tpmg_solve_host.argtypes = [P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D), P]
     lib.tpmg_query.argtypes = [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(I)]
@@ -209,6 +211,12 @@ class Solver:
 
     def vcycle(self, r, z):
         self._check(self._lib.tpmg_vcycle(self._h, self._vec(r, "r"), self._vec(z, "z")), "tpmg_vcycle")
+
+    def vcycle_noalloc(self, r, z):
+        """z = B r like vcycle(), with the coarse-level work vectors in the
+        library's fixed device array instead of the context's (no allocation)."""
+        self._check(self._lib.tpmg_vcycle_noalloc(self._h, self._vec(r, "r"), self._vec(z, "z")),
+                    "tpmg_vcycle_noalloc")
 
     def solve(self, f, u, rtol: float = 1e-5, max_iter: int = 100, history: bool = False, raise_on_fail: bool = True):
         """PCG; u holds the initial guess and receives the solution.

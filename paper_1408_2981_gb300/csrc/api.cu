@@ -434,6 +434,51 @@ tpmg_status tpmg_vcycle(tpmg_ctx *ctx, const double *d_r, double *d_z)
     return vcycle_fine(ctx, d_r, d_z);
 }
 
+// The V-cycle of tpmg_vcycle with the level work vectors taken from the fixed
+// array of noalloc.cu.  The context's own work-vector pointers are pointed
+// into that array for the duration of the call (the launches capture the
+// pointer values when they are enqueued) and then restored, so the sequence
+// of kernels is exactly the one tpmg_vcycle runs.
+tpmg_status tpmg_vcycle_noalloc(tpmg_ctx *ctx, const double *d_r, double *d_z)
+{
+    if (!ctx || !d_r || !d_z) return fail(ctx, TPMG_ERR_INVALID_ARG, "NULL argument");
+    if (d_r == d_z) return fail(ctx, TPMG_ERR_INVALID_ARG, "r and z must not overlap");
+    const int L = ctx->p.n_levels;
+    const bool jac = ctx->p.smoother == TPMG_SMOOTH_JACOBI;
+    auto padded = [&](int l) { return ((size_t)ctx->lv[l].n * ctx->p.n_r + 31) & ~(size_t)31; };
+    size_t need = 0;
+    for (int l = 0; l < L; ++l) need += (l < L - 1 ? 2 : 0) * padded(l) + (jac ? padded(l) : 0);
+    if (need > (size_t)TPMG_VCYCLE_NOALLOC_MAX_DOUBLES) {
+        char msg[160];
+        std::snprintf(msg, sizeof msg, "problem needs %zu doubles of scratch; the fixed array holds %u", need,
+                      (unsigned)TPMG_VCYCLE_NOALLOC_MAX_DOUBLES);
+        return fail(ctx, TPMG_ERR_INVALID_ARG, msg);
+    }
+    int dev = -1;
+    CU(cudaGetDevice(&dev));
+    if (dev != ctx->device) return fail(ctx, TPMG_ERR_INVALID_ARG, "the context's device must be current");
+    double *base = nullptr;
+    CU(noalloc_scratch(dev, &base));
+    struct Saved { double *f, *u, *u2; } saved[16];   // n_levels <= 10
+    size_t off = 0;
+    for (int l = 0; l < L; ++l) {
+        LevelDev &D = ctx->lv[l];
+        saved[l] = Saved{D.f, D.u, D.u2};
+        if (l < L - 1) {
+            D.f = base + off; off += padded(l);
+            D.u = base + off; off += padded(l);
+        }
+        if (jac) { D.u2 = base + off; off += padded(l); }
+    }
+    const tpmg_status st = vcycle_fine(ctx, d_r, d_z);
+    for (int l = 0; l < L; ++l) {
+        ctx->lv[l].f = saved[l].f;
+        ctx->lv[l].u = saved[l].u;
+        ctx->lv[l].u2 = saved[l].u2;
+    }
+    return st;
+}
+
 tpmg_status tpmg_solve(tpmg_ctx *ctx, const double *d_f, double *d_u, double rtol, int max_iter, int *iters,
                        double *rel_resid, double *resid_hist)
 {

@@ -112,6 +112,11 @@ cudaError_t launch_axpy_pair(const Launch &L, long n, const Scalars *sc, const d
                              double *r, double *partials, int n_part);
 cudaError_t launch_xpby(const Launch &L, long n, const Scalars *sc, const double *z, double *p);
 
+// noalloc.cu: device address of the fixed scratch array of
+// tpmg_vcycle_noalloc on `device`, which must be the current device (looked
+// up once per device).
+cudaError_t noalloc_scratch(int device, double **ptr);
+
 enum FinishWhat { FIN_RR0 = 0, FIN_ALPHA = 1, FIN_RR = 2, FIN_BETA = 3, FIN_RZ0 = 4 };
 
 }  // namespace tpmg
