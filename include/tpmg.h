@@ -92,11 +92,14 @@ typedef struct {
     int    coeff_storage;/* TPMG_COEFF_* */
     int    centre;       /* TPMG_CENTRE_* */
     int    precision;    /* TPMG_PREC_* */
+    int    graphs;       /* 1: tpmg_solve replays its V-cycle from a CUDA graph captured at the first
+                            solve (one graph launch instead of ~15 launches per level); 0: kernel
+                            by kernel.  The results are identical. */
 } tpmg_params;
 
 /* Fills *p with the defaults: refinement 3, n_levels 4, n_r 16, H = 10/6371,
  * grading 1, omega2 0 with courant_c 8, nu 2/2/1, block-SOR with relax 1,
- * factorised storage, circumcentres, FP64.  Returns TPMG_ERR_INVALID_ARG if p is NULL. */
+ * factorised storage, circumcentres, FP64, graphs on.  Returns TPMG_ERR_INVALID_ARG if p is NULL. */
 tpmg_status tpmg_default_params(tpmg_params *p);
 
 /* Builds the grid hierarchy, geometry, colouring and coefficients on the host
@@ -200,12 +203,16 @@ enum { TPMG_K_APPLY = 0,      /* y = A x (with the fused dot of CG) */
 tpmg_status tpmg_profile(tpmg_ctx *ctx, unsigned class_mask);
 
 /* Reads the counters of one kernel class since the last tpmg_profile call:
- * launches, total device time in ms of the timed launches (0 if the class is
- * not timed), and units = number of (cell, level) unknowns the launches
- * processed (for the algorithmic bytes / flops per launch).  Synchronises the
- * context stream.  Any output may be NULL.  Errors: INVALID_ARG, CUDA. */
+ * launches, units = number of (cell, level) unknowns the launches processed
+ * (for the algorithmic bytes / flops per launch), and -- if the class is
+ * timed -- total_ms, the summed device time of the `timed` launches that carry
+ * an event pair.  Launches made one by one are all timed; launches replayed
+ * from a captured graph carry event-record nodes, so their pairs hold the
+ * most recent replay only (timed counts one replay's launches).  The average
+ * duration of a launch is total_ms / timed.  Synchronises the context stream.
+ * Any output may be NULL.  Errors: INVALID_ARG, CUDA. */
 tpmg_status tpmg_profile_read(tpmg_ctx *ctx, int kernel_class, long long *launches, double *total_ms,
-                              double *units);
+                              double *units, long long *timed);
 
 /* Static description of a status value. */
 const char *tpmg_status_string(tpmg_status s);

@@ -47,7 +47,8 @@ class tpmg_params(ctypes.Structure):
                 ("H", ctypes.c_double), ("grading", ctypes.c_double), ("omega2", ctypes.c_double),
                 ("courant_c", ctypes.c_double), ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int),
                 ("nu_coarse", ctypes.c_int), ("smoother", ctypes.c_int), ("relax", ctypes.c_double),
-                ("coeff_storage", ctypes.c_int), ("centre", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("coeff_storage", ctypes.c_int), ("centre", ctypes.c_int), ("precision", ctypes.c_int),
+                ("graphs", ctypes.c_int)]
 
 
 class TPMGError(RuntimeError):
@@ -80,7 +81,8 @@ def load(path: str | None = None):
     lib.tpmg_query.argtypes = [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(I)]
     lib.tpmg_export_mesh.argtypes = [P, I, P, P, P, P, P, P]
     lib.tpmg_profile.argtypes = [P, ctypes.c_uint]
-    lib.tpmg_profile_read.argtypes = [P, I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(D), ctypes.POINTER(D)]
+    lib.tpmg_profile_read.argtypes = [P, I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(D), ctypes.POINTER(D),
+                                      ctypes.POINTER(ctypes.c_longlong)]
     lib.tpmg_status_string.argtypes = [I]
     lib.tpmg_status_string.restype = ctypes.c_char_p
     lib.tpmg_last_error.argtypes = [P]
@@ -199,10 +201,10 @@ class Solver:
     def profile_read(self) -> dict:
         out = {}
         for i, name in enumerate(KERNEL_CLASSES):
-            n, ms, units = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
-            self._check(self._lib.tpmg_profile_read(self._h, i, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(units)),
-                        "tpmg_profile_read")
-            out[name] = dict(launches=n.value, ms=ms.value, units=units.value)
+            n, ms, units, timed = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double(), ctypes.c_longlong()
+            self._check(self._lib.tpmg_profile_read(self._h, i, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(units),
+                                                    ctypes.byref(timed)), "tpmg_profile_read")
+            out[name] = dict(launches=n.value, ms=ms.value, units=units.value, timed=timed.value)
         return out
 
     # --------------------------------------------------------------- compute

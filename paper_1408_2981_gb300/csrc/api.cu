@@ -26,10 +26,22 @@ struct Tracer {
     size_t used = 0;
 };
 
+// The V-cycle of tpmg_solve (r -> z on the context's own vectors) replayed
+// from a captured CUDA graph, with the launch counts of one replay.
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    long long launches[TPMG_K_COUNT] = {};
+    double units[TPMG_K_COUNT] = {};
+};
+
 struct tpmg_ctx {
     tpmg_params p{};
     Tracer tr;
     cudaStream_t stream = nullptr;
+    cudaStream_t issue = nullptr;       // stream the next launches go to (stream, or cap_stream while capturing)
+    cudaStream_t cap_stream = nullptr;  // private stream on which graphs are captured
+    bool capturing = false;
+    GraphCache vc;
     int device = 0;
     int sm_count = 0;
     HostGrid host;
@@ -97,10 +109,11 @@ bool validate(const tpmg_params *p, std::string &msg)
     if (p->coeff_storage != TPMG_COEFF_FACTORISED) { msg = "only factorised coefficient storage is built"; return false; }
     if (p->centre != TPMG_CENTRE_CIRCUM && p->centre != TPMG_CENTRE_VERTEX_MEAN) { msg = "unknown centre kind"; return false; }
     if (p->precision != TPMG_PREC_FP64) { msg = "only FP64 precision is built"; return false; }
+    if (p->graphs != 0 && p->graphs != 1) { msg = "graphs must be 0 or 1"; return false; }
     return true;
 }
 
-Launch launch_of(const tpmg_ctx *ctx) { return Launch{ctx->stream, ctx->p.n_r, ctx->sm_count}; }
+Launch launch_of(const tpmg_ctx *ctx) { return Launch{ctx->issue, ctx->p.n_r, ctx->sm_count}; }
 
 cudaError_t grow_events(Tracer &t, size_t pairs)
 {
@@ -116,7 +129,9 @@ cudaError_t grow_events(Tracer &t, size_t pairs)
 
 // Every device operation of the library goes through run(): it counts the
 // launch and the unknowns it processes, and brackets it with an event pair on
-// the context stream when its class is being timed.
+// the issuing stream when its class is being timed.  While a graph is being
+// captured the pair becomes two event-record nodes of the graph, re-recorded
+// by every replay.
 template <class F>
 cudaError_t run(tpmg_ctx *ctx, int kclass, double units, F &&launch)
 {
@@ -129,12 +144,13 @@ cudaError_t run(tpmg_ctx *ctx, int kclass, double units, F &&launch)
             cudaError_t e = grow_events(t, t.used + 1024);
             if (e != cudaSuccess) return e;
         }
-        cudaError_t e = cudaEventRecord(t.ev[2 * t.used], ctx->stream);
+        cudaError_t e = cudaEventRecordWithFlags(t.ev[2 * t.used], ctx->issue,
+                                                 ctx->capturing ? cudaEventRecordExternal : 0);
         if (e != cudaSuccess) return e;
     }
     cudaError_t e = launch();
     if (timed && e == cudaSuccess) {
-        e = cudaEventRecord(t.ev[2 * t.used + 1], ctx->stream);
+        e = cudaEventRecordWithFlags(t.ev[2 * t.used + 1], ctx->issue, ctx->capturing ? cudaEventRecordExternal : 0);
         t.cls[t.used] = kclass;
         ++t.used;
     }
@@ -147,93 +163,150 @@ cudaError_t run(tpmg_ctx *ctx, int kclass, double units, F &&launch)
         if (e_ != cudaSuccess) return fail(ctx, TPMG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
-cudaError_t relax_pass(tpmg_ctx *ctx, const LevelDev &lv, int c, int mode, const double *f, double *u,
-                       const double *uc)
-{
-    const double units = (double)(lv.colour_off[c + 1] - lv.colour_off[c]) * ctx->p.n_r;
-    return run(ctx, TPMG_K_RELAX, units,
-               [&] { return launch_mcsor_pass(launch_of(ctx), lv, ctx->vert, c, mode, ctx->p.relax, f, u, uc); });
-}
-
 // Algorithm 1 on multigrid level l: u = V-cycle(f) from a zero initial guess.
-// `scratch` is a second vector of the level size (block Jacobi ping-pong).
-tpmg_status vcycle_level(tpmg_ctx *ctx, int l, const double *f, double *u, double *scratch)
+// `scratch` is a second vector of the level size (block-Jacobi ping-pong).
+// Below the finest level the result is a coarse-grid correction: it is added
+// to the 4 children of every cell in u_fine (prolongation P = R^T) by the pass
+// that writes that column's final value, so no separate prolongation pass and
+// no re-read of the correction is needed.
+tpmg_status vcycle_level(tpmg_ctx *ctx, int l, const double *f, double *u, double *scratch, double *u_fine)
 {
     const Launch L = launch_of(ctx);
     const tpmg_params &p = ctx->p;
     const LevelDev &lv = ctx->lv[l];
     const int C = lv.n_colours;
     const bool jac = p.smoother == TPMG_SMOOTH_JACOBI;
+    const double nunits = (double)lv.n * p.n_r;
+    const size_t nbytes = sizeof(double) * lv.n * p.n_r;
     double *cur = u, *oth = scratch;   // Jacobi: current iterate / other buffer
-    auto jacobi = [&](int mode, const double *uc) -> cudaError_t {
-        cudaError_t e = run(ctx, TPMG_K_RELAX, (double)lv.n * p.n_r,
-                            [&] { return launch_jacobi(L, lv, ctx->vert, mode, p.relax, f, cur, oth, uc); });
+    // one multicolour block-SOR pass over colour c, in place in u
+    auto pass = [&](int c, int mode, double *fine) -> cudaError_t {
+        const int t0 = lv.colour_task_off[c], nt = lv.colour_task_off[c + 1] - t0;
+        const int m = (mode == PASS_ZERO && c == 0) ? PASS_RHS_ONLY : mode;
+        return run(ctx, TPMG_K_RELAX, (double)lv.colour_cells[c] * p.n_r, [&] {
+            return launch_relax(L, lv, ctx->vert, m, t0, nt, p.relax, f, u, u, fine);
+        });
+    };
+    // one block-Jacobi sweep from cur into oth
+    auto jacobi = [&](int mode, double *fine) -> cudaError_t {
+        const int m = mode == PASS_ZERO ? PASS_RHS_ONLY : mode;
+        cudaError_t e = run(ctx, TPMG_K_RELAX, nunits, [&] {
+            return launch_relax(L, lv, ctx->vert, m, 0, lv.n_tasks, p.relax, f, cur, oth, fine);
+        });
         std::swap(cur, oth);
         return e;
     };
-    auto finish_in_u = [&]() -> tpmg_status {
-        if (cur != u) LCHK(run(ctx, TPMG_K_COPY, (double)lv.n * p.n_r, [&] { return cudaMemcpyAsync(u, cur, sizeof(double) * lv.n * p.n_r, cudaMemcpyDeviceToDevice, ctx->stream); }));
-        cur = u; oth = scratch;
-        return TPMG_OK;
+    auto clear = [&](double *x) -> cudaError_t {
+        return run(ctx, TPMG_K_COPY, nunits, [&] { return cudaMemsetAsync(x, 0, nbytes, ctx->issue); });
     };
     if (l == 0) {
-        if (p.nu_coarse == 0) {
-            LCHK(run(ctx, TPMG_K_COPY, (double)lv.n * p.n_r, [&] { return cudaMemsetAsync(u, 0, sizeof(double) * lv.n * p.n_r, ctx->stream); }));
-            return TPMG_OK;
-        }
+        // coarsest level: nu_coarse symmetric sweeps (a zero correction prolongates to nothing)
+        if (p.nu_coarse == 0) LCHK(clear(u));
         for (int s = 0; s < p.nu_coarse; ++s) {
+            const bool last = s == p.nu_coarse - 1;
             if (jac) {
-                LCHK(jacobi(s == 0 ? PASS_ZERO : PASS_NORMAL, nullptr));
+                LCHK(jacobi(s == 0 ? PASS_ZERO : PASS_NORMAL, last ? u_fine : nullptr));
                 continue;
             }
             for (int c = 0; c < C; ++c)
-                LCHK(relax_pass(ctx, lv, c, s == 0 ? PASS_ZERO : PASS_NORMAL, f, u, nullptr));
-            for (int c = C - 2; c >= 0; --c)
-                LCHK(relax_pass(ctx, lv, c, PASS_NORMAL, f, u, nullptr));
+                LCHK(pass(c, s == 0 ? PASS_ZERO : PASS_NORMAL, last && c == C - 1 ? u_fine : nullptr));
+            for (int c = C - 2; c >= 0; --c) LCHK(pass(c, PASS_NORMAL, last ? u_fine : nullptr));
         }
-        return jac ? finish_in_u() : TPMG_OK;
-    }
-    // pre-smoothing (forward colour order)
-    if (p.nu_pre == 0) {
-        LCHK(run(ctx, TPMG_K_COPY, (double)lv.n * p.n_r, [&] { return cudaMemsetAsync(u, 0, sizeof(double) * lv.n * p.n_r, ctx->stream); }));
     } else {
+        // pre-smoothing (forward colour order)
+        if (p.nu_pre == 0) LCHK(clear(cur));
         for (int s = 0; s < p.nu_pre; ++s) {
             if (jac) {
                 LCHK(jacobi(s == 0 ? PASS_ZERO : PASS_NORMAL, nullptr));
                 continue;
             }
-            for (int c = 0; c < C; ++c)
-                LCHK(relax_pass(ctx, lv, c, s == 0 ? PASS_ZERO : PASS_NORMAL, f, u, nullptr));
+            for (int c = 0; c < C; ++c) LCHK(pass(c, s == 0 ? PASS_ZERO : PASS_NORMAL, nullptr));
         }
-        if (jac) { tpmg_status st = finish_in_u(); if (st != TPMG_OK) return st; }
-    }
-    // residual, restriction, recursion with zero guess
-    LevelDev &co = ctx->lv[l - 1];
-    LCHK(run(ctx, TPMG_K_RESTRICT, (double)lv.n * p.n_r,
-             [&] { return launch_resid_restrict(L, lv, co, ctx->vert, f, u, co.f); }));
-    tpmg_status st = vcycle_level(ctx, l - 1, co.f, co.u, co.u2);
-    if (st != TPMG_OK) return st;
-    // coarse-grid correction fused into the first post-smoothing sweep (reverse colours)
-    if (p.nu_post == 0) {
-        LCHK(run(ctx, TPMG_K_PROLONG, (double)lv.n * p.n_r, [&] { return launch_prolong_add(L, lv, co.u, u); }));
-        return TPMG_OK;
-    }
-    for (int s = 0; s < p.nu_post; ++s) {
-        const int mode = s == 0 ? PASS_PROLONG : PASS_NORMAL;
-        if (jac) {
-            LCHK(jacobi(mode, co.u));
-            continue;
+        // residual + restriction, then the coarse V-cycle adds its correction into cur
+        LevelDev &co = ctx->lv[l - 1];
+        const double *uc = cur;
+        LCHK(run(ctx, TPMG_K_RESTRICT, nunits,
+                 [&] { return launch_resid_restrict(L, lv, co, ctx->vert, f, uc, co.f); }));
+        tpmg_status st = vcycle_level(ctx, l - 1, co.f, co.u, co.u2, cur);
+        if (st != TPMG_OK) return st;
+        // post-smoothing (reverse colour order, the adjoint of the pre-smoothing)
+        for (int s = 0; s < p.nu_post; ++s) {
+            const bool last = s == p.nu_post - 1;
+            if (jac) {
+                LCHK(jacobi(PASS_NORMAL, last ? u_fine : nullptr));
+                continue;
+            }
+            for (int c = C - 1; c >= 0; --c) LCHK(pass(c, PASS_NORMAL, last ? u_fine : nullptr));
         }
-        for (int c = C - 1; c >= 0; --c)
-            LCHK(relax_pass(ctx, lv, c, mode, f, u, co.u));
+        if (p.nu_post == 0 && u_fine) {
+            const LevelDev &fl = ctx->lv[l + 1];
+            const double *cc = cur;
+            LCHK(run(ctx, TPMG_K_PROLONG, (double)fl.n * p.n_r,
+                     [&] { return launch_prolong_add(L, fl, cc, u_fine); }));
+        }
     }
-    return jac ? finish_in_u() : TPMG_OK;
+    // the finest level returns its result in u (coarse levels have handed theirs on already)
+    if (!u_fine && cur != u) {
+        const double *cc = cur;
+        LCHK(run(ctx, TPMG_K_COPY, nunits,
+                 [&] { return cudaMemcpyAsync(u, cc, nbytes, cudaMemcpyDeviceToDevice, ctx->issue); }));
+    }
+    return TPMG_OK;
 }
 
 tpmg_status vcycle_fine(tpmg_ctx *ctx, const double *r, double *z)
 {
     const int l = ctx->p.n_levels - 1;
-    return vcycle_level(ctx, l, r, z, ctx->lv[l].u2);
+    return vcycle_level(ctx, l, r, z, ctx->lv[l].u2, nullptr);
+}
+
+void drop_graph(tpmg_ctx *ctx)
+{
+    if (ctx->vc.exec) cudaGraphExecDestroy(ctx->vc.exec);
+    ctx->vc = GraphCache{};
+}
+
+// z = B r on the PCG vectors of the context.  With graphs enabled the V-cycle
+// (about 90 launches for 6 levels) is captured once on the private stream and
+// then replayed on the context stream as one graph launch.
+tpmg_status vcycle_pcg(tpmg_ctx *ctx)
+{
+    if (!ctx->p.graphs) return vcycle_fine(ctx, ctx->r, ctx->z);
+    Tracer &t = ctx->tr;
+    if (!ctx->vc.exec) {
+        long long l0[TPMG_K_COUNT];
+        double u0[TPMG_K_COUNT];
+        std::copy(t.launches, t.launches + TPMG_K_COUNT, l0);
+        std::copy(t.units, t.units + TPMG_K_COUNT, u0);
+        CU(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+        ctx->capturing = true;
+        ctx->issue = ctx->cap_stream;
+        const tpmg_status st = vcycle_fine(ctx, ctx->r, ctx->z);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+        ctx->capturing = false;
+        ctx->issue = ctx->stream;
+        cudaGraphExec_t exec = nullptr;
+        cudaError_t ei = cudaErrorUnknown;
+        if (st == TPMG_OK && e == cudaSuccess && g) ei = cudaGraphInstantiate(&exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        for (int c = 0; c < TPMG_K_COUNT; ++c) {   // the captured launches belong to every replay
+            ctx->vc.launches[c] = t.launches[c] - l0[c];
+            ctx->vc.units[c] = t.units[c] - u0[c];
+            t.launches[c] = l0[c];
+            t.units[c] = u0[c];
+        }
+        if (st != TPMG_OK) return st;
+        if (e != cudaSuccess) return fail(ctx, TPMG_ERR_CUDA, std::string("V-cycle capture: ") + cudaGetErrorString(e));
+        if (ei != cudaSuccess) return fail(ctx, TPMG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+        ctx->vc.exec = exec;
+    }
+    CU(cudaGraphLaunch(ctx->vc.exec, ctx->stream));
+    for (int c = 0; c < TPMG_K_COUNT; ++c) {
+        t.launches[c] += ctx->vc.launches[c];
+        t.units[c] += ctx->vc.units[c];
+    }
+    return TPMG_OK;
 }
 
 tpmg_status read_scalars(tpmg_ctx *ctx)
@@ -260,7 +333,7 @@ tpmg_status pcg(tpmg_ctx *ctx, const double *f, double *u, double rtol, int max_
     if (hist) hist[0] = 1.0;
     if (!std::isfinite(rr0)) return fail(ctx, TPMG_ERR_BREAKDOWN, "initial residual is not finite");
     if (rr0 == 0.0) { *rel = 0.0; return TPMG_OK; }
-    if ((st = vcycle_fine(ctx, ctx->r, ctx->z)) != TPMG_OK) return st;
+    if ((st = vcycle_pcg(ctx)) != TPMG_OK) return st;
     LCHK(run(ctx, TPMG_K_DOT, (double)N, [&] { return launch_dot(L, N, ctx->r, ctx->z, ctx->partials, np); }));
     LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_RZ0, ctx->partials, np, ctx->sc); }));
     LCHK(run(ctx, TPMG_K_COPY, (double)N, [&] { return cudaMemcpyAsync(ctx->pv, ctx->z, sizeof(double) * N, cudaMemcpyDeviceToDevice, ctx->stream); }));
@@ -278,7 +351,7 @@ tpmg_status pcg(tpmg_ctx *ctx, const double *f, double *u, double rtol, int max_
         if (hist) hist[it + 1] = *rel;
         if (*rel <= rtol) return TPMG_OK;
         if (it + 1 == max_iter) break;
-        if ((st = vcycle_fine(ctx, ctx->r, ctx->z)) != TPMG_OK) return st;
+        if ((st = vcycle_pcg(ctx)) != TPMG_OK) return st;
         LCHK(run(ctx, TPMG_K_DOT, (double)N, [&] { return launch_dot(L, N, ctx->r, ctx->z, ctx->partials, np); }));
         LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_BETA, ctx->partials, np, ctx->sc); }));
         LCHK(run(ctx, TPMG_K_XPBY, (double)N, [&] { return launch_xpby(L, N, ctx->sc, ctx->z, ctx->pv); }));
@@ -304,22 +377,35 @@ tpmg_status upload_level(tpmg_ctx *ctx, int l)
         const double g0 = H.g[3 * T], g1 = H.g[3 * T + 1], g2 = H.g[3 * T + 2];
         g[T] = dbl4{g0, g1, g2, (g0 + g1) + g2};
     }
-    std::vector<int> cells;
-    D.colour_off.assign(H.n_colours + 1, 0);
+    // relaxation tasks: the cells of each colour in ascending order, padded to whole tasks
+    std::vector<int> tasks;
+    D.colour_task_off.assign(H.n_colours + 1, 0);
+    D.colour_cells.assign(H.n_colours, 0);
     for (int c = 0; c < H.n_colours; ++c) {
-        D.colour_off[c] = (int)cells.size();
+        D.colour_task_off[c] = (int)(tasks.size() / kRelaxCols);
         for (int T = 0; T < H.n; ++T)
-            if (H.colour[T] == c) cells.push_back(T);
+            if (H.colour[T] == c) {
+                tasks.push_back(T);
+                ++D.colour_cells[c];
+            }
+        while (tasks.size() % kRelaxCols) tasks.push_back(-1);
     }
-    D.colour_off[H.n_colours] = (int)cells.size();
+    D.n_tasks = (int)(tasks.size() / kRelaxCols);
+    D.colour_task_off[H.n_colours] = D.n_tasks;
+    D.jmid = (p.n_r - 1) / 2;
+    D.steps = p.n_r - 1 - D.jmid;
     const size_t n = H.n, nn = (size_t)H.n * p.n_r;
+    const size_t nf = (size_t)D.n_tasks * std::max(D.steps, 1) * 32;
     CU(dalloc(ctx, &D.nbr, n));
     CU(dalloc(ctx, &D.g, n));
     CU(dalloc(ctx, &D.area, n));
-    CU(dalloc(ctx, &D.cells_by_colour, n));
-    CU(dalloc(ctx, &D.inv, nn));
-    CU(dalloc(ctx, &D.ef, nn));
-    CU(dalloc(ctx, &D.cpf, nn));
+    CU(dalloc(ctx, &D.task_cells, tasks.size()));
+    CU(dalloc(ctx, &D.task_nbr, tasks.size()));
+    CU(dalloc(ctx, &D.task_g, tasks.size()));
+    CU(dalloc(ctx, &D.rinv, nn));
+    CU(dalloc(ctx, &D.fb, nf));
+    CU(dalloc(ctx, &D.fc, nf));
+    CU(dalloc(ctx, &D.fm, (size_t)D.n_tasks * 2 * kRelaxCols));
     CU(dalloc(ctx, &D.u2, nn));
     if (l < p.n_levels - 1) {
         CU(dalloc(ctx, &D.f, nn));
@@ -328,8 +414,14 @@ tpmg_status upload_level(tpmg_ctx *ctx, int l)
     CU(cudaMemcpyAsync(D.nbr, nb.data(), n * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(D.g, g.data(), n * sizeof(dbl4), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(D.area, H.area.data(), n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-    CU(cudaMemcpyAsync(D.cells_by_colour, cells.data(), n * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
-    CU(launch_thomas_factors(launch_of(ctx), D, ctx->vert));
+    CU(cudaMemcpyAsync(D.task_cells, tasks.data(), tasks.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    std::vector<int4> tnb(tasks.size(), make_int4(0, 0, 0, 0));
+    std::vector<dbl4> tg(tasks.size(), dbl4{0.0, 0.0, 0.0, 0.0});
+    for (size_t q = 0; q < tasks.size(); ++q)
+        if (tasks[q] >= 0) { tnb[q] = nb[tasks[q]]; tg[q] = g[tasks[q]]; }
+    CU(cudaMemcpyAsync(D.task_nbr, tnb.data(), tnb.size() * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(D.task_g, tg.data(), tg.size() * sizeof(dbl4), cudaMemcpyHostToDevice, ctx->stream));
+    CU(launch_twisted_factors(launch_of(ctx), D, ctx->vert));
     // the host vectors above must outlive the asynchronous copies
     CU(cudaStreamSynchronize(ctx->stream));
     return TPMG_OK;
@@ -358,6 +450,7 @@ tpmg_status tpmg_default_params(tpmg_params *p)
     p->coeff_storage = TPMG_COEFF_FACTORISED;
     p->centre = TPMG_CENTRE_CIRCUM;
     p->precision = TPMG_PREC_FP64;
+    p->graphs = 1;
     return TPMG_OK;
 }
 
@@ -374,6 +467,8 @@ tpmg_status tpmg_setup(const tpmg_params *params, void *cuda_stream, tpmg_ctx **
     };
     ctx->p = *params;
     ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    ctx->issue = ctx->stream;
+    if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return bail(TPMG_ERR_CUDA);
     if (cudaGetDevice(&ctx->device) != cudaSuccess) return bail(TPMG_ERR_CUDA);
     if (cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess)
         return bail(TPMG_ERR_CUDA);
@@ -406,7 +501,7 @@ tpmg_status tpmg_setup(const tpmg_params *params, void *cuda_stream, tpmg_ctx **
         if (st != TPMG_OK) return bail(st);
     }
     ctx->N = (long)ctx->lv.back().n * n_r;
-    ctx->n_part = 2 * ctx->sm_count;
+    ctx->n_part = 8 * ctx->sm_count;   // blocks of the reducing kernels, one partial each
     if (dalloc(ctx, &ctx->r, ctx->N) != cudaSuccess || dalloc(ctx, &ctx->z, ctx->N) != cudaSuccess ||
         dalloc(ctx, &ctx->pv, ctx->N) != cudaSuccess || dalloc(ctx, &ctx->q, ctx->N) != cudaSuccess ||
         dalloc(ctx, &ctx->hf, ctx->N) != cudaSuccess || dalloc(ctx, &ctx->hu, ctx->N) != cudaSuccess ||
@@ -531,6 +626,7 @@ tpmg_status tpmg_profile(tpmg_ctx *ctx, unsigned class_mask)
     if (!ctx) return TPMG_ERR_INVALID_ARG;
     if (class_mask >> TPMG_K_COUNT) return fail(ctx, TPMG_ERR_INVALID_ARG, "unknown kernel class in mask");
     CU(cudaStreamSynchronize(ctx->stream));
+    drop_graph(ctx);   // its captured event nodes would alias the reset event pool
     Tracer &t = ctx->tr;
     t.mask = class_mask;
     std::fill(t.launches, t.launches + TPMG_K_COUNT, 0LL);
@@ -540,21 +636,25 @@ tpmg_status tpmg_profile(tpmg_ctx *ctx, unsigned class_mask)
     return TPMG_OK;
 }
 
-tpmg_status tpmg_profile_read(tpmg_ctx *ctx, int kernel_class, long long *launches, double *total_ms, double *units)
+tpmg_status tpmg_profile_read(tpmg_ctx *ctx, int kernel_class, long long *launches, double *total_ms, double *units,
+                              long long *timed)
 {
     if (!ctx || kernel_class < 0 || kernel_class >= TPMG_K_COUNT) return fail(ctx, TPMG_ERR_INVALID_ARG, "bad class");
     CU(cudaStreamSynchronize(ctx->stream));
     const Tracer &t = ctx->tr;
     double ms = 0.0;
+    long long n = 0;
     for (size_t i = 0; i < t.used; ++i) {
         if (t.cls[i] != kernel_class) continue;
         float m = 0.f;
         CU(cudaEventElapsedTime(&m, t.ev[2 * i], t.ev[2 * i + 1]));
         ms += m;
+        ++n;
     }
     if (launches) *launches = t.launches[kernel_class];
     if (total_ms) *total_ms = ms;
     if (units) *units = t.units[kernel_class];
+    if (timed) *timed = n;
     return TPMG_OK;
 }
 
@@ -570,6 +670,8 @@ void tpmg_destroy(tpmg_ctx *ctx)
 {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
+    drop_graph(ctx);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (void *p : ctx->allocs) cudaFree(p);
     if (ctx->h_sc) cudaFreeHost(ctx->h_sc);
     for (cudaEvent_t e : ctx->tr.ev) cudaEventDestroy(e);

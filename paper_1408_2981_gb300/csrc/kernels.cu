@@ -29,7 +29,6 @@ namespace tpmg {
 namespace {
 
 constexpr int kThreads = 256;   // element-wise kernels
-constexpr int kSmooth = 128;    // line-relaxation kernels
 
 template <int NT>
 __device__ __forceinline__ double block_sum(double v)
@@ -94,16 +93,54 @@ __global__ void __launch_bounds__(NT) k_apply(OpView o, const double *__restrict
     }
 }
 
+__device__ __forceinline__ bool is_zero(double v) { return (__double_as_longlong(v) << 1) == 0; }
+
+// r = f - A u with partial ||r||^2.  Where the whole stencil of every lane of
+// a warp reads exact zeros (for example a zero initial guess) A u is exactly
+// zero and the warp skips its FP64 arithmetic; the test is on bit patterns,
+// so it costs no FP64 instruction.
 template <int NT>
 __global__ void __launch_bounds__(NT) k_residual(OpView o, const double *__restrict__ f, const double *__restrict__ u,
                                                  double *__restrict__ r, int N, double *__restrict__ partials)
 {
     double acc = 0.0;
-    for (int i = blockIdx.x * NT + threadIdx.x; i < N; i += gridDim.x * NT) {
-        const int T = i / o.n_r, k = i - T * o.n_r;
-        const double v = f[i] - apply_at(o, u, T, k, i);
-        r[i] = v;
-        acc = fma(v, v, acc);
+    const int stride = gridDim.x * NT, n_r = o.n_r;
+    for (int i0 = blockIdx.x * NT + threadIdx.x; i0 < N; i0 += 2 * stride) {
+        double fv[2], uc[2], um[2], up[2], u0[2], u1[2], u2[2];
+        int T[2], k[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int i = i0 + q * stride;
+            fv[q] = uc[q] = um[q] = up[q] = u0[q] = u1[q] = u2[q] = 0.0;
+            T[q] = k[q] = 0;
+            if (i < N) {
+                T[q] = i / n_r;
+                k[q] = i - T[q] * n_r;
+                const int4 nb = __ldg(&o.nbr[T[q]]);
+                fv[q] = f[i];
+                uc[q] = u[i];
+                if (k[q] > 0) um[q] = u[i - 1];
+                if (k[q] < n_r - 1) up[q] = u[i + 1];
+                u0[q] = u[nb.x * n_r + k[q]];
+                u1[q] = u[nb.y * n_r + k[q]];
+                u2[q] = u[nb.z * n_r + k[q]];
+            }
+        }
+        bool zero = true;
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+            zero = zero && is_zero(uc[q]) && is_zero(um[q]) && is_zero(up[q]) && is_zero(u0[q]) && is_zero(u1[q]) &&
+                   is_zero(u2[q]);
+        const bool skip = __all_sync(__activemask(), zero);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int i = i0 + q * stride;
+            if (i >= N) continue;
+            double v = fv[q];
+            if (!skip) v = v - apply_at(o, u, T[q], k[q], i);
+            r[i] = v;
+            acc = fma(v, v, acc);
+        }
     }
     if (partials) {
         acc = block_sum<NT>(acc);
@@ -137,123 +174,412 @@ __global__ void __launch_bounds__(NT) k_prolong_add(const double *__restrict__ u
     }
 }
 
-// Thomas pivots of the column block A_T (one thread per column).  A_T has
-// couplings c_k = |T| w_k to the level below, c_{k+1} above, and diagonal
-// c_k + c_{k+1} + m_k with excess m_k = |T| v_k + hr_k G_T.  The pivots are
-// carried through their excess, e_0 = m_0, e_k = m_k + c_k e_{k-1} / p_{k-1},
-// p_k = e_k + c_{k+1}: only sums of non-negative terms, so they keep full
-// relative precision although c_k / m_k reaches 1e6-1e9 in a thin shell.
-// Stored: inv = 1/p_k, ef = c_k/p_k, cpf = c_{k+1}/p_k, so that the solve is
-//   y_k = rhs_k inv_k + ef_k y_{k-1};   x_k = y_k + cpf_k x_{k+1}.
-__global__ void k_factors(int n, OpView o, double *__restrict__ inv, double *__restrict__ ef, double *__restrict__ cpf)
+// Twisted Thomas factors of the column blocks A_T (Sec. 4.1; set-up, one
+// thread per column of a task).  A_T has couplings c_k = |T| w_k between rows
+// k-1 and k and diagonal c_k + c_{k+1} + m_k with excess m_k = |T| v_k +
+// hr_k G_T.  Rows 0..j-1 are eliminated from the top and rows n_r-1..j+1 from
+// the bottom; each pivot is carried through its excess over the coupling it
+// has not yet eliminated:
+//   top:    e_0 = m_0,          e_k = m_k + c_k e_{k-1} / p_{k-1},       p_k = e_k + c_{k+1}
+//   bottom: e'_{n-1} = m_{n-1}, e'_k = m_k + c_{k+1} e'_{k+1} / q_{k+1}, q_k = e'_k + c_k
+//   meeting row: gamma_j = m_j + c_j e_{j-1} / p_{j-1} + c_{j+1} e'_{j+1} / q_{j+1}.
+// Only sums of non-negative terms: full relative precision although c_k / m_k
+// reaches 1e6-1e9 in a thin shell.  With t_k = d_k / pivot_k the solve is
+//   top:    y_k = t_k + (c_k / p_k) y_{k-1},      x_k = y_k + (c_{k+1} / p_k) x_{k+1}
+//   bottom: z_k = t_k + (c_{k+1} / q_k) z_{k+1},  x_k = z_k + (c_k / q_k) x_{k-1}
+//   x_j = t_j + (c_j / gamma) y_{j-1} + (c_{j+1} / gamma) z_{j+1}.
+// Stored: rinv [cell][k] = 1 / pivot of row k (cell-major, read with d);
+// fb, fc [task][step][lane] the forward and backward multipliers; fm
+// [task][2][16] the two multipliers of the meeting row.
+__global__ void k_twisted_factors(int n_tasks, OpView o, const int *__restrict__ cells, int S, int j,
+                                  double *__restrict__ rinv, double *__restrict__ fb, double *__restrict__ fc,
+                                  double *__restrict__ fm)
 {
-    const int T = blockIdx.x * blockDim.x + threadIdx.x;
-    if (T >= n) return;
-    const int n_r = o.n_r;
-    const double A = o.area[T], Gs = o.g[T].w;
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= n_tasks * kRelaxCols) return;
+    const int t = gid / kRelaxCols, col = gid - t * kRelaxCols;
+    const int T = cells[gid];
+    const int n = o.n_r;
+    const size_t base = (size_t)t * S * 32;
+    for (int s = 0; s < S; ++s) {
+        fb[base + s * 32 + col] = fc[base + s * 32 + col] = 0.0;
+        fb[base + s * 32 + col + 16] = fc[base + s * 32 + col + 16] = 0.0;
+    }
+    double *M = fm + (size_t)t * 2 * kRelaxCols;
+    M[col] = M[kRelaxCols + col] = 0.0;
+    if (T < 0) return;
+    double *ri = rinv + (size_t)T * n;
+    const double A = o.area[T], G = o.g[T].w;
     double e = 0.0, p = 1.0;
-    for (int k = 0; k < n_r; ++k) {
-        const double m = A * o.vol[k] + o.hr[k] * Gs;
+    for (int k = 0; k < j; ++k) {
+        const double m = fma(A, o.vol[k], o.hr[k] * G);
         const double c = A * o.w[k], cu = A * o.w[k + 1];
         e = k == 0 ? m : m + c * e / p;
         p = e + cu;
         const double iv = 1.0 / p;
-        inv[T * n_r + k] = iv;
-        ef[T * n_r + k] = c * iv;
-        cpf[T * n_r + k] = cu * iv;
+        ri[k] = iv;
+        fb[base + k * 32 + col] = c * iv;
+        fc[base + k * 32 + col] = cu * iv;
     }
+    double eb = 0.0, q = 1.0;
+    for (int k = n - 1, s = 0; k > j; --k, ++s) {
+        const double m = fma(A, o.vol[k], o.hr[k] * G);
+        const double cd = A * o.w[k], cu = A * o.w[k + 1];
+        eb = k == n - 1 ? m : m + cu * eb / q;
+        q = eb + cd;
+        const double iv = 1.0 / q;
+        ri[k] = iv;
+        fb[base + s * 32 + col + 16] = cu * iv;
+        fc[base + s * 32 + col + 16] = cd * iv;
+    }
+    const double cj = A * o.w[j], cj1 = A * o.w[j + 1];
+    double gam = fma(A, o.vol[j], o.hr[j] * G);
+    if (j > 0) gam += cj * e / p;
+    if (j < n - 1) gam += cj1 * eb / q;
+    const double ig = 1.0 / gam;
+    ri[j] = ig;
+    M[col] = cj * ig;
+    M[kRelaxCols + col] = cj1 * ig;
 }
 
-// One colour pass of multicolour block-SOR (eq. BlockJacobi) over a tile of
-// CT columns of colour c:
-//   u_T <- (1 - relax) u_T + relax A_T^{-1} (f_T + hr sum_e g_e u_{T_e}).
-// MODE PASS_ZERO: first forward sweep from a zero guess (neighbours of a larger
-// colour and the old u_T are zero).  MODE PASS_PROLONG: first reverse sweep after
-// the coarse-grid correction u += P u_c, applied on the fly to every value not
-// yet overwritten in this sweep (neighbours of a smaller colour, the old u_T).
-// Phase 1 (all threads, coalesced along k): t = rhs * inv into shared memory;
-// phase 2 (one thread per column): the two Thomas recurrences, 2 FP64 each;
-// phase 3 (all threads): write back.  u_in and u_out are the same array in
-// the multicolour passes (in-place; a pass reads only other colours'
-// columns and its own column before writing it), distinct for block Jacobi.
-template <int MODE, bool JACOBI>
-__global__ void __launch_bounds__(kSmooth)
-    k_relax(OpView o, const int *__restrict__ cells, int nc, int CT, const double *__restrict__ f,
-            const double *u_in, double *u_out, const double *__restrict__ uc,
-            const double *__restrict__ inv, const double *__restrict__ ef, const double *__restrict__ cpf, double relax)
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
-    extern __shared__ double sm[];
-    const int n_r = o.n_r, ld = n_r + 1;
-    double *st = sm, *se = sm + CT * ld, *sc = sm + 2 * CT * ld;
-    const int c0 = blockIdx.x * CT;
-    const int nt = min(CT, nc - c0);
-    const int ne = nt * n_r;
-    for (int idx = threadIdx.x; idx < ne; idx += kSmooth) {
-        const int j = idx / n_r, k = idx - j * n_r;
-        const int T = JACOBI ? c0 + j : __ldg(&cells[c0 + j]);
-        const int i = T * n_r + k;
-        const int4 nb = __ldg(&o.nbr[T]);
-        const dbl4 g = o.g[T];
-        double v0, v1, v2;
-        if (MODE == PASS_NORMAL) {
-            v0 = u_in[nb.x * n_r + k]; v1 = u_in[nb.y * n_r + k]; v2 = u_in[nb.z * n_r + k];
-        } else if (MODE == PASS_ZERO) {
-            if (JACOBI) {
-                v0 = v1 = v2 = 0.0;
-            } else {
-                v0 = (nb.w & 1) ? u_in[nb.x * n_r + k] : 0.0;
-                v1 = (nb.w & 2) ? u_in[nb.y * n_r + k] : 0.0;
-                v2 = (nb.w & 4) ? u_in[nb.z * n_r + k] : 0.0;
+    const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Twisted Thomas solve of one column pair (one warp of k_relax): lane =
+// column + 16 * half.  B, C point at the task's [step][32] multiplier blocks
+// (global or shared memory), tc at the column's row of the shared tile, which
+// holds t = d / pivot on entry and x on exit.  Each half is a chain of `rows`
+// dependent FMAs forward and back; the loads of the next P steps are issued
+// while the current P are computed.
+template <int P>
+__device__ __forceinline__ void twisted_solve(const double *B, const double *C, const double *M, double *tc,
+                                              int n_r, int j, int lane)
+{
+    const int c = lane & (kRelaxCols - 1), half = lane >> 4;
+    const int rows = half ? n_r - 1 - j : j;
+    auto row_of = [&](int s) { return half ? n_r - 1 - s : s; };
+    double y = 0.0;
+    {
+        double b[P], d[P];
+#pragma unroll
+        for (int q = 0; q < P; ++q)
+            if (q < rows) { b[q] = B[q * 32]; d[q] = tc[row_of(q)]; }
+        for (int s0 = 0; s0 < rows; s0 += P) {
+            double bn[P], dn[P];
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                const int s = s0 + P + q;
+                if (s < rows) { bn[q] = B[s * 32]; dn[q] = tc[row_of(s)]; }
             }
-        } else {
-            const bool a0 = JACOBI || (nb.w & 1), a1 = JACOBI || (nb.w & 2), a2 = JACOBI || (nb.w & 4);
-            v0 = u_in[nb.x * n_r + k] + (a0 ? uc[(nb.x >> 2) * n_r + k] : 0.0);
-            v1 = u_in[nb.y * n_r + k] + (a1 ? uc[(nb.y >> 2) * n_r + k] : 0.0);
-            v2 = u_in[nb.z * n_r + k] + (a2 ? uc[(nb.z >> 2) * n_r + k] : 0.0);
-        }
-        const double h = fma(g.z, v2, fma(g.y, v1, g.x * v0));
-        const double rhs = fma(__ldg(&o.hr[k]), h, f[i]);
-        st[j * ld + k] = rhs * inv[i];
-        se[j * ld + k] = ef[i];
-        sc[j * ld + k] = cpf[i];
-    }
-    __syncthreads();
-    if (threadIdx.x < nt) {
-        double *t = st + threadIdx.x * ld;
-        const double *e = se + threadIdx.x * ld, *c = sc + threadIdx.x * ld;
-        double y = t[0];
-        for (int k = 1; k < n_r; ++k) {
-            y = fma(e[k], y, t[k]);
-            t[k] = y;
-        }
-        double x = y;
-        for (int k = n_r - 2; k >= 0; --k) {
-            x = fma(c[k], x, t[k]);
-            t[k] = x;
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                const int s = s0 + q;
+                if (s < rows) {
+                    y = fma(b[q], y, d[q]);
+                    tc[row_of(s)] = y;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < P; ++q) { b[q] = bn[q]; d[q] = dn[q]; }
         }
     }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < ne; idx += kSmooth) {
-        const int j = idx / n_r, k = idx - j * n_r;
-        const int T = JACOBI ? c0 + j : __ldg(&cells[c0 + j]);
-        const int i = T * n_r + k;
-        double x = st[j * ld + k];
-        if (relax != 1.0) {
-            double uo = 0.0;
-            if (MODE == PASS_NORMAL) uo = u_in[i];
-            if (MODE == PASS_PROLONG) uo = u_in[i] + uc[(T >> 2) * n_r + k];
-            x = fma(relax, x - uo, uo);
+    __syncwarp();
+    const double other = __shfl_xor_sync(0xffffffffu, y, 16);
+    const double ytop = half ? other : y, zbot = half ? y : other;
+    const double xj = fma(M[kRelaxCols + c], zbot, fma(M[c], ytop, tc[j]));
+    __syncwarp();
+    if (half == 0) tc[j] = xj;
+    double x = xj;
+    {
+        double cc[P], yy[P];
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const int s = rows - 1 - q;
+            if (s >= 0) { cc[q] = C[s * 32]; yy[q] = tc[row_of(s)]; }
         }
-        u_out[i] = x;
+        for (int s0 = rows - 1; s0 >= 0; s0 -= P) {
+            double cn[P], yn[P];
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                const int s = s0 - P - q;
+                if (s >= 0) { cn[q] = C[s * 32]; yn[q] = tc[row_of(s)]; }
+            }
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                const int s = s0 - q;
+                if (s >= 0) {
+                    x = fma(cc[q], x, yy[q]);
+                    tc[row_of(s)] = x;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < P; ++q) { cc[q] = cn[q]; yy[q] = yn[q]; }
+        }
     }
 }
 
+// One relaxation pass (eq. BlockJacobi) over whole tasks of 16 columns, one
+// task per CTA of 128 threads:
+//   u_T <- (1 - relax) u_T + relax A_T^{-1} (f_T + hr sum_e g_e u_{T_e}).
+// Phase A (all threads, coalesced along k, the loads of several elements in
+// flight per thread): t = (f + hr_k sum_e g_e u_{T_e,k}) / pivot_k into a
+// [16][n_r+1] shared tile.  STAGE (small levels, where few CTAs cannot hide
+// the load latency): the task's multiplier blocks are copied to shared memory
+// by cp.async meanwhile, and deeper unrolling keeps more loads in flight;
+// otherwise the register budget is kept for 6 resident CTAs per SM.
+// Phase B (one warp, rotating with the CTA index so that the serial phases of
+// the CTAs resident on an SM spread over its four FP64 units): the twisted
+// Thomas solve.  Phase C (all threads): write back, optional relaxation
+// weight, optional prolongation into the 4 children (u_fine += P x), loads
+// issued before their stores.  In the multicolour passes u_in == u_out: a pass
+// reads other colours' columns and its own column before writing it.
+template <int MODE, bool STAGE>
+__global__ void __launch_bounds__(128, STAGE ? 1 : 6)
+    k_relax(OpView o, const int *__restrict__ cells, const int4 *__restrict__ tnb, const dbl4 *__restrict__ tg,
+            const double *__restrict__ rinv, const double *__restrict__ fb, const double *__restrict__ fcf,
+            const double *__restrict__ fm, int S, int j, int task0, const double *__restrict__ f, const double *u_in,
+            double *u_out, double *__restrict__ u_fine, double relax)
+{
+    extern __shared__ double smem[];
+    __shared__ int s_cell[kRelaxCols];
+    __shared__ int4 s_nb[kRelaxCols];
+    __shared__ dbl4 s_g[kRelaxCols];
+    __shared__ double s_m[2 * kRelaxCols];
+    const int t = task0 + blockIdx.x;
+    const int n_r = o.n_r, ld = n_r + 1, ne = kRelaxCols * n_r;
+    double *tile = smem;
+    double *sf = smem + ((kRelaxCols * ld + 1) & ~1);   // staged multipliers, 16-byte aligned
+    const size_t fbase = (size_t)t * S * 32;
+    if (STAGE) {
+        const int chunks = S * 16;   // 16-byte chunks per multiplier block
+        for (int q = threadIdx.x; q < 2 * chunks; q += 128) {
+            const int a = q >= chunks, r = q - a * chunks;
+            cp_async16(sf + (size_t)a * S * 32 + 2 * r, (a ? fcf : fb) + fbase + 2 * r);
+        }
+    }
+    if (threadIdx.x < kRelaxCols) {
+        const int q = t * kRelaxCols + threadIdx.x;
+        s_cell[threadIdx.x] = __ldg(&cells[q]);
+        s_nb[threadIdx.x] = __ldg(&tnb[q]);
+        s_g[threadIdx.x] = tg[q];
+    } else if (threadIdx.x < 3 * kRelaxCols) {
+        const int q = threadIdx.x - kRelaxCols;
+        s_m[q] = __ldg(&fm[(size_t)t * 2 * kRelaxCols + q]);
+    }
+    __syncthreads();
+    constexpr int U = STAGE ? 8 : 4;   // elements per thread with loads in flight
+    for (int e0 = threadIdx.x; e0 < ne; e0 += 128 * U) {
+        double fv[U], iv[U], v0[U], v1[U], v2[U];
+        int col[U], kk[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int e = e0 + 128 * q;
+            col[q] = -1;
+            kk[q] = 0;
+            fv[q] = iv[q] = v0[q] = v1[q] = v2[q] = 0.0;
+            if (e < ne) {
+                const int c = e / n_r, k = e - c * n_r;
+                col[q] = c;
+                kk[q] = k;
+                const int T = s_cell[c];
+                if (T >= 0) {
+                    fv[q] = f[T * n_r + k];
+                    iv[q] = __ldg(&rinv[T * n_r + k]);
+                    if (MODE != PASS_RHS_ONLY) {
+                        const int4 nb = s_nb[c];
+                        if (MODE == PASS_NORMAL || (nb.w & 1)) v0[q] = u_in[nb.x * n_r + k];
+                        if (MODE == PASS_NORMAL || (nb.w & 2)) v1[q] = u_in[nb.y * n_r + k];
+                        if (MODE == PASS_NORMAL || (nb.w & 4)) v2[q] = u_in[nb.z * n_r + k];
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            if (col[q] < 0) continue;
+            double d = fv[q];
+            if (MODE != PASS_RHS_ONLY) {
+                const dbl4 g = s_g[col[q]];
+                d = fma(__ldg(&o.hr[kk[q]]), fma(g.z, v2[q], fma(g.y, v1[q], g.x * v0[q])), d);
+            }
+            tile[col[q] * ld + kk[q]] = d * iv[q];
+        }
+    }
+    if (STAGE) cp_async_wait_all();
+    __syncthreads();
+    if ((threadIdx.x >> 5) == (blockIdx.x & 3)) {
+        const int lane = threadIdx.x & 31;
+        const double *B = STAGE ? sf + lane : fb + fbase + lane;
+        const double *C = STAGE ? sf + (size_t)S * 32 + lane : fcf + fbase + lane;
+        twisted_solve<STAGE ? 8 : 4>(B, C, s_m, tile + (lane & (kRelaxCols - 1)) * ld, n_r, j, lane);
+    }
+    __syncthreads();
+    constexpr int W = STAGE ? 4 : 2;
+    for (int e0 = threadIdx.x; e0 < ne; e0 += 128 * W) {
+        double x[W], uo[W], uf[W][4];
+        int idx[W], fi[W];
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            const int e = e0 + 128 * q;
+            idx[q] = -1;
+            if (e >= ne) continue;
+            const int c = e / n_r, k = e - c * n_r;
+            const int T = s_cell[c];
+            if (T < 0) continue;
+            idx[q] = T * n_r + k;
+            fi[q] = 4 * T * n_r + k;
+            x[q] = tile[c * ld + k];
+            uo[q] = (MODE == PASS_NORMAL && relax != 1.0) ? u_in[idx[q]] : 0.0;
+            if (u_fine) {
+#pragma unroll
+                for (int h = 0; h < 4; ++h) uf[q][h] = u_fine[fi[q] + h * n_r];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            if (idx[q] < 0) continue;
+            double v = x[q];
+            if (relax != 1.0) v = fma(relax, v - uo[q], uo[q]);
+            u_out[idx[q]] = v;
+            if (u_fine) {
+#pragma unroll
+                for (int h = 0; h < 4; ++h) u_fine[fi[q] + h * n_r] = uf[q][h] + v;
+            }
+        }
+    }
+}
+
+// The same relaxation pass with one warp per task and no block barriers, for
+// passes with many tasks: each warp gathers, solves and writes back its own
+// 16 columns, so the serial phases of the tasks resident on an SM overlap
+// with the gather and write-back phases of others and keep its four FP64
+// units busy.  One warp per CTA spreads the tasks evenly over the SMs and
+// their sub-partitions.
+template <int MODE>
+__global__ void __launch_bounds__(32, 16)
+    k_relax_warp(OpView o, const int *__restrict__ cells, const int4 *__restrict__ tnb, const dbl4 *__restrict__ tg,
+                 const double *__restrict__ rinv, const double *__restrict__ fb, const double *__restrict__ fcf,
+                 const double *__restrict__ fm, int S, int j, int task0, const double *__restrict__ f,
+                 const double *u_in, double *u_out, double *__restrict__ u_fine, double relax)
+{
+    extern __shared__ double tile[];
+    __shared__ int s_cell[kRelaxCols];
+    __shared__ int4 s_nb[kRelaxCols];
+    __shared__ dbl4 s_g[kRelaxCols];
+    __shared__ double s_m[2 * kRelaxCols];
+    const int t = task0 + blockIdx.x, lane = threadIdx.x;
+    const int n_r = o.n_r, ld = n_r + 1, ne = kRelaxCols * n_r;
+    s_m[lane] = __ldg(&fm[(size_t)t * 2 * kRelaxCols + lane]);
+    if (lane < kRelaxCols) {
+        const int q = t * kRelaxCols + lane;
+        s_cell[lane] = __ldg(&cells[q]);
+        s_nb[lane] = __ldg(&tnb[q]);
+        s_g[lane] = tg[q];
+    }
+    __syncwarp();
+    constexpr int U = 4;
+    for (int e0 = lane; e0 < ne; e0 += 32 * U) {
+        double fv[U], iv[U], v0[U], v1[U], v2[U];
+        int col[U], kk[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int e = e0 + 32 * q;
+            col[q] = -1;
+            kk[q] = 0;
+            fv[q] = iv[q] = v0[q] = v1[q] = v2[q] = 0.0;
+            if (e < ne) {
+                const int c = e / n_r, k = e - c * n_r;
+                col[q] = c;
+                kk[q] = k;
+                const int T = s_cell[c];
+                if (T >= 0) {
+                    fv[q] = f[T * n_r + k];
+                    iv[q] = __ldg(&rinv[T * n_r + k]);
+                    if (MODE != PASS_RHS_ONLY) {
+                        const int4 nb = s_nb[c];
+                        if (MODE == PASS_NORMAL || (nb.w & 1)) v0[q] = u_in[nb.x * n_r + k];
+                        if (MODE == PASS_NORMAL || (nb.w & 2)) v1[q] = u_in[nb.y * n_r + k];
+                        if (MODE == PASS_NORMAL || (nb.w & 4)) v2[q] = u_in[nb.z * n_r + k];
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            if (col[q] < 0) continue;
+            double d = fv[q];
+            if (MODE != PASS_RHS_ONLY) {
+                const dbl4 g = s_g[col[q]];
+                d = fma(__ldg(&o.hr[kk[q]]), fma(g.z, v2[q], fma(g.y, v1[q], g.x * v0[q])), d);
+            }
+            tile[col[q] * ld + kk[q]] = d * iv[q];
+        }
+    }
+    __syncwarp();
+    const size_t fbase = (size_t)t * S * 32 + lane;
+    twisted_solve<4>(fb + fbase, fcf + fbase, s_m, tile + (lane & (kRelaxCols - 1)) * ld, n_r, j, lane);
+    __syncwarp();
+    constexpr int W = 2;
+    for (int e0 = lane; e0 < ne; e0 += 32 * W) {
+        double x[W], uo[W], uf[W][4];
+        int idx[W], fi[W];
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            const int e = e0 + 32 * q;
+            idx[q] = -1;
+            if (e >= ne) continue;
+            const int c = e / n_r, k = e - c * n_r;
+            const int T = s_cell[c];
+            if (T < 0) continue;
+            idx[q] = T * n_r + k;
+            fi[q] = 4 * T * n_r + k;
+            x[q] = tile[c * ld + k];
+            uo[q] = (MODE == PASS_NORMAL && relax != 1.0) ? u_in[idx[q]] : 0.0;
+            if (u_fine) {
+#pragma unroll
+                for (int h = 0; h < 4; ++h) uf[q][h] = u_fine[fi[q] + h * n_r];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            if (idx[q] < 0) continue;
+            double v = x[q];
+            if (relax != 1.0) v = fma(relax, v - uo[q], uo[q]);
+            u_out[idx[q]] = v;
+            if (u_fine) {
+#pragma unroll
+                for (int h = 0; h < 4; ++h) u_fine[fi[q] + h * n_r] = uf[q][h] + v;
+            }
+        }
+    }
+}
+
+// The vector kernels below are HBM-bound: each thread keeps the loads of 4
+// grid-stride iterations in flight, and the grid holds 8 blocks per SM.
+
+// partial <a, b>
 template <int NT>
 __global__ void __launch_bounds__(NT) k_dot(const double *__restrict__ a, const double *__restrict__ b, int N,
                                             double *__restrict__ partials)
 {
     double acc = 0.0;
-    for (int i = blockIdx.x * NT + threadIdx.x; i < N; i += gridDim.x * NT) acc = fma(a[i], b[i], acc);
+    const int stride = gridDim.x * NT;
+    int i = blockIdx.x * NT + threadIdx.x;
+    for (; i + 3 * stride < N; i += 4 * stride) {
+        double x[4], y[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { x[q] = a[i + q * stride]; y[q] = b[i + q * stride]; }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc = fma(x[q], y[q], acc);
+    }
+    for (; i < N; i += stride) acc = fma(a[i], b[i], acc);
     acc = block_sum<NT>(acc);
     if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
@@ -266,11 +592,29 @@ __global__ void __launch_bounds__(NT) k_axpy_pair(const Scalars *__restrict__ sc
 {
     const double alpha = sc->alpha;
     double acc = 0.0;
-    for (int i = blockIdx.x * NT + threadIdx.x; i < N; i += gridDim.x * NT) {
+    const int stride = gridDim.x * NT;
+    int i = blockIdx.x * NT + threadIdx.x;
+    for (; i + 3 * stride < N; i += 4 * stride) {
+        double pv[4], qv[4], uv[4], rv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int j = i + k * stride;
+            pv[k] = p[j]; qv[k] = q[j]; uv[k] = u[j]; rv[k] = r[j];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int j = i + k * stride;
+            u[j] = fma(alpha, pv[k], uv[k]);
+            const double x = fma(-alpha, qv[k], rv[k]);
+            r[j] = x;
+            acc = fma(x, x, acc);
+        }
+    }
+    for (; i < N; i += stride) {
         u[i] = fma(alpha, p[i], u[i]);
-        const double rv = fma(-alpha, q[i], r[i]);
-        r[i] = rv;
-        acc = fma(rv, rv, acc);
+        const double x = fma(-alpha, q[i], r[i]);
+        r[i] = x;
+        acc = fma(x, x, acc);
     }
     acc = block_sum<NT>(acc);
     if (threadIdx.x == 0) partials[blockIdx.x] = acc;
@@ -282,7 +626,16 @@ __global__ void __launch_bounds__(NT) k_xpby(const Scalars *__restrict__ sc, con
                                              double *__restrict__ p, int N)
 {
     const double beta = sc->beta;
-    for (int i = blockIdx.x * NT + threadIdx.x; i < N; i += gridDim.x * NT) p[i] = fma(beta, p[i], z[i]);
+    const int stride = gridDim.x * NT;
+    int i = blockIdx.x * NT + threadIdx.x;
+    for (; i + 3 * stride < N; i += 4 * stride) {
+        double zv[4], pv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { zv[k] = z[i + k * stride]; pv[k] = p[i + k * stride]; }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) p[i + k * stride] = fma(beta, pv[k], zv[k]);
+    }
+    for (; i < N; i += stride) p[i] = fma(beta, p[i], z[i]);
 }
 
 // Deterministic reduction of the block partials (fixed order) and the PCG scalar step.
@@ -335,15 +688,6 @@ inline int grid_for(long work, int nt, int sm_count)
     return (int)b;
 }
 
-// Columns per tile of the line-relaxation kernels: three [CT][n_r+1] FP64
-// tiles in shared memory, at most 96 KB, at least one column.
-inline int relax_tile(int n_r)
-{
-    int ct = 32;
-    while (ct > 1 && 3 * ct * (n_r + 1) * (int)sizeof(double) > 96 * 1024) ct >>= 1;
-    return ct;
-}
-
 }  // namespace
 
 cudaError_t launch_apply(const Launch &L, const LevelDev &lv, const VertDev &v, const double *x, double *y,
@@ -380,48 +724,58 @@ cudaError_t launch_prolong_add(const Launch &L, const LevelDev &fine, const doub
     return cudaGetLastError();
 }
 
-cudaError_t launch_thomas_factors(const Launch &L, const LevelDev &lv, const VertDev &v)
+cudaError_t launch_twisted_factors(const Launch &L, const LevelDev &lv, const VertDev &v)
 {
-    k_factors<<<(lv.n + 127) / 128, 128, 0, L.s>>>(lv.n, make_view(lv, v, L.n_r), lv.inv, lv.ef, lv.cpf);
+    const int n = lv.n_tasks * kRelaxCols;
+    k_twisted_factors<<<(n + 127) / 128, 128, 0, L.s>>>(lv.n_tasks, make_view(lv, v, L.n_r), lv.task_cells, lv.steps,
+                                                         lv.jmid, lv.rinv, lv.fb, lv.fc, lv.fm);
     return cudaGetLastError();
 }
 
-template <int MODE, bool JACOBI>
-static cudaError_t relax_launch(const Launch &L, const LevelDev &lv, const VertDev &v, const int *cells, int nc,
-                                const double *f, const double *u_in, double *u_out, const double *uc, double relax)
+template <int MODE, bool STAGE>
+static cudaError_t relax_launch_t(const Launch &L, const LevelDev &lv, const VertDev &v, int task0, int n_tasks,
+                                  double relax, const double *f, const double *u_in, double *u_out, double *u_fine,
+                                  size_t smem)
 {
-    if (nc <= 0) return cudaSuccess;
-    const int ct = relax_tile(L.n_r);
-    const size_t smem = (size_t)3 * ct * (L.n_r + 1) * sizeof(double);
-    auto kern = k_relax<MODE, JACOBI>;
+    auto kern = k_relax<MODE, STAGE>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    kern<<<(nc + ct - 1) / ct, kSmooth, smem, L.s>>>(make_view(lv, v, L.n_r), cells, nc, ct, f, u_in, u_out, uc,
-                                                      lv.inv, lv.ef, lv.cpf, relax);
+    kern<<<n_tasks, 128, smem, L.s>>>(make_view(lv, v, L.n_r), lv.task_cells, lv.task_nbr, lv.task_g, lv.rinv, lv.fb,
+                                      lv.fc, lv.fm, lv.steps, lv.jmid, task0, f, u_in, u_out, u_fine, relax);
     return cudaGetLastError();
 }
 
-cudaError_t launch_mcsor_pass(const Launch &L, const LevelDev &lv, const VertDev &v, int colour, int mode, double relax,
-                              const double *f, double *u, const double *uc)
+// Kernel choice: many tasks (at least 4 per SM) and a tile of at most 32 KB
+// -> one warp per task; otherwise one CTA per task, with the multipliers
+// staged in shared memory by cp.async when they fit (small passes, where few
+// CTAs cannot hide the load latency of the serial phase).
+template <int MODE>
+static cudaError_t relax_launch(const Launch &L, const LevelDev &lv, const VertDev &v, int task0, int n_tasks,
+                                double relax, const double *f, const double *u_in, double *u_out, double *u_fine)
 {
-    const int off = lv.colour_off[colour], nc = lv.colour_off[colour + 1] - off;
-    const int *cells = lv.cells_by_colour + off;
-    switch (mode) {
-    case PASS_ZERO: return relax_launch<PASS_ZERO, false>(L, lv, v, cells, nc, f, u, u, uc, relax);
-    case PASS_PROLONG: return relax_launch<PASS_PROLONG, false>(L, lv, v, cells, nc, f, u, u, uc, relax);
-    default: return relax_launch<PASS_NORMAL, false>(L, lv, v, cells, nc, f, u, u, uc, relax);
+    if (n_tasks <= 0) return cudaSuccess;
+    const size_t tile = (((size_t)kRelaxCols * (L.n_r + 1) + 1) & ~(size_t)1) * sizeof(double);
+    if (n_tasks >= 4 * L.sm_count && tile <= 32 * 1024) {
+        k_relax_warp<MODE><<<n_tasks, 32, tile, L.s>>>(make_view(lv, v, L.n_r), lv.task_cells, lv.task_nbr, lv.task_g,
+                                                       lv.rinv, lv.fb, lv.fc, lv.fm, lv.steps, lv.jmid, task0, f,
+                                                       u_in, u_out, u_fine, relax);
+        return cudaGetLastError();
     }
+    const size_t staged = tile + (size_t)2 * lv.steps * 32 * sizeof(double);
+    if (staged <= 160 * 1024)
+        return relax_launch_t<MODE, true>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine, staged);
+    return relax_launch_t<MODE, false>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine, tile);
 }
 
-cudaError_t launch_jacobi(const Launch &L, const LevelDev &lv, const VertDev &v, int mode, double relax,
-                          const double *f, const double *u_in, double *u_out, const double *uc)
+cudaError_t launch_relax(const Launch &L, const LevelDev &lv, const VertDev &v, int mode, int task0, int n_tasks,
+                         double relax, const double *f, const double *u_in, double *u_out, double *u_fine)
 {
     switch (mode) {
-    case PASS_ZERO: return relax_launch<PASS_ZERO, true>(L, lv, v, nullptr, lv.n, f, u_in, u_out, uc, relax);
-    case PASS_PROLONG: return relax_launch<PASS_PROLONG, true>(L, lv, v, nullptr, lv.n, f, u_in, u_out, uc, relax);
-    default: return relax_launch<PASS_NORMAL, true>(L, lv, v, nullptr, lv.n, f, u_in, u_out, uc, relax);
+    case PASS_ZERO: return relax_launch<PASS_ZERO>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
+    case PASS_RHS_ONLY: return relax_launch<PASS_RHS_ONLY>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
+    default: return relax_launch<PASS_NORMAL>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
     }
 }
 

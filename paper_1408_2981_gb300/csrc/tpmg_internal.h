@@ -52,24 +52,40 @@ struct VertDev {            // vertical factors shared by every level (no vertic
     const float *vol32, *w32, *hr32;  // FP32 copies for the mixed-precision V-cycle
 };
 
+// Line relaxation works on tasks of kRelaxCols columns of one colour (the
+// cells of a colour in ascending order, padded with -1 to whole tasks).  The
+// column blocks A_T are factorised from both ends (twisted factorisation):
+// rows 0..jmid-1 from the top, rows n_r-1..jmid+1 from the bottom, meeting in
+// row jmid.  Factors are stored per task as [step][lane] with lane = column +
+// 16 * half, so that the serial phase reads 32 consecutive doubles per step.
+constexpr int kRelaxCols = 16;
+
 struct LevelDev {
     int n = 0;              // cells
     int ref = 0;
     int n_colours = 0;
-    std::vector<int> colour_off;  // [n_colours+1] offsets into cells_by_colour (host copy)
+    int n_tasks = 0;        // relaxation tasks over all colours
+    int steps = 0;          // S = n_r - 1 - jmid: elimination steps of the longer half
+    int jmid = 0;           // meeting row (n_r - 1) / 2
+    std::vector<int> colour_task_off;  // [n_colours+1] first task of each colour (host copy)
+    std::vector<int> colour_cells;     // [n_colours] cells of each colour (host copy)
     int4 *nbr = nullptr;          // [n] {nbr0, nbr1, nbr2, lower-colour mask}
     dbl4 *g = nullptr;            // [n] {g0, g1, g2, g0+g1+g2}
     double *area = nullptr;       // [n]
-    int *cells_by_colour = nullptr;   // [n] cell ids grouped by colour, ascending within a colour
-    // Thomas factors of the column blocks A_T, [n][n_r]
-    double *inv = nullptr;        // 1 / pivot_k
-    double *ef = nullptr;         // forward multiplier  area*w_k / pivot_k
-    double *cpf = nullptr;        // backward multiplier area*w_{k+1} / pivot_k
+    int *task_cells = nullptr;    // [n_tasks][16] cell ids, -1 = padding
+    int4 *task_nbr = nullptr;     // [n_tasks][16] nbr of the task's cells (zero for padding)
+    dbl4 *task_g = nullptr;       // [n_tasks][16] g of the task's cells (zero for padding)
+    // twisted Thomas factors of the column blocks A_T:
+    // rinv [n][n_r] (cell-major) 1 / pivot of row k (p_k above jmid, gamma at jmid, q_k below);
+    // fb, fc [n_tasks][steps][32] forward / backward multipliers,
+    //   top lane (row k = s):          fb = c_k/p_k,     fc = c_{k+1}/p_k
+    //   bottom lane (row k = n_r-1-s): fb = c_{k+1}/q_k, fc = c_k/q_k
+    // fm [n_tasks][2][16] meeting row: c_j/gamma, c_{j+1}/gamma
+    double *rinv = nullptr, *fb = nullptr, *fc = nullptr, *fm = nullptr;
     // workspaces (coarse levels; the finest level uses caller / PCG buffers)
     double *f = nullptr, *u = nullptr, *u2 = nullptr;
     // mixed precision copies
     float *f32 = nullptr, *u32 = nullptr, *u2_32 = nullptr;
-    float *inv32 = nullptr, *ef32 = nullptr, *cpf32 = nullptr;
     float4 *g32 = nullptr;
     float *area32 = nullptr;
 };
@@ -92,7 +108,10 @@ struct Launch {
     int sm_count;
 };
 
-enum PassMode { PASS_NORMAL = 0, PASS_ZERO = 1, PASS_PROLONG = 2 };
+// Right-hand side of a relaxation pass: NORMAL f + sum of all neighbours;
+// ZERO (first forward sweep from a zero guess) only neighbours of a smaller
+// colour (mask bits); RHS_ONLY f alone (colour 0 of a ZERO sweep, Jacobi ZERO).
+enum PassMode { PASS_NORMAL = 0, PASS_ZERO = 1, PASS_RHS_ONLY = 2 };
 
 cudaError_t launch_apply(const Launch &L, const LevelDev &lv, const VertDev &v, const double *x, double *y,
                          double *partials, int n_part);
@@ -100,12 +119,15 @@ cudaError_t launch_residual(const Launch &L, const LevelDev &lv, const VertDev &
                             const double *u, double *r, double *partials, int n_part);
 cudaError_t launch_resid_restrict(const Launch &L, const LevelDev &fine, const LevelDev &coarse, const VertDev &v,
                                   const double *f, const double *u, double *fc);
-cudaError_t launch_mcsor_pass(const Launch &L, const LevelDev &lv, const VertDev &v, int colour, int mode,
-                              double relax, const double *f, double *u, const double *uc);
-cudaError_t launch_jacobi(const Launch &L, const LevelDev &lv, const VertDev &v, int mode, double relax,
-                          const double *f, const double *u_in, double *u_out, const double *uc);
+// One relaxation pass over tasks [task0, task0 + n_tasks) of level lv:
+// u_out_T = (1 - relax) u_in_T + relax A_T^{-1} (f_T + sum_T' alphaS_hat u_in_T').
+// If u_fine is not NULL the new values are also added to the 4 children of
+// each cell in u_fine (prolongation P = R^T of Algorithm 1, fused into the
+// last pass that writes a colour).
+cudaError_t launch_relax(const Launch &L, const LevelDev &lv, const VertDev &v, int mode, int task0, int n_tasks,
+                         double relax, const double *f, const double *u_in, double *u_out, double *u_fine);
 cudaError_t launch_prolong_add(const Launch &L, const LevelDev &fine, const double *uc, double *u);
-cudaError_t launch_thomas_factors(const Launch &L, const LevelDev &lv, const VertDev &v);
+cudaError_t launch_twisted_factors(const Launch &L, const LevelDev &lv, const VertDev &v);
 cudaError_t launch_dot(const Launch &L, long n, const double *a, const double *b, double *partials, int n_part);
 cudaError_t launch_finish(const Launch &L, int what, const double *partials, int n_part, Scalars *sc);
 cudaError_t launch_axpy_pair(const Launch &L, long n, const Scalars *sc, const double *p, const double *q, double *u,
