@@ -63,7 +63,7 @@ typedef struct {
     vec3 *centre;       /* [n_cells] cell centre r_T                        */
     double *area;       /* [n_cells] |T|                                    */
     double *g;          /* [n_cells][3] |S_TT'| n.(r_T'-r_T)/|r_T'-r_T|^2  */
-    int *colour;        /* [n_cells] greedy colour of the neighbour graph   */
+    int *colour;        /* [n_cells] DSATUR colour of the neighbour graph   */
     int n_colours;
 } ogrid;
 
@@ -263,22 +263,95 @@ static void compute_geometry(ogrid *G, int centre_kind)
         }
 }
 
-/* Greedy colouring in cell-index order: smallest colour not taken by an
- * already-coloured neighbour (Reading C4: multicolour block-SOR). */
-static void greedy_colour(ogrid *G)
+/* Colouring by saturation degree (Brelaz's DSATUR; Reading C4: multicolour
+ * block-SOR, as few colours -- sequential passes -- as possible): repeatedly
+ * take, among the uncoloured cells, one whose coloured neighbours show the
+ * most distinct colours, the one with the smallest index among those, and
+ * give it the smallest colour none of its neighbours has.  Every cell has 3
+ * neighbours, so at most 4 colours are used; on the refined icosahedra 3
+ * suffice.  Candidates wait in one binary min-heap of cell indices per
+ * saturation value; a popped entry is skipped if its cell has been coloured or
+ * has reached a higher saturation since it was pushed. */
+typedef struct { int *a; int n; } iheap;
+
+static void iheap_push(iheap *h, int v)
 {
-    int T, e, c;
+    int i = h->n++;
+    h->a[i] = v;
+    while (i > 0 && h->a[(i - 1) / 2] > h->a[i]) {
+        int t = h->a[i]; h->a[i] = h->a[(i - 1) / 2]; h->a[(i - 1) / 2] = t;
+        i = (i - 1) / 2;
+    }
+}
+
+static int iheap_pop(iheap *h)
+{
+    int top = h->a[0], i = 0;
+    h->a[0] = h->a[--h->n];
+    for (;;) {
+        int l = 2 * i + 1, r = l + 1, m = i, t;
+        if (l < h->n && h->a[l] < h->a[m]) m = l;
+        if (r < h->n && h->a[r] < h->a[m]) m = r;
+        if (m == i) break;
+        t = h->a[i]; h->a[i] = h->a[m]; h->a[m] = t;
+        i = m;
+    }
+    return top;
+}
+
+static int saturation(const ogrid *G, int T)
+{
+    int seen[4] = {0, 0, 0, 0}, e, s = 0;
+    for (e = 0; e < 3; ++e) {
+        int c = G->colour[G->nbr[3 * T + e]];
+        if (c >= 0 && !seen[c]) { seen[c] = 1; ++s; }
+    }
+    return s;
+}
+
+static int dsatur_colour(ogrid *G)
+{
+    int n = G->n_cells, T, e, c, s, step;
+    int *sat = (int *)calloc((size_t)n, sizeof(int));
+    iheap h[4];
+    int ok = sat != NULL;
+    for (s = 0; s < 4; ++s) {
+        h[s].a = (int *)malloc((size_t)n * sizeof(int));
+        h[s].n = 0;
+        ok = ok && h[s].a != NULL;
+    }
+    if (!ok) {
+        free(sat);
+        for (s = 0; s < 4; ++s) free(h[s].a);
+        return -1;
+    }
+    for (T = 0; T < n; ++T) { G->colour[T] = -1; iheap_push(&h[0], T); }
     G->n_colours = 0;
-    for (T = 0; T < G->n_cells; ++T) {
+    for (step = 0; step < n; ++step) {
         int used[4] = {0, 0, 0, 0};
+        T = -1;
+        for (s = 3; s >= 0 && T < 0; --s)
+            while (h[s].n > 0) {
+                int cand = iheap_pop(&h[s]);
+                if (G->colour[cand] < 0 && sat[cand] == s) { T = cand; break; }
+            }
         for (e = 0; e < 3; ++e) {
-            int Tp = G->nbr[3 * T + e];
-            if (Tp < T) used[G->colour[Tp]] = 1;
+            c = G->colour[G->nbr[3 * T + e]];
+            if (c >= 0) used[c] = 1;
         }
         for (c = 0; c < 4 && used[c]; ++c) {}
-        G->colour[T] = c; /* a cubic graph never needs a fifth colour */
+        G->colour[T] = c;
         if (c + 1 > G->n_colours) G->n_colours = c + 1;
+        for (e = 0; e < 3; ++e) {
+            int U = G->nbr[3 * T + e], su;
+            if (G->colour[U] >= 0) continue;
+            su = saturation(G, U);
+            if (su > sat[U]) { sat[U] = su; iheap_push(&h[su], U); }
+        }
     }
+    free(sat);
+    for (s = 0; s < 4; ++s) free(h[s].a);
+    return 0;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -570,7 +643,7 @@ void *oracle_create(int refinement, int n_levels, int n_r, double H, double grad
         if (refine(&o->grid[l - 1], &o->grid[l]) || match_edges(&o->grid[l])) goto fail;
     for (l = 0; l <= refinement; ++l) {
         compute_geometry(&o->grid[l], centre_kind);
-        greedy_colour(&o->grid[l]);
+        if (dsatur_colour(&o->grid[l])) goto fail;
     }
     /* smallest centre distance on the finest level */
     {

@@ -14,6 +14,8 @@
 #include <array>
 #include <cmath>
 #include <cstdio>
+#include <functional>
+#include <queue>
 
 #include "tpmg_internal.h"
 
@@ -178,20 +180,50 @@ void geometry(HostLevel &L, int centre_kind)
         }
 }
 
-void colour_greedy(HostLevel &L)
+// Colouring for the multicolour block-SOR: Brelaz's saturation-degree
+// order (DSATUR).  The next cell coloured is, among the uncoloured ones, one
+// whose coloured neighbours show the most distinct colours (the lowest cell id
+// among those), and it takes the lowest colour its neighbours do not have.
+// With 3 neighbours per cell at most 4 colours occur; the refined icosahedra
+// need 3, i.e. 3 sequential passes per sweep.
+void colour_dsatur(HostLevel &L)
 {
     L.colour.assign(L.n, -1);
     L.n_colours = 0;
-    for (int T = 0; T < L.n; ++T) {
-        unsigned used = 0;
+    std::vector<int> sat(L.n, 0);
+    using MinHeap = std::priority_queue<int, std::vector<int>, std::greater<int>>;
+    MinHeap cand[4];   // cell ids by saturation; stale entries are skipped
+    for (int T = 0; T < L.n; ++T) cand[0].push(T);
+    auto colours_around = [&](int T) {
+        unsigned m = 0;
         for (int e = 0; e < 3; ++e) {
-            const int U = L.nbr[3 * T + e];
-            if (U < T) used |= 1u << L.colour[U];
+            const int c = L.colour[L.nbr[3 * T + e]];
+            if (c >= 0) m |= 1u << c;
         }
+        return m;
+    };
+    for (int done = 0; done < L.n; ++done) {
+        int T = -1;
+        for (int s = 3; s >= 0 && T < 0; --s)
+            while (!cand[s].empty()) {
+                const int v = cand[s].top();
+                cand[s].pop();
+                if (L.colour[v] < 0 && sat[v] == s) { T = v; break; }
+            }
+        const unsigned used = colours_around(T);
         int c = 0;
         while (used & (1u << c)) ++c;
         L.colour[T] = c;
         L.n_colours = std::max(L.n_colours, c + 1);
+        for (int e = 0; e < 3; ++e) {
+            const int U = L.nbr[3 * T + e];
+            if (L.colour[U] >= 0) continue;
+            const int su = __builtin_popcount(colours_around(U));
+            if (su > sat[U]) {
+                sat[U] = su;
+                cand[su].push(U);
+            }
+        }
     }
 }
 
@@ -209,7 +241,7 @@ bool build_host_grid(const tpmg_params &p, HostGrid &G, std::string &err)
             continue;
         }
         geometry(G.lev[l], p.centre);
-        colour_greedy(G.lev[l]);
+        colour_dsatur(G.lev[l]);
         if (G.lev[l].n_colours > 4) { err = "colouring needed more than 4 colours"; return false; }
         for (int T = 0; T < G.lev[l].n; ++T)
             for (int e = 0; e < 3; ++e)

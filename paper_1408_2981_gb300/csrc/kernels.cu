@@ -747,8 +747,8 @@ static cudaError_t relax_launch_t(const Launch &L, const LevelDev &lv, const Ver
     return cudaGetLastError();
 }
 
-// Kernel choice: many tasks (at least 4 per SM) and a tile of at most 32 KB
-// -> one warp per task; otherwise one CTA per task, with the multipliers
+// Kernel choice: more tasks than one wave of CTAs holds (8 per SM) and a tile
+// of at most 32 KB -> one warp per task; otherwise one CTA per task, with the multipliers
 // staged in shared memory by cp.async when they fit (small passes, where few
 // CTAs cannot hide the load latency of the serial phase).
 template <int MODE>
@@ -757,7 +757,7 @@ static cudaError_t relax_launch(const Launch &L, const LevelDev &lv, const VertD
 {
     if (n_tasks <= 0) return cudaSuccess;
     const size_t tile = (((size_t)kRelaxCols * (L.n_r + 1) + 1) & ~(size_t)1) * sizeof(double);
-    if (n_tasks >= 4 * L.sm_count && tile <= 32 * 1024) {
+    if (n_tasks >= 8 * L.sm_count && tile <= 32 * 1024) {
         k_relax_warp<MODE><<<n_tasks, 32, tile, L.s>>>(make_view(lv, v, L.n_r), lv.task_cells, lv.task_nbr, lv.task_g,
                                                        lv.rinv, lv.fb, lv.fc, lv.fm, lv.steps, lv.jmid, task0, f,
                                                        u_in, u_out, u_fine, relax);

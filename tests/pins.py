@@ -74,8 +74,11 @@ def pin_level0_closed_forms(ns):
 def pin_mesh_topology(ns, max_ref: int = 4):
     """Neighbour relation symmetric, cells counter-clockwise seen from outside,
     the centre child 4T of a refined cell borders exactly its three siblings,
-    colouring valid with <= 4 colours, g_TT' > 0 and g_TT' = g_T'T, vertices and
-    centres on the unit sphere, circumcentres equidistant from the corners."""
+    colouring valid with exactly 3 colours (the 5 cells around an original
+    icosahedron vertex form an odd cycle, so 2 never suffice; Brooks' theorem
+    guarantees 3 for this cubic planar graph and the saturation-degree order
+    finds them), g_TT' > 0 and g_TT' = g_T'T, vertices and centres on the unit
+    sphere, circumcentres equidistant from the corners."""
     for ck in (0, 1):
         o = ns.Oracle(refinement=max_ref, n_levels=1, n_r=1, centre_kind=ck)
         for ref in range(max_ref + 1):
@@ -96,7 +99,7 @@ def pin_mesh_topology(ns, max_ref: int = 4):
                     ep = back[0]
                     np.testing.assert_array_equal(cor[Tp, ep], q)
                     np.testing.assert_array_equal(cor[Tp, (ep + 1) % 3], p)
-            assert col.max() <= 3 and col.min() >= 0
+            assert col.max() == 2 and col.min() >= 0
             assert np.all(gg > 0)
             np.testing.assert_allclose(np.linalg.norm(cor, axis=2), 1.0, rtol=4 * EPS)
             np.testing.assert_allclose(np.linalg.norm(cen, axis=1), 1.0, rtol=4 * EPS)

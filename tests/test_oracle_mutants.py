@@ -55,7 +55,8 @@ MUTANTS = {
     "child_orientation": ("c[3] = v0;  c[4] = m01; c[5] = m20;", "c[3] = v0;  c[4] = m20; c[5] = m01;"),
     "residual_sign": ("o->mg_r[l][i] = f[i] - o->mg_r[l][i];", "o->mg_r[l][i] = o->mg_r[l][i] - f[i];"),
     "vertex_mean_centre": ("G->centre[T] = v_unit(v_add(v_add(a, b), c));", "G->centre[T] = v_unit(v_add(a, b));"),
-    "colouring_looks_ahead": ("if (Tp < T) used[G->colour[Tp]] = 1;", "if (Tp > T) used[G->colour[Tp]] = 1;"),
+    "colouring_ignores_colour0": ("            if (c >= 0) used[c] = 1;", "            if (c >= 1) used[c] = 1;"),
+    "colouring_lowest_saturation": ("for (s = 3; s >= 0 && T < 0; --s)", "for (s = 0; s < 4 && T < 0; ++s)"),
     "grading_exponent": ("pow(grading, (double)k)", "pow(grading, (double)(k + 1))"),
     "relaxation_ignored": ("u_in[(size_t)T * n + k] + o->relax * o->col_x[k];", "u_in[(size_t)T * n + k] + o->col_x[k];"),
     "diag_misses_mass": ("o->col_b[k] = beta_hat(o, G, T, k) + hs;", "o->col_b[k] = hs;"),
