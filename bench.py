@@ -53,8 +53,27 @@ FLOPS_PER_UNIT = {"relax": 12.0, "apply": 17.0, "restrict": 16.0, "residual": 17
                   "dot": 2.0, "xpby": 2.0, "prolong": 1.0}
 BYTES_PER_UNIT = {"relax": 48.0, "apply": 24.0, "restrict": 18.0, "residual": 24.0, "axpy": 48.0,
                   "dot": 16.0, "xpby": 24.0, "prolong": 20.0}
+# DRAM bytes per launch of a kernel class from an ncu capture (profiles/), valid
+# while kernels.cu is the file that was profiled (sha256 prefix)
+TRAFFIC = {"relax": {"bytes_per_launch": 18.16e6, "kernels_sha256": "8127efee1267ae08",
+                     "source": "profiles/relax_dram_81920x64.md", "workload": "81920x64"}}
 SM_COUNT_GB300 = 152
 FP64_FMA_PER_CLK_PER_SM = 2     # GB300: 1.25 TFLOP/s dense FP64 at 2.07 GHz over 152 SMs
+
+
+def kernels_sha256() -> str:
+    import hashlib
+
+    with open(os.path.join(ROOT, "paper_1408_2981_gb300", "csrc", "kernels.cu"), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def traffic_of(kernel: str, workload: str):
+    """ncu DRAM bytes per launch, or None once the kernels changed after the capture."""
+    t = TRAFFIC.get(kernel)
+    if t and t["workload"] == workload and t["kernels_sha256"] == kernels_sha256():
+        return t["bytes_per_launch"]
+    return None
 
 
 def load_peaks() -> dict:
@@ -309,7 +328,8 @@ def run_tpmg(args, wl):
         achieved = flops / (d["ms"] / 1e3) / 1e12
         peak = fp64_peak_tflops(sm_count, peaks["sm_max_mhz"])
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": f"{dominant} (FP64)",
+                "traffic": traffic_of(dominant, args.workload), "traffic_unit": "bytes per launch (ncu)",
+                "algorithmic_bytes_per_launch": nbytes / d["timed"], "kernel": f"{dominant} (FP64)",
                 "peak_source": f"FP64 pipe: {sm_count} SMs x {FP64_FMA_PER_CLK_PER_SM} DFMA/clk x 2 x "
                                f"{peaks['sm_max_mhz']:.0f} MHz",
                 "launches_per_step": (d["launches"] - before[dominant]["launches"]) / args.steps,
