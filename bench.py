@@ -12,6 +12,11 @@ manufactured solution u* = sum of 8 seeded low-order spherical harmonics x
 vertical cosines, f = A u*; 6 multigrid levels, 2/2 line-SOR sweeps, 1 coarse
 sweep; FP64 throughout.
 
+Other workloads (--workload): 1280x16 (the small parity case), 81920x64-mixed
+(the same solve with the V-cycle in FP32 on a BF16 stencil and flexible CG in
+FP64), 327680x128-mixed (refinement 7 x 128 levels, 41.9M unknowns, mixed
+precision) and 327680x128 (the same grid in FP64).
+
 Flags: --gpus N --steps K --warmup W [--impl tpmg|reference] [--workload NAME]
 Under torchrun (N > 1) every rank solves its own replica (no data exchange:
 the path shards only through independent problems on this pool).
@@ -34,6 +39,8 @@ if ROOT not in sys.path:
 
 METRIC = "unknowns/sec to 1e-5 residual reduction (TPMG-PCG) at 1 GB300; HBM GB/s vs peak"
 
+MIXED = dict(precision=1, coeff_storage=1)   # TPMG_PREC_MIXED, TPMG_COEFF_FULL
+
 WORKLOADS = {
     "81920x64": dict(
         params=dict(refinement=6, n_levels=6, n_r=64, grading=1.05, courant_c=80.0, nu_pre=2, nu_post=2, nu_coarse=1),
@@ -45,20 +52,41 @@ WORKLOADS = {
         rhs="uniform", seed=2981001,
         text="icosahedral refinement 3 (1280 triangles) x 16 uniform levels over 10 km, omega^2/h^2=8, "
              "RHS uniform[-1,1], 4 MG levels, nu 1/1/1, rtol 1e-5"),
+    "81920x64-mixed": dict(
+        params=dict(refinement=6, n_levels=6, n_r=64, grading=1.05, courant_c=80.0, nu_pre=2, nu_post=2, nu_coarse=1,
+                    **MIXED),
+        rhs="manufactured", seed=2981002,
+        text="as 81920x64, V-cycle in FP32 on a BF16 stencil, outer flexible CG in FP64"),
+    "327680x128-mixed": dict(
+        params=dict(refinement=7, n_levels=6, n_r=128, grading=1.05, courant_c=8.0, nu_pre=2, nu_post=2, nu_coarse=1,
+                    **MIXED),
+        rhs="uniform", seed=2981003,
+        text="icosahedral refinement 7 (327680 triangles) x 128 levels graded 1.05 over 10 km, omega^2/h^2=8, "
+             "RHS uniform[-1,1], 6 MG levels, nu 2/2/1, V-cycle in FP32 on a BF16 stencil, outer flexible CG "
+             "in FP64, rtol 1e-5"),
+    "327680x128": dict(
+        params=dict(refinement=7, n_levels=6, n_r=128, grading=1.05, courant_c=8.0, nu_pre=2, nu_post=2, nu_coarse=1),
+        rhs="uniform", seed=2981003,
+        text="as 327680x128-mixed, everything in FP64 (plain TPMG-PCG on the same grid)"),
 }
 
-# FP64 flops per unknown of each kernel class as written (FMA = 2 flops), and
-# algorithmic HBM bytes per unknown (each array streamed once).
-FLOPS_PER_UNIT = {"relax": 12.0, "apply": 17.0, "restrict": 16.0, "residual": 17.0, "axpy": 6.0,
-                  "dot": 2.0, "xpby": 2.0, "prolong": 1.0}
-BYTES_PER_UNIT = {"relax": 48.0, "apply": 24.0, "restrict": 18.0, "residual": 24.0, "axpy": 48.0,
-                  "dot": 16.0, "xpby": 24.0, "prolong": 20.0}
+# Flops per unknown of each kernel class as written (FMA = 2 flops) and
+# algorithmic HBM bytes per unknown (each array streamed once), per precision
+# of the V-cycle; the outer Krylov kernels are FP64 in both forms.
+OUTER = {"apply": (17.0, 24.0), "residual": (17.0, 24.0), "axpy": (6.0, 48.0), "dot": (2.0, 16.0),
+         "xpby": (2.0, 24.0)}
+PER_UNIT = {
+    0: dict(OUTER, relax=(12.0, 48.0), restrict=(16.0, 18.0), prolong=(1.0, 20.0)),
+    # mixed: FP32 relax reads f (4), BF16 stencil (8 + 2), u (4), writes u (4)
+    1: dict(OUTER, relax=(20.0, 22.0), restrict=(20.0, 19.0), prolong=(1.0, 10.0)),
+}
 # DRAM bytes per launch of a kernel class from an ncu capture (profiles/), valid
 # while kernels.cu is the file that was profiled (sha256 prefix)
 TRAFFIC = {"relax": {"bytes_per_launch": 18.16e6, "kernels_sha256": "8127efee1267ae08",
                      "source": "profiles/relax_dram_81920x64.md", "workload": "81920x64"}}
 SM_COUNT_GB300 = 152
 FP64_FMA_PER_CLK_PER_SM = 2     # GB300: 1.25 TFLOP/s dense FP64 at 2.07 GHz over 152 SMs
+ORACLE_FULL_SOLVE_MAX_UNKNOWNS = 6_000_000   # larger workloads: the CPU baseline times one iteration
 
 
 def kernels_sha256() -> str:
@@ -181,7 +209,7 @@ def oracle_inputs(wl: dict):
     import oracle
     from paper_1408_2981_gb300 import inputs
 
-    o = oracle.Oracle(**wl["params"])
+    o = oracle.Oracle(**{k: v for k, v in wl["params"].items() if k not in ("precision", "coeff_storage")})
     if wl["rhs"] == "manufactured":
         g, v = o.grid(o.refinement), o.vertical()
         ustar = inputs.manufactured_solution(g["centre"], v["r"], wl["seed"])
@@ -191,44 +219,64 @@ def oracle_inputs(wl: dict):
     return o, f
 
 
-def time_oracle(wl: dict, min_seconds: float, max_solves: int, rtol: float):
+def time_oracle(wl: dict, min_seconds: float, max_solves: int, rtol: float, iters_hint: int | None = None):
+    """Oracle solves of the workload on the host cores (setup excluded).
+
+    Returns (unknowns per second of a full solve, sample text, oracle iterations).
+    Up to ORACLE_FULL_SOLVE_MAX_UNKNOWNS the oracle runs whole solves (at least
+    one, until min_seconds).  Beyond that a bounded sample: the oracle runs one
+    PCG iteration (initial residual, V-cycle, operator, update), and a full
+    solve is taken as that time x the iteration count of the GPU solve."""
     o, f = oracle_inputs(wl)
-    times, iters = [], None
-    while len(times) < max_solves and (sum(times) < min_seconds or not times):
-        t0 = time.perf_counter()
-        res = o.pcg(f, rtol=rtol, max_iter=200)
-        times.append(time.perf_counter() - t0)
-        iters = res["iters"]
-    return o.size(), times, iters
+    N = o.size()
+    flexible = wl["params"].get("precision", 0) == 1
+    if flexible:
+        o.set_vcycle_bf16(True)
+    if N <= ORACLE_FULL_SOLVE_MAX_UNKNOWNS:
+        times, iters = [], None
+        while len(times) < max_solves and (sum(times) < min_seconds or not times):
+            t0 = time.perf_counter()
+            res = o.pcg(f, rtol=rtol, max_iter=200, flexible=flexible)
+            times.append(time.perf_counter() - t0)
+            iters = res["iters"]
+        return N * len(times) / sum(times), (f"{len(times)} full oracle solve(s) of the same workload, setup "
+                                             f"excluded, {iters} iterations, single thread"), iters
+    t0 = time.perf_counter()
+    o.pcg(f, rtol=0.0, max_iter=1, flexible=flexible)
+    t1 = time.perf_counter() - t0
+    k = max(1, iters_hint or 1)
+    return N / (t1 * k), (f"bounded sample: 1 oracle PCG iteration of the same workload ({t1:.1f} s, "
+                          f"single thread), scaled to the GPU's {k} iterations"), None
 
 
 # ----------------------------------------------------------------------------- arms
 def run_reference(args, wl):
+    """The oracle as the reference arm, on the machine's host cores (rank 0 only).
+    Each step is one full oracle solve, or for workloads beyond
+    ORACLE_FULL_SOLVE_MAX_UNKNOWNS the bounded one-iteration sample of time_oracle."""
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
-    o, f = oracle_inputs(wl)
-    N = o.size()
-    for _ in range(min(args.warmup, 1)):
-        o.pcg(f, rtol=args.rtol, max_iter=200)
-    times = []
+    values, sample, iters = [], "", None
     for _ in range(args.steps):
-        t0 = time.perf_counter()
-        res = o.pcg(f, rtol=args.rtol, max_iter=200)
-        times.append(time.perf_counter() - t0)
-    total = sum(times)
-    value = N * len(times) / total
+        v, sample, iters = time_oracle(wl, min_seconds=0.0, max_solves=1, rtol=args.rtol, iters_hint=args.iters_hint)
+        values.append(v)
+    N = WORKLOADS_N(wl)
+    value = len(values) / sum(1.0 / v for v in values)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world,
-            "steps": len(times), "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * total / len(times),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl["text"], "n_unknowns": N},
-            "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{len(times)} full oracle solves of the workload (setup excluded), "
-                                       f"{res['iters']} PCG iterations each"},
+            "steps": len(values), "warmup": 0, "ms_per_step": 1e3 * N / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": {"workload": wl["text"], "n_unknowns": N},
+            "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "iters": res["iters"], "rel_resid": res["rel_resid"]}
+            "iters": iters}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def WORKLOADS_N(wl: dict) -> int:
+    p = wl["params"]
+    return 20 * 4 ** p["refinement"] * p["n_r"]
 
 
 def run_tpmg(args, wl):
@@ -247,6 +295,8 @@ def run_tpmg(args, wl):
     stream = torch.cuda.current_stream()
     s = binding.Solver(stream=stream, **wl["params"])
     N = s.N
+    mixed = wl["params"].get("precision", 0) == 1
+    per_unit = PER_UNIT[1 if mixed else 0]
     m = s.export_mesh()
     if wl["rhs"] == "manufactured":
         ustar = torch.from_numpy(inputs.manufactured_solution(m["centres"], m["r_faces"], wl["seed"])).cuda()
@@ -323,37 +373,43 @@ def run_tpmg(args, wl):
     roof = None
     if d["ms"] > 0 and d["timed"] > 0:
         units_timed = (d["units"] - before[dominant]["units"]) * d["timed"] / max(1, d["launches"] - before[dominant]["launches"])
-        flops = FLOPS_PER_UNIT.get(dominant, 0.0) * units_timed
-        nbytes = BYTES_PER_UNIT.get(dominant, 0.0) * units_timed
-        achieved = flops / (d["ms"] / 1e3) / 1e12
-        peak = fp64_peak_tflops(sm_count, peaks["sm_max_mhz"])
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+        fpu, bpu = per_unit.get(dominant, (0.0, 0.0))
+        flops, nbytes = fpu * units_timed, bpu * units_timed
+        secs = d["ms"] / 1e3
+        fp64_kernel = not mixed or dominant in OUTER
+        if fp64_kernel:   # FP64 arithmetic: bound by the FP64 pipe
+            achieved, peak = flops / secs / 1e12, fp64_peak_tflops(sm_count, peaks["sm_max_mhz"])
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "peak_source": f"FP64 pipe: {sm_count} SMs x {FP64_FMA_PER_CLK_PER_SM} DFMA/clk x 2 x "
+                                   f"{peaks['sm_max_mhz']:.0f} MHz"}
+        else:             # FP32 V-cycle on a BF16 stencil: bound by HBM
+            achieved, peak = nbytes / secs / 1e9, peaks["hbm_gbs"]
+            roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "peak_source": f"{peaks['source']} HBM copy bandwidth"}
+        roof.update({"frac": achieved / peak,
                 "traffic": traffic_of(dominant, args.workload), "traffic_unit": "bytes per launch (ncu)",
-                "algorithmic_bytes_per_launch": nbytes / d["timed"], "kernel": f"{dominant} (FP64)",
-                "peak_source": f"FP64 pipe: {sm_count} SMs x {FP64_FMA_PER_CLK_PER_SM} DFMA/clk x 2 x "
-                               f"{peaks['sm_max_mhz']:.0f} MHz",
+                "algorithmic_bytes_per_launch": nbytes / d["timed"],
+                "kernel": f"{dominant} ({'FP64' if fp64_kernel else 'FP32/BF16'})",
                 "launches_per_step": (d["launches"] - before[dominant]["launches"]) / args.steps,
                 "avg_launch_us": 1e3 * d["ms"] / d["timed"],
                 "timed_launches": d["timed"],
                 "hbm_gbs_algorithmic": nbytes / (d["ms"] / 1e3) / 1e9,
                 "hbm_frac_of_measured": nbytes / (d["ms"] / 1e3) / 1e9 / peaks["hbm_gbs"],
-                "share_of_step": d["ms"] / (local_ms / args.steps)}
+                "share_of_step": d["ms"] / (local_ms / args.steps)})
     # aggregate algorithmic HBM rate of the whole solve
-    tot_bytes = sum(BYTES_PER_UNIT.get(c, 0.0) * (v["units"] - before[c]["units"]) for c, v in prof.items())
+    tot_bytes = sum(per_unit.get(c, (0.0, 0.0))[1] * (v["units"] - before[c]["units"]) for c, v in prof.items())
     hbm = {"achieved_gbs": tot_bytes / (local_ms / 1e3) / 1e9, "peak_gbs": peaks["hbm_gbs"],
            "frac": tot_bytes / (local_ms / 1e3) / 1e9 / peaks["hbm_gbs"], "source": peaks["source"]}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        n_o, times, o_iters = time_oracle(wl, min_seconds=10.0, max_solves=3, rtol=args.rtol)
-        cpu = {"value": n_o * len(times) / sum(times), "unit": "unknowns/s", "cores": 1, "kind": "oracle",
-               "sample": f"{len(times)} full oracle solve(s) of the same workload, setup excluded, "
-                         f"{o_iters} PCG iterations, single thread"}
+        v_o, sample, _ = time_oracle(wl, min_seconds=10.0, max_solves=3, rtol=args.rtol, iters_hint=iters[-1])
+        cpu = {"value": v_o, "unit": "unknowns/s", "cores": 1, "kind": "oracle", "sample": sample}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
                 "config": {"workload": wl["text"], "n_unknowns": N, "parallelism": f"replicas{world}",
                            "l2": "flushed between steps (write of 2x L2 outside the timed events)"},
                 "e2e": {"value": e2e_value, "unit": "unknowns/s", "h2d_bytes_per_step": 2 * 8 * N,
@@ -378,6 +434,8 @@ def main(argv=None):
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="81920x64")
     ap.add_argument("--rtol", type=float, default=1e-5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--iters-hint", type=int, default=None,
+                    help="reference arm on workloads sampled by one iteration: iterations of a full solve")
     args = ap.parse_args(argv)
     if args.warmup < 1 and args.impl == "tpmg":
         ap.error("--warmup must be >= 1")

@@ -62,17 +62,24 @@ typedef enum {
 enum { TPMG_SMOOTH_MCSOR = 0,   /* multicolour block-SOR: forward colours before, reverse after the correction */
        TPMG_SMOOTH_JACOBI = 1 }; /* weighted block-Jacobi */
 
-/* Storage of the stencil (Sec. 3.2): recomputed on the fly from O(n_r + n_cells)
- * factorised data (TPMG^otimes), or stored per unknown (TPMG^full). */
+/* Storage of the V-cycle's stencil (Sec. 4.2): recomputed on the fly from
+ * O(n_r + n_cells) factorised FP64 data (TPMG^otimes; the FP64 V-cycle), or
+ * stored per unknown (TPMG^full) in BF16 (the mixed-precision V-cycle).  The
+ * outer operator of tpmg_solve and tpmg_apply_operator is always the exact
+ * factorised FP64 one. */
 enum { TPMG_COEFF_FACTORISED = 0, TPMG_COEFF_FULL = 1 };
 
 /* Cell centre used by the two-point flux of Appendix A. */
 enum { TPMG_CENTRE_CIRCUM = 0,      /* spherical circumcentre (centre chord normal to the edge) */
        TPMG_CENTRE_VERTEX_MEAN = 1 };
 
-/* Arithmetic of the V-cycle.  FP64: everything in double.  MIXED: the V-cycle
- * (operator, line smoother, transfers) in FP32 with BF16-stored stencil
- * factors; the outer Krylov vectors, residual and dot products in FP64. */
+/* Arithmetic of the V-cycle.  FP64: everything in double (requires
+ * TPMG_COEFF_FACTORISED).  MIXED (requires TPMG_COEFF_FULL): the V-cycle
+ * (operator, line smoother, transfers) in FP32 on the BF16 stencil, with the
+ * column factors precomputed per level in FP32; the outer Krylov vectors,
+ * residual, dot products and updates in FP64.  Because the FP32 V-cycle is not
+ * exactly symmetric, tpmg_solve then runs flexible CG (Polak-Ribiere
+ * coefficient), which reaches the FP64 solution to the requested tolerance. */
 enum { TPMG_PREC_FP64 = 0, TPMG_PREC_MIXED = 1 };
 
 typedef struct {
@@ -139,7 +146,7 @@ tpmg_status tpmg_vcycle(tpmg_ctx *ctx, const double *d_r, double *d_z);
  * convenience, not part of the method.
  *
  * d_r, d_z: device, n_cells*n_r doubles, must not overlap; d_r is not modified.
- * The context's device must be current.  Scratch needed: 2 * sum over the
+ * FP64 contexts only (TPMG_ERR_INVALID_ARG otherwise).  The context's device must be current.  Scratch needed: 2 * sum over the
  * coarse levels of n_cells_l * n_r doubles for block-SOR, plus sum over all
  * levels of n_cells_l * n_r for block Jacobi (each part rounded up to 32
  * doubles); a larger problem is rejected with INVALID_ARG before anything is

@@ -74,6 +74,11 @@ def _load(path: str | None = None):
         lib.oracle_prolong_add.argtypes = [_P, _I, _P, _P]
         lib.oracle_vcycle.argtypes = [_P, _P, _P]
         lib.oracle_pcg.argtypes = [_P, _P, _P, _D, _I, _P, _P, _P, _P]
+        lib.oracle_fcg.argtypes = [_P, _P, _P, _D, _I, _P, _P, _P, _P]
+        lib.oracle_set_vcycle_bf16.argtypes = [_P, _I]
+        lib.oracle_set_vcycle_bf16.restype = None
+        lib.oracle_bf16.argtypes = [_D]
+        lib.oracle_bf16.restype = _D
         lib.oracle_richardson.argtypes = [_P, _P, _P, _I, _P]
         lib.oracle_thomas.argtypes = [_I, _P, _P, _P, _P, _P]
         lib.oracle_column_solve.argtypes = [_I, _P, _P, _P, _P]
@@ -103,6 +108,11 @@ def thomas(a, b, c, d, lib_path: str | None = None) -> np.ndarray:
     if _load(lib_path).oracle_thomas(n, _ptr(a), _ptr(b), _ptr(c), _ptr(d), _ptr(x)) != 0:
         raise ValueError("oracle_thomas failed")
     return x
+
+
+def bf16(x: float, lib_path: str | None = None) -> float:
+    """x rounded to the nearest bfloat16 value (ties to even), as the oracle rounds coefficients."""
+    return _load(lib_path).oracle_bf16(float(x))
 
 
 def column_solve(c, m, d, lib_path: str | None = None) -> np.ndarray:
@@ -241,15 +251,22 @@ class Oracle:
         self._lib.oracle_vcycle(self._h, _ptr(r), _ptr(z))
         return z
 
-    def pcg(self, f, u0=None, rtol: float = 1e-5, max_iter: int = 100) -> dict:
+    def set_vcycle_bf16(self, on: bool = True):
+        """Use the V-cycle of the mixed-precision form (BF16-rounded coefficients,
+        FP64 arithmetic) in vcycle(), pcg() and fcg()."""
+        self._lib.oracle_set_vcycle_bf16(self._h, 1 if on else 0)
+
+    def pcg(self, f, u0=None, rtol: float = 1e-5, max_iter: int = 100, flexible: bool = False) -> dict:
+        """Preconditioned CG; flexible=True uses the Polak-Ribiere coefficient."""
         f = _f64(f).reshape(-1)
         u = np.zeros_like(f) if u0 is None else _f64(u0).reshape(-1).copy()
         iters = ctypes.c_int(0)
         rel = ctypes.c_double(0.0)
         true_rel = ctypes.c_double(0.0)
         hist = np.zeros(max_iter + 1)
-        status = self._lib.oracle_pcg(self._h, _ptr(f), _ptr(u), rtol, max_iter, ctypes.byref(iters),
-                                      ctypes.byref(rel), _ptr(hist), ctypes.byref(true_rel))
+        fn = self._lib.oracle_fcg if flexible else self._lib.oracle_pcg
+        status = fn(self._h, _ptr(f), _ptr(u), rtol, max_iter, ctypes.byref(iters),
+                    ctypes.byref(rel), _ptr(hist), ctypes.byref(true_rel))
         return dict(u=u, iters=iters.value, rel_resid=rel.value, true_rel=true_rel.value,
                     hist=hist[:iters.value + 1].copy(), status=status)
 

@@ -362,6 +362,8 @@ typedef struct {
     double H, grading, omega2, h_min;
     int nu_pre, nu_post, nu_coarse, smoother; /* smoother: 0 multicolour block-SOR, 1 block-Jacobi */
     int centre_kind;                          /* 0 circumcentre, 1 normalised vertex mean */
+    int vc_bf16;          /* V-cycle of the mixed-precision form: BF16-rounded coefficients */
+    int bf16_now;         /* set while such a V-cycle runs                         */
     double relax;
     ogrid *grid;          /* [L+1] refinement levels 0..L                     */
     /* vertical grid (Appendix A), faces k = 0..n_r                           */
@@ -382,14 +384,29 @@ static const ogrid *mg_grid(const octx *o, int l) { return &o->grid[o->L - (o->n
  * alphaS_hat_{TT',k}    = omega^2 (r_{k+1} - r_k) g_TT'
  * alphar_hat_{T,k}      = omega^2 sigma_k |T| 2 r_k^2 / (r_{k+1} - r_{k-1})   (face k)
  * Reading C2: a single factor omega^2 in the horizontal term. */
-static double beta_hat(const octx *o, const ogrid *G, int T, int k) { return G->area[T] * o->vol[k]; }
+/* x rounded to the nearest bfloat16 value (8 significant bits, the exponent
+ * range of binary32), ties to the even significand.  x = m 2^e with
+ * m in [0.5, 1): m 2^8 is rounded to an integer by rint (round-half-even in
+ * the default rounding mode) and scaled back.  For finite normal-range x. */
+double oracle_bf16(double x)
+{
+    int e;
+    double m;
+    if (x == 0.0 || !isfinite(x)) return x;
+    m = frexp(x, &e);
+    return ldexp(rint(ldexp(m, 8)), e - 8);
+}
+
+static double coeff(const octx *o, double v) { return o->bf16_now ? oracle_bf16(v) : v; }
+
+static double beta_hat(const octx *o, const ogrid *G, int T, int k) { return coeff(o, G->area[T] * o->vol[k]); }
 static double alphaS_hat(const octx *o, const ogrid *G, int T, int e, int k)
 {
-    return o->omega2 * o->dr[k] * G->g[3 * T + e];
+    return coeff(o, o->omega2 * o->dr[k] * G->g[3 * T + e]);
 }
 static double alphar_hat(const octx *o, const ogrid *G, int T, int face)
 {
-    return o->omega2 * G->area[T] * o->arv[face];
+    return coeff(o, o->omega2 * G->area[T] * o->arv[face]);
 }
 
 /* Column T of the operator as a tridiagonal matrix (eq. ColumnEquation,
@@ -834,15 +851,23 @@ int oracle_prolong_add(void *h, int l_fine, const double *uc, double *uf)
     return 0;
 }
 
-/* One V-cycle on the finest level from a zero initial guess: z = B r. */
+/* One V-cycle on the finest level from a zero initial guess: z = B r.  With
+ * vc_bf16 set, every hat coefficient the V-cycle uses (operator, column
+ * blocks, coarse levels) is rounded to bfloat16 first: the preconditioner of
+ * the mixed-precision form, here in FP64 arithmetic. */
 int oracle_vcycle(void *h, const double *r, double *z)
 {
     octx *o = (octx *)h;
     int l = o->n_levels - 1;
     memset(z, 0, (size_t)mg_grid(o, l)->n_cells * o->n_r * sizeof(double));
+    o->bf16_now = o->vc_bf16;
     vcycle_level(o, l, r, z);
+    o->bf16_now = 0;
     return 0;
 }
+
+/* Select the V-cycle of the mixed-precision form (on != 0) or the plain one. */
+void oracle_set_vcycle_bf16(void *h, int on) { ((octx *)h)->vc_bf16 = on != 0; }
 
 static double dot(size_t N, const double *a, const double *b)
 {
@@ -898,6 +923,64 @@ int oracle_pcg(void *h, const double *f, double *u, double rtol, int max_iter, i
         oracle_vcycle(h, r, z);
         rz_new = dot(N, r, z);
         beta = rz_new / rz;
+        rz = rz_new;
+        for (i = 0; i < N; ++i) p[i] = z[i] + beta * p[i];
+    }
+done:
+    if (true_rel) {
+        apply_level(o, lf, u, q);
+        for (i = 0; i < N; ++i) q[i] = f[i] - q[i];
+        *true_rel = rnorm0 > 0.0 ? sqrt(dot(N, q, q)) / rnorm0 : 0.0;
+    }
+    free(r); free(z); free(p); free(q);
+    return status;
+}
+
+/* Flexible conjugate gradients for a preconditioner that is not exactly
+ * symmetric (the FP32 / BF16 V-cycle of the mixed-precision form): as
+ * oracle_pcg, but with the Polak-Ribiere coefficient
+ *     beta_k = <r_{k+1}, z_{k+1} - z_k> / <r_k, z_k>,
+ * which equals the Fletcher-Reeves coefficient of plain PCG when B is
+ * symmetric (then <r_{k+1}, z_k> = 0).  Same stopping rule, counts and returns. */
+int oracle_fcg(void *h, const double *f, double *u, double rtol, int max_iter, int *iters, double *rel_resid,
+               double *hist, double *true_rel)
+{
+    octx *o = (octx *)h;
+    int lf = o->n_levels - 1, it, status = 1;
+    size_t N = (size_t)mg_grid(o, lf)->n_cells * o->n_r, i;
+    double *r = (double *)malloc(N * sizeof(double));
+    double *z = (double *)malloc(N * sizeof(double));
+    double *p = (double *)malloc(N * sizeof(double));
+    double *q = (double *)malloc(N * sizeof(double));
+    double rz, rnorm0, rnorm;
+    if (!r || !z || !p || !q) { free(r); free(z); free(p); free(q); return -2; }
+    apply_level(o, lf, u, q);
+    for (i = 0; i < N; ++i) r[i] = f[i] - q[i];
+    rnorm0 = sqrt(dot(N, r, r));
+    *iters = 0;
+    *rel_resid = 1.0;
+    if (hist) hist[0] = 1.0;
+    if (!isfinite(rnorm0)) { status = -3; goto done; }
+    if (rnorm0 == 0.0) { *rel_resid = 0.0; status = 0; goto done; }
+    oracle_vcycle(h, r, z);
+    memcpy(p, z, N * sizeof(double));
+    rz = dot(N, r, z);
+    for (it = 0; it < max_iter; ++it) {
+        double pq, alpha, rz_old_new, rz_new, beta;
+        apply_level(o, lf, p, q);
+        pq = dot(N, p, q);
+        if (!(pq > 0.0) || !isfinite(pq)) { status = -3; break; }
+        alpha = rz / pq;
+        for (i = 0; i < N; ++i) { u[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
+        rnorm = sqrt(dot(N, r, r));
+        *iters = it + 1;
+        *rel_resid = rnorm / rnorm0;
+        if (hist) hist[it + 1] = *rel_resid;
+        if (rnorm <= rtol * rnorm0) { status = 0; break; }
+        rz_old_new = dot(N, r, z);          /* <r_{k+1}, z_k> before z is overwritten */
+        oracle_vcycle(h, r, z);
+        rz_new = dot(N, r, z);
+        beta = (rz_new - rz_old_new) / rz;
         rz = rz_new;
         for (i = 0; i < N; ++i) p[i] = z[i] + beta * p[i];
     }

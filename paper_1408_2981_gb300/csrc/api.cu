@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <new>
 #include <string>
@@ -106,9 +107,13 @@ bool validate(const tpmg_params *p, std::string &msg)
     }
     if (p->smoother != TPMG_SMOOTH_MCSOR && p->smoother != TPMG_SMOOTH_JACOBI) { msg = "unknown smoother"; return false; }
     if (!(p->relax > 0.0 && p->relax < 2.0)) { msg = "relax must be in (0, 2)"; return false; }
-    if (p->coeff_storage != TPMG_COEFF_FACTORISED) { msg = "only factorised coefficient storage is built"; return false; }
+    if (p->coeff_storage != TPMG_COEFF_FACTORISED && p->coeff_storage != TPMG_COEFF_FULL) { msg = "unknown coefficient storage"; return false; }
     if (p->centre != TPMG_CENTRE_CIRCUM && p->centre != TPMG_CENTRE_VERTEX_MEAN) { msg = "unknown centre kind"; return false; }
-    if (p->precision != TPMG_PREC_FP64) { msg = "only FP64 precision is built"; return false; }
+    if (p->precision != TPMG_PREC_FP64 && p->precision != TPMG_PREC_MIXED) { msg = "unknown precision"; return false; }
+    if ((p->precision == TPMG_PREC_MIXED) != (p->coeff_storage == TPMG_COEFF_FULL)) {
+        msg = "the FP64 V-cycle uses factorised storage, the mixed-precision V-cycle full BF16 storage";
+        return false;
+    }
     if (p->graphs != 0 && p->graphs != 1) { msg = "graphs must be 0 or 1"; return false; }
     return true;
 }
@@ -254,10 +259,120 @@ tpmg_status vcycle_level(tpmg_ctx *ctx, int l, const double *f, double *u, doubl
     return TPMG_OK;
 }
 
+// The bfloat16 bits of the value nearest to x (8 significant bits, ties to the
+// even significand), for finite x in the binary32 range: the 45 low
+// significand bits of the double are rounded away in integer arithmetic, and
+// the result, exact in binary32, gives its upper 16 bits.
+unsigned short bf16_bits(double x)
+{
+    uint64_t b;
+    std::memcpy(&b, &x, sizeof b);
+    const uint64_t lsb = (b >> 45) & 1u;
+    b += (((uint64_t)1 << 44) - 1) + lsb;
+    b &= ~(((uint64_t)1 << 45) - 1);
+    double r;
+    std::memcpy(&r, &b, sizeof r);
+    const float f = (float)r;
+    uint32_t fb;
+    std::memcpy(&fb, &f, sizeof fb);
+    return (unsigned short)(fb >> 16);
+}
+
+// Algorithm 1 in the mixed-precision form on level l: u = V-cycle(f), FP32
+// arithmetic on the BF16 stencil.  TF is double on the finest level (the
+// FP64 residual of the outer Krylov loop is read directly) and float below.
+// As in vcycle_level, a coarse level adds its result into the 4 children in
+// u_fine in the pass that writes each column's final value; the finest level
+// writes its final values also as double into z64.
+template <typename TF>
+tpmg_status vcycle_mixed(tpmg_ctx *ctx, int l, const TF *f, float *u, float *scratch, float *u_fine, double *z64)
+{
+    const Launch L = launch_of(ctx);
+    const tpmg_params &p = ctx->p;
+    const LevelDev &lv = ctx->lv[l];
+    const int C = lv.n_colours;
+    const bool jac = p.smoother == TPMG_SMOOTH_JACOBI;
+    const float relax = (float)p.relax;
+    const double nunits = (double)lv.n * p.n_r;
+    const size_t nbytes = sizeof(float) * lv.n * p.n_r;
+    float *cur = u, *oth = scratch;
+    auto pass = [&](int c, int mode, float *fine, double *out) -> cudaError_t {
+        const int t0 = lv.colour_task_off[c], nt = lv.colour_task_off[c + 1] - t0;
+        const int m = (mode == PASS_ZERO && c == 0) ? PASS_RHS_ONLY : mode;
+        return run(ctx, TPMG_K_RELAX, (double)lv.colour_cells[c] * p.n_r,
+                   [&] { return launch_relax32<TF>(L, lv, m, t0, nt, relax, f, u, u, fine, out); });
+    };
+    auto jacobi = [&](int mode, float *fine, double *out) -> cudaError_t {
+        const int m = mode == PASS_ZERO ? PASS_RHS_ONLY : mode;
+        cudaError_t e = run(ctx, TPMG_K_RELAX, nunits, [&] {
+            return launch_relax32<TF>(L, lv, m, 0, lv.n_tasks, relax, f, cur, oth, fine, out);
+        });
+        std::swap(cur, oth);
+        return e;
+    };
+    auto clear = [&](float *x) -> cudaError_t {
+        return run(ctx, TPMG_K_COPY, nunits, [&] { return cudaMemsetAsync(x, 0, nbytes, ctx->issue); });
+    };
+    if (l == 0) {
+        if (p.nu_coarse == 0) {
+            LCHK(clear(u));
+            if (z64) LCHK(run(ctx, TPMG_K_COPY, nunits, [&] { return launch_to_f64(L, (long)lv.n * p.n_r, u, z64); }));
+        }
+        for (int s = 0; s < p.nu_coarse; ++s) {
+            const bool last = s == p.nu_coarse - 1;
+            if (jac) {
+                LCHK(jacobi(s == 0 ? PASS_ZERO : PASS_NORMAL, last ? u_fine : nullptr, last ? z64 : nullptr));
+                continue;
+            }
+            for (int c = 0; c < C; ++c) {
+                const bool fin = last && c == C - 1;
+                LCHK(pass(c, s == 0 ? PASS_ZERO : PASS_NORMAL, fin ? u_fine : nullptr, fin ? z64 : nullptr));
+            }
+            for (int c = C - 2; c >= 0; --c)
+                LCHK(pass(c, PASS_NORMAL, last ? u_fine : nullptr, last ? z64 : nullptr));
+        }
+        return TPMG_OK;
+    }
+    if (p.nu_pre == 0) LCHK(clear(cur));
+    for (int s = 0; s < p.nu_pre; ++s) {
+        if (jac) {
+            LCHK(jacobi(s == 0 ? PASS_ZERO : PASS_NORMAL, nullptr, nullptr));
+            continue;
+        }
+        for (int c = 0; c < C; ++c) LCHK(pass(c, s == 0 ? PASS_ZERO : PASS_NORMAL, nullptr, nullptr));
+    }
+    LevelDev &co = ctx->lv[l - 1];
+    const float *uc = cur;
+    LCHK(run(ctx, TPMG_K_RESTRICT, nunits,
+             [&] { return launch_resid_restrict32<TF>(L, lv, co, f, uc, co.f32); }));
+    tpmg_status st = vcycle_mixed<float>(ctx, l - 1, co.f32, co.u32, co.u2_32, cur, nullptr);
+    if (st != TPMG_OK) return st;
+    for (int s = 0; s < p.nu_post; ++s) {
+        const bool last = s == p.nu_post - 1;
+        if (jac) {
+            LCHK(jacobi(PASS_NORMAL, last ? u_fine : nullptr, last ? z64 : nullptr));
+            continue;
+        }
+        for (int c = C - 1; c >= 0; --c) LCHK(pass(c, PASS_NORMAL, last ? u_fine : nullptr, last ? z64 : nullptr));
+    }
+    if (p.nu_post == 0) {
+        const float *cc = cur;
+        if (u_fine) {
+            const LevelDev &fl = ctx->lv[l + 1];
+            LCHK(run(ctx, TPMG_K_PROLONG, (double)fl.n * p.n_r,
+                     [&] { return launch_prolong_add32(L, fl, cc, u_fine); }));
+        }
+        if (z64) LCHK(run(ctx, TPMG_K_COPY, nunits, [&] { return launch_to_f64(L, (long)lv.n * p.n_r, cc, z64); }));
+    }
+    return TPMG_OK;
+}
+
 tpmg_status vcycle_fine(tpmg_ctx *ctx, const double *r, double *z)
 {
     const int l = ctx->p.n_levels - 1;
-    return vcycle_level(ctx, l, r, z, ctx->lv[l].u2, nullptr);
+    LevelDev &fl = ctx->lv[l];
+    if (ctx->p.precision == TPMG_PREC_MIXED) return vcycle_mixed<double>(ctx, l, r, fl.u32, fl.u2_32, nullptr, z);
+    return vcycle_level(ctx, l, r, z, fl.u2, nullptr);
 }
 
 void drop_graph(tpmg_ctx *ctx)
@@ -323,6 +438,8 @@ tpmg_status pcg(tpmg_ctx *ctx, const double *f, double *u, double rtol, int max_
     LevelDev &fl = ctx->lv[ctx->p.n_levels - 1];
     const long N = ctx->N;
     const int np = ctx->n_part;
+    // the FP32 V-cycle is not exactly symmetric: Polak-Ribiere coefficient (flexible CG)
+    const bool flexible = ctx->p.precision == TPMG_PREC_MIXED;
     *iters = 0;
     *rel = 1.0;
     LCHK(run(ctx, TPMG_K_RESIDUAL, (double)N, [&] { return launch_residual(L, fl, ctx->vert, f, u, ctx->r, ctx->partials, np); }));
@@ -340,8 +457,11 @@ tpmg_status pcg(tpmg_ctx *ctx, const double *f, double *u, double rtol, int max_
     for (int it = 0; it < max_iter; ++it) {
         LCHK(run(ctx, TPMG_K_APPLY, (double)N, [&] { return launch_apply(L, fl, ctx->vert, ctx->pv, ctx->q, ctx->partials, np); }));
         LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_ALPHA, ctx->partials, np, ctx->sc); }));
-        LCHK(run(ctx, TPMG_K_AXPY, (double)N, [&] { return launch_axpy_pair(L, N, ctx->sc, ctx->pv, ctx->q, u, ctx->r, ctx->partials, np); }));
+        // flexible CG (mixed precision): the axpy also forms <r_new, z_old>
+        const double *z_old = flexible ? ctx->z : nullptr;
+        LCHK(run(ctx, TPMG_K_AXPY, (double)N, [&] { return launch_axpy_pair(L, N, ctx->sc, ctx->pv, ctx->q, u, ctx->r, ctx->partials, np, z_old); }));
         LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_RR, ctx->partials, np, ctx->sc); }));
+        if (flexible) LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_RZC, ctx->partials + np, np, ctx->sc); }));
         if ((st = read_scalars(ctx)) != TPMG_OK) return st;
         const Scalars &s = *ctx->h_sc;
         if (s.flag & 1) return fail(ctx, TPMG_ERR_BREAKDOWN, "p.Ap <= 0: operator or preconditioner not SPD");
@@ -353,7 +473,7 @@ tpmg_status pcg(tpmg_ctx *ctx, const double *f, double *u, double rtol, int max_
         if (it + 1 == max_iter) break;
         if ((st = vcycle_pcg(ctx)) != TPMG_OK) return st;
         LCHK(run(ctx, TPMG_K_DOT, (double)N, [&] { return launch_dot(L, N, ctx->r, ctx->z, ctx->partials, np); }));
-        LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_BETA, ctx->partials, np, ctx->sc); }));
+        LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, flexible ? FIN_BETA_PR : FIN_BETA, ctx->partials, np, ctx->sc); }));
         LCHK(run(ctx, TPMG_K_XPBY, (double)N, [&] { return launch_xpby(L, N, ctx->sc, ctx->z, ctx->pv); }));
     }
     return fail(ctx, TPMG_ERR_NOT_CONVERGED, "max_iter reached before rtol");
@@ -402,14 +522,43 @@ tpmg_status upload_level(tpmg_ctx *ctx, int l)
     CU(dalloc(ctx, &D.task_cells, tasks.size()));
     CU(dalloc(ctx, &D.task_nbr, tasks.size()));
     CU(dalloc(ctx, &D.task_g, tasks.size()));
-    CU(dalloc(ctx, &D.rinv, nn));
-    CU(dalloc(ctx, &D.fb, nf));
-    CU(dalloc(ctx, &D.fc, nf));
-    CU(dalloc(ctx, &D.fm, (size_t)D.n_tasks * 2 * kRelaxCols));
-    CU(dalloc(ctx, &D.u2, nn));
-    if (l < p.n_levels - 1) {
-        CU(dalloc(ctx, &D.f, nn));
-        CU(dalloc(ctx, &D.u, nn));
+    const bool mixed = p.precision == TPMG_PREC_MIXED;
+    if (!mixed) {
+        CU(dalloc(ctx, &D.rinv, nn));
+        CU(dalloc(ctx, &D.fb, nf));
+        CU(dalloc(ctx, &D.fc, nf));
+        CU(dalloc(ctx, &D.fm, (size_t)D.n_tasks * 2 * kRelaxCols));
+        CU(dalloc(ctx, &D.u2, nn));
+        if (l < p.n_levels - 1) {
+            CU(dalloc(ctx, &D.f, nn));
+            CU(dalloc(ctx, &D.u, nn));
+        }
+    } else {
+        // BF16 stencil, full storage: per (T, k) alphaS_hat of the 3 edges and beta_hat,
+        // and alphar_hat of face k (Appendix A, eq. hatFunctionsNonFac, constant profiles)
+        const HostGrid &G = ctx->host;
+        std::vector<bf16x4> cp(nn);
+        std::vector<unsigned short> cv(nn);
+        for (int T = 0; T < H.n; ++T)
+            for (int k = 0; k < p.n_r; ++k) {
+                const size_t i = (size_t)T * p.n_r + k;
+                const double hr = G.omega2 * G.dr[k];
+                cp[i] = bf16x4{bf16_bits(hr * H.g[3 * T]), bf16_bits(hr * H.g[3 * T + 1]),
+                               bf16_bits(hr * H.g[3 * T + 2]), bf16_bits(H.area[T] * G.vol[k])};
+                cv[i] = bf16_bits(G.omega2 * H.area[T] * G.face[k]);
+            }
+        CU(dalloc(ctx, &D.cpack, nn));
+        CU(dalloc(ctx, &D.cvert, nn));
+        CU(dalloc(ctx, &D.rinv32, nn));
+        CU(dalloc(ctx, &D.fb32, nf));
+        CU(dalloc(ctx, &D.fc32, nf));
+        CU(dalloc(ctx, &D.fm32, (size_t)D.n_tasks * 2 * kRelaxCols));
+        CU(dalloc(ctx, &D.u32, nn));
+        CU(dalloc(ctx, &D.u2_32, nn));
+        if (l < p.n_levels - 1) CU(dalloc(ctx, &D.f32, nn));
+        CU(cudaMemcpyAsync(D.cpack, cp.data(), nn * sizeof(bf16x4), cudaMemcpyHostToDevice, ctx->stream));
+        CU(cudaMemcpyAsync(D.cvert, cv.data(), nn * sizeof(unsigned short), cudaMemcpyHostToDevice, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));   // cp, cv are local
     }
     CU(cudaMemcpyAsync(D.nbr, nb.data(), n * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(D.g, g.data(), n * sizeof(dbl4), cudaMemcpyHostToDevice, ctx->stream));
@@ -421,7 +570,8 @@ tpmg_status upload_level(tpmg_ctx *ctx, int l)
         if (tasks[q] >= 0) { tnb[q] = nb[tasks[q]]; tg[q] = g[tasks[q]]; }
     CU(cudaMemcpyAsync(D.task_nbr, tnb.data(), tnb.size() * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(D.task_g, tg.data(), tg.size() * sizeof(dbl4), cudaMemcpyHostToDevice, ctx->stream));
-    CU(launch_twisted_factors(launch_of(ctx), D, ctx->vert));
+    if (!mixed) CU(launch_twisted_factors(launch_of(ctx), D, ctx->vert));
+    else CU(launch_twisted_factors32(launch_of(ctx), D));
     // the host vectors above must outlive the asynchronous copies
     CU(cudaStreamSynchronize(ctx->stream));
     return TPMG_OK;
@@ -505,7 +655,7 @@ tpmg_status tpmg_setup(const tpmg_params *params, void *cuda_stream, tpmg_ctx **
     if (dalloc(ctx, &ctx->r, ctx->N) != cudaSuccess || dalloc(ctx, &ctx->z, ctx->N) != cudaSuccess ||
         dalloc(ctx, &ctx->pv, ctx->N) != cudaSuccess || dalloc(ctx, &ctx->q, ctx->N) != cudaSuccess ||
         dalloc(ctx, &ctx->hf, ctx->N) != cudaSuccess || dalloc(ctx, &ctx->hu, ctx->N) != cudaSuccess ||
-        dalloc(ctx, &ctx->partials, ctx->n_part) != cudaSuccess || dalloc(ctx, &ctx->sc, 1) != cudaSuccess)
+        dalloc(ctx, &ctx->partials, 2 * (size_t)ctx->n_part) != cudaSuccess || dalloc(ctx, &ctx->sc, 1) != cudaSuccess)
         return bail(TPMG_ERR_OOM);
     if (cudaMallocHost(&ctx->h_sc, sizeof(Scalars)) != cudaSuccess) return bail(TPMG_ERR_OOM);
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return bail(TPMG_ERR_CUDA);
@@ -538,6 +688,8 @@ tpmg_status tpmg_vcycle_noalloc(tpmg_ctx *ctx, const double *d_r, double *d_z)
 {
     if (!ctx || !d_r || !d_z) return fail(ctx, TPMG_ERR_INVALID_ARG, "NULL argument");
     if (d_r == d_z) return fail(ctx, TPMG_ERR_INVALID_ARG, "r and z must not overlap");
+    if (ctx->p.precision != TPMG_PREC_FP64)
+        return fail(ctx, TPMG_ERR_INVALID_ARG, "the fixed-scratch V-cycle is built for FP64 precision only");
     const int L = ctx->p.n_levels;
     const bool jac = ctx->p.smoother == TPMG_SMOOTH_JACOBI;
     auto padded = [&](int l) { return ((size_t)ctx->lv[l].n * ctx->p.n_r + 31) & ~(size_t)31; };

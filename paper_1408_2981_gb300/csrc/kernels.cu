@@ -584,22 +584,25 @@ __global__ void __launch_bounds__(NT) k_dot(const double *__restrict__ a, const 
     if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
-// u += alpha p; r -= alpha q; partial ||r||^2
-template <int NT>
+// u += alpha p; r -= alpha q; partial ||r||^2.  With z_old (flexible CG) also
+// the partial <r_new, z_old> of the Polak-Ribiere coefficient, in partials[gridDim.x + block].
+template <int NT, bool CROSS>
 __global__ void __launch_bounds__(NT) k_axpy_pair(const Scalars *__restrict__ sc, const double *__restrict__ p,
                                                   const double *__restrict__ q, double *__restrict__ u,
-                                                  double *__restrict__ r, int N, double *__restrict__ partials)
+                                                  double *__restrict__ r, int N, double *__restrict__ partials,
+                                                  const double *__restrict__ z_old)
 {
     const double alpha = sc->alpha;
-    double acc = 0.0;
+    double acc = 0.0, accz = 0.0;
     const int stride = gridDim.x * NT;
     int i = blockIdx.x * NT + threadIdx.x;
     for (; i + 3 * stride < N; i += 4 * stride) {
-        double pv[4], qv[4], uv[4], rv[4];
+        double pv[4], qv[4], uv[4], rv[4], zv[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int j = i + k * stride;
             pv[k] = p[j]; qv[k] = q[j]; uv[k] = u[j]; rv[k] = r[j];
+            if (CROSS) zv[k] = z_old[j];
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -608,6 +611,7 @@ __global__ void __launch_bounds__(NT) k_axpy_pair(const Scalars *__restrict__ sc
             const double x = fma(-alpha, qv[k], rv[k]);
             r[j] = x;
             acc = fma(x, x, acc);
+            if (CROSS) accz = fma(x, zv[k], accz);
         }
     }
     for (; i < N; i += stride) {
@@ -615,9 +619,15 @@ __global__ void __launch_bounds__(NT) k_axpy_pair(const Scalars *__restrict__ sc
         const double x = fma(-alpha, q[i], r[i]);
         r[i] = x;
         acc = fma(x, x, acc);
+        if (CROSS) accz = fma(x, z_old[i], accz);
     }
     acc = block_sum<NT>(acc);
     if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+    if (CROSS) {
+        __syncthreads();   // block_sum's shared scratch is reused
+        accz = block_sum<NT>(accz);
+        if (threadIdx.x == 0) partials[gridDim.x + blockIdx.x] = accz;
+    }
 }
 
 // p = z + beta p
@@ -671,6 +681,15 @@ __global__ void __launch_bounds__(256) k_finish(int what, const double *__restri
     case FIN_BETA:
         sc->rz_new = v;
         sc->beta = v / sc->rz;
+        sc->rz = v;
+        if (!isfinite(v)) sc->flag |= 2;
+        break;
+    case FIN_RZC:
+        sc->rzc = v;
+        break;
+    case FIN_BETA_PR:   // flexible CG: beta = (<r, z_new> - <r, z_old>) / <r_old, z_old>
+        sc->rz_new = v;
+        sc->beta = (v - sc->rzc) / sc->rz;
         sc->rz = v;
         if (!isfinite(v)) sc->flag |= 2;
         break;
@@ -792,9 +811,12 @@ cudaError_t launch_finish(const Launch &L, int what, const double *partials, int
 }
 
 cudaError_t launch_axpy_pair(const Launch &L, long n, const Scalars *sc, const double *p, const double *q, double *u,
-                             double *r, double *partials, int n_part)
+                             double *r, double *partials, int n_part, const double *z_old)
 {
-    k_axpy_pair<kThreads><<<n_part, kThreads, 0, L.s>>>(sc, p, q, u, r, (int)n, partials);
+    if (z_old)
+        k_axpy_pair<kThreads, true><<<n_part, kThreads, 0, L.s>>>(sc, p, q, u, r, (int)n, partials, z_old);
+    else
+        k_axpy_pair<kThreads, false><<<n_part, kThreads, 0, L.s>>>(sc, p, q, u, r, (int)n, partials, nullptr);
     return cudaGetLastError();
 }
 

@@ -45,11 +45,13 @@ bool build_host_grid(const tpmg_params &p, HostGrid &grid, std::string &err);
 struct alignas(32) dbl4 {   // four doubles, one 32-byte load
     double x, y, z, w;
 };
+struct alignas(8) bf16x4 {   // four bfloat16 values (raw bits), one 8-byte load
+    unsigned short x, y, z, w;
+};
 struct VertDev {            // vertical factors shared by every level (no vertical coarsening)
     const double *vol;      // [n_r]   v_k = (r_{k+1}^3 - r_k^3)/3
     const double *w;        // [n_r+1] omega^2 sigma_k 2 r_k^2 / (r_{k+1} - r_{k-1})
     const double *hr;       // [n_r]   omega^2 (r_{k+1} - r_k)
-    const float *vol32, *w32, *hr32;  // FP32 copies for the mixed-precision V-cycle
 };
 
 // Line relaxation works on tasks of kRelaxCols columns of one colour (the
@@ -84,10 +86,13 @@ struct LevelDev {
     double *rinv = nullptr, *fb = nullptr, *fc = nullptr, *fm = nullptr;
     // workspaces (coarse levels; the finest level uses caller / PCG buffers)
     double *f = nullptr, *u = nullptr, *u2 = nullptr;
-    // mixed precision copies
+    // mixed-precision form: the stencil stored per unknown in BF16 (full
+    // storage, Sec. 4.2) and FP32 work vectors on every level
+    bf16x4 *cpack = nullptr;        // [n][n_r] {alphaS_hat e = 0, 1, 2, beta_hat}
+    unsigned short *cvert = nullptr;   // [n][n_r] alphar_hat of face k (coupling to level k-1)
+    // twisted Thomas factors of the BF16 column blocks in FP32, laid out as rinv / fb / fc / fm
+    float *rinv32 = nullptr, *fb32 = nullptr, *fc32 = nullptr, *fm32 = nullptr;
     float *f32 = nullptr, *u32 = nullptr, *u2_32 = nullptr;
-    float4 *g32 = nullptr;
-    float *area32 = nullptr;
 };
 
 struct Scalars {            // PCG scalars kept in device memory
@@ -97,6 +102,7 @@ struct Scalars {            // PCG scalars kept in device memory
     double rr;              // ||r||^2
     double rr0;             // ||r_0||^2
     double rz_new;
+    double rzc;             // <r_{k+1}, z_k> (flexible CG)
     int flag;               // bit 0: p.Ap <= 0 or non-finite; bit 1: non-finite residual
     int pad;
 };
@@ -128,10 +134,22 @@ cudaError_t launch_relax(const Launch &L, const LevelDev &lv, const VertDev &v, 
                          double relax, const double *f, const double *u_in, double *u_out, double *u_fine);
 cudaError_t launch_prolong_add(const Launch &L, const LevelDev &fine, const double *uc, double *u);
 cudaError_t launch_twisted_factors(const Launch &L, const LevelDev &lv, const VertDev &v);
+// Mixed-precision V-cycle (FP32 arithmetic, BF16 stencil).  TF is the type of
+// the right-hand side (double on the finest level, float below).
+template <typename TF>
+cudaError_t launch_relax32(const Launch &L, const LevelDev &lv, int mode, int task0, int n_tasks, float relax,
+                           const TF *f, const float *u_in, float *u_out, float *u_fine, double *out64);
+template <typename TF>
+cudaError_t launch_resid_restrict32(const Launch &L, const LevelDev &fine, const LevelDev &coarse, const TF *f,
+                                    const float *u, float *fc);
+cudaError_t launch_prolong_add32(const Launch &L, const LevelDev &fine, const float *uc, float *u);
+cudaError_t launch_to_f64(const Launch &L, long n, const float *x, double *y);
+cudaError_t launch_twisted_factors32(const Launch &L, const LevelDev &lv);
 cudaError_t launch_dot(const Launch &L, long n, const double *a, const double *b, double *partials, int n_part);
 cudaError_t launch_finish(const Launch &L, int what, const double *partials, int n_part, Scalars *sc);
+// z_old != NULL (flexible CG): also partials of <r_new, z_old> in partials[n_part..2 n_part)
 cudaError_t launch_axpy_pair(const Launch &L, long n, const Scalars *sc, const double *p, const double *q, double *u,
-                             double *r, double *partials, int n_part);
+                             double *r, double *partials, int n_part, const double *z_old);
 cudaError_t launch_xpby(const Launch &L, long n, const Scalars *sc, const double *z, double *p);
 
 // noalloc.cu: device address of the fixed scratch array of
@@ -139,6 +157,6 @@ cudaError_t launch_xpby(const Launch &L, long n, const Scalars *sc, const double
 // up once per device).
 cudaError_t noalloc_scratch(int device, double **ptr);
 
-enum FinishWhat { FIN_RR0 = 0, FIN_ALPHA = 1, FIN_RR = 2, FIN_BETA = 3, FIN_RZ0 = 4 };
+enum FinishWhat { FIN_RR0 = 0, FIN_ALPHA = 1, FIN_RR = 2, FIN_BETA = 3, FIN_RZ0 = 4, FIN_RZC = 5, FIN_BETA_PR = 6 };
 
 }  // namespace tpmg

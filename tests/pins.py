@@ -510,6 +510,74 @@ def pin_pcg_dense(ns):
         assert anorm(res["u"] - ud) <= floor, (anorm(res["u"] - ud) / anorm(ud), floor / anorm(ud))
 
 
+def pin_bf16_rounding(ns):
+    """The coefficients of the mixed-precision V-cycle are rounded to bfloat16:
+    the nearest number with an 8-bit significand (binary32 exponent range),
+    ties to the even significand.  Checked against that definition by brute
+    force: the two bfloat16 neighbours of x are built from its exponent, and the
+    result must be the nearer one (the even one on a tie)."""
+    rng = np.random.default_rng(21)
+    xs = list(rng.uniform(-1, 1, 400) * 10.0 ** rng.integers(-30, 30, 400))
+    xs += [1.0 + 2.0 ** -9, 1.0 + 3 * 2.0 ** -9, -(1.0 + 2.0 ** -9), 255.5 / 128, 1.0, 0.0, 3.0e-12, 1.0 / 3.0]
+    for x in xs:
+        y = ns.bf16(x)
+        if x == 0.0:
+            assert y == 0.0
+            continue
+        e = math.floor(math.log2(abs(x)))
+        if 2.0 ** e > abs(x):   # guard log2 rounding at powers of two
+            e -= 1
+        ulp = 2.0 ** (e - 7)
+        lo = math.floor(abs(x) / ulp) * ulp
+        hi = lo + ulp
+        dlo, dhi = abs(x) - lo, hi - abs(x)
+        if dlo < dhi:
+            want = lo
+        elif dhi < dlo:
+            want = hi
+        else:
+            want = lo if round(lo / ulp) % 2 == 0 else hi
+        assert y == math.copysign(want, x), (x, y, want)
+
+
+def pin_flexible_cg(ns):
+    """Flexible CG (Polak-Ribiere coefficient) takes the iterates of plain PCG
+    when the preconditioner is symmetric, since then <r_{k+1}, z_k> = 0; with the
+    mixed-precision V-cycle (BF16 coefficients) it still reaches the dense direct
+    solution, because the outer residual uses the exact operator."""
+    kw = dict(refinement=2, n_levels=3, n_r=8, grading=1.05, H=0.1, courant_c=8.0)
+    o = ns.Oracle(**kw)
+    f = inputs.uniform_pm1(inputs.SEED_UNIFORM_SMALL + 2, o.size())
+    a = o.pcg(f, rtol=1e-10, max_iter=200)
+    b = o.pcg(f, rtol=1e-10, max_iter=200, flexible=True)
+    assert a["status"] == 0 and b["status"] == 0 and a["iters"] == b["iters"]
+    assert np.linalg.norm(a["u"] - b["u"]) <= 1e-12 * np.linalg.norm(a["u"])
+    o.set_vcycle_bf16(True)
+    c = o.pcg(f, rtol=1e-13, max_iter=300, flexible=True)
+    assert c["status"] == 0
+    A = o.dense_operator()
+    ud = sla.cho_solve(sla.cho_factor(A), f)
+    assert np.linalg.norm(c["u"] - ud) <= 1e-10 * np.linalg.norm(ud)
+
+
+def pin_bf16_vcycle(ns):
+    """The V-cycle with BF16-rounded coefficients is the V-cycle of a nearby
+    operator that is still symmetric (each edge coupling is rounded once and used
+    by both of its cells): <B x, y> = <x, B y> to rounding, <B x, x> > 0, and
+    B x differs from the plain V-cycle by a few times the BF16 rounding 2^-9."""
+    rng = np.random.default_rng(22)
+    o = ns.Oracle(refinement=3, n_levels=3, n_r=12, grading=1.05, courant_c=80.0)
+    x, y = rng.uniform(-1, 1, o.size()), rng.uniform(-1, 1, o.size())
+    bx_plain = o.vcycle(x)
+    o.set_vcycle_bf16(True)
+    bx, by = o.vcycle(x), o.vcycle(y)
+    assert abs(bx @ y - x @ by) <= 1e-12 * np.linalg.norm(bx) * np.linalg.norm(y)
+    assert bx @ x > 0
+    e = bx - bx_plain
+    assert math.sqrt(e @ o.apply(e)) <= 16 * 2.0 ** -9 * math.sqrt(bx_plain @ o.apply(bx_plain))
+    assert math.sqrt(e @ o.apply(e)) > 0
+
+
 def pin_manufactured(ns):
     """Manufactured solution: f = A u*, solve to rtol 1e-12, recover u* in the
     energy norm to 1e-9 (a residual drop of 1e-12 bounds the error by cond-weighted 1e-12)."""
@@ -550,5 +618,6 @@ ALL_PINS = [
     pin_mesh_counts, pin_mesh_areas, pin_level0_closed_forms, pin_mesh_topology, pin_vertical,
     pin_constants_in_kernel, pin_symmetric_spd, pin_kronecker, pin_horizontal_consistency,
     pin_vertical_consistency, pin_thomas, pin_column_solve_exact, pin_transfers, pin_vcycle_dense, pin_preconditioner_symmetric,
-    pin_invariant_subspaces, pin_pcg_dense, pin_manufactured, pin_robust_convergence,
+    pin_invariant_subspaces, pin_pcg_dense, pin_bf16_rounding, pin_flexible_cg, pin_bf16_vcycle,
+    pin_manufactured, pin_robust_convergence,
 ]

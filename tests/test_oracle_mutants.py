@@ -44,8 +44,9 @@ MUTANTS = {
                      "uf[(size_t)(4 * T + j) * n + k] += 0.5 * uc[(size_t)T * n + k];"),
     "correction_sign": ("uf[(size_t)(4 * T + j) * n + k] += uc[(size_t)T * n + k];",
                         "uf[(size_t)(4 * T + j) * n + k] -= uc[(size_t)T * n + k];"),
-    "horizontal_uses_volume": ("return o->omega2 * o->dr[k] * G->g[3 * T + e];",
-                               "return o->omega2 * o->vol[k] * G->g[3 * T + e];"),
+    "horizontal_uses_volume": ("return coeff(o, o->omega2 * o->dr[k] * G->g[3 * T + e]);",
+                               "return coeff(o, o->omega2 * o->vol[k] * G->g[3 * T + e]);"),
+    "bf16_truncates": ("return ldexp(rint(ldexp(m, 8)), e - 8);", "return ldexp(floor(ldexp(m, 8)), e - 8);"),
     "vertical_missing_r2": ("2.0 * o->r[k] * o->r[k] / (o->zeta[k + 1] - o->zeta[k - 1])",
                             "2.0 / (o->zeta[k + 1] - o->zeta[k - 1])"),
     "vertical_distance": ("2.0 * o->r[k] * o->r[k] / (o->zeta[k + 1] - o->zeta[k - 1])",
@@ -71,7 +72,8 @@ DRIVER = textwrap.dedent("""
     lib = sys.argv[1]
     ns = types.SimpleNamespace(Oracle=functools.partial(oracle.Oracle, lib_path=lib),
                                thomas=functools.partial(oracle.thomas, lib_path=lib),
-                               column_solve=functools.partial(oracle.column_solve, lib_path=lib))
+                               column_solve=functools.partial(oracle.column_solve, lib_path=lib),
+                               bf16=functools.partial(oracle.bf16, lib_path=lib))
     for p in pins.ALL_PINS:
         try:
             p(ns)
