@@ -12,7 +12,8 @@ manufactured solution u* = sum of 8 seeded low-order spherical harmonics x
 vertical cosines, f = A u*; 6 multigrid levels, 2/2 line-SOR sweeps, 1 coarse
 sweep; FP64 throughout.
 
-Other workloads (--workload): 1280x16 (the small parity case), 81920x64-mixed
+Other workloads (--workload): batch48 (48 uneven mixed-precision solves in one
+graph launch), 1280x16 (the small parity case), 81920x64-mixed
 (the same solve with the V-cycle in FP32 on a BF16 stencil and flexible CG in
 FP64), 327680x128-mixed (refinement 7 x 128 levels, 41.9M unknowns, mixed
 precision) and 327680x128 (the same grid in FP64).
@@ -32,6 +33,8 @@ import subprocess
 import sys
 import tempfile
 import time
+
+import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
@@ -68,7 +71,23 @@ WORKLOADS = {
         params=dict(refinement=7, n_levels=6, n_r=128, grading=1.05, courant_c=8.0, nu_pre=2, nu_post=2, nu_coarse=1),
         rhs="uniform", seed=2981003,
         text="as 327680x128-mixed, everything in FP64 (plain TPMG-PCG on the same grid)"),
+    "batch48": dict(
+        batch=48, seed=2981004,
+        text="48 independent solves in one graph launch: refinement drawn from {4,5,6}, vertical levels from "
+             "{32,64,128} graded 1.05, omega^2/h^2 log-uniform in [4,200], all seeded; RHS uniform[-1,1]; "
+             "V-cycle in FP32 on a BF16 stencil, outer flexible CG in FP64; 5-6 MG levels, nu 2/2/1, rtol 1e-5"),
 }
+
+
+def batch_problems(seed: int, n: int) -> list:
+    """The seeded parameter sets of the batched workload."""
+    from paper_1408_2981_gb300 import inputs
+
+    refs = inputs.randint(seed, n, 4, 6)
+    nrs = np.array([32, 64, 128])[inputs.randint(seed, n, 0, 2, offset=n)]
+    cs = np.exp(np.log(4.0) + (np.log(200.0) - np.log(4.0)) * inputs.uniform01(seed, n, offset=2 * n))
+    return [dict(refinement=int(r), n_levels=int(min(r, 5) + 1 if r < 6 else 6), n_r=int(k), grading=1.05,
+                 courant_c=float(c), nu_pre=2, nu_post=2, nu_coarse=1, **MIXED) for r, k, c in zip(refs, nrs, cs)]
 
 # Flops per unknown of each kernel class as written (FMA = 2 flops) and
 # algorithmic HBM bytes per unknown (each array streamed once), per precision
@@ -425,6 +444,92 @@ def run_tpmg(args, wl):
     return 0
 
 
+def run_batch(args, wl):
+    """The batched form: one step = one tpmg_batch run of all problems (device-side
+    loops, one graph launch).  value = unknowns of all problems / device time."""
+    import torch
+
+    from paper_1408_2981_gb300 import binding, build as _build, inputs
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    _build.build()
+    stream = torch.cuda.current_stream()
+    probs = batch_problems(wl["seed"], wl["batch"])
+    solvers = [binding.Solver(stream=stream, **kw) for kw in probs]
+    fs = [torch.from_numpy(inputs.uniform_pm1(wl["seed"] + 100 + j, s.N)).cuda() for j, s in enumerate(solvers)]
+    us = [torch.zeros_like(f) for f in fs]
+    N = sum(s.N for s in solvers)
+    batch = binding.Batch(solvers, fs, us, rtol=args.rtol, max_iter=200)
+    l2 = torch.cuda.get_device_properties(local).L2_cache_size
+    flush = torch.empty(max(2 * l2, 256 << 20) // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        for u in us:
+            u.zero_()
+        return batch.run(stream)
+
+    for _ in range(args.warmup):
+        step()
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches, iters = 0, None
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        evs[k][0].record(stream)
+        st, iters, rel, sts, nl = step()
+        evs[k][1].record(stream)
+        launches += nl
+        if st != binding.TPMG_OK:
+            raise RuntimeError(f"batch did not converge: statuses {sts.tolist()}")
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    local_ms = sum(a.elapsed_time(b) for a, b in evs)
+    value, t_ms = aggregate_value(N, args.steps, world, local_ms)
+
+    # end to end: right-hand sides from pinned host memory and solutions back, inside the timed region
+    f_host = [torch.empty(f.numel(), dtype=torch.float64, pin_memory=True).copy_(f) for f in fs]
+    u_host = [torch.empty(f.numel(), dtype=torch.float64, pin_memory=True) for f in fs]
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 5))
+    for _ in range(e2e_steps):
+        for f, fh in zip(fs, f_host):
+            f.copy_(fh, non_blocking=True)
+        step()
+        for u, uh in zip(us, u_host):
+            uh.copy_(u, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0), world)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": wl["text"], "n_unknowns": N, "problems": len(solvers),
+                           "parallelism": f"replicas{world}",
+                           "l2": "flushed between steps (write of 2x L2 outside the timed events)"},
+                "e2e": {"value": N * e2e_steps * world / (e2e_ms / 1e3), "unit": "unknowns/s",
+                        "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N},
+                "gpu_launches": launches, "roofline": None, "cpu_baseline": None, "clocks": clk,
+                "iters": [int(i) for i in iters],
+                "note": "the loops run on the device, so kernels carry no event pairs: no per-kernel roofline here"}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -441,7 +546,13 @@ def main(argv=None):
         ap.error("--warmup must be >= 1")
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
+        if "batch" in wl:
+            print(json.dumps({"impl": "reference", "unavailable": "the batched workload has no oracle arm: its "
+                              "problems are each an oracle solve of the single-problem workloads"}))
+            return 0
         return run_reference(args, wl)
+    if "batch" in wl:
+        return run_batch(args, wl)
     return run_tpmg(args, wl)
 
 

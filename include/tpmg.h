@@ -166,7 +166,10 @@ tpmg_status tpmg_vcycle_noalloc(tpmg_ctx *ctx, const double *d_r, double *d_z);
  * resid_hist (host, nullable, max_iter+1 doubles) receives ||r_k|| / ||r_0||
  * for k = 0..*iters.  Synchronises the context stream before returning.
  * Returns OK, NOT_CONVERGED (iters = max_iter), BREAKDOWN (p.Ap <= 0 or a
- * non-finite norm; the solution holds the last finite iterate), INVALID_ARG, CUDA. */
+ * non-finite norm; the solution holds the last finite iterate), INVALID_ARG, CUDA.
+ * With graphs on (and no kernel class being timed) the whole solve is one graph
+ * launch with the loop on the device; otherwise the host drives the loop.
+ * Both run the same kernels in the same order. */
 tpmg_status tpmg_solve(tpmg_ctx *ctx, const double *d_f, double *d_u, double rtol, int max_iter,
                        int *iters, double *rel_resid, double *resid_hist);
 
@@ -176,6 +179,31 @@ tpmg_status tpmg_solve(tpmg_ctx *ctx, const double *d_f, double *d_u, double rto
  * Same arguments and returns as tpmg_solve. */
 tpmg_status tpmg_solve_host(tpmg_ctx *ctx, const double *h_f, double *h_u, double rtol, int max_iter,
                             int *iters, double *rel_resid, double *resid_hist);
+
+/* Many independent solves in one graph launch (the batched form).  A batch
+ * holds one PCG solve (tpmg_solve's algorithm and arithmetic, rtol, max_iter)
+ * for each of n contexts -- of any sizes and parameters, on the current
+ * device -- with the loop of each solve on the device: the whole batch is a
+ * single CUDA graph in which every problem is an independent branch, so the
+ * problems' kernels overlap.  d_f[i], d_u[i]: device vectors of ctxs[i] as in
+ * tpmg_solve (d_u[i] = initial guess, overwritten by the solution); the
+ * pointers are baked into the batch, which stays valid while the contexts and
+ * vectors live.  A context may belong to one batch and must not run another
+ * solve while its batch runs.  max_iter < 4096.
+ * Errors: INVALID_ARG (NULL, repeated context, other device), OOM, CUDA. */
+typedef struct tpmg_batch tpmg_batch;
+tpmg_status tpmg_batch_create(tpmg_ctx *const *ctxs, int n, const double *const *d_f, double *const *d_u,
+                              double rtol, int max_iter, tpmg_batch **out);
+
+/* Runs the batch on cuda_stream and waits for it.  iters[i], rel_resid[i]
+ * (host, n entries) as tpmg_solve; status (nullable, n entries) per problem;
+ * kernel_launches (nullable) = kernels the run executed.  Returns OK when every
+ * problem converged, otherwise the first problem's non-OK status. */
+tpmg_status tpmg_batch_run(tpmg_batch *b, void *cuda_stream, int *iters, double *rel_resid, int *status,
+                           long long *kernel_launches);
+
+/* Releases the batch (not the contexts).  NULL is ignored. */
+void tpmg_batch_destroy(tpmg_batch *b);
 
 /* Sizes of multigrid level `level` (0 = coarsest, n_levels-1 = finest):
  * cells, vertical cells, omega^2 actually used, number of colours.  Any output

@@ -37,7 +37,8 @@ TPMG_PREC_MIXED = 1
 EXPORTS = ["tpmg_default_params", "tpmg_setup", "tpmg_apply_operator", "tpmg_vcycle", "tpmg_vcycle_noalloc",
            "tpmg_solve",
            "tpmg_solve_host", "tpmg_query", "tpmg_export_mesh", "tpmg_profile", "tpmg_profile_read",
-           "tpmg_status_string", "tpmg_last_error", "tpmg_destroy"]
+           "tpmg_status_string", "tpmg_last_error", "tpmg_destroy", "tpmg_batch_create", "tpmg_batch_run",
+           "tpmg_batch_destroy"]
 
 KERNEL_CLASSES = ["apply", "residual", "restrict", "relax", "prolong", "dot", "axpy", "xpby", "finish", "copy"]
 
@@ -89,8 +90,12 @@ def load(path: str | None = None):
     lib.tpmg_last_error.restype = ctypes.c_char_p
     lib.tpmg_destroy.argtypes = [P]
     lib.tpmg_destroy.restype = None
+    lib.tpmg_batch_create.argtypes = [P, I, P, P, D, I, ctypes.POINTER(P)]
+    lib.tpmg_batch_run.argtypes = [P, P, P, P, P, ctypes.POINTER(ctypes.c_longlong)]
+    lib.tpmg_batch_destroy.argtypes = [P]
+    lib.tpmg_batch_destroy.restype = None
     for name in EXPORTS:
-        if name not in ("tpmg_destroy", "tpmg_status_string", "tpmg_last_error"):
+        if name not in ("tpmg_destroy", "tpmg_status_string", "tpmg_last_error", "tpmg_batch_destroy"):
             getattr(lib, name).restype = I
     if path is None:
         _lib = lib
@@ -246,3 +251,52 @@ class Solver:
         if raise_on_fail and st != TPMG_OK:
             self._check(st, "tpmg_solve_host")
         return st, it.value, rel.value
+
+
+class Batch:
+    """tpmg_batch: one PCG solve per Solver in one graph launch.
+
+    ``solvers``, ``fs``, ``us``: equal-length lists; fs[i], us[i] are float64 CUDA
+    tensors of solvers[i] (us[i] = initial guess, overwritten by the solution).
+    The tensors must stay alive while the batch is used.
+    """
+
+    def __init__(self, solvers, fs, us, rtol: float = 1e-5, max_iter: int = 100):
+        if not (len(solvers) == len(fs) == len(us)) or not solvers:
+            raise ValueError("solvers, fs and us must be non-empty lists of equal length")
+        self._lib = load()
+        self.solvers, self.fs, self.us = list(solvers), list(fs), list(us)
+        n = len(solvers)
+        self.n = n
+        ctxs = (ctypes.c_void_p * n)(*[s._h.value for s in solvers])
+        fp = (ctypes.c_void_p * n)(*[s._vec(f, "f") for s, f in zip(solvers, fs)])
+        up = (ctypes.c_void_p * n)(*[s._vec(u, "u") for s, u in zip(solvers, us)])
+        h = ctypes.c_void_p()
+        st = self._lib.tpmg_batch_create(ctxs, n, fp, up, rtol, max_iter, ctypes.byref(h))
+        if st != TPMG_OK:
+            raise TPMGError(st, "tpmg_batch_create")
+        self._h = h
+
+    def run(self, stream=None):
+        """Returns (status, iters[n], rel_resid[n], status[n], kernel_launches)."""
+        import torch
+
+        stream = stream if stream is not None else torch.cuda.current_stream()
+        it = np.zeros(self.n, dtype=np.int32)
+        rel = np.zeros(self.n)
+        sts = np.zeros(self.n, dtype=np.int32)
+        launches = ctypes.c_longlong(0)
+        st = self._lib.tpmg_batch_run(self._h, ctypes.c_void_p(stream.cuda_stream), it.ctypes.data, rel.ctypes.data,
+                                      sts.ctypes.data, ctypes.byref(launches))
+        return st, it, rel, sts, launches.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.tpmg_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -43,6 +43,15 @@ struct tpmg_ctx {
     cudaStream_t cap_stream = nullptr;  // private stream on which graphs are captured
     bool capturing = false;
     GraphCache vc;
+    // whole solve as one graph (device-side loop), cached for one argument set
+    struct {
+        cudaGraphExec_t exec = nullptr;
+        const double *f = nullptr;
+        double *u = nullptr;
+        double rtol = 0.0;
+        int max_iter = -1;
+    } sg;
+    double *d_hist = nullptr;     // [kHistCap] residual history of the device-side loop
     int device = 0;
     int sm_count = 0;
     HostGrid host;
@@ -59,6 +68,14 @@ struct tpmg_ctx {
     Scalars *h_sc = nullptr;      // pinned host mirror
     std::vector<void *> allocs;   // every device allocation, freed by tpmg_destroy
     std::string err;
+};
+
+struct tpmg_batch {
+    std::vector<tpmg_ctx *> ctx;
+    std::vector<long long> init_launches, iter_launches;   // per problem
+    double rtol = 0.0;
+    int max_iter = 0;
+    cudaGraphExec_t exec = nullptr;
 };
 
 namespace {
@@ -379,6 +396,9 @@ void drop_graph(tpmg_ctx *ctx)
 {
     if (ctx->vc.exec) cudaGraphExecDestroy(ctx->vc.exec);
     ctx->vc = GraphCache{};
+    if (ctx->sg.exec) cudaGraphExecDestroy(ctx->sg.exec);
+    ctx->sg.exec = nullptr;
+    ctx->sg.max_iter = -1;
 }
 
 // z = B r on the PCG vectors of the context.  With graphs enabled the V-cycle
@@ -429,6 +449,147 @@ tpmg_status read_scalars(tpmg_ctx *ctx)
     CU(cudaMemcpyAsync(ctx->h_sc, ctx->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     return TPMG_OK;
+}
+
+constexpr int kHistCap = 4096;   // longest residual history of the device-side loop
+
+// Stream capture into an existing graph (after `deps`), launches issued on the
+// private stream; *leaves receives the capture's final nodes.
+template <class F>
+tpmg_status capture_into(tpmg_ctx *ctx, cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps,
+                         std::vector<cudaGraphNode_t> *leaves, F &&body)
+{
+    CU(cudaStreamBeginCaptureToGraph(ctx->cap_stream, g, deps, nullptr, ndeps, cudaStreamCaptureModeThreadLocal));
+    ctx->issue = ctx->cap_stream;
+    ctx->capturing = true;
+    tpmg_status st = body();
+    const cudaGraphNode_t *out = nullptr;
+    size_t nout = 0;
+    cudaStreamCaptureStatus cs;
+    const cudaError_t ei = cudaStreamGetCaptureInfo(ctx->cap_stream, &cs, nullptr, nullptr, &out, nullptr, &nout);
+    if (leaves && ei == cudaSuccess) leaves->assign(out, out + nout);
+    cudaGraph_t gout = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(ctx->cap_stream, &gout);
+    ctx->capturing = false;
+    ctx->issue = ctx->stream;
+    if (st != TPMG_OK) return st;
+    if (ei != cudaSuccess || ee != cudaSuccess)
+        return fail(ctx, TPMG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ei != cudaSuccess ? ei : ee));
+    return TPMG_OK;
+}
+
+// Appends one whole PCG solve of ctx to graph g (no dependencies: a root
+// branch): the initial residual, then a conditional WHILE node whose body is
+// one iteration, in the order
+//   z = B r;  beta (0 on the first pass, p cleared before the loop);  p = z + beta p;
+//   q = A p, alpha;  u += alpha p, r -= alpha q;  stop test,
+// which performs the arithmetic of the host-driven loop of pcg() step for step.
+// The finish kernels record the history in ctx->d_hist, count the iterations
+// in the device scalars and set the loop condition.  The launch counters of
+// the captured kernels are restored (a graph's launches are counted per run).
+tpmg_status append_solve(tpmg_ctx *ctx, cudaGraph_t g, const double *f, double *u, double rtol, int max_iter,
+                         long long *init_launches = nullptr, long long *iter_launches = nullptr)
+{
+    Tracer &t = ctx->tr;
+    long long l0[TPMG_K_COUNT];
+    double u0[TPMG_K_COUNT];
+    std::copy(t.launches, t.launches + TPMG_K_COUNT, l0);
+    std::copy(t.units, t.units + TPMG_K_COUNT, u0);
+    cudaGraphConditionalHandle h;
+    CU(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+    const LoopCtl loop{h, rtol, max_iter, ctx->d_hist};
+    LevelDev &fl = ctx->lv[ctx->p.n_levels - 1];
+    const long N = ctx->N;
+    const int np = ctx->n_part;
+    const bool flexible = ctx->p.precision == TPMG_PREC_MIXED;
+    std::vector<cudaGraphNode_t> leaves;
+    tpmg_status st = capture_into(ctx, g, nullptr, 0, &leaves, [&]() -> tpmg_status {
+        const Launch L = launch_of(ctx);
+        LCHK(run(ctx, TPMG_K_RESIDUAL, (double)N, [&] { return launch_residual(L, fl, ctx->vert, f, u, ctx->r, ctx->partials, np); }));
+        LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_LOOP_RR0, ctx->partials, np, ctx->sc, &loop); }));
+        LCHK(run(ctx, TPMG_K_COPY, (double)N, [&] { return cudaMemsetAsync(ctx->pv, 0, sizeof(double) * N, ctx->issue); }));
+        return TPMG_OK;
+    });
+    if (st != TPMG_OK) return st;
+    long long after_init = 0;
+    for (int c = 0; c < TPMG_K_COUNT; ++c) after_init += t.launches[c] - l0[c];
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    CU(cudaGraphAddNode(&node, g, leaves.data(), nullptr, leaves.size(), &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    st = capture_into(ctx, body, nullptr, 0, nullptr, [&]() -> tpmg_status {
+        const Launch L = launch_of(ctx);
+        tpmg_status s2 = vcycle_fine(ctx, ctx->r, ctx->z);
+        if (s2 != TPMG_OK) return s2;
+        LCHK(run(ctx, TPMG_K_DOT, (double)N, [&] { return launch_dot(L, N, ctx->r, ctx->z, ctx->partials, np); }));
+        LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] {
+            return launch_finish(L, flexible ? FIN_LOOP_BETA_PR : FIN_LOOP_BETA, ctx->partials, np, ctx->sc, &loop);
+        }));
+        LCHK(run(ctx, TPMG_K_XPBY, (double)N, [&] { return launch_xpby(L, N, ctx->sc, ctx->z, ctx->pv); }));
+        LCHK(run(ctx, TPMG_K_APPLY, (double)N, [&] { return launch_apply(L, fl, ctx->vert, ctx->pv, ctx->q, ctx->partials, np); }));
+        LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_ALPHA, ctx->partials, np, ctx->sc); }));
+        const double *z_old = flexible ? ctx->z : nullptr;
+        LCHK(run(ctx, TPMG_K_AXPY, (double)N, [&] { return launch_axpy_pair(L, N, ctx->sc, ctx->pv, ctx->q, u, ctx->r, ctx->partials, np, z_old); }));
+        LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_LOOP_RR, ctx->partials, np, ctx->sc, &loop); }));
+        if (flexible)
+            LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_RZC, ctx->partials + np, np, ctx->sc); }));
+        return TPMG_OK;
+    });
+    long long total = 0;
+    for (int c = 0; c < TPMG_K_COUNT; ++c) total += t.launches[c] - l0[c];
+    if (init_launches) *init_launches = after_init;
+    if (iter_launches) *iter_launches = total - after_init;
+    std::copy(l0, l0 + TPMG_K_COUNT, t.launches);
+    std::copy(u0, u0 + TPMG_K_COUNT, t.units);
+    return st;
+}
+
+// Result of a device-side solve from the scalars (and history) read back.
+tpmg_status loop_result(tpmg_ctx *ctx, const Scalars &s, double rtol, int max_iter, int *iters, double *rel)
+{
+    *iters = s.it;
+    if (s.flag & 2) return fail(ctx, TPMG_ERR_BREAKDOWN, "non-finite residual");
+    if (s.flag & 1) return fail(ctx, TPMG_ERR_BREAKDOWN, "p.Ap <= 0: operator or preconditioner not SPD");
+    if (s.rr0 == 0.0) {
+        *rel = 0.0;
+        return TPMG_OK;
+    }
+    *rel = std::sqrt(s.rr / s.rr0);
+    if (*rel <= rtol && s.it <= max_iter) return TPMG_OK;
+    return fail(ctx, TPMG_ERR_NOT_CONVERGED, "max_iter reached before rtol");
+}
+
+// tpmg_solve with the loop on the device: one graph launch per solve (the
+// graph is captured once per argument set), one read-back at the end.
+tpmg_status pcg_graph(tpmg_ctx *ctx, const double *f, double *u, double rtol, int max_iter, int *iters, double *rel,
+                      double *hist)
+{
+    auto &sg = ctx->sg;
+    if (!sg.exec || sg.f != f || sg.u != u || sg.rtol != rtol || sg.max_iter != max_iter) {
+        if (sg.exec) cudaGraphExecDestroy(sg.exec);
+        sg.exec = nullptr;
+        cudaGraph_t g;
+        CU(cudaGraphCreate(&g, 0));
+        tpmg_status st = append_solve(ctx, g, f, u, rtol, max_iter);
+        cudaError_t e = st == TPMG_OK ? cudaGraphInstantiate(&sg.exec, g, 0) : cudaSuccess;
+        cudaGraphDestroy(g);
+        if (st != TPMG_OK) return st;
+        if (e != cudaSuccess) return fail(ctx, TPMG_ERR_CUDA, std::string("solve graph: ") + cudaGetErrorString(e));
+        sg.f = f;
+        sg.u = u;
+        sg.rtol = rtol;
+        sg.max_iter = max_iter;
+    }
+    CU(cudaGraphLaunch(sg.exec, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->h_sc, ctx->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    const Scalars s = *ctx->h_sc;
+    if (hist && s.it >= 0) CU(cudaMemcpy(hist, ctx->d_hist, sizeof(double) * (s.it + 1), cudaMemcpyDeviceToHost));
+    return loop_result(ctx, s, rtol, max_iter, iters, rel);
 }
 
 tpmg_status pcg(tpmg_ctx *ctx, const double *f, double *u, double rtol, int max_iter, int *iters, double *rel,
@@ -655,7 +816,8 @@ tpmg_status tpmg_setup(const tpmg_params *params, void *cuda_stream, tpmg_ctx **
     if (dalloc(ctx, &ctx->r, ctx->N) != cudaSuccess || dalloc(ctx, &ctx->z, ctx->N) != cudaSuccess ||
         dalloc(ctx, &ctx->pv, ctx->N) != cudaSuccess || dalloc(ctx, &ctx->q, ctx->N) != cudaSuccess ||
         dalloc(ctx, &ctx->hf, ctx->N) != cudaSuccess || dalloc(ctx, &ctx->hu, ctx->N) != cudaSuccess ||
-        dalloc(ctx, &ctx->partials, 2 * (size_t)ctx->n_part) != cudaSuccess || dalloc(ctx, &ctx->sc, 1) != cudaSuccess)
+        dalloc(ctx, &ctx->partials, 2 * (size_t)ctx->n_part) != cudaSuccess ||
+        dalloc(ctx, &ctx->d_hist, kHistCap) != cudaSuccess || dalloc(ctx, &ctx->sc, 1) != cudaSuccess)
         return bail(TPMG_ERR_OOM);
     if (cudaMallocHost(&ctx->h_sc, sizeof(Scalars)) != cudaSuccess) return bail(TPMG_ERR_OOM);
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return bail(TPMG_ERR_CUDA);
@@ -732,7 +894,76 @@ tpmg_status tpmg_solve(tpmg_ctx *ctx, const double *d_f, double *d_u, double rto
     if (!ctx || !d_f || !d_u || !iters || !rel_resid) return fail(ctx, TPMG_ERR_INVALID_ARG, "NULL argument");
     if (!(rtol >= 0.0) || max_iter < 0) return fail(ctx, TPMG_ERR_INVALID_ARG, "rtol must be >= 0, max_iter >= 0");
     if (d_f == d_u) return fail(ctx, TPMG_ERR_INVALID_ARG, "f and u must not overlap");
+    // the device-side loop cannot carry the event pairs of a timed kernel class
+    if (ctx->p.graphs && ctx->tr.mask == 0 && max_iter < kHistCap)
+        return pcg_graph(ctx, d_f, d_u, rtol, max_iter, iters, rel_resid, resid_hist);
     return pcg(ctx, d_f, d_u, rtol, max_iter, iters, rel_resid, resid_hist);
+}
+
+tpmg_status tpmg_batch_create(tpmg_ctx *const *ctxs, int n, const double *const *d_f, double *const *d_u, double rtol,
+                              int max_iter, tpmg_batch **out)
+{
+    if (!out || !ctxs || !d_f || !d_u || n < 1) return TPMG_ERR_INVALID_ARG;
+    if (!(rtol >= 0.0) || max_iter < 0 || max_iter >= kHistCap) return TPMG_ERR_INVALID_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TPMG_ERR_CUDA;
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i] || !d_f[i] || !d_u[i] || d_f[i] == d_u[i] || ctxs[i]->device != dev) return TPMG_ERR_INVALID_ARG;
+        for (int k = 0; k < i; ++k)
+            if (ctxs[k] == ctxs[i]) return TPMG_ERR_INVALID_ARG;   // one problem per context
+    }
+    tpmg_batch *b = new (std::nothrow) tpmg_batch();
+    if (!b) return TPMG_ERR_OOM;
+    b->ctx.assign(ctxs, ctxs + n);
+    b->init_launches.assign(n, 0);
+    b->iter_launches.assign(n, 0);
+    b->rtol = rtol;
+    b->max_iter = max_iter;
+    cudaGraph_t g;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) {
+        delete b;
+        return TPMG_ERR_CUDA;
+    }
+    tpmg_status st = TPMG_OK;
+    for (int i = 0; i < n && st == TPMG_OK; ++i)
+        st = append_solve(ctxs[i], g, d_f[i], d_u[i], rtol, max_iter, &b->init_launches[i], &b->iter_launches[i]);
+    if (st == TPMG_OK && cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) st = TPMG_ERR_CUDA;
+    cudaGraphDestroy(g);
+    if (st != TPMG_OK) {
+        tpmg_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_batch_run(tpmg_batch *b, void *cuda_stream, int *iters, double *rel_resid, int *status,
+                           long long *kernel_launches)
+{
+    if (!b || !iters || !rel_resid) return TPMG_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if (cudaGraphLaunch(b->exec, s) != cudaSuccess) return TPMG_ERR_CUDA;
+    for (tpmg_ctx *c : b->ctx)
+        if (cudaMemcpyAsync(c->h_sc, c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return TPMG_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return TPMG_ERR_CUDA;
+    tpmg_status first = TPMG_OK;
+    long long launches = 0;
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        const tpmg_status st = loop_result(b->ctx[i], *b->ctx[i]->h_sc, b->rtol, b->max_iter, &iters[i], &rel_resid[i]);
+        if (status) status[i] = st;
+        if (st != TPMG_OK && first == TPMG_OK) first = st;
+        launches += b->init_launches[i] + (long long)iters[i] * b->iter_launches[i];
+    }
+    if (kernel_launches) *kernel_launches = launches;
+    return first;
+}
+
+void tpmg_batch_destroy(tpmg_batch *b)
+{
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    delete b;
 }
 
 tpmg_status tpmg_solve_host(tpmg_ctx *ctx, const double *h_f, double *h_u, double rtol, int max_iter, int *iters,

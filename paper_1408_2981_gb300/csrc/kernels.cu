@@ -649,7 +649,8 @@ __global__ void __launch_bounds__(NT) k_xpby(const Scalars *__restrict__ sc, con
 }
 
 // Deterministic reduction of the block partials (fixed order) and the PCG scalar step.
-__global__ void __launch_bounds__(256) k_finish(int what, const double *__restrict__ partials, int n, Scalars *sc)
+__global__ void __launch_bounds__(256) k_finish(int what, const double *__restrict__ partials, int n, Scalars *sc,
+                                                LoopCtl loop)
 {
     double v = 0.0;
     for (int i = threadIdx.x; i < n; i += 256) v += partials[i];
@@ -693,6 +694,32 @@ __global__ void __launch_bounds__(256) k_finish(int what, const double *__restri
         sc->rz = v;
         if (!isfinite(v)) sc->flag |= 2;
         break;
+    case FIN_LOOP_RR0: {
+        sc->rr0 = v;
+        sc->rr = v;
+        sc->it = 0;
+        sc->flag = isfinite(v) ? 0 : 2;
+        if (loop.hist) loop.hist[0] = 1.0;
+        cudaGraphSetConditional(loop.cond, (isfinite(v) && v > 0.0 && loop.max_iter > 0) ? 1u : 0u);
+        break;
+    }
+    case FIN_LOOP_BETA:
+    case FIN_LOOP_BETA_PR:
+        sc->rz_new = v;
+        sc->beta = sc->it == 0 ? 0.0 : (what == FIN_LOOP_BETA ? v : v - sc->rzc) / sc->rz;
+        sc->rz = v;
+        if (!isfinite(v)) sc->flag |= 2;
+        break;
+    case FIN_LOOP_RR: {
+        sc->rr = v;
+        const int it = ++sc->it;
+        if (!isfinite(v)) sc->flag |= 2;
+        const double rel = sqrt(v / sc->rr0);
+        if (loop.hist) loop.hist[it] = rel;
+        const bool go = sc->flag == 0 && !(rel <= loop.rtol) && it < loop.max_iter;
+        cudaGraphSetConditional(loop.cond, go ? 1u : 0u);
+        break;
+    }
     default:
         break;
     }
@@ -804,9 +831,10 @@ cudaError_t launch_dot(const Launch &L, long n, const double *a, const double *b
     return cudaGetLastError();
 }
 
-cudaError_t launch_finish(const Launch &L, int what, const double *partials, int n_part, Scalars *sc)
+cudaError_t launch_finish(const Launch &L, int what, const double *partials, int n_part, Scalars *sc,
+                          const LoopCtl *loop)
 {
-    k_finish<<<1, 256, 0, L.s>>>(what, partials, n_part, sc);
+    k_finish<<<1, 256, 0, L.s>>>(what, partials, n_part, sc, loop ? *loop : LoopCtl{0, 0.0, 0, nullptr});
     return cudaGetLastError();
 }
 

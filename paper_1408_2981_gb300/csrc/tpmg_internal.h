@@ -104,7 +104,17 @@ struct Scalars {            // PCG scalars kept in device memory
     double rz_new;
     double rzc;             // <r_{k+1}, z_k> (flexible CG)
     int flag;               // bit 0: p.Ap <= 0 or non-finite; bit 1: non-finite residual
-    int pad;
+    int it;                 // iterations done by the device-side loop
+};
+
+// Control of a PCG loop that runs on the device (a CUDA graph with a
+// conditional WHILE node): the finish kernels record the residual history,
+// count the iterations and set the loop condition.
+struct LoopCtl {
+    cudaGraphConditionalHandle cond;   // 0: host-driven loop
+    double rtol;                       // stop when sqrt(||r||^2 / ||r_0||^2) <= rtol (as the host loop)
+    int max_iter;
+    double *hist;                      // [max_iter + 1] ||r_k|| / ||r_0|| (device), or NULL
 };
 
 // kernels.cu launchers ------------------------------------------------------
@@ -146,7 +156,8 @@ cudaError_t launch_prolong_add32(const Launch &L, const LevelDev &fine, const fl
 cudaError_t launch_to_f64(const Launch &L, long n, const float *x, double *y);
 cudaError_t launch_twisted_factors32(const Launch &L, const LevelDev &lv);
 cudaError_t launch_dot(const Launch &L, long n, const double *a, const double *b, double *partials, int n_part);
-cudaError_t launch_finish(const Launch &L, int what, const double *partials, int n_part, Scalars *sc);
+cudaError_t launch_finish(const Launch &L, int what, const double *partials, int n_part, Scalars *sc,
+                          const LoopCtl *loop = nullptr);
 // z_old != NULL (flexible CG): also partials of <r_new, z_old> in partials[n_part..2 n_part)
 cudaError_t launch_axpy_pair(const Launch &L, long n, const Scalars *sc, const double *p, const double *q, double *u,
                              double *r, double *partials, int n_part, const double *z_old);
@@ -157,6 +168,9 @@ cudaError_t launch_xpby(const Launch &L, long n, const Scalars *sc, const double
 // up once per device).
 cudaError_t noalloc_scratch(int device, double **ptr);
 
-enum FinishWhat { FIN_RR0 = 0, FIN_ALPHA = 1, FIN_RR = 2, FIN_BETA = 3, FIN_RZ0 = 4, FIN_RZC = 5, FIN_BETA_PR = 6 };
+enum FinishWhat { FIN_RR0 = 0, FIN_ALPHA = 1, FIN_RR = 2, FIN_BETA = 3, FIN_RZ0 = 4, FIN_RZC = 5, FIN_BETA_PR = 6,
+                  // device-side loop: RR0 and RR also drive the loop condition; BETA and
+                  // BETA_PR give beta = 0 on the first pass (p is cleared before the loop)
+                  FIN_LOOP_RR0 = 7, FIN_LOOP_RR = 8, FIN_LOOP_BETA = 9, FIN_LOOP_BETA_PR = 10 };
 
 }  // namespace tpmg

@@ -1,0 +1,95 @@
+"""Batched form: many independent solves in one graph launch (tpmg_batch_*),
+through the C ABI (needs a GPU).
+
+A batched solve runs the same kernels in the same order as tpmg_solve, with
+its loop on the device, so every problem's solution and iteration count must
+equal those of its own solve bit for bit (the solve itself is checked against
+the oracle by the parity tests).
+"""
+import numpy as np
+import pytest
+
+from paper_1408_2981_gb300 import binding, build, inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+MIXED = dict(precision=binding.TPMG_PREC_MIXED, coeff_storage=binding.TPMG_COEFF_FULL)
+
+PROBLEMS = [
+    dict(refinement=3, n_levels=4, n_r=16, courant_c=8.0, nu_pre=1, nu_post=1),
+    dict(refinement=4, n_levels=5, n_r=32, grading=1.05, courant_c=80.0),
+    dict(refinement=2, n_levels=3, n_r=7, grading=1.1, courant_c=20.0, smoother=1, relax=0.6),
+    dict(refinement=4, n_levels=4, n_r=64, grading=1.05, courant_c=150.0, **MIXED),
+    dict(refinement=3, n_levels=2, n_r=128, grading=1.02, courant_c=4.0, **MIXED),
+    dict(refinement=1, n_levels=2, n_r=33, courant_c=30.0),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+
+
+def rhs(s, j):
+    return torch.from_numpy(inputs.uniform_pm1(inputs.SEED_BATCH + j, s.N)).cuda()
+
+
+def test_batch_matches_individual_solves():
+    solvers = [binding.Solver(**kw) for kw in PROBLEMS]
+    fs = [rhs(s, j) for j, s in enumerate(solvers)]
+    us = [torch.zeros_like(f) for f in fs]
+    b = binding.Batch(solvers, fs, us, rtol=1e-6, max_iter=100)
+    for rep in range(2):   # a second run from zero guesses repeats the first
+        for u in us:
+            u.zero_()
+        st, it, rel, sts, launches = b.run()
+        torch.cuda.synchronize()
+        assert st == binding.TPMG_OK and np.all(sts == binding.TPMG_OK) and launches > 0
+        for j, (kw, f, u) in enumerate(zip(PROBLEMS, fs, us)):
+            ref = binding.Solver(graphs=0, **kw)
+            u_ref = torch.zeros_like(f)
+            st_r, it_r, rel_r, _ = ref.solve(f, u_ref, rtol=1e-6, max_iter=100)
+            assert (st_r, it_r) == (binding.TPMG_OK, it[j]), (j, it_r, it[j])
+            assert rel_r == rel[j]
+            assert torch.equal(u, u_ref), j
+
+
+def test_batch_reports_each_problem():
+    solvers = [binding.Solver(**kw) for kw in PROBLEMS[:3]]
+    fs = [rhs(s, j) for j, s in enumerate(solvers)]
+    fs[1] = torch.zeros_like(fs[1])          # zero right-hand side: done in 0 iterations
+    us = [torch.zeros_like(f) for f in fs]
+    b = binding.Batch(solvers, fs, us, rtol=1e-12, max_iter=3)
+    st, it, rel, sts, _ = b.run()
+    assert sts[1] == binding.TPMG_OK and it[1] == 0 and rel[1] == 0.0
+    assert sts[0] == binding.TPMG_ERR_NOT_CONVERGED and it[0] == 3 and rel[0] > 1e-12
+    assert st == binding.TPMG_ERR_NOT_CONVERGED
+
+
+def test_batch_rejects_a_repeated_context():
+    s = binding.Solver(**PROBLEMS[0])
+    f = rhs(s, 0)
+    u1, u2 = torch.zeros_like(f), torch.zeros_like(f)
+    with pytest.raises(binding.TPMGError) as exc:
+        binding.Batch([s, s], [f, f], [u1, u2])
+    assert exc.value.status == binding.TPMG_ERR_INVALID_ARG
+
+
+def test_device_loop_solve_matches_host_loop():
+    """tpmg_solve with graphs on runs its loop on the device; with graphs off the
+    host drives it: same kernels, same order, same bits."""
+    for kw in PROBLEMS:
+        outs = []
+        for graphs in (0, 1):
+            s = binding.Solver(graphs=graphs, **kw)
+            f = rhs(s, 9)
+            u = torch.zeros_like(f)
+            st, it, rel, hist = s.solve(f, u, rtol=1e-8, max_iter=200, history=True)
+            torch.cuda.synchronize()
+            outs.append((st, it, rel, hist, u.cpu().numpy()))
+        (a, b) = outs
+        assert a[:3] == b[:3]
+        np.testing.assert_array_equal(a[3], b[3])
+        np.testing.assert_array_equal(a[4], b[4])
