@@ -430,7 +430,9 @@ def run_tpmg(args, wl):
                 "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
                 "config": {"workload": wl["text"], "n_unknowns": N, "parallelism": f"replicas{world}",
-                           "l2": "flushed between steps (write of 2x L2 outside the timed events)"},
+                           "l2": "flushed between steps (write of 2x L2 outside the timed events)",
+                           "relax_kernel_per_level": [["warp", "cta64", "cta128", "cta256"][v] if v >= 0 else "heuristic"
+                                                      for v, _ in s.tuning()]},
                 "e2e": {"value": e2e_value, "unit": "unknowns/s", "h2d_bytes_per_step": 2 * 8 * N,
                         "d2h_bytes_per_step": 8 * N},
                 "gpu_launches": gpu_launches, "roofline": roof, "hbm": hbm, "cpu_baseline": cpu,

@@ -99,14 +99,18 @@ typedef struct {
     int    coeff_storage;/* TPMG_COEFF_* */
     int    centre;       /* TPMG_CENTRE_* */
     int    precision;    /* TPMG_PREC_* */
-    int    graphs;       /* 1: tpmg_solve replays its V-cycle from a CUDA graph captured at the first
-                            solve (one graph launch instead of ~15 launches per level); 0: kernel
-                            by kernel.  The results are identical. */
+    int    graphs;       /* 1: tpmg_solve runs as one CUDA graph launch with its loop on the device
+                            (captured at the first solve with given vectors); 0: kernel by kernel
+                            from a host loop.  The results are identical. */
+    int    autotune;     /* 1: tpmg_setup times the relaxation kernel variants on every level and
+                            keeps the fastest (see tpmg_query_tuning); 0: a fixed heuristic.  The
+                            results are identical. */
 } tpmg_params;
 
 /* Fills *p with the defaults: refinement 3, n_levels 4, n_r 16, H = 10/6371,
  * grading 1, omega2 0 with courant_c 8, nu 2/2/1, block-SOR with relax 1,
- * factorised storage, circumcentres, FP64, graphs on.  Returns TPMG_ERR_INVALID_ARG if p is NULL. */
+ * factorised storage, circumcentres, FP64, graphs and autotuning on.  Returns TPMG_ERR_INVALID_ARG if
+ * p is NULL. */
 tpmg_status tpmg_default_params(tpmg_params *p);
 
 /* Builds the grid hierarchy, geometry, colouring and coefficients on the host
@@ -209,6 +213,13 @@ void tpmg_batch_destroy(tpmg_batch *b);
  * cells, vertical cells, omega^2 actually used, number of colours.  Any output
  * may be NULL.  Errors: INVALID_ARG. */
 tpmg_status tpmg_query(const tpmg_ctx *ctx, int level, int *n_cells, int *n_r, double *omega2, int *n_colours);
+
+/* The autotuner's choice on multigrid level `level`: variant = relaxation kernel
+ * (0 one warp per 16-column task, 1/2/3 one CTA of 64/128/256 threads per
+ * task, -1 heuristic: not tuned) and us[4] = measured microseconds of the
+ * level's largest colour pass with each variant.  Any output may be NULL.
+ * Errors: INVALID_ARG. */
+tpmg_status tpmg_query_tuning(const tpmg_ctx *ctx, int level, int *variant, float *us);
 
 /* Host copies of the grid of multigrid level `level`: centres [n][3] (unit
  * vectors), areas [n] (spherical), nbrs [n][3] (cell across edge e of the

@@ -36,7 +36,7 @@ TPMG_PREC_MIXED = 1
 # every entry point declared in include/tpmg.h
 EXPORTS = ["tpmg_default_params", "tpmg_setup", "tpmg_apply_operator", "tpmg_vcycle", "tpmg_vcycle_noalloc",
            "tpmg_solve",
-           "tpmg_solve_host", "tpmg_query", "tpmg_export_mesh", "tpmg_profile", "tpmg_profile_read",
+           "tpmg_solve_host", "tpmg_query", "tpmg_query_tuning", "tpmg_export_mesh", "tpmg_profile", "tpmg_profile_read",
            "tpmg_status_string", "tpmg_last_error", "tpmg_destroy", "tpmg_batch_create", "tpmg_batch_run",
            "tpmg_batch_destroy"]
 
@@ -49,7 +49,7 @@ class tpmg_params(ctypes.Structure):
                 ("courant_c", ctypes.c_double), ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int),
                 ("nu_coarse", ctypes.c_int), ("smoother", ctypes.c_int), ("relax", ctypes.c_double),
                 ("coeff_storage", ctypes.c_int), ("centre", ctypes.c_int), ("precision", ctypes.c_int),
-                ("graphs", ctypes.c_int)]
+                ("graphs", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class TPMGError(RuntimeError):
@@ -81,6 +81,7 @@ def load(path: str | None = None):
     lib.tpmg_solve_host.argtypes = [P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D), P]
     lib.tpmg_query.argtypes = [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(I)]
     lib.tpmg_export_mesh.argtypes = [P, I, P, P, P, P, P, P]
+    lib.tpmg_query_tuning.argtypes = [P, I, ctypes.POINTER(I), P]
     lib.tpmg_profile.argtypes = [P, ctypes.c_uint]
     lib.tpmg_profile_read.argtypes = [P, I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(D), ctypes.POINTER(D),
                                       ctypes.POINTER(ctypes.c_longlong)]
@@ -183,6 +184,18 @@ class Solver:
         if st != TPMG_OK:
             raise TPMGError(st, "tpmg_query")
         return n.value, nr.value, w.value, c.value
+
+    def tuning(self) -> list:
+        """Per level (coarsest first): (chosen relaxation variant, microseconds of each variant)."""
+        out = []
+        for level in range(self.n_levels):
+            v = ctypes.c_int()
+            us = np.zeros(4, dtype=np.float32)
+            st = self._lib.tpmg_query_tuning(self._h, level, ctypes.byref(v), us.ctypes.data)
+            if st != TPMG_OK:
+                raise TPMGError(st, "tpmg_query_tuning")
+            out.append((v.value, us.tolist()))
+        return out
 
     def export_mesh(self, level: int | None = None) -> dict:
         level = self.n_levels - 1 if level is None else level

@@ -132,6 +132,7 @@ bool validate(const tpmg_params *p, std::string &msg)
         return false;
     }
     if (p->graphs != 0 && p->graphs != 1) { msg = "graphs must be 0 or 1"; return false; }
+    if (p->autotune != 0 && p->autotune != 1) { msg = "autotune must be 0 or 1"; return false; }
     return true;
 }
 
@@ -738,6 +739,57 @@ tpmg_status upload_level(tpmg_ctx *ctx, int l)
     return TPMG_OK;
 }
 
+// Autotuner: on every level each relaxation kernel variant (one warp per task,
+// or one CTA of 64 / 128 / 256 threads per task) is timed on the level's
+// largest colour pass -- NORMAL mode, on the level's zeroed work vectors, one
+// warm-up and three timed launches -- and the fastest is kept.  All variants
+// perform the same arithmetic in the same order, so the choice changes no
+// result, only the time.
+tpmg_status autotune(tpmg_ctx *ctx)
+{
+    const Launch L = launch_of(ctx);
+    const bool mixed = ctx->p.precision == TPMG_PREC_MIXED;
+    cudaEvent_t a, b;
+    CU(cudaEventCreate(&a));
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return fail(ctx, TPMG_ERR_CUDA, "autotune: cudaEventCreate");
+    }
+    tpmg_status st = TPMG_OK;
+    for (LevelDev &D : ctx->lv) {
+        int c = 0;
+        for (int k = 1; k < D.n_colours; ++k)
+            if (D.colour_cells[k] > D.colour_cells[c]) c = k;
+        const int t0 = D.colour_task_off[c], nt = D.colour_task_off[c + 1] - t0;
+        auto pass = [&]() {
+            return mixed ? launch_relax32<float>(L, D, PASS_NORMAL, t0, nt, 1.f, D.u2_32, D.u32, D.u32, nullptr, nullptr)
+                         : launch_relax(L, D, ctx->vert, PASS_NORMAL, t0, nt, 1.0, D.u2, D.u2, D.u2, nullptr);
+        };
+        float best = 0.f;
+        int best_var = RELAX_CTA128;
+        for (int var = 0; var < RELAX_VARIANTS && st == TPMG_OK; ++var) {
+            D.relax_variant = var;
+            cudaError_t e = pass();
+            if (e == cudaSuccess) e = cudaEventRecord(a, ctx->stream);
+            for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = pass();
+            if (e == cudaSuccess) e = cudaEventRecord(b, ctx->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(b);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+            if (e != cudaSuccess) st = fail(ctx, TPMG_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+            D.relax_us[var] = 1e3f * ms / 3.f;
+            if (var == 0 || D.relax_us[var] < best) {
+                best = D.relax_us[var];
+                best_var = var;
+            }
+        }
+        D.relax_variant = best_var;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return st;
+}
+
 }  // namespace
 
 extern "C" {
@@ -762,6 +814,7 @@ tpmg_status tpmg_default_params(tpmg_params *p)
     p->centre = TPMG_CENTRE_CIRCUM;
     p->precision = TPMG_PREC_FP64;
     p->graphs = 1;
+    p->autotune = 1;
     return TPMG_OK;
 }
 
@@ -821,6 +874,10 @@ tpmg_status tpmg_setup(const tpmg_params *params, void *cuda_stream, tpmg_ctx **
         return bail(TPMG_ERR_OOM);
     if (cudaMallocHost(&ctx->h_sc, sizeof(Scalars)) != cudaSuccess) return bail(TPMG_ERR_OOM);
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return bail(TPMG_ERR_CUDA);
+    if (ctx->p.autotune) {
+        tpmg_status st = autotune(ctx);
+        if (st != TPMG_OK) return bail(st);
+    }
     *out = ctx;
     return TPMG_OK;
 }
@@ -987,6 +1044,15 @@ tpmg_status tpmg_query(const tpmg_ctx *ctx, int level, int *n_cells, int *n_r, d
     if (n_r) *n_r = ctx->p.n_r;
     if (omega2) *omega2 = ctx->host.omega2;
     if (n_colours) *n_colours = ctx->lv[level].n_colours;
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_query_tuning(const tpmg_ctx *ctx, int level, int *variant, float *us)
+{
+    if (!ctx || level < 0 || level >= ctx->p.n_levels) return TPMG_ERR_INVALID_ARG;
+    const LevelDev &D = ctx->lv[level];
+    if (variant) *variant = D.relax_variant;
+    if (us) std::copy(D.relax_us, D.relax_us + RELAX_VARIANTS, us);
     return TPMG_OK;
 }
 

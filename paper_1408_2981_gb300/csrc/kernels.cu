@@ -326,7 +326,7 @@ __device__ __forceinline__ void twisted_solve(const double *B, const double *C, 
 }
 
 // One relaxation pass (eq. BlockJacobi) over whole tasks of 16 columns, one
-// task per CTA of 128 threads:
+// task per CTA of NT threads (64, 128 or 256; chosen per level by the autotuner):
 //   u_T <- (1 - relax) u_T + relax A_T^{-1} (f_T + hr sum_e g_e u_{T_e}).
 // Phase A (all threads, coalesced along k, the loads of several elements in
 // flight per thread): t = (f + hr_k sum_e g_e u_{T_e,k}) / pivot_k into a
@@ -340,8 +340,8 @@ __device__ __forceinline__ void twisted_solve(const double *B, const double *C, 
 // weight, optional prolongation into the 4 children (u_fine += P x), loads
 // issued before their stores.  In the multicolour passes u_in == u_out: a pass
 // reads other colours' columns and its own column before writing it.
-template <int MODE, bool STAGE>
-__global__ void __launch_bounds__(128, STAGE ? 1 : 6)
+template <int MODE, bool STAGE, int NT>
+__global__ void __launch_bounds__(NT, STAGE ? 1 : 6)
     k_relax(OpView o, const int *__restrict__ cells, const int4 *__restrict__ tnb, const dbl4 *__restrict__ tg,
             const double *__restrict__ rinv, const double *__restrict__ fb, const double *__restrict__ fcf,
             const double *__restrict__ fm, int S, int j, int task0, const double *__restrict__ f, const double *u_in,
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(128, STAGE ? 1 : 6)
     const size_t fbase = (size_t)t * S * 32;
     if (STAGE) {
         const int chunks = S * 16;   // 16-byte chunks per multiplier block
-        for (int q = threadIdx.x; q < 2 * chunks; q += 128) {
+        for (int q = threadIdx.x; q < 2 * chunks; q += NT) {
             const int a = q >= chunks, r = q - a * chunks;
             cp_async16(sf + (size_t)a * S * 32 + 2 * r, (a ? fcf : fb) + fbase + 2 * r);
         }
@@ -375,12 +375,12 @@ __global__ void __launch_bounds__(128, STAGE ? 1 : 6)
     }
     __syncthreads();
     constexpr int U = STAGE ? 8 : 4;   // elements per thread with loads in flight
-    for (int e0 = threadIdx.x; e0 < ne; e0 += 128 * U) {
+    for (int e0 = threadIdx.x; e0 < ne; e0 += NT * U) {
         double fv[U], iv[U], v0[U], v1[U], v2[U];
         int col[U], kk[U];
 #pragma unroll
         for (int q = 0; q < U; ++q) {
-            const int e = e0 + 128 * q;
+            const int e = e0 + NT * q;
             col[q] = -1;
             kk[q] = 0;
             fv[q] = iv[q] = v0[q] = v1[q] = v2[q] = 0.0;
@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(128, STAGE ? 1 : 6)
     }
     if (STAGE) cp_async_wait_all();
     __syncthreads();
-    if ((threadIdx.x >> 5) == (blockIdx.x & 3)) {
+    if ((threadIdx.x >> 5) == (int)(blockIdx.x % (NT / 32))) {
         const int lane = threadIdx.x & 31;
         const double *B = STAGE ? sf + lane : fb + fbase + lane;
         const double *C = STAGE ? sf + (size_t)S * 32 + lane : fcf + fbase + lane;
@@ -422,12 +422,12 @@ __global__ void __launch_bounds__(128, STAGE ? 1 : 6)
     }
     __syncthreads();
     constexpr int W = STAGE ? 4 : 2;
-    for (int e0 = threadIdx.x; e0 < ne; e0 += 128 * W) {
+    for (int e0 = threadIdx.x; e0 < ne; e0 += NT * W) {
         double x[W], uo[W], uf[W][4];
         int idx[W], fi[W];
 #pragma unroll
         for (int q = 0; q < W; ++q) {
-            const int e = e0 + 128 * q;
+            const int e = e0 + NT * q;
             idx[q] = -1;
             if (e >= ne) continue;
             const int c = e / n_r, k = e - c * n_r;
@@ -778,41 +778,48 @@ cudaError_t launch_twisted_factors(const Launch &L, const LevelDev &lv, const Ve
     return cudaGetLastError();
 }
 
-template <int MODE, bool STAGE>
+template <int MODE, bool STAGE, int NT>
 static cudaError_t relax_launch_t(const Launch &L, const LevelDev &lv, const VertDev &v, int task0, int n_tasks,
                                   double relax, const double *f, const double *u_in, double *u_out, double *u_fine,
                                   size_t smem)
 {
-    auto kern = k_relax<MODE, STAGE>;
+    auto kern = k_relax<MODE, STAGE, NT>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    kern<<<n_tasks, 128, smem, L.s>>>(make_view(lv, v, L.n_r), lv.task_cells, lv.task_nbr, lv.task_g, lv.rinv, lv.fb,
-                                      lv.fc, lv.fm, lv.steps, lv.jmid, task0, f, u_in, u_out, u_fine, relax);
+    kern<<<n_tasks, NT, smem, L.s>>>(make_view(lv, v, L.n_r), lv.task_cells, lv.task_nbr, lv.task_g, lv.rinv, lv.fb,
+                                     lv.fc, lv.fm, lv.steps, lv.jmid, task0, f, u_in, u_out, u_fine, relax);
     return cudaGetLastError();
 }
 
-// Kernel choice: more tasks than one wave of CTAs holds (8 per SM) and a tile
-// of at most 32 KB -> one warp per task; otherwise one CTA per task, with the multipliers
-// staged in shared memory by cp.async when they fit (small passes, where few
-// CTAs cannot hide the load latency of the serial phase).
+// Kernel choice (RELAX_*): the level's autotuned variant, or without one the
+// heuristic -- more tasks than one wave of CTAs holds (8 per SM) and a tile of
+// at most 32 KB -> one warp per task, otherwise one 128-thread CTA per task.
+// CTA variants stage the multipliers in shared memory by cp.async when they
+// fit; a column too tall for that runs unstaged with 128 threads.
 template <int MODE>
 static cudaError_t relax_launch(const Launch &L, const LevelDev &lv, const VertDev &v, int task0, int n_tasks,
                                 double relax, const double *f, const double *u_in, double *u_out, double *u_fine)
 {
     if (n_tasks <= 0) return cudaSuccess;
     const size_t tile = (((size_t)kRelaxCols * (L.n_r + 1) + 1) & ~(size_t)1) * sizeof(double);
-    if (n_tasks >= 8 * L.sm_count && tile <= 32 * 1024) {
+    int var = lv.relax_variant;
+    if (var < 0) var = (n_tasks >= 8 * L.sm_count && tile <= 32 * 1024) ? RELAX_WARP : RELAX_CTA128;
+    if (var == RELAX_WARP && tile <= 32 * 1024) {
         k_relax_warp<MODE><<<n_tasks, 32, tile, L.s>>>(make_view(lv, v, L.n_r), lv.task_cells, lv.task_nbr, lv.task_g,
                                                        lv.rinv, lv.fb, lv.fc, lv.fm, lv.steps, lv.jmid, task0, f,
                                                        u_in, u_out, u_fine, relax);
         return cudaGetLastError();
     }
     const size_t staged = tile + (size_t)2 * lv.steps * 32 * sizeof(double);
-    if (staged <= 160 * 1024)
-        return relax_launch_t<MODE, true>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine, staged);
-    return relax_launch_t<MODE, false>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine, tile);
+    if (staged > 160 * 1024)
+        return relax_launch_t<MODE, false, 128>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine, tile);
+    if (var == RELAX_CTA64)
+        return relax_launch_t<MODE, true, 64>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine, staged);
+    if (var == RELAX_CTA256)
+        return relax_launch_t<MODE, true, 256>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine, staged);
+    return relax_launch_t<MODE, true, 128>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine, staged);
 }
 
 cudaError_t launch_relax(const Launch &L, const LevelDev &lv, const VertDev &v, int mode, int task0, int n_tasks,

@@ -255,12 +255,12 @@ __device__ __forceinline__ void write_back32(const int *s_cell, const float *til
 }
 
 // One relaxation pass (eq. BlockJacobi) in FP32 over whole tasks of 16 columns,
-// one task per CTA of 128 threads (passes with few tasks):
+// one task per CTA of NT threads (64, 128 or 256; chosen per level by the autotuner):
 //   u_T <- (1 - relax) u_T + relax A_T^{-1} (f_T + sum_e alphaS_hat_e u_{T_e}).
 // The task's multiplier blocks are copied to shared memory by cp.async during
 // the gather; one warp (rotating over the sub-partitions) solves.
-template <int MODE, typename TF>
-__global__ void __launch_bounds__(128)
+template <int MODE, typename TF, int NT>
+__global__ void __launch_bounds__(NT)
     k_relax32(const int *__restrict__ cells, const int4 *__restrict__ tnb, const bf16x4 *__restrict__ cpack,
               const float *__restrict__ rinv, const float *__restrict__ fb, const float *__restrict__ fcf,
               const float *__restrict__ fm, int n_r, int S, int j, int task0, const TF *__restrict__ f,
@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(128)
     const size_t fbase = (size_t)t * S * 32;
     {
         const int chunks = S * 8;   // 16-byte chunks per multiplier block
-        for (int q = threadIdx.x; q < 2 * chunks; q += 128) {
+        for (int q = threadIdx.x; q < 2 * chunks; q += NT) {
             const int a = q >= chunks, r = q - a * chunks;
             cp_async16(sf + (size_t)a * S * 32 + 4 * r, (a ? fcf : fb) + fbase + 4 * r);
         }
@@ -291,16 +291,16 @@ __global__ void __launch_bounds__(128)
         s_m[q] = __ldg(&fm[(size_t)t * 2 * kRelaxCols + q]);
     }
     __syncthreads();
-    gather32<MODE, TF, 8>(s_cell, s_nb, cpack, rinv, f, u_in, n_r, ld, threadIdx.x, 128, tile);
+    gather32<MODE, TF, 8>(s_cell, s_nb, cpack, rinv, f, u_in, n_r, ld, threadIdx.x, NT, tile);
     cp_async_wait_all();
     __syncthreads();
-    if ((threadIdx.x >> 5) == (blockIdx.x & 3)) {
+    if ((threadIdx.x >> 5) == (int)(blockIdx.x % (NT / 32))) {
         const int lane = threadIdx.x & 31;
         twisted_solve32<8>(sf + lane, sf + (size_t)S * 32 + lane, s_m, tile + (lane & (kRelaxCols - 1)) * ld, n_r, j,
                            lane);
     }
     __syncthreads();
-    write_back32<MODE, 4>(s_cell, tile, n_r, ld, threadIdx.x, 128, u_in, u_out, u_fine, out64, relax);
+    write_back32<MODE, 4>(s_cell, tile, n_r, ld, threadIdx.x, NT, u_in, u_out, u_fine, out64, relax);
 }
 
 // The same pass with one warp per task and no block barrier (passes with many
@@ -386,31 +386,39 @@ inline int grid32(long work, int sm_count)
     return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
-// Kernel choice: one CTA per task, with the multipliers staged; the
-// warp-per-task kernel measured slower for FP32 at every pass size tried
-// (352 us against 232 us for 10k tasks of 128 levels), so its threshold is
-// set beyond any grid of this library.
-constexpr int kWarpTasksPerSm = 1 << 20;
+template <int MODE, typename TF, int NT>
+cudaError_t relax32_cta(const Launch &L, const LevelDev &lv, int task0, int n_tasks, float relax, const TF *f,
+                        const float *u_in, float *u_out, float *u_fine, double *out64, size_t smem)
+{
+    auto kern = k_relax32<MODE, TF, NT>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<n_tasks, NT, smem, L.s>>>(lv.task_cells, lv.task_nbr, lv.cpack, lv.rinv32, lv.fb32, lv.fc32, lv.fm32, L.n_r,
+                                     lv.steps, lv.jmid, task0, f, u_in, u_out, u_fine, out64, relax);
+    return cudaGetLastError();
+}
+
+// Kernel choice (RELAX_*): the level's autotuned variant; without one a
+// 128-thread CTA per task (measured faster than one warp per task at every
+// FP32 pass size tried, e.g. 313 against 352 us for 10k tasks of 128 levels).
 template <int MODE, typename TF>
 cudaError_t relax32_t(const Launch &L, const LevelDev &lv, int task0, int n_tasks, float relax, const TF *f,
                       const float *u_in, float *u_out, float *u_fine, double *out64)
 {
     const size_t tile = (((size_t)kRelaxCols * (L.n_r + 1) + 3) & ~(size_t)3) * sizeof(float);
-    if (n_tasks >= kWarpTasksPerSm * L.sm_count && tile <= 32 * 1024) {
+    const int var = lv.relax_variant < 0 ? RELAX_CTA128 : lv.relax_variant;
+    if (var == RELAX_WARP && tile <= 32 * 1024) {
         k_relax32_warp<MODE, TF><<<n_tasks, 32, tile, L.s>>>(lv.task_cells, lv.task_nbr, lv.cpack, lv.rinv32,
                                                              lv.fb32, lv.fc32, lv.fm32, L.n_r, lv.steps, lv.jmid,
                                                              task0, f, u_in, u_out, u_fine, out64, relax);
         return cudaGetLastError();
     }
     const size_t smem = tile + (size_t)2 * lv.steps * 32 * sizeof(float);
-    auto kern = k_relax32<MODE, TF>;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    kern<<<n_tasks, 128, smem, L.s>>>(lv.task_cells, lv.task_nbr, lv.cpack, lv.rinv32, lv.fb32, lv.fc32, lv.fm32,
-                                      L.n_r, lv.steps, lv.jmid, task0, f, u_in, u_out, u_fine, out64, relax);
-    return cudaGetLastError();
+    if (var == RELAX_CTA64) return relax32_cta<MODE, TF, 64>(L, lv, task0, n_tasks, relax, f, u_in, u_out, u_fine, out64, smem);
+    if (var == RELAX_CTA256) return relax32_cta<MODE, TF, 256>(L, lv, task0, n_tasks, relax, f, u_in, u_out, u_fine, out64, smem);
+    return relax32_cta<MODE, TF, 128>(L, lv, task0, n_tasks, relax, f, u_in, u_out, u_fine, out64, smem);
 }
 
 }  // namespace

@@ -62,6 +62,9 @@ struct VertDev {            // vertical factors shared by every level (no vertic
 // 16 * half, so that the serial phase reads 32 consecutive doubles per step.
 constexpr int kRelaxCols = 16;
 
+// Kernel variants of a relaxation pass (chosen per level by the autotuner).
+enum RelaxVariant { RELAX_WARP = 0, RELAX_CTA64 = 1, RELAX_CTA128 = 2, RELAX_CTA256 = 3, RELAX_VARIANTS = 4 };
+
 struct LevelDev {
     int n = 0;              // cells
     int ref = 0;
@@ -69,6 +72,8 @@ struct LevelDev {
     int n_tasks = 0;        // relaxation tasks over all colours
     int steps = 0;          // S = n_r - 1 - jmid: elimination steps of the longer half
     int jmid = 0;           // meeting row (n_r - 1) / 2
+    int relax_variant = -1; // RELAX_* chosen by the autotuner, -1 = heuristic
+    float relax_us[RELAX_VARIANTS] = {};   // autotuner timings of the level's largest pass
     std::vector<int> colour_task_off;  // [n_colours+1] first task of each colour (host copy)
     std::vector<int> colour_cells;     // [n_colours] cells of each colour (host copy)
     int4 *nbr = nullptr;          // [n] {nbr0, nbr1, nbr2, lower-colour mask}

@@ -93,3 +93,27 @@ def test_device_loop_solve_matches_host_loop():
         assert a[:3] == b[:3]
         np.testing.assert_array_equal(a[3], b[3])
         np.testing.assert_array_equal(a[4], b[4])
+
+
+def test_autotuned_kernels_give_identical_results():
+    """The autotuner picks among relaxation kernels that do the same arithmetic
+    in the same order, so tuned and untuned solves agree bit for bit."""
+    for kw in (PROBLEMS[1], PROBLEMS[3], PROBLEMS[4]):
+        outs = []
+        for tune in (0, 1):
+            s = binding.Solver(autotune=tune, **kw)
+            tuning = s.tuning()
+            assert len(tuning) == s.n_levels
+            if tune:
+                for variant, us in tuning:
+                    assert variant in (0, 1, 2, 3) and all(t > 0 for t in us)
+                    assert us[variant] == min(us)
+            else:
+                assert all(v == -1 for v, _ in tuning)
+            f = rhs(s, 11)
+            u = torch.zeros_like(f)
+            st, it, rel, _ = s.solve(f, u, rtol=1e-8, max_iter=200)
+            torch.cuda.synchronize()
+            outs.append((st, it, rel, u.cpu().numpy()))
+        assert outs[0][:3] == outs[1][:3]
+        np.testing.assert_array_equal(outs[0][3], outs[1][3])
