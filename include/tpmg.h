@@ -240,7 +240,8 @@ enum { TPMG_K_APPLY = 0,      /* y = A x (with the fused dot of CG) */
        TPMG_K_XPBY = 7,       /* p = z + beta p */
        TPMG_K_FINISH = 8,     /* deterministic reduction of partials + CG scalar step */
        TPMG_K_COPY = 9,       /* device-to-device copies and clears issued by the library */
-       TPMG_K_COUNT = 10 };
+       TPMG_K_NET = 10,       /* learned form (tpmg_learned.h): features, network layers, output */
+       TPMG_K_COUNT = 11 };
 
 /* Resets the tracing counters of ctx and times (with a CUDA event pair on the
  * context stream around each launch) the kernel classes whose bit is set in

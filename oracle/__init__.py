@@ -77,6 +77,8 @@ def _load(path: str | None = None):
         lib.oracle_fcg.argtypes = [_P, _P, _P, _D, _I, _P, _P, _P, _P]
         lib.oracle_set_vcycle_bf16.argtypes = [_P, _I]
         lib.oracle_set_vcycle_bf16.restype = None
+        lib.oracle_set_coarse_solve.argtypes = [_P, COARSE_SOLVE_FN]
+        lib.oracle_set_coarse_solve.restype = None
         lib.oracle_bf16.argtypes = [_D]
         lib.oracle_bf16.restype = _D
         lib.oracle_richardson.argtypes = [_P, _P, _P, _I, _P]
@@ -87,6 +89,11 @@ def _load(path: str | None = None):
         if path is None:
             _lib = lib
         return lib
+
+
+# coarsest-level solve callback of the V-cycle: (n_cells, n_r, f, u)
+COARSE_SOLVE_FN = ctypes.CFUNCTYPE(None, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double))
 
 
 def _ptr(a: np.ndarray | None):
@@ -255,6 +262,23 @@ class Oracle:
         """Use the V-cycle of the mixed-precision form (BF16-rounded coefficients,
         FP64 arithmetic) in vcycle(), pcg() and fcg()."""
         self._lib.oracle_set_vcycle_bf16(self._h, 1 if on else 0)
+
+    def set_coarse_solve(self, fn=None):
+        """Replace the V-cycle's coarsest-level solve by fn(f [n_cells * n_r]) -> u
+        (the learned form's network); None restores Algorithm 1's sweeps."""
+        if fn is None:
+            self._coarse_cb = None
+            self._lib.oracle_set_coarse_solve(self._h, COARSE_SOLVE_FN())
+            return
+
+        def cb(n_cells, n_r, f_ptr, u_ptr):
+            n = n_cells * n_r
+            f = np.ctypeslib.as_array(f_ptr, shape=(n,)).copy()
+            u = np.asarray(fn(f), dtype=np.float64).reshape(n)
+            np.ctypeslib.as_array(u_ptr, shape=(n,))[:] = u
+
+        self._coarse_cb = COARSE_SOLVE_FN(cb)   # kept alive while installed
+        self._lib.oracle_set_coarse_solve(self._h, self._coarse_cb)
 
     def pcg(self, f, u0=None, rtol: float = 1e-5, max_iter: int = 100, flexible: bool = False) -> dict:
         """Preconditioned CG; flexible=True uses the Polak-Ribiere coefficient."""

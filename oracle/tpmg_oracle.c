@@ -357,9 +357,14 @@ static int dsatur_colour(ogrid *G)
 /* ------------------------------------------------------------------------- */
 /* Oracle context                                                              */
 /* ------------------------------------------------------------------------- */
+/* Coarsest-level solve supplied by the caller (the learned form's network):
+ * u [n_cells * n_r] = solve(f [n_cells * n_r]). */
+typedef void (*coarse_solve_fn)(int n_cells, int n_r, const double *f, double *u);
+
 typedef struct {
     int L, n_levels, n_r;
     double H, grading, omega2, h_min;
+    coarse_solve_fn coarse_cb;   /* NULL: Algorithm 1's nu_coarse sweeps */
     int nu_pre, nu_post, nu_coarse, smoother; /* smoother: 0 multicolour block-SOR, 1 block-Jacobi */
     int centre_kind;                          /* 0 circumcentre, 1 normalised vertex mean */
     int vc_bf16;          /* V-cycle of the mixed-precision form: BF16-rounded coefficients */
@@ -603,7 +608,8 @@ static void vcycle_level(octx *o, int l, const double *f, double *u)
     const ogrid *G = mg_grid(o, l);
     size_t N = (size_t)G->n_cells * o->n_r, i;
     if (l == 0) {
-        smooth(o, l, f, u, o->nu_coarse, 0);
+        if (o->coarse_cb) o->coarse_cb(G->n_cells, o->n_r, f, u);
+        else smooth(o, l, f, u, o->nu_coarse, 0);
         return;
     }
     smooth(o, l, f, u, o->nu_pre, +1);                       /* pre-smoothing    */
@@ -865,6 +871,11 @@ int oracle_vcycle(void *h, const double *r, double *z)
     o->bf16_now = 0;
     return 0;
 }
+
+/* Replace the coarsest-level solve of the V-cycle by fn (NULL restores the
+ * nu_coarse sweeps): the learned form, where a network predicts the coarse
+ * solution. */
+void oracle_set_coarse_solve(void *h, coarse_solve_fn fn) { ((octx *)h)->coarse_cb = fn; }
 
 /* Select the V-cycle of the mixed-precision form (on != 0) or the plain one. */
 void oracle_set_vcycle_bf16(void *h, int on) { ((octx *)h)->vc_bf16 = on != 0; }

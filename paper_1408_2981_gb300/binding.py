@@ -40,7 +40,21 @@ EXPORTS = ["tpmg_default_params", "tpmg_setup", "tpmg_apply_operator", "tpmg_vcy
            "tpmg_status_string", "tpmg_last_error", "tpmg_destroy", "tpmg_batch_create", "tpmg_batch_run",
            "tpmg_batch_destroy"]
 
-KERNEL_CLASSES = ["apply", "residual", "restrict", "relax", "prolong", "dot", "axpy", "xpby", "finish", "copy"]
+# every entry point declared in include/tpmg_learned.h
+EXPORTS_LEARNED = ["tpmg_net_create", "tpmg_net_n_params", "tpmg_net_set_params", "tpmg_net_get_params",
+                   "tpmg_net_forward", "tpmg_net_gradients", "tpmg_net_train_step", "tpmg_net_last_error",
+                   "tpmg_net_destroy", "tpmg_net_features", "tpmg_net_targets", "tpmg_record_coarse",
+                   "tpmg_record_count", "tpmg_coarse_solve", "tpmg_attach_net", "tpmg_vcycle_learned",
+                   "tpmg_solve_learned"]
+
+TPMG_NET_COARSE = 0
+TPMG_NET_WARM = 1
+TPMG_LEARNED_WARM_USED = 1
+TPMG_LEARNED_WARM_REJECTED = 2
+TPMG_LEARNED_FALLBACK = 4
+
+KERNEL_CLASSES = ["apply", "residual", "restrict", "relax", "prolong", "dot", "axpy", "xpby", "finish", "copy",
+                  "net"]
 
 
 class tpmg_params(ctypes.Structure):
@@ -95,8 +109,32 @@ def load(path: str | None = None):
     lib.tpmg_batch_run.argtypes = [P, P, P, P, P, ctypes.POINTER(ctypes.c_longlong)]
     lib.tpmg_batch_destroy.argtypes = [P]
     lib.tpmg_batch_destroy.restype = None
-    for name in EXPORTS:
-        if name not in ("tpmg_destroy", "tpmg_status_string", "tpmg_last_error", "tpmg_batch_destroy"):
+    L, F, LL = ctypes.c_long, ctypes.c_float, ctypes.c_longlong
+    lib.tpmg_net_create.argtypes = [I, I, P, ctypes.POINTER(P)]
+    lib.tpmg_net_n_params.argtypes = [P]
+    lib.tpmg_net_n_params.restype = ctypes.c_size_t
+    lib.tpmg_net_set_params.argtypes = [P, P]
+    lib.tpmg_net_get_params.argtypes = [P, P]
+    lib.tpmg_net_forward.argtypes = [P, P, L, P]
+    lib.tpmg_net_gradients.argtypes = [P, P, P, L, P, P]
+    lib.tpmg_net_train_step.argtypes = [P, P, P, L, F, P]
+    lib.tpmg_net_last_error.argtypes = [P]
+    lib.tpmg_net_last_error.restype = ctypes.c_char_p
+    lib.tpmg_net_destroy.argtypes = [P]
+    lib.tpmg_net_destroy.restype = None
+    lib.tpmg_net_features.argtypes = [P, I, P, P, L, P, P]
+    lib.tpmg_net_targets.argtypes = [P, I, P, P, P, L, P]
+    lib.tpmg_record_coarse.argtypes = [P, P, I]
+    lib.tpmg_record_count.argtypes = [P, ctypes.POINTER(I)]
+    lib.tpmg_coarse_solve.argtypes = [P, P, P, I]
+    lib.tpmg_attach_net.argtypes = [P, I, P]
+    lib.tpmg_vcycle_learned.argtypes = [P, P, P]
+    lib.tpmg_solve_learned.argtypes = [P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(I),
+                                       ctypes.POINTER(I), ctypes.POINTER(LL)]
+    no_status = ("tpmg_destroy", "tpmg_status_string", "tpmg_last_error", "tpmg_batch_destroy", "tpmg_net_n_params",
+                 "tpmg_net_last_error", "tpmg_net_destroy")
+    for name in EXPORTS + EXPORTS_LEARNED:
+        if name not in no_status:
             getattr(lib, name).restype = I
     if path is None:
         _lib = lib
@@ -264,6 +302,180 @@ class Solver:
         if raise_on_fail and st != TPMG_OK:
             self._check(st, "tpmg_solve_host")
         return st, it.value, rel.value
+
+
+    # --------------------------------------------------------------- learned form
+    def _level_vec(self, t, level: int, name: str, dtype=None):
+        torch = self._torch
+        dtype = dtype or torch.float64
+        n = self.query(level)[0] * self.n_r
+        if not isinstance(t, torch.Tensor) or t.dtype != dtype or not t.is_cuda or not t.is_contiguous():
+            raise TypeError(f"{name} must be a contiguous {dtype} CUDA tensor")
+        if t.numel() != n:
+            raise ValueError(f"{name} must have {n} elements (level {level})")
+        return _ptr(t)
+
+    @staticmethod
+    def _rows(cells, rows):
+        if cells is None:
+            return None, rows
+        import torch
+        if cells.dtype != torch.int32 or not cells.is_cuda or not cells.is_contiguous():
+            raise TypeError("cells must be a contiguous int32 CUDA tensor")
+        return _ptr(cells), cells.numel()
+
+    def net_features(self, level: int, f, x, cells=None) -> float:
+        """x [rows, 2 n_r] float32 <- the network inputs of the columns `cells`
+        (int32 CUDA tensor; None = every column) of f on `level`.  Returns s."""
+        cp, rows = self._rows(cells, self.query(level)[0])
+        if x.dtype != self._torch.float32 or not x.is_cuda or x.numel() != rows * 2 * self.n_r or not x.is_contiguous():
+            raise ValueError("x must be a contiguous float32 CUDA tensor of rows x 2 n_r")
+        s = ctypes.c_double()
+        self._check(self._lib.tpmg_net_features(self._h, level, self._level_vec(f, level, "f"), cp, rows, _ptr(x),
+                                                ctypes.byref(s)), "tpmg_net_features")
+        return s.value
+
+    def net_targets(self, level: int, f, u, t, cells=None):
+        """t [rows, n_r] float32 <- u / s (s of f) on the columns `cells`."""
+        cp, rows = self._rows(cells, self.query(level)[0])
+        if t.dtype != self._torch.float32 or not t.is_cuda or t.numel() != rows * self.n_r or not t.is_contiguous():
+            raise ValueError("t must be a contiguous float32 CUDA tensor of rows x n_r")
+        self._check(self._lib.tpmg_net_targets(self._h, level, self._level_vec(f, level, "f"),
+                                               self._level_vec(u, level, "u"), cp, rows, _ptr(t)), "tpmg_net_targets")
+
+    def record_coarse(self, buf=None, capacity: int = 0):
+        """Record the coarsest-level right-hand side of every V-cycle into buf
+        (float64 CUDA tensor of capacity x n_cells(0) x n_r); None stops."""
+        if buf is None:
+            self._check(self._lib.tpmg_record_coarse(self._h, None, 0), "tpmg_record_coarse")
+            return
+        n0 = self.query(0)[0] * self.n_r
+        if buf.dtype != self._torch.float64 or not buf.is_cuda or buf.numel() < capacity * n0:
+            raise ValueError("buf must be a float64 CUDA tensor of at least capacity x n_cells(0) x n_r")
+        self._rec = buf
+        self._check(self._lib.tpmg_record_coarse(self._h, _ptr(buf), capacity), "tpmg_record_coarse")
+
+    def record_count(self) -> int:
+        c = ctypes.c_int()
+        self._check(self._lib.tpmg_record_count(self._h, ctypes.byref(c)), "tpmg_record_count")
+        return c.value
+
+    def coarse_solve(self, f0, u0, sweeps: int):
+        """u0 <- coarsest-level solution of f0 by `sweeps` symmetric line-relaxation sweeps."""
+        self._check(self._lib.tpmg_coarse_solve(self._h, self._level_vec(f0, 0, "f0"), self._level_vec(u0, 0, "u0"),
+                                                sweeps), "tpmg_coarse_solve")
+
+    def attach_net(self, role: int, net):
+        if not hasattr(self, "_nets"):
+            self._nets = {}
+        self._check(self._lib.tpmg_attach_net(self._h, role, net._h if net is not None else None), "tpmg_attach_net")
+        self._nets[role] = net   # keep the network alive while attached
+
+    def vcycle_learned(self, r, z):
+        """z = B r with the attached COARSE network as the coarsest-level solve."""
+        self._check(self._lib.tpmg_vcycle_learned(self._h, self._vec(r, "r"), self._vec(z, "z")), "tpmg_vcycle_learned")
+
+    def solve_learned(self, f, u, rtol: float = 1e-5, max_iter: int = 100, raise_on_fail: bool = True):
+        """Flexible CG with the attached networks, stop at ||r|| <= rtol ||f||.
+        Returns (status, iters, rel_resid, info bits, fallback_iters, kernel_launches)."""
+        it, fb, info = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        rel = ctypes.c_double(0.0)
+        launches = ctypes.c_longlong(0)
+        st = self._lib.tpmg_solve_learned(self._h, self._vec(f, "f"), self._vec(u, "u"), rtol, max_iter,
+                                          ctypes.byref(it), ctypes.byref(rel), ctypes.byref(info), ctypes.byref(fb),
+                                          ctypes.byref(launches))
+        if raise_on_fail and st != TPMG_OK:
+            self._check(st, "tpmg_solve_learned")
+        return st, it.value, rel.value, info.value, fb.value, launches.value
+
+
+class Net:
+    """tpmg_net: the learned form's per-column network (include/tpmg_learned.h).
+
+    Tensors are float32 CUDA tensors; ``x`` [rows, 2 n_r], ``t``/``y`` [rows, n_r].
+    """
+
+    def __init__(self, n_r: int, hidden: int = 64, stream=None):
+        import torch
+
+        self._torch = torch
+        self._lib = load()
+        stream = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        st = self._lib.tpmg_net_create(n_r, hidden, ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h))
+        if st != TPMG_OK:
+            raise TPMGError(st, "tpmg_net_create")
+        self._h = h
+        self.n_r, self.hidden = n_r, hidden
+        self.sizes = [2 * n_r, hidden, hidden, hidden, n_r]
+        self.n_params = int(self._lib.tpmg_net_n_params(h))
+
+    def _check(self, st: int, what: str):
+        if st != TPMG_OK:
+            raise TPMGError(st, f"{what}: {self._lib.tpmg_net_last_error(self._h).decode()}")
+
+    def _f32(self, t, cols: int, name: str) -> int:
+        torch = self._torch
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+            raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+        if t.numel() % cols:
+            raise ValueError(f"{name} must have a multiple of {cols} elements")
+        return _ptr(t)
+
+    def set_params(self, flat: np.ndarray):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        if a.size != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters")
+        self._check(self._lib.tpmg_net_set_params(self._h, a.ctypes.data), "tpmg_net_set_params")
+
+    def get_params(self) -> np.ndarray:
+        a = np.zeros(self.n_params, dtype=np.float32)
+        self._check(self._lib.tpmg_net_get_params(self._h, a.ctypes.data), "tpmg_net_get_params")
+        return a
+
+    def unflatten(self, flat: np.ndarray) -> list:
+        """[(W_l [out, in], b_l [out])] of a flat parameter vector."""
+        out, off = [], 0
+        for i, o in zip(self.sizes[:-1], self.sizes[1:]):
+            W = flat[off:off + o * i].reshape(o, i)
+            off += o * i
+            b = flat[off:off + o]
+            off += o
+            out.append((W, b))
+        return out
+
+    def forward(self, x, y):
+        rows = x.numel() // (2 * self.n_r)
+        self._check(self._lib.tpmg_net_forward(self._h, self._f32(x, 2 * self.n_r, "x"), rows,
+                                               self._f32(y, self.n_r, "y")), "tpmg_net_forward")
+
+    def gradients(self, x, t, grad) -> float:
+        rows = x.numel() // (2 * self.n_r)
+        loss = ctypes.c_double()
+        self._check(self._lib.tpmg_net_gradients(self._h, self._f32(x, 2 * self.n_r, "x"), self._f32(t, self.n_r, "t"),
+                                                 rows, self._f32(grad, 1, "grad"), ctypes.byref(loss)),
+                    "tpmg_net_gradients")
+        return loss.value
+
+    def train_step(self, x, t, lr: float, want_loss: bool = False):
+        rows = x.numel() // (2 * self.n_r)
+        loss = ctypes.c_double()
+        self._check(self._lib.tpmg_net_train_step(self._h, self._f32(x, 2 * self.n_r, "x"),
+                                                  self._f32(t, self.n_r, "t"), rows, float(lr),
+                                                  ctypes.byref(loss) if want_loss else None), "tpmg_net_train_step")
+        return loss.value if want_loss else None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.tpmg_net_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batch:

@@ -11,6 +11,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "tpmg_internal.h"
@@ -51,6 +52,29 @@ struct tpmg_ctx {
         double rtol = 0.0;
         int max_iter = -1;
     } sg;
+    long long sg_init = 0, sg_iter = 0;   // launches of sg's initial part and of one iteration
+    long long last_launches = 0;          // kernels executed by the last solve
+    // learned form (tpmg_learned.h): attached networks (COARSE, WARM), their
+    // inference workspaces, scales, the learned solve's graph and the
+    // coarsest-level recording
+    tpmg_net *net[2] = {nullptr, nullptr};
+    struct NetWs {
+        float *x = nullptr, *h0 = nullptr, *h1 = nullptr, *y = nullptr;
+        long rows = 0;
+    } nws[2];
+    double *d_net_s = nullptr;    // [2] feature scales s (COARSE, WARM)
+    bool net_coarse_on = false;   // the V-cycle being issued uses the COARSE network
+    struct {
+        cudaGraphExec_t exec = nullptr;
+        const double *f = nullptr;
+        double *u = nullptr;
+        double rtol = 0.0;
+        int max_iter = -1;
+        const tpmg_net *nets[2] = {nullptr, nullptr};
+        long long init = 0, iter = 0;
+    } lg;
+    double *rec = nullptr;        // coarsest-level right-hand sides being recorded
+    int rec_cap = 0, rec_n = 0;
     double *d_hist = nullptr;     // [kHistCap] residual history of the device-side loop
     int device = 0;
     int sm_count = 0;
@@ -296,6 +320,31 @@ unsigned short bf16_bits(double x)
     return (unsigned short)(fb >> 16);
 }
 
+// The network attached in `role` on level lv: u_out = s network(features(f))
+// for every column of the level (scale, features, four layers, output).
+template <typename TF, typename TO>
+tpmg_status net_infer(tpmg_ctx *ctx, int role, const LevelDev &lv, const TF *f, TO *u_out)
+{
+    const Launch L = launch_of(ctx);
+    const NetView v = net_view(ctx->net[role]);
+    const auto &w = ctx->nws[role];
+    double *s = ctx->d_net_s + role;
+    const long rows = lv.n;
+    const double nunits = (double)lv.n * ctx->p.n_r;
+    LCHK(run(ctx, TPMG_K_NET, nunits, [&] { return launch_net_scale<TF>(L, lv, ctx->vert, f, ctx->partials, ctx->n_part); }));
+    LCHK(run(ctx, TPMG_K_NET, 1.0, [&] { return launch_net_scale_finish(L, lv, ctx->partials, ctx->n_part, s); }));
+    LCHK(run(ctx, TPMG_K_NET, nunits, [&] { return launch_net_features<TF>(L, lv, ctx->vert, f, nullptr, rows, s, w.x); }));
+    const float *in = w.x;
+    float *bufs[2] = {w.h0, w.h1};
+    for (int l = 0; l < 4; ++l) {
+        float *out = l == 3 ? w.y : bufs[l & 1];
+        LCHK(run(ctx, TPMG_K_NET, nunits, [&] { return launch_net_layer(ctx->issue, v, l, in, rows, out); }));
+        in = out;
+    }
+    LCHK(run(ctx, TPMG_K_NET, nunits, [&] { return launch_net_output<TO>(L, w.y, rows * ctx->p.n_r, s, u_out); }));
+    return TPMG_OK;
+}
+
 // Algorithm 1 in the mixed-precision form on level l: u = V-cycle(f), FP32
 // arithmetic on the BF16 stencil.  TF is double on the finest level (the
 // FP64 residual of the outer Krylov loop is read directly) and float below.
@@ -332,6 +381,24 @@ tpmg_status vcycle_mixed(tpmg_ctx *ctx, int l, const TF *f, float *u, float *scr
         return run(ctx, TPMG_K_COPY, nunits, [&] { return cudaMemsetAsync(x, 0, nbytes, ctx->issue); });
     };
     if (l == 0) {
+        if constexpr (std::is_same<TF, float>::value) {
+            // recording of the coarsest-level right-hand sides (training data of the learned form)
+            if (ctx->rec && !ctx->capturing && ctx->rec_n < ctx->rec_cap) {
+                double *dst = ctx->rec + (size_t)ctx->rec_n * lv.n * p.n_r;
+                LCHK(run(ctx, TPMG_K_COPY, nunits, [&] { return launch_to_f64(L, (long)lv.n * p.n_r, f, dst); }));
+                ++ctx->rec_n;
+            }
+            // learned form: the network's prediction replaces the coarsest-level solve
+            if (ctx->net_coarse_on) {
+                tpmg_status st = net_infer<float, float>(ctx, TPMG_NET_COARSE, lv, f, u);
+                if (st != TPMG_OK) return st;
+                if (u_fine) {
+                    const LevelDev &fl = ctx->lv[1];
+                    LCHK(run(ctx, TPMG_K_PROLONG, (double)fl.n * p.n_r, [&] { return launch_prolong_add32(L, fl, u, u_fine); }));
+                }
+                return TPMG_OK;
+            }
+        }
         if (p.nu_coarse == 0) {
             LCHK(clear(u));
             if (z64) LCHK(run(ctx, TPMG_K_COPY, nunits, [&] { return launch_to_f64(L, (long)lv.n * p.n_r, u, z64); }));
@@ -400,6 +467,9 @@ void drop_graph(tpmg_ctx *ctx)
     if (ctx->sg.exec) cudaGraphExecDestroy(ctx->sg.exec);
     ctx->sg.exec = nullptr;
     ctx->sg.max_iter = -1;
+    if (ctx->lg.exec) cudaGraphExecDestroy(ctx->lg.exec);
+    ctx->lg.exec = nullptr;
+    ctx->lg.max_iter = -1;
 }
 
 // z = B r on the PCG vectors of the context.  With graphs enabled the V-cycle
@@ -488,8 +558,11 @@ tpmg_status capture_into(tpmg_ctx *ctx, cudaGraph_t g, const cudaGraphNode_t *de
 // The finish kernels record the history in ctx->d_hist, count the iterations
 // in the device scalars and set the loop condition.  The launch counters of
 // the captured kernels are restored (a graph's launches are counted per run).
+// learned = true (tpmg_solve_learned): the initial guess is the WARM network's
+// prediction if one is attached, the stop test is relative to ||f||, and the
+// judge replaces a guess whose residual is not below ||f|| by zero.
 tpmg_status append_solve(tpmg_ctx *ctx, cudaGraph_t g, const double *f, double *u, double rtol, int max_iter,
-                         long long *init_launches = nullptr, long long *iter_launches = nullptr)
+                         long long *init_launches = nullptr, long long *iter_launches = nullptr, bool learned = false)
 {
     Tracer &t = ctx->tr;
     long long l0[TPMG_K_COUNT];
@@ -502,12 +575,29 @@ tpmg_status append_solve(tpmg_ctx *ctx, cudaGraph_t g, const double *f, double *
     LevelDev &fl = ctx->lv[ctx->p.n_levels - 1];
     const long N = ctx->N;
     const int np = ctx->n_part;
-    const bool flexible = ctx->p.precision == TPMG_PREC_MIXED;
+    const bool flexible = ctx->p.precision == TPMG_PREC_MIXED || learned;
     std::vector<cudaGraphNode_t> leaves;
     tpmg_status st = capture_into(ctx, g, nullptr, 0, &leaves, [&]() -> tpmg_status {
         const Launch L = launch_of(ctx);
+        if (learned && ctx->net[TPMG_NET_WARM]) {
+            // the network's guess, then one block-Jacobi line relaxation (eq. BlockJacobi,
+            // the V-cycle's smoother in FP32) from it on the finest level, which removes
+            // the vertically oscillating part of the network's error; written to u in FP64
+            tpmg_status s1 = net_infer<double, float>(ctx, TPMG_NET_WARM, fl, f, fl.u32);
+            if (s1 != TPMG_OK) return s1;
+            LCHK(run(ctx, TPMG_K_RELAX, (double)N, [&] {
+                return launch_relax32<double>(L, fl, PASS_NORMAL, 0, fl.n_tasks, (float)ctx->p.relax, f, fl.u32,
+                                              fl.u2_32, nullptr, u);
+            }));
+        }
         LCHK(run(ctx, TPMG_K_RESIDUAL, (double)N, [&] { return launch_residual(L, fl, ctx->vert, f, u, ctx->r, ctx->partials, np); }));
-        LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_LOOP_RR0, ctx->partials, np, ctx->sc, &loop); }));
+        if (learned) {
+            LCHK(run(ctx, TPMG_K_DOT, (double)N, [&] { return launch_dot(L, N, f, f, ctx->partials + np, np); }));
+            LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_LOOP_RR0F, ctx->partials, np, ctx->sc, &loop); }));
+            LCHK(run(ctx, TPMG_K_COPY, (double)N, [&] { return launch_judge_reset(L, ctx->sc, N, f, u, ctx->r); }));
+        } else {
+            LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_LOOP_RR0, ctx->partials, np, ctx->sc, &loop); }));
+        }
         LCHK(run(ctx, TPMG_K_COPY, (double)N, [&] { return cudaMemsetAsync(ctx->pv, 0, sizeof(double) * N, ctx->issue); }));
         return TPMG_OK;
     });
@@ -524,7 +614,9 @@ tpmg_status append_solve(tpmg_ctx *ctx, cudaGraph_t g, const double *f, double *
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     st = capture_into(ctx, body, nullptr, 0, nullptr, [&]() -> tpmg_status {
         const Launch L = launch_of(ctx);
+        ctx->net_coarse_on = learned && ctx->net[TPMG_NET_COARSE];
         tpmg_status s2 = vcycle_fine(ctx, ctx->r, ctx->z);
+        ctx->net_coarse_on = false;
         if (s2 != TPMG_OK) return s2;
         LCHK(run(ctx, TPMG_K_DOT, (double)N, [&] { return launch_dot(L, N, ctx->r, ctx->z, ctx->partials, np); }));
         LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] {
@@ -575,7 +667,7 @@ tpmg_status pcg_graph(tpmg_ctx *ctx, const double *f, double *u, double rtol, in
         sg.exec = nullptr;
         cudaGraph_t g;
         CU(cudaGraphCreate(&g, 0));
-        tpmg_status st = append_solve(ctx, g, f, u, rtol, max_iter);
+        tpmg_status st = append_solve(ctx, g, f, u, rtol, max_iter, &ctx->sg_init, &ctx->sg_iter);
         cudaError_t e = st == TPMG_OK ? cudaGraphInstantiate(&sg.exec, g, 0) : cudaSuccess;
         cudaGraphDestroy(g);
         if (st != TPMG_OK) return st;
@@ -589,6 +681,7 @@ tpmg_status pcg_graph(tpmg_ctx *ctx, const double *f, double *u, double rtol, in
     CU(cudaMemcpyAsync(ctx->h_sc, ctx->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     const Scalars s = *ctx->h_sc;
+    ctx->last_launches = ctx->sg_init + (long long)s.it * ctx->sg_iter;
     if (hist && s.it >= 0) CU(cudaMemcpy(hist, ctx->d_hist, sizeof(double) * (s.it + 1), cudaMemcpyDeviceToHost));
     return loop_result(ctx, s, rtol, max_iter, iters, rel);
 }
@@ -870,7 +963,8 @@ tpmg_status tpmg_setup(const tpmg_params *params, void *cuda_stream, tpmg_ctx **
         dalloc(ctx, &ctx->pv, ctx->N) != cudaSuccess || dalloc(ctx, &ctx->q, ctx->N) != cudaSuccess ||
         dalloc(ctx, &ctx->hf, ctx->N) != cudaSuccess || dalloc(ctx, &ctx->hu, ctx->N) != cudaSuccess ||
         dalloc(ctx, &ctx->partials, 2 * (size_t)ctx->n_part) != cudaSuccess ||
-        dalloc(ctx, &ctx->d_hist, kHistCap) != cudaSuccess || dalloc(ctx, &ctx->sc, 1) != cudaSuccess)
+        dalloc(ctx, &ctx->d_hist, kHistCap) != cudaSuccess || dalloc(ctx, &ctx->sc, 1) != cudaSuccess ||
+        dalloc(ctx, &ctx->d_net_s, 3) != cudaSuccess)
         return bail(TPMG_ERR_OOM);
     if (cudaMallocHost(&ctx->h_sc, sizeof(Scalars)) != cudaSuccess) return bail(TPMG_ERR_OOM);
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return bail(TPMG_ERR_CUDA);
@@ -954,7 +1048,12 @@ tpmg_status tpmg_solve(tpmg_ctx *ctx, const double *d_f, double *d_u, double rto
     // the device-side loop cannot carry the event pairs of a timed kernel class
     if (ctx->p.graphs && ctx->tr.mask == 0 && max_iter < kHistCap)
         return pcg_graph(ctx, d_f, d_u, rtol, max_iter, iters, rel_resid, resid_hist);
-    return pcg(ctx, d_f, d_u, rtol, max_iter, iters, rel_resid, resid_hist);
+    long long before = 0, after = 0;
+    for (int c = 0; c < TPMG_K_COUNT; ++c) before += ctx->tr.launches[c];
+    const tpmg_status st = pcg(ctx, d_f, d_u, rtol, max_iter, iters, rel_resid, resid_hist);
+    for (int c = 0; c < TPMG_K_COUNT; ++c) after += ctx->tr.launches[c];
+    ctx->last_launches = after - before;
+    return st;
 }
 
 tpmg_status tpmg_batch_create(tpmg_ctx *const *ctxs, int n, const double *const *d_f, double *const *d_u, double rtol,
@@ -1114,6 +1213,214 @@ const char *tpmg_status_string(tpmg_status s)
 }
 
 const char *tpmg_last_error(const tpmg_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+// ---- learned form (tpmg_learned.h) ------------------------------------------
+
+namespace {
+
+tpmg_status level_arg(tpmg_ctx *ctx, int level, const void *a, const void *b, long rows, const int *cells)
+{
+    if (!ctx) return TPMG_ERR_INVALID_ARG;
+    if (level < 0 || level >= ctx->p.n_levels) return fail(ctx, TPMG_ERR_INVALID_ARG, "level out of range");
+    if (!a || !b) return fail(ctx, TPMG_ERR_INVALID_ARG, "NULL argument");
+    if (rows < 1 || (!cells && rows > ctx->lv[level].n) || rows > 64L * 65535L)
+        return fail(ctx, TPMG_ERR_INVALID_ARG, "rows out of range");
+    return TPMG_OK;
+}
+
+// s of the field f on level: partials + finish into d_net_s[2]
+tpmg_status level_scale(tpmg_ctx *ctx, int level, const double *f)
+{
+    const Launch L = launch_of(ctx);
+    const LevelDev &lv = ctx->lv[level];
+    double *s = ctx->d_net_s + 2;
+    const double nunits = (double)lv.n * ctx->p.n_r;
+    LCHK(run(ctx, TPMG_K_NET, nunits, [&] { return launch_net_scale<double>(L, lv, ctx->vert, f, ctx->partials, ctx->n_part); }));
+    LCHK(run(ctx, TPMG_K_NET, 1.0, [&] { return launch_net_scale_finish(L, lv, ctx->partials, ctx->n_part, s); }));
+    return TPMG_OK;
+}
+
+}  // namespace
+
+tpmg_status tpmg_net_features(tpmg_ctx *ctx, int level, const double *d_f, const int *d_cells, long rows, float *d_x,
+                              double *h_scale)
+{
+    tpmg_status st = level_arg(ctx, level, d_f, d_x, rows, d_cells);
+    if (st != TPMG_OK || (st = level_scale(ctx, level, d_f)) != TPMG_OK) return st;
+    const Launch L = launch_of(ctx);
+    const double *s = ctx->d_net_s + 2;
+    LCHK(run(ctx, TPMG_K_NET, (double)rows * ctx->p.n_r, [&] {
+        return launch_net_features<double>(L, ctx->lv[level], ctx->vert, d_f, d_cells, rows, s, d_x);
+    }));
+    if (h_scale) {
+        CU(cudaMemcpyAsync(&ctx->h_sc->ff, s, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        *h_scale = ctx->h_sc->ff;
+    }
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_net_targets(tpmg_ctx *ctx, int level, const double *d_f, const double *d_u, const int *d_cells,
+                             long rows, float *d_t)
+{
+    tpmg_status st = level_arg(ctx, level, d_f, d_t, rows, d_cells);
+    if (st == TPMG_OK && !d_u) st = fail(ctx, TPMG_ERR_INVALID_ARG, "NULL argument");
+    if (st != TPMG_OK || (st = level_scale(ctx, level, d_f)) != TPMG_OK) return st;
+    const Launch L = launch_of(ctx);
+    const double *s = ctx->d_net_s + 2;
+    LCHK(run(ctx, TPMG_K_NET, (double)rows * ctx->p.n_r, [&] { return launch_net_targets(L, d_u, d_cells, rows, s, d_t); }));
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_record_coarse(tpmg_ctx *ctx, double *d_buf, int capacity)
+{
+    if (!ctx) return TPMG_ERR_INVALID_ARG;
+    if (d_buf) {
+        if (ctx->p.precision != TPMG_PREC_MIXED || ctx->p.n_levels < 2 || ctx->p.graphs != 0)
+            return fail(ctx, TPMG_ERR_INVALID_ARG, "recording needs the mixed-precision form, n_levels >= 2, graphs 0");
+        if (capacity < 1) return fail(ctx, TPMG_ERR_INVALID_ARG, "capacity must be >= 1");
+    }
+    ctx->rec = d_buf;
+    ctx->rec_cap = d_buf ? capacity : 0;
+    ctx->rec_n = 0;
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_record_count(const tpmg_ctx *ctx, int *count)
+{
+    if (!ctx || !count) return TPMG_ERR_INVALID_ARG;
+    *count = ctx->rec_n;
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_coarse_solve(tpmg_ctx *ctx, const double *d_f0, double *d_u0, int sweeps)
+{
+    if (!ctx || !d_f0 || !d_u0) return fail(ctx, TPMG_ERR_INVALID_ARG, "NULL argument");
+    if (ctx->p.precision != TPMG_PREC_MIXED || ctx->p.n_levels < 2)
+        return fail(ctx, TPMG_ERR_INVALID_ARG, "the coarse solve needs the mixed-precision form and n_levels >= 2");
+    if (sweeps < 1 || sweeps > 64) return fail(ctx, TPMG_ERR_INVALID_ARG, "sweeps must be in 1..64");
+    LevelDev &c = ctx->lv[0];
+    const long n = (long)c.n * ctx->p.n_r;
+    const Launch L = launch_of(ctx);
+    LCHK(run(ctx, TPMG_K_COPY, (double)n, [&] { return launch_to_f32(L, n, d_f0, c.f32); }));
+    // Algorithm 1's coarsest-level solve with nu_coarse = sweeps, without the
+    // network or the recording
+    const int nu = ctx->p.nu_coarse;
+    double *rec = ctx->rec;
+    ctx->p.nu_coarse = sweeps;
+    ctx->rec = nullptr;
+    ctx->net_coarse_on = false;
+    const tpmg_status st = vcycle_mixed<float>(ctx, 0, c.f32, c.u32, c.u2_32, nullptr, nullptr);
+    ctx->p.nu_coarse = nu;
+    ctx->rec = rec;
+    if (st != TPMG_OK) return st;
+    LCHK(run(ctx, TPMG_K_COPY, (double)n, [&] { return launch_to_f64(L, n, c.u32, d_u0); }));
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_vcycle_learned(tpmg_ctx *ctx, const double *d_r, double *d_z)
+{
+    if (!ctx || !d_r || !d_z) return fail(ctx, TPMG_ERR_INVALID_ARG, "NULL argument");
+    if (d_r == d_z) return fail(ctx, TPMG_ERR_INVALID_ARG, "r and z must not overlap");
+    if (!ctx->net[TPMG_NET_COARSE]) return fail(ctx, TPMG_ERR_INVALID_ARG, "no COARSE network attached");
+    ctx->net_coarse_on = true;
+    const tpmg_status st = vcycle_fine(ctx, d_r, d_z);
+    ctx->net_coarse_on = false;
+    return st;
+}
+
+tpmg_status tpmg_attach_net(tpmg_ctx *ctx, int role, tpmg_net *net)
+{
+    if (!ctx) return TPMG_ERR_INVALID_ARG;
+    if (role != TPMG_NET_COARSE && role != TPMG_NET_WARM) return fail(ctx, TPMG_ERR_INVALID_ARG, "unknown role");
+    if (net) {
+        const NetView v = net_view(net);
+        if (v.sizes[0] != 2 * ctx->p.n_r || v.sizes[4] != ctx->p.n_r)
+            return fail(ctx, TPMG_ERR_INVALID_ARG, "the network's columns do not have the context's n_r");
+        if (role == TPMG_NET_COARSE && (ctx->p.precision != TPMG_PREC_MIXED || ctx->p.n_levels < 2))
+            return fail(ctx, TPMG_ERR_INVALID_ARG, "a coarse network needs the mixed-precision form and n_levels >= 2");
+        auto &w = ctx->nws[role];
+        const long rows = role == TPMG_NET_COARSE ? ctx->lv[0].n : ctx->lv.back().n;
+        const long h = v.sizes[1];
+        if (w.rows != rows * h) {   // (re)allocate for this hidden width; old blocks are freed at destroy
+            const size_t nr = (size_t)ctx->p.n_r;
+            CU(dalloc(ctx, &w.x, (size_t)rows * 2 * nr));
+            CU(dalloc(ctx, &w.h0, (size_t)rows * h));
+            CU(dalloc(ctx, &w.h1, (size_t)rows * h));
+            CU(dalloc(ctx, &w.y, (size_t)rows * nr));
+            w.rows = rows * h;
+        }
+    }
+    ctx->net[role] = net;
+    if (ctx->lg.exec) cudaGraphExecDestroy(ctx->lg.exec);
+    ctx->lg.exec = nullptr;
+    ctx->lg.max_iter = -1;
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_solve_learned(tpmg_ctx *ctx, const double *d_f, double *d_u, double rtol, int max_iter, int *iters,
+                               double *rel_resid, int *info, int *fallback_iters, long long *kernel_launches)
+{
+    if (!ctx || !d_f || !d_u || !iters || !rel_resid) return fail(ctx, TPMG_ERR_INVALID_ARG, "NULL argument");
+    if (ctx->p.precision != TPMG_PREC_MIXED)
+        return fail(ctx, TPMG_ERR_INVALID_ARG, "the learned solve needs the mixed-precision form");
+    if (!(rtol >= 0.0) || max_iter < 1 || max_iter >= kHistCap)
+        return fail(ctx, TPMG_ERR_INVALID_ARG, "rtol must be >= 0, max_iter in 1..4095");
+    if (d_f == d_u) return fail(ctx, TPMG_ERR_INVALID_ARG, "f and u must not overlap");
+    auto &lg = ctx->lg;
+    if (!lg.exec || lg.f != d_f || lg.u != d_u || lg.rtol != rtol || lg.max_iter != max_iter ||
+        lg.nets[0] != ctx->net[0] || lg.nets[1] != ctx->net[1]) {
+        if (lg.exec) cudaGraphExecDestroy(lg.exec);
+        lg.exec = nullptr;
+        cudaGraph_t g;
+        CU(cudaGraphCreate(&g, 0));
+        // event pairs of timed classes cannot live inside the loop body: not timed here
+        const unsigned mask = ctx->tr.mask;
+        ctx->tr.mask = 0;
+        tpmg_status st = append_solve(ctx, g, d_f, d_u, rtol, max_iter, &lg.init, &lg.iter, true);
+        ctx->tr.mask = mask;
+        cudaError_t e = st == TPMG_OK ? cudaGraphInstantiate(&lg.exec, g, 0) : cudaSuccess;
+        cudaGraphDestroy(g);
+        if (st != TPMG_OK) return st;
+        if (e != cudaSuccess) return fail(ctx, TPMG_ERR_CUDA, std::string("learned solve graph: ") + cudaGetErrorString(e));
+        lg.f = d_f;
+        lg.u = d_u;
+        lg.rtol = rtol;
+        lg.max_iter = max_iter;
+        lg.nets[0] = ctx->net[0];
+        lg.nets[1] = ctx->net[1];
+    }
+    CU(cudaGraphLaunch(lg.exec, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->h_sc, ctx->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    const Scalars s = *ctx->h_sc;
+    int bits = s.info & 3;
+    if (!ctx->net[TPMG_NET_WARM]) bits = 0;   // the guess judged was the caller's, not a network's
+    long long launches = lg.init + (long long)s.it * lg.iter;
+    *iters = s.it;
+    double rel = s.ff > 0.0 ? std::sqrt(s.rr / s.ff) : 0.0;
+    int it_fb = 0;
+    tpmg_status st = TPMG_OK;
+    if (s.flag != 0 || !(rel <= rtol)) {
+        // fallback: plain TPMG-PCG to the same ||f||-relative tolerance
+        bits |= TPMG_LEARNED_FALLBACK;
+        double rtol_fb = rtol;
+        if (s.flag != 0) CU(cudaMemsetAsync(d_u, 0, sizeof(double) * ctx->N, ctx->stream));
+        else rtol_fb = rtol * std::sqrt(s.ff / s.rr);
+        double rel_fb = 1.0;
+        st = tpmg_solve(ctx, d_f, d_u, rtol_fb, max_iter, &it_fb, &rel_fb, nullptr);
+        launches += ctx->last_launches;
+        const double rr0_fb = ctx->h_sc->rr0;
+        rel = s.ff > 0.0 ? rel_fb * std::sqrt(rr0_fb / s.ff) : 0.0;
+        *iters += it_fb;
+    }
+    *rel_resid = rel;
+    if (info) *info = bits;
+    if (fallback_iters) *fallback_iters = it_fb;
+    if (kernel_launches) *kernel_launches = launches;
+    ctx->last_launches = launches;
+    return st;
+}
 
 void tpmg_destroy(tpmg_ctx *ctx)
 {

@@ -652,9 +652,14 @@ __global__ void __launch_bounds__(NT) k_xpby(const Scalars *__restrict__ sc, con
 __global__ void __launch_bounds__(256) k_finish(int what, const double *__restrict__ partials, int n, Scalars *sc,
                                                 LoopCtl loop)
 {
-    double v = 0.0;
+    double v = 0.0, v2 = 0.0;
     for (int i = threadIdx.x; i < n; i += 256) v += partials[i];
     v = block_sum<256>(v);
+    if (what == FIN_LOOP_RR0F) {   // second set of partials: ||f||^2
+        for (int i = threadIdx.x; i < n; i += 256) v2 += partials[n + i];
+        __syncthreads();
+        v2 = block_sum<256>(v2);
+    }
     if (threadIdx.x != 0) return;
     switch (what) {
     case FIN_RR0:
@@ -701,6 +706,21 @@ __global__ void __launch_bounds__(256) k_finish(int what, const double *__restri
         sc->flag = isfinite(v) ? 0 : 2;
         if (loop.hist) loop.hist[0] = 1.0;
         cudaGraphSetConditional(loop.cond, (isfinite(v) && v > 0.0 && loop.max_iter > 0) ? 1u : 0u);
+        break;
+    }
+    case FIN_LOOP_RR0F: {
+        // judge of the initial guess: kept only if its residual is below that of u = 0
+        const bool keep = v < v2;
+        const double rr = keep ? v : v2;
+        sc->ff = v2;
+        sc->info = keep ? 1 : 2;
+        sc->rr0 = v2;
+        sc->rr = rr;
+        sc->it = 0;
+        sc->flag = isfinite(rr) ? 0 : 2;
+        const double rel = v2 > 0.0 ? sqrt(rr / v2) : 0.0;
+        if (loop.hist) loop.hist[0] = rel;
+        cudaGraphSetConditional(loop.cond, (isfinite(rr) && rr > 0.0 && !(rel <= loop.rtol) && loop.max_iter > 0) ? 1u : 0u);
         break;
     }
     case FIN_LOOP_BETA:

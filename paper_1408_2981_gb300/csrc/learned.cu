@@ -1,0 +1,691 @@
+// The learned form: a small multilayer perceptron that stands in for the
+// coarsest-level solve of the V-cycle and predicts a warm-start guess.
+//
+// Network: four affine layers 2 n_r -> h -> h -> h -> n_r, ReLU after the
+// first three, evaluated per column.  Weights are used in bfloat16 (rounded
+// from FP32 masters after every update), activations and accumulation are
+// FP32, biases FP32.  Training minimises the mean squared error with Adam
+// (Kingma & Ba, 2015); every step -- forward, loss, backward, update -- runs
+// in the kernels below.
+//
+// Features of a column T (on one multigrid level, vertical index k):
+//   x_T[k]       = f_Tk / (|T| v_k) / s,
+//   x_T[n_r + k] = sum_e g_e f_{n_e k} / (|n_e| v_k) / (s sum_e g_e),
+// i.e. the right-hand side as point values (cell integral over cell volume)
+// of the column and the flux-weighted mean over its three edge neighbours
+// (a symmetric function of the 1-ring, whose order is arbitrary on a
+// triangle), scaled by the root mean square s of the point values over the
+// whole level.  The network predicts u_T / s, so the map f -> u is equivariant
+// under scaling of f, as the operator's inverse is.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "tpmg_internal.h"
+#include "../../include/tpmg_learned.h"
+
+struct tpmg_net {
+    int sizes[5] = {};            // layer widths: in, h, h, h, out
+    size_t off_w[4] = {}, off_b[4] = {}, n_params = 0;
+    float *master = nullptr;      // FP32 parameters: W_1 [h][in] row-major, b_1, W_2, b_2, ...
+    float *grad = nullptr;        // gradient, same layout
+    float *adam_m = nullptr, *adam_v = nullptr;
+    uint16_t *wbf = nullptr;      // bfloat16 copy of master (the weights every pass uses)
+    long step = 0;                // Adam steps taken
+    cudaStream_t stream = nullptr;
+    // training workspace: activations a_1..a_3, output y, two gradient
+    // buffers, split-K partials of the weight gradients
+    long ws_rows = 0;
+    float *ws = nullptr;
+    float *split = nullptr;
+    size_t split_cap = 0;
+    double *d_part = nullptr, *d_loss = nullptr, *h_loss = nullptr;
+    std::string err;
+};
+
+namespace tpmg {
+
+namespace {
+
+constexpr int GBM = 64, GBN = 64, GBK = 16, GNT = 256;
+constexpr int kLossBlocks = 256;
+
+enum { EPI_NONE = 0, EPI_BIAS = 1, EPI_BIAS_RELU = 2, EPI_MASK = 3 };
+
+__device__ __forceinline__ float ldf(float x) { return x; }
+__device__ __forceinline__ float ldf(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
+
+// bfloat16 nearest, ties to even, of an FP32 value (NaN stays NaN)
+__device__ __forceinline__ uint16_t to_bf16(float x)
+{
+    uint32_t u = __float_as_uint(x);
+    if ((u & 0x7fffffffu) > 0x7f800000u) return (uint16_t)((u >> 16) | 0x40u);
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+template <int NT>
+__device__ __forceinline__ double block_sum_d(double v)
+{
+    __shared__ double red[NT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < NT / 32 ? red[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    return v;   // valid in thread 0
+}
+
+// C[m][n] = epi(sum_{k in chunk z} A(m, k) B(k, n)), FP32 accumulation in
+// ascending k.  A(m, k) = A[m lda + k], or A[k lda + m] if AT; B(k, n) =
+// B[n ldb + k] if BT (a weight matrix [out][in]), else B[k ldb + n].  Split-K:
+// block z covers k in [z k_chunk, (z+1) k_chunk) and writes slice z of C
+// (C + z M ldc).  64 x 64 tile per CTA, 4 x 4 outputs per thread at rows
+// ty + 16 i and columns tx + 16 j.
+template <bool AT, bool BT, typename TB, int EPI>
+__global__ void __launch_bounds__(GNT) k_gemm(int M, int N, int K, int k_chunk, const float *__restrict__ A, int lda,
+                                              const TB *__restrict__ B, int ldb, float *__restrict__ C, int ldc,
+                                              const float *__restrict__ bias, const float *__restrict__ mask, int ldm)
+{
+    __shared__ float As[GBK][GBM + 4];
+    __shared__ float Bs[GBK][GBN + 4];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
+    const int kb = blockIdx.z * k_chunk, ke = min(K, kb + k_chunk);
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int k0 = kb; k0 < ke; k0 += GBK) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + GNT * q;   // 0 .. 1023: one element of each 64 x 16 tile
+            const int am = AT ? e % GBM : e / GBK, ak = AT ? e / GBM : e % GBK;
+            const int gm = m0 + am, gk = k0 + ak;
+            As[ak][am] = (gm < M && gk < ke) ? (AT ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk]) : 0.f;
+            const int bn = BT ? e / GBK : e % GBN, bk = BT ? e % GBK : e / GBN;
+            const int gn = n0 + bn, gk2 = k0 + bk;
+            Bs[bk][bn] = (gn < N && gk2 < ke) ? ldf(BT ? B[(size_t)gn * ldb + gk2] : B[(size_t)gk2 * ldb + gn]) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < GBK; ++k) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[k][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    float *Cz = C + (size_t)blockIdx.z * M * ldc;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int m = m0 + ty + 16 * i;
+        if (m >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = n0 + tx + 16 * j;
+            if (n >= N) continue;
+            float v = acc[i][j];
+            if (EPI == EPI_BIAS || EPI == EPI_BIAS_RELU) v += bias[n];
+            if (EPI == EPI_BIAS_RELU) v = v > 0.f ? v : 0.f;
+            if (EPI == EPI_MASK) v = mask[(size_t)m * ldm + n] > 0.f ? v : 0.f;
+            Cz[(size_t)m * ldc + n] = v;
+        }
+    }
+}
+
+// out[z][c] = sum over rows r in chunk z (ascending) of G[r][c]
+__global__ void __launch_bounds__(256) k_colsum(const float *__restrict__ G, int rows, int n, int k_chunk,
+                                                float *__restrict__ out)
+{
+    __shared__ float part[8][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + tx;
+    const int rb = blockIdx.y * k_chunk, re = min(rows, rb + k_chunk);
+    float acc = 0.f;
+    if (c < n)
+        for (int r = rb + ty; r < re; r += 8) acc += G[(size_t)r * n + c];
+    part[ty][tx] = acc;
+    __syncthreads();
+    if (ty == 0 && c < n) {
+        float s = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) s += part[q][tx];
+        out[(size_t)blockIdx.y * n + c] = s;
+    }
+}
+
+// out[i] = sum_{z = 0 .. S-1} parts[z count + i]
+__global__ void k_sum_slices(const float *__restrict__ parts, int S, long count, float *__restrict__ out)
+{
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int z = 0; z < S; ++z) s += parts[(size_t)z * count + i];
+        out[i] = s;
+    }
+}
+
+// G = 2 (y - t) / n and per-block partial sums of (y - t)^2 (double)
+__global__ void __launch_bounds__(256) k_mse(const float *__restrict__ y, const float *__restrict__ t, long n,
+                                             float *__restrict__ g, double *__restrict__ partials)
+{
+    const float scale = (float)(2.0 / (double)n);
+    double acc = 0.0;
+    for (long i = blockIdx.x * 256L + threadIdx.x; i < n; i += (long)gridDim.x * 256) {
+        const float d = y[i] - t[i];
+        g[i] = scale * d;
+        acc += (double)d * (double)d;
+    }
+    acc = block_sum_d<256>(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+__global__ void k_loss_finish(const double *__restrict__ partials, int np, long n, double *__restrict__ loss)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s = 0.0;
+    for (int i = 0; i < np; ++i) s += partials[i];
+    *loss = s / (double)n;
+}
+
+// Adam with bias correction (c1 = 1 - b1^t, c2 = 1 - b2^t); refreshes the bfloat16 copy
+__global__ void k_adam(long n, float *__restrict__ w, float *__restrict__ m, float *__restrict__ v,
+                       const float *__restrict__ g, uint16_t *__restrict__ wbf, float lr, float b1, float b2, float eps,
+                       float c1, float c2)
+{
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        w[i] = wi;
+        wbf[i] = to_bf16(wi);
+    }
+}
+
+__global__ void k_round_bf16(long n, const float *__restrict__ w, uint16_t *__restrict__ wbf)
+{
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        wbf[i] = to_bf16(w[i]);
+}
+
+// ---- features -------------------------------------------------------------
+
+// partials of sum over the level of (f_Tk / (|T| v_k))^2
+template <typename TF>
+__global__ void __launch_bounds__(256) k_net_scale(const TF *__restrict__ f, const double *__restrict__ area,
+                                                   const double *__restrict__ vol, long N, int n_r,
+                                                   double *__restrict__ partials)
+{
+    double acc = 0.0;
+    for (long i = blockIdx.x * 256L + threadIdx.x; i < N; i += (long)gridDim.x * 256) {
+        const long T = i / n_r;
+        const int k = (int)(i - T * n_r);
+        const double g = (double)f[i] / (area[T] * vol[k]);
+        acc = fma(g, g, acc);
+    }
+    acc = block_sum_d<256>(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+// s = sqrt(sum / N) (0 for a zero field)
+__global__ void k_net_scale_finish(const double *__restrict__ partials, int np, long N, double *__restrict__ s)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double v = 0.0;
+    for (int i = 0; i < np; ++i) v += partials[i];
+    *s = sqrt(v / (double)N);
+}
+
+template <typename TF>
+__global__ void k_net_features(const TF *__restrict__ f, const double *__restrict__ area,
+                               const double *__restrict__ vol, const int4 *__restrict__ nbr,
+                               const dbl4 *__restrict__ gg, const int *__restrict__ cells, long rows, int n_r,
+                               const double *__restrict__ s, float *__restrict__ X)
+{
+    const double sv = *s;
+    const double inv = sv > 0.0 ? 1.0 / sv : 0.0;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < rows * n_r; i += (long)gridDim.x * blockDim.x) {
+        const long j = i / n_r;
+        const int k = (int)(i - j * n_r);
+        const long T = cells ? cells[j] : j;
+        const int4 nb = nbr[T];
+        const dbl4 w = gg[T];
+        const double vk = vol[k];
+        const double own = (double)f[T * n_r + k] / (area[T] * vk);
+        const double mean = (w.x * ((double)f[(long)nb.x * n_r + k] / area[nb.x]) +
+                             w.y * ((double)f[(long)nb.y * n_r + k] / area[nb.y]) +
+                             w.z * ((double)f[(long)nb.z * n_r + k] / area[nb.z])) / (w.w * vk);
+        X[j * 2 * n_r + k] = (float)(own * inv);
+        X[j * 2 * n_r + n_r + k] = (float)(mean * inv);
+    }
+}
+
+__global__ void k_net_targets(const double *__restrict__ u, const int *__restrict__ cells, long rows, int n_r,
+                              const double *__restrict__ s, float *__restrict__ t)
+{
+    const double sv = *s;
+    const double inv = sv > 0.0 ? 1.0 / sv : 0.0;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < rows * n_r; i += (long)gridDim.x * blockDim.x) {
+        const long j = i / n_r;
+        const int k = (int)(i - j * n_r);
+        const long T = cells ? cells[j] : j;
+        t[i] = (float)(u[T * n_r + k] * inv);
+    }
+}
+
+template <typename TO>
+__global__ void k_net_output(const float *__restrict__ y, long n, const double *__restrict__ s, TO *__restrict__ u)
+{
+    const double sv = *s;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        u[i] = (TO)(sv * (double)y[i]);
+}
+
+// judge of the initial guess: if the finish kernel rejected it, u = 0 and r = f
+__global__ void k_judge_reset(const Scalars *__restrict__ sc, long n, const double *__restrict__ f,
+                              double *__restrict__ u, double *__restrict__ r)
+{
+    if (!(sc->info & 2)) return;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        u[i] = 0.0;
+        r[i] = f[i];
+    }
+}
+
+__global__ void k_to_f32(long n, const double *__restrict__ x, float *__restrict__ y)
+{
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        y[i] = (float)x[i];
+}
+
+inline int grid_1d(long work, int nt, int sm_count)
+{
+    long b = (work + nt - 1) / nt;
+    const long cap = (long)std::max(sm_count, 1) * 8;
+    return (int)std::max(1L, std::min(b, cap));
+}
+
+template <bool AT, bool BT, typename TB, int EPI>
+cudaError_t gemm(cudaStream_t s, int M, int N, int K, int splits, const float *A, int lda, const TB *B, int ldb,
+                 float *C, int ldc, const float *bias = nullptr, const float *mask = nullptr, int ldm = 0)
+{
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    splits = std::max(1, splits);
+    int chunk = (K + splits - 1) / splits;
+    chunk = std::max(GBK, (chunk + GBK - 1) / GBK * GBK);
+    splits = std::max(1, (K + chunk - 1) / chunk);
+    const dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM, splits);
+    k_gemm<AT, BT, TB, EPI><<<grid, GNT, 0, s>>>(M, N, K, chunk, A, lda, B, ldb, C, ldc, bias, mask, ldm);
+    return cudaGetLastError();
+}
+
+int sm_count_of_current()
+{
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+    return std::max(n, 1);
+}
+
+}  // namespace
+
+// ---- launchers shared with api.cu ------------------------------------------
+
+NetView net_view(const tpmg_net *net)
+{
+    NetView v{};
+    for (int i = 0; i < 5; ++i) v.sizes[i] = net->sizes[i];
+    for (int l = 0; l < 4; ++l) {
+        v.w[l] = net->wbf + net->off_w[l];
+        v.b[l] = net->master + net->off_b[l];
+    }
+    return v;
+}
+
+cudaError_t launch_net_layer(cudaStream_t s, const NetView &v, int l, const float *x, long rows, float *y)
+{
+    const int in = v.sizes[l], out = v.sizes[l + 1];
+    if (l < 3)
+        return gemm<false, true, uint16_t, EPI_BIAS_RELU>(s, (int)rows, out, in, 1, x, in, v.w[l], in, y, out, v.b[l]);
+    return gemm<false, true, uint16_t, EPI_BIAS>(s, (int)rows, out, in, 1, x, in, v.w[l], in, y, out, v.b[l]);
+}
+
+template <typename TF>
+cudaError_t launch_net_scale(const Launch &L, const LevelDev &lv, const VertDev &vert, const TF *f, double *partials,
+                             int n_part)
+{
+    const long N = (long)lv.n * L.n_r;
+    k_net_scale<TF><<<n_part, 256, 0, L.s>>>(f, lv.area, vert.vol, N, L.n_r, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_net_scale_finish(const Launch &L, const LevelDev &lv, const double *partials, int n_part, double *s)
+{
+    k_net_scale_finish<<<1, 32, 0, L.s>>>(partials, n_part, (long)lv.n * L.n_r, s);
+    return cudaGetLastError();
+}
+
+template <typename TF>
+cudaError_t launch_net_features(const Launch &L, const LevelDev &lv, const VertDev &vert, const TF *f, const int *cells,
+                                long rows, const double *s, float *X)
+{
+    if (rows <= 0) return cudaSuccess;
+    k_net_features<TF><<<grid_1d(rows * L.n_r, 256, L.sm_count), 256, 0, L.s>>>(f, lv.area, vert.vol, lv.nbr, lv.g,
+                                                                             cells, rows, L.n_r, s, X);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_net_targets(const Launch &L, const double *u, const int *cells, long rows, const double *s, float *t)
+{
+    if (rows <= 0) return cudaSuccess;
+    k_net_targets<<<grid_1d(rows * L.n_r, 256, L.sm_count), 256, 0, L.s>>>(u, cells, rows, L.n_r, s, t);
+    return cudaGetLastError();
+}
+
+template <typename TO>
+cudaError_t launch_net_output(const Launch &L, const float *y, long n, const double *s, TO *u)
+{
+    k_net_output<TO><<<grid_1d(n, 256, L.sm_count), 256, 0, L.s>>>(y, n, s, u);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_judge_reset(const Launch &L, const Scalars *sc, long n, const double *f, double *u, double *r)
+{
+    k_judge_reset<<<grid_1d(n, 256, L.sm_count), 256, 0, L.s>>>(sc, n, f, u, r);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_f32(const Launch &L, long n, const double *x, float *y)
+{
+    k_to_f32<<<grid_1d(n, 256, L.sm_count), 256, 0, L.s>>>(n, x, y);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_net_scale<float>(const Launch &, const LevelDev &, const VertDev &, const float *, double *, int);
+template cudaError_t launch_net_scale<double>(const Launch &, const LevelDev &, const VertDev &, const double *, double *, int);
+template cudaError_t launch_net_features<float>(const Launch &, const LevelDev &, const VertDev &, const float *,
+                                                const int *, long, const double *, float *);
+template cudaError_t launch_net_features<double>(const Launch &, const LevelDev &, const VertDev &, const double *,
+                                                 const int *, long, const double *, float *);
+template cudaError_t launch_net_output<float>(const Launch &, const float *, long, const double *, float *);
+template cudaError_t launch_net_output<double>(const Launch &, const float *, long, const double *, double *);
+
+}  // namespace tpmg
+
+// ---- C ABI: the network -----------------------------------------------------
+
+using namespace tpmg;
+
+namespace {
+
+tpmg_status net_fail(tpmg_net *net, tpmg_status s, const std::string &msg)
+{
+    if (net) net->err = msg;
+    return s;
+}
+
+#define NCU(call)                                                                                 \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return net_fail(net, e_ == cudaErrorMemoryAllocation ? TPMG_ERR_OOM : TPMG_ERR_CUDA,  \
+                            std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+    } while (0)
+
+constexpr long kMaxRows = 64L * 65535L;   // rows of one pass (grid.y limit of the GEMM)
+
+// workspace floats per row: a_1..a_3 (3 h), y (out), two gradient buffers (2 max(h, out))
+long ws_per_row(const tpmg_net *net)
+{
+    const long h = net->sizes[1], out = net->sizes[4];
+    return 3 * h + out + 2 * std::max(h, out);
+}
+
+tpmg_status ensure_ws(tpmg_net *net, long rows, bool training)
+{
+    if (rows > net->ws_rows) {
+        if (net->ws) cudaFree(net->ws);
+        net->ws = nullptr;
+        net->ws_rows = 0;
+        NCU(cudaMalloc(&net->ws, sizeof(float) * (size_t)rows * ws_per_row(net)));
+        net->ws_rows = rows;
+    }
+    if (training) {
+        // split-K slices of the largest weight gradient; chunks of >= 256 rows
+        const int splits = (int)std::min<long>(64, std::max<long>(1, rows / 256));
+        size_t need = 0;
+        for (int l = 0; l < 4; ++l) need = std::max(need, (size_t)net->sizes[l] * net->sizes[l + 1]);
+        need = need * splits + (size_t)splits * std::max(net->sizes[1], net->sizes[4]);
+        if (need > net->split_cap) {
+            if (net->split) cudaFree(net->split);
+            net->split = nullptr;
+            net->split_cap = 0;
+            NCU(cudaMalloc(&net->split, sizeof(float) * need));
+            net->split_cap = need;
+        }
+    }
+    return TPMG_OK;
+}
+
+// forward pass into the workspace: a_l at ws + (l-1) rows h (l = 1..3), y after them
+tpmg_status forward_ws(tpmg_net *net, const float *x, long rows, float **acts, float **y)
+{
+    const long h = net->sizes[1];
+    float *a = net->ws;
+    acts[0] = const_cast<float *>(x);
+    for (int l = 1; l < 4; ++l) acts[l] = a + (size_t)(l - 1) * rows * h;
+    *y = a + (size_t)3 * rows * h;
+    const NetView v = net_view(net);
+    for (int l = 0; l < 4; ++l) NCU(launch_net_layer(net->stream, v, l, acts[l], rows, l < 3 ? acts[l + 1] : *y));
+    return TPMG_OK;
+}
+
+// loss and gradient (parameter layout) into net->grad / out; the loss stays on the device
+tpmg_status backward_ws(tpmg_net *net, const float *x, const float *t, long rows, float *gout)
+{
+    float *acts[4], *y;
+    tpmg_status st = forward_ws(net, x, rows, acts, &y);
+    if (st != TPMG_OK) return st;
+    const long h = net->sizes[1], out = net->sizes[4];
+    float *g0 = y + (size_t)rows * out, *g1 = g0 + (size_t)rows * std::max(h, out);
+    const long n = rows * out;
+    k_mse<<<kLossBlocks, 256, 0, net->stream>>>(y, t, n, g0, net->d_part);
+    NCU(cudaGetLastError());
+    k_loss_finish<<<1, 32, 0, net->stream>>>(net->d_part, kLossBlocks, n, net->d_loss);
+    NCU(cudaGetLastError());
+    const int splits = (int)std::min<long>(64, std::max<long>(1, rows / 256));
+    const NetView v = net_view(net);
+    float *g = g0, *gn = g1;
+    for (int l = 3; l >= 0; --l) {
+        const int in = net->sizes[l], o = net->sizes[l + 1];
+        // dW_l = G_l^T a_{l-1}: split-K over the rows, then the slices summed in order
+        NCU((gemm<true, false, float, EPI_NONE>(net->stream, o, in, (int)rows, splits, g, o, acts[l], in, net->split, in)));
+        int chunk = (int)((rows + splits - 1) / splits);
+        chunk = std::max(GBK, (chunk + GBK - 1) / GBK * GBK);
+        const int S = (int)((rows + chunk - 1) / chunk);
+        const long nw = (long)o * in;
+        k_sum_slices<<<grid_1d(nw, 256, sm_count_of_current()), 256, 0, net->stream>>>(net->split, S, nw,
+                                                                                     gout + net->off_w[l]);
+        NCU(cudaGetLastError());
+        // db_l = column sums of G_l (same row chunks)
+        float *cs = net->split + (size_t)S * nw;
+        k_colsum<<<dim3((o + 31) / 32, S), 256, 0, net->stream>>>(g, (int)rows, o, chunk, cs);
+        NCU(cudaGetLastError());
+        k_sum_slices<<<1, 256, 0, net->stream>>>(cs, S, o, gout + net->off_b[l]);
+        NCU(cudaGetLastError());
+        if (l > 0) {
+            // G_{l-1} = (G_l W_l) * [a_{l-1} > 0]
+            NCU((gemm<false, false, uint16_t, EPI_MASK>(net->stream, (int)rows, in, o, 1, g, o, v.w[l], in, gn, in,
+                                                          nullptr, acts[l], in)));
+            std::swap(g, gn);
+        }
+    }
+    return TPMG_OK;
+}
+
+tpmg_status check_rows(tpmg_net *net, const void *x, const void *p2, long rows)
+{
+    if (!x || !p2) return net_fail(net, TPMG_ERR_INVALID_ARG, "NULL pointer");
+    if (rows < 1 || rows > kMaxRows) return net_fail(net, TPMG_ERR_INVALID_ARG, "rows must be in 1..4194240");
+    return TPMG_OK;
+}
+
+tpmg_status read_loss(tpmg_net *net, double *h_loss)
+{
+    if (!h_loss) return TPMG_OK;
+    NCU(cudaMemcpyAsync(net->h_loss, net->d_loss, sizeof(double), cudaMemcpyDeviceToHost, net->stream));
+    NCU(cudaStreamSynchronize(net->stream));
+    *h_loss = *net->h_loss;
+    return TPMG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tpmg_status tpmg_net_create(int n_r, int hidden, void *cuda_stream, tpmg_net **out)
+{
+    if (!out || n_r < 1 || n_r > 1024 || hidden < 1 || hidden > 1024) return TPMG_ERR_INVALID_ARG;
+    tpmg_net *net = new (std::nothrow) tpmg_net();
+    if (!net) return TPMG_ERR_OOM;
+    net->stream = static_cast<cudaStream_t>(cuda_stream);
+    const int sz[5] = {2 * n_r, hidden, hidden, hidden, n_r};
+    size_t off = 0;
+    for (int l = 0; l < 5; ++l) net->sizes[l] = sz[l];
+    for (int l = 0; l < 4; ++l) {
+        net->off_w[l] = off;
+        off += (size_t)sz[l] * sz[l + 1];
+        net->off_b[l] = off;
+        off += sz[l + 1];
+    }
+    net->n_params = off;
+    const size_t n = off;
+    cudaError_t e = cudaMalloc(&net->master, n * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&net->grad, n * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&net->adam_m, n * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&net->adam_v, n * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&net->wbf, n * sizeof(uint16_t));
+    if (e == cudaSuccess) e = cudaMalloc(&net->d_part, kLossBlocks * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&net->d_loss, sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&net->h_loss, sizeof(double));
+    if (e == cudaSuccess) e = cudaMemsetAsync(net->master, 0, n * sizeof(float), net->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(net->grad, 0, n * sizeof(float), net->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(net->adam_m, 0, n * sizeof(float), net->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(net->adam_v, 0, n * sizeof(float), net->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(net->wbf, 0, n * sizeof(uint16_t), net->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(net->stream);
+    if (e != cudaSuccess) {
+        tpmg_net_destroy(net);
+        return e == cudaErrorMemoryAllocation ? TPMG_ERR_OOM : TPMG_ERR_CUDA;
+    }
+    *out = net;
+    return TPMG_OK;
+}
+
+size_t tpmg_net_n_params(const tpmg_net *net) { return net ? net->n_params : 0; }
+
+tpmg_status tpmg_net_set_params(tpmg_net *net, const float *h_params)
+{
+    if (!net || !h_params) return net_fail(net, TPMG_ERR_INVALID_ARG, "NULL pointer");
+    const size_t n = net->n_params;
+    NCU(cudaMemcpyAsync(net->master, h_params, n * sizeof(float), cudaMemcpyHostToDevice, net->stream));
+    NCU(cudaMemsetAsync(net->adam_m, 0, n * sizeof(float), net->stream));
+    NCU(cudaMemsetAsync(net->adam_v, 0, n * sizeof(float), net->stream));
+    k_round_bf16<<<grid_1d((long)n, 256, sm_count_of_current()), 256, 0, net->stream>>>((long)n, net->master, net->wbf);
+    NCU(cudaGetLastError());
+    NCU(cudaStreamSynchronize(net->stream));
+    net->step = 0;
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_net_get_params(tpmg_net *net, float *h_params)
+{
+    if (!net || !h_params) return net_fail(net, TPMG_ERR_INVALID_ARG, "NULL pointer");
+    NCU(cudaMemcpyAsync(h_params, net->master, net->n_params * sizeof(float), cudaMemcpyDeviceToHost, net->stream));
+    NCU(cudaStreamSynchronize(net->stream));
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_net_forward(tpmg_net *net, const float *d_x, long rows, float *d_y)
+{
+    if (!net) return TPMG_ERR_INVALID_ARG;
+    tpmg_status st = check_rows(net, d_x, d_y, rows);
+    if (st != TPMG_OK || (st = ensure_ws(net, rows, false)) != TPMG_OK) return st;
+    float *acts[4], *y;
+    if ((st = forward_ws(net, d_x, rows, acts, &y)) != TPMG_OK) return st;
+    NCU(cudaMemcpyAsync(d_y, y, sizeof(float) * rows * net->sizes[4], cudaMemcpyDeviceToDevice, net->stream));
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_net_gradients(tpmg_net *net, const float *d_x, const float *d_t, long rows, float *d_grad,
+                               double *h_loss)
+{
+    if (!net) return TPMG_ERR_INVALID_ARG;
+    tpmg_status st = check_rows(net, d_x, d_t, rows);
+    if (st == TPMG_OK && !d_grad) st = net_fail(net, TPMG_ERR_INVALID_ARG, "NULL pointer");
+    if (st != TPMG_OK || (st = ensure_ws(net, rows, true)) != TPMG_OK) return st;
+    if ((st = backward_ws(net, d_x, d_t, rows, d_grad)) != TPMG_OK) return st;
+    return read_loss(net, h_loss);
+}
+
+tpmg_status tpmg_net_train_step(tpmg_net *net, const float *d_x, const float *d_t, long rows, float lr,
+                                double *h_loss)
+{
+    if (!net) return TPMG_ERR_INVALID_ARG;
+    if (!(lr >= 0.f) || !std::isfinite(lr)) return net_fail(net, TPMG_ERR_INVALID_ARG, "lr must be finite and >= 0");
+    tpmg_status st = check_rows(net, d_x, d_t, rows);
+    if (st != TPMG_OK || (st = ensure_ws(net, rows, true)) != TPMG_OK) return st;
+    if ((st = backward_ws(net, d_x, d_t, rows, net->grad)) != TPMG_OK) return st;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    ++net->step;
+    const float c1 = (float)(1.0 - std::pow(0.9, (double)net->step));
+    const float c2 = (float)(1.0 - std::pow(0.999, (double)net->step));
+    const long n = (long)net->n_params;
+    k_adam<<<grid_1d(n, 256, sm_count_of_current()), 256, 0, net->stream>>>(n, net->master, net->adam_m, net->adam_v,
+                                                                          net->grad, net->wbf, lr, b1, b2, eps, c1, c2);
+    NCU(cudaGetLastError());
+    return read_loss(net, h_loss);
+}
+
+const char *tpmg_net_last_error(const tpmg_net *net) { return net ? net->err.c_str() : ""; }
+
+void tpmg_net_destroy(tpmg_net *net)
+{
+    if (!net) return;
+    if (net->stream) cudaStreamSynchronize(net->stream);
+    else cudaDeviceSynchronize();
+    cudaFree(net->master);
+    cudaFree(net->grad);
+    cudaFree(net->adam_m);
+    cudaFree(net->adam_v);
+    cudaFree(net->wbf);
+    cudaFree(net->ws);
+    cudaFree(net->split);
+    cudaFree(net->d_part);
+    cudaFree(net->d_loss);
+    if (net->h_loss) cudaFreeHost(net->h_loss);
+    delete net;
+}
+
+}  // extern "C"

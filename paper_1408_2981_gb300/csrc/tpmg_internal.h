@@ -3,10 +3,13 @@
 
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 #include <string>
 #include <vector>
 
 #include "../../include/tpmg.h"
+#include "../../include/tpmg_learned.h"
 
 namespace tpmg {
 
@@ -110,6 +113,8 @@ struct Scalars {            // PCG scalars kept in device memory
     double rzc;             // <r_{k+1}, z_k> (flexible CG)
     int flag;               // bit 0: p.Ap <= 0 or non-finite; bit 1: non-finite residual
     int it;                 // iterations done by the device-side loop
+    double ff;              // ||f||^2 (learned solve: the stop test is relative to ||f||)
+    int info;               // learned solve: bit 0 initial guess kept, bit 1 rejected (u_0 = 0)
 };
 
 // Control of a PCG loop that runs on the device (a CUDA graph with a
@@ -176,6 +181,32 @@ cudaError_t noalloc_scratch(int device, double **ptr);
 enum FinishWhat { FIN_RR0 = 0, FIN_ALPHA = 1, FIN_RR = 2, FIN_BETA = 3, FIN_RZ0 = 4, FIN_RZC = 5, FIN_BETA_PR = 6,
                   // device-side loop: RR0 and RR also drive the loop condition; BETA and
                   // BETA_PR give beta = 0 on the first pass (p is cleared before the loop)
-                  FIN_LOOP_RR0 = 7, FIN_LOOP_RR = 8, FIN_LOOP_BETA = 9, FIN_LOOP_BETA_PR = 10 };
+                  FIN_LOOP_RR0 = 7, FIN_LOOP_RR = 8, FIN_LOOP_BETA = 9, FIN_LOOP_BETA_PR = 10,
+                  // learned solve: partials [0, n) of ||r_0||^2 and [n, 2n) of ||f||^2; the
+                  // initial guess is rejected unless ||r_0|| < ||f||; rr0 = ||f||^2
+                  FIN_LOOP_RR0F = 11 };
+
+// learned.cu: the network of the learned form (tpmg_learned.h) -----------------
+struct NetView {            // device pointers of a network's weights
+    int sizes[5];           // 2 n_r, h, h, h, n_r
+    const uint16_t *w[4];   // bfloat16 W_l [sizes[l+1]][sizes[l]]
+    const float *b[4];      // FP32 b_l
+};
+NetView net_view(const tpmg_net *net);
+// y [rows][sizes[l+1]] = act(x W_l^T + b_l), ReLU for l < 3
+cudaError_t launch_net_layer(cudaStream_t s, const NetView &v, int l, const float *x, long rows, float *y);
+// partials [n_part] of the squared point values of f on lv; the finish writes s
+template <typename TF>
+cudaError_t launch_net_scale(const Launch &L, const LevelDev &lv, const VertDev &vert, const TF *f, double *partials,
+                             int n_part);
+cudaError_t launch_net_scale_finish(const Launch &L, const LevelDev &lv, const double *partials, int n_part, double *s);
+template <typename TF>
+cudaError_t launch_net_features(const Launch &L, const LevelDev &lv, const VertDev &vert, const TF *f, const int *cells,
+                                long rows, const double *s, float *X);
+cudaError_t launch_net_targets(const Launch &L, const double *u, const int *cells, long rows, const double *s, float *t);
+template <typename TO>
+cudaError_t launch_net_output(const Launch &L, const float *y, long n, const double *s, TO *u);
+cudaError_t launch_judge_reset(const Launch &L, const Scalars *sc, long n, const double *f, double *u, double *r);
+cudaError_t launch_to_f32(const Launch &L, long n, const double *x, float *y);
 
 }  // namespace tpmg

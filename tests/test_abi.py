@@ -73,3 +73,40 @@ def test_status_strings(lib):
     assert lib.tpmg_status_string(0) == b"TPMG_OK"
     assert lib.tpmg_status_string(5) == b"TPMG_ERR_BREAKDOWN"
     assert lib.tpmg_status_string(99) == b"TPMG_UNKNOWN_STATUS"
+
+
+def declared_learned_functions():
+    txt = open(os.path.join(ROOT, "include", "tpmg_learned.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(tpmg_[a-z_]+)\s*\(", txt)))
+
+
+def test_learned_header_and_binding_agree(lib):
+    assert declared_learned_functions() == sorted(binding.EXPORTS_LEARNED)
+    for name in declared_learned_functions():
+        assert hasattr(lib, name), name
+
+
+def test_kernel_classes_follow_the_header_enum():
+    txt = open(os.path.join(ROOT, "include", "tpmg.h")).read()
+    names = re.findall(r"TPMG_K_([A-Z]+) = (\d+)", txt)
+    order = [n.lower() for n, v in sorted(((n, int(v)) for n, v in names if n != "COUNT"), key=lambda t: t[1])]
+    assert order == binding.KERNEL_CLASSES
+
+
+def test_learned_entry_points_reject_bad_arguments_on_host(lib):
+    h = ctypes.c_void_p()
+    assert lib.tpmg_net_create(0, 64, None, ctypes.byref(h)) == binding.TPMG_ERR_INVALID_ARG
+    assert lib.tpmg_net_create(16, 0, None, ctypes.byref(h)) == binding.TPMG_ERR_INVALID_ARG
+    assert lib.tpmg_net_create(16, 64, None, None) == binding.TPMG_ERR_INVALID_ARG
+    assert not h.value
+    assert lib.tpmg_net_n_params(None) == 0
+    assert lib.tpmg_net_forward(None, None, 1, None) == binding.TPMG_ERR_INVALID_ARG
+    assert lib.tpmg_net_train_step(None, None, None, 1, 1e-3, None) == binding.TPMG_ERR_INVALID_ARG
+    assert lib.tpmg_attach_net(None, 0, None) == binding.TPMG_ERR_INVALID_ARG
+    assert lib.tpmg_record_coarse(None, None, 0) == binding.TPMG_ERR_INVALID_ARG
+    assert lib.tpmg_coarse_solve(None, None, None, 1) == binding.TPMG_ERR_INVALID_ARG
+    it, rel = ctypes.c_int(), ctypes.c_double()
+    assert lib.tpmg_solve_learned(None, None, None, 1e-5, 10, ctypes.byref(it), ctypes.byref(rel), None, None,
+                                  None) == binding.TPMG_ERR_INVALID_ARG
+    lib.tpmg_net_destroy(None)

@@ -54,3 +54,90 @@ def test_forward_is_the_composition_of_layers():
     np.testing.assert_allclose(y, x @ W.T + b, rtol=1e-15)
     y2, cache = mlp.forward([(W, b), (np.eye(3), np.zeros(3))], x, bf16_weights=False)
     np.testing.assert_allclose(y2, np.maximum(x @ W.T + b, 0.0), rtol=1e-15)
+
+
+def _level(o, level):
+    grid = o.grid(o.level_ref(level))
+    return grid["area"], o.vertical()["vol"], grid["nbr"], grid["g"]
+
+
+def test_features_of_constant_point_values():
+    """p = c everywhere: s = |c| and every input is sign(c)."""
+    import oracle
+    o = oracle.Oracle(refinement=2, n_levels=2, n_r=5, grading=1.1)
+    area, vol, nbr, g = _level(o, 1)
+    for c in (2.5, -0.75):
+        f = c * np.outer(area, vol).reshape(-1)
+        x, s = mlp.features(f, area, vol, nbr, g)
+        assert abs(s - abs(c)) <= 1e-15 * abs(c)
+        np.testing.assert_allclose(x, np.sign(c), rtol=1e-14)
+
+
+def test_features_of_a_single_cell_pick_the_flux_weights():
+    """A unit point value in one cell: its own input is 1/s at its level, and each
+    edge neighbour sees it in the mean block with weight g_e / sum g of the
+    neighbour's edge that faces it; every other input is zero."""
+    import oracle
+    o = oracle.Oracle(refinement=2, n_levels=2, n_r=4, grading=1.2)
+    area, vol, nbr, g = _level(o, 1)
+    n, n_r = area.shape[0], vol.shape[0]
+    T0, k0 = 17, 2
+    p = np.zeros((n, n_r))
+    p[T0, k0] = 1.0
+    f = (p * np.outer(area, vol)).reshape(-1)
+    x, s = mlp.features(f, area, vol, nbr, g)
+    assert abs(s - 1.0 / np.sqrt(n * n_r)) < 1e-15
+    expect = np.zeros((n, 2 * n_r))
+    expect[T0, k0] = 1.0 / s
+    for T in range(n):
+        for e in range(3):
+            if nbr[T, e] == T0:
+                expect[T, n_r + k0] += g[T, e] / g[T].sum() / s
+    assert np.count_nonzero(expect[:, n_r:]) == 3
+    np.testing.assert_allclose(x, expect, rtol=1e-13, atol=1e-13)
+
+
+def test_features_are_odd_and_scale_free():
+    import oracle
+    o = oracle.Oracle(refinement=2, n_levels=2, n_r=3)
+    area, vol, nbr, g = _level(o, 1)
+    f = np.random.default_rng(5).uniform(-1, 1, area.shape[0] * 3)
+    x, s = mlp.features(f, area, vol, nbr, g)
+    x2, s2 = mlp.features(-4.0 * f, area, vol, nbr, g)
+    assert abs(s2 - 4.0 * s) <= 1e-14 * s2
+    np.testing.assert_allclose(x2, -x, rtol=1e-13, atol=1e-15)
+    x0, s0 = mlp.features(0.0 * f, area, vol, nbr, g)
+    assert s0 == 0.0 and not np.any(x0)
+
+
+def test_adam_first_step_is_the_sign_of_the_gradient():
+    """With zero moments, bias correction makes the first Adam step
+    lr g / (|g| + eps) = lr sign(g) for |g| >> eps."""
+    p = [np.array([1.0, -2.0, 0.5])]
+    g = [np.array([3.0, -0.01, 1e-3])]
+    z = [np.zeros(3)]
+    p1, m1, v1 = mlp.adam_step(p, g, z, z, t=1, lr=0.1)
+    np.testing.assert_allclose(p1[0], p[0] - 0.1 * g[0] / (np.abs(g[0]) + 1e-8), rtol=1e-15)
+    np.testing.assert_allclose(p1[0], p[0] - 0.1 * np.sign(g[0]), rtol=1e-5)
+    np.testing.assert_allclose(m1[0], 0.1 * g[0], rtol=1e-15)
+    np.testing.assert_allclose(v1[0], 0.001 * g[0] ** 2, rtol=1e-12)
+
+
+def test_oracle_coarse_solve_hook():
+    """The V-cycle's coarsest-level solve replaced through the hook: a zero
+    solve equals nu_coarse = 0, and the exact dense solve equals converged
+    sweeps."""
+    import oracle
+    kw = dict(refinement=3, n_levels=2, n_r=6, grading=1.1, courant_c=8.0)
+    r = np.random.default_rng(6).uniform(-1, 1, 1280 * 6)
+    o0 = oracle.Oracle(nu_coarse=0, **kw)
+    o = oracle.Oracle(**kw)
+    o.set_coarse_solve(lambda f: np.zeros_like(f))
+    np.testing.assert_array_equal(o.vcycle(r), o0.vcycle(r))
+    A0 = o.dense_operator(level=0)
+    o.set_coarse_solve(lambda f: np.linalg.solve(A0, f))
+    o_many = oracle.Oracle(nu_coarse=40, **kw)
+    z, z_ref = o.vcycle(r), o_many.vcycle(r)
+    assert np.max(np.abs(z - z_ref)) <= 1e-11 * np.max(np.abs(z_ref))
+    o.set_coarse_solve(None)
+    np.testing.assert_array_equal(o.vcycle(r), oracle.Oracle(**kw).vcycle(r))
