@@ -71,6 +71,17 @@ WORKLOADS = {
         params=dict(refinement=7, n_levels=6, n_r=128, grading=1.05, courant_c=8.0, nu_pre=2, nu_post=2, nu_coarse=1),
         rhs="uniform", seed=2981003,
         text="as 327680x128-mixed, everything in FP64 (plain TPMG-PCG on the same grid)"),
+    "327680x128-learned": dict(
+        params=dict(refinement=7, n_levels=6, n_r=128, grading=1.05, courant_c=8.0, nu_pre=2, nu_post=2, nu_coarse=1,
+                    **MIXED),
+        learned=dict(pairs=2000, cells_per_pair=512, coarse_per_pair=4, hidden=64, l_max=16, train_steps=4000,
+                     batch=4096, lr=2e-3),
+        rhs="smooth", seed=2981005,
+        text="learned form on the 327680x128-mixed grid: a 4-layer per-column network (2 n_r -> 64 -> 64 -> 64 -> "
+             "n_r, BF16 weights, FP32 accumulate) as coarsest-level solve and as warm start (+ one line "
+             "relaxation), trained by the library's kernels on 2000 seeded (f, u) pairs from plain TPMG-PCG "
+             "(smooth f: spherical harmonics up to degree 16 x vertical cosines); flexible CG, "
+             "||r|| <= 1e-5 ||f|| on held-out smooth right-hand sides"),
     "batch48": dict(
         batch=48, seed=2981004,
         text="48 independent solves in one graph launch: refinement drawn from {4,5,6}, vertical levels from "
@@ -532,6 +543,209 @@ def run_batch(args, wl):
     return 0
 
 
+def run_learned(args, wl):
+    """The learned form: training data from plain solves, training of both
+    networks (outside the timed region, reported), then K timed learned solves
+    of held-out right-hand sides beside K plain mixed-precision solves of the
+    same right-hand sides (same context, same stop test ||r|| <= rtol ||f||)."""
+    import torch
+
+    from paper_1408_2981_gb300 import binding, build as _build, learned
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    _build.build()
+    stream = torch.cuda.current_stream()
+    cfg = dict(wl["learned"])
+    if args.pairs:
+        cfg["pairs"] = args.pairs
+    seed = wl["seed"] + 7919 * rank
+    t_setup = time.perf_counter()
+    data_solver = binding.Solver(stream=stream, graphs=0, **wl["params"])
+    fields = learned.SmoothFields(data_solver, l_max=cfg["l_max"])
+    data = learned.generate(data_solver, fields, n_pairs=cfg["pairs"], seed=seed + 1000,
+                            cells_per_pair=cfg["cells_per_pair"], coarse_per_pair=cfg["coarse_per_pair"])
+    data_solver.close()
+    nets, train_out = {}, {}
+    for name, role, x, t in (("warm", binding.TPMG_NET_WARM, data["xw"], data["tw"]),
+                             ("coarse", binding.TPMG_NET_COARSE, data["xc"], data["tc"])):
+        net = binding.Net(wl["params"]["n_r"], cfg["hidden"], stream=stream)
+        net.set_params(learned.init_params(net.sizes, seed + 11 * role + 3))
+        out = learned.train(net, x, t, steps=cfg["train_steps"], seed=seed + 13 * role + 5, batch=cfg["batch"],
+                            lr=cfg["lr"])
+        nets[name] = net
+        train_out[name] = {"rows": int(x.shape[0]), "loss_first": out["history"][0][1], "loss_final": out["final"],
+                           "target_mean_square": float(t.double().pow(2).mean()), "seconds": out["seconds"]}
+    del data
+    torch.cuda.empty_cache()
+    s = binding.Solver(stream=stream, **wl["params"])
+    N = s.N
+    s.attach_net(binding.TPMG_NET_WARM, nets["warm"])
+    s.attach_net(binding.TPMG_NET_COARSE, nets["coarse"])
+    setup_s = time.perf_counter() - t_setup
+    fs = [fields.field(seed + 10_000_000 + k) for k in range(args.steps)]   # held out
+    u = torch.zeros(N, dtype=torch.float64, device="cuda")
+    l2 = torch.cuda.get_device_properties(local).L2_cache_size
+    flush = torch.empty(max(2 * l2, 256 << 20) // 4, dtype=torch.float32, device="cuda")
+    # one right-hand-side buffer: the solve graphs are captured for fixed vectors
+    f_buf = torch.empty(N, dtype=torch.float64, device="cuda")
+    for w in range(args.warmup):
+        f_buf.copy_(fs[w % len(fs)])
+        u.zero_()
+        s.solve_learned(f_buf, u, rtol=args.rtol, max_iter=200)
+        u.zero_()
+        s.solve(f_buf, u, rtol=args.rtol, max_iter=200)
+    torch.cuda.synchronize()
+
+    def timed(learned_arm: bool):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in fs]
+        its, rels, infos, fbs, launches = [], [], [], [], 0
+        barrier(world)
+        torch.cuda.synchronize()
+        for k, f in enumerate(fs):
+            f_buf.copy_(f)
+            flush.fill_(float(k))
+            evs[k][0].record(stream)
+            u.zero_()
+            if learned_arm:
+                st, it, rel, info, fb, nl = s.solve_learned(f_buf, u, rtol=args.rtol, max_iter=200)
+                infos.append(info)
+                fbs.append(fb)
+                launches += nl
+            else:
+                st, it, rel, _ = s.solve(f_buf, u, rtol=args.rtol, max_iter=200)
+            evs[k][1].record(stream)
+            its.append(it)
+            rels.append(rel)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        return ms, its, rels, infos, fbs, launches
+
+    def attach(coarse, warm):
+        s.attach_net(binding.TPMG_NET_COARSE, coarse)
+        s.attach_net(binding.TPMG_NET_WARM, warm)
+        f_buf.copy_(fs[0])
+        u.zero_()
+        s.solve_learned(f_buf, u, rtol=args.rtol, max_iter=200)   # capture the solve graph, untimed
+
+    # the learned form (both networks) is the headline arm; each network alone and
+    # plain TPMG-PCG are timed on the same right-hand sides
+    arms = {}
+    for name, coarse, warm in (("warm", None, nets["warm"]), ("coarse", nets["coarse"], None)):
+        attach(coarse, warm)
+        ms_a, its_a, _, infos_a, fbs_a, _ = timed(True)
+        arms[name] = {"value": aggregate_value(N, len(fs), world, ms_a)[0], "ms_per_step": ms_a / len(fs),
+                      "iters": its_a, "info": infos_a, "fallback_iters": fbs_a}
+    attach(nets["coarse"], nets["warm"])
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms_l, its_l, rels_l, infos, fbs, launches = timed(True)
+    clk = clocks.stop()
+    ms_p, its_p, rels_p, _, _, _ = timed(False)
+    value, t_ms = aggregate_value(N, len(fs), world, ms_l)
+    plain_value, _ = aggregate_value(N, len(fs), world, ms_p)
+
+    # initial residual of the warm start alone (network + one line relaxation), held-out f
+    r0s = []
+    s.attach_net(binding.TPMG_NET_COARSE, None)
+    for f in fs[:3]:
+        f_buf.copy_(f)
+        u.zero_()
+        s.solve_learned(f_buf, u, rtol=1.0, max_iter=1)
+        r = torch.empty_like(f)
+        s.apply_operator(u, r)
+        r0s.append(float(torch.linalg.norm(f - r) / torch.linalg.norm(f)))
+    s.attach_net(binding.TPMG_NET_COARSE, nets["coarse"])
+
+    # the network kernels: warm-start forward over every fine column, timed alone
+    x = torch.empty((s.n_cells, 2 * s.n_r), dtype=torch.float32, device="cuda")
+    y = torch.empty((s.n_cells, s.n_r), dtype=torch.float32, device="cuda")
+    s.net_features(s.n_levels - 1, fs[0], x)
+    nets["warm"].forward(x, y)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(5):
+        nets["warm"].forward(x, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / 5
+    sizes = nets["warm"].sizes
+    fwd_flops = 2.0 * s.n_cells * sum(i * o for i, o in zip(sizes[:-1], sizes[1:]))
+
+    # end to end with host buffers: f in, learned solve, u out
+    f_host = torch.empty(N, dtype=torch.float64, pin_memory=True).copy_(fs[0])
+    u_host = torch.empty(N, dtype=torch.float64, pin_memory=True)
+    f_dev = f_buf
+    f_dev.copy_(fs[0])
+    u.zero_()
+    s.solve_learned(f_dev, u, rtol=args.rtol, max_iter=200)   # re-capture after the re-attachment, untimed
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(len(fs), 5))
+    for _ in range(e2e_steps):
+        f_dev.copy_(f_host, non_blocking=True)
+        u.zero_()
+        s.solve_learned(f_dev, u, rtol=args.rtol, max_iter=200)
+        u_host.copy_(u, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0), world)
+
+    # roofline of the dominant kernel (the line relaxation) from a host-driven
+    # plain solve of the same context with relax timed
+    peaks = load_peaks()
+    s.profile(classes=("relax", "net"))
+    u.zero_()
+    s.solve(fs[0], u, rtol=args.rtol, max_iter=200)
+    z = torch.empty_like(u)
+    s.vcycle_learned(fs[0], z)
+    prof = s.profile_read()
+    d = prof["relax"]
+    nbytes = PER_UNIT[1]["relax"][1] * d["units"]
+    roof = {"bound": "hbm", "achieved": nbytes / (d["ms"] / 1e3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "peak_source": f"{peaks['source']} HBM copy bandwidth",
+            "kernel": "relax (FP32/BF16), from a host-driven plain solve + one learned V-cycle of the same context",
+            "avg_launch_us": 1e3 * d["ms"] / max(1, d["timed"]), "traffic": None,
+            "algorithmic_bytes_per_launch": nbytes / max(1, d["launches"])}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v_o, sample, _ = time_oracle(dict(wl, rhs="uniform"), min_seconds=10.0, max_solves=1, rtol=args.rtol,
+                                     iters_hint=its_p[-1])
+        cpu = {"value": v_o, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
+               "sample": sample + " (plain oracle PCG; the per-iteration cost does not depend on the RHS values)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world, "steps": len(fs),
+                "warmup": args.warmup, "ms_per_step": t_ms / len(fs), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64+bf16w", "data": "synthetic",
+                "config": {"workload": wl["text"], "n_unknowns": N, "parallelism": f"replicas{world}",
+                           "pairs": cfg["pairs"], "stop": "||r|| <= rtol ||f||",
+                           "l2": "flushed between steps (write of 2x L2 outside the timed events)"},
+                "e2e": {"value": N * e2e_steps * world / (e2e_ms / 1e3), "unit": "unknowns/s",
+                        "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N},
+                "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+                "learned": {"iters": its_l, "rel_resid": rels_l, "info": infos, "fallback_iters": fbs,
+                            "warm_start_rel_resid": r0s},
+                "plain": {"value": plain_value, "iters": its_p, "rel_resid": rels_p, "ms_per_step": ms_p / len(fs)},
+                "arms": arms,
+                "speedup_vs_plain": value / plain_value,
+                "training": train_out, "setup_seconds": setup_s,
+                "net_forward": {"rows": s.n_cells, "ms": fwd_ms, "tflops": fwd_flops / (fwd_ms / 1e3) / 1e12},
+                "net_kernels_in_learned_vcycle": {"launches": prof["net"]["launches"], "ms": prof["net"]["ms"]}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -541,6 +755,7 @@ def main(argv=None):
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="81920x64")
     ap.add_argument("--rtol", type=float, default=1e-5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--pairs", type=int, default=None, help="learned workload: training pairs (default 2000)")
     ap.add_argument("--iters-hint", type=int, default=None,
                     help="reference arm on workloads sampled by one iteration: iterations of a full solve")
     args = ap.parse_args(argv)
@@ -555,6 +770,8 @@ def main(argv=None):
         return run_reference(args, wl)
     if "batch" in wl:
         return run_batch(args, wl)
+    if "learned" in wl:
+        return run_learned(args, wl)
     return run_tpmg(args, wl)
 
 

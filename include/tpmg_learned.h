@@ -6,7 +6,8 @@
  *
  *  - COARSE: the solve on the coarsest multigrid level of the V-cycle
  *    (Algorithm 1 applies nu_coarse line-relaxation sweeps there) is replaced
- *    by the network's prediction of the coarse solution;
+ *    by the network's prediction of the coarse solution followed by one
+ *    block-Jacobi line relaxation from it;
  *  - WARM: the initial guess of CG is the network's prediction of the solution
  *    from the right-hand side, followed by one block-Jacobi line relaxation
  *    (eq. BlockJacobi: the V-cycle's smoother) on the finest level.  The

@@ -264,8 +264,9 @@ class Oracle:
         self._lib.oracle_set_vcycle_bf16(self._h, 1 if on else 0)
 
     def set_coarse_solve(self, fn=None):
-        """Replace the V-cycle's coarsest-level solve by fn(f [n_cells * n_r]) -> u
-        (the learned form's network); None restores Algorithm 1's sweeps."""
+        """Replace the V-cycle's coarsest-level solve by the guess fn(f [n_cells *
+        n_r]) -> u (the learned form's network) followed by one block-Jacobi
+        line relaxation; None restores Algorithm 1's sweeps."""
         if fn is None:
             self._coarse_cb = None
             self._lib.oracle_set_coarse_solve(self._h, COARSE_SOLVE_FN())

@@ -357,8 +357,9 @@ static int dsatur_colour(ogrid *G)
 /* ------------------------------------------------------------------------- */
 /* Oracle context                                                              */
 /* ------------------------------------------------------------------------- */
-/* Coarsest-level solve supplied by the caller (the learned form's network):
- * u [n_cells * n_r] = solve(f [n_cells * n_r]). */
+/* Coarsest-level guess supplied by the caller (the learned form's network):
+ * u [n_cells * n_r] = guess(f [n_cells * n_r]); the V-cycle follows it with one
+ * block-Jacobi line relaxation (eq. BlockJacobi) on the coarsest level. */
 typedef void (*coarse_solve_fn)(int n_cells, int n_r, const double *f, double *u);
 
 typedef struct {
@@ -608,8 +609,12 @@ static void vcycle_level(octx *o, int l, const double *f, double *u)
     const ogrid *G = mg_grid(o, l);
     size_t N = (size_t)G->n_cells * o->n_r, i;
     if (l == 0) {
-        if (o->coarse_cb) o->coarse_cb(G->n_cells, o->n_r, f, u);
-        else smooth(o, l, f, u, o->nu_coarse, 0);
+        if (o->coarse_cb) {
+            o->coarse_cb(G->n_cells, o->n_r, f, u);
+            jacobi_sweep(o, l, f, u);
+        } else {
+            smooth(o, l, f, u, o->nu_coarse, 0);
+        }
         return;
     }
     smooth(o, l, f, u, o->nu_pre, +1);                       /* pre-smoothing    */
@@ -872,9 +877,9 @@ int oracle_vcycle(void *h, const double *r, double *z)
     return 0;
 }
 
-/* Replace the coarsest-level solve of the V-cycle by fn (NULL restores the
- * nu_coarse sweeps): the learned form, where a network predicts the coarse
- * solution. */
+/* Replace the coarsest-level solve of the V-cycle by fn followed by one
+ * block-Jacobi line relaxation (NULL restores the nu_coarse sweeps): the
+ * learned form, where a network predicts the coarse solution. */
 void oracle_set_coarse_solve(void *h, coarse_solve_fn fn) { ((octx *)h)->coarse_cb = fn; }
 
 /* Select the V-cycle of the mixed-precision form (on != 0) or the plain one. */

@@ -388,14 +388,15 @@ tpmg_status vcycle_mixed(tpmg_ctx *ctx, int l, const TF *f, float *u, float *scr
                 LCHK(run(ctx, TPMG_K_COPY, nunits, [&] { return launch_to_f64(L, (long)lv.n * p.n_r, f, dst); }));
                 ++ctx->rec_n;
             }
-            // learned form: the network's prediction replaces the coarsest-level solve
+            // learned form: the network's prediction and one block-Jacobi line
+            // relaxation from it replace the coarsest-level solve; the relaxation
+            // pass adds the result into u_fine (prolongation)
             if (ctx->net_coarse_on) {
-                tpmg_status st = net_infer<float, float>(ctx, TPMG_NET_COARSE, lv, f, u);
+                tpmg_status st = net_infer<float, float>(ctx, TPMG_NET_COARSE, lv, f, scratch);
                 if (st != TPMG_OK) return st;
-                if (u_fine) {
-                    const LevelDev &fl = ctx->lv[1];
-                    LCHK(run(ctx, TPMG_K_PROLONG, (double)fl.n * p.n_r, [&] { return launch_prolong_add32(L, fl, u, u_fine); }));
-                }
+                LCHK(run(ctx, TPMG_K_RELAX, nunits, [&] {
+                    return launch_relax32<float>(L, lv, PASS_NORMAL, 0, lv.n_tasks, relax, f, scratch, u, u_fine, nullptr);
+                }));
                 return TPMG_OK;
             }
         }
@@ -818,6 +819,17 @@ tpmg_status upload_level(tpmg_ctx *ctx, int l)
     CU(cudaMemcpyAsync(D.nbr, nb.data(), n * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(D.g, g.data(), n * sizeof(dbl4), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(D.area, H.area.data(), n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    std::vector<float> ia(H.n);
+    std::vector<float4> wn(H.n);
+    for (int T = 0; T < H.n; ++T) {
+        ia[T] = (float)(1.0 / H.area[T]);
+        const double sg = g[T].w;
+        wn[T] = make_float4((float)(g[T].x / sg), (float)(g[T].y / sg), (float)(g[T].z / sg), 0.f);
+    }
+    CU(dalloc(ctx, &D.iarea32, n));
+    CU(dalloc(ctx, &D.wnb32, n));
+    CU(cudaMemcpyAsync(D.iarea32, ia.data(), n * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(D.wnb32, wn.data(), n * sizeof(float4), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(D.task_cells, tasks.data(), tasks.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
     std::vector<int4> tnb(tasks.size(), make_int4(0, 0, 0, 0));
     std::vector<dbl4> tg(tasks.size(), dbl4{0.0, 0.0, 0.0, 0.0});
@@ -951,6 +963,14 @@ tpmg_status tpmg_setup(const tpmg_params *params, void *cuda_stream, tpmg_ctx **
         ctx->vert.vol = ctx->d_vert;
         ctx->vert.w = ctx->d_vert + n_r;
         ctx->vert.hr = ctx->d_vert + 2 * n_r + 1;
+        std::vector<float> iv(n_r);
+        for (int k = 0; k < n_r; ++k) iv[k] = (float)(1.0 / G.vol[k]);
+        float *d_iv = nullptr;
+        if (dalloc(ctx, &d_iv, n_r) != cudaSuccess) return bail(TPMG_ERR_OOM);
+        if (cudaMemcpyAsync(d_iv, iv.data(), n_r * sizeof(float), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
+            cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+            return bail(TPMG_ERR_CUDA);
+        ctx->vert.ivol32 = d_iv;
     }
     ctx->lv.assign(ctx->p.n_levels, LevelDev());
     for (int l = 0; l < ctx->p.n_levels; ++l) {

@@ -8,7 +8,7 @@
 // (Kingma & Ba, 2015); every step -- forward, loss, backward, update -- runs
 // in the kernels below.
 //
-// Features of a column T (on one multigrid level, vertical index k):
+// Features of a column T (on one multigrid level, vertical index k), in FP32:
 //   x_T[k]       = f_Tk / (|T| v_k) / s,
 //   x_T[n_r + k] = sum_e g_e f_{n_e k} / (|n_e| v_k) / (s sum_e g_e),
 // i.e. the right-hand side as point values (cell integral over cell volume)
@@ -231,21 +231,22 @@ __global__ void k_round_bf16(long n, const float *__restrict__ w, uint16_t *__re
 
 // ---- features -------------------------------------------------------------
 
-// partials of sum over the level of (f_Tk / (|T| v_k))^2
+// partials of sum over the level of (f_Tk / (|T| v_k))^2 (point values in
+// FP32, each thread's sum in FP32, the block's in double)
 template <typename TF>
-__global__ void __launch_bounds__(256) k_net_scale(const TF *__restrict__ f, const double *__restrict__ area,
-                                                   const double *__restrict__ vol, long N, int n_r,
+__global__ void __launch_bounds__(256) k_net_scale(const TF *__restrict__ f, const float *__restrict__ iarea,
+                                                   const float *__restrict__ ivol, long N, int n_r,
                                                    double *__restrict__ partials)
 {
-    double acc = 0.0;
+    float acc = 0.f;
     for (long i = blockIdx.x * 256L + threadIdx.x; i < N; i += (long)gridDim.x * 256) {
         const long T = i / n_r;
         const int k = (int)(i - T * n_r);
-        const double g = (double)f[i] / (area[T] * vol[k]);
-        acc = fma(g, g, acc);
+        const float p = (float)f[i] * iarea[T] * ivol[k];
+        acc = fmaf(p, p, acc);
     }
-    acc = block_sum_d<256>(acc);
-    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+    const double tot = block_sum_d<256>((double)acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
 }
 
 // s = sqrt(sum / N) (0 for a zero field)
@@ -257,27 +258,29 @@ __global__ void k_net_scale_finish(const double *__restrict__ partials, int np, 
     *s = sqrt(v / (double)N);
 }
 
+// inputs in FP32: point values p = f / (|T| v_k) of the column and the
+// flux-weighted mean over its edge neighbours, times 1 / s
 template <typename TF>
-__global__ void k_net_features(const TF *__restrict__ f, const double *__restrict__ area,
-                               const double *__restrict__ vol, const int4 *__restrict__ nbr,
-                               const dbl4 *__restrict__ gg, const int *__restrict__ cells, long rows, int n_r,
+__global__ void k_net_features(const TF *__restrict__ f, const float *__restrict__ iarea,
+                               const float *__restrict__ ivol, const int4 *__restrict__ nbr,
+                               const float4 *__restrict__ wnb, const int *__restrict__ cells, long rows, int n_r,
                                const double *__restrict__ s, float *__restrict__ X)
 {
     const double sv = *s;
-    const double inv = sv > 0.0 ? 1.0 / sv : 0.0;
+    const float inv = sv > 0.0 ? (float)(1.0 / sv) : 0.f;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < rows * n_r; i += (long)gridDim.x * blockDim.x) {
         const long j = i / n_r;
         const int k = (int)(i - j * n_r);
         const long T = cells ? cells[j] : j;
         const int4 nb = nbr[T];
-        const dbl4 w = gg[T];
-        const double vk = vol[k];
-        const double own = (double)f[T * n_r + k] / (area[T] * vk);
-        const double mean = (w.x * ((double)f[(long)nb.x * n_r + k] / area[nb.x]) +
-                             w.y * ((double)f[(long)nb.y * n_r + k] / area[nb.y]) +
-                             w.z * ((double)f[(long)nb.z * n_r + k] / area[nb.z])) / (w.w * vk);
-        X[j * 2 * n_r + k] = (float)(own * inv);
-        X[j * 2 * n_r + n_r + k] = (float)(mean * inv);
+        const float4 w = wnb[T];
+        const float iv = ivol[k] * inv;
+        const float own = (float)f[T * n_r + k] * iarea[T];
+        const float mean = fmaf(w.z, (float)f[(long)nb.z * n_r + k] * iarea[nb.z],
+                                fmaf(w.y, (float)f[(long)nb.y * n_r + k] * iarea[nb.y],
+                                     w.x * ((float)f[(long)nb.x * n_r + k] * iarea[nb.x])));
+        X[j * 2 * n_r + k] = own * iv;
+        X[j * 2 * n_r + n_r + k] = mean * iv;
     }
 }
 
@@ -297,9 +300,9 @@ __global__ void k_net_targets(const double *__restrict__ u, const int *__restric
 template <typename TO>
 __global__ void k_net_output(const float *__restrict__ y, long n, const double *__restrict__ s, TO *__restrict__ u)
 {
-    const double sv = *s;
+    const float sv = (float)*s;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-        u[i] = (TO)(sv * (double)y[i]);
+        u[i] = (TO)(sv * y[i]);
 }
 
 // judge of the initial guess: if the finish kernel rejected it, u = 0 and r = f
@@ -376,7 +379,7 @@ cudaError_t launch_net_scale(const Launch &L, const LevelDev &lv, const VertDev 
                              int n_part)
 {
     const long N = (long)lv.n * L.n_r;
-    k_net_scale<TF><<<n_part, 256, 0, L.s>>>(f, lv.area, vert.vol, N, L.n_r, partials);
+    k_net_scale<TF><<<n_part, 256, 0, L.s>>>(f, lv.iarea32, vert.ivol32, N, L.n_r, partials);
     return cudaGetLastError();
 }
 
@@ -391,8 +394,8 @@ cudaError_t launch_net_features(const Launch &L, const LevelDev &lv, const VertD
                                 long rows, const double *s, float *X)
 {
     if (rows <= 0) return cudaSuccess;
-    k_net_features<TF><<<grid_1d(rows * L.n_r, 256, L.sm_count), 256, 0, L.s>>>(f, lv.area, vert.vol, lv.nbr, lv.g,
-                                                                             cells, rows, L.n_r, s, X);
+    k_net_features<TF><<<grid_1d(rows * L.n_r, 256, L.sm_count), 256, 0, L.s>>>(f, lv.iarea32, vert.ivol32, lv.nbr,
+                                                                             lv.wnb32, cells, rows, L.n_r, s, X);
     return cudaGetLastError();
 }
 

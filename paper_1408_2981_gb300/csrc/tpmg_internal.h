@@ -55,6 +55,7 @@ struct VertDev {            // vertical factors shared by every level (no vertic
     const double *vol;      // [n_r]   v_k = (r_{k+1}^3 - r_k^3)/3
     const double *w;        // [n_r+1] omega^2 sigma_k 2 r_k^2 / (r_{k+1} - r_{k-1})
     const double *hr;       // [n_r]   omega^2 (r_{k+1} - r_k)
+    const float *ivol32;    // [n_r]   1 / v_k (network features of the learned form)
 };
 
 // Line relaxation works on tasks of kRelaxCols columns of one colour (the
@@ -82,6 +83,8 @@ struct LevelDev {
     int4 *nbr = nullptr;          // [n] {nbr0, nbr1, nbr2, lower-colour mask}
     dbl4 *g = nullptr;            // [n] {g0, g1, g2, g0+g1+g2}
     double *area = nullptr;       // [n]
+    float *iarea32 = nullptr;     // [n] 1 / |T| (network features of the learned form)
+    float4 *wnb32 = nullptr;      // [n] {g0, g1, g2} / (g0 + g1 + g2), 0
     int *task_cells = nullptr;    // [n_tasks][16] cell ids, -1 = padding
     int4 *task_nbr = nullptr;     // [n_tasks][16] nbr of the task's cells (zero for padding)
     dbl4 *task_g = nullptr;       // [n_tasks][16] g of the task's cells (zero for padding)

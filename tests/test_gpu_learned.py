@@ -122,7 +122,7 @@ def test_features_and_targets_match_the_oracle():
         t = torch.empty((37, n_r), dtype=torch.float32, device="cuda")
         sg = s.net_features(level, fg, x, cells=torch.from_numpy(cells).cuda())
         s.net_targets(level, fg, ug, t, cells=torch.from_numpy(cells).cuda())
-        assert abs(sg - s_ref) <= 1e-13 * s_ref
+        assert abs(sg - s_ref) <= 1e-6 * s_ref   # point values in FP32, sums in double
         np.testing.assert_allclose(x.cpu().double().numpy(), x_ref, rtol=1e-6, atol=1e-6 * np.max(np.abs(x_ref)))
         np.testing.assert_allclose(t.cpu().double().numpy(), t_ref, rtol=1e-6, atol=1e-7)
         # all columns in order when no cells are given
@@ -133,9 +133,10 @@ def test_features_and_targets_match_the_oracle():
 
 
 def test_vcycle_with_network_coarse_solve_matches_the_oracle():
-    """B r with the network as coarsest-level solve: FP32 V-cycle on the BF16
-    stencil against the oracle's V-cycle (BF16-rounded coefficients, FP64) with
-    the same network (bfloat16 weights, float64 activations) hooked in."""
+    """B r with the network's guess and one line relaxation as coarsest-level
+    solve: FP32 V-cycle on the BF16 stencil against the oracle's V-cycle
+    (BF16-rounded coefficients, FP64) with the same network (bfloat16 weights,
+    float64 activations) hooked in."""
     s = binding.Solver(**SMALL, **MIXED)
     o = oracle.Oracle(**SMALL)
     o.set_vcycle_bf16(True)

@@ -124,20 +124,24 @@ def test_adam_first_step_is_the_sign_of_the_gradient():
 
 
 def test_oracle_coarse_solve_hook():
-    """The V-cycle's coarsest-level solve replaced through the hook: a zero
-    solve equals nu_coarse = 0, and the exact dense solve equals converged
-    sweeps."""
+    """The coarsest-level solve replaced through the hook by a guess and one
+    block-Jacobi sweep: with a single level, a zero guess is exactly one Jacobi
+    sweep from zero (the V-cycle of a Jacobi-smoothed oracle with nu_coarse 1);
+    with two levels, the exact dense solve as guess is left unchanged by the
+    sweep and equals converged sweeps."""
     import oracle
-    kw = dict(refinement=3, n_levels=2, n_r=6, grading=1.1, courant_c=8.0)
-    r = np.random.default_rng(6).uniform(-1, 1, 1280 * 6)
-    o0 = oracle.Oracle(nu_coarse=0, **kw)
-    o = oracle.Oracle(**kw)
+    r1 = np.random.default_rng(6).uniform(-1, 1, 320 * 6)
+    o = oracle.Oracle(refinement=2, n_levels=1, n_r=6, grading=1.1)
     o.set_coarse_solve(lambda f: np.zeros_like(f))
-    np.testing.assert_array_equal(o.vcycle(r), o0.vcycle(r))
+    np.testing.assert_array_equal(o.vcycle(r1), oracle.Oracle(refinement=2, n_levels=1, n_r=6, grading=1.1,
+                                                              smoother=1, nu_coarse=1).vcycle(r1))
+    kw = dict(refinement=3, n_levels=2, n_r=6, grading=1.1, courant_c=8.0)
+    r = np.random.default_rng(7).uniform(-1, 1, 1280 * 6)
+    o = oracle.Oracle(**kw)
     A0 = o.dense_operator(level=0)
     o.set_coarse_solve(lambda f: np.linalg.solve(A0, f))
-    o_many = oracle.Oracle(nu_coarse=40, **kw)
-    z, z_ref = o.vcycle(r), o_many.vcycle(r)
-    assert np.max(np.abs(z - z_ref)) <= 1e-11 * np.max(np.abs(z_ref))
+    z, z_ref = o.vcycle(r), oracle.Oracle(nu_coarse=40, **kw).vcycle(r)
+    # the sweep re-solves the stiff columns from a residual of rounding size
+    assert np.max(np.abs(z - z_ref)) <= 1e-10 * np.max(np.abs(z_ref))
     o.set_coarse_solve(None)
     np.testing.assert_array_equal(o.vcycle(r), oracle.Oracle(**kw).vcycle(r))
