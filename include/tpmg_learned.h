@@ -138,6 +138,16 @@ tpmg_status tpmg_attach_net(tpmg_ctx *ctx, int role, tpmg_net *net);
  * (also when no COARSE network is attached), CUDA. */
 tpmg_status tpmg_vcycle_learned(tpmg_ctx *ctx, const double *d_r, double *d_z);
 
+/* d_u = s network(features(d_f)) for every column of the level of `role`
+ * (COARSE: level 0, WARM: the finest level; doubles of that level's size) with
+ * the network attached in that role, evaluated as inside the solve but without
+ * the line relaxation that follows there.  Inside the solve the network runs as
+ * one fused tensor-core kernel when its hidden width is 64 and n_r is a
+ * multiple of 8 (inputs and activations rounded to bfloat16, FP32
+ * accumulation); otherwise layer by layer with FP32 activations.
+ * Asynchronous.  Errors: INVALID_ARG (also: no network in `role`), CUDA. */
+tpmg_status tpmg_net_predict(tpmg_ctx *ctx, int role, const double *d_f, double *d_u);
+
 /* Bits of *info of tpmg_solve_learned. */
 enum { TPMG_LEARNED_WARM_USED = 1,      /* the network's initial guess was kept */
        TPMG_LEARNED_WARM_REJECTED = 2,  /* its residual was not below ||f||: restarted from u = 0 */

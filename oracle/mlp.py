@@ -42,12 +42,16 @@ def bf16_round(a: np.ndarray) -> np.ndarray:
     return np.array([_bf16(float(v)) for v in flat]).reshape(np.shape(a))
 
 
-def forward(params, x, bf16_weights: bool = True):
-    """params: list of (W [out, in], b [out]).  Returns (y, cache of (a_{l-1}, z_l, W_l))."""
+def forward(params, x, bf16_weights: bool = True, bf16_acts: bool = False):
+    """params: list of (W [out, in], b [out]).  Returns (y, cache of (a_{l-1}, z_l, W_l)).
+    bf16_acts: every layer's input (x and the hidden activations) is rounded to
+    bfloat16 first, as in the library's fused tensor-core inference."""
     a = np.asarray(x, dtype=np.float64)
     cache = []
     for l, (W, b) in enumerate(params):
         Wl = bf16_round(W) if bf16_weights else np.asarray(W, dtype=np.float64)
+        if bf16_acts:
+            a = bf16_round(a)
         z = a @ Wl.T + np.asarray(b, dtype=np.float64)
         cache.append((a, z, Wl))
         a = np.maximum(z, 0.0) if l < len(params) - 1 else z
@@ -106,11 +110,11 @@ def targets(u, s, n_r, cells=None):
     return t[np.asarray(cells)] if cells is not None else t
 
 
-def predict(params, f, area, vol, nbr, g, bf16_weights: bool = True):
+def predict(params, f, area, vol, nbr, g, bf16_weights: bool = True, bf16_acts: bool = False):
     """u = s network(x) for every column of the level: the learned coarse solve
     or warm start as the library computes it."""
     x, s = features(f, area, vol, nbr, g)
-    y, _ = forward(params, x, bf16_weights)
+    y, _ = forward(params, x, bf16_weights, bf16_acts)
     return (s * y).reshape(-1)
 
 

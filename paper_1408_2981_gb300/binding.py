@@ -44,7 +44,7 @@ EXPORTS = ["tpmg_default_params", "tpmg_setup", "tpmg_apply_operator", "tpmg_vcy
 EXPORTS_LEARNED = ["tpmg_net_create", "tpmg_net_n_params", "tpmg_net_set_params", "tpmg_net_get_params",
                    "tpmg_net_forward", "tpmg_net_gradients", "tpmg_net_train_step", "tpmg_net_last_error",
                    "tpmg_net_destroy", "tpmg_net_features", "tpmg_net_targets", "tpmg_record_coarse",
-                   "tpmg_record_count", "tpmg_coarse_solve", "tpmg_attach_net", "tpmg_vcycle_learned",
+                   "tpmg_record_count", "tpmg_coarse_solve", "tpmg_attach_net", "tpmg_net_predict", "tpmg_vcycle_learned",
                    "tpmg_solve_learned"]
 
 TPMG_NET_COARSE = 0
@@ -129,6 +129,7 @@ def load(path: str | None = None):
     lib.tpmg_coarse_solve.argtypes = [P, P, P, I]
     lib.tpmg_attach_net.argtypes = [P, I, P]
     lib.tpmg_vcycle_learned.argtypes = [P, P, P]
+    lib.tpmg_net_predict.argtypes = [P, I, P, P]
     lib.tpmg_solve_learned.argtypes = [P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(I),
                                        ctypes.POINTER(I), ctypes.POINTER(LL)]
     no_status = ("tpmg_destroy", "tpmg_status_string", "tpmg_last_error", "tpmg_batch_destroy", "tpmg_net_n_params",
@@ -370,6 +371,12 @@ class Solver:
             self._nets = {}
         self._check(self._lib.tpmg_attach_net(self._h, role, net._h if net is not None else None), "tpmg_attach_net")
         self._nets[role] = net   # keep the network alive while attached
+
+    def net_predict(self, role: int, f, u):
+        """u = s network(features(f)) of the network attached in `role` on its level."""
+        level = 0 if role == TPMG_NET_COARSE else self.n_levels - 1
+        self._check(self._lib.tpmg_net_predict(self._h, role, self._level_vec(f, level, "f"),
+                                               self._level_vec(u, level, "u")), "tpmg_net_predict")
 
     def vcycle_learned(self, r, z):
         """z = B r with the attached COARSE network as the coarsest-level solve."""

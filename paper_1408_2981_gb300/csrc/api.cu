@@ -334,6 +334,10 @@ tpmg_status net_infer(tpmg_ctx *ctx, int role, const LevelDev &lv, const TF *f, 
     LCHK(run(ctx, TPMG_K_NET, nunits, [&] { return launch_net_scale<TF>(L, lv, ctx->vert, f, ctx->partials, ctx->n_part); }));
     LCHK(run(ctx, TPMG_K_NET, 1.0, [&] { return launch_net_scale_finish(L, lv, ctx->partials, ctx->n_part, s); }));
     LCHK(run(ctx, TPMG_K_NET, nunits, [&] { return launch_net_features<TF>(L, lv, ctx->vert, f, nullptr, rows, s, w.x); }));
+    if (net_fused_ok(v)) {   // one tensor-core kernel for the whole network
+        LCHK(run(ctx, TPMG_K_NET, nunits, [&] { return launch_net_fused<TO>(L, v, w.x, rows, s, u_out); }));
+        return TPMG_OK;
+    }
     const float *in = w.x;
     float *bufs[2] = {w.h0, w.h1};
     for (int l = 0; l < 4; ++l) {
@@ -1336,6 +1340,15 @@ tpmg_status tpmg_coarse_solve(tpmg_ctx *ctx, const double *d_f0, double *d_u0, i
     if (st != TPMG_OK) return st;
     LCHK(run(ctx, TPMG_K_COPY, (double)n, [&] { return launch_to_f64(L, n, c.u32, d_u0); }));
     return TPMG_OK;
+}
+
+tpmg_status tpmg_net_predict(tpmg_ctx *ctx, int role, const double *d_f, double *d_u)
+{
+    if (!ctx || !d_f || !d_u) return fail(ctx, TPMG_ERR_INVALID_ARG, "NULL argument");
+    if (role != TPMG_NET_COARSE && role != TPMG_NET_WARM) return fail(ctx, TPMG_ERR_INVALID_ARG, "unknown role");
+    if (!ctx->net[role]) return fail(ctx, TPMG_ERR_INVALID_ARG, "no network attached in this role");
+    const LevelDev &lv = role == TPMG_NET_COARSE ? ctx->lv[0] : ctx->lv.back();
+    return net_infer<double, double>(ctx, role, lv, d_f, d_u);
 }
 
 tpmg_status tpmg_vcycle_learned(tpmg_ctx *ctx, const double *d_r, double *d_z)

@@ -322,6 +322,160 @@ __global__ void k_to_f32(long n, const double *__restrict__ x, float *__restrict
         y[i] = (float)x[i];
 }
 
+// ---- fused inference on the tensor cores ------------------------------------
+//
+// The whole network for 16 columns per warp with mma.sync m16n8k16 (bfloat16
+// operands, FP32 accumulation): every weight matrix is staged once per CTA in
+// shared memory ([out][in] rows padded by 8 bfloat16, so that the B fragments
+// of the 8 row groups fall in distinct banks), and the activations never leave
+// the registers: the accumulator fragments of two adjacent 8-column tiles are,
+// after bias, ReLU and rounding to bfloat16, exactly the A fragment of one
+// 16-wide k-step of the next layer.  Inputs are rounded to bfloat16 as they
+// are loaded.  Hidden width 64; n_r a multiple of 8.
+constexpr int kFusedH = 64;
+constexpr int kFusedWarps = 4;
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    return (uint32_t)to_bf16(lo) | ((uint32_t)to_bf16(hi) << 16);
+}
+
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// accumulators of 8 n-tiles (64 columns) -> A fragments of the next layer's 4 k-steps
+__device__ __forceinline__ void to_fragments(const float acc[8][4], const float *bias, int t, uint32_t h[4][4])
+{
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int c0 = 16 * j + 2 * t, c1 = c0 + 8;
+        const float p0 = bias[c0], p1 = bias[c0 + 1], q0 = bias[c1], q1 = bias[c1 + 1];
+        h[j][0] = pack_bf16(fmaxf(acc[2 * j][0] + p0, 0.f), fmaxf(acc[2 * j][1] + p1, 0.f));
+        h[j][1] = pack_bf16(fmaxf(acc[2 * j][2] + p0, 0.f), fmaxf(acc[2 * j][3] + p1, 0.f));
+        h[j][2] = pack_bf16(fmaxf(acc[2 * j + 1][0] + q0, 0.f), fmaxf(acc[2 * j + 1][1] + q1, 0.f));
+        h[j][3] = pack_bf16(fmaxf(acc[2 * j + 1][2] + q0, 0.f), fmaxf(acc[2 * j + 1][3] + q1, 0.f));
+    }
+}
+
+// one hidden layer (64 -> 64) on the fragments h, in place
+__device__ __forceinline__ void hidden_layer(uint32_t h[4][4], const uint32_t *w, int ldw, const float *bias, int g,
+                                             int t)
+{
+    float acc[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const uint32_t *wr = w + (nt * 8 + g) * ldw + 8 * j + t;
+            mma_bf16(acc[nt], h[j], wr[0], wr[4]);
+        }
+    to_fragments(acc, bias, t, h);
+}
+
+template <typename TO>
+__global__ void __launch_bounds__(32 * kFusedWarps) k_mlp_fused(const float *__restrict__ X, long rows, int n_r,
+                                                                 NetView v, const double *__restrict__ s,
+                                                                 TO *__restrict__ out)
+{
+    extern __shared__ uint32_t sm[];
+    const int K1 = 2 * n_r;
+    const int ld1 = K1 / 2 + 4, ldh = kFusedH / 2 + 4;   // words per padded row
+    uint32_t *s1 = sm, *s2 = s1 + kFusedH * ld1, *s3 = s2 + kFusedH * ldh, *s4 = s3 + kFusedH * ldh;
+    float *sb = reinterpret_cast<float *>(s4 + n_r * ldh);   // b_1 | b_2 | b_3 | b_4
+    {
+        const uint32_t *g1 = reinterpret_cast<const uint32_t *>(v.w[0]);
+        for (int i = threadIdx.x; i < kFusedH * (K1 / 2); i += blockDim.x)
+            s1[(i / (K1 / 2)) * ld1 + i % (K1 / 2)] = g1[i];
+        const uint32_t *g2 = reinterpret_cast<const uint32_t *>(v.w[1]);
+        const uint32_t *g3 = reinterpret_cast<const uint32_t *>(v.w[2]);
+        for (int i = threadIdx.x; i < kFusedH * (kFusedH / 2); i += blockDim.x) {
+            s2[(i / (kFusedH / 2)) * ldh + i % (kFusedH / 2)] = g2[i];
+            s3[(i / (kFusedH / 2)) * ldh + i % (kFusedH / 2)] = g3[i];
+        }
+        const uint32_t *g4 = reinterpret_cast<const uint32_t *>(v.w[3]);
+        for (int i = threadIdx.x; i < n_r * (kFusedH / 2); i += blockDim.x)
+            s4[(i / (kFusedH / 2)) * ldh + i % (kFusedH / 2)] = g4[i];
+        for (int i = threadIdx.x; i < kFusedH; i += blockDim.x) {
+            sb[i] = v.b[0][i];
+            sb[kFusedH + i] = v.b[1][i];
+            sb[2 * kFusedH + i] = v.b[2][i];
+        }
+        for (int i = threadIdx.x; i < n_r; i += blockDim.x) sb[3 * kFusedH + i] = v.b[3][i];
+    }
+    __syncthreads();
+    const float sv = (float)*s;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const long n_tiles = (rows + 15) / 16;
+    for (long tile = (long)blockIdx.x * kFusedWarps + warp; tile < n_tiles; tile += (long)gridDim.x * kFusedWarps) {
+        const long r0 = tile * 16 + g, r1 = r0 + 8;
+        const bool v0 = r0 < rows, v1 = r1 < rows;
+        const float *x0 = X + r0 * K1 + 2 * t, *x1 = X + r1 * K1 + 2 * t;
+        float acc[8][4];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+        for (int kk = 0; kk < K1; kk += 16) {
+            const float2 z = make_float2(0.f, 0.f);
+            const float2 a00 = v0 ? __ldg(reinterpret_cast<const float2 *>(x0 + kk)) : z;
+            const float2 a10 = v1 ? __ldg(reinterpret_cast<const float2 *>(x1 + kk)) : z;
+            const float2 a01 = v0 ? __ldg(reinterpret_cast<const float2 *>(x0 + kk + 8)) : z;
+            const float2 a11 = v1 ? __ldg(reinterpret_cast<const float2 *>(x1 + kk + 8)) : z;
+            const uint32_t a[4] = {pack_bf16(a00.x, a00.y), pack_bf16(a10.x, a10.y), pack_bf16(a01.x, a01.y),
+                                   pack_bf16(a11.x, a11.y)};
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                const uint32_t *wr = s1 + (nt * 8 + g) * ld1 + kk / 2 + t;
+                mma_bf16(acc[nt], a, wr[0], wr[4]);
+            }
+        }
+        uint32_t h[4][4];
+        to_fragments(acc, sb, t, h);
+        hidden_layer(h, s2, ldh, sb + kFusedH, g, t);
+        hidden_layer(h, s3, ldh, sb + 2 * kFusedH, g, t);
+        const float *b4 = sb + 3 * kFusedH;
+        for (int n0 = 0; n0 < n_r; n0 += 64) {
+            const int ntn = min(8, (n_r - n0) / 8);
+            float o[8][4];
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) o[nt][0] = o[nt][1] = o[nt][2] = o[nt][3] = 0.f;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int nt = 0; nt < 8; ++nt)
+                    if (nt < ntn) {
+                        const uint32_t *wr = s4 + (n0 + nt * 8 + g) * ldh + 8 * j + t;
+                        mma_bf16(o[nt], h[j], wr[0], wr[4]);
+                    }
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt)
+                if (nt < ntn) {
+                    const int c = n0 + nt * 8 + 2 * t;
+                    if (v0) {
+                        out[r0 * n_r + c] = (TO)(sv * (o[nt][0] + b4[c]));
+                        out[r0 * n_r + c + 1] = (TO)(sv * (o[nt][1] + b4[c + 1]));
+                    }
+                    if (v1) {
+                        out[r1 * n_r + c] = (TO)(sv * (o[nt][2] + b4[c]));
+                        out[r1 * n_r + c + 1] = (TO)(sv * (o[nt][3] + b4[c + 1]));
+                    }
+                }
+        }
+    }
+}
+
+size_t fused_smem_bytes(int n_r)
+{
+    const size_t ld1 = (size_t)n_r + 4, ldh = kFusedH / 2 + 4;
+    return 4 * (kFusedH * ld1 + 2 * kFusedH * ldh + (size_t)n_r * ldh + 3 * kFusedH + (size_t)n_r);
+}
+
 inline int grid_1d(long work, int nt, int sm_count)
 {
     long b = (work + nt - 1) / nt;
@@ -372,6 +526,29 @@ cudaError_t launch_net_layer(cudaStream_t s, const NetView &v, int l, const floa
     if (l < 3)
         return gemm<false, true, uint16_t, EPI_BIAS_RELU>(s, (int)rows, out, in, 1, x, in, v.w[l], in, y, out, v.b[l]);
     return gemm<false, true, uint16_t, EPI_BIAS>(s, (int)rows, out, in, 1, x, in, v.w[l], in, y, out, v.b[l]);
+}
+
+bool net_fused_ok(const NetView &v)
+{
+    const int n_r = v.sizes[4];
+    return v.sizes[1] == kFusedH && v.sizes[2] == kFusedH && v.sizes[3] == kFusedH && v.sizes[0] == 2 * n_r &&
+           n_r % 8 == 0 && fused_smem_bytes(n_r) <= 200 * 1024;
+}
+
+template <typename TO>
+cudaError_t launch_net_fused(const Launch &L, const NetView &v, const float *X, long rows, const double *s, TO *out)
+{
+    const int n_r = v.sizes[4];
+    const size_t smem = fused_smem_bytes(n_r);
+    static_assert(kFusedWarps == 4, "launch shape");
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_fused<TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const long tiles = (rows + 15) / 16;
+    const long per_sm = std::max<long>(1, (long)(220 * 1024 / std::max<size_t>(smem, 1)));
+    const long grid = std::max<long>(1, std::min<long>((tiles + kFusedWarps - 1) / kFusedWarps,
+                                                       (long)std::max(L.sm_count, 1) * std::min<long>(per_sm, 4)));
+    k_mlp_fused<TO><<<(int)grid, 32 * kFusedWarps, smem, L.s>>>(X, rows, n_r, v, s, out);
+    return cudaGetLastError();
 }
 
 template <typename TF>
@@ -431,6 +608,9 @@ template cudaError_t launch_net_features<float>(const Launch &, const LevelDev &
                                                 const int *, long, const double *, float *);
 template cudaError_t launch_net_features<double>(const Launch &, const LevelDev &, const VertDev &, const double *,
                                                  const int *, long, const double *, float *);
+template cudaError_t launch_net_fused<float>(const Launch &, const NetView &, const float *, long, const double *, float *);
+template cudaError_t launch_net_fused<double>(const Launch &, const NetView &, const float *, long, const double *,
+                                              double *);
 template cudaError_t launch_net_output<float>(const Launch &, const float *, long, const double *, float *);
 template cudaError_t launch_net_output<double>(const Launch &, const float *, long, const double *, double *);
 

@@ -198,6 +198,11 @@ struct NetView {            // device pointers of a network's weights
 NetView net_view(const tpmg_net *net);
 // y [rows][sizes[l+1]] = act(x W_l^T + b_l), ReLU for l < 3
 cudaError_t launch_net_layer(cudaStream_t s, const NetView &v, int l, const float *x, long rows, float *y);
+// the whole network in one tensor-core kernel (hidden width 64, n_r % 8 == 0):
+// out [rows][n_r] = s * network(X), activations rounded to bfloat16 between layers
+bool net_fused_ok(const NetView &v);
+template <typename TO>
+cudaError_t launch_net_fused(const Launch &L, const NetView &v, const float *X, long rows, const double *s, TO *out);
 // partials [n_part] of the squared point values of f on lv; the finish writes s
 template <typename TF>
 cudaError_t launch_net_scale(const Launch &L, const LevelDev &lv, const VertDev &vert, const TF *f, double *partials,

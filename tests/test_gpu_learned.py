@@ -144,7 +144,8 @@ def test_vcycle_with_network_coarse_solve_matches_the_oracle():
     params = net.unflatten(flat.astype(np.float64))
     grid0 = o.grid(o.level_ref(0))
     vol = o.vertical()["vol"]
-    o.set_coarse_solve(lambda f0: mlp.predict(params, f0, grid0["area"], vol, grid0["nbr"], grid0["g"]))
+    o.set_coarse_solve(lambda f0: mlp.predict(params, f0, grid0["area"], vol, grid0["nbr"], grid0["g"],
+                                              bf16_acts=True))
     s.attach_net(binding.TPMG_NET_COARSE, net)
     r = inputs.uniform_pm1(inputs.SEED_LEARNED + 51, s.N)
     z = torch.zeros(s.N, dtype=torch.float64, device="cuda")
@@ -156,6 +157,34 @@ def test_vcycle_with_network_coarse_solve_matches_the_oracle():
     o.set_coarse_solve(None)
     z_plain = o.vcycle(r)
     assert np.max(np.abs(z_plain - z_ref)) / np.max(np.abs(z_ref)) > 10 * err
+
+
+@pytest.mark.parametrize("hidden", [64, 48])
+def test_network_prediction_matches_the_oracle(hidden):
+    """The attached network's prediction u = s network(features(f)) on the
+    coarsest and the finest level.  Hidden width 64 runs the fused tensor-core
+    kernel (inputs and activations rounded to bfloat16: the oracle rounds the
+    same way; a rounding boundary crossed differently moves a value by one
+    bfloat16 step, hence the tolerance); width 48 runs layer by layer in FP32."""
+    s = binding.Solver(**SMALL, **MIXED)
+    o = oracle.Oracle(**SMALL)
+    vol = o.vertical()["vol"]
+    net, flat = random_net(s.n_r, hidden, seed=inputs.SEED_LEARNED + 80 + hidden)
+    params = net.unflatten(flat.astype(np.float64))
+    for role, level in ((binding.TPMG_NET_COARSE, 0), (binding.TPMG_NET_WARM, s.n_levels - 1)):
+        s.attach_net(role, net)
+        grid = o.grid(o.level_ref(level))
+        n = grid["area"].shape[0] * s.n_r
+        f = inputs.uniform_pm1(inputs.SEED_LEARNED + 81 + level, n)
+        u = torch.zeros(n, dtype=torch.float64, device="cuda")
+        s.net_predict(role, torch.from_numpy(f).cuda(), u)
+        ref = mlp.predict(params, f, grid["area"], vol, grid["nbr"], grid["g"], bf16_acts=hidden == 64)
+        got = u.cpu().numpy()
+        err = np.abs(got - ref)
+        scale = np.max(np.abs(ref))
+        assert np.max(err) <= (2e-2 if hidden == 64 else 1e-5) * scale, (role, np.max(err) / scale)
+        assert np.mean(err) <= (2e-3 if hidden == 64 else 1e-6) * np.mean(np.abs(ref)), (role, np.mean(err))
+        s.attach_net(role, None)
 
 
 def _smooth_rhs(s, seed):

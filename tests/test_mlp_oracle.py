@@ -145,3 +145,20 @@ def test_oracle_coarse_solve_hook():
     assert np.max(np.abs(z - z_ref)) <= 1e-10 * np.max(np.abs(z_ref))
     o.set_coarse_solve(None)
     np.testing.assert_array_equal(o.vcycle(r), oracle.Oracle(**kw).vcycle(r))
+
+
+def test_bf16_activations_round_every_layer_input():
+    """forward(bf16_acts=True) rounds x and each hidden activation to bfloat16
+    before the product: for one layer it is the plain forward of bf16(x), for
+    two layers the second layer sees bf16(relu(.))."""
+    rng = np.random.default_rng(34)
+    W1, b1 = rng.uniform(-1, 1, (5, 4)), rng.uniform(-1, 1, 5)
+    W2, b2 = rng.uniform(-1, 1, (3, 5)), rng.uniform(-1, 1, 3)
+    x = rng.uniform(-1, 1, (6, 4))
+    y, _ = mlp.forward([(W1, b1)], x, bf16_acts=True)
+    y_ref, _ = mlp.forward([(W1, b1)], mlp.bf16_round(x))
+    np.testing.assert_array_equal(y, y_ref)
+    y2, _ = mlp.forward([(W1, b1), (W2, b2)], x, bf16_acts=True)
+    h = np.maximum(mlp.bf16_round(x) @ mlp.bf16_round(W1).T + b1, 0.0)
+    np.testing.assert_array_equal(y2, mlp.bf16_round(h) @ mlp.bf16_round(W2).T + b2)
+    assert not np.array_equal(y2, mlp.forward([(W1, b1), (W2, b2)], x)[0])
