@@ -59,9 +59,11 @@ struct tpmg_ctx {
     // coarsest-level recording
     tpmg_net *net[2] = {nullptr, nullptr};
     struct NetWs {
-        float *x = nullptr, *h0 = nullptr, *h1 = nullptr, *y = nullptr;
+        float *p = nullptr, *x = nullptr, *h0 = nullptr, *h1 = nullptr, *y = nullptr;
         long rows = 0;
     } nws[2];
+    float *net_p = nullptr;       // point values of tpmg_net_features / tpmg_net_targets
+    long net_p_cap = 0;
     double *d_net_s = nullptr;    // [2] feature scales s (COARSE, WARM)
     bool net_coarse_on = false;   // the V-cycle being issued uses the COARSE network
     struct {
@@ -331,9 +333,11 @@ tpmg_status net_infer(tpmg_ctx *ctx, int role, const LevelDev &lv, const TF *f, 
     double *s = ctx->d_net_s + role;
     const long rows = lv.n;
     const double nunits = (double)lv.n * ctx->p.n_r;
-    LCHK(run(ctx, TPMG_K_NET, nunits, [&] { return launch_net_scale<TF>(L, lv, ctx->vert, f, ctx->partials, ctx->n_part); }));
+    LCHK(run(ctx, TPMG_K_NET, nunits, [&] {
+        return launch_net_prepare<TF>(L, lv, ctx->vert, f, w.p, ctx->partials, ctx->n_part);
+    }));
     LCHK(run(ctx, TPMG_K_NET, 1.0, [&] { return launch_net_scale_finish(L, lv, ctx->partials, ctx->n_part, s); }));
-    LCHK(run(ctx, TPMG_K_NET, nunits, [&] { return launch_net_features<TF>(L, lv, ctx->vert, f, nullptr, rows, s, w.x); }));
+    LCHK(run(ctx, TPMG_K_NET, nunits, [&] { return launch_net_features(L, lv, w.p, nullptr, rows, s, w.x); }));
     if (net_fused_ok(v)) {   // one tensor-core kernel for the whole network
         LCHK(run(ctx, TPMG_K_NET, nunits, [&] { return launch_net_fused<TO>(L, v, w.x, rows, s, u_out); }));
         return TPMG_OK;
@@ -691,26 +695,53 @@ tpmg_status pcg_graph(tpmg_ctx *ctx, const double *f, double *u, double rtol, in
     return loop_result(ctx, s, rtol, max_iter, iters, rel);
 }
 
+// learned = true: the host-driven form of tpmg_solve_learned's loop (same
+// kernels, same order as append_solve with learned set).
 tpmg_status pcg(tpmg_ctx *ctx, const double *f, double *u, double rtol, int max_iter, int *iters, double *rel,
-                double *hist)
+                double *hist, bool learned = false)
 {
     const Launch L = launch_of(ctx);
     LevelDev &fl = ctx->lv[ctx->p.n_levels - 1];
     const long N = ctx->N;
     const int np = ctx->n_part;
     // the FP32 V-cycle is not exactly symmetric: Polak-Ribiere coefficient (flexible CG)
-    const bool flexible = ctx->p.precision == TPMG_PREC_MIXED;
+    const bool flexible = ctx->p.precision == TPMG_PREC_MIXED || learned;
     *iters = 0;
     *rel = 1.0;
+    if (learned && ctx->net[TPMG_NET_WARM]) {
+        tpmg_status s1 = net_infer<double, float>(ctx, TPMG_NET_WARM, fl, f, fl.u32);
+        if (s1 != TPMG_OK) return s1;
+        LCHK(run(ctx, TPMG_K_RELAX, (double)N, [&] {
+            return launch_relax32<double>(L, fl, PASS_NORMAL, 0, fl.n_tasks, (float)ctx->p.relax, f, fl.u32, fl.u2_32,
+                                          nullptr, u);
+        }));
+    }
     LCHK(run(ctx, TPMG_K_RESIDUAL, (double)N, [&] { return launch_residual(L, fl, ctx->vert, f, u, ctx->r, ctx->partials, np); }));
-    LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_RR0, ctx->partials, np, ctx->sc); }));
+    if (learned) {
+        LCHK(run(ctx, TPMG_K_DOT, (double)N, [&] { return launch_dot(L, N, f, f, ctx->partials + np, np); }));
+        LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_RR0F, ctx->partials, np, ctx->sc); }));
+        LCHK(run(ctx, TPMG_K_COPY, (double)N, [&] { return launch_judge_reset(L, ctx->sc, N, f, u, ctx->r); }));
+    } else {
+        LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_RR0, ctx->partials, np, ctx->sc); }));
+    }
     tpmg_status st = read_scalars(ctx);
     if (st != TPMG_OK) return st;
     const double rr0 = ctx->h_sc->rr0;
-    if (hist) hist[0] = 1.0;
-    if (!std::isfinite(rr0)) return fail(ctx, TPMG_ERR_BREAKDOWN, "initial residual is not finite");
+    const double rel0 = learned && rr0 > 0.0 ? std::sqrt(ctx->h_sc->rr / rr0) : 1.0;
+    if (hist) hist[0] = rel0;
+    if (!std::isfinite(rr0) || !std::isfinite(rel0)) return fail(ctx, TPMG_ERR_BREAKDOWN, "initial residual is not finite");
     if (rr0 == 0.0) { *rel = 0.0; return TPMG_OK; }
-    if ((st = vcycle_pcg(ctx)) != TPMG_OK) return st;
+    *rel = rel0;
+    if (learned && (rel0 <= rtol || max_iter == 0)) return rel0 <= rtol ? TPMG_OK : fail(ctx, TPMG_ERR_NOT_CONVERGED, "max_iter reached before rtol");
+    // z = B r: the learned form's V-cycle runs kernel by kernel with the COARSE network
+    auto precondition = [&]() -> tpmg_status {
+        if (!learned) return vcycle_pcg(ctx);
+        ctx->net_coarse_on = ctx->net[TPMG_NET_COARSE] != nullptr;
+        const tpmg_status s2 = vcycle_fine(ctx, ctx->r, ctx->z);
+        ctx->net_coarse_on = false;
+        return s2;
+    };
+    if ((st = precondition()) != TPMG_OK) return st;
     LCHK(run(ctx, TPMG_K_DOT, (double)N, [&] { return launch_dot(L, N, ctx->r, ctx->z, ctx->partials, np); }));
     LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_RZ0, ctx->partials, np, ctx->sc); }));
     LCHK(run(ctx, TPMG_K_COPY, (double)N, [&] { return cudaMemcpyAsync(ctx->pv, ctx->z, sizeof(double) * N, cudaMemcpyDeviceToDevice, ctx->stream); }));
@@ -731,7 +762,7 @@ tpmg_status pcg(tpmg_ctx *ctx, const double *f, double *u, double rtol, int max_
         if (hist) hist[it + 1] = *rel;
         if (*rel <= rtol) return TPMG_OK;
         if (it + 1 == max_iter) break;
-        if ((st = vcycle_pcg(ctx)) != TPMG_OK) return st;
+        if ((st = precondition()) != TPMG_OK) return st;
         LCHK(run(ctx, TPMG_K_DOT, (double)N, [&] { return launch_dot(L, N, ctx->r, ctx->z, ctx->partials, np); }));
         LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, flexible ? FIN_BETA_PR : FIN_BETA, ctx->partials, np, ctx->sc); }));
         LCHK(run(ctx, TPMG_K_XPBY, (double)N, [&] { return launch_xpby(L, N, ctx->sc, ctx->z, ctx->pv); }));
@@ -1252,14 +1283,20 @@ tpmg_status level_arg(tpmg_ctx *ctx, int level, const void *a, const void *b, lo
     return TPMG_OK;
 }
 
-// s of the field f on level: partials + finish into d_net_s[2]
+// point values of the field f on level into ctx->net_p and its scale s into d_net_s[2]
 tpmg_status level_scale(tpmg_ctx *ctx, int level, const double *f)
 {
     const Launch L = launch_of(ctx);
     const LevelDev &lv = ctx->lv[level];
     double *s = ctx->d_net_s + 2;
-    const double nunits = (double)lv.n * ctx->p.n_r;
-    LCHK(run(ctx, TPMG_K_NET, nunits, [&] { return launch_net_scale<double>(L, lv, ctx->vert, f, ctx->partials, ctx->n_part); }));
+    const long n = (long)lv.n * ctx->p.n_r;
+    if (n > ctx->net_p_cap) {   // grows to the finest level at most; freed by tpmg_destroy
+        CU(dalloc(ctx, &ctx->net_p, (size_t)n));
+        ctx->net_p_cap = n;
+    }
+    LCHK(run(ctx, TPMG_K_NET, (double)n, [&] {
+        return launch_net_prepare<double>(L, lv, ctx->vert, f, ctx->net_p, ctx->partials, ctx->n_part);
+    }));
     LCHK(run(ctx, TPMG_K_NET, 1.0, [&] { return launch_net_scale_finish(L, lv, ctx->partials, ctx->n_part, s); }));
     return TPMG_OK;
 }
@@ -1274,7 +1311,7 @@ tpmg_status tpmg_net_features(tpmg_ctx *ctx, int level, const double *d_f, const
     const Launch L = launch_of(ctx);
     const double *s = ctx->d_net_s + 2;
     LCHK(run(ctx, TPMG_K_NET, (double)rows * ctx->p.n_r, [&] {
-        return launch_net_features<double>(L, ctx->lv[level], ctx->vert, d_f, d_cells, rows, s, d_x);
+        return launch_net_features(L, ctx->lv[level], ctx->net_p, d_cells, rows, s, d_x);
     }));
     if (h_scale) {
         CU(cudaMemcpyAsync(&ctx->h_sc->ff, s, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1377,6 +1414,7 @@ tpmg_status tpmg_attach_net(tpmg_ctx *ctx, int role, tpmg_net *net)
         const long h = v.sizes[1];
         if (w.rows != rows * h) {   // (re)allocate for this hidden width; old blocks are freed at destroy
             const size_t nr = (size_t)ctx->p.n_r;
+            CU(dalloc(ctx, &w.p, (size_t)rows * nr));
             CU(dalloc(ctx, &w.x, (size_t)rows * 2 * nr));
             CU(dalloc(ctx, &w.h0, (size_t)rows * h));
             CU(dalloc(ctx, &w.h1, (size_t)rows * h));
@@ -1401,6 +1439,21 @@ tpmg_status tpmg_solve_learned(tpmg_ctx *ctx, const double *d_f, double *d_u, do
         return fail(ctx, TPMG_ERR_INVALID_ARG, "rtol must be >= 0, max_iter in 1..4095");
     if (d_f == d_u) return fail(ctx, TPMG_ERR_INVALID_ARG, "f and u must not overlap");
     auto &lg = ctx->lg;
+    Scalars s{};
+    long long launches = 0;
+    int it_learned = 0;
+    if (!ctx->p.graphs || ctx->tr.mask != 0) {
+        // host-driven loop (graphs off, or a kernel class being timed): same kernels, same order
+        long long before = 0, after = 0;
+        for (int c = 0; c < TPMG_K_COUNT; ++c) before += ctx->tr.launches[c];
+        double rel_h = 1.0;
+        const tpmg_status sh = pcg(ctx, d_f, d_u, rtol, max_iter, &it_learned, &rel_h, nullptr, true);
+        for (int c = 0; c < TPMG_K_COUNT; ++c) after += ctx->tr.launches[c];
+        launches = after - before;
+        if (sh != TPMG_OK && sh != TPMG_ERR_NOT_CONVERGED && sh != TPMG_ERR_BREAKDOWN) return sh;
+        s = *ctx->h_sc;
+        if (sh == TPMG_ERR_BREAKDOWN && s.flag == 0) s.flag = 2;
+    } else {
     if (!lg.exec || lg.f != d_f || lg.u != d_u || lg.rtol != rtol || lg.max_iter != max_iter ||
         lg.nets[0] != ctx->net[0] || lg.nets[1] != ctx->net[1]) {
         if (lg.exec) cudaGraphExecDestroy(lg.exec);
@@ -1426,11 +1479,13 @@ tpmg_status tpmg_solve_learned(tpmg_ctx *ctx, const double *d_f, double *d_u, do
     CU(cudaGraphLaunch(lg.exec, ctx->stream));
     CU(cudaMemcpyAsync(ctx->h_sc, ctx->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
-    const Scalars s = *ctx->h_sc;
+    s = *ctx->h_sc;
+    launches = lg.init + (long long)s.it * lg.iter;
+    it_learned = s.it;
+    }
     int bits = s.info & 3;
     if (!ctx->net[TPMG_NET_WARM]) bits = 0;   // the guess judged was the caller's, not a network's
-    long long launches = lg.init + (long long)s.it * lg.iter;
-    *iters = s.it;
+    *iters = it_learned;
     double rel = s.ff > 0.0 ? std::sqrt(s.rr / s.ff) : 0.0;
     int it_fb = 0;
     tpmg_status st = TPMG_OK;

@@ -655,7 +655,7 @@ __global__ void __launch_bounds__(256) k_finish(int what, const double *__restri
     double v = 0.0, v2 = 0.0;
     for (int i = threadIdx.x; i < n; i += 256) v += partials[i];
     v = block_sum<256>(v);
-    if (what == FIN_LOOP_RR0F) {   // second set of partials: ||f||^2
+    if (what == FIN_LOOP_RR0F || what == FIN_RR0F) {   // second set of partials: ||f||^2
         for (int i = threadIdx.x; i < n; i += 256) v2 += partials[n + i];
         __syncthreads();
         v2 = block_sum<256>(v2);
@@ -708,6 +708,7 @@ __global__ void __launch_bounds__(256) k_finish(int what, const double *__restri
         cudaGraphSetConditional(loop.cond, (isfinite(v) && v > 0.0 && loop.max_iter > 0) ? 1u : 0u);
         break;
     }
+    case FIN_RR0F:
     case FIN_LOOP_RR0F: {
         // judge of the initial guess: kept only if its residual is below that of u = 0
         const bool keep = v < v2;
@@ -719,8 +720,10 @@ __global__ void __launch_bounds__(256) k_finish(int what, const double *__restri
         sc->it = 0;
         sc->flag = isfinite(rr) ? 0 : 2;
         const double rel = v2 > 0.0 ? sqrt(rr / v2) : 0.0;
-        if (loop.hist) loop.hist[0] = rel;
-        cudaGraphSetConditional(loop.cond, (isfinite(rr) && rr > 0.0 && !(rel <= loop.rtol) && loop.max_iter > 0) ? 1u : 0u);
+        if (what == FIN_LOOP_RR0F) {
+            if (loop.hist) loop.hist[0] = rel;
+            cudaGraphSetConditional(loop.cond, (isfinite(rr) && rr > 0.0 && !(rel <= loop.rtol) && loop.max_iter > 0) ? 1u : 0u);
+        }
         break;
     }
     case FIN_LOOP_BETA:

@@ -231,19 +231,20 @@ __global__ void k_round_bf16(long n, const float *__restrict__ w, uint16_t *__re
 
 // ---- features -------------------------------------------------------------
 
-// partials of sum over the level of (f_Tk / (|T| v_k))^2 (point values in
-// FP32, each thread's sum in FP32, the block's in double)
+// point values p = f / (|T| v_k) in FP32 -- each double converted once -- and
+// per-block partial sums of p^2 (each thread's sum in FP32, the block's in double)
 template <typename TF>
-__global__ void __launch_bounds__(256) k_net_scale(const TF *__restrict__ f, const float *__restrict__ iarea,
-                                                   const float *__restrict__ ivol, long N, int n_r,
-                                                   double *__restrict__ partials)
+__global__ void __launch_bounds__(256) k_net_prepare(const TF *__restrict__ f, const float *__restrict__ iarea,
+                                                     const float *__restrict__ ivol, long N, int n_r,
+                                                     float *__restrict__ p, double *__restrict__ partials)
 {
     float acc = 0.f;
     for (long i = blockIdx.x * 256L + threadIdx.x; i < N; i += (long)gridDim.x * 256) {
         const long T = i / n_r;
         const int k = (int)(i - T * n_r);
-        const float p = (float)f[i] * iarea[T] * ivol[k];
-        acc = fmaf(p, p, acc);
+        const float v = (float)f[i] * iarea[T] * ivol[k];
+        p[i] = v;
+        acc = fmaf(v, v, acc);
     }
     const double tot = block_sum_d<256>((double)acc);
     if (threadIdx.x == 0) partials[blockIdx.x] = tot;
@@ -258,11 +259,9 @@ __global__ void k_net_scale_finish(const double *__restrict__ partials, int np, 
     *s = sqrt(v / (double)N);
 }
 
-// inputs in FP32: point values p = f / (|T| v_k) of the column and the
-// flux-weighted mean over its edge neighbours, times 1 / s
-template <typename TF>
-__global__ void k_net_features(const TF *__restrict__ f, const float *__restrict__ iarea,
-                               const float *__restrict__ ivol, const int4 *__restrict__ nbr,
+// inputs from the FP32 point values: the column and the flux-weighted mean over
+// its edge neighbours, times 1 / s
+__global__ void k_net_features(const float *__restrict__ p, const int4 *__restrict__ nbr,
                                const float4 *__restrict__ wnb, const int *__restrict__ cells, long rows, int n_r,
                                const double *__restrict__ s, float *__restrict__ X)
 {
@@ -274,13 +273,10 @@ __global__ void k_net_features(const TF *__restrict__ f, const float *__restrict
         const long T = cells ? cells[j] : j;
         const int4 nb = nbr[T];
         const float4 w = wnb[T];
-        const float iv = ivol[k] * inv;
-        const float own = (float)f[T * n_r + k] * iarea[T];
-        const float mean = fmaf(w.z, (float)f[(long)nb.z * n_r + k] * iarea[nb.z],
-                                fmaf(w.y, (float)f[(long)nb.y * n_r + k] * iarea[nb.y],
-                                     w.x * ((float)f[(long)nb.x * n_r + k] * iarea[nb.x])));
-        X[j * 2 * n_r + k] = own * iv;
-        X[j * 2 * n_r + n_r + k] = mean * iv;
+        const float mean = fmaf(w.z, p[(long)nb.z * n_r + k], fmaf(w.y, p[(long)nb.y * n_r + k],
+                                                                   w.x * p[(long)nb.x * n_r + k]));
+        X[j * 2 * n_r + k] = p[T * n_r + k] * inv;
+        X[j * 2 * n_r + n_r + k] = mean * inv;
     }
 }
 
@@ -552,11 +548,11 @@ cudaError_t launch_net_fused(const Launch &L, const NetView &v, const float *X, 
 }
 
 template <typename TF>
-cudaError_t launch_net_scale(const Launch &L, const LevelDev &lv, const VertDev &vert, const TF *f, double *partials,
-                             int n_part)
+cudaError_t launch_net_prepare(const Launch &L, const LevelDev &lv, const VertDev &vert, const TF *f, float *p,
+                               double *partials, int n_part)
 {
     const long N = (long)lv.n * L.n_r;
-    k_net_scale<TF><<<n_part, 256, 0, L.s>>>(f, lv.iarea32, vert.ivol32, N, L.n_r, partials);
+    k_net_prepare<TF><<<n_part, 256, 0, L.s>>>(f, lv.iarea32, vert.ivol32, N, L.n_r, p, partials);
     return cudaGetLastError();
 }
 
@@ -566,13 +562,12 @@ cudaError_t launch_net_scale_finish(const Launch &L, const LevelDev &lv, const d
     return cudaGetLastError();
 }
 
-template <typename TF>
-cudaError_t launch_net_features(const Launch &L, const LevelDev &lv, const VertDev &vert, const TF *f, const int *cells,
-                                long rows, const double *s, float *X)
+cudaError_t launch_net_features(const Launch &L, const LevelDev &lv, const float *p, const int *cells, long rows,
+                                const double *s, float *X)
 {
     if (rows <= 0) return cudaSuccess;
-    k_net_features<TF><<<grid_1d(rows * L.n_r, 256, L.sm_count), 256, 0, L.s>>>(f, lv.iarea32, vert.ivol32, lv.nbr,
-                                                                             lv.wnb32, cells, rows, L.n_r, s, X);
+    k_net_features<<<grid_1d(rows * L.n_r, 256, L.sm_count), 256, 0, L.s>>>(p, lv.nbr, lv.wnb32, cells, rows, L.n_r,
+                                                                          s, X);
     return cudaGetLastError();
 }
 
@@ -602,12 +597,10 @@ cudaError_t launch_to_f32(const Launch &L, long n, const double *x, float *y)
     return cudaGetLastError();
 }
 
-template cudaError_t launch_net_scale<float>(const Launch &, const LevelDev &, const VertDev &, const float *, double *, int);
-template cudaError_t launch_net_scale<double>(const Launch &, const LevelDev &, const VertDev &, const double *, double *, int);
-template cudaError_t launch_net_features<float>(const Launch &, const LevelDev &, const VertDev &, const float *,
-                                                const int *, long, const double *, float *);
-template cudaError_t launch_net_features<double>(const Launch &, const LevelDev &, const VertDev &, const double *,
-                                                 const int *, long, const double *, float *);
+template cudaError_t launch_net_prepare<float>(const Launch &, const LevelDev &, const VertDev &, const float *, float *,
+                                               double *, int);
+template cudaError_t launch_net_prepare<double>(const Launch &, const LevelDev &, const VertDev &, const double *,
+                                                float *, double *, int);
 template cudaError_t launch_net_fused<float>(const Launch &, const NetView &, const float *, long, const double *, float *);
 template cudaError_t launch_net_fused<double>(const Launch &, const NetView &, const float *, long, const double *,
                                               double *);

@@ -187,7 +187,9 @@ enum FinishWhat { FIN_RR0 = 0, FIN_ALPHA = 1, FIN_RR = 2, FIN_BETA = 3, FIN_RZ0 
                   FIN_LOOP_RR0 = 7, FIN_LOOP_RR = 8, FIN_LOOP_BETA = 9, FIN_LOOP_BETA_PR = 10,
                   // learned solve: partials [0, n) of ||r_0||^2 and [n, 2n) of ||f||^2; the
                   // initial guess is rejected unless ||r_0|| < ||f||; rr0 = ||f||^2
-                  FIN_LOOP_RR0F = 11 };
+                  FIN_LOOP_RR0F = 11,
+                  // the same for the host-driven loop (no loop condition)
+                  FIN_RR0F = 12 };
 
 // learned.cu: the network of the learned form (tpmg_learned.h) -----------------
 struct NetView {            // device pointers of a network's weights
@@ -203,14 +205,14 @@ cudaError_t launch_net_layer(cudaStream_t s, const NetView &v, int l, const floa
 bool net_fused_ok(const NetView &v);
 template <typename TO>
 cudaError_t launch_net_fused(const Launch &L, const NetView &v, const float *X, long rows, const double *s, TO *out);
-// partials [n_part] of the squared point values of f on lv; the finish writes s
+// p = f / (|T| v_k) in FP32 (level size) and partials [n_part] of sum p^2; the finish writes s
 template <typename TF>
-cudaError_t launch_net_scale(const Launch &L, const LevelDev &lv, const VertDev &vert, const TF *f, double *partials,
-                             int n_part);
+cudaError_t launch_net_prepare(const Launch &L, const LevelDev &lv, const VertDev &vert, const TF *f, float *p,
+                               double *partials, int n_part);
 cudaError_t launch_net_scale_finish(const Launch &L, const LevelDev &lv, const double *partials, int n_part, double *s);
-template <typename TF>
-cudaError_t launch_net_features(const Launch &L, const LevelDev &lv, const VertDev &vert, const TF *f, const int *cells,
-                                long rows, const double *s, float *X);
+// X [rows][2 n_r] network inputs from the point values p of the level (cells NULL: rows 0..rows-1)
+cudaError_t launch_net_features(const Launch &L, const LevelDev &lv, const float *p, const int *cells, long rows,
+                                const double *s, float *X);
 cudaError_t launch_net_targets(const Launch &L, const double *u, const int *cells, long rows, const double *s, float *t);
 template <typename TO>
 cudaError_t launch_net_output(const Launch &L, const float *y, long n, const double *s, TO *u);

@@ -206,6 +206,25 @@ def test_learned_solve_without_networks_equals_flexible_cg():
     assert torch.equal(u1, u2)
 
 
+def test_learned_host_loop_matches_device_loop():
+    """graphs 0 (or a timed kernel class) runs the learned solve kernel by
+    kernel from the host: same kernels, same order, same bits."""
+    warm, _ = random_net(16, 64, seed=inputs.SEED_LEARNED + 90, scale=0.3)
+    coarse, _ = random_net(16, 64, seed=inputs.SEED_LEARNED + 91, scale=0.3)
+    outs = []
+    for graphs in (1, 0):
+        s = binding.Solver(graphs=graphs, **SMALL, **MIXED)
+        _, f = _smooth_rhs(s, inputs.SEED_LEARNED + 92)
+        s.attach_net(binding.TPMG_NET_WARM, warm)
+        s.attach_net(binding.TPMG_NET_COARSE, coarse)
+        u = torch.zeros_like(f)
+        res = s.solve_learned(f, u, rtol=1e-8, max_iter=60)
+        torch.cuda.synchronize()
+        outs.append((res[:5], u.cpu().numpy()))
+    assert outs[0][0] == outs[1][0], (outs[0][0], outs[1][0])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+
+
 def test_judge_rejects_a_useless_warm_start():
     """A network predicting a wildly wrong field: the judge replaces the guess
     by zero and the solve is the plain one, bit for bit.  A network predicting
