@@ -215,9 +215,10 @@ void tpmg_batch_destroy(tpmg_batch *b);
 tpmg_status tpmg_query(const tpmg_ctx *ctx, int level, int *n_cells, int *n_r, double *omega2, int *n_colours);
 
 /* The autotuner's choice on multigrid level `level`: variant = relaxation kernel
- * (0 one warp per 16-column task, 1/2/3 one CTA of 64/128/256 threads per
- * task, -1 heuristic: not tuned) and us[4] = measured microseconds of the
- * level's largest colour pass with each variant.  Any output may be NULL.
+ * (FP64: 0 one warp per 16-column task, 1/2/3 one CTA of 64/128/256 threads per
+ * task; mixed precision: one warp per column in CTAs of 1/2/4/8 warps; -1
+ * heuristic: not tuned) and us[4] = measured microseconds of the level's
+ * largest colour pass with each variant.  Any output may be NULL.
  * Errors: INVALID_ARG. */
 tpmg_status tpmg_query_tuning(const tpmg_ctx *ctx, int level, int *variant, float *us);
 

@@ -841,9 +841,8 @@ tpmg_status upload_level(tpmg_ctx *ctx, int l)
         CU(dalloc(ctx, &D.cpack, nn));
         CU(dalloc(ctx, &D.cvert, nn));
         CU(dalloc(ctx, &D.rinv32, nn));
-        CU(dalloc(ctx, &D.fb32, nf));
-        CU(dalloc(ctx, &D.fc32, nf));
-        CU(dalloc(ctx, &D.fm32, (size_t)D.n_tasks * 2 * kRelaxCols));
+        CU(dalloc(ctx, &D.fb32, nn));
+        CU(dalloc(ctx, &D.fc32, nn));
         CU(dalloc(ctx, &D.u32, nn));
         CU(dalloc(ctx, &D.u2_32, nn));
         if (l < p.n_levels - 1) CU(dalloc(ctx, &D.f32, nn));
@@ -873,7 +872,7 @@ tpmg_status upload_level(tpmg_ctx *ctx, int l)
     CU(cudaMemcpyAsync(D.task_nbr, tnb.data(), tnb.size() * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(D.task_g, tg.data(), tg.size() * sizeof(dbl4), cudaMemcpyHostToDevice, ctx->stream));
     if (!mixed) CU(launch_twisted_factors(launch_of(ctx), D, ctx->vert));
-    else CU(launch_twisted_factors32(launch_of(ctx), D));
+    else CU(launch_thomas_factors32(launch_of(ctx), D));
     // the host vectors above must outlive the asynchronous copies
     CU(cudaStreamSynchronize(ctx->stream));
     return TPMG_OK;

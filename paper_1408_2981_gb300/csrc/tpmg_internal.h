@@ -67,6 +67,8 @@ struct VertDev {            // vertical factors shared by every level (no vertic
 constexpr int kRelaxCols = 16;
 
 // Kernel variants of a relaxation pass (chosen per level by the autotuner).
+// FP64: one warp per 16-column task, or one CTA of 64 / 128 / 256 threads per
+// task.  FP32: one warp per column in CTAs of 1 / 2 / 4 / 8 warps.
 enum RelaxVariant { RELAX_WARP = 0, RELAX_CTA64 = 1, RELAX_CTA128 = 2, RELAX_CTA256 = 3, RELAX_VARIANTS = 4 };
 
 struct LevelDev {
@@ -101,8 +103,9 @@ struct LevelDev {
     // storage, Sec. 4.2) and FP32 work vectors on every level
     bf16x4 *cpack = nullptr;        // [n][n_r] {alphaS_hat e = 0, 1, 2, beta_hat}
     unsigned short *cvert = nullptr;   // [n][n_r] alphar_hat of face k (coupling to level k-1)
-    // twisted Thomas factors of the BF16 column blocks in FP32, laid out as rinv / fb / fc / fm
-    float *rinv32 = nullptr, *fb32 = nullptr, *fc32 = nullptr, *fm32 = nullptr;
+    // Thomas factors of the BF16 column blocks in FP32, per unknown [n][n_r] (bottom-up
+    // elimination): rinv32 = 1 / p_k, fb32 = c_k / p_k, fc32 = c_{k+1} / p_k
+    float *rinv32 = nullptr, *fb32 = nullptr, *fc32 = nullptr;
     float *f32 = nullptr, *u32 = nullptr, *u2_32 = nullptr;
 };
 
@@ -167,7 +170,7 @@ cudaError_t launch_resid_restrict32(const Launch &L, const LevelDev &fine, const
                                     const float *u, float *fc);
 cudaError_t launch_prolong_add32(const Launch &L, const LevelDev &fine, const float *uc, float *u);
 cudaError_t launch_to_f64(const Launch &L, long n, const float *x, double *y);
-cudaError_t launch_twisted_factors32(const Launch &L, const LevelDev &lv);
+cudaError_t launch_thomas_factors32(const Launch &L, const LevelDev &lv);
 cudaError_t launch_dot(const Launch &L, long n, const double *a, const double *b, double *partials, int n_part);
 cudaError_t launch_finish(const Launch &L, int what, const double *partials, int n_part, Scalars *sc,
                           const LoopCtl *loop = nullptr);
