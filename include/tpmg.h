@@ -105,12 +105,16 @@ typedef struct {
     int    autotune;     /* 1: tpmg_setup times the relaxation kernel variants on every level and
                             keeps the fastest (see tpmg_query_tuning); 0: a fixed heuristic.  The
                             results are identical. */
+    int    scan_max_cells; /* FP64 V-cycle: levels with at most this many cells relax one warp per
+                            column with the Thomas recurrences as warp scans (short latency, more
+                            FP64 work); larger levels use the 16-column twisted-factorisation tasks.
+                            A fixed rule, so the results do not depend on timings (>= 0). */
 } tpmg_params;
 
 /* Fills *p with the defaults: refinement 3, n_levels 4, n_r 16, H = 10/6371,
  * grading 1, omega2 0 with courant_c 8, nu 2/2/1, block-SOR with relax 1,
- * factorised storage, circumcentres, FP64, graphs and autotuning on.  Returns TPMG_ERR_INVALID_ARG if
- * p is NULL. */
+ * factorised storage, circumcentres, FP64, graphs and autotuning on,
+ * scan_max_cells 5120.  Returns TPMG_ERR_INVALID_ARG if p is NULL. */
 tpmg_status tpmg_default_params(tpmg_params *p);
 
 /* Builds the grid hierarchy, geometry, colouring and coefficients on the host

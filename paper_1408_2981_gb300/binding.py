@@ -63,7 +63,7 @@ class tpmg_params(ctypes.Structure):
                 ("courant_c", ctypes.c_double), ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int),
                 ("nu_coarse", ctypes.c_int), ("smoother", ctypes.c_int), ("relax", ctypes.c_double),
                 ("coeff_storage", ctypes.c_int), ("centre", ctypes.c_int), ("precision", ctypes.c_int),
-                ("graphs", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("graphs", ctypes.c_int), ("autotune", ctypes.c_int), ("scan_max_cells", ctypes.c_int)]
 
 
 class TPMGError(RuntimeError):

@@ -159,6 +159,7 @@ bool validate(const tpmg_params *p, std::string &msg)
     }
     if (p->graphs != 0 && p->graphs != 1) { msg = "graphs must be 0 or 1"; return false; }
     if (p->autotune != 0 && p->autotune != 1) { msg = "autotune must be 0 or 1"; return false; }
+    if (p->scan_max_cells < 0) { msg = "scan_max_cells must be >= 0"; return false; }
     return true;
 }
 
@@ -815,6 +816,12 @@ tpmg_status upload_level(tpmg_ctx *ctx, int l)
     CU(dalloc(ctx, &D.task_g, tasks.size()));
     const bool mixed = p.precision == TPMG_PREC_MIXED;
     if (!mixed) {
+        D.scan = H.n <= p.scan_max_cells;
+        if (D.scan) {
+            CU(dalloc(ctx, &D.rinv1, nn));
+            CU(dalloc(ctx, &D.fb1, nn));
+            CU(dalloc(ctx, &D.fc1, nn));
+        }
         CU(dalloc(ctx, &D.rinv, nn));
         CU(dalloc(ctx, &D.fb, nf));
         CU(dalloc(ctx, &D.fc, nf));
@@ -871,8 +878,12 @@ tpmg_status upload_level(tpmg_ctx *ctx, int l)
         if (tasks[q] >= 0) { tnb[q] = nb[tasks[q]]; tg[q] = g[tasks[q]]; }
     CU(cudaMemcpyAsync(D.task_nbr, tnb.data(), tnb.size() * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(D.task_g, tg.data(), tg.size() * sizeof(dbl4), cudaMemcpyHostToDevice, ctx->stream));
-    if (!mixed) CU(launch_twisted_factors(launch_of(ctx), D, ctx->vert));
-    else CU(launch_thomas_factors32(launch_of(ctx), D));
+    if (!mixed) {
+        CU(launch_twisted_factors(launch_of(ctx), D, ctx->vert));
+        if (D.scan) CU(launch_thomas_factors(launch_of(ctx), D, ctx->vert));
+    } else {
+        CU(launch_thomas_factors32(launch_of(ctx), D));
+    }
     // the host vectors above must outlive the asynchronous copies
     CU(cudaStreamSynchronize(ctx->stream));
     return TPMG_OK;
@@ -954,6 +965,7 @@ tpmg_status tpmg_default_params(tpmg_params *p)
     p->precision = TPMG_PREC_FP64;
     p->graphs = 1;
     p->autotune = 1;
+    p->scan_max_cells = 5120;
     return TPMG_OK;
 }
 

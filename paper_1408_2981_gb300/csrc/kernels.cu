@@ -340,6 +340,124 @@ __device__ __forceinline__ void twisted_solve(const double *B, const double *C, 
 // weight, optional prolongation into the 4 children (u_fine += P x), loads
 // issued before their stores.  In the multicolour passes u_in == u_out: a pass
 // reads other colours' columns and its own column before writing it.
+// One-directional Thomas factors per unknown (levels relaxed by k_relax_scan):
+// the excess-carried recurrence (reading C16) from the bottom row upwards,
+//   e_0 = m_0, e_k = m_k + c_k e_{k-1} / p_{k-1}, p_k = e_k + c_{k+1},
+// rinv = 1 / p_k, fb = c_k / p_k (0 for k = 0), fc = c_{k+1} / p_k.
+__global__ void k_thomas_factors(OpView o, int n_cells, double *__restrict__ rinv, double *__restrict__ fb,
+                                 double *__restrict__ fc)
+{
+    const int T = blockIdx.x * blockDim.x + threadIdx.x;
+    if (T >= n_cells) return;
+    const int n = o.n_r;
+    const size_t row0 = (size_t)T * n;
+    const double A = o.area[T], G = o.g[T].w;
+    double e = 0.0, p = 1.0;
+    for (int k = 0; k < n; ++k) {
+        const double m = fma(A, o.vol[k], o.hr[k] * G);
+        const double c = k > 0 ? A * o.w[k] : 0.0, cu = k < n - 1 ? A * o.w[k + 1] : 0.0;
+        e = k == 0 ? m : m + c * e / p;
+        p = e + cu;
+        const double iv = 1.0 / p;
+        rinv[row0 + k] = iv;
+        fb[row0 + k] = c * iv;
+        fc[row0 + k] = cu * iv;
+    }
+}
+
+// One relaxation pass (eq. BlockJacobi) in FP64 with one warp per column, for
+// levels whose passes are latency-bound (few columns per colour): row k on
+// lane k mod 32, the Thomas recurrences y_k = t_k + fb_k y_{k-1} and
+// x_k = y_k + fc_k x_{k+1} as warp-shuffle scans of affine maps, 32 rows at a
+// time (no shared memory, no barrier, no serial chain of n_r FP64 FMAs).  The
+// right-hand side is formed exactly as in k_relax.
+template <int MODE, int R>
+__global__ void __launch_bounds__(256)
+    k_relax_scan(OpView o, const int *__restrict__ cells, const int4 *__restrict__ tnb, const dbl4 *__restrict__ tg,
+                 const double *__restrict__ rinv, const double *__restrict__ fb, const double *__restrict__ fcf,
+                 int slot0, int n_slots, const double *__restrict__ f, const double *u_in, double *u_out,
+                 double *__restrict__ u_fine, double relax)
+{
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (w >= n_slots) return;
+    const int T = __ldg(&cells[slot0 + w]);
+    if (T < 0) return;
+    const int n_r = o.n_r;
+    const int4 nb = MODE == PASS_RHS_ONLY ? make_int4(0, 0, 0, 0) : __ldg(&tnb[slot0 + w]);
+    const dbl4 g = MODE == PASS_RHS_ONLY ? dbl4{0.0, 0.0, 0.0, 0.0} : tg[slot0 + w];
+    const bool n0 = MODE == PASS_NORMAL || (nb.w & 1), n1 = MODE == PASS_NORMAL || (nb.w & 2),
+               n2 = MODE == PASS_NORMAL || (nb.w & 4);
+    const size_t base = (size_t)T * n_r;
+    double x[R];
+    double carry = 0.0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int k = 32 * r + lane;
+        double A = 0.0, B = 0.0;
+        if (k < n_r) {
+            const size_t i = base + k;
+            double d = f[i];
+            if (MODE != PASS_RHS_ONLY) {
+                const double v0 = n0 ? u_in[(size_t)nb.x * n_r + k] : 0.0;
+                const double v1 = n1 ? u_in[(size_t)nb.y * n_r + k] : 0.0;
+                const double v2 = n2 ? u_in[(size_t)nb.z * n_r + k] : 0.0;
+                d = fma(__ldg(&o.hr[k]), fma(g.z, v2, fma(g.y, v1, g.x * v0)), d);
+            }
+            B = d * __ldg(&rinv[i]);
+            A = __ldg(&fb[i]);
+        }
+#pragma unroll
+        for (int s = 1; s < 32; s <<= 1) {
+            const double Ap = __shfl_up_sync(full, A, s), Bp = __shfl_up_sync(full, B, s);
+            if (lane >= s) {
+                B = fma(A, Bp, B);
+                A *= Ap;
+            }
+        }
+        x[r] = fma(A, carry, B);
+        carry = __shfl_sync(full, x[r], 31);
+    }
+    carry = 0.0;
+#pragma unroll
+    for (int r = R - 1; r >= 0; --r) {
+        const int k = 32 * r + lane;
+        double A = 0.0, B = 0.0;
+        if (k < n_r) {
+            A = __ldg(&fcf[base + k]);
+            B = x[r];
+        }
+#pragma unroll
+        for (int s = 1; s < 32; s <<= 1) {
+            const double Ad = __shfl_down_sync(full, A, s), Bd = __shfl_down_sync(full, B, s);
+            if (lane + s < 32) {
+                B = fma(A, Bd, B);
+                A *= Ad;
+            }
+        }
+        x[r] = fma(A, carry, B);
+        carry = __shfl_sync(full, x[r], 0);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int k = 32 * r + lane;
+        if (k >= n_r) continue;
+        const size_t i = base + k;
+        double v = x[r];
+        if (relax != 1.0) {   // from a zero guess (ZERO, RHS_ONLY) the old value is 0
+            const double uo = MODE == PASS_NORMAL ? u_in[i] : 0.0;
+            v = fma(relax, v - uo, uo);
+        }
+        u_out[i] = v;
+        if (u_fine) {
+            const size_t fi = (size_t)4 * T * n_r + k;
+#pragma unroll
+            for (int h = 0; h < 4; ++h) u_fine[fi + (size_t)h * n_r] += v;
+        }
+    }
+}
+
 template <int MODE, bool STAGE, int NT>
 __global__ void __launch_bounds__(NT, STAGE ? 1 : 6)
     k_relax(OpView o, const int *__restrict__ cells, const int4 *__restrict__ tnb, const dbl4 *__restrict__ tg,
@@ -821,11 +939,38 @@ static cudaError_t relax_launch_t(const Launch &L, const LevelDev &lv, const Ver
 // at most 32 KB -> one warp per task, otherwise one 128-thread CTA per task.
 // CTA variants stage the multipliers in shared memory by cp.async when they
 // fit; a column too tall for that runs unstaged with 128 threads.
+template <int MODE, int R>
+static cudaError_t relax_scan_r(const Launch &L, const LevelDev &lv, const VertDev &v, int task0, int n_tasks,
+                                double relax, const double *f, const double *u_in, double *u_out, double *u_fine)
+{
+    const int var = lv.relax_variant < 0 ? RELAX_CTA128 : lv.relax_variant;
+    const int wpb = 1 << var;   // CTAs of 1, 2, 4 or 8 warps: the autotuner's variants, same arithmetic
+    const int n_slots = n_tasks * kRelaxCols;
+    k_relax_scan<MODE, R><<<(n_slots + wpb - 1) / wpb, 32 * wpb, 0, L.s>>>(
+        make_view(lv, v, L.n_r), lv.task_cells, lv.task_nbr, lv.task_g, lv.rinv1, lv.fb1, lv.fc1, task0 * kRelaxCols,
+        n_slots, f, u_in, u_out, u_fine, relax);
+    return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t relax_scan(const Launch &L, const LevelDev &lv, const VertDev &v, int task0, int n_tasks,
+                              double relax, const double *f, const double *u_in, double *u_out, double *u_fine)
+{
+    const int n = L.n_r;
+    if (n <= 32) return relax_scan_r<MODE, 1>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
+    if (n <= 64) return relax_scan_r<MODE, 2>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
+    if (n <= 128) return relax_scan_r<MODE, 4>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
+    if (n <= 256) return relax_scan_r<MODE, 8>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
+    if (n <= 512) return relax_scan_r<MODE, 16>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
+    return relax_scan_r<MODE, 32>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
+}
+
 template <int MODE>
 static cudaError_t relax_launch(const Launch &L, const LevelDev &lv, const VertDev &v, int task0, int n_tasks,
                                 double relax, const double *f, const double *u_in, double *u_out, double *u_fine)
 {
     if (n_tasks <= 0) return cudaSuccess;
+    if (lv.scan) return relax_scan<MODE>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
     const size_t tile = (((size_t)kRelaxCols * (L.n_r + 1) + 1) & ~(size_t)1) * sizeof(double);
     int var = lv.relax_variant;
     if (var < 0) var = (n_tasks >= 8 * L.sm_count && tile <= 32 * 1024) ? RELAX_WARP : RELAX_CTA128;
@@ -843,6 +988,12 @@ static cudaError_t relax_launch(const Launch &L, const LevelDev &lv, const VertD
     if (var == RELAX_CTA256)
         return relax_launch_t<MODE, true, 256>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine, staged);
     return relax_launch_t<MODE, true, 128>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine, staged);
+}
+
+cudaError_t launch_thomas_factors(const Launch &L, const LevelDev &lv, const VertDev &v)
+{
+    k_thomas_factors<<<(lv.n + 127) / 128, 128, 0, L.s>>>(make_view(lv, v, L.n_r), lv.n, lv.rinv1, lv.fb1, lv.fc1);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_relax(const Launch &L, const LevelDev &lv, const VertDev &v, int mode, int task0, int n_tasks,

@@ -97,6 +97,11 @@ struct LevelDev {
     //   bottom lane (row k = n_r-1-s): fb = c_{k+1}/q_k, fc = c_k/q_k
     // fm [n_tasks][2][16] meeting row: c_j/gamma, c_{j+1}/gamma
     double *rinv = nullptr, *fb = nullptr, *fc = nullptr, *fm = nullptr;
+    // FP64 levels with at most params.scan_max_cells cells: relaxed one warp per column
+    // (k_relax_scan) with one-directional factors per unknown [n][n_r]:
+    // rinv1 = 1 / p_k, fb1 = c_k / p_k, fc1 = c_{k+1} / p_k
+    bool scan = false;
+    double *rinv1 = nullptr, *fb1 = nullptr, *fc1 = nullptr;
     // workspaces (coarse levels; the finest level uses caller / PCG buffers)
     double *f = nullptr, *u = nullptr, *u2 = nullptr;
     // mixed-precision form: the stencil stored per unknown in BF16 (full
@@ -160,6 +165,7 @@ cudaError_t launch_relax(const Launch &L, const LevelDev &lv, const VertDev &v, 
                          double relax, const double *f, const double *u_in, double *u_out, double *u_fine);
 cudaError_t launch_prolong_add(const Launch &L, const LevelDev &fine, const double *uc, double *u);
 cudaError_t launch_twisted_factors(const Launch &L, const LevelDev &lv, const VertDev &v);
+cudaError_t launch_thomas_factors(const Launch &L, const LevelDev &lv, const VertDev &v);
 // Mixed-precision V-cycle (FP32 arithmetic, BF16 stencil).  TF is the type of
 // the right-hand side (double on the finest level, float below).
 template <typename TF>
