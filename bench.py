@@ -116,7 +116,7 @@ PER_UNIT = {
 }
 # DRAM bytes per launch of a kernel class from an ncu capture (profiles/), valid
 # while kernels.cu is the file that was profiled (sha256 prefix)
-TRAFFIC = {"relax": {"bytes_per_launch": 18.16e6, "kernels_sha256": "8127efee1267ae08",
+TRAFFIC = {"relax": {"bytes_per_launch": 18.27e6, "kernels_sha256": "2ee09730ea09aba5",
                      "source": "profiles/relax_dram_81920x64.md", "workload": "81920x64"}}
 SM_COUNT_GB300 = 152
 FP64_FMA_PER_CLK_PER_SM = 2     # GB300: 1.25 TFLOP/s dense FP64 at 2.07 GHz over 152 SMs
@@ -431,7 +431,10 @@ def run_tpmg(args, wl):
                 "timed_launches": d["timed"],
                 "hbm_gbs_algorithmic": nbytes / (d["ms"] / 1e3) / 1e9,
                 "hbm_frac_of_measured": nbytes / (d["ms"] / 1e3) / 1e9 / peaks["hbm_gbs"],
-                "share_of_step": d["ms"] / (local_ms / args.steps)})
+                # average timed launch x the class's launches per step (a replayed graph's
+                # event pairs hold its last replay only)
+                "share_of_step": (d["ms"] / d["timed"]) * ((d["launches"] - before[dominant]["launches"]) / args.steps)
+                                 / (local_ms / args.steps)})
     # aggregate algorithmic HBM rate of the whole solve
     tot_bytes = sum(per_unit.get(c, (0.0, 0.0))[1] * (v["units"] - before[c]["units"]) for c, v in prof.items())
     hbm = {"achieved_gbs": tot_bytes / (local_ms / 1e3) / 1e9, "peak_gbs": peaks["hbm_gbs"],

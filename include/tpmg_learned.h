@@ -95,7 +95,7 @@ void tpmg_net_destroy(tpmg_net *net);
 /* Network inputs of `rows` columns of multigrid level `level` of ctx for the
  * field d_f (doubles, n_cells*n_r of that level, cell integrals): d_cells
  * (device ints, nullable = columns 0..rows-1) selects the columns, d_x
- * receives [rows][2 n_r] floats.  The scale s is taken over the whole level
+ * receives [rows][2 n_r] floats (rows * n_r < 2^31).  The scale s is taken over the whole level
  * field; h_scale (nullable) receives it (synchronises).  Asynchronous on the
  * context stream otherwise.  Errors: INVALID_ARG, CUDA. */
 tpmg_status tpmg_net_features(tpmg_ctx *ctx, int level, const double *d_f, const int *d_cells, long rows, float *d_x,

@@ -1289,8 +1289,9 @@ tpmg_status level_arg(tpmg_ctx *ctx, int level, const void *a, const void *b, lo
     if (!ctx) return TPMG_ERR_INVALID_ARG;
     if (level < 0 || level >= ctx->p.n_levels) return fail(ctx, TPMG_ERR_INVALID_ARG, "level out of range");
     if (!a || !b) return fail(ctx, TPMG_ERR_INVALID_ARG, "NULL argument");
-    if (rows < 1 || (!cells && rows > ctx->lv[level].n) || rows > 64L * 65535L)
-        return fail(ctx, TPMG_ERR_INVALID_ARG, "rows out of range");
+    if (rows < 1 || (!cells && rows > ctx->lv[level].n) || rows > 64L * 65535L ||
+        (double)rows * ctx->p.n_r > 2147483647.0)
+        return fail(ctx, TPMG_ERR_INVALID_ARG, "rows out of range (rows * n_r must fit in a 32-bit index)");
     return TPMG_OK;
 }
 

@@ -198,12 +198,14 @@ __global__ void __launch_bounds__(256) k_mse(const float *__restrict__ y, const 
     if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
-__global__ void k_loss_finish(const double *__restrict__ partials, int np, long n, double *__restrict__ loss)
+// one block of 256 threads: a fixed-order tree sum of the partials
+__global__ void __launch_bounds__(256) k_loss_finish(const double *__restrict__ partials, int np, long n,
+                                                     double *__restrict__ loss)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double s = 0.0;
-    for (int i = 0; i < np; ++i) s += partials[i];
-    *loss = s / (double)n;
+    double v = 0.0;
+    for (int i = threadIdx.x; i < np; i += 256) v += partials[i];
+    v = block_sum_d<256>(v);
+    if (threadIdx.x == 0) *loss = v / (double)n;
 }
 
 // Adam with bias correction (c1 = 1 - b1^t, c2 = 1 - b2^t); refreshes the bfloat16 copy
@@ -239,9 +241,10 @@ __global__ void __launch_bounds__(256) k_net_prepare(const TF *__restrict__ f, c
                                                      float *__restrict__ p, double *__restrict__ partials)
 {
     float acc = 0.f;
-    for (long i = blockIdx.x * 256L + threadIdx.x; i < N; i += (long)gridDim.x * 256) {
-        const long T = i / n_r;
-        const int k = (int)(i - T * n_r);
+    // 32-bit indices: a level holds fewer than 2^31 unknowns (checked at set-up)
+    for (int i = blockIdx.x * 256 + threadIdx.x; i < (int)N; i += gridDim.x * 256) {
+        const int T = i / n_r;
+        const int k = i - T * n_r;
         const float v = (float)f[i] * iarea[T] * ivol[k];
         p[i] = v;
         acc = fmaf(v, v, acc);
@@ -250,13 +253,14 @@ __global__ void __launch_bounds__(256) k_net_prepare(const TF *__restrict__ f, c
     if (threadIdx.x == 0) partials[blockIdx.x] = tot;
 }
 
-// s = sqrt(sum / N) (0 for a zero field)
-__global__ void k_net_scale_finish(const double *__restrict__ partials, int np, long N, double *__restrict__ s)
+// s = sqrt(sum / N) (0 for a zero field); one block of 256 threads, fixed-order tree sum
+__global__ void __launch_bounds__(256) k_net_scale_finish(const double *__restrict__ partials, int np, long N,
+                                                          double *__restrict__ s)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double v = 0.0;
-    for (int i = 0; i < np; ++i) v += partials[i];
-    *s = sqrt(v / (double)N);
+    for (int i = threadIdx.x; i < np; i += 256) v += partials[i];
+    v = block_sum_d<256>(v);
+    if (threadIdx.x == 0) *s = sqrt(v / (double)N);
 }
 
 // inputs from the FP32 point values: the column and the flux-weighted mean over
@@ -267,16 +271,17 @@ __global__ void k_net_features(const float *__restrict__ p, const int4 *__restri
 {
     const double sv = *s;
     const float inv = sv > 0.0 ? (float)(1.0 / sv) : 0.f;
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < rows * n_r; i += (long)gridDim.x * blockDim.x) {
-        const long j = i / n_r;
-        const int k = (int)(i - j * n_r);
-        const long T = cells ? cells[j] : j;
+    const int n = (int)(rows * n_r);   // < 2^31: rows * 2 n_r floats are addressed in 64 bits below
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int j = i / n_r;
+        const int k = i - j * n_r;
+        const int T = cells ? cells[j] : j;
         const int4 nb = nbr[T];
         const float4 w = wnb[T];
-        const float mean = fmaf(w.z, p[(long)nb.z * n_r + k], fmaf(w.y, p[(long)nb.y * n_r + k],
-                                                                   w.x * p[(long)nb.x * n_r + k]));
-        X[j * 2 * n_r + k] = p[T * n_r + k] * inv;
-        X[j * 2 * n_r + n_r + k] = mean * inv;
+        const float mean = fmaf(w.z, p[nb.z * n_r + k], fmaf(w.y, p[nb.y * n_r + k], w.x * p[nb.x * n_r + k]));
+        float *xr = X + (size_t)j * 2 * n_r;
+        xr[k] = p[T * n_r + k] * inv;
+        xr[n_r + k] = mean * inv;
     }
 }
 
@@ -329,7 +334,7 @@ __global__ void k_to_f32(long n, const double *__restrict__ x, float *__restrict
 // 16-wide k-step of the next layer.  Inputs are rounded to bfloat16 as they
 // are loaded.  Hidden width 64; n_r a multiple of 8.
 constexpr int kFusedH = 64;
-constexpr int kFusedWarps = 4;
+constexpr int kFusedWarps = 8;
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
@@ -536,7 +541,6 @@ cudaError_t launch_net_fused(const Launch &L, const NetView &v, const float *X, 
 {
     const int n_r = v.sizes[4];
     const size_t smem = fused_smem_bytes(n_r);
-    static_assert(kFusedWarps == 4, "launch shape");
     cudaError_t e = cudaFuncSetAttribute(k_mlp_fused<TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const long tiles = (rows + 15) / 16;
@@ -558,7 +562,7 @@ cudaError_t launch_net_prepare(const Launch &L, const LevelDev &lv, const VertDe
 
 cudaError_t launch_net_scale_finish(const Launch &L, const LevelDev &lv, const double *partials, int n_part, double *s)
 {
-    k_net_scale_finish<<<1, 32, 0, L.s>>>(partials, n_part, (long)lv.n * L.n_r, s);
+    k_net_scale_finish<<<1, 256, 0, L.s>>>(partials, n_part, (long)lv.n * L.n_r, s);
     return cudaGetLastError();
 }
 
@@ -688,7 +692,7 @@ tpmg_status backward_ws(tpmg_net *net, const float *x, const float *t, long rows
     const long n = rows * out;
     k_mse<<<kLossBlocks, 256, 0, net->stream>>>(y, t, n, g0, net->d_part);
     NCU(cudaGetLastError());
-    k_loss_finish<<<1, 32, 0, net->stream>>>(net->d_part, kLossBlocks, n, net->d_loss);
+    k_loss_finish<<<1, 256, 0, net->stream>>>(net->d_part, kLossBlocks, n, net->d_loss);
     NCU(cudaGetLastError());
     const int splits = (int)std::min<long>(64, std::max<long>(1, rows / 256));
     const NetView v = net_view(net);
