@@ -69,6 +69,12 @@ enum { TPMG_SMOOTH_MCSOR = 0,   /* multicolour block-SOR: forward colours before
  * factorised FP64 one. */
 enum { TPMG_COEFF_FACTORISED = 0, TPMG_COEFF_FULL = 1 };
 
+/* Outer iteration of tpmg_solve (Sec. 5 uses Richardson and BiCGStab; with constant
+ * profiles the operator and the V-cycle are symmetric positive definite, so CG applies). */
+enum { TPMG_OUTER_CG = 0,          /* preconditioned CG (flexible CG in the mixed-precision form) */
+       TPMG_OUTER_RICHARDSON = 1,  /* u <- u + B (f - A u) */
+       TPMG_OUTER_BICGSTAB = 2 };  /* BiCGStab, preconditioned from the right (2 V-cycles per iteration) */
+
 /* Cell centre used by the two-point flux of Appendix A. */
 enum { TPMG_CENTRE_CIRCUM = 0,      /* spherical circumcentre (centre chord normal to the edge) */
        TPMG_CENTRE_VERTEX_MEAN = 1 };
@@ -109,12 +115,15 @@ typedef struct {
                             column with the Thomas recurrences as warp scans (short latency, more
                             FP64 work); larger levels use the 16-column twisted-factorisation tasks.
                             A fixed rule, so the results do not depend on timings (>= 0). */
+    int    outer;        /* TPMG_OUTER_*: the outer iteration of tpmg_solve.  Richardson and
+                            BiCGStab run their loop from the host (one read-back per dot product)
+                            and are not available in a batch. */
 } tpmg_params;
 
 /* Fills *p with the defaults: refinement 3, n_levels 4, n_r 16, H = 10/6371,
  * grading 1, omega2 0 with courant_c 8, nu 2/2/1, block-SOR with relax 1,
  * factorised storage, circumcentres, FP64, graphs and autotuning on,
- * scan_max_cells 5120.  Returns TPMG_ERR_INVALID_ARG if p is NULL. */
+ * scan_max_cells 5120, outer CG.  Returns TPMG_ERR_INVALID_ARG if p is NULL. */
 tpmg_status tpmg_default_params(tpmg_params *p);
 
 /* Builds the grid hierarchy, geometry, colouring and coefficients on the host
@@ -167,9 +176,11 @@ tpmg_status tpmg_vcycle(tpmg_ctx *ctx, const double *d_r, double *d_z);
  * Asynchronous on the context stream.  Errors: INVALID_ARG, CUDA. */
 tpmg_status tpmg_vcycle_noalloc(tpmg_ctx *ctx, const double *d_r, double *d_z);
 
-/* Preconditioned CG for A u = f with B = one V-cycle.  d_u holds the initial
- * guess on entry and the solution on return.  Stops when ||r_k||_2 <=
- * rtol * ||r_0||_2 (recursively updated residual; Sec. 5 uses rtol = 1e-5).
+/* The outer iteration params.outer (preconditioned CG by default) for A u = f
+ * with B = one V-cycle.  d_u holds the initial guess on entry and the solution
+ * on return.  Stops when ||r_k||_2 <= rtol * ||r_0||_2 (recursively updated
+ * residual for CG and BiCGStab, the true residual for Richardson; Sec. 5 uses
+ * rtol = 1e-5).  *iters counts outer iterations (BiCGStab: 2 V-cycles each).
  * *iters = number of products q = A p; *rel_resid = ||r_k|| / ||r_0||.
  * resid_hist (host, nullable, max_iter+1 doubles) receives ||r_k|| / ||r_0||
  * for k = 0..*iters.  Synchronises the context stream before returning.

@@ -82,6 +82,7 @@ def _load(path: str | None = None):
         lib.oracle_bf16.argtypes = [_D]
         lib.oracle_bf16.restype = _D
         lib.oracle_richardson.argtypes = [_P, _P, _P, _I, _P]
+        lib.oracle_bicgstab.argtypes = [_P, _P, _P, _D, _I, _P, _P, _P]
         lib.oracle_thomas.argtypes = [_I, _P, _P, _P, _P, _P]
         lib.oracle_column_solve.argtypes = [_I, _P, _P, _P, _P]
         lib.oracle_column_couplings.argtypes = [_P, _I, _P, _P]
@@ -301,6 +302,16 @@ class Oracle:
         hist = np.zeros(n_iter + 1)
         self._lib.oracle_richardson(self._h, _ptr(f), _ptr(u), n_iter, _ptr(hist))
         return u, hist
+
+    def bicgstab(self, f, u0=None, rtol: float = 1e-5, max_iter: int = 100) -> dict:
+        """BiCGStab preconditioned from the right by one V-cycle per application."""
+        f = _f64(f).reshape(-1)
+        u = np.zeros_like(f) if u0 is None else _f64(u0).reshape(-1).copy()
+        it = np.zeros(1, dtype=np.int32)
+        rel = np.zeros(1)
+        hist = np.zeros(max_iter + 1)
+        st = self._lib.oracle_bicgstab(self._h, _ptr(f), _ptr(u), rtol, max_iter, _ptr(it), _ptr(rel), _ptr(hist))
+        return dict(u=u, status=int(st), iters=int(it[0]), rel_resid=float(rel[0]), hist=hist[:int(it[0]) + 1])
 
     def dense_operator(self, level: int | None = None) -> np.ndarray:
         """Assemble A column by column from the matrix-free apply (tiny grids only)."""

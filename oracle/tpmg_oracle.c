@@ -1012,6 +1012,69 @@ done:
 
 /* Preconditioned Richardson iteration u <- u + B (f - A u), n_iter steps
  * (Sec. 3.3).  hist (nullable, n_iter+1) receives ||f - A u_k||_2. */
+/* BiCGStab (van der Vorst 1992) preconditioned from the right with one V-cycle
+ * per preconditioner application (the paper's Sec. 5 alternative to
+ * Richardson): with r^ = r_0,
+ *   rho = <r^, r>,  beta = (rho / rho_prev)(alpha / omega),  p = r + beta (p - omega v),
+ *   y = B p,  v = A y,  alpha = rho / <r^, v>,  s = r - alpha v,
+ *   z = B s,  t = A z,  omega = <t, s> / <t, t>,
+ *   u = u + alpha y + omega z,  r = s - omega t,
+ * stopping when ||r_k|| <= rtol ||r_0|| (recursively updated residual).  Returns 0
+ * (converged), 1 (max_iter), -3 (breakdown: rho, <r^, v> or <t, t> zero or not finite). */
+int oracle_bicgstab(void *h, const double *f, double *u, double rtol, int max_iter, int *iters, double *rel_resid,
+                    double *hist)
+{
+    octx *o = (octx *)h;
+    int lf = o->n_levels - 1, it, status = 1;
+    size_t N = (size_t)mg_grid(o, lf)->n_cells * o->n_r, i;
+    double *r = (double *)calloc(N, sizeof(double)), *rh = (double *)calloc(N, sizeof(double));
+    double *p = (double *)calloc(N, sizeof(double)), *v = (double *)calloc(N, sizeof(double));
+    double *y = (double *)calloc(N, sizeof(double)), *sv = (double *)calloc(N, sizeof(double));
+    double *z = (double *)calloc(N, sizeof(double)), *t = (double *)calloc(N, sizeof(double));
+    double rho_prev = 1.0, alpha = 1.0, omega = 1.0, rnorm0;
+    *iters = 0;
+    *rel_resid = 1.0;
+    if (!r || !rh || !p || !v || !y || !sv || !z || !t) { status = -2; goto done; }
+    apply_level(o, lf, u, t);
+    for (i = 0; i < N; ++i) r[i] = f[i] - t[i];
+    memcpy(rh, r, N * sizeof(double));
+    rnorm0 = sqrt(dot(N, r, r));
+    if (hist) hist[0] = 1.0;
+    if (!isfinite(rnorm0)) { status = -3; goto done; }
+    if (rnorm0 == 0.0) { *rel_resid = 0.0; status = 0; goto done; }
+    for (it = 0; it < max_iter; ++it) {
+        double rho = dot(N, rh, r), beta, rv, tt, rel;
+        if (!(rho != 0.0) || !isfinite(rho)) { status = -3; break; }
+        beta = (rho / rho_prev) * (alpha / omega);
+        for (i = 0; i < N; ++i) p[i] = r[i] + beta * (p[i] - omega * v[i]);
+        oracle_vcycle(h, p, y);
+        apply_level(o, lf, y, v);
+        rv = dot(N, rh, v);
+        if (!(rv != 0.0) || !isfinite(rv)) { status = -3; break; }
+        alpha = rho / rv;
+        for (i = 0; i < N; ++i) sv[i] = r[i] - alpha * v[i];
+        oracle_vcycle(h, sv, z);
+        apply_level(o, lf, z, t);
+        tt = dot(N, t, t);
+        if (!(tt > 0.0) || !isfinite(tt)) { status = -3; break; }
+        omega = dot(N, t, sv) / tt;
+        for (i = 0; i < N; ++i) {
+            u[i] += alpha * y[i] + omega * z[i];
+            r[i] = sv[i] - omega * t[i];
+        }
+        rho_prev = rho;
+        rel = sqrt(dot(N, r, r)) / rnorm0;
+        *iters = it + 1;
+        *rel_resid = rel;
+        if (hist) hist[it + 1] = rel;
+        if (!isfinite(rel)) { status = -3; break; }
+        if (rel <= rtol) { status = 0; break; }
+    }
+done:
+    free(r); free(rh); free(p); free(v); free(y); free(sv); free(z); free(t);
+    return status;
+}
+
 int oracle_richardson(void *h, const double *f, double *u, int n_iter, double *hist)
 {
     octx *o = (octx *)h;

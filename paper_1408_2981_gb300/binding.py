@@ -32,6 +32,9 @@ TPMG_CENTRE_CIRCUM = 0
 TPMG_CENTRE_VERTEX_MEAN = 1
 TPMG_PREC_FP64 = 0
 TPMG_PREC_MIXED = 1
+TPMG_OUTER_CG = 0
+TPMG_OUTER_RICHARDSON = 1
+TPMG_OUTER_BICGSTAB = 2
 
 # every entry point declared in include/tpmg.h
 EXPORTS = ["tpmg_default_params", "tpmg_setup", "tpmg_apply_operator", "tpmg_vcycle", "tpmg_vcycle_noalloc",
@@ -63,7 +66,8 @@ class tpmg_params(ctypes.Structure):
                 ("courant_c", ctypes.c_double), ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int),
                 ("nu_coarse", ctypes.c_int), ("smoother", ctypes.c_int), ("relax", ctypes.c_double),
                 ("coeff_storage", ctypes.c_int), ("centre", ctypes.c_int), ("precision", ctypes.c_int),
-                ("graphs", ctypes.c_int), ("autotune", ctypes.c_int), ("scan_max_cells", ctypes.c_int)]
+                ("graphs", ctypes.c_int), ("autotune", ctypes.c_int), ("scan_max_cells", ctypes.c_int),
+                ("outer", ctypes.c_int)]
 
 
 class TPMGError(RuntimeError):

@@ -75,6 +75,7 @@ struct tpmg_ctx {
         const tpmg_net *nets[2] = {nullptr, nullptr};
         long long init = 0, iter = 0;
     } lg;
+    double *bv = nullptr, *bs = nullptr, *bz = nullptr, *bh = nullptr;   // BiCGStab's v, s, z, r^ (on first use)
     double *rec = nullptr;        // coarsest-level right-hand sides being recorded
     int rec_cap = 0, rec_n = 0;
     double *d_hist = nullptr;     // [kHistCap] residual history of the device-side loop
@@ -160,6 +161,7 @@ bool validate(const tpmg_params *p, std::string &msg)
     if (p->graphs != 0 && p->graphs != 1) { msg = "graphs must be 0 or 1"; return false; }
     if (p->autotune != 0 && p->autotune != 1) { msg = "autotune must be 0 or 1"; return false; }
     if (p->scan_max_cells < 0) { msg = "scan_max_cells must be >= 0"; return false; }
+    if (p->outer < TPMG_OUTER_CG || p->outer > TPMG_OUTER_BICGSTAB) { msg = "unknown outer iteration"; return false; }
     return true;
 }
 
@@ -696,6 +698,120 @@ tpmg_status pcg_graph(tpmg_ctx *ctx, const double *f, double *u, double rtol, in
     return loop_result(ctx, s, rtol, max_iter, iters, rel);
 }
 
+// The sum of a dot product on the host (block partials, fixed-order finish, one read-back).
+tpmg_status dot_host(tpmg_ctx *ctx, const double *a, const double *b, double *out)
+{
+    const Launch L = launch_of(ctx);
+    const long N = ctx->N;
+    const int np = ctx->n_part;
+    LCHK(run(ctx, TPMG_K_DOT, (double)N, [&] { return launch_dot(L, N, a, b, ctx->partials, np); }));
+    LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_SUM, ctx->partials, np, ctx->sc); }));
+    tpmg_status st = read_scalars(ctx);
+    if (st == TPMG_OK) *out = ctx->h_sc->sum;
+    return st;
+}
+
+// Preconditioned Richardson iteration (Sec. 5): r = f - A u (the true residual,
+// with ||r||^2), z = B r, u <- u + z, until ||r|| <= rtol ||r_0||.
+tpmg_status richardson(tpmg_ctx *ctx, const double *f, double *u, double rtol, int max_iter, int *iters, double *rel,
+                       double *hist)
+{
+    const Launch L = launch_of(ctx);
+    LevelDev &fl = ctx->lv[ctx->p.n_levels - 1];
+    const long N = ctx->N;
+    const int np = ctx->n_part;
+    *iters = 0;
+    *rel = 1.0;
+    double rr0 = 0.0;
+    for (int it = 0;; ++it) {
+        LCHK(run(ctx, TPMG_K_RESIDUAL, (double)N, [&] { return launch_residual(L, fl, ctx->vert, f, u, ctx->r, ctx->partials, np); }));
+        LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_SUM, ctx->partials, np, ctx->sc); }));
+        tpmg_status st = read_scalars(ctx);
+        if (st != TPMG_OK) return st;
+        const double rr = ctx->h_sc->sum;
+        if (!std::isfinite(rr)) return fail(ctx, TPMG_ERR_BREAKDOWN, "non-finite residual");
+        if (it == 0) {
+            rr0 = rr;
+            if (hist) hist[0] = 1.0;
+            if (rr0 == 0.0) { *rel = 0.0; return TPMG_OK; }
+        } else {
+            *iters = it;
+            *rel = std::sqrt(rr / rr0);
+            if (hist) hist[it] = *rel;
+            if (*rel <= rtol) return TPMG_OK;
+        }
+        if (it == max_iter) break;
+        if ((st = vcycle_fine(ctx, ctx->r, ctx->z)) != TPMG_OK) return st;
+        LCHK(run(ctx, TPMG_K_AXPY, (double)N, [&] { return launch_lincomb(L, N, 1.0, u, 1.0, ctx->z, 0.0, nullptr, u); }));
+    }
+    return fail(ctx, TPMG_ERR_NOT_CONVERGED, "max_iter reached before rtol");
+}
+
+// BiCGStab (van der Vorst 1992) preconditioned from the right by one V-cycle per
+// application, the oracle's steps in the same order: with r^ = r_0,
+//   rho = <r^, r>, beta = (rho / rho_prev)(alpha / omega), p = r + beta (p - omega v),
+//   y = B p, v = A y, alpha = rho / <r^, v>, s = r - alpha v,
+//   z = B s, t = A z, omega = <t, s> / <t, t>, u += alpha y + omega z, r = s - omega t.
+tpmg_status bicgstab(tpmg_ctx *ctx, const double *f, double *u, double rtol, int max_iter, int *iters, double *rel,
+                     double *hist)
+{
+    const Launch L = launch_of(ctx);
+    LevelDev &fl = ctx->lv[ctx->p.n_levels - 1];
+    const long N = ctx->N;
+    const int np = ctx->n_part;
+    if (!ctx->bv) {
+        CU(dalloc(ctx, &ctx->bv, (size_t)N));
+        CU(dalloc(ctx, &ctx->bs, (size_t)N));
+        CU(dalloc(ctx, &ctx->bz, (size_t)N));
+        CU(dalloc(ctx, &ctx->bh, (size_t)N));
+    }
+    double *r = ctx->r, *rh = ctx->bh, *p = ctx->pv, *v = ctx->bv, *y = ctx->z, *sv = ctx->bs, *z = ctx->bz, *t = ctx->q;
+    *iters = 0;
+    *rel = 1.0;
+    LCHK(run(ctx, TPMG_K_RESIDUAL, (double)N, [&] { return launch_residual(L, fl, ctx->vert, f, u, r, ctx->partials, np); }));
+    LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_SUM, ctx->partials, np, ctx->sc); }));
+    tpmg_status st = read_scalars(ctx);
+    if (st != TPMG_OK) return st;
+    const double rr0 = ctx->h_sc->sum;
+    if (hist) hist[0] = 1.0;
+    if (!std::isfinite(rr0)) return fail(ctx, TPMG_ERR_BREAKDOWN, "initial residual is not finite");
+    if (rr0 == 0.0) { *rel = 0.0; return TPMG_OK; }
+    LCHK(run(ctx, TPMG_K_COPY, (double)N, [&] { return cudaMemcpyAsync(rh, r, sizeof(double) * N, cudaMemcpyDeviceToDevice, ctx->issue); }));
+    LCHK(run(ctx, TPMG_K_COPY, (double)N, [&] { return cudaMemsetAsync(p, 0, sizeof(double) * N, ctx->issue); }));
+    LCHK(run(ctx, TPMG_K_COPY, (double)N, [&] { return cudaMemsetAsync(v, 0, sizeof(double) * N, ctx->issue); }));
+    double rho_prev = 1.0, alpha = 1.0, omega = 1.0;
+    for (int it = 0; it < max_iter; ++it) {
+        double rho, rv, ts, tt, rr;
+        if ((st = dot_host(ctx, rh, r, &rho)) != TPMG_OK) return st;
+        if (!(rho != 0.0) || !std::isfinite(rho)) return fail(ctx, TPMG_ERR_BREAKDOWN, "BiCGStab: <r^, r> = 0");
+        const double beta = (rho / rho_prev) * (alpha / omega);
+        // p = r + beta (p - omega v)
+        LCHK(run(ctx, TPMG_K_XPBY, (double)N, [&] { return launch_lincomb(L, N, 1.0, r, beta, p, -beta * omega, v, p); }));
+        if ((st = vcycle_fine(ctx, p, y)) != TPMG_OK) return st;
+        LCHK(run(ctx, TPMG_K_APPLY, (double)N, [&] { return launch_apply(L, fl, ctx->vert, y, v, ctx->partials, np); }));
+        if ((st = dot_host(ctx, rh, v, &rv)) != TPMG_OK) return st;
+        if (!(rv != 0.0) || !std::isfinite(rv)) return fail(ctx, TPMG_ERR_BREAKDOWN, "BiCGStab: <r^, v> = 0");
+        alpha = rho / rv;
+        LCHK(run(ctx, TPMG_K_AXPY, (double)N, [&] { return launch_lincomb(L, N, 1.0, r, -alpha, v, 0.0, nullptr, sv); }));
+        if ((st = vcycle_fine(ctx, sv, z)) != TPMG_OK) return st;
+        LCHK(run(ctx, TPMG_K_APPLY, (double)N, [&] { return launch_apply(L, fl, ctx->vert, z, t, ctx->partials, np); }));
+        if ((st = dot_host(ctx, t, t, &tt)) != TPMG_OK) return st;
+        if (!(tt > 0.0) || !std::isfinite(tt)) return fail(ctx, TPMG_ERR_BREAKDOWN, "BiCGStab: <t, t> = 0");
+        if ((st = dot_host(ctx, t, sv, &ts)) != TPMG_OK) return st;
+        omega = ts / tt;
+        LCHK(run(ctx, TPMG_K_AXPY, (double)N, [&] { return launch_lincomb(L, N, 1.0, u, alpha, y, omega, z, u); }));
+        LCHK(run(ctx, TPMG_K_AXPY, (double)N, [&] { return launch_lincomb(L, N, 1.0, sv, -omega, t, 0.0, nullptr, r); }));
+        rho_prev = rho;
+        if ((st = dot_host(ctx, r, r, &rr)) != TPMG_OK) return st;
+        *iters = it + 1;
+        *rel = std::sqrt(rr / rr0);
+        if (hist) hist[it + 1] = *rel;
+        if (!std::isfinite(*rel)) return fail(ctx, TPMG_ERR_BREAKDOWN, "non-finite residual");
+        if (*rel <= rtol) return TPMG_OK;
+    }
+    return fail(ctx, TPMG_ERR_NOT_CONVERGED, "max_iter reached before rtol");
+}
+
 // learned = true: the host-driven form of tpmg_solve_learned's loop (same
 // kernels, same order as append_solve with learned set).
 tpmg_status pcg(tpmg_ctx *ctx, const double *f, double *u, double rtol, int max_iter, int *iters, double *rel,
@@ -769,6 +885,15 @@ tpmg_status pcg(tpmg_ctx *ctx, const double *f, double *u, double rtol, int max_
         LCHK(run(ctx, TPMG_K_XPBY, (double)N, [&] { return launch_xpby(L, N, ctx->sc, ctx->z, ctx->pv); }));
     }
     return fail(ctx, TPMG_ERR_NOT_CONVERGED, "max_iter reached before rtol");
+}
+
+// The host-driven outer iteration of params.outer.
+tpmg_status outer_host(tpmg_ctx *ctx, const double *f, double *u, double rtol, int max_iter, int *iters, double *rel,
+                       double *hist)
+{
+    if (ctx->p.outer == TPMG_OUTER_RICHARDSON) return richardson(ctx, f, u, rtol, max_iter, iters, rel, hist);
+    if (ctx->p.outer == TPMG_OUTER_BICGSTAB) return bicgstab(ctx, f, u, rtol, max_iter, iters, rel, hist);
+    return pcg(ctx, f, u, rtol, max_iter, iters, rel, hist);
 }
 
 tpmg_status upload_level(tpmg_ctx *ctx, int l)
@@ -966,6 +1091,7 @@ tpmg_status tpmg_default_params(tpmg_params *p)
     p->graphs = 1;
     p->autotune = 1;
     p->scan_max_cells = 5120;
+    p->outer = TPMG_OUTER_CG;
     return TPMG_OK;
 }
 
@@ -1112,11 +1238,11 @@ tpmg_status tpmg_solve(tpmg_ctx *ctx, const double *d_f, double *d_u, double rto
     if (!(rtol >= 0.0) || max_iter < 0) return fail(ctx, TPMG_ERR_INVALID_ARG, "rtol must be >= 0, max_iter >= 0");
     if (d_f == d_u) return fail(ctx, TPMG_ERR_INVALID_ARG, "f and u must not overlap");
     // the device-side loop cannot carry the event pairs of a timed kernel class
-    if (ctx->p.graphs && ctx->tr.mask == 0 && max_iter < kHistCap)
+    if (ctx->p.outer == TPMG_OUTER_CG && ctx->p.graphs && ctx->tr.mask == 0 && max_iter < kHistCap)
         return pcg_graph(ctx, d_f, d_u, rtol, max_iter, iters, rel_resid, resid_hist);
     long long before = 0, after = 0;
     for (int c = 0; c < TPMG_K_COUNT; ++c) before += ctx->tr.launches[c];
-    const tpmg_status st = pcg(ctx, d_f, d_u, rtol, max_iter, iters, rel_resid, resid_hist);
+    const tpmg_status st = outer_host(ctx, d_f, d_u, rtol, max_iter, iters, rel_resid, resid_hist);
     for (int c = 0; c < TPMG_K_COUNT; ++c) after += ctx->tr.launches[c];
     ctx->last_launches = after - before;
     return st;
@@ -1131,6 +1257,7 @@ tpmg_status tpmg_batch_create(tpmg_ctx *const *ctxs, int n, const double *const 
     if (cudaGetDevice(&dev) != cudaSuccess) return TPMG_ERR_CUDA;
     for (int i = 0; i < n; ++i) {
         if (!ctxs[i] || !d_f[i] || !d_u[i] || d_f[i] == d_u[i] || ctxs[i]->device != dev) return TPMG_ERR_INVALID_ARG;
+        if (ctxs[i]->p.outer != TPMG_OUTER_CG) return TPMG_ERR_INVALID_ARG;   // batches hold device-side CG loops
         for (int k = 0; k < i; ++k)
             if (ctxs[k] == ctxs[i]) return TPMG_ERR_INVALID_ARG;   // one problem per context
     }
@@ -1196,7 +1323,7 @@ tpmg_status tpmg_solve_host(tpmg_ctx *ctx, const double *h_f, double *h_u, doubl
     const size_t bytes = sizeof(double) * ctx->N;
     CU(cudaMemcpyAsync(ctx->hf, h_f, bytes, cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(ctx->hu, h_u, bytes, cudaMemcpyHostToDevice, ctx->stream));
-    tpmg_status st = pcg(ctx, ctx->hf, ctx->hu, rtol, max_iter, iters, rel_resid, resid_hist);
+    tpmg_status st = outer_host(ctx, ctx->hf, ctx->hu, rtol, max_iter, iters, rel_resid, resid_hist);
     CU(cudaMemcpyAsync(h_u, ctx->hu, bytes, cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     return st;

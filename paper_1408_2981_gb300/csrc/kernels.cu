@@ -811,6 +811,9 @@ __global__ void __launch_bounds__(256) k_finish(int what, const double *__restri
     case FIN_RZC:
         sc->rzc = v;
         break;
+    case FIN_SUM:
+        sc->sum = v;
+        break;
     case FIN_BETA_PR:   // flexible CG: beta = (<r, z_new> - <r, z_old>) / <r_old, z_old>
         sc->rz_new = v;
         sc->beta = (v - sc->rzc) / sc->rz;
@@ -863,6 +866,17 @@ __global__ void __launch_bounds__(256) k_finish(int what, const double *__restri
     }
     default:
         break;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_lincomb(long n, double a, const double *x, double b, const double *y,
+                                                 double c, const double *z, double *out)
+{
+    for (long i = blockIdx.x * 256L + threadIdx.x; i < n; i += (long)gridDim.x * 256) {
+        double v = a * x[i];
+        if (y) v = fma(b, y[i], v);
+        if (z) v = fma(c, z[i], v);
+        out[i] = v;
     }
 }
 
@@ -1026,6 +1040,13 @@ cudaError_t launch_axpy_pair(const Launch &L, long n, const Scalars *sc, const d
         k_axpy_pair<kThreads, true><<<n_part, kThreads, 0, L.s>>>(sc, p, q, u, r, (int)n, partials, z_old);
     else
         k_axpy_pair<kThreads, false><<<n_part, kThreads, 0, L.s>>>(sc, p, q, u, r, (int)n, partials, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lincomb(const Launch &L, long n, double a, const double *x, double b, const double *y, double c,
+                           const double *z, double *out)
+{
+    k_lincomb<<<grid_for(n, 256, L.sm_count), 256, 0, L.s>>>(n, a, x, b, y, c, z, out);
     return cudaGetLastError();
 }
 

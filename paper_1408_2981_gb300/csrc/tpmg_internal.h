@@ -125,6 +125,7 @@ struct Scalars {            // PCG scalars kept in device memory
     int flag;               // bit 0: p.Ap <= 0 or non-finite; bit 1: non-finite residual
     int it;                 // iterations done by the device-side loop
     double ff;              // ||f||^2 (learned solve: the stop test is relative to ||f||)
+    double sum;             // FIN_SUM: a reduced dot product for the host-driven outer loops
     int info;               // learned solve: bit 0 initial guess kept, bit 1 rejected (u_0 = 0)
 };
 
@@ -184,6 +185,9 @@ cudaError_t launch_finish(const Launch &L, int what, const double *partials, int
 cudaError_t launch_axpy_pair(const Launch &L, long n, const Scalars *sc, const double *p, const double *q, double *u,
                              double *r, double *partials, int n_part, const double *z_old);
 cudaError_t launch_xpby(const Launch &L, long n, const Scalars *sc, const double *z, double *p);
+// out = a x + b y + c z (y, z nullable: terms dropped); out may alias x, y or z elementwise
+cudaError_t launch_lincomb(const Launch &L, long n, double a, const double *x, double b, const double *y, double c,
+                           const double *z, double *out);
 
 // noalloc.cu: device address of the fixed scratch array of
 // tpmg_vcycle_noalloc on `device`, which must be the current device (looked
@@ -198,7 +202,9 @@ enum FinishWhat { FIN_RR0 = 0, FIN_ALPHA = 1, FIN_RR = 2, FIN_BETA = 3, FIN_RZ0 
                   // initial guess is rejected unless ||r_0|| < ||f||; rr0 = ||f||^2
                   FIN_LOOP_RR0F = 11,
                   // the same for the host-driven loop (no loop condition)
-                  FIN_RR0F = 12 };
+                  FIN_RR0F = 12,
+                  // Richardson / BiCGStab: the reduced dot product into sum
+                  FIN_SUM = 13 };
 
 // learned.cu: the network of the learned form (tpmg_learned.h) -----------------
 struct NetView {            // device pointers of a network's weights

@@ -40,6 +40,8 @@ MUTANTS = {
     "g_without_edge_length": ("gval = len * v_dot(n, d) / v_dot(d, d);", "gval = v_dot(n, d) / v_dot(d, d);"),
     "g_distance_power": ("gval = len * v_dot(n, d) / v_dot(d, d);", "gval = len * v_dot(n, d) / sqrt(v_dot(d, d));"),
     "pcg_beta_inverted": ("beta = rz_new / rz;", "beta = rz / rz_new;"),
+    "bicgstab_omega_sign": ("r[i] = sv[i] - omega * t[i];", "r[i] = sv[i] + omega * t[i];"),
+    "bicgstab_beta_ratio": ("beta = (rho / rho_prev) * (alpha / omega);", "beta = (rho / rho_prev) * (omega / alpha);"),
     "prolong_half": ("uf[(size_t)(4 * T + j) * n + k] += uc[(size_t)T * n + k];",
                      "uf[(size_t)(4 * T + j) * n + k] += 0.5 * uc[(size_t)T * n + k];"),
     "correction_sign": ("uf[(size_t)(4 * T + j) * n + k] += uc[(size_t)T * n + k];",
