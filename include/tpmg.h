@@ -126,6 +126,25 @@ typedef struct {
  * scan_max_cells 5120, outer CG.  Returns TPMG_ERR_INVALID_ARG if p is NULL. */
 tpmg_status tpmg_default_params(tpmg_params *p);
 
+/* Factorised profiles (Sec. 2, eq. profiles): alpha_r(r, x) = alpha_r^r(r) alpha_r^S(x),
+ * alpha_S(r, x) = alpha_S^r(r) alpha_S^S(x), beta(r, x) = beta^r(r) beta^S(x), the form
+ * the tensor-product V-cycle handles exactly.  Host arrays, positive and finite; a
+ * NULL array is the constant 1.
+ *   beta_r, alphaS_r  [n_r]      vertical factors at the cell centres (level k)
+ *   alphar_r          [n_r + 1]  vertical factor at the faces (face k between levels k-1, k)
+ *   beta_s, alphar_s, alphaS_s   [20 * 4^refinement] horizontal factors on the cells of
+ *                                the finest level, in the library's cell order
+ * Coarse multigrid levels use the area-weighted mean of each cell's 4 children; an
+ * edge uses the mean of its two cells' alphaS_s, so the operator stays symmetric. */
+typedef struct {
+    const double *beta_r;
+    const double *alphaS_r;
+    const double *alphar_r;
+    const double *beta_s;
+    const double *alphar_s;
+    const double *alphaS_s;
+} tpmg_profiles;
+
 /* Builds the grid hierarchy, geometry, colouring and coefficients on the host
  * (Sec. 4.1-4.2, Appendix A), uploads them, and allocates all workspaces on the
  * current device.  cuda_stream is a cudaStream_t (NULL = legacy default
@@ -133,6 +152,11 @@ tpmg_status tpmg_default_params(tpmg_params *p);
  * tpmg_destroy.  Errors: INVALID_ARG (bad parameter, *out untouched),
  * OOM, CUDA. */
 tpmg_status tpmg_setup(const tpmg_params *p, void *cuda_stream, tpmg_ctx **out);
+
+/* tpmg_setup with factorised profiles (prof NULL: constant profiles, as tpmg_setup).
+ * The arrays are copied.  Errors as tpmg_setup; INVALID_ARG also for a profile value
+ * that is not positive and finite. */
+tpmg_status tpmg_setup_profiles(const tpmg_params *p, const tpmg_profiles *prof, void *cuda_stream, tpmg_ctx **out);
 
 /* y = A x on the finest level (eq. ColumnEquation: matrix-free finite-volume
  * operator).  d_x, d_y: device, n_cells*n_r doubles, must not overlap.

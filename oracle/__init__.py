@@ -77,6 +77,8 @@ def _load(path: str | None = None):
         lib.oracle_fcg.argtypes = [_P, _P, _P, _D, _I, _P, _P, _P, _P]
         lib.oracle_set_vcycle_bf16.argtypes = [_P, _I]
         lib.oracle_set_vcycle_bf16.restype = None
+        lib.oracle_set_profiles.argtypes = [_P, _P, _P, _P, _P, _P, _P]
+        lib.oracle_set_profiles.restype = None
         lib.oracle_set_coarse_solve.argtypes = [_P, COARSE_SOLVE_FN]
         lib.oracle_set_coarse_solve.restype = None
         lib.oracle_bf16.argtypes = [_D]
@@ -263,6 +265,15 @@ class Oracle:
         """Use the V-cycle of the mixed-precision form (BF16-rounded coefficients,
         FP64 arithmetic) in vcycle(), pcg() and fcg()."""
         self._lib.oracle_set_vcycle_bf16(self._h, 1 if on else 0)
+
+    def set_profiles(self, beta_r=None, alphaS_r=None, alphar_r=None, beta_s=None, alphar_s=None, alphaS_s=None):
+        """Factorised profiles alpha(r, x) = alpha^r(r) alpha^S(x) (None = 1): vertical
+        factors of beta and alpha_S at the cell centres [n_r], of alpha_r at the faces
+        [n_r + 1]; horizontal factors on the finest level's cells."""
+        arrs = [None if a is None else _f64(a).reshape(-1).copy() for a in
+                (beta_r, alphaS_r, alphar_r, beta_s, alphar_s, alphaS_s)]
+        self._profiles = arrs
+        self._lib.oracle_set_profiles(self._h, *(_ptr(a) for a in arrs))
 
     def set_coarse_solve(self, fn=None):
         """Replace the V-cycle's coarsest-level solve by the guess fn(f [n_cells *

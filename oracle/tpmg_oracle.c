@@ -378,6 +378,12 @@ typedef struct {
     double *dr;           /* [n_r]   r_{k+1} - r_k                            */
     double *vol;          /* [n_r]   v_k = (r_{k+1}^3 - r_k^3)/3              */
     double *arv;          /* [n_r+1] sigma_k 2 r_k^2 / (r_{k+1} - r_{k-1})    */
+    /* profiles (Sec. 2, eq. profiles) in factorised form, alpha(r, x) = alpha^r(r) alpha^S(x):
+     * vertical factors of beta and alpha_S at the cell centres [n_r] and of alpha_r at the
+     * faces [n_r+1]; horizontal factors per refinement level [n_cells] (the finest given,
+     * coarser levels the area-weighted mean over the 4 children); NULL = 1 */
+    double *pr_beta, *pr_aS, *pr_ar;
+    double **ps_beta, **ps_ar, **ps_aS;
     /* multigrid work arrays per multigrid level (0 = coarsest)               */
     double **mg_f, **mg_u, **mg_r;
     double *col_a, *col_b, *col_c, *col_d, *col_x, *col_cp, *col_dp;
@@ -405,14 +411,30 @@ double oracle_bf16(double x)
 
 static double coeff(const octx *o, double v) { return o->bf16_now ? oracle_bf16(v) : v; }
 
-static double beta_hat(const octx *o, const ogrid *G, int T, int k) { return coeff(o, G->area[T] * o->vol[k]); }
+/* factor of profile p: vertical array v at index k times horizontal array of the
+ * refinement level of G at cell T (1 where absent) */
+static double vfac(const double *v, int k) { return v ? v[k] : 1.0; }
+static double hfac(const octx *o, double *const *h, const ogrid *G, int T)
+{
+    return h ? h[G - o->grid][T] : 1.0;
+}
+
+/* With profiles: beta_hat x beta^r_k beta^S_T, alphar_hat x alpha_r^r(face) alpha_r^S_T,
+ * alphaS_hat x alpha_S^r_k (alpha_S^S_T + alpha_S^S_T') / 2 (the edge value is the mean
+ * of its two cells', so the operator stays symmetric). */
+static double beta_hat(const octx *o, const ogrid *G, int T, int k)
+{
+    return coeff(o, G->area[T] * o->vol[k] * vfac(o->pr_beta, k) * hfac(o, o->ps_beta, G, T));
+}
 static double alphaS_hat(const octx *o, const ogrid *G, int T, int e, int k)
 {
-    return coeff(o, o->omega2 * o->dr[k] * G->g[3 * T + e]);
+    double edge = 1.0;
+    if (o->ps_aS) edge = 0.5 * (hfac(o, o->ps_aS, G, T) + hfac(o, o->ps_aS, G, G->nbr[3 * T + e]));
+    return coeff(o, o->omega2 * o->dr[k] * G->g[3 * T + e] * vfac(o->pr_aS, k) * edge);
 }
 static double alphar_hat(const octx *o, const ogrid *G, int T, int face)
 {
-    return coeff(o, o->omega2 * G->area[T] * o->arv[face]);
+    return coeff(o, o->omega2 * G->area[T] * o->arv[face] * vfac(o->pr_ar, face) * hfac(o, o->ps_ar, G, T));
 }
 
 /* Column T of the operator as a tridiagonal matrix (eq. ColumnEquation,
@@ -630,6 +652,66 @@ static void vcycle_level(octx *o, int l, const double *f, double *u)
 /* ------------------------------------------------------------------------- */
 /* Exported API (ctypes)                                                       */
 /* ------------------------------------------------------------------------- */
+static void free_level_profile(const octx *o, double **p)
+{
+    int l;
+    if (!p) return;
+    for (l = 0; l <= o->L; ++l) free(p[l]);
+    free(p);
+}
+
+/* per refinement level: the finest copied from fine, each coarser cell the
+ * area-weighted mean of its 4 children */
+static double **level_profile(const octx *o, const double *fine)
+{
+    int l, T, j;
+    double **p;
+    if (!fine) return NULL;
+    p = (double **)calloc((size_t)o->L + 1, sizeof(double *));
+    if (!p) return NULL;
+    for (l = 0; l <= o->L; ++l) p[l] = (double *)calloc((size_t)o->grid[l].n_cells, sizeof(double));
+    memcpy(p[o->L], fine, (size_t)o->grid[o->L].n_cells * sizeof(double));
+    for (l = o->L - 1; l >= 0; --l)
+        for (T = 0; T < o->grid[l].n_cells; ++T) {
+            double s = 0.0, a = 0.0;
+            for (j = 0; j < 4; ++j) {
+                const double aj = o->grid[l + 1].area[4 * T + j];
+                s += aj * p[l + 1][4 * T + j];
+                a += aj;
+            }
+            p[l][T] = s / a;
+        }
+    return p;
+}
+
+static double *copy_vec(const double *v, int n)
+{
+    double *c;
+    if (!v) return NULL;
+    c = (double *)malloc((size_t)n * sizeof(double));
+    if (c) memcpy(c, v, (size_t)n * sizeof(double));
+    return c;
+}
+
+/* Factorised profiles (NULL = 1): vertical beta^r, alpha_S^r at the n_r cell
+ * centres, alpha_r^r at the n_r + 1 faces; horizontal beta^S, alpha_r^S,
+ * alpha_S^S on the cells of the finest level. */
+void oracle_set_profiles(void *h, const double *beta_r, const double *aS_r, const double *ar_r, const double *beta_s,
+                         const double *ar_s, const double *aS_s)
+{
+    octx *o = (octx *)h;
+    free(o->pr_beta); free(o->pr_aS); free(o->pr_ar);
+    free_level_profile(o, o->ps_beta);
+    free_level_profile(o, o->ps_ar);
+    free_level_profile(o, o->ps_aS);
+    o->pr_beta = copy_vec(beta_r, o->n_r);
+    o->pr_aS = copy_vec(aS_r, o->n_r);
+    o->pr_ar = copy_vec(ar_r, o->n_r + 1);
+    o->ps_beta = level_profile(o, beta_s);
+    o->ps_ar = level_profile(o, ar_s);
+    o->ps_aS = level_profile(o, aS_s);
+}
+
 void oracle_destroy(void *h)
 {
     octx *o = (octx *)h;
@@ -644,6 +726,10 @@ void oracle_destroy(void *h)
     free(o->mg_f); free(o->mg_u); free(o->mg_r);
     free(o->col_a); free(o->col_b); free(o->col_c); free(o->col_d); free(o->col_x);
     free(o->col_cp); free(o->col_dp);
+    free(o->pr_beta); free(o->pr_aS); free(o->pr_ar);
+    free_level_profile(o, o->ps_beta);
+    free_level_profile(o, o->ps_ar);
+    free_level_profile(o, o->ps_aS);
     free(o);
 }
 

@@ -37,7 +37,7 @@ TPMG_OUTER_RICHARDSON = 1
 TPMG_OUTER_BICGSTAB = 2
 
 # every entry point declared in include/tpmg.h
-EXPORTS = ["tpmg_default_params", "tpmg_setup", "tpmg_apply_operator", "tpmg_vcycle", "tpmg_vcycle_noalloc",
+EXPORTS = ["tpmg_default_params", "tpmg_setup", "tpmg_setup_profiles", "tpmg_apply_operator", "tpmg_vcycle", "tpmg_vcycle_noalloc",
            "tpmg_solve",
            "tpmg_solve_host", "tpmg_query", "tpmg_query_tuning", "tpmg_export_mesh", "tpmg_profile", "tpmg_profile_read",
            "tpmg_status_string", "tpmg_last_error", "tpmg_destroy", "tpmg_batch_create", "tpmg_batch_run",
@@ -70,6 +70,11 @@ class tpmg_params(ctypes.Structure):
                 ("outer", ctypes.c_int)]
 
 
+class tpmg_profiles(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_void_p) for name in
+                ("beta_r", "alphaS_r", "alphar_r", "beta_s", "alphar_s", "alphaS_s")]
+
+
 class TPMGError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{status_name(status)}: {msg}")
@@ -92,6 +97,8 @@ def load(path: str | None = None):
     P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
     lib.tpmg_default_params.argtypes = [ctypes.POINTER(tpmg_params)]
     lib.tpmg_setup.argtypes = [ctypes.POINTER(tpmg_params), P, ctypes.POINTER(P)]
+    lib.tpmg_setup_profiles.argtypes = [ctypes.POINTER(tpmg_params), ctypes.POINTER(tpmg_profiles), P,
+                                        ctypes.POINTER(P)]
     lib.tpmg_apply_operator.argtypes = [P, P, P]
     lib.tpmg_vcycle.argtypes = [P, P, P]
     lib.tpmg_vcycle_noalloc.argtypes = [P, P, P]
@@ -174,9 +181,11 @@ class Solver:
 
     Keyword arguments are the fields of ``tpmg_params``.  Vectors are torch
     float64 CUDA tensors with ``n_cells * n_r`` elements ([cell][k], k fastest).
+    ``profiles``: optional dict of factorised profiles (the fields of
+    ``tpmg_profiles``, numpy float64 arrays; absent = 1).
     """
 
-    def __init__(self, stream=None, **params):
+    def __init__(self, stream=None, profiles=None, **params):
         import torch
 
         self._torch = torch
@@ -186,7 +195,16 @@ class Solver:
             stream = torch.cuda.current_stream()
         self.stream = stream
         h = ctypes.c_void_p()
-        st = self._lib.tpmg_setup(ctypes.byref(self.params), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h))
+        if profiles:
+            arrs = {k: np.ascontiguousarray(v, dtype=np.float64) for k, v in profiles.items()}
+            unknown = set(arrs) - {f[0] for f in tpmg_profiles._fields_}
+            if unknown:
+                raise KeyError(sorted(unknown))
+            prof = tpmg_profiles(**{k: a.ctypes.data for k, a in arrs.items()})
+            st = self._lib.tpmg_setup_profiles(ctypes.byref(self.params), ctypes.byref(prof),
+                                               ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h))
+        else:
+            st = self._lib.tpmg_setup(ctypes.byref(self.params), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h))
         if st != TPMG_OK:
             raise TPMGError(st, "tpmg_setup rejected the parameters or failed")
         self._h = h

@@ -76,6 +76,10 @@ struct tpmg_ctx {
         long long init = 0, iter = 0;
     } lg;
     double *bv = nullptr, *bs = nullptr, *bz = nullptr, *bh = nullptr;   // BiCGStab's v, s, z, r^ (on first use)
+    // factorised profiles (tpmg_setup_profiles): vertical factors and the horizontal
+    // factors of every refinement level; empty = the constant 1
+    std::vector<double> pr_beta, pr_aS, pr_ar;
+    std::vector<std::vector<double>> ps_beta, ps_ar, ps_aS;
     double *rec = nullptr;        // coarsest-level right-hand sides being recorded
     int rec_cap = 0, rec_n = 0;
     double *d_hist = nullptr;     // [kHistCap] residual history of the device-side loop
@@ -166,6 +170,44 @@ bool validate(const tpmg_params *p, std::string &msg)
 }
 
 Launch launch_of(const tpmg_ctx *ctx) { return Launch{ctx->issue, ctx->p.n_r, ctx->sm_count}; }
+
+double vfac(const std::vector<double> &v, int k) { return v.empty() ? 1.0 : v[k]; }
+double hfac(const std::vector<std::vector<double>> &h, int ref, int T) { return h.empty() ? 1.0 : h[ref][T]; }
+
+// horizontal profile factors on every refinement level: the finest as given, each
+// coarser cell the area-weighted mean of its 4 children
+bool level_means(const HostGrid &G, int L, const double *fine, std::vector<std::vector<double>> &out)
+{
+    out.clear();
+    if (!fine) return true;
+    out.assign(L + 1, std::vector<double>());
+    out[L].assign(fine, fine + G.lev[L].n);
+    for (double v : out[L])
+        if (!(v > 0.0) || !std::isfinite(v)) return false;
+    for (int l = L - 1; l >= 0; --l) {
+        out[l].resize(G.lev[l].n);
+        for (int T = 0; T < G.lev[l].n; ++T) {
+            double sum = 0.0, a = 0.0;
+            for (int j = 0; j < 4; ++j) {
+                const double aj = G.lev[l + 1].area[4 * T + j];
+                sum += aj * out[l + 1][4 * T + j];
+                a += aj;
+            }
+            out[l][T] = sum / a;
+        }
+    }
+    return true;
+}
+
+bool copy_vertical(const double *v, int n, std::vector<double> &out)
+{
+    out.clear();
+    if (!v) return true;
+    out.assign(v, v + n);
+    for (double x : out)
+        if (!(x > 0.0) || !std::isfinite(x)) return false;
+    return true;
+}
 
 cudaError_t grow_events(Tracer &t, size_t pairs)
 {
@@ -906,13 +948,20 @@ tpmg_status upload_level(tpmg_ctx *ctx, int l)
     D.n_colours = H.n_colours;
     std::vector<int4> nb(H.n);
     std::vector<dbl4> g(H.n);
+    std::vector<double> areaB(H.n), areaR(H.n);
+    // an edge's alpha_S^S: the mean of its two cells' factors (symmetric operator)
+    auto edge = [&](int T, int e) {
+        return ctx->ps_aS.empty() ? 1.0 : 0.5 * (ctx->ps_aS[H.ref][T] + ctx->ps_aS[H.ref][H.nbr[3 * T + e]]);
+    };
     for (int T = 0; T < H.n; ++T) {
         int mask = 0;
         for (int e = 0; e < 3; ++e)
             if (H.colour[H.nbr[3 * T + e]] < H.colour[T]) mask |= 1 << e;
         nb[T] = make_int4(H.nbr[3 * T], H.nbr[3 * T + 1], H.nbr[3 * T + 2], mask);
-        const double g0 = H.g[3 * T], g1 = H.g[3 * T + 1], g2 = H.g[3 * T + 2];
+        const double g0 = H.g[3 * T] * edge(T, 0), g1 = H.g[3 * T + 1] * edge(T, 1), g2 = H.g[3 * T + 2] * edge(T, 2);
         g[T] = dbl4{g0, g1, g2, (g0 + g1) + g2};
+        areaB[T] = H.area[T] * hfac(ctx->ps_beta, H.ref, T);
+        areaR[T] = H.area[T] * hfac(ctx->ps_ar, H.ref, T);
     }
     // relaxation tasks: the cells of each colour in ascending order, padded to whole tasks
     std::vector<int> tasks;
@@ -936,6 +985,7 @@ tpmg_status upload_level(tpmg_ctx *ctx, int l)
     CU(dalloc(ctx, &D.nbr, n));
     CU(dalloc(ctx, &D.g, n));
     CU(dalloc(ctx, &D.area, n));
+    CU(dalloc(ctx, &D.area_r, n));
     CU(dalloc(ctx, &D.task_cells, tasks.size()));
     CU(dalloc(ctx, &D.task_nbr, tasks.size()));
     CU(dalloc(ctx, &D.task_g, tasks.size()));
@@ -965,10 +1015,10 @@ tpmg_status upload_level(tpmg_ctx *ctx, int l)
         for (int T = 0; T < H.n; ++T)
             for (int k = 0; k < p.n_r; ++k) {
                 const size_t i = (size_t)T * p.n_r + k;
-                const double hr = G.omega2 * G.dr[k];
-                cp[i] = bf16x4{bf16_bits(hr * H.g[3 * T]), bf16_bits(hr * H.g[3 * T + 1]),
-                               bf16_bits(hr * H.g[3 * T + 2]), bf16_bits(H.area[T] * G.vol[k])};
-                cv[i] = bf16_bits(G.omega2 * H.area[T] * G.face[k]);
+                const double hr = G.omega2 * G.dr[k] * vfac(ctx->pr_aS, k);
+                cp[i] = bf16x4{bf16_bits(hr * g[T].x), bf16_bits(hr * g[T].y), bf16_bits(hr * g[T].z),
+                               bf16_bits(areaB[T] * (G.vol[k] * vfac(ctx->pr_beta, k)))};
+                cv[i] = bf16_bits(areaR[T] * (G.omega2 * G.face[k] * vfac(ctx->pr_ar, k)));
             }
         CU(dalloc(ctx, &D.cpack, nn));
         CU(dalloc(ctx, &D.cvert, nn));
@@ -984,13 +1034,15 @@ tpmg_status upload_level(tpmg_ctx *ctx, int l)
     }
     CU(cudaMemcpyAsync(D.nbr, nb.data(), n * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(D.g, g.data(), n * sizeof(dbl4), cudaMemcpyHostToDevice, ctx->stream));
-    CU(cudaMemcpyAsync(D.area, H.area.data(), n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(D.area, areaB.data(), n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(D.area_r, areaR.data(), n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    // learned-form features: geometric cell areas and flux weights
     std::vector<float> ia(H.n);
     std::vector<float4> wn(H.n);
     for (int T = 0; T < H.n; ++T) {
         ia[T] = (float)(1.0 / H.area[T]);
-        const double sg = g[T].w;
-        wn[T] = make_float4((float)(g[T].x / sg), (float)(g[T].y / sg), (float)(g[T].z / sg), 0.f);
+        const double g0 = H.g[3 * T], g1 = H.g[3 * T + 1], g2 = H.g[3 * T + 2], sg = (g0 + g1) + g2;
+        wn[T] = make_float4((float)(g0 / sg), (float)(g1 / sg), (float)(g2 / sg), 0.f);
     }
     CU(dalloc(ctx, &D.iarea32, n));
     CU(dalloc(ctx, &D.wnb32, n));
@@ -1097,9 +1149,26 @@ tpmg_status tpmg_default_params(tpmg_params *p)
 
 tpmg_status tpmg_setup(const tpmg_params *params, void *cuda_stream, tpmg_ctx **out)
 {
+    return tpmg_setup_profiles(params, nullptr, cuda_stream, out);
+}
+
+tpmg_status tpmg_setup_profiles(const tpmg_params *params, const tpmg_profiles *prof, void *cuda_stream,
+                                tpmg_ctx **out)
+{
     std::string msg;
     if (!out) return TPMG_ERR_INVALID_ARG;
     if (!validate(params, msg)) return TPMG_ERR_INVALID_ARG;
+    if (prof) {   // every profile value positive and finite (checked before any CUDA call)
+        const long n_fine = 20L << (2 * params->refinement);
+        auto ok = [](const double *v, long n) {
+            for (long i = 0; v && i < n; ++i)
+                if (!(v[i] > 0.0) || !std::isfinite(v[i])) return false;
+            return true;
+        };
+        if (!ok(prof->beta_r, params->n_r) || !ok(prof->alphaS_r, params->n_r) || !ok(prof->alphar_r, params->n_r + 1) ||
+            !ok(prof->beta_s, n_fine) || !ok(prof->alphar_s, n_fine) || !ok(prof->alphaS_s, n_fine))
+            return TPMG_ERR_INVALID_ARG;
+    }
     tpmg_ctx *ctx = new (std::nothrow) tpmg_ctx();
     if (!ctx) return TPMG_ERR_OOM;
     auto bail = [&](tpmg_status s) {
@@ -1115,15 +1184,24 @@ tpmg_status tpmg_setup(const tpmg_params *params, void *cuda_stream, tpmg_ctx **
         return bail(TPMG_ERR_CUDA);
     if (!build_host_grid(ctx->p, ctx->host, msg)) return bail(TPMG_ERR_INVALID_ARG);
     const int n_r = ctx->p.n_r;
+    if (prof) {
+        const int L = ctx->p.refinement;
+        if (!copy_vertical(prof->beta_r, n_r, ctx->pr_beta) || !copy_vertical(prof->alphaS_r, n_r, ctx->pr_aS) ||
+            !copy_vertical(prof->alphar_r, n_r + 1, ctx->pr_ar) ||
+            !level_means(ctx->host, L, prof->beta_s, ctx->ps_beta) ||
+            !level_means(ctx->host, L, prof->alphar_s, ctx->ps_ar) ||
+            !level_means(ctx->host, L, prof->alphaS_s, ctx->ps_aS))
+            return bail(TPMG_ERR_INVALID_ARG);
+    }
     // vertical factors: vol | w | hr
     {
         const HostGrid &G = ctx->host;
         std::vector<double> hv(3 * n_r + 1);
         double *vol = hv.data(), *w = vol + n_r, *hr = w + n_r + 1;
-        for (int k = 0; k <= n_r; ++k) w[k] = G.omega2 * G.face[k];
+        for (int k = 0; k <= n_r; ++k) w[k] = G.omega2 * G.face[k] * vfac(ctx->pr_ar, k);
         for (int k = 0; k < n_r; ++k) {
-            vol[k] = G.vol[k];
-            hr[k] = G.omega2 * G.dr[k];
+            vol[k] = G.vol[k] * vfac(ctx->pr_beta, k);
+            hr[k] = G.omega2 * G.dr[k] * vfac(ctx->pr_aS, k);
         }
         tpmg_status st = TPMG_OK;
         if (dalloc(ctx, &ctx->d_vert, hv.size()) != cudaSuccess) return bail(TPMG_ERR_OOM);

@@ -50,7 +50,8 @@ __device__ __forceinline__ double block_sum(double v)
 struct OpView {
     const int4 *__restrict__ nbr;
     const dbl4 *__restrict__ g;
-    const double *__restrict__ area;
+    const double *__restrict__ area;     // |T| beta^S_T
+    const double *__restrict__ area_r;   // |T| alpha_r^S_T
     const double *__restrict__ vol;
     const double *__restrict__ w;
     const double *__restrict__ hr;
@@ -59,7 +60,7 @@ struct OpView {
 
 inline OpView make_view(const LevelDev &lv, const VertDev &v, int n_r)
 {
-    return OpView{lv.nbr, lv.g, lv.area, v.vol, v.w, v.hr, n_r};
+    return OpView{lv.nbr, lv.g, lv.area, lv.area_r, v.vol, v.w, v.hr, n_r};
 }
 
 // (A x)_{T,k} in flux form: 13 FP64 instructions.
@@ -71,9 +72,9 @@ __device__ __forceinline__ double apply_at(const OpView &o, const double *__rest
     const double xc = x[i];
     const double dm = k > 0 ? xc - x[i - 1] : 0.0;
     const double dp = k < n_r - 1 ? xc - x[i + 1] : 0.0;
-    const double vert = fma(__ldg(&o.w[k + 1]), dp, fma(__ldg(&o.w[k]), dm, __ldg(&o.vol[k]) * xc));
+    const double vert = fma(__ldg(&o.w[k + 1]), dp, __ldg(&o.w[k]) * dm);
     const double hor = fma(g.z, xc - x[nb.z * n_r + k], fma(g.y, xc - x[nb.y * n_r + k], g.x * (xc - x[nb.x * n_r + k])));
-    return fma(__ldg(&o.area[T]), vert, __ldg(&o.hr[k]) * hor);
+    return fma(__ldg(&o.area_r[T]), vert, fma(__ldg(&o.area[T]) * __ldg(&o.vol[k]), xc, __ldg(&o.hr[k]) * hor));
 }
 
 template <int NT>
@@ -209,11 +210,11 @@ __global__ void k_twisted_factors(int n_tasks, OpView o, const int *__restrict__
     M[col] = M[kRelaxCols + col] = 0.0;
     if (T < 0) return;
     double *ri = rinv + (size_t)T * n;
-    const double A = o.area[T], G = o.g[T].w;
+    const double A = o.area[T], Ar = o.area_r[T], G = o.g[T].w;
     double e = 0.0, p = 1.0;
     for (int k = 0; k < j; ++k) {
         const double m = fma(A, o.vol[k], o.hr[k] * G);
-        const double c = A * o.w[k], cu = A * o.w[k + 1];
+        const double c = Ar * o.w[k], cu = Ar * o.w[k + 1];
         e = k == 0 ? m : m + c * e / p;
         p = e + cu;
         const double iv = 1.0 / p;
@@ -224,7 +225,7 @@ __global__ void k_twisted_factors(int n_tasks, OpView o, const int *__restrict__
     double eb = 0.0, q = 1.0;
     for (int k = n - 1, s = 0; k > j; --k, ++s) {
         const double m = fma(A, o.vol[k], o.hr[k] * G);
-        const double cd = A * o.w[k], cu = A * o.w[k + 1];
+        const double cd = Ar * o.w[k], cu = Ar * o.w[k + 1];
         eb = k == n - 1 ? m : m + cu * eb / q;
         q = eb + cd;
         const double iv = 1.0 / q;
@@ -232,7 +233,7 @@ __global__ void k_twisted_factors(int n_tasks, OpView o, const int *__restrict__
         fb[base + s * 32 + col + 16] = cu * iv;
         fc[base + s * 32 + col + 16] = cd * iv;
     }
-    const double cj = A * o.w[j], cj1 = A * o.w[j + 1];
+    const double cj = Ar * o.w[j], cj1 = Ar * o.w[j + 1];
     double gam = fma(A, o.vol[j], o.hr[j] * G);
     if (j > 0) gam += cj * e / p;
     if (j < n - 1) gam += cj1 * eb / q;
@@ -351,11 +352,11 @@ __global__ void k_thomas_factors(OpView o, int n_cells, double *__restrict__ rin
     if (T >= n_cells) return;
     const int n = o.n_r;
     const size_t row0 = (size_t)T * n;
-    const double A = o.area[T], G = o.g[T].w;
+    const double A = o.area[T], Ar = o.area_r[T], G = o.g[T].w;
     double e = 0.0, p = 1.0;
     for (int k = 0; k < n; ++k) {
         const double m = fma(A, o.vol[k], o.hr[k] * G);
-        const double c = k > 0 ? A * o.w[k] : 0.0, cu = k < n - 1 ? A * o.w[k + 1] : 0.0;
+        const double c = k > 0 ? Ar * o.w[k] : 0.0, cu = k < n - 1 ? Ar * o.w[k + 1] : 0.0;
         e = k == 0 ? m : m + c * e / p;
         p = e + cu;
         const double iv = 1.0 / p;

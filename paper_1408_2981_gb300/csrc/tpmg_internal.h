@@ -84,7 +84,8 @@ struct LevelDev {
     std::vector<int> colour_cells;     // [n_colours] cells of each colour (host copy)
     int4 *nbr = nullptr;          // [n] {nbr0, nbr1, nbr2, lower-colour mask}
     dbl4 *g = nullptr;            // [n] {g0, g1, g2, g0+g1+g2}
-    double *area = nullptr;       // [n]
+    double *area = nullptr;       // [n] |T| beta^S_T (factor of the beta term)
+    double *area_r = nullptr;     // [n] |T| alpha_r^S_T (factor of the vertical couplings)
     float *iarea32 = nullptr;     // [n] 1 / |T| (network features of the learned form)
     float4 *wnb32 = nullptr;      // [n] {g0, g1, g2} / (g0 + g1 + g2), 0
     int *task_cells = nullptr;    // [n_tasks][16] cell ids, -1 = padding

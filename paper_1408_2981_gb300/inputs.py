@@ -13,6 +13,9 @@ produces.  Numpy only; no torch, no CUDA.
 * ``manufactured_solution`` -- a sum of low-order spherical harmonics times
   vertical cosines (the cosines satisfy the zero-flux vertical conditions).
 * ``smooth_field`` -- a random band-limited field on the shell.
+* ``balanced_flow_profiles`` -- the factorised profile shapes of the balanced-flow
+  atmosphere with two mid-latitude jets (Sec. 5), at the buoyancy frequency where they
+  factorise exactly.
 """
 from __future__ import annotations
 
@@ -145,3 +148,38 @@ def smooth_field(centres: np.ndarray, r_faces: np.ndarray, seed: int, l_max: int
                 out += c[idx] * np.outer(y, np.cos(n * math.pi * zmid / H))
                 idx += 1
     return out.reshape(-1)
+
+
+def jet_function(phi: np.ndarray, u0: float = 100.0, phi_m: float = math.pi / 4, sigma: float = 0.1,
+                 radius: float = 6.371e6, omega: float = 2.0 * math.pi / (24 * 3600), n_quad: int = 20001) -> np.ndarray:
+    """F(phi) with dF/dphi = 2 R Omega u(phi) sin(phi) + u(phi)^2 tan(phi), F(0) = 0, for the
+    two-jet zonal wind u(phi) = u0 cos(phi) / cos(phi_M) exp(-(cos(phi) - cos(phi_M))^2 / (2 sigma^2))
+    (m^2 s^-2; trapezoidal quadrature on a fine latitude grid, then interpolation)."""
+    grid = np.linspace(0.0, math.pi / 2 * (1 - 1e-9), n_quad)
+    u = u0 * np.cos(grid) / math.cos(phi_m) * np.exp(-(np.cos(grid) - math.cos(phi_m)) ** 2 / (2 * sigma ** 2))
+    dF = 2 * radius * omega * u * np.sin(grid) + u * u * np.tan(grid)
+    F = np.concatenate([[0.0], np.cumsum(0.5 * (dF[1:] + dF[:-1]) * np.diff(grid))])
+    return np.interp(np.abs(np.asarray(phi, dtype=np.float64)), grid, F)   # F is even in phi
+
+
+def balanced_flow_profiles(centres: np.ndarray, r_faces: np.ndarray, cp: float = 1005.0, rd: float = 287.0,
+                           t0: float = 273.0, g: float = 9.81, radius: float = 6.371e6) -> dict:
+    """Factorised profiles (horizontal x vertical) of the balanced atmosphere at the buoyancy
+    frequency N = N* = g / sqrt(cp T0), where the Exner pressure pi = e_H e_V factorises:
+    e_H = exp(-N^2 F(phi) / g^2), e_V = exp(-N^2 R (r - 1) / g) (r in units of the earth's
+    radius).  Then rho theta and rho / pi are both proportional to (e_H e_V)^gamma with
+    gamma = cv / rd, so alpha_S = rho theta, alpha_r = r^2 Lambda rho theta (Lambda = 1) and
+    beta = gamma rho / pi factorise into (e_H)^gamma times a vertical factor.  Each factor is
+    normalised to 1 at the equator and the surface.  Returns the tpmg_profiles fields."""
+    centres = np.asarray(centres, dtype=np.float64)
+    r_faces = np.asarray(r_faces, dtype=np.float64)
+    n_star = g / math.sqrt(cp * t0)
+    gamma = (cp - rd) / rd
+    phi = np.arcsin(np.clip(centres[:, 2], -1.0, 1.0))
+    e_h = np.exp(-n_star ** 2 * jet_function(phi) / g ** 2)
+    rc = 0.5 * (r_faces[:-1] + r_faces[1:])
+    e_v = lambda r: np.exp(-n_star ** 2 * radius * (r - 1.0) / g)
+    h = e_h ** gamma
+    vc = e_v(rc) ** gamma / e_v(rc[0]) ** gamma
+    vf = r_faces ** 2 * e_v(r_faces) ** gamma / (r_faces[0] ** 2 * e_v(r_faces[0]) ** gamma)
+    return dict(beta_r=vc, alphaS_r=vc, alphar_r=vf, beta_s=h, alphar_s=h, alphaS_s=h)

@@ -599,6 +599,66 @@ def pin_bicgstab(ns):
         assert res["status"] == 0 and res["iters"] == 1, res["hist"]
 
 
+def _profiles(o, seed):
+    """Seeded positive factorised profiles for an oracle instance (all in [0.5, 1.5])."""
+    n = o.level_cells(o.n_levels - 1)
+    u = lambda k, m: 1.0 + 0.5 * inputs.uniform_pm1(seed + k, m)
+    return dict(beta_r=u(1, o.n_r), alphaS_r=u(2, o.n_r), alphar_r=u(3, o.n_r + 1),
+                beta_s=u(4, n), alphar_s=u(5, n), alphaS_s=u(6, n))
+
+
+def pin_profiles(ns):
+    """Factorised profiles (Sec. 2, eq. profiles; the TPMG^otimes form):
+    unit profiles leave the operator bit for bit; random positive profiles keep it
+    symmetric positive definite; a profile of beta alone adds exactly
+    (beta - 1) |T| v_k to the diagonal, on the finest level with the given factors
+    and on the coarsest with their area-weighted means over the children; and an
+    edge couples with the mean of its two cells' alpha_S factors."""
+    kw = dict(refinement=2, n_levels=3, n_r=5, grading=1.1, H=0.1, courant_c=8.0)
+    o = ns.Oracle(**kw)
+    n_f = o.level_cells(2)
+    x = inputs.uniform_pm1(inputs.SEED_UNIFORM_SMALL + 7, o.size())
+    y0 = o.apply(x)
+    o.set_profiles(**{k: np.ones_like(v) for k, v in _profiles(o, 11).items()})
+    assert np.array_equal(o.apply(x), y0)
+    o.set_profiles(**_profiles(o, 12))
+    A = o.dense_operator()
+    assert np.abs(A - A.T).max() <= 1e-12 * np.abs(A).max()
+    assert np.linalg.eigvalsh(0.5 * (A + A.T)).min() > 0.0
+    # beta alone: diagonal shift on the finest and the coarsest level
+    bs = 1.0 + 0.5 * inputs.uniform_pm1(inputs.SEED_UNIFORM_SMALL + 8, n_f)
+    br = 1.0 + 0.5 * inputs.uniform_pm1(inputs.SEED_UNIFORM_SMALL + 9, o.n_r)
+    o.set_profiles()
+    vol = o.vertical()["vol"]
+    for level in (2, 0):
+        n = o.level_cells(level)
+        xl = inputs.uniform_pm1(inputs.SEED_UNIFORM_SMALL + 10 + level, n * o.n_r)
+        plain = o.apply(xl, level)
+        o.set_profiles(beta_r=br, beta_s=bs)
+        prof = o.apply(xl, level)
+        o.set_profiles()
+        area = o.grid(o.level_ref(level))["area"]
+        if level == 2:
+            bl = bs
+        else:   # area-weighted means over the children, twice
+            a1, a2 = o.grid(o.level_ref(1))["area"], o.grid(o.level_ref(2))["area"]
+            b1 = (a2 * bs).reshape(-1, 4).sum(1) / a2.reshape(-1, 4).sum(1)
+            bl = (a1 * b1).reshape(-1, 4).sum(1) / a1.reshape(-1, 4).sum(1)
+        expect = plain + (np.outer(area * bl, vol * br) - np.outer(area, vol)).reshape(-1) * xl
+        assert np.max(np.abs(prof - expect)) <= 1e-12 * np.max(np.abs(prof)), level
+    # edge coupling: the mean of the two cells' alpha_S^S
+    aSs = 1.0 + 0.5 * inputs.uniform_pm1(inputs.SEED_UNIFORM_SMALL + 13, n_f)
+    grid = o.grid(o.level_ref(2))
+    A0 = o.dense_operator()
+    o.set_profiles(alphaS_s=aSs)
+    A1 = o.dense_operator()
+    o.set_profiles()
+    T, e, k = 7, 1, 2
+    Tn = grid["nbr"][T, e]
+    i, j = T * o.n_r + k, Tn * o.n_r + k
+    assert abs(A1[i, j] - A0[i, j] * 0.5 * (aSs[T] + aSs[Tn])) <= 1e-13 * abs(A0[i, j])
+
+
 def pin_manufactured(ns):
     """Manufactured solution: f = A u*, solve to rtol 1e-12, recover u* in the
     energy norm to 1e-9 (a residual drop of 1e-12 bounds the error by cond-weighted 1e-12)."""
@@ -640,5 +700,5 @@ ALL_PINS = [
     pin_constants_in_kernel, pin_symmetric_spd, pin_kronecker, pin_horizontal_consistency,
     pin_vertical_consistency, pin_thomas, pin_column_solve_exact, pin_transfers, pin_vcycle_dense, pin_preconditioner_symmetric,
     pin_invariant_subspaces, pin_pcg_dense, pin_bf16_rounding, pin_flexible_cg, pin_bf16_vcycle,
-    pin_manufactured, pin_robust_convergence, pin_bicgstab,
+    pin_manufactured, pin_robust_convergence, pin_bicgstab, pin_profiles,
 ]

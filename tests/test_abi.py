@@ -110,3 +110,16 @@ def test_learned_entry_points_reject_bad_arguments_on_host(lib):
     assert lib.tpmg_solve_learned(None, None, None, 1e-5, 10, ctypes.byref(it), ctypes.byref(rel), None, None,
                                   None) == binding.TPMG_ERR_INVALID_ARG
     lib.tpmg_net_destroy(None)
+
+
+def test_setup_profiles_rejects_non_positive_profiles_before_touching_cuda(lib):
+    import numpy as np
+    p = binding.default_params(refinement=1, n_levels=2, n_r=4)
+    for field, n in (("beta_r", 4), ("alphar_r", 5), ("alphaS_s", 80)):
+        bad = np.ones(n)
+        bad[n // 2] = -1.0 if field != "alphar_r" else 0.0
+        prof = binding.tpmg_profiles(**{field: bad.ctypes.data})
+        h = ctypes.c_void_p()
+        assert lib.tpmg_setup_profiles(ctypes.byref(p), ctypes.byref(prof), None, ctypes.byref(h)) == \
+            binding.TPMG_ERR_INVALID_ARG
+        assert not h.value

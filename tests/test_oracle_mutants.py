@@ -40,14 +40,17 @@ MUTANTS = {
     "g_without_edge_length": ("gval = len * v_dot(n, d) / v_dot(d, d);", "gval = v_dot(n, d) / v_dot(d, d);"),
     "g_distance_power": ("gval = len * v_dot(n, d) / v_dot(d, d);", "gval = len * v_dot(n, d) / sqrt(v_dot(d, d));"),
     "pcg_beta_inverted": ("beta = rz_new / rz;", "beta = rz / rz_new;"),
+    "profile_edge_one_side": ("edge = 0.5 * (hfac(o, o->ps_aS, G, T) + hfac(o, o->ps_aS, G, G->nbr[3 * T + e]));",
+                              "edge = hfac(o, o->ps_aS, G, T);"),
+    "profile_coarse_unweighted": ("s += aj * p[l + 1][4 * T + j];", "s += p[l + 1][4 * T + j];"),
     "bicgstab_omega_sign": ("r[i] = sv[i] - omega * t[i];", "r[i] = sv[i] + omega * t[i];"),
     "bicgstab_beta_ratio": ("beta = (rho / rho_prev) * (alpha / omega);", "beta = (rho / rho_prev) * (omega / alpha);"),
     "prolong_half": ("uf[(size_t)(4 * T + j) * n + k] += uc[(size_t)T * n + k];",
                      "uf[(size_t)(4 * T + j) * n + k] += 0.5 * uc[(size_t)T * n + k];"),
     "correction_sign": ("uf[(size_t)(4 * T + j) * n + k] += uc[(size_t)T * n + k];",
                         "uf[(size_t)(4 * T + j) * n + k] -= uc[(size_t)T * n + k];"),
-    "horizontal_uses_volume": ("return coeff(o, o->omega2 * o->dr[k] * G->g[3 * T + e]);",
-                               "return coeff(o, o->omega2 * o->vol[k] * G->g[3 * T + e]);"),
+    "horizontal_uses_volume": ("return coeff(o, o->omega2 * o->dr[k] * G->g[3 * T + e] * vfac(o->pr_aS, k) * edge);",
+                               "return coeff(o, o->omega2 * o->vol[k] * G->g[3 * T + e] * vfac(o->pr_aS, k) * edge);"),
     "bf16_truncates": ("return ldexp(rint(ldexp(m, 8)), e - 8);", "return ldexp(floor(ldexp(m, 8)), e - 8);"),
     "vertical_missing_r2": ("2.0 * o->r[k] * o->r[k] / (o->zeta[k + 1] - o->zeta[k - 1])",
                             "2.0 / (o->zeta[k + 1] - o->zeta[k - 1])"),
