@@ -158,6 +158,21 @@ tpmg_status tpmg_setup(const tpmg_params *p, void *cuda_stream, tpmg_ctx **out);
  * that is not positive and finite. */
 tpmg_status tpmg_setup_profiles(const tpmg_params *p, const tpmg_profiles *prof, void *cuda_stream, tpmg_ctx **out);
 
+/* The problem's operator with general (non-factorising) profiles on the finest level
+ * (Sec. 2, eq. profiles; the TPMG^full storage of Sec. 4.2 for the operator only):
+ * h_beta, h_alphaS [n_cells * n_r] at the cell centres and h_alphar [n_cells * (n_r + 1)]
+ * at the faces (cell-major), host arrays, positive and finite; three NULLs restore the
+ * factorised operator.  From then on the outer iteration -- tpmg_solve, tpmg_apply_operator,
+ * the learned and batched solves -- applies this operator with per-unknown FP64
+ * coefficients (edges: the mean of the two cells' alpha_S).  The FP64 V-cycle keeps the
+ * factorised profiles given to tpmg_setup_profiles: TPMG^fac preconditioning the full
+ * operator (Sec. 3.4, Sec. 5).  The mixed-precision V-cycle, which stores its stencil per
+ * unknown, adopts the general profiles as well (TPMG^full; each coarse level takes the
+ * area-weighted mean over the 4 children per vertical index).  Synchronous.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+tpmg_status tpmg_set_outer_profiles(tpmg_ctx *ctx, const double *h_beta, const double *h_alphar,
+                                    const double *h_alphaS);
+
 /* y = A x on the finest level (eq. ColumnEquation: matrix-free finite-volume
  * operator).  d_x, d_y: device, n_cells*n_r doubles, must not overlap.
  * Asynchronous on the context stream.  Errors: INVALID_ARG (NULL pointer), CUDA. */

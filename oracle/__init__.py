@@ -79,6 +79,11 @@ def _load(path: str | None = None):
         lib.oracle_set_vcycle_bf16.restype = None
         lib.oracle_set_profiles.argtypes = [_P, _P, _P, _P, _P, _P, _P]
         lib.oracle_set_profiles.restype = None
+        lib.oracle_set_outer_profiles.argtypes = [_P, _P, _P, _P]
+        lib.oracle_set_outer_profiles.restype = None
+        lib.oracle_apply_outer.argtypes = [_P, _P, _P]
+        lib.oracle_set_vcycle_full.argtypes = [_P, _I]
+        lib.oracle_set_vcycle_full.restype = None
         lib.oracle_set_coarse_solve.argtypes = [_P, COARSE_SOLVE_FN]
         lib.oracle_set_coarse_solve.restype = None
         lib.oracle_bf16.argtypes = [_D]
@@ -274,6 +279,29 @@ class Oracle:
                 (beta_r, alphaS_r, alphar_r, beta_s, alphar_s, alphaS_s)]
         self._profiles = arrs
         self._lib.oracle_set_profiles(self._h, *(_ptr(a) for a in arrs))
+
+    def set_outer_profiles(self, beta=None, alphar=None, alphaS=None):
+        """General profiles of the problem's operator on the finest level (beta,
+        alpha_S [n_cells, n_r], alpha_r [n_cells, n_r + 1]; None clears): the outer
+        iterations apply this operator, the V-cycle keeps its own profiles."""
+        if beta is None:
+            self._outer = None
+            self._lib.oracle_set_outer_profiles(self._h, None, None, None)
+            return
+        self._outer = [_f64(a).reshape(-1).copy() for a in (beta, alphar, alphaS)]
+        self._lib.oracle_set_outer_profiles(self._h, *(_ptr(a) for a in self._outer))
+
+    def set_vcycle_full(self, on: bool = True):
+        """The V-cycle's operators use the general profiles of set_outer_profiles
+        (TPMG^full) instead of the factorised ones (TPMG^fac)."""
+        self._lib.oracle_set_vcycle_full(self._h, 1 if on else 0)
+
+    def apply_outer(self, x) -> np.ndarray:
+        """y = A x with the problem's operator (the general profiles where set)."""
+        x = _f64(x).reshape(-1)
+        y = np.empty_like(x)
+        self._lib.oracle_apply_outer(self._h, _ptr(x), _ptr(y))
+        return y
 
     def set_coarse_solve(self, fn=None):
         """Replace the V-cycle's coarsest-level solve by the guess fn(f [n_cells *

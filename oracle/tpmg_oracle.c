@@ -384,6 +384,16 @@ typedef struct {
      * coarser levels the area-weighted mean over the 4 children); NULL = 1 */
     double *pr_beta, *pr_aS, *pr_ar;
     double **ps_beta, **ps_ar, **ps_aS;
+    /* general (non-factorising) profiles of the problem's operator on the finest level:
+     * beta, alpha_S per unknown [n_cells][n_r], alpha_r per face [n_cells][n_r + 1];
+     * NULL = the V-cycle's operator.  The outer iterations apply this operator; the
+     * V-cycle keeps its (factorised) profiles: TPMG preconditioning the full operator. */
+    double *pf_beta, *pf_ar, *pf_aS;
+    /* the same general profiles on every refinement level (coarse: area-weighted means
+     * over the 4 children, per vertical index) and the switch vc_full that makes the
+     * V-cycle's operators use them (TPMG^full) instead of the factorised profiles */
+    double **pl_beta, **pl_ar, **pl_aS;
+    int vc_full;
     /* multigrid work arrays per multigrid level (0 = coarsest)               */
     double **mg_f, **mg_u, **mg_r;
     double *col_a, *col_b, *col_c, *col_d, *col_x, *col_cp, *col_dp;
@@ -422,18 +432,27 @@ static double hfac(const octx *o, double *const *h, const ogrid *G, int T)
 /* With profiles: beta_hat x beta^r_k beta^S_T, alphar_hat x alpha_r^r(face) alpha_r^S_T,
  * alphaS_hat x alpha_S^r_k (alpha_S^S_T + alpha_S^S_T') / 2 (the edge value is the mean
  * of its two cells', so the operator stays symmetric). */
+static int full_now(const octx *o) { return o->vc_full && o->pl_beta; }
 static double beta_hat(const octx *o, const ogrid *G, int T, int k)
 {
+    if (full_now(o)) return coeff(o, G->area[T] * o->vol[k] * o->pl_beta[G - o->grid][(size_t)T * o->n_r + k]);
     return coeff(o, G->area[T] * o->vol[k] * vfac(o->pr_beta, k) * hfac(o, o->ps_beta, G, T));
 }
 static double alphaS_hat(const octx *o, const ogrid *G, int T, int e, int k)
 {
     double edge = 1.0;
+    if (full_now(o)) {
+        const double *a = o->pl_aS[G - o->grid];
+        edge = 0.5 * (a[(size_t)T * o->n_r + k] + a[(size_t)G->nbr[3 * T + e] * o->n_r + k]);
+        return coeff(o, o->omega2 * o->dr[k] * G->g[3 * T + e] * edge);
+    }
     if (o->ps_aS) edge = 0.5 * (hfac(o, o->ps_aS, G, T) + hfac(o, o->ps_aS, G, G->nbr[3 * T + e]));
     return coeff(o, o->omega2 * o->dr[k] * G->g[3 * T + e] * vfac(o->pr_aS, k) * edge);
 }
 static double alphar_hat(const octx *o, const ogrid *G, int T, int face)
 {
+    if (full_now(o))
+        return coeff(o, o->omega2 * G->area[T] * o->arv[face] * o->pl_ar[G - o->grid][(size_t)T * (o->n_r + 1) + face]);
     return coeff(o, o->omega2 * G->area[T] * o->arv[face] * vfac(o->pr_ar, face) * hfac(o, o->ps_ar, G, T));
 }
 
@@ -480,6 +499,39 @@ static void apply_level(octx *o, int l, const double *u, double *y)
     int n = o->n_r, T, k;
     for (T = 0; T < G->n_cells; ++T)
         for (k = 0; k < n; ++k) y[(size_t)T * n + k] = apply_row(o, G, u, T, k);
+}
+
+/* Row (T, k) of the problem's operator with the general profiles: the flux form of
+ * apply_row with beta_hat = |T| v_k beta_{T,k}, alphar_hat = omega^2 |T| (face
+ * factor) alpha_r at the face, alphaS_hat = omega^2 dr_k g_TT' (alpha_S_{T,k} +
+ * alpha_S_{T',k}) / 2. */
+static double apply_row_full(const octx *o, const ogrid *G, const double *u, int T, int k)
+{
+    int n = o->n_r, e;
+    size_t i = (size_t)T * n + k, fa = (size_t)T * (n + 1) + k;
+    double s = G->area[T] * o->vol[k] * o->pf_beta[i] * u[i];
+    if (k > 0) s += o->omega2 * G->area[T] * o->arv[k] * o->pf_ar[fa] * (u[i] - u[i - 1]);
+    if (k < n - 1) s += o->omega2 * G->area[T] * o->arv[k + 1] * o->pf_ar[fa + 1] * (u[i] - u[i + 1]);
+    for (e = 0; e < 3; ++e) {
+        const int Tn = G->nbr[3 * T + e];
+        const double edge = 0.5 * (o->pf_aS[i] + o->pf_aS[(size_t)Tn * n + k]);
+        s += o->omega2 * o->dr[k] * G->g[3 * T + e] * edge * (u[i] - u[(size_t)Tn * n + k]);
+    }
+    return s;
+}
+
+/* y = A u with the problem's operator (the general profiles where set) on the finest level */
+static void apply_outer(octx *o, const double *u, double *y)
+{
+    const int lf = o->n_levels - 1;
+    const ogrid *G = mg_grid(o, lf);
+    int n = o->n_r, T, k;
+    if (!o->pf_beta) {
+        apply_level(o, lf, u, y);
+        return;
+    }
+    for (T = 0; T < G->n_cells; ++T)
+        for (k = 0; k < n; ++k) y[(size_t)T * n + k] = apply_row_full(o, G, u, T, k);
 }
 
 /* Textbook Thomas algorithm for a general tridiag(a, b, c) x = d, no pivoting:
@@ -693,6 +745,61 @@ static double *copy_vec(const double *v, int n)
     return c;
 }
 
+/* General profiles of the problem's operator on the finest level (NULL clears all
+ * three; all three must be given otherwise): beta, alpha_S [n_cells][n_r], alpha_r
+ * [n_cells][n_r + 1] (faces). */
+/* per refinement level, m values per cell: the finest copied, each coarser (cell, j)
+ * the area-weighted mean over the 4 children's (cell, j) */
+static double **level_profile_cols(const octx *o, const double *fine, int m)
+{
+    int l, T, c, j;
+    double **p = (double **)calloc((size_t)o->L + 1, sizeof(double *));
+    if (!p) return NULL;
+    for (l = 0; l <= o->L; ++l) p[l] = (double *)calloc((size_t)o->grid[l].n_cells * m, sizeof(double));
+    memcpy(p[o->L], fine, (size_t)o->grid[o->L].n_cells * m * sizeof(double));
+    for (l = o->L - 1; l >= 0; --l)
+        for (T = 0; T < o->grid[l].n_cells; ++T)
+            for (j = 0; j < m; ++j) {
+                double s = 0.0, a = 0.0;
+                for (c = 0; c < 4; ++c) {
+                    const double ac = o->grid[l + 1].area[4 * T + c];
+                    s += ac * p[l + 1][(size_t)(4 * T + c) * m + j];
+                    a += ac;
+                }
+                p[l][(size_t)T * m + j] = s / a;
+            }
+    return p;
+}
+
+void oracle_set_outer_profiles(void *h, const double *beta, const double *ar, const double *aS)
+{
+    octx *o = (octx *)h;
+    const size_t n = (size_t)mg_grid(o, o->n_levels - 1)->n_cells;
+    free(o->pf_beta); free(o->pf_ar); free(o->pf_aS);
+    free_level_profile(o, o->pl_beta);
+    free_level_profile(o, o->pl_ar);
+    free_level_profile(o, o->pl_aS);
+    o->pf_beta = o->pf_ar = o->pf_aS = NULL;
+    o->pl_beta = o->pl_ar = o->pl_aS = NULL;
+    if (!beta || !ar || !aS) return;
+    o->pf_beta = copy_vec(beta, (int)(n * o->n_r));
+    o->pf_ar = copy_vec(ar, (int)(n * (o->n_r + 1)));
+    o->pf_aS = copy_vec(aS, (int)(n * o->n_r));
+    o->pl_beta = level_profile_cols(o, beta, o->n_r);
+    o->pl_ar = level_profile_cols(o, ar, o->n_r + 1);
+    o->pl_aS = level_profile_cols(o, aS, o->n_r);
+}
+
+/* on != 0: the V-cycle's operators use the general profiles too (TPMG^full) */
+void oracle_set_vcycle_full(void *h, int on) { ((octx *)h)->vc_full = on != 0; }
+
+/* y = A x with the problem's operator (oracle_apply gives the V-cycle's level operators). */
+int oracle_apply_outer(void *h, const double *x, double *y)
+{
+    apply_outer((octx *)h, x, y);
+    return 0;
+}
+
 /* Factorised profiles (NULL = 1): vertical beta^r, alpha_S^r at the n_r cell
  * centres, alpha_r^r at the n_r + 1 faces; horizontal beta^S, alpha_r^S,
  * alpha_S^S on the cells of the finest level. */
@@ -730,6 +837,10 @@ void oracle_destroy(void *h)
     free_level_profile(o, o->ps_beta);
     free_level_profile(o, o->ps_ar);
     free_level_profile(o, o->ps_aS);
+    free(o->pf_beta); free(o->pf_ar); free(o->pf_aS);
+    free_level_profile(o, o->pl_beta);
+    free_level_profile(o, o->pl_ar);
+    free_level_profile(o, o->pl_aS);
     free(o);
 }
 
@@ -999,7 +1110,7 @@ int oracle_pcg(void *h, const double *f, double *u, double rtol, int max_iter, i
     double *q = (double *)malloc(N * sizeof(double));
     double rz, rnorm0, rnorm;
     if (!r || !z || !p || !q) { free(r); free(z); free(p); free(q); return -2; }
-    apply_level(o, lf, u, q);
+    apply_outer(o, u, q);
     for (i = 0; i < N; ++i) r[i] = f[i] - q[i];
     rnorm0 = sqrt(dot(N, r, r));
     *iters = 0;
@@ -1012,7 +1123,7 @@ int oracle_pcg(void *h, const double *f, double *u, double rtol, int max_iter, i
     rz = dot(N, r, z);
     for (it = 0; it < max_iter; ++it) {
         double pq, alpha, rz_new, beta;
-        apply_level(o, lf, p, q);
+        apply_outer(o, p, q);
         pq = dot(N, p, q);
         if (!(pq > 0.0) || !isfinite(pq)) { status = -3; break; }
         alpha = rz / pq;
@@ -1030,7 +1141,7 @@ int oracle_pcg(void *h, const double *f, double *u, double rtol, int max_iter, i
     }
 done:
     if (true_rel) {
-        apply_level(o, lf, u, q);
+        apply_outer(o, u, q);
         for (i = 0; i < N; ++i) q[i] = f[i] - q[i];
         *true_rel = rnorm0 > 0.0 ? sqrt(dot(N, q, q)) / rnorm0 : 0.0;
     }
@@ -1056,7 +1167,7 @@ int oracle_fcg(void *h, const double *f, double *u, double rtol, int max_iter, i
     double *q = (double *)malloc(N * sizeof(double));
     double rz, rnorm0, rnorm;
     if (!r || !z || !p || !q) { free(r); free(z); free(p); free(q); return -2; }
-    apply_level(o, lf, u, q);
+    apply_outer(o, u, q);
     for (i = 0; i < N; ++i) r[i] = f[i] - q[i];
     rnorm0 = sqrt(dot(N, r, r));
     *iters = 0;
@@ -1069,7 +1180,7 @@ int oracle_fcg(void *h, const double *f, double *u, double rtol, int max_iter, i
     rz = dot(N, r, z);
     for (it = 0; it < max_iter; ++it) {
         double pq, alpha, rz_old_new, rz_new, beta;
-        apply_level(o, lf, p, q);
+        apply_outer(o, p, q);
         pq = dot(N, p, q);
         if (!(pq > 0.0) || !isfinite(pq)) { status = -3; break; }
         alpha = rz / pq;
@@ -1088,7 +1199,7 @@ int oracle_fcg(void *h, const double *f, double *u, double rtol, int max_iter, i
     }
 done:
     if (true_rel) {
-        apply_level(o, lf, u, q);
+        apply_outer(o, u, q);
         for (i = 0; i < N; ++i) q[i] = f[i] - q[i];
         *true_rel = rnorm0 > 0.0 ? sqrt(dot(N, q, q)) / rnorm0 : 0.0;
     }
@@ -1121,7 +1232,7 @@ int oracle_bicgstab(void *h, const double *f, double *u, double rtol, int max_it
     *iters = 0;
     *rel_resid = 1.0;
     if (!r || !rh || !p || !v || !y || !sv || !z || !t) { status = -2; goto done; }
-    apply_level(o, lf, u, t);
+    apply_outer(o, u, t);
     for (i = 0; i < N; ++i) r[i] = f[i] - t[i];
     memcpy(rh, r, N * sizeof(double));
     rnorm0 = sqrt(dot(N, r, r));
@@ -1134,13 +1245,13 @@ int oracle_bicgstab(void *h, const double *f, double *u, double rtol, int max_it
         beta = (rho / rho_prev) * (alpha / omega);
         for (i = 0; i < N; ++i) p[i] = r[i] + beta * (p[i] - omega * v[i]);
         oracle_vcycle(h, p, y);
-        apply_level(o, lf, y, v);
+        apply_outer(o, y, v);
         rv = dot(N, rh, v);
         if (!(rv != 0.0) || !isfinite(rv)) { status = -3; break; }
         alpha = rho / rv;
         for (i = 0; i < N; ++i) sv[i] = r[i] - alpha * v[i];
         oracle_vcycle(h, sv, z);
-        apply_level(o, lf, z, t);
+        apply_outer(o, z, t);
         tt = dot(N, t, t);
         if (!(tt > 0.0) || !isfinite(tt)) { status = -3; break; }
         omega = dot(N, t, sv) / tt;
@@ -1170,7 +1281,7 @@ int oracle_richardson(void *h, const double *f, double *u, int n_iter, double *h
     double *z = (double *)malloc(N * sizeof(double));
     if (!r || !z) { free(r); free(z); return -2; }
     for (it = 0; it <= n_iter; ++it) {
-        apply_level(o, lf, u, r);
+        apply_outer(o, u, r);
         for (i = 0; i < N; ++i) r[i] = f[i] - r[i];
         if (hist) hist[it] = sqrt(dot(N, r, r));
         if (it == n_iter) break;

@@ -37,7 +37,8 @@ TPMG_OUTER_RICHARDSON = 1
 TPMG_OUTER_BICGSTAB = 2
 
 # every entry point declared in include/tpmg.h
-EXPORTS = ["tpmg_default_params", "tpmg_setup", "tpmg_setup_profiles", "tpmg_apply_operator", "tpmg_vcycle", "tpmg_vcycle_noalloc",
+EXPORTS = ["tpmg_default_params", "tpmg_setup", "tpmg_setup_profiles", "tpmg_set_outer_profiles",
+           "tpmg_apply_operator", "tpmg_vcycle", "tpmg_vcycle_noalloc",
            "tpmg_solve",
            "tpmg_solve_host", "tpmg_query", "tpmg_query_tuning", "tpmg_export_mesh", "tpmg_profile", "tpmg_profile_read",
            "tpmg_status_string", "tpmg_last_error", "tpmg_destroy", "tpmg_batch_create", "tpmg_batch_run",
@@ -100,6 +101,7 @@ def load(path: str | None = None):
     lib.tpmg_setup_profiles.argtypes = [ctypes.POINTER(tpmg_params), ctypes.POINTER(tpmg_profiles), P,
                                         ctypes.POINTER(P)]
     lib.tpmg_apply_operator.argtypes = [P, P, P]
+    lib.tpmg_set_outer_profiles.argtypes = [P, P, P, P]
     lib.tpmg_vcycle.argtypes = [P, P, P]
     lib.tpmg_vcycle_noalloc.argtypes = [P, P, P]
     lib.tpmg_solve.argtypes = [P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D), P]
@@ -285,6 +287,17 @@ class Solver:
                                                     ctypes.byref(timed)), "tpmg_profile_read")
             out[name] = dict(launches=n.value, ms=ms.value, units=units.value, timed=timed.value)
         return out
+
+    def set_outer_profiles(self, beta=None, alphar=None, alphaS=None):
+        """The problem's operator with general profiles on the finest level (numpy
+        arrays: beta, alphaS [n_cells, n_r], alphar [n_cells, n_r + 1]); None restores
+        the factorised operator.  The V-cycle keeps the profiles of the set-up."""
+        if beta is None:
+            self._check(self._lib.tpmg_set_outer_profiles(self._h, None, None, None), "tpmg_set_outer_profiles")
+            return
+        arrs = [np.ascontiguousarray(a, dtype=np.float64).reshape(-1) for a in (beta, alphar, alphaS)]
+        self._check(self._lib.tpmg_set_outer_profiles(self._h, *(a.ctypes.data for a in arrs)),
+                    "tpmg_set_outer_profiles")
 
     # --------------------------------------------------------------- compute
     def apply_operator(self, x, y):

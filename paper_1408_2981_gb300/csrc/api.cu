@@ -80,6 +80,7 @@ struct tpmg_ctx {
     // factors of every refinement level; empty = the constant 1
     std::vector<double> pr_beta, pr_aS, pr_ar;
     std::vector<std::vector<double>> ps_beta, ps_ar, ps_aS;
+    dbl4 *cfull_store = nullptr;   // the finest level's general-profile coefficients (on first use)
     double *rec = nullptr;        // coarsest-level right-hand sides being recorded
     int rec_cap = 0, rec_n = 0;
     double *d_hist = nullptr;     // [kHistCap] residual history of the device-side loop
@@ -938,6 +939,65 @@ tpmg_status outer_host(tpmg_ctx *ctx, const double *f, double *u, double rtol, i
     return pcg(ctx, f, u, rtol, max_iter, iters, rel, hist);
 }
 
+// The BF16 stencil of one multigrid level (refinement of H), full storage (Sec. 4.2):
+// with pb == NULL from the factorised profiles; otherwise from general profiles of
+// this level, pb, ps [n][n_r] (beta, alpha_S at the cells) and pr [n][n_r+1] (alpha_r
+// at the faces), an edge taking the mean of its two cells' alpha_S.
+void bf16_stencil(const tpmg_ctx *ctx, const HostLevel &H, const double *pb, const double *pr, const double *ps,
+                  std::vector<bf16x4> &cp, std::vector<unsigned short> &cv)
+{
+    const HostGrid &G = ctx->host;
+    const int n_r = ctx->p.n_r;
+    cp.resize((size_t)H.n * n_r);
+    cv.resize((size_t)H.n * n_r);
+    for (int T = 0; T < H.n; ++T) {
+        double ge[3], aB = 0.0, aR = 0.0;
+        if (!pb) {
+            for (int e = 0; e < 3; ++e)
+                ge[e] = H.g[3 * T + e] * (ctx->ps_aS.empty() ? 1.0
+                                          : 0.5 * (ctx->ps_aS[H.ref][T] + ctx->ps_aS[H.ref][H.nbr[3 * T + e]]));
+            aB = H.area[T] * hfac(ctx->ps_beta, H.ref, T);
+            aR = H.area[T] * hfac(ctx->ps_ar, H.ref, T);
+        }
+        for (int k = 0; k < n_r; ++k) {
+            const size_t i = (size_t)T * n_r + k;
+            if (!pb) {
+                const double hr = G.omega2 * G.dr[k] * vfac(ctx->pr_aS, k);
+                cp[i] = bf16x4{bf16_bits(hr * ge[0]), bf16_bits(hr * ge[1]), bf16_bits(hr * ge[2]),
+                               bf16_bits(aB * (G.vol[k] * vfac(ctx->pr_beta, k)))};
+                cv[i] = bf16_bits(aR * (G.omega2 * G.face[k] * vfac(ctx->pr_ar, k)));
+            } else {
+                unsigned short a[3];
+                for (int e = 0; e < 3; ++e) {
+                    const double edge = 0.5 * (ps[i] + ps[(size_t)H.nbr[3 * T + e] * n_r + k]);
+                    a[e] = bf16_bits(G.omega2 * G.dr[k] * H.g[3 * T + e] * edge);
+                }
+                cp[i] = bf16x4{a[0], a[1], a[2], bf16_bits(H.area[T] * G.vol[k] * pb[i])};
+                cv[i] = bf16_bits(G.omega2 * H.area[T] * G.face[k] * pr[(size_t)T * (n_r + 1) + k]);
+            }
+        }
+    }
+}
+
+// General per-unknown profiles of one level from the next finer (m values per cell):
+// each coarse (cell, j) the area-weighted mean over the 4 children's (cell, j).
+std::vector<double> average_children(const HostLevel &fine, const std::vector<double> &pf, int m)
+{
+    const int nc = fine.n / 4;
+    std::vector<double> pc((size_t)nc * m);
+    for (int T = 0; T < nc; ++T)
+        for (int j = 0; j < m; ++j) {
+            double s = 0.0, a = 0.0;
+            for (int c = 0; c < 4; ++c) {
+                const double ac = fine.area[4 * T + c];
+                s += ac * pf[(size_t)(4 * T + c) * m + j];
+                a += ac;
+            }
+            pc[(size_t)T * m + j] = s / a;
+        }
+    return pc;
+}
+
 tpmg_status upload_level(tpmg_ctx *ctx, int l)
 {
     const tpmg_params &p = ctx->p;
@@ -1008,18 +1068,10 @@ tpmg_status upload_level(tpmg_ctx *ctx, int l)
         }
     } else {
         // BF16 stencil, full storage: per (T, k) alphaS_hat of the 3 edges and beta_hat,
-        // and alphar_hat of face k (Appendix A, eq. hatFunctionsNonFac, constant profiles)
-        const HostGrid &G = ctx->host;
-        std::vector<bf16x4> cp(nn);
-        std::vector<unsigned short> cv(nn);
-        for (int T = 0; T < H.n; ++T)
-            for (int k = 0; k < p.n_r; ++k) {
-                const size_t i = (size_t)T * p.n_r + k;
-                const double hr = G.omega2 * G.dr[k] * vfac(ctx->pr_aS, k);
-                cp[i] = bf16x4{bf16_bits(hr * g[T].x), bf16_bits(hr * g[T].y), bf16_bits(hr * g[T].z),
-                               bf16_bits(areaB[T] * (G.vol[k] * vfac(ctx->pr_beta, k)))};
-                cv[i] = bf16_bits(areaR[T] * (G.omega2 * G.face[k] * vfac(ctx->pr_ar, k)));
-            }
+        // and alphar_hat of face k (Appendix A, eq. hatFunctionsNonFac)
+        std::vector<bf16x4> cp;
+        std::vector<unsigned short> cv;
+        bf16_stencil(ctx, H, nullptr, nullptr, nullptr, cp, cv);
         CU(dalloc(ctx, &D.cpack, nn));
         CU(dalloc(ctx, &D.cvert, nn));
         CU(dalloc(ctx, &D.rinv32, nn));
@@ -1253,6 +1305,86 @@ tpmg_status tpmg_apply_operator(tpmg_ctx *ctx, const double *d_x, double *d_y)
     LCHK(run(ctx, TPMG_K_APPLY, (double)ctx->N,
              [&] { return launch_apply(launch_of(ctx), ctx->lv.back(), ctx->vert, d_x, d_y, nullptr, 0); }));
     return TPMG_OK;
+}
+
+tpmg_status tpmg_set_outer_profiles(tpmg_ctx *ctx, const double *h_beta, const double *h_alphar,
+                                    const double *h_alphaS)
+{
+    if (!ctx) return TPMG_ERR_INVALID_ARG;
+    LevelDev &D = ctx->lv.back();
+    const HostLevel &H = ctx->host.lev[ctx->p.refinement];
+    const HostGrid &G = ctx->host;
+    const int n_r = ctx->p.n_r, n = H.n;
+    CU(cudaStreamSynchronize(ctx->stream));
+    drop_graph(ctx);   // captured solves hold the operator's kernels
+    // the mixed-precision V-cycle stores its stencil per unknown: it adopts the general
+    // profiles too (TPMG^full; coarse levels average them over the children), or goes
+    // back to the factorised ones
+    auto restencil = [&](const double *pb, const double *pr, const double *ps) -> tpmg_status {
+        if (ctx->p.precision != TPMG_PREC_MIXED) return TPMG_OK;
+        std::vector<double> b, r, a;
+        if (pb) { b.assign(pb, pb + (size_t)n * n_r); r.assign(pr, pr + (size_t)n * (n_r + 1)); a.assign(ps, ps + (size_t)n * n_r); }
+        for (int l = ctx->p.n_levels - 1; l >= 0; --l) {
+            const HostLevel &Hl = ctx->host.lev[ctx->p.refinement - (ctx->p.n_levels - 1 - l)];
+            if (pb && l < ctx->p.n_levels - 1) {
+                const HostLevel &Hf = ctx->host.lev[Hl.ref + 1];
+                b = average_children(Hf, b, n_r);
+                r = average_children(Hf, r, n_r + 1);
+                a = average_children(Hf, a, n_r);
+            }
+            std::vector<bf16x4> cp;
+            std::vector<unsigned short> cv;
+            bf16_stencil(ctx, Hl, pb ? b.data() : nullptr, pb ? r.data() : nullptr, pb ? a.data() : nullptr, cp, cv);
+            LevelDev &Dl = ctx->lv[l];
+            CU(cudaMemcpyAsync(Dl.cpack, cp.data(), cp.size() * sizeof(bf16x4), cudaMemcpyHostToDevice, ctx->stream));
+            CU(cudaMemcpyAsync(Dl.cvert, cv.data(), cv.size() * sizeof(unsigned short), cudaMemcpyHostToDevice,
+                               ctx->stream));
+            CU(launch_thomas_factors32(launch_of(ctx), Dl));
+            CU(cudaStreamSynchronize(ctx->stream));   // cp, cv are local
+        }
+        return TPMG_OK;
+    };
+    if (!h_beta && !h_alphar && !h_alphaS) {
+        D.cfull = nullptr;   // the arrays stay allocated for a later call (freed by tpmg_destroy)
+        return restencil(nullptr, nullptr, nullptr);
+    }
+    if (!h_beta || !h_alphar || !h_alphaS) return fail(ctx, TPMG_ERR_INVALID_ARG, "give all three profiles or none");
+    const size_t nn = (size_t)n * n_r, nf = (size_t)n * (n_r + 1);
+    auto ok = [](const double *v, size_t m) {
+        for (size_t i = 0; i < m; ++i)
+            if (!(v[i] > 0.0) || !std::isfinite(v[i])) return false;
+        return true;
+    };
+    if (!ok(h_beta, nn) || !ok(h_alphaS, nn) || !ok(h_alphar, nf))
+        return fail(ctx, TPMG_ERR_INVALID_ARG, "profiles must be positive and finite");
+    std::vector<dbl4> c(nn);
+    std::vector<double> cr(nf);
+    for (int T = 0; T < n; ++T) {
+        for (int k = 0; k < n_r; ++k) {
+            const size_t i = (size_t)T * n_r + k;
+            const double hr = G.omega2 * G.dr[k];
+            double a[3];
+            for (int e = 0; e < 3; ++e)
+                a[e] = hr * H.g[3 * T + e] * (0.5 * (h_alphaS[i] + h_alphaS[(size_t)H.nbr[3 * T + e] * n_r + k]));
+            c[i] = dbl4{a[0], a[1], a[2], H.area[T] * G.vol[k] * h_beta[i]};
+        }
+        for (int k = 0; k <= n_r; ++k) {
+            // the boundary faces carry no flux (zero-flux vertical conditions)
+            const size_t fi = (size_t)T * (n_r + 1) + k;
+            cr[fi] = (k == 0 || k == n_r) ? 0.0 : G.omega2 * H.area[T] * G.face[k] * h_alphar[fi];
+        }
+    }
+    if (!D.cvr) {
+        dbl4 *cf = nullptr;
+        CU(dalloc(ctx, &cf, nn));
+        CU(dalloc(ctx, &D.cvr, nf));
+        ctx->cfull_store = cf;
+    }
+    CU(cudaMemcpyAsync(ctx->cfull_store, c.data(), nn * sizeof(dbl4), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(D.cvr, cr.data(), nf * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    D.cfull = ctx->cfull_store;
+    return restencil(h_beta, h_alphar, h_alphaS);
 }
 
 tpmg_status tpmg_vcycle(tpmg_ctx *ctx, const double *d_r, double *d_z)

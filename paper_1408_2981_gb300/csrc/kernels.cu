@@ -77,14 +77,44 @@ __device__ __forceinline__ double apply_at(const OpView &o, const double *__rest
     return fma(__ldg(&o.area_r[T]), vert, fma(__ldg(&o.area[T]) * __ldg(&o.vol[k]), xc, __ldg(&o.hr[k]) * hor));
 }
 
-template <int NT>
-__global__ void __launch_bounds__(NT) k_apply(OpView o, const double *__restrict__ x, double *__restrict__ y,
-                                              int N, double *__restrict__ partials)
+// Row (T, k) of the problem's operator from its per-unknown coefficients (general,
+// non-factorising profiles; the same flux form as apply_at).
+struct FullView {
+    const dbl4 *__restrict__ c;       // [n][n_r] {alphaS_hat 0, 1, 2, beta_hat}
+    const double *__restrict__ cr;    // [n][n_r + 1] alphar_hat of face k
+};
+
+__device__ __forceinline__ double apply_full_at(const OpView &o, const FullView &fv, const double *__restrict__ x,
+                                                int T, int k, int i)
+{
+    const int n_r = o.n_r;
+    const int4 nb = __ldg(&o.nbr[T]);
+    const dbl4 c = fv.c[i];
+    const double xc = x[i];
+    const double dm = k > 0 ? xc - x[i - 1] : 0.0;
+    const double dp = k < n_r - 1 ? xc - x[i + 1] : 0.0;
+    const double *cr = fv.cr + (size_t)T * (n_r + 1) + k;
+    const double vert = fma(__ldg(&cr[1]), dp, __ldg(&cr[0]) * dm);
+    const double hor = fma(c.z, xc - x[nb.z * n_r + k], fma(c.y, xc - x[nb.y * n_r + k], c.x * (xc - x[nb.x * n_r + k])));
+    return fma(c.w, xc, vert + hor);
+}
+
+template <int NT, bool FULL>
+__device__ __forceinline__ double apply_any(const OpView &o, const FullView &fv, const double *__restrict__ x, int T,
+                                            int k, int i)
+{
+    if (FULL) return apply_full_at(o, fv, x, T, k, i);
+    return apply_at(o, x, T, k, i);
+}
+
+template <int NT, bool FULL = false>
+__global__ void __launch_bounds__(NT) k_apply(OpView o, FullView fv, const double *__restrict__ x,
+                                              double *__restrict__ y, int N, double *__restrict__ partials)
 {
     double acc = 0.0;
     for (int i = blockIdx.x * NT + threadIdx.x; i < N; i += gridDim.x * NT) {
         const int T = i / o.n_r, k = i - T * o.n_r;
-        const double v = apply_at(o, x, T, k, i);
+        const double v = apply_any<NT, FULL>(o, fv, x, T, k, i);
         y[i] = v;
         acc = fma(x[i], v, acc);
     }
@@ -100,9 +130,10 @@ __device__ __forceinline__ bool is_zero(double v) { return (__double_as_longlong
 // a warp reads exact zeros (for example a zero initial guess) A u is exactly
 // zero and the warp skips its FP64 arithmetic; the test is on bit patterns,
 // so it costs no FP64 instruction.
-template <int NT>
-__global__ void __launch_bounds__(NT) k_residual(OpView o, const double *__restrict__ f, const double *__restrict__ u,
-                                                 double *__restrict__ r, int N, double *__restrict__ partials)
+template <int NT, bool FULL = false>
+__global__ void __launch_bounds__(NT) k_residual(OpView o, FullView full, const double *__restrict__ f,
+                                                 const double *__restrict__ u, double *__restrict__ r, int N,
+                                                 double *__restrict__ partials)
 {
     double acc = 0.0;
     const int stride = gridDim.x * NT, n_r = o.n_r;
@@ -138,7 +169,7 @@ __global__ void __launch_bounds__(NT) k_residual(OpView o, const double *__restr
             const int i = i0 + q * stride;
             if (i >= N) continue;
             double v = fv[q];
-            if (!skip) v = v - apply_at(o, u, T[q], k[q], i);
+            if (!skip) v = v - apply_any<NT, FULL>(o, full, u, T[q], k[q], i);
             r[i] = v;
             acc = fma(v, v, acc);
         }
@@ -897,7 +928,11 @@ cudaError_t launch_apply(const Launch &L, const LevelDev &lv, const VertDev &v, 
 {
     const int N = lv.n * L.n_r;
     const int grid = partials ? n_part : grid_for(N, kThreads, L.sm_count);
-    k_apply<kThreads><<<grid, kThreads, 0, L.s>>>(make_view(lv, v, L.n_r), x, y, N, partials);
+    const FullView fv{lv.cfull, lv.cvr};
+    if (lv.cfull)
+        k_apply<kThreads, true><<<grid, kThreads, 0, L.s>>>(make_view(lv, v, L.n_r), fv, x, y, N, partials);
+    else
+        k_apply<kThreads, false><<<grid, kThreads, 0, L.s>>>(make_view(lv, v, L.n_r), fv, x, y, N, partials);
     return cudaGetLastError();
 }
 
@@ -906,7 +941,11 @@ cudaError_t launch_residual(const Launch &L, const LevelDev &lv, const VertDev &
 {
     const int N = lv.n * L.n_r;
     const int grid = partials ? n_part : grid_for(N, kThreads, L.sm_count);
-    k_residual<kThreads><<<grid, kThreads, 0, L.s>>>(make_view(lv, v, L.n_r), f, u, r, N, partials);
+    const FullView fv{lv.cfull, lv.cvr};
+    if (lv.cfull)
+        k_residual<kThreads, true><<<grid, kThreads, 0, L.s>>>(make_view(lv, v, L.n_r), fv, f, u, r, N, partials);
+    else
+        k_residual<kThreads, false><<<grid, kThreads, 0, L.s>>>(make_view(lv, v, L.n_r), fv, f, u, r, N, partials);
     return cudaGetLastError();
 }
 

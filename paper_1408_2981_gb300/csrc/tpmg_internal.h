@@ -86,6 +86,10 @@ struct LevelDev {
     dbl4 *g = nullptr;            // [n] {g0, g1, g2, g0+g1+g2}
     double *area = nullptr;       // [n] |T| beta^S_T (factor of the beta term)
     double *area_r = nullptr;     // [n] |T| alpha_r^S_T (factor of the vertical couplings)
+    // finest level with general profiles (tpmg_set_outer_profiles): the problem's operator
+    // per unknown, cfull [n][n_r] {alphaS_hat e = 0, 1, 2, beta_hat}, cvr [n][n_r+1] alphar_hat
+    dbl4 *cfull = nullptr;
+    double *cvr = nullptr;
     float *iarea32 = nullptr;     // [n] 1 / |T| (network features of the learned form)
     float4 *wnb32 = nullptr;      // [n] {g0, g1, g2} / (g0 + g1 + g2), 0
     int *task_cells = nullptr;    // [n_tasks][16] cell ids, -1 = padding

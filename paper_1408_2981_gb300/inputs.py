@@ -16,6 +16,8 @@ produces.  Numpy only; no torch, no CUDA.
 * ``balanced_flow_profiles`` -- the factorised profile shapes of the balanced-flow
   atmosphere with two mid-latitude jets (Sec. 5), at the buoyancy frequency where they
   factorise exactly.
+* ``balanced_flow`` -- the same atmosphere at any buoyancy frequency N >= N*: its exact,
+  non-factorising profiles per unknown and their factorised approximation.
 """
 from __future__ import annotations
 
@@ -183,3 +185,39 @@ def balanced_flow_profiles(centres: np.ndarray, r_faces: np.ndarray, cp: float =
     vc = e_v(rc) ** gamma / e_v(rc[0]) ** gamma
     vf = r_faces ** 2 * e_v(r_faces) ** gamma / (r_faces[0] ** 2 * e_v(r_faces[0]) ** gamma)
     return dict(beta_r=vc, alphaS_r=vc, alphar_r=vf, beta_s=h, alphar_s=h, alphaS_s=h)
+
+
+def balanced_flow(centres: np.ndarray, r_faces: np.ndarray, n_freq: float, cp: float = 1005.0, rd: float = 287.0,
+                  t0: float = 273.0, g: float = 9.81, radius: float = 6.371e6) -> tuple[dict, dict, float]:
+    """The balanced atmosphere at buoyancy frequency N (Sec. 5, after Davies 2005): with
+    eps = (N / N*)^2 - 1, e_H = exp(-N^2 F(phi) / g^2), e_V = exp(-N^2 R (r - 1) / g),
+    the Exner pressure pi = (eps + e_H e_V) / (1 + eps), theta = T0 / (e_H e_V),
+    rho = p0 / (Rd T0) pi^gamma e_H e_V (gamma = cv / Rd), and the profiles
+    alpha_S = rho theta, alpha_r = r^2 Lambda rho theta (Lambda = 1), beta = gamma rho / pi.
+    Returns (exact profiles per unknown: beta, alphaS [n, n_r] at the cell centres,
+    alphar [n, n_r + 1] at the faces; the factorised approximation from
+    pi^x = (eps + e_V) / (1 + eps) * e_H as tpmg_profiles fields; eps).  Every profile
+    is normalised by its value at the equator and the surface, where pi = pi^x = 1."""
+    centres = np.asarray(centres, dtype=np.float64)
+    r_faces = np.asarray(r_faces, dtype=np.float64)
+    n_star = g / math.sqrt(cp * t0)
+    eps = (n_freq / n_star) ** 2 - 1.0
+    gamma = (cp - rd) / rd
+    phi = np.arcsin(np.clip(centres[:, 2], -1.0, 1.0))
+    e_h = np.exp(-n_freq ** 2 * jet_function(phi) / g ** 2)
+    rc = 0.5 * (r_faces[:-1] + r_faces[1:])
+    e_v = lambda r: np.exp(-n_freq ** 2 * radius * (r - 1.0) / g)
+
+    def exact(r):   # [n, len(r)]: rho theta and rho / pi up to constants
+        ehv = np.outer(e_h, e_v(r))
+        pi = (eps + ehv) / (1.0 + eps)
+        return pi ** gamma, pi ** (gamma - 1.0) * ehv
+
+    a_c, b_c = exact(rc)
+    a_f, _ = exact(r_faces)
+    outer = dict(beta=b_c, alphaS=a_c, alphar=a_f * (r_faces / r_faces[0]) ** 2)
+    pv = lambda r: (eps + e_v(r)) / (1.0 + eps)
+    fac = dict(alphaS_r=pv(rc) ** gamma, beta_r=pv(rc) ** (gamma - 1.0) * e_v(rc),
+               alphar_r=pv(r_faces) ** gamma * (r_faces / r_faces[0]) ** 2,
+               alphaS_s=e_h ** gamma, alphar_s=e_h ** gamma, beta_s=e_h ** gamma)
+    return outer, fac, eps

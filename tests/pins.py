@@ -659,6 +659,51 @@ def pin_profiles(ns):
     assert abs(A1[i, j] - A0[i, j] * 0.5 * (aSs[T] + aSs[Tn])) <= 1e-13 * abs(A0[i, j])
 
 
+def pin_outer_operator(ns):
+    """The problem's operator with general (per-unknown) profiles: for profiles that
+    happen to factorise it equals the V-cycle's operator with the factors (two
+    independent statements of the same coefficients); it is symmetric positive
+    definite; and PCG with the factorised V-cycle as preconditioner reaches its dense
+    solution (Sec. 3.4: TPMG preconditioning a non-factorising operator)."""
+    kw = dict(refinement=2, n_levels=2, n_r=6, grading=1.1, H=0.1, courant_c=8.0)
+    o = ns.Oracle(**kw)
+    n = o.level_cells(1)
+    prof = _profiles(o, 21)
+    o.set_profiles(**prof)
+    o.set_outer_profiles(beta=np.outer(prof["beta_s"], prof["beta_r"]),
+                         alphar=np.outer(prof["alphar_s"], prof["alphar_r"]),
+                         alphaS=np.outer(prof["alphaS_s"], prof["alphaS_r"]))
+    x = inputs.uniform_pm1(inputs.SEED_UNIFORM_SMALL + 21, o.size())
+    y_fac, y_out = o.apply(x), o.apply_outer(x)
+    assert np.max(np.abs(y_out - y_fac)) <= 1e-13 * np.max(np.abs(y_fac))
+    # the V-cycle on the general profiles (TPMG^full; coarse levels averaged per vertical
+    # index) equals the factorised one when the profiles are an outer product
+    z_fac = o.vcycle(x)
+    o.set_vcycle_full(True)
+    z_full = o.vcycle(x)
+    o.set_vcycle_full(False)
+    assert np.max(np.abs(z_full - z_fac)) <= 1e-12 * np.max(np.abs(z_fac))
+    # a non-factorising operator: perturb every profile value independently
+    pert = lambda k, shape: 1.0 + 0.3 * inputs.uniform_pm1(inputs.SEED_UNIFORM_SMALL + k, int(np.prod(shape))).reshape(shape)
+    o.set_outer_profiles(beta=np.outer(prof["beta_s"], prof["beta_r"]) * pert(31, (n, o.n_r)),
+                         alphar=np.outer(prof["alphar_s"], prof["alphar_r"]) * pert(32, (n, o.n_r + 1)),
+                         alphaS=np.outer(prof["alphaS_s"], prof["alphaS_r"]) * pert(33, (n, o.n_r)))
+    A = np.stack([o.apply_outer(e) for e in np.eye(o.size())], axis=1)
+    assert np.abs(A - A.T).max() <= 1e-12 * np.abs(A).max()
+    assert np.linalg.eigvalsh(0.5 * (A + A.T)).min() > 0.0
+    assert np.abs(A - o.dense_operator()).max() > 1e-3 * np.abs(A).max()   # it is not the V-cycle's operator
+    f = inputs.uniform_pm1(inputs.SEED_UNIFORM_SMALL + 22, o.size())
+    res = o.pcg(f, rtol=1e-13, max_iter=300)
+    assert res["status"] == 0
+    ud = np.linalg.solve(A, f)
+    assert np.linalg.norm(res["u"] - ud) <= 1e-9 * np.linalg.norm(ud)
+    # with the V-cycle on the same general profiles (TPMG^full) too
+    o.set_vcycle_full(True)
+    res2 = o.pcg(f, rtol=1e-13, max_iter=300)
+    o.set_vcycle_full(False)
+    assert res2["status"] == 0 and np.linalg.norm(res2["u"] - ud) <= 1e-9 * np.linalg.norm(ud)
+
+
 def pin_manufactured(ns):
     """Manufactured solution: f = A u*, solve to rtol 1e-12, recover u* in the
     energy norm to 1e-9 (a residual drop of 1e-12 bounds the error by cond-weighted 1e-12)."""
@@ -700,5 +745,5 @@ ALL_PINS = [
     pin_constants_in_kernel, pin_symmetric_spd, pin_kronecker, pin_horizontal_consistency,
     pin_vertical_consistency, pin_thomas, pin_column_solve_exact, pin_transfers, pin_vcycle_dense, pin_preconditioner_symmetric,
     pin_invariant_subspaces, pin_pcg_dense, pin_bf16_rounding, pin_flexible_cg, pin_bf16_vcycle,
-    pin_manufactured, pin_robust_convergence, pin_bicgstab, pin_profiles,
+    pin_manufactured, pin_robust_convergence, pin_bicgstab, pin_profiles, pin_outer_operator,
 ]

@@ -105,3 +105,96 @@ def test_mixed_precision_with_profiles():
     ref = o.pcg(r, rtol=1e-12, max_iter=200)
     assert st == binding.TPMG_OK
     assert energy(o, u.cpu().numpy() - ref["u"]) <= 1e-8 * energy(o, ref["u"])
+
+
+# ---- general (non-factorising) profiles: the balanced flow at N > N* ---------------
+
+N_STAR = 9.81 / math.sqrt(1005.0 * 273.0)
+
+
+def flow_pair(n_freq, **extra):
+    o = oracle.Oracle(**KW)
+    outer, fac, eps = inputs.balanced_flow(o.grid(o.refinement)["centre"], o.vertical()["r"], n_freq)
+    o.set_profiles(**fac)
+    o.set_outer_profiles(**outer)
+    s = binding.Solver(profiles=fac, **KW, **extra)
+    s.set_outer_profiles(**outer)
+    return s, o, eps
+
+
+def test_full_operator_parity():
+    """The problem's operator from per-unknown coefficients (TPMG^full storage) against
+    the oracle's.  Bound: 64 ulp of |A||x|, with |A| from the factorised operator (the
+    general profiles differ from it by less than a factor 2 here) times 2."""
+    s, o, eps = flow_pair(0.028)
+    assert eps > 1.0
+    x = inputs.uniform_pm1(inputs.SEED_UNIFORM_SMALL + 60, s.N)
+    y = torch.empty(s.N, dtype=torch.float64, device="cuda")
+    s.apply_operator(torch.from_numpy(x).cuda(), y)
+    yo = o.apply_outer(x)
+    _, diag, _ = o.column_blocks()
+    bound = 2.0 * (2.0 * diag.reshape(-1) * np.abs(x) - o.apply(np.abs(x)))
+    assert np.all(np.abs(y.cpu().numpy() - yo) <= 64 * EPS * bound)
+    assert np.max(np.abs(yo - o.apply(x))) > 1e-3 * np.max(np.abs(yo))   # not the factorised operator
+
+
+@pytest.mark.parametrize("outer", [binding.TPMG_OUTER_CG, binding.TPMG_OUTER_BICGSTAB])
+def test_tpmg_fac_preconditions_the_full_operator(outer):
+    """FP64: the V-cycle of the factorised approximation preconditions the full operator
+    (Sec. 3.4); the solve matches the oracle's."""
+    s, o, _ = flow_pair(0.025, outer=outer)
+    f = inputs.uniform_pm1(inputs.SEED_UNIFORM_SMALL + 61, s.N)
+    u = torch.zeros(s.N, dtype=torch.float64, device="cuda")
+    st, it, rel, _ = s.solve(torch.from_numpy(f).cuda(), u, rtol=1e-10, max_iter=200)
+    ref = o.pcg(f, rtol=1e-10, max_iter=200) if outer == binding.TPMG_OUTER_CG else o.bicgstab(f, rtol=1e-10, max_iter=200)
+    assert st == binding.TPMG_OK and ref["status"] == 0 and abs(it - ref["iters"]) <= 1, (it, ref["iters"])
+    e = u.cpu().numpy() - ref["u"]
+    assert math.sqrt(e @ o.apply_outer(e)) <= 1e-8 * math.sqrt(ref["u"] @ o.apply_outer(ref["u"]))
+
+
+def test_mixed_vcycle_on_general_profiles_matches_the_oracle():
+    """Mixed precision: the BF16 stencil rebuilt from the general profiles on every level
+    (TPMG^full) against the oracle's V-cycle on the same profiles (BF16-rounded
+    coefficients, FP64 arithmetic)."""
+    s, o, _ = flow_pair(0.028, **MIXED)
+    o.set_vcycle_full(True)
+    o.set_vcycle_bf16(True)
+    r = inputs.uniform_pm1(inputs.SEED_UNIFORM_SMALL + 62, s.N)
+    z = torch.empty(s.N, dtype=torch.float64, device="cuda")
+    s.vcycle(torch.from_numpy(r).cuda(), z)
+    zo = o.vcycle(r)
+    e = z.cpu().numpy() - zo
+    assert math.sqrt(e @ o.apply_outer(e)) <= 5e-3 * math.sqrt(zo @ o.apply_outer(zo))
+    s.set_outer_profiles(None)   # back to the factorised stencil and operator
+    o.set_outer_profiles(None)
+    o.set_vcycle_full(False)
+    s.vcycle(torch.from_numpy(r).cuda(), z)
+    zf = o.vcycle(r)
+    assert math.sqrt((z.cpu().numpy() - zf) @ o.apply(z.cpu().numpy() - zf)) <= 5e-3 * math.sqrt(zf @ o.apply(zf))
+
+
+def test_factorisation_sweep_reports_iterations():
+    """Iterations to ||r|| <= 1e-5 ||r_0|| against the buoyancy frequency (eps = 0 ... 1.24),
+    the experiment of Sec. 5 (Fig. 3, right): the FP64 V-cycle on the factorised
+    approximation (TPMG^fac) and the mixed V-cycle on the full profiles (TPMG^full), each
+    preconditioning the full operator with Richardson, CG and BiCGStab."""
+    f = inputs.uniform_pm1(inputs.SEED_UNIFORM_SMALL + 63, 20 * 4 ** KW["refinement"] * KW["n_r"])
+    rows = []
+    for n_freq in (N_STAR, 0.022, 0.025, 0.028):
+        row = []
+        for extra in ({}, MIXED):
+            for outer in (binding.TPMG_OUTER_RICHARDSON, binding.TPMG_OUTER_CG, binding.TPMG_OUTER_BICGSTAB):
+                s, _, eps = flow_pair(n_freq, outer=outer, **extra)
+                fg = torch.from_numpy(f).cuda()
+                u = torch.zeros_like(fg)
+                st, it, rel, _ = s.solve(fg, u, rtol=1e-5, max_iter=300)
+                assert st == binding.TPMG_OK
+                row.append(it)
+        rows.append((eps, row))
+    print("\neps    | TPMG^fac (FP64): Richardson CG BiCGStab | TPMG^full (mixed): Richardson CG BiCGStab")
+    for eps, row in rows:
+        print(f"{eps:5.2f}  | {row[0]:4d} {row[1]:4d} {row[2]:4d} | {row[3]:4d} {row[4]:4d} {row[5]:4d}")
+    fac0, fac1 = rows[0][1][:3], rows[-1][1][:3]
+    full0, full1 = rows[0][1][3:], rows[-1][1][3:]
+    assert all(b >= a for a, b in zip(fac0, fac1))        # the factorised preconditioner degrades
+    assert all(b <= a + 2 for a, b in zip(full0, full1))  # the full one is robust

@@ -43,6 +43,10 @@ MUTANTS = {
     "profile_edge_one_side": ("edge = 0.5 * (hfac(o, o->ps_aS, G, T) + hfac(o, o->ps_aS, G, G->nbr[3 * T + e]));",
                               "edge = hfac(o, o->ps_aS, G, T);"),
     "profile_coarse_unweighted": ("s += aj * p[l + 1][4 * T + j];", "s += p[l + 1][4 * T + j];"),
+    "outer_edge_one_side": ("const double edge = 0.5 * (o->pf_aS[i] + o->pf_aS[(size_t)Tn * n + k]);",
+                            "const double edge = o->pf_aS[i];"),
+    "outer_upper_face": ("o->arv[k + 1] * o->pf_ar[fa + 1] * (u[i] - u[i + 1]);",
+                         "o->arv[k + 1] * o->pf_ar[fa] * (u[i] - u[i + 1]);"),
     "bicgstab_omega_sign": ("r[i] = sv[i] - omega * t[i];", "r[i] = sv[i] + omega * t[i];"),
     "bicgstab_beta_ratio": ("beta = (rho / rho_prev) * (alpha / omega);", "beta = (rho / rho_prev) * (omega / alpha);"),
     "prolong_half": ("uf[(size_t)(4 * T + j) * n + k] += uc[(size_t)T * n + k];",
