@@ -84,6 +84,8 @@ def _load(path: str | None = None):
         lib.oracle_apply_outer.argtypes = [_P, _P, _P]
         lib.oracle_set_vcycle_full.argtypes = [_P, _I]
         lib.oracle_set_vcycle_full.restype = None
+        lib.oracle_set_vcycle_partial.argtypes = [_P, _I]
+        lib.oracle_set_vcycle_partial.restype = None
         lib.oracle_set_coarse_solve.argtypes = [_P, COARSE_SOLVE_FN]
         lib.oracle_set_coarse_solve.restype = None
         lib.oracle_bf16.argtypes = [_D]
@@ -295,6 +297,12 @@ class Oracle:
         """The V-cycle's operators use the general profiles of set_outer_profiles
         (TPMG^full) instead of the factorised ones (TPMG^fac)."""
         self._lib.oracle_set_vcycle_full(self._h, 1 if on else 0)
+
+    def set_vcycle_partial(self, on: bool = True):
+        """The V-cycle's operators take alpha_r from the general profiles of
+        set_outer_profiles and beta, alpha_S from the factorised ones (TPMG^partial,
+        Sec. 6); off: the factorised profiles throughout (TPMG^fac)."""
+        self._lib.oracle_set_vcycle_partial(self._h, 1 if on else 0)
 
     def apply_outer(self, x) -> np.ndarray:
         """y = A x with the problem's operator (the general profiles where set)."""

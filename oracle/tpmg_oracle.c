@@ -391,7 +391,8 @@ typedef struct {
     double *pf_beta, *pf_ar, *pf_aS;
     /* the same general profiles on every refinement level (coarse: area-weighted means
      * over the 4 children, per vertical index) and the switch vc_full that makes the
-     * V-cycle's operators use them (TPMG^full) instead of the factorised profiles */
+     * V-cycle's operators use them: 0 none (TPMG^fac, the factorised profiles), 1 all
+     * three (TPMG^full), 2 alpha_r only, beta and alpha_S factorised (TPMG^partial, Sec. 6) */
     double **pl_beta, **pl_ar, **pl_aS;
     int vc_full;
     /* multigrid work arrays per multigrid level (0 = coarsest)               */
@@ -432,7 +433,8 @@ static double hfac(const octx *o, double *const *h, const ogrid *G, int T)
 /* With profiles: beta_hat x beta^r_k beta^S_T, alphar_hat x alpha_r^r(face) alpha_r^S_T,
  * alphaS_hat x alpha_S^r_k (alpha_S^S_T + alpha_S^S_T') / 2 (the edge value is the mean
  * of its two cells', so the operator stays symmetric). */
-static int full_now(const octx *o) { return o->vc_full && o->pl_beta; }
+static int full_now(const octx *o) { return o->vc_full == 1 && o->pl_beta; }
+static int general_ar_now(const octx *o) { return o->vc_full >= 1 && o->pl_ar; }
 static double beta_hat(const octx *o, const ogrid *G, int T, int k)
 {
     if (full_now(o)) return coeff(o, G->area[T] * o->vol[k] * o->pl_beta[G - o->grid][(size_t)T * o->n_r + k]);
@@ -451,7 +453,7 @@ static double alphaS_hat(const octx *o, const ogrid *G, int T, int e, int k)
 }
 static double alphar_hat(const octx *o, const ogrid *G, int T, int face)
 {
-    if (full_now(o))
+    if (general_ar_now(o))
         return coeff(o, o->omega2 * G->area[T] * o->arv[face] * o->pl_ar[G - o->grid][(size_t)T * (o->n_r + 1) + face]);
     return coeff(o, o->omega2 * G->area[T] * o->arv[face] * vfac(o->pr_ar, face) * hfac(o, o->ps_ar, G, T));
 }
@@ -792,6 +794,10 @@ void oracle_set_outer_profiles(void *h, const double *beta, const double *ar, co
 
 /* on != 0: the V-cycle's operators use the general profiles too (TPMG^full) */
 void oracle_set_vcycle_full(void *h, int on) { ((octx *)h)->vc_full = on != 0; }
+
+/* on != 0: the V-cycle's operators take alpha_r from the general profiles and beta,
+ * alpha_S from the factorised ones (partial factorisation TPMG^partial, Sec. 6) */
+void oracle_set_vcycle_partial(void *h, int on) { ((octx *)h)->vc_full = on != 0 ? 2 : 0; }
 
 /* y = A x with the problem's operator (oracle_apply gives the V-cycle's level operators). */
 int oracle_apply_outer(void *h, const double *x, double *y)

@@ -704,6 +704,59 @@ def pin_outer_operator(ns):
     assert res2["status"] == 0 and np.linalg.norm(res2["u"] - ud) <= 1e-9 * np.linalg.norm(ud)
 
 
+def pin_partial_profiles(ns):
+    """Partial factorisation TPMG^partial (Sec. 6): the V-cycle's operators take alpha_r
+    from the general profiles and beta, alpha_S from the factorised ones.  On the finest
+    level every vertical coupling is the factorised one times alpha_r / (alpha_r^S
+    alpha_r^r) and nothing else changes; where only alpha_r departs from a factorisation
+    the partial V-cycle is the full one (TPMG^full), and where only beta and alpha_S
+    depart it is the factorised one (TPMG^fac), on every level and for the whole cycle."""
+    kw = dict(refinement=2, n_levels=2, n_r=5, grading=1.1, H=0.1, courant_c=8.0)
+    o = ns.Oracle(**kw)
+    n = o.level_cells(1)
+    prof = _profiles(o, 41)
+    o.set_profiles(**prof)
+    pert = lambda k, shape: 1.0 + 0.3 * inputs.uniform_pm1(inputs.SEED_UNIFORM_SMALL + k, int(np.prod(shape))).reshape(shape)
+    fac = dict(beta=np.outer(prof["beta_s"], prof["beta_r"]), alphar=np.outer(prof["alphar_s"], prof["alphar_r"]),
+               alphaS=np.outer(prof["alphaS_s"], prof["alphaS_r"]))
+    x = inputs.uniform_pm1(inputs.SEED_UNIFORM_SMALL + 42, o.size())
+
+    def modes(**general):
+        o.set_outer_profiles(**general)
+        out = {}
+        for name, sw in (("fac", None), ("full", o.set_vcycle_full), ("partial", o.set_vcycle_partial)):
+            if sw:
+                sw(True)
+            out[name] = ([o.dense_operator(l) for l in range(o.n_levels)], o.vcycle(x))
+            if sw:
+                sw(False)
+        return out
+
+    def same(a, b, tol):
+        return all(np.abs(p - q).max() <= tol * np.abs(q).max() for p, q in zip(a[0], b[0])) and \
+            np.abs(a[1] - b[1]).max() <= tol * np.abs(b[1]).max()
+
+    # alpha_r alone departs: partial = full, not fac; the finest level's vertical
+    # couplings carry exactly the ratio of the profiles
+    pr = pert(43, (n, o.n_r + 1))
+    m = modes(beta=fac["beta"], alphar=fac["alphar"] * pr, alphaS=fac["alphaS"])
+    assert same(m["partial"], m["full"], 1e-12)
+    assert not same(m["partial"], m["fac"], 1e-3)
+    Ap, Af = m["partial"][0][-1], m["fac"][0][-1]
+    for T, k in ((0, 1), (17, 3), (n - 1, 4)):
+        i = T * o.n_r + k
+        assert abs(Ap[i, i - 1] - Af[i, i - 1] * pr[T, k]) <= 1e-13 * abs(Af[i, i - 1])
+        assert abs(Ap[i, i - 1] - Ap[i - 1, i]) <= 1e-13 * abs(Ap[i, i - 1])   # still symmetric
+    off_vertical = np.abs(np.subtract.outer(np.arange(o.size()) // o.n_r, np.arange(o.size()) // o.n_r)) > 0
+    assert np.abs((Ap - Af)[off_vertical]).max() <= 1e-13 * np.abs(Af).max()
+    # beta and alpha_S depart: partial = fac, not full
+    m = modes(beta=fac["beta"] * pert(44, (n, o.n_r)), alphar=fac["alphar"],
+              alphaS=fac["alphaS"] * pert(45, (n, o.n_r)))
+    assert same(m["partial"], m["fac"], 1e-12)
+    assert not same(m["partial"], m["full"], 1e-3)
+    o.set_outer_profiles()
+
+
 def pin_manufactured(ns):
     """Manufactured solution: f = A u*, solve to rtol 1e-12, recover u* in the
     energy norm to 1e-9 (a residual drop of 1e-12 bounds the error by cond-weighted 1e-12)."""
@@ -746,4 +799,5 @@ ALL_PINS = [
     pin_vertical_consistency, pin_thomas, pin_column_solve_exact, pin_transfers, pin_vcycle_dense, pin_preconditioner_symmetric,
     pin_invariant_subspaces, pin_pcg_dense, pin_bf16_rounding, pin_flexible_cg, pin_bf16_vcycle,
     pin_manufactured, pin_robust_convergence, pin_bicgstab, pin_profiles, pin_outer_operator,
+    pin_partial_profiles,
 ]

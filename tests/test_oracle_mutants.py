@@ -55,6 +55,10 @@ MUTANTS = {
                         "uf[(size_t)(4 * T + j) * n + k] -= uc[(size_t)T * n + k];"),
     "horizontal_uses_volume": ("return coeff(o, o->omega2 * o->dr[k] * G->g[3 * T + e] * vfac(o->pr_aS, k) * edge);",
                                "return coeff(o, o->omega2 * o->vol[k] * G->g[3 * T + e] * vfac(o->pr_aS, k) * edge);"),
+    "partial_takes_general_beta": ("static int full_now(const octx *o) { return o->vc_full == 1 && o->pl_beta; }",
+                                   "static int full_now(const octx *o) { return o->vc_full >= 1 && o->pl_beta; }"),
+    "partial_keeps_factorised_alphar": ("static int general_ar_now(const octx *o) { return o->vc_full >= 1 && o->pl_ar; }",
+                                        "static int general_ar_now(const octx *o) { return o->vc_full == 1 && o->pl_ar; }"),
     "bf16_truncates": ("return ldexp(rint(ldexp(m, 8)), e - 8);", "return ldexp(floor(ldexp(m, 8)), e - 8);"),
     "vertical_missing_r2": ("2.0 * o->r[k] * o->r[k] / (o->zeta[k + 1] - o->zeta[k - 1])",
                             "2.0 / (o->zeta[k + 1] - o->zeta[k - 1])"),
