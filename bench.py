@@ -16,7 +16,11 @@ Other workloads (--workload): batch48 (48 uneven mixed-precision solves in one
 graph launch), 1280x16 (the small parity case), 81920x64-mixed
 (the same solve with the V-cycle in FP32 on a BF16 stencil and flexible CG in
 FP64), 327680x128-mixed (refinement 7 x 128 levels, 41.9M unknowns, mixed
-precision) and 327680x128 (the same grid in FP64).
+precision), 327680x128 (the same grid in FP64) and 327680x128-learned (the
+learned form).  Two studies print the paper's measurements instead of a
+throughput: nr-sweep (time per iteration against n_r, Sec. 4.3) and
+balanced-flow (TPMG^fac / TPMG^partial / TPMG^full against the buoyancy
+frequency, Sec. 5).
 
 Flags: --gpus N --steps K --warmup W [--impl tpmg|reference] [--workload NAME]
 Under torchrun (N > 1) every rank solves its own replica (no data exchange:
@@ -82,6 +86,20 @@ WORKLOADS = {
              "relaxation), trained by the library's kernels on 2000 seeded (f, u) pairs from plain TPMG-PCG "
              "(smooth f: spherical harmonics up to degree 16 x vertical cosines); flexible CG, "
              "||r|| <= 1e-5 ||f|| on held-out smooth right-hand sides"),
+    "nr-sweep": dict(
+        study="nr_sweep", refinement=6, n_r=(16, 32, 64, 128, 256), iters=8, seed=2981010,
+        text="time per PCG iteration against the number of vertical levels (Sec. 4.3, eq. nzDependency: "
+             "t_iter = C + q n_r): icosahedral refinement 6 (81920 columns) x n_r in {16, 32, 64, 128, 256} "
+             "graded 1.05 over 10 km, omega^2/h^2=80, RHS uniform[-1,1], 6 MG levels, nu 2/2/1, 8 iterations per "
+             "solve (rtol 0); V-cycle TPMG^fac in FP64, TPMG^full in FP64, TPMG^full in mixed precision"),
+    "balanced-flow": dict(
+        study="balanced_flow", refinement=5, n_r=128, seed=2981011,
+        n_freq=(None, 0.022, 0.025, 0.028),   # None: N* = g / sqrt(cp T0), where the profiles factorise
+        text="balanced zonal flow (Sec. 5, after Davies 2005) at the paper's size: icosahedral refinement 5 "
+             "(20480 columns) x 128 levels graded 1.05 over 10 km (2.6M unknowns), omega^2/h^2=8, RHS "
+             "uniform[-1,1], 6 MG levels, nu 2/2/1, rtol 1e-5; buoyancy frequency N in {N*, 0.022, 0.025, "
+             "0.028} 1/s; the full operator preconditioned by TPMG^fac, TPMG^partial, TPMG^full (FP64) and "
+             "TPMG^full (mixed precision) with Richardson, CG and BiCGStab"),
     "batch48": dict(
         batch=48, seed=2981004,
         text="48 independent solves in one graph launch: refinement drawn from {4,5,6}, vertical levels from "
@@ -766,6 +784,168 @@ def run_learned(args, wl):
     return 0
 
 
+def time_solves(s, f, steps: int, warmup: int, rtol: float, max_iter: int, flush, stream):
+    """Device time (ms) and iterations of `steps` solves from a zero guess, L2 flushed
+    between solves outside the events, after `warmup` untimed solves."""
+    import torch
+
+    u = torch.zeros_like(f)
+    for _ in range(warmup):
+        u.zero_()
+        s.solve(f, u, rtol=rtol, max_iter=max_iter, raise_on_fail=False)
+    out = []
+    for k in range(steps):
+        flush.fill_(float(k))
+        u.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st, it, rel, _ = s.solve(f, u, rtol=rtol, max_iter=max_iter, raise_on_fail=False)
+        b.record(stream)
+        b.synchronize()
+        out.append((a.elapsed_time(b), it, st, rel))
+    return out
+
+
+def launches_of(s) -> int:
+    prof = s.profile_read()
+    return int(sum(v["launches"] for c, v in prof.items() if c != "copy"))
+
+
+def study_line(args, wl, metric, value, unit, higher, dtype, extra, clk, launches, world):
+    line = {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": higher, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": wl["text"], "parallelism": f"replicas{world}",
+                       "l2": "flushed between solves (write of 2x L2 outside the timed events)"},
+            "e2e": None, "gpu_launches": launches, "roofline": None, "cpu_baseline": None, "clocks": clk}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
+def run_nr_sweep(args, wl):
+    """Sec. 4.3, eq. nzDependency: time per iteration against n_r, fitted by least
+    squares to t = C + q n_r; C / t is the share of the per-column work that does
+    not grow with n_r (indirect addressing, launches, the coarse levels)."""
+    import torch
+
+    from paper_1408_2981_gb300 import binding, build as _build, inputs
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    _build.build()
+    stream = torch.cuda.current_stream()
+    l2 = torch.cuda.get_device_properties(local).L2_cache_size
+    flush = torch.empty(max(2 * l2, 256 << 20) // 4, dtype=torch.float32, device="cuda")
+    variants = {"TPMG^fac FP64": dict(),
+                "TPMG^full FP64": dict(coeff_storage=binding.TPMG_COEFF_FULL),
+                "TPMG^full mixed": dict(MIXED)}
+    K = wl["iters"]
+    points, launches = [], 0
+    clocks = ClockSampler(local)
+    clocks.start()
+    for n_r in wl["n_r"]:
+        for name, extra in variants.items():
+            s = binding.Solver(stream=stream, refinement=wl["refinement"], n_levels=6, n_r=n_r, grading=1.05,
+                               courant_c=80.0, nu_pre=2, nu_post=2, nu_coarse=1, **extra)
+            f = torch.from_numpy(inputs.uniform_pm1(wl["seed"], s.N)).cuda()
+            s.profile(classes=())
+            res = time_solves(s, f, args.steps, args.warmup, 0.0, K, flush, stream)
+            launches += launches_of(s)
+            assert all(it == K for _, it, _, _ in res), res
+            ms = statistics.median(r[0] for r in res)
+            points.append({"n_r": n_r, "variant": name, "t_iter_ms": ms / K, "unknowns": s.N,
+                           "ns_per_unknown_iter": 1e6 * ms / K / s.N})
+            del s
+            torch.cuda.synchronize()
+    clk = clocks.stop()
+    fits = {}
+    for name in variants:
+        xs = np.array([p["n_r"] for p in points if p["variant"] == name], dtype=np.float64)
+        ys = np.array([p["t_iter_ms"] for p in points if p["variant"] == name])
+        q, c = np.polyfit(xs, ys, 1)
+        pred = c + q * xs
+        r2 = 1.0 - float(((ys - pred) ** 2).sum() / ((ys - ys.mean()) ** 2).sum())
+        fits[name] = {"C_ms": c, "q_ms_per_level": q, "r2": r2,
+                      "overhead_at_128": c / (c + 128 * q), "overhead_at_256": c / (c + 256 * q)}
+    if rank == 0:
+        study_line(args, wl, "share of the time per iteration that does not grow with n_r, at n_r = 128 "
+                   "(Sec. 4.3: C / (C + 128 q), TPMG^fac FP64)", fits["TPMG^fac FP64"]["overhead_at_128"],
+                   "fraction", False, "f64", {"points": points, "fit": fits, "iters_per_solve": K}, clk, launches,
+                   world)
+    return 0
+
+
+def run_balanced_flow(args, wl):
+    """Sec. 5, Figs. 3-4 and Table 1's preconditioners: iterations, time per iteration
+    and total solve time against the buoyancy frequency for TPMG^fac, TPMG^partial and
+    TPMG^full (FP64) and TPMG^full in mixed precision, each preconditioning the full
+    operator with Richardson, CG and BiCGStab."""
+    import torch
+
+    from paper_1408_2981_gb300 import binding, build as _build, inputs
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    _build.build()
+    stream = torch.cuda.current_stream()
+    l2 = torch.cuda.get_device_properties(local).L2_cache_size
+    flush = torch.empty(max(2 * l2, 256 << 20) // 4, dtype=torch.float32, device="cuda")
+    precs = {"TPMG^fac FP64": dict(),
+             "TPMG^partial FP64": dict(coeff_storage=binding.TPMG_COEFF_PARTIAL),
+             "TPMG^full FP64": dict(coeff_storage=binding.TPMG_COEFF_FULL),
+             "TPMG^full mixed": dict(MIXED)}
+    outers = {"Richardson": binding.TPMG_OUTER_RICHARDSON, "CG": binding.TPMG_OUTER_CG,
+              "BiCGStab": binding.TPMG_OUTER_BICGSTAB}
+    kw = dict(refinement=wl["refinement"], n_levels=6, n_r=wl["n_r"], grading=1.05, courant_c=8.0,
+              nu_pre=2, nu_post=2, nu_coarse=1)
+    probe = binding.Solver(stream=stream, **kw)
+    mesh = probe.export_mesh()
+    N = probe.N
+    del probe
+    f = torch.from_numpy(inputs.uniform_pm1(wl["seed"], N)).cuda()
+    rows, launches = [], 0
+    steps = max(1, min(args.steps, 5))
+    clocks = ClockSampler(local)
+    clocks.start()
+    for n_freq in wl["n_freq"]:
+        n_freq = 9.81 / math.sqrt(1005.0 * 273.0) if n_freq is None else n_freq
+        outer_prof, fac_prof, eps = inputs.balanced_flow(mesh["centres"], mesh["r_faces"], n_freq)
+        for pname, pextra in precs.items():
+            for oname, outer in outers.items():
+                s = binding.Solver(stream=stream, profiles=fac_prof, outer=outer, **kw, **pextra)
+                s.set_outer_profiles(**outer_prof)
+                s.profile(classes=())
+                res = time_solves(s, f, steps, args.warmup, 1e-5, 300, flush, stream)
+                launches += launches_of(s)
+                ms = statistics.median(r[0] for r in res)
+                it, st, rel = res[-1][1], res[-1][2], res[-1][3]
+                rows.append({"N": n_freq, "eps": round(eps, 3), "preconditioner": pname, "outer": oname,
+                             "status": st, "iters": it, "rel_resid": rel, "t_solve_ms": ms,
+                             "t_iter_ms": ms / max(it, 1)})
+                del s
+                torch.cuda.synchronize()
+    clk = clocks.stop()
+    ok = [r for r in rows if r["status"] == 0]
+
+    def t_iter(prec, outer, eps_i=0):
+        e = sorted({r["eps"] for r in rows})[eps_i]
+        return next(r["t_iter_ms"] for r in rows if r["preconditioner"] == prec and r["outer"] == outer
+                    and r["eps"] == e)
+
+    ratios = {o: {"full/fac": t_iter("TPMG^full FP64", o) / t_iter("TPMG^fac FP64", o),
+                  "partial/fac": t_iter("TPMG^partial FP64", o) / t_iter("TPMG^fac FP64", o),
+                  "full-mixed/fac": t_iter("TPMG^full mixed", o) / t_iter("TPMG^fac FP64", o)}
+              for o in ("Richardson", "BiCGStab")}
+    eps_max = max(r["eps"] for r in rows)
+    best = min((r for r in ok if r["eps"] == eps_max), key=lambda r: r["t_solve_ms"])
+    if rank == 0:
+        study_line(args, wl, "time to a 1e-5 residual reduction at the largest eps (Sec. 5, Fig. 4), fastest "
+                   "preconditioner and outer iteration", best["t_solve_ms"], "ms", False, "f64 / f32+f64",
+                   {"best": best, "t_iter_ratio_eps0": ratios, "table": rows, "unknowns": N}, clk, launches,
+                   world)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -783,11 +963,17 @@ def main(argv=None):
         ap.error("--warmup must be >= 1")
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
+        if "study" in wl:
+            print(json.dumps({"impl": "reference", "unavailable": "a study of the GPU kernels' time per iteration "
+                              "(no oracle arm); the oracle arm times the single-problem workloads"}))
+            return 0
         if "batch" in wl:
             print(json.dumps({"impl": "reference", "unavailable": "the batched workload has no oracle arm: its "
                               "problems are each an oracle solve of the single-problem workloads"}))
             return 0
         return run_reference(args, wl)
+    if "study" in wl:
+        return run_nr_sweep(args, wl) if wl["study"] == "nr_sweep" else run_balanced_flow(args, wl)
     if "batch" in wl:
         return run_batch(args, wl)
     if "learned" in wl:

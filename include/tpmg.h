@@ -62,12 +62,19 @@ typedef enum {
 enum { TPMG_SMOOTH_MCSOR = 0,   /* multicolour block-SOR: forward colours before, reverse after the correction */
        TPMG_SMOOTH_JACOBI = 1 }; /* weighted block-Jacobi */
 
-/* Storage of the V-cycle's stencil (Sec. 4.2): recomputed on the fly from
- * O(n_r + n_cells) factorised FP64 data (TPMG^otimes; the FP64 V-cycle), or
- * stored per unknown (TPMG^full) in BF16 (the mixed-precision V-cycle).  The
- * outer operator of tpmg_solve and tpmg_apply_operator is always the exact
- * factorised FP64 one. */
-enum { TPMG_COEFF_FACTORISED = 0, TPMG_COEFF_FULL = 1 };
+/* Storage of the V-cycle's stencil (Sec. 4.2):
+ *   FACTORISED: recomputed on the fly from O(n_r + n_cells) factorised FP64 data
+ *     (TPMG^otimes, TPMG^fac);
+ *   FULL: stored per unknown (TPMG^full) -- in FP64 for the FP64 V-cycle (40 bytes
+ *     per unknown and level), in BF16 for the mixed-precision V-cycle;
+ *   PARTIAL (FP64 only): alpha_r stored per face and column, beta and alpha_S
+ *     factorised (the partial factorisation TPMG^partial of Sec. 6; 8 bytes per
+ *     unknown and level).
+ * Until tpmg_set_outer_profiles gives general profiles, FULL and PARTIAL store the
+ * factorised profiles' coefficients, so all three are the same preconditioner up to
+ * rounding.  The outer operator of tpmg_solve and tpmg_apply_operator is the exact
+ * factorised FP64 one, or the general one of tpmg_set_outer_profiles. */
+enum { TPMG_COEFF_FACTORISED = 0, TPMG_COEFF_FULL = 1, TPMG_COEFF_PARTIAL = 2 };
 
 /* Outer iteration of tpmg_solve (Sec. 5 uses Richardson and BiCGStab; with constant
  * profiles the operator and the V-cycle are symmetric positive definite, so CG applies). */
@@ -79,8 +86,8 @@ enum { TPMG_OUTER_CG = 0,          /* preconditioned CG (flexible CG in the mixe
 enum { TPMG_CENTRE_CIRCUM = 0,      /* spherical circumcentre (centre chord normal to the edge) */
        TPMG_CENTRE_VERTEX_MEAN = 1 };
 
-/* Arithmetic of the V-cycle.  FP64: everything in double (requires
- * TPMG_COEFF_FACTORISED).  MIXED (requires TPMG_COEFF_FULL): the V-cycle
+/* Arithmetic of the V-cycle.  FP64: everything in double (any TPMG_COEFF_*).
+ * MIXED (requires TPMG_COEFF_FULL): the V-cycle
  * (operator, line smoother, transfers) in FP32 on the BF16 stencil, with the
  * column factors precomputed per level in FP32; the outer Krylov vectors,
  * residual, dot products and updates in FP64.  Because the FP32 V-cycle is not
@@ -164,12 +171,14 @@ tpmg_status tpmg_setup_profiles(const tpmg_params *p, const tpmg_profiles *prof,
  * at the faces (cell-major), host arrays, positive and finite; three NULLs restore the
  * factorised operator.  From then on the outer iteration -- tpmg_solve, tpmg_apply_operator,
  * the learned and batched solves -- applies this operator with per-unknown FP64
- * coefficients (edges: the mean of the two cells' alpha_S).  The FP64 V-cycle keeps the
- * factorised profiles given to tpmg_setup_profiles: TPMG^fac preconditioning the full
- * operator (Sec. 3.4, Sec. 5).  The mixed-precision V-cycle, which stores its stencil per
- * unknown, adopts the general profiles as well (TPMG^full; each coarse level takes the
- * area-weighted mean over the 4 children per vertical index).  Synchronous.
- * Errors: INVALID_ARG, OOM, CUDA. */
+ * coefficients (edges: the mean of the two cells' alpha_S).  The V-cycle follows its
+ * coefficient storage (Sec. 3.4, Sec. 5, Sec. 6):
+ *   FACTORISED keeps the factorised profiles given to tpmg_setup_profiles (TPMG^fac
+ *     preconditioning the full operator);
+ *   FULL (FP64 or mixed precision) adopts all three general profiles (TPMG^full);
+ *   PARTIAL adopts alpha_r and keeps the factorised beta and alpha_S (TPMG^partial).
+ * Each coarse level takes the area-weighted mean of a general profile over the 4
+ * children per vertical index.  Synchronous.  Errors: INVALID_ARG, OOM, CUDA. */
 tpmg_status tpmg_set_outer_profiles(tpmg_ctx *ctx, const double *h_beta, const double *h_alphar,
                                     const double *h_alphaS);
 

@@ -28,6 +28,7 @@ TPMG_SMOOTH_MCSOR = 0
 TPMG_SMOOTH_JACOBI = 1
 TPMG_COEFF_FACTORISED = 0
 TPMG_COEFF_FULL = 1
+TPMG_COEFF_PARTIAL = 2
 TPMG_CENTRE_CIRCUM = 0
 TPMG_CENTRE_VERTEX_MEAN = 1
 TPMG_PREC_FP64 = 0
@@ -291,7 +292,9 @@ class Solver:
     def set_outer_profiles(self, beta=None, alphar=None, alphaS=None):
         """The problem's operator with general profiles on the finest level (numpy
         arrays: beta, alphaS [n_cells, n_r], alphar [n_cells, n_r + 1]); None restores
-        the factorised operator.  The V-cycle keeps the profiles of the set-up."""
+        the factorised operator.  The V-cycle follows its coefficient storage:
+        FACTORISED keeps the profiles of the set-up (TPMG^fac), FULL adopts all three
+        (TPMG^full), PARTIAL adopts alpha_r (TPMG^partial)."""
         if beta is None:
             self._check(self._lib.tpmg_set_outer_profiles(self._h, None, None, None), "tpmg_set_outer_profiles")
             return

@@ -156,11 +156,14 @@ bool validate(const tpmg_params *p, std::string &msg)
     }
     if (p->smoother != TPMG_SMOOTH_MCSOR && p->smoother != TPMG_SMOOTH_JACOBI) { msg = "unknown smoother"; return false; }
     if (!(p->relax > 0.0 && p->relax < 2.0)) { msg = "relax must be in (0, 2)"; return false; }
-    if (p->coeff_storage != TPMG_COEFF_FACTORISED && p->coeff_storage != TPMG_COEFF_FULL) { msg = "unknown coefficient storage"; return false; }
+    if (p->coeff_storage != TPMG_COEFF_FACTORISED && p->coeff_storage != TPMG_COEFF_FULL &&
+        p->coeff_storage != TPMG_COEFF_PARTIAL) {
+        msg = "unknown coefficient storage"; return false;
+    }
     if (p->centre != TPMG_CENTRE_CIRCUM && p->centre != TPMG_CENTRE_VERTEX_MEAN) { msg = "unknown centre kind"; return false; }
     if (p->precision != TPMG_PREC_FP64 && p->precision != TPMG_PREC_MIXED) { msg = "unknown precision"; return false; }
-    if ((p->precision == TPMG_PREC_MIXED) != (p->coeff_storage == TPMG_COEFF_FULL)) {
-        msg = "the FP64 V-cycle uses factorised storage, the mixed-precision V-cycle full BF16 storage";
+    if (p->precision == TPMG_PREC_MIXED && p->coeff_storage != TPMG_COEFF_FULL) {
+        msg = "the mixed-precision V-cycle stores its stencil per unknown in BF16 (TPMG_COEFF_FULL)";
         return false;
     }
     if (p->graphs != 0 && p->graphs != 1) { msg = "graphs must be 0 or 1"; return false; }
@@ -979,6 +982,60 @@ void bf16_stencil(const tpmg_ctx *ctx, const HostLevel &H, const double *pb, con
     }
 }
 
+// The FP64 stencil of one multigrid level stored per unknown (Sec. 4.2; Appendix A,
+// eq. hatFunctionsNonFac), horizontal part: c [n][n_r] {alphaS_hat e = 0, 1, 2, beta_hat}.
+// With pb == NULL from the factorised profiles (the products the factorised kernels
+// form); otherwise from general profiles of this level, pb, ps [n][n_r] (beta, alpha_S
+// at the cells), an edge taking the mean of its two cells' alpha_S.
+void fp64_horizontal(const tpmg_ctx *ctx, const HostLevel &H, const double *pb, const double *ps, std::vector<dbl4> &c)
+{
+    const HostGrid &G = ctx->host;
+    const int n_r = ctx->p.n_r;
+    c.resize((size_t)H.n * n_r);
+    for (int T = 0; T < H.n; ++T) {
+        double ge[3];
+        for (int e = 0; e < 3; ++e)
+            ge[e] = H.g[3 * T + e] * (ctx->ps_aS.empty() ? 1.0
+                                      : 0.5 * (ctx->ps_aS[H.ref][T] + ctx->ps_aS[H.ref][H.nbr[3 * T + e]]));
+        const double aB = H.area[T] * hfac(ctx->ps_beta, H.ref, T);
+        for (int k = 0; k < n_r; ++k) {
+            const size_t i = (size_t)T * n_r + k;
+            if (!pb) {
+                const double hr = G.omega2 * G.dr[k] * vfac(ctx->pr_aS, k);
+                c[i] = dbl4{hr * ge[0], hr * ge[1], hr * ge[2], aB * (G.vol[k] * vfac(ctx->pr_beta, k))};
+            } else {
+                const double hr = G.omega2 * G.dr[k];
+                double a[3];
+                for (int e = 0; e < 3; ++e)
+                    a[e] = hr * H.g[3 * T + e] * (0.5 * (ps[i] + ps[(size_t)H.nbr[3 * T + e] * n_r + k]));
+                c[i] = dbl4{a[0], a[1], a[2], H.area[T] * G.vol[k] * pb[i]};
+            }
+        }
+    }
+}
+
+// Vertical part: cr [n][n_r + 1] alphar_hat of face k, zero on the two boundary faces
+// (no flux through the bottom and the top).  With pr == NULL from the factorised
+// profiles, otherwise from a general alpha_r of this level [n][n_r + 1].
+void fp64_vertical(const tpmg_ctx *ctx, const HostLevel &H, const double *pr, std::vector<double> &cr)
+{
+    const HostGrid &G = ctx->host;
+    const int n_r = ctx->p.n_r;
+    cr.resize((size_t)H.n * (n_r + 1));
+    for (int T = 0; T < H.n; ++T) {
+        const double aR = H.area[T] * hfac(ctx->ps_ar, H.ref, T);
+        for (int k = 0; k <= n_r; ++k) {
+            const size_t fi = (size_t)T * (n_r + 1) + k;
+            if (k == 0 || k == n_r)
+                cr[fi] = 0.0;
+            else if (!pr)
+                cr[fi] = aR * (G.omega2 * G.face[k] * vfac(ctx->pr_ar, k));
+            else
+                cr[fi] = G.omega2 * H.area[T] * G.face[k] * pr[fi];
+        }
+    }
+}
+
 // General per-unknown profiles of one level from the next finer (m values per cell):
 // each coarse (cell, j) the area-weighted mean over the 4 children's (cell, j).
 std::vector<double> average_children(const HostLevel &fine, const std::vector<double> &pf, int m)
@@ -1050,6 +1107,18 @@ tpmg_status upload_level(tpmg_ctx *ctx, int l)
     CU(dalloc(ctx, &D.task_nbr, tasks.size()));
     CU(dalloc(ctx, &D.task_g, tasks.size()));
     const bool mixed = p.precision == TPMG_PREC_MIXED;
+    std::vector<dbl4> hc;     // FP64 stencil per unknown (FULL, PARTIAL), alive until the final synchronise
+    std::vector<double> hcr;
+    if (!mixed && p.coeff_storage != TPMG_COEFF_FACTORISED) {
+        fp64_vertical(ctx, H, nullptr, hcr);
+        CU(dalloc(ctx, &D.vcr, hcr.size()));
+        CU(cudaMemcpyAsync(D.vcr, hcr.data(), hcr.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        if (p.coeff_storage == TPMG_COEFF_FULL) {
+            fp64_horizontal(ctx, H, nullptr, nullptr, hc);
+            CU(dalloc(ctx, &D.vc, nn));
+            CU(cudaMemcpyAsync(D.vc, hc.data(), nn * sizeof(dbl4), cudaMemcpyHostToDevice, ctx->stream));
+        }
+    }
     if (!mixed) {
         D.scan = H.n <= p.scan_max_cells;
         if (D.scan) {
@@ -1317,11 +1386,13 @@ tpmg_status tpmg_set_outer_profiles(tpmg_ctx *ctx, const double *h_beta, const d
     const int n_r = ctx->p.n_r, n = H.n;
     CU(cudaStreamSynchronize(ctx->stream));
     drop_graph(ctx);   // captured solves hold the operator's kernels
-    // the mixed-precision V-cycle stores its stencil per unknown: it adopts the general
-    // profiles too (TPMG^full; coarse levels average them over the children), or goes
-    // back to the factorised ones
+    // a V-cycle that stores its stencil per unknown adopts the general profiles too
+    // (FULL: all three, TPMG^full; PARTIAL: alpha_r, TPMG^partial; coarse levels average
+    // them over the children), or goes back to the factorised ones; then its column
+    // factors are formed again
     auto restencil = [&](const double *pb, const double *pr, const double *ps) -> tpmg_status {
-        if (ctx->p.precision != TPMG_PREC_MIXED) return TPMG_OK;
+        const bool mixed = ctx->p.precision == TPMG_PREC_MIXED;
+        if (ctx->p.coeff_storage == TPMG_COEFF_FACTORISED) return TPMG_OK;
         std::vector<double> b, r, a;
         if (pb) { b.assign(pb, pb + (size_t)n * n_r); r.assign(pr, pr + (size_t)n * (n_r + 1)); a.assign(ps, ps + (size_t)n * n_r); }
         for (int l = ctx->p.n_levels - 1; l >= 0; --l) {
@@ -1332,15 +1403,31 @@ tpmg_status tpmg_set_outer_profiles(tpmg_ctx *ctx, const double *h_beta, const d
                 r = average_children(Hf, r, n_r + 1);
                 a = average_children(Hf, a, n_r);
             }
-            std::vector<bf16x4> cp;
-            std::vector<unsigned short> cv;
-            bf16_stencil(ctx, Hl, pb ? b.data() : nullptr, pb ? r.data() : nullptr, pb ? a.data() : nullptr, cp, cv);
             LevelDev &Dl = ctx->lv[l];
-            CU(cudaMemcpyAsync(Dl.cpack, cp.data(), cp.size() * sizeof(bf16x4), cudaMemcpyHostToDevice, ctx->stream));
-            CU(cudaMemcpyAsync(Dl.cvert, cv.data(), cv.size() * sizeof(unsigned short), cudaMemcpyHostToDevice,
-                               ctx->stream));
-            CU(launch_thomas_factors32(launch_of(ctx), Dl));
-            CU(cudaStreamSynchronize(ctx->stream));   // cp, cv are local
+            if (mixed) {
+                std::vector<bf16x4> cp;
+                std::vector<unsigned short> cv;
+                bf16_stencil(ctx, Hl, pb ? b.data() : nullptr, pb ? r.data() : nullptr, pb ? a.data() : nullptr, cp, cv);
+                CU(cudaMemcpyAsync(Dl.cpack, cp.data(), cp.size() * sizeof(bf16x4), cudaMemcpyHostToDevice, ctx->stream));
+                CU(cudaMemcpyAsync(Dl.cvert, cv.data(), cv.size() * sizeof(unsigned short), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+                CU(launch_thomas_factors32(launch_of(ctx), Dl));
+                CU(cudaStreamSynchronize(ctx->stream));   // cp, cv are local
+                continue;
+            }
+            std::vector<dbl4> c;
+            std::vector<double> cr;
+            fp64_vertical(ctx, Hl, pb ? r.data() : nullptr, cr);
+            CU(cudaMemcpyAsync(Dl.vcr, cr.data(), cr.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+            if (ctx->p.coeff_storage == TPMG_COEFF_FULL) {
+                fp64_horizontal(ctx, Hl, pb ? b.data() : nullptr, pb ? a.data() : nullptr, c);
+                CU(cudaMemcpyAsync(Dl.vc, c.data(), c.size() * sizeof(dbl4), cudaMemcpyHostToDevice, ctx->stream));
+            }
+            CU(launch_twisted_factors(launch_of(ctx), Dl, ctx->vert));
+            if (Dl.scan) {
+                CU(launch_thomas_factors(launch_of(ctx), Dl, ctx->vert));
+            }
+            CU(cudaStreamSynchronize(ctx->stream));   // c, cr are local
         }
         return TPMG_OK;
     };
@@ -1357,23 +1444,10 @@ tpmg_status tpmg_set_outer_profiles(tpmg_ctx *ctx, const double *h_beta, const d
     };
     if (!ok(h_beta, nn) || !ok(h_alphaS, nn) || !ok(h_alphar, nf))
         return fail(ctx, TPMG_ERR_INVALID_ARG, "profiles must be positive and finite");
-    std::vector<dbl4> c(nn);
-    std::vector<double> cr(nf);
-    for (int T = 0; T < n; ++T) {
-        for (int k = 0; k < n_r; ++k) {
-            const size_t i = (size_t)T * n_r + k;
-            const double hr = G.omega2 * G.dr[k];
-            double a[3];
-            for (int e = 0; e < 3; ++e)
-                a[e] = hr * H.g[3 * T + e] * (0.5 * (h_alphaS[i] + h_alphaS[(size_t)H.nbr[3 * T + e] * n_r + k]));
-            c[i] = dbl4{a[0], a[1], a[2], H.area[T] * G.vol[k] * h_beta[i]};
-        }
-        for (int k = 0; k <= n_r; ++k) {
-            // the boundary faces carry no flux (zero-flux vertical conditions)
-            const size_t fi = (size_t)T * (n_r + 1) + k;
-            cr[fi] = (k == 0 || k == n_r) ? 0.0 : G.omega2 * H.area[T] * G.face[k] * h_alphar[fi];
-        }
-    }
+    std::vector<dbl4> c;
+    std::vector<double> cr;
+    fp64_horizontal(ctx, H, h_beta, h_alphaS, c);
+    fp64_vertical(ctx, H, h_alphar, cr);
     if (!D.cvr) {
         dbl4 *cf = nullptr;
         CU(dalloc(ctx, &cf, nn));

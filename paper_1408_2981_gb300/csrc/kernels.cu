@@ -56,11 +56,38 @@ struct OpView {
     const double *__restrict__ w;
     const double *__restrict__ hr;
     int n_r;
+    // the V-cycle's stencil stored per unknown (Sec. 4.2), or NULL for the factorised form:
+    // c [n][n_r] {alphaS_hat e = 0, 1, 2, beta_hat} (TPMG^full), cr [n][n_r + 1]
+    // alphar_hat of face k (TPMG^full and TPMG^partial)
+    const dbl4 *__restrict__ c;
+    const double *__restrict__ cr;
 };
 
 inline OpView make_view(const LevelDev &lv, const VertDev &v, int n_r)
 {
-    return OpView{lv.nbr, lv.g, lv.area, lv.area_r, v.vol, v.w, v.hr, n_r};
+    return OpView{lv.nbr, lv.g, lv.area, lv.area_r, v.vol, v.w, v.hr, n_r, lv.vc, lv.vcr};
+}
+
+// Stencil form of a level's V-cycle operator: factorised profiles (TPMG^fac), alpha_r
+// per face (TPMG^partial), or everything per unknown (TPMG^full).
+enum { CM_FAC = 0, CM_PARTIAL = 1, CM_FULL = 2 };
+inline int stencil_form(const LevelDev &lv) { return lv.vc ? CM_FULL : (lv.vcr ? CM_PARTIAL : CM_FAC); }
+
+// Column block A_T of a level (set-up kernels): the excess m_k of row k (its diagonal
+// minus its vertical couplings) and the coupling c_k of face k (rows k-1 and k).
+// A = |T| beta^S_T, G = sum of the edge weights g_e, Ar = |T| alpha_r^S_T.
+__device__ __forceinline__ double col_excess(const OpView &o, int T, int k, double A, double G)
+{
+    if (o.c) {
+        const dbl4 c = o.c[(size_t)T * o.n_r + k];
+        return c.w + ((c.x + c.y) + c.z);
+    }
+    return fma(A, o.vol[k], o.hr[k] * G);
+}
+__device__ __forceinline__ double col_coupling(const OpView &o, int T, int k, double Ar)
+{
+    if (o.cr) return o.cr[(size_t)T * (o.n_r + 1) + k];
+    return Ar * o.w[k];
 }
 
 // (A x)_{T,k} in flux form: 13 FP64 instructions.
@@ -104,6 +131,31 @@ __device__ __forceinline__ double apply_any(const OpView &o, const FullView &fv,
                                             int k, int i)
 {
     if (FULL) return apply_full_at(o, fv, x, T, k, i);
+    return apply_at(o, x, T, k, i);
+}
+
+// Row (T, k) with the vertical couplings per face (TPMG^partial): apply_at with
+// area_r w_k replaced by the stored alphar_hat of face k.
+__device__ __forceinline__ double apply_partial_at(const OpView &o, const double *__restrict__ x, int T, int k, int i)
+{
+    const int n_r = o.n_r;
+    const int4 nb = __ldg(&o.nbr[T]);
+    const dbl4 g = o.g[T];
+    const double xc = x[i];
+    const double dm = k > 0 ? xc - x[i - 1] : 0.0;
+    const double dp = k < n_r - 1 ? xc - x[i + 1] : 0.0;
+    const double *cr = o.cr + (size_t)T * (n_r + 1) + k;
+    const double vert = fma(__ldg(&cr[1]), dp, __ldg(&cr[0]) * dm);
+    const double hor = fma(g.z, xc - x[nb.z * n_r + k], fma(g.y, xc - x[nb.y * n_r + k], g.x * (xc - x[nb.x * n_r + k])));
+    return vert + fma(__ldg(&o.area[T]) * __ldg(&o.vol[k]), xc, __ldg(&o.hr[k]) * hor);
+}
+
+// Row (T, k) of a level's V-cycle operator in stencil form CM.
+template <int CM>
+__device__ __forceinline__ double apply_vc(const OpView &o, const double *__restrict__ x, int T, int k, int i)
+{
+    if (CM == CM_FULL) return apply_full_at(o, FullView{o.c, o.cr}, x, T, k, i);
+    if (CM == CM_PARTIAL) return apply_partial_at(o, x, T, k, i);
     return apply_at(o, x, T, k, i);
 }
 
@@ -181,7 +233,7 @@ __global__ void __launch_bounds__(NT) k_residual(OpView o, FullView full, const 
 }
 
 // f_c[T][k] = sum_j (f - A u)[4T + j][k]  (Algorithm 1 residual + restriction, Sec. 5)
-template <int NT>
+template <int NT, int CM>
 __global__ void __launch_bounds__(NT) k_resid_restrict(OpView o, const double *__restrict__ f,
                                                        const double *__restrict__ u, double *__restrict__ fc, int Nc)
 {
@@ -191,7 +243,7 @@ __global__ void __launch_bounds__(NT) k_resid_restrict(OpView o, const double *_
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int T = 4 * Tc + j, i = T * o.n_r + k;
-            s += f[i] - apply_at(o, u, T, k, i);
+            s += f[i] - apply_vc<CM>(o, u, T, k, i);
         }
         fc[ic] = s;
     }
@@ -244,8 +296,8 @@ __global__ void k_twisted_factors(int n_tasks, OpView o, const int *__restrict__
     const double A = o.area[T], Ar = o.area_r[T], G = o.g[T].w;
     double e = 0.0, p = 1.0;
     for (int k = 0; k < j; ++k) {
-        const double m = fma(A, o.vol[k], o.hr[k] * G);
-        const double c = Ar * o.w[k], cu = Ar * o.w[k + 1];
+        const double m = col_excess(o, T, k, A, G);
+        const double c = col_coupling(o, T, k, Ar), cu = col_coupling(o, T, k + 1, Ar);
         e = k == 0 ? m : m + c * e / p;
         p = e + cu;
         const double iv = 1.0 / p;
@@ -255,8 +307,8 @@ __global__ void k_twisted_factors(int n_tasks, OpView o, const int *__restrict__
     }
     double eb = 0.0, q = 1.0;
     for (int k = n - 1, s = 0; k > j; --k, ++s) {
-        const double m = fma(A, o.vol[k], o.hr[k] * G);
-        const double cd = Ar * o.w[k], cu = Ar * o.w[k + 1];
+        const double m = col_excess(o, T, k, A, G);
+        const double cd = col_coupling(o, T, k, Ar), cu = col_coupling(o, T, k + 1, Ar);
         eb = k == n - 1 ? m : m + cu * eb / q;
         q = eb + cd;
         const double iv = 1.0 / q;
@@ -264,8 +316,8 @@ __global__ void k_twisted_factors(int n_tasks, OpView o, const int *__restrict__
         fb[base + s * 32 + col + 16] = cu * iv;
         fc[base + s * 32 + col + 16] = cd * iv;
     }
-    const double cj = Ar * o.w[j], cj1 = Ar * o.w[j + 1];
-    double gam = fma(A, o.vol[j], o.hr[j] * G);
+    const double cj = col_coupling(o, T, j, Ar), cj1 = col_coupling(o, T, j + 1, Ar);
+    double gam = col_excess(o, T, j, A, G);
     if (j > 0) gam += cj * e / p;
     if (j < n - 1) gam += cj1 * eb / q;
     const double ig = 1.0 / gam;
@@ -386,8 +438,8 @@ __global__ void k_thomas_factors(OpView o, int n_cells, double *__restrict__ rin
     const double A = o.area[T], Ar = o.area_r[T], G = o.g[T].w;
     double e = 0.0, p = 1.0;
     for (int k = 0; k < n; ++k) {
-        const double m = fma(A, o.vol[k], o.hr[k] * G);
-        const double c = k > 0 ? Ar * o.w[k] : 0.0, cu = k < n - 1 ? Ar * o.w[k + 1] : 0.0;
+        const double m = col_excess(o, T, k, A, G);
+        const double c = k > 0 ? col_coupling(o, T, k, Ar) : 0.0, cu = k < n - 1 ? col_coupling(o, T, k + 1, Ar) : 0.0;
         e = k == 0 ? m : m + c * e / p;
         p = e + cu;
         const double iv = 1.0 / p;
@@ -402,8 +454,9 @@ __global__ void k_thomas_factors(OpView o, int n_cells, double *__restrict__ rin
 // lane k mod 32, the Thomas recurrences y_k = t_k + fb_k y_{k-1} and
 // x_k = y_k + fc_k x_{k+1} as warp-shuffle scans of affine maps, 32 rows at a
 // time (no shared memory, no barrier, no serial chain of n_r FP64 FMAs).  The
-// right-hand side is formed exactly as in k_relax.
-template <int MODE, int R>
+// right-hand side is formed exactly as in k_relax (HF: the horizontal couplings of
+// the stencil stored per unknown, TPMG^full).
+template <int MODE, int R, bool HF>
 __global__ void __launch_bounds__(256)
     k_relax_scan(OpView o, const int *__restrict__ cells, const int4 *__restrict__ tnb, const dbl4 *__restrict__ tg,
                  const double *__restrict__ rinv, const double *__restrict__ fb, const double *__restrict__ fcf,
@@ -418,7 +471,7 @@ __global__ void __launch_bounds__(256)
     if (T < 0) return;
     const int n_r = o.n_r;
     const int4 nb = MODE == PASS_RHS_ONLY ? make_int4(0, 0, 0, 0) : __ldg(&tnb[slot0 + w]);
-    const dbl4 g = MODE == PASS_RHS_ONLY ? dbl4{0.0, 0.0, 0.0, 0.0} : tg[slot0 + w];
+    const dbl4 g = (MODE == PASS_RHS_ONLY || HF) ? dbl4{0.0, 0.0, 0.0, 0.0} : tg[slot0 + w];
     const bool n0 = MODE == PASS_NORMAL || (nb.w & 1), n1 = MODE == PASS_NORMAL || (nb.w & 2),
                n2 = MODE == PASS_NORMAL || (nb.w & 4);
     const size_t base = (size_t)T * n_r;
@@ -435,7 +488,12 @@ __global__ void __launch_bounds__(256)
                 const double v0 = n0 ? u_in[(size_t)nb.x * n_r + k] : 0.0;
                 const double v1 = n1 ? u_in[(size_t)nb.y * n_r + k] : 0.0;
                 const double v2 = n2 ? u_in[(size_t)nb.z * n_r + k] : 0.0;
-                d = fma(__ldg(&o.hr[k]), fma(g.z, v2, fma(g.y, v1, g.x * v0)), d);
+                if (HF) {
+                    const dbl4 c = o.c[i];
+                    d = fma(c.z, v2, fma(c.y, v1, fma(c.x, v0, d)));
+                } else {
+                    d = fma(__ldg(&o.hr[k]), fma(g.z, v2, fma(g.y, v1, g.x * v0)), d);
+                }
             }
             B = d * __ldg(&rinv[i]);
             A = __ldg(&fb[i]);
@@ -490,7 +548,7 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-template <int MODE, bool STAGE, int NT>
+template <int MODE, bool STAGE, int NT, bool HF>
 __global__ void __launch_bounds__(NT, STAGE ? 1 : 6)
     k_relax(OpView o, const int *__restrict__ cells, const int4 *__restrict__ tnb, const dbl4 *__restrict__ tg,
             const double *__restrict__ rinv, const double *__restrict__ fb, const double *__restrict__ fcf,
@@ -524,9 +582,12 @@ __global__ void __launch_bounds__(NT, STAGE ? 1 : 6)
         s_m[q] = __ldg(&fm[(size_t)t * 2 * kRelaxCols + q]);
     }
     __syncthreads();
-    constexpr int U = STAGE ? 8 : 4;   // elements per thread with loads in flight
+    // elements per thread with loads in flight (fewer with the per-unknown stencil,
+    // whose 32-byte rows take registers of their own)
+    constexpr int U = HF ? (STAGE ? 4 : 2) : (STAGE ? 8 : 4);
     for (int e0 = threadIdx.x; e0 < ne; e0 += NT * U) {
         double fv[U], iv[U], v0[U], v1[U], v2[U];
+        dbl4 cs[U];
         int col[U], kk[U];
 #pragma unroll
         for (int q = 0; q < U; ++q) {
@@ -534,6 +595,7 @@ __global__ void __launch_bounds__(NT, STAGE ? 1 : 6)
             col[q] = -1;
             kk[q] = 0;
             fv[q] = iv[q] = v0[q] = v1[q] = v2[q] = 0.0;
+            if (HF) cs[q] = dbl4{0.0, 0.0, 0.0, 0.0};
             if (e < ne) {
                 const int c = e / n_r, k = e - c * n_r;
                 col[q] = c;
@@ -547,6 +609,7 @@ __global__ void __launch_bounds__(NT, STAGE ? 1 : 6)
                         if (MODE == PASS_NORMAL || (nb.w & 1)) v0[q] = u_in[nb.x * n_r + k];
                         if (MODE == PASS_NORMAL || (nb.w & 2)) v1[q] = u_in[nb.y * n_r + k];
                         if (MODE == PASS_NORMAL || (nb.w & 4)) v2[q] = u_in[nb.z * n_r + k];
+                        if (HF) cs[q] = o.c[T * n_r + k];
                     }
                 }
             }
@@ -556,8 +619,12 @@ __global__ void __launch_bounds__(NT, STAGE ? 1 : 6)
             if (col[q] < 0) continue;
             double d = fv[q];
             if (MODE != PASS_RHS_ONLY) {
-                const dbl4 g = s_g[col[q]];
-                d = fma(__ldg(&o.hr[kk[q]]), fma(g.z, v2[q], fma(g.y, v1[q], g.x * v0[q])), d);
+                if (HF) {
+                    d = fma(cs[q].z, v2[q], fma(cs[q].y, v1[q], fma(cs[q].x, v0[q], d)));
+                } else {
+                    const dbl4 g = s_g[col[q]];
+                    d = fma(__ldg(&o.hr[kk[q]]), fma(g.z, v2[q], fma(g.y, v1[q], g.x * v0[q])), d);
+                }
             }
             tile[col[q] * ld + kk[q]] = d * iv[q];
         }
@@ -612,7 +679,7 @@ __global__ void __launch_bounds__(NT, STAGE ? 1 : 6)
 // with the gather and write-back phases of others and keep its four FP64
 // units busy.  One warp per CTA spreads the tasks evenly over the SMs and
 // their sub-partitions.
-template <int MODE>
+template <int MODE, bool HF>
 __global__ void __launch_bounds__(32, 16)
     k_relax_warp(OpView o, const int *__restrict__ cells, const int4 *__restrict__ tnb, const dbl4 *__restrict__ tg,
                  const double *__restrict__ rinv, const double *__restrict__ fb, const double *__restrict__ fcf,
@@ -637,6 +704,7 @@ __global__ void __launch_bounds__(32, 16)
     constexpr int U = 4;
     for (int e0 = lane; e0 < ne; e0 += 32 * U) {
         double fv[U], iv[U], v0[U], v1[U], v2[U];
+        dbl4 cs[U];
         int col[U], kk[U];
 #pragma unroll
         for (int q = 0; q < U; ++q) {
@@ -644,6 +712,7 @@ __global__ void __launch_bounds__(32, 16)
             col[q] = -1;
             kk[q] = 0;
             fv[q] = iv[q] = v0[q] = v1[q] = v2[q] = 0.0;
+            if (HF) cs[q] = dbl4{0.0, 0.0, 0.0, 0.0};
             if (e < ne) {
                 const int c = e / n_r, k = e - c * n_r;
                 col[q] = c;
@@ -657,6 +726,7 @@ __global__ void __launch_bounds__(32, 16)
                         if (MODE == PASS_NORMAL || (nb.w & 1)) v0[q] = u_in[nb.x * n_r + k];
                         if (MODE == PASS_NORMAL || (nb.w & 2)) v1[q] = u_in[nb.y * n_r + k];
                         if (MODE == PASS_NORMAL || (nb.w & 4)) v2[q] = u_in[nb.z * n_r + k];
+                        if (HF) cs[q] = o.c[T * n_r + k];
                     }
                 }
             }
@@ -666,8 +736,12 @@ __global__ void __launch_bounds__(32, 16)
             if (col[q] < 0) continue;
             double d = fv[q];
             if (MODE != PASS_RHS_ONLY) {
-                const dbl4 g = s_g[col[q]];
-                d = fma(__ldg(&o.hr[kk[q]]), fma(g.z, v2[q], fma(g.y, v1[q], g.x * v0[q])), d);
+                if (HF) {
+                    d = fma(cs[q].z, v2[q], fma(cs[q].y, v1[q], fma(cs[q].x, v0[q], d)));
+                } else {
+                    const dbl4 g = s_g[col[q]];
+                    d = fma(__ldg(&o.hr[kk[q]]), fma(g.z, v2[q], fma(g.y, v1[q], g.x * v0[q])), d);
+                }
             }
             tile[col[q] * ld + kk[q]] = d * iv[q];
         }
@@ -952,9 +1026,13 @@ cudaError_t launch_residual(const Launch &L, const LevelDev &lv, const VertDev &
 cudaError_t launch_resid_restrict(const Launch &L, const LevelDev &fine, const LevelDev &coarse, const VertDev &v,
                                   const double *f, const double *u, double *fc)
 {
-    const int Nc = coarse.n * L.n_r;
-    k_resid_restrict<kThreads><<<grid_for(Nc, kThreads, L.sm_count), kThreads, 0, L.s>>>(make_view(fine, v, L.n_r), f,
-                                                                                          u, fc, Nc);
+    const int Nc = coarse.n * L.n_r, grid = grid_for(Nc, kThreads, L.sm_count);
+    const OpView o = make_view(fine, v, L.n_r);
+    switch (stencil_form(fine)) {
+    case CM_FULL: k_resid_restrict<kThreads, CM_FULL><<<grid, kThreads, 0, L.s>>>(o, f, u, fc, Nc); break;
+    case CM_PARTIAL: k_resid_restrict<kThreads, CM_PARTIAL><<<grid, kThreads, 0, L.s>>>(o, f, u, fc, Nc); break;
+    default: k_resid_restrict<kThreads, CM_FAC><<<grid, kThreads, 0, L.s>>>(o, f, u, fc, Nc);
+    }
     return cudaGetLastError();
 }
 
@@ -973,12 +1051,12 @@ cudaError_t launch_twisted_factors(const Launch &L, const LevelDev &lv, const Ve
     return cudaGetLastError();
 }
 
-template <int MODE, bool STAGE, int NT>
+template <int MODE, bool STAGE, int NT, bool HF>
 static cudaError_t relax_launch_t(const Launch &L, const LevelDev &lv, const VertDev &v, int task0, int n_tasks,
                                   double relax, const double *f, const double *u_in, double *u_out, double *u_fine,
                                   size_t smem)
 {
-    auto kern = k_relax<MODE, STAGE, NT>;
+    auto kern = k_relax<MODE, STAGE, NT, HF>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -993,55 +1071,65 @@ static cudaError_t relax_launch_t(const Launch &L, const LevelDev &lv, const Ver
 // at most 32 KB -> one warp per task, otherwise one 128-thread CTA per task.
 // CTA variants stage the multipliers in shared memory by cp.async when they
 // fit; a column too tall for that runs unstaged with 128 threads.
-template <int MODE, int R>
+template <int MODE, int R, bool HF>
 static cudaError_t relax_scan_r(const Launch &L, const LevelDev &lv, const VertDev &v, int task0, int n_tasks,
                                 double relax, const double *f, const double *u_in, double *u_out, double *u_fine)
 {
     const int var = lv.relax_variant < 0 ? RELAX_CTA128 : lv.relax_variant;
     const int wpb = 1 << var;   // CTAs of 1, 2, 4 or 8 warps: the autotuner's variants, same arithmetic
     const int n_slots = n_tasks * kRelaxCols;
-    k_relax_scan<MODE, R><<<(n_slots + wpb - 1) / wpb, 32 * wpb, 0, L.s>>>(
+    k_relax_scan<MODE, R, HF><<<(n_slots + wpb - 1) / wpb, 32 * wpb, 0, L.s>>>(
         make_view(lv, v, L.n_r), lv.task_cells, lv.task_nbr, lv.task_g, lv.rinv1, lv.fb1, lv.fc1, task0 * kRelaxCols,
         n_slots, f, u_in, u_out, u_fine, relax);
     return cudaGetLastError();
 }
 
-template <int MODE>
+template <int MODE, bool HF>
 static cudaError_t relax_scan(const Launch &L, const LevelDev &lv, const VertDev &v, int task0, int n_tasks,
                               double relax, const double *f, const double *u_in, double *u_out, double *u_fine)
 {
     const int n = L.n_r;
-    if (n <= 32) return relax_scan_r<MODE, 1>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
-    if (n <= 64) return relax_scan_r<MODE, 2>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
-    if (n <= 128) return relax_scan_r<MODE, 4>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
-    if (n <= 256) return relax_scan_r<MODE, 8>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
-    if (n <= 512) return relax_scan_r<MODE, 16>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
-    return relax_scan_r<MODE, 32>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
+    if (n <= 32) return relax_scan_r<MODE, 1, HF>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
+    if (n <= 64) return relax_scan_r<MODE, 2, HF>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
+    if (n <= 128) return relax_scan_r<MODE, 4, HF>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
+    if (n <= 256) return relax_scan_r<MODE, 8, HF>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
+    if (n <= 512) return relax_scan_r<MODE, 16, HF>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
+    return relax_scan_r<MODE, 32, HF>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
 }
 
+template <int MODE, bool HF>
+static cudaError_t relax_launch_hf(const Launch &L, const LevelDev &lv, const VertDev &v, int task0, int n_tasks,
+                                   double relax, const double *f, const double *u_in, double *u_out, double *u_fine)
+{
+    if (lv.scan) return relax_scan<MODE, HF>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
+    const size_t tile = (((size_t)kRelaxCols * (L.n_r + 1) + 1) & ~(size_t)1) * sizeof(double);
+    int var = lv.relax_variant;
+    if (var < 0) var = (n_tasks >= 8 * L.sm_count && tile <= 32 * 1024) ? RELAX_WARP : RELAX_CTA128;
+    if (var == RELAX_WARP && tile <= 32 * 1024) {
+        k_relax_warp<MODE, HF><<<n_tasks, 32, tile, L.s>>>(make_view(lv, v, L.n_r), lv.task_cells, lv.task_nbr,
+                                                           lv.task_g, lv.rinv, lv.fb, lv.fc, lv.fm, lv.steps, lv.jmid,
+                                                           task0, f, u_in, u_out, u_fine, relax);
+        return cudaGetLastError();
+    }
+    const size_t staged = tile + (size_t)2 * lv.steps * 32 * sizeof(double);
+    if (staged > 160 * 1024)
+        return relax_launch_t<MODE, false, 128, HF>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine, tile);
+    if (var == RELAX_CTA64)
+        return relax_launch_t<MODE, true, 64, HF>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine, staged);
+    if (var == RELAX_CTA256)
+        return relax_launch_t<MODE, true, 256, HF>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine, staged);
+    return relax_launch_t<MODE, true, 128, HF>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine, staged);
+}
+
+// HF: the level's stencil is stored per unknown (TPMG^full), and the right-hand
+// side's horizontal couplings come from it.
 template <int MODE>
 static cudaError_t relax_launch(const Launch &L, const LevelDev &lv, const VertDev &v, int task0, int n_tasks,
                                 double relax, const double *f, const double *u_in, double *u_out, double *u_fine)
 {
     if (n_tasks <= 0) return cudaSuccess;
-    if (lv.scan) return relax_scan<MODE>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
-    const size_t tile = (((size_t)kRelaxCols * (L.n_r + 1) + 1) & ~(size_t)1) * sizeof(double);
-    int var = lv.relax_variant;
-    if (var < 0) var = (n_tasks >= 8 * L.sm_count && tile <= 32 * 1024) ? RELAX_WARP : RELAX_CTA128;
-    if (var == RELAX_WARP && tile <= 32 * 1024) {
-        k_relax_warp<MODE><<<n_tasks, 32, tile, L.s>>>(make_view(lv, v, L.n_r), lv.task_cells, lv.task_nbr, lv.task_g,
-                                                       lv.rinv, lv.fb, lv.fc, lv.fm, lv.steps, lv.jmid, task0, f,
-                                                       u_in, u_out, u_fine, relax);
-        return cudaGetLastError();
-    }
-    const size_t staged = tile + (size_t)2 * lv.steps * 32 * sizeof(double);
-    if (staged > 160 * 1024)
-        return relax_launch_t<MODE, false, 128>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine, tile);
-    if (var == RELAX_CTA64)
-        return relax_launch_t<MODE, true, 64>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine, staged);
-    if (var == RELAX_CTA256)
-        return relax_launch_t<MODE, true, 256>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine, staged);
-    return relax_launch_t<MODE, true, 128>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine, staged);
+    if (lv.vc) return relax_launch_hf<MODE, true>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
+    return relax_launch_hf<MODE, false>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
 }
 
 cudaError_t launch_thomas_factors(const Launch &L, const LevelDev &lv, const VertDev &v)

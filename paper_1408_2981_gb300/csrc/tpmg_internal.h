@@ -90,6 +90,10 @@ struct LevelDev {
     // per unknown, cfull [n][n_r] {alphaS_hat e = 0, 1, 2, beta_hat}, cvr [n][n_r+1] alphar_hat
     dbl4 *cfull = nullptr;
     double *cvr = nullptr;
+    // the FP64 V-cycle's stencil stored per unknown (coeff_storage FULL: vc and vcr;
+    // PARTIAL: vcr only), the same layout as cfull / cvr
+    dbl4 *vc = nullptr;
+    double *vcr = nullptr;
     float *iarea32 = nullptr;     // [n] 1 / |T| (network features of the learned form)
     float4 *wnb32 = nullptr;      // [n] {g0, g1, g2} / (g0 + g1 + g2), 0
     int *task_cells = nullptr;    // [n_tasks][16] cell ids, -1 = padding
