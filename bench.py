@@ -18,7 +18,7 @@ graph launch), 1280x16 (the small parity case), 81920x64-mixed
 FP64), 327680x128-mixed (refinement 7 x 128 levels, 41.9M unknowns, mixed
 precision), 327680x128 (the same grid in FP64) and 327680x128-learned (the
 learned form).  Two studies print the paper's measurements instead of a
-throughput: nr-sweep (time per iteration against n_r, Sec. 4.3) and
+throughput: nr-sweep (time per iteration against n_r, Sec. 5.1) and
 balanced-flow (TPMG^fac / TPMG^partial / TPMG^full against the buoyancy
 frequency, Sec. 5).
 
@@ -88,7 +88,7 @@ WORKLOADS = {
              "||r|| <= 1e-5 ||f|| on held-out smooth right-hand sides"),
     "nr-sweep": dict(
         study="nr_sweep", refinement=6, n_r=(16, 32, 64, 128, 256), iters=8, seed=2981010,
-        text="time per PCG iteration against the number of vertical levels (Sec. 4.3, eq. nzDependency: "
+        text="time per PCG iteration against the number of vertical levels (Sec. 5.1, eq. nzDependency: "
              "t_iter = C + q n_r): icosahedral refinement 6 (81920 columns) x n_r in {16, 32, 64, 128, 256} "
              "graded 1.05 over 10 km, omega^2/h^2=80, RHS uniform[-1,1], 6 MG levels, nu 2/2/1, 8 iterations per "
              "solve (rtol 0); V-cycle TPMG^fac in FP64, TPMG^full in FP64, TPMG^full in mixed precision"),
@@ -823,7 +823,7 @@ def study_line(args, wl, metric, value, unit, higher, dtype, extra, clk, launche
 
 
 def run_nr_sweep(args, wl):
-    """Sec. 4.3, eq. nzDependency: time per iteration against n_r, fitted by least
+    """Sec. 5.1, eq. nzDependency: time per iteration against n_r, fitted by least
     squares to t = C + q n_r; C / t is the share of the per-column work that does
     not grow with n_r (indirect addressing, launches, the coarse levels)."""
     import torch
@@ -869,7 +869,7 @@ def run_nr_sweep(args, wl):
                       "overhead_at_128": c / (c + 128 * q), "overhead_at_256": c / (c + 256 * q)}
     if rank == 0:
         study_line(args, wl, "share of the time per iteration that does not grow with n_r, at n_r = 128 "
-                   "(Sec. 4.3: C / (C + 128 q), TPMG^fac FP64)", fits["TPMG^fac FP64"]["overhead_at_128"],
+                   "(Sec. 5.1: C / (C + 128 q), TPMG^fac FP64)", fits["TPMG^fac FP64"]["overhead_at_128"],
                    "fraction", False, "f64", {"points": points, "fit": fits, "iters_per_solve": K}, clk, launches,
                    world)
     return 0

@@ -68,7 +68,7 @@ enum { TPMG_SMOOTH_MCSOR = 0,   /* multicolour block-SOR: forward colours before
  *   FULL: stored per unknown (TPMG^full) -- in FP64 for the FP64 V-cycle (40 bytes
  *     per unknown and level), in BF16 for the mixed-precision V-cycle;
  *   PARTIAL (FP64 only): alpha_r stored per face and column, beta and alpha_S
- *     factorised (the partial factorisation TPMG^partial of Sec. 6; 8 bytes per
+ *     factorised (the partial factorisation TPMG^partial of Sec. 5.3; 8 bytes per
  *     unknown and level).
  * Until tpmg_set_outer_profiles gives general profiles, FULL and PARTIAL store the
  * factorised profiles' coefficients, so all three are the same preconditioner up to
@@ -172,7 +172,7 @@ tpmg_status tpmg_setup_profiles(const tpmg_params *p, const tpmg_profiles *prof,
  * factorised operator.  From then on the outer iteration -- tpmg_solve, tpmg_apply_operator,
  * the learned and batched solves -- applies this operator with per-unknown FP64
  * coefficients (edges: the mean of the two cells' alpha_S).  The V-cycle follows its
- * coefficient storage (Sec. 3.4, Sec. 5, Sec. 6):
+ * coefficient storage (Sec. 3.2.2, Sec. 5, Sec. 5.3):
  *   FACTORISED keeps the factorised profiles given to tpmg_setup_profiles (TPMG^fac
  *     preconditioning the full operator);
  *   FULL (FP64 or mixed precision) adopts all three general profiles (TPMG^full);

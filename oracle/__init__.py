@@ -301,7 +301,7 @@ class Oracle:
     def set_vcycle_partial(self, on: bool = True):
         """The V-cycle's operators take alpha_r from the general profiles of
         set_outer_profiles and beta, alpha_S from the factorised ones (TPMG^partial,
-        Sec. 6); off: the factorised profiles throughout (TPMG^fac)."""
+        Sec. 5.3); off: the factorised profiles throughout (TPMG^fac)."""
         self._lib.oracle_set_vcycle_partial(self._h, 1 if on else 0)
 
     def apply_outer(self, x) -> np.ndarray:

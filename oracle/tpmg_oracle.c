@@ -392,7 +392,7 @@ typedef struct {
     /* the same general profiles on every refinement level (coarse: area-weighted means
      * over the 4 children, per vertical index) and the switch vc_full that makes the
      * V-cycle's operators use them: 0 none (TPMG^fac, the factorised profiles), 1 all
-     * three (TPMG^full), 2 alpha_r only, beta and alpha_S factorised (TPMG^partial, Sec. 6) */
+     * three (TPMG^full), 2 alpha_r only, beta and alpha_S factorised (TPMG^partial, Sec. 5.3) */
     double **pl_beta, **pl_ar, **pl_aS;
     int vc_full;
     /* multigrid work arrays per multigrid level (0 = coarsest)               */
@@ -796,7 +796,7 @@ void oracle_set_outer_profiles(void *h, const double *beta, const double *ar, co
 void oracle_set_vcycle_full(void *h, int on) { ((octx *)h)->vc_full = on != 0; }
 
 /* on != 0: the V-cycle's operators take alpha_r from the general profiles and beta,
- * alpha_S from the factorised ones (partial factorisation TPMG^partial, Sec. 6) */
+ * alpha_S from the factorised ones (partial factorisation TPMG^partial, Sec. 5.3) */
 void oracle_set_vcycle_partial(void *h, int on) { ((octx *)h)->vc_full = on != 0 ? 2 : 0; }
 
 /* y = A x with the problem's operator (oracle_apply gives the V-cycle's level operators). */
@@ -1214,7 +1214,7 @@ done:
 }
 
 /* Preconditioned Richardson iteration u <- u + B (f - A u), n_iter steps
- * (Sec. 3.3).  hist (nullable, n_iter+1) receives ||f - A u_k||_2. */
+ * (Sec. 3.2.2).  hist (nullable, n_iter+1) receives ||f - A u_k||_2. */
 /* BiCGStab (van der Vorst 1992) preconditioned from the right with one V-cycle
  * per preconditioner application (the paper's Sec. 5 alternative to
  * Richardson): with r^ = r_0,

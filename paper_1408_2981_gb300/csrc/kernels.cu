@@ -4,10 +4,10 @@
 // column of a horizontal cell is stored contiguously).  Per cell: int4
 // {nbr0, nbr1, nbr2, mask}, mask bit e set when neighbour e has a smaller
 // colour; double4 {g0, g1, g2, g0+g1+g2}; area |T|.  Vertical factors are
-// shared by all levels (no vertical coarsening, Sec. 3.3).
+// shared by all levels (no vertical coarsening, Sec. 3).
 //
 // The operator in the flux form of Appendix A (constant profiles, factorised
-// storage: per-level vertical vectors times per-cell scalars, Sec. 3.2):
+// storage: per-level vertical vectors times per-cell scalars, Sec. 3.1):
 //   (A x)_{T,k} = |T| (v_k x_k + w_k (x_k - x_{k-1}) + w_{k+1} (x_k - x_{k+1}))
 //               + hr_k sum_e g_e (x_k - x_{T_e,k}),
 // w_k = omega^2 sigma_k 2 r_k^2/(r_{k+1}-r_{k-1}), hr_k = omega^2 (r_{k+1}-r_k).

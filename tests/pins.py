@@ -150,7 +150,7 @@ SMALL_CASES = [
 
 def _vertical_matrix(o):
     """The vertical factor K = diag(v) + omega^2 V^r of the Kronecker form
-    (Sec. 3.3, A = (omega^2 A^r + B^r) (x) M^S + omega^2 M^r (x) A^S), from the
+    (Sec. 3.2.1, A = (omega^2 A^r + B^r) (x) M^S + omega^2 M^r (x) A^S), from the
     exported vertical grid: face coupling 2 r_k^2 / (r_{k+1} - r_{k-1}) (eq. VerticalDiffusion)."""
     v = o.vertical()
     r, vol = v["r"], v["vol"]
@@ -188,7 +188,7 @@ def pin_constants_in_kernel(ns):
 
 def pin_symmetric_spd(ns):
     """With xi = 0 and constant profiles the operator is symmetric positive
-    definite (Sec. 3.3); the two-point fluxes also make it an M-matrix: positive
+    definite (Sec. 3.2.1); the two-point fluxes also make it an M-matrix: positive
     diagonal, non-positive off-diagonals, strict diagonal dominance (beta_hat > 0)."""
     for kw in SMALL_CASES:
         o = ns.Oracle(**kw)
@@ -202,7 +202,7 @@ def pin_symmetric_spd(ns):
 
 
 def pin_kronecker(ns):
-    """Sec. 3.3: for factorising profiles A = diag|T| (x) (diag v + omega^2 V^r)
+    """Sec. 3.2.1: for factorising profiles A = diag|T| (x) (diag v + omega^2 V^r)
     + omega^2 L^S (x) diag(dr), assembled here from small matrices and compared
     entry by entry with the matrix-free operator."""
     for kw in SMALL_CASES:
@@ -447,7 +447,7 @@ def pin_preconditioner_symmetric(ns):
 
 
 def pin_invariant_subspaces(ns):
-    """Sec. 3.3 (reduction to two dimensions): with (omega^2 A^r + B^r) e_j =
+    """Sec. 3.2.1 (reduction to two dimensions): with (omega^2 A^r + B^r) e_j =
     lambda_j M^r e_j, A maps e_j (x) V^S into M^r e_j (x) V^S, the block smoother
     keeps e_j (x) V^S invariant, and the V-cycle maps M^r e_j (x) V^S into
     e_j (x) V^S; components along the other e_i stay at rounding level."""
@@ -664,7 +664,7 @@ def pin_outer_operator(ns):
     happen to factorise it equals the V-cycle's operator with the factors (two
     independent statements of the same coefficients); it is symmetric positive
     definite; and PCG with the factorised V-cycle as preconditioner reaches its dense
-    solution (Sec. 3.4: TPMG preconditioning a non-factorising operator)."""
+    solution (Sec. 3.2.2: TPMG preconditioning a non-factorising operator)."""
     kw = dict(refinement=2, n_levels=2, n_r=6, grading=1.1, H=0.1, courant_c=8.0)
     o = ns.Oracle(**kw)
     n = o.level_cells(1)
@@ -705,7 +705,7 @@ def pin_outer_operator(ns):
 
 
 def pin_partial_profiles(ns):
-    """Partial factorisation TPMG^partial (Sec. 6): the V-cycle's operators take alpha_r
+    """Partial factorisation TPMG^partial (Sec. 5.3): the V-cycle's operators take alpha_r
     from the general profiles and beta, alpha_S from the factorised ones.  On the finest
     level every vertical coupling is the factorised one times alpha_r / (alpha_r^S
     alpha_r^r) and nothing else changes; where only alpha_r departs from a factorisation
@@ -778,7 +778,7 @@ def convergence_factor(o, n_iter: int = 8, seed: int = 77) -> float:
 
 
 def pin_robust_convergence(ns):
-    """Theorem (Sec. 3.3): the TPMG V-cycle factor is bounded away from 1
+    """Theorem (Sec. 3.2.1): the TPMG V-cycle factor is bounded away from 1
     independently of h and of the vertical aspect ratio.  Measured over grids and
     anisotropies: every factor < 0.5 and their spread (max/min) <= 2."""
     rhos = []

@@ -141,7 +141,7 @@ def test_full_operator_parity():
 @pytest.mark.parametrize("outer", [binding.TPMG_OUTER_CG, binding.TPMG_OUTER_BICGSTAB])
 def test_tpmg_fac_preconditions_the_full_operator(outer):
     """FP64: the V-cycle of the factorised approximation preconditions the full operator
-    (Sec. 3.4); the solve matches the oracle's."""
+    (Sec. 3.2.2); the solve matches the oracle's."""
     s, o, _ = flow_pair(0.025, outer=outer)
     f = inputs.uniform_pm1(inputs.SEED_UNIFORM_SMALL + 61, s.N)
     u = torch.zeros(s.N, dtype=torch.float64, device="cuda")

@@ -1,6 +1,6 @@
 """The FP64 V-cycle with its stencil stored per unknown: coeff_storage FULL (TPMG^full)
 and PARTIAL (alpha_r per face and column, beta and alpha_S factorised: TPMG^partial),
-Sec. 4.2 and Sec. 6, against the oracle's V-cycle on the same profiles, through the
+Sec. 4.2 and Sec. 5.3, against the oracle's V-cycle on the same profiles, through the
 C ABI (needs a GPU).  scan_max_cells 0 relaxes every level with the twisted
 factorisation, 5120 every level of these grids with the warp-scan kernel."""
 import math
