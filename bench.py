@@ -132,26 +132,31 @@ PER_UNIT = {
     # (12 B) are this design's extra traffic; ncu's DRAM counters include them.
     1: dict(OUTER, relax=(20.0, 25.0), restrict=(20.0, 19.0), prolong=(1.0, 10.0)),
 }
-# DRAM bytes per launch of a kernel class from an ncu capture (profiles/), valid
-# while kernels.cu is the file that was profiled (sha256 prefix)
-TRAFFIC = {"relax": {"bytes_per_launch": 18.27e6, "kernels_sha256": "2ee09730ea09aba5",
-                     "source": "profiles/relax_dram_81920x64.md", "workload": "81920x64"}}
+# DRAM bytes per launch of a kernel class on a workload from an ncu capture
+# (profiles/), valid while the kernel source is the file that was profiled
+# (sha256 prefix)
+TRAFFIC = {
+    ("relax", "81920x64"): {"bytes_per_launch": 18.27e6, "file": "kernels.cu", "sha256": "c278fc30b275b9d9",
+                            "source": "profiles/relax_dram_81920x64.md"},
+    ("relax", "327680x128-mixed"): {"bytes_per_launch": 121.67e6, "file": "kernels32.cu", "sha256": "bd909699a991d52a",
+                                    "source": "profiles/relax32_dram_327680x128.md"},
+}
 SM_COUNT_GB300 = 152
 FP64_FMA_PER_CLK_PER_SM = 2     # GB300: 1.25 TFLOP/s dense FP64 at 2.07 GHz over 152 SMs
 ORACLE_FULL_SOLVE_MAX_UNKNOWNS = 6_000_000   # larger workloads: the CPU baseline times one iteration
 
 
-def kernels_sha256() -> str:
+def source_sha256(name: str) -> str:
     import hashlib
 
-    with open(os.path.join(ROOT, "paper_1408_2981_gb300", "csrc", "kernels.cu"), "rb") as fh:
+    with open(os.path.join(ROOT, "paper_1408_2981_gb300", "csrc", name), "rb") as fh:
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
 def traffic_of(kernel: str, workload: str):
-    """ncu DRAM bytes per launch, or None once the kernels changed after the capture."""
-    t = TRAFFIC.get(kernel)
-    if t and t["workload"] == workload and t["kernels_sha256"] == kernels_sha256():
+    """ncu DRAM bytes per launch, or None once the kernel source changed after the capture."""
+    t = TRAFFIC.get((kernel, workload))
+    if t and t["sha256"] == source_sha256(t["file"]):
         return t["bytes_per_launch"]
     return None
 
