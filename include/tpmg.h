@@ -142,7 +142,17 @@ tpmg_status tpmg_default_params(tpmg_params *p);
  *   beta_s, alphar_s, alphaS_s   [20 * 4^refinement] horizontal factors on the cells of
  *                                the finest level, in the library's cell order
  * Coarse multigrid levels use the area-weighted mean of each cell's 4 children; an
- * edge uses the mean of its two cells' alphaS_s, so the operator stays symmetric. */
+ * edge uses the mean of its two cells' alphaS_s, so the operator stays symmetric.
+ *   xi_r [n_r + 1], xi_s [20 * 4^refinement]  vertical advection xi_r(r, x) = xi_r^r(r)
+ *                                xi_r^S(x) at the faces (finite, any sign); both NULL =
+ *                                no advection, one NULL = that factor 1.
+ * Vertical advection (the -omega^2 xi_r d_r u term of eq. HelmholtzVector, centred as in
+ * Appendix A) makes the operator non-symmetric: row k of a column couples to the row
+ * below with down_k = alphar_hat_k - dr_k X_k and to the row above with up_k =
+ * alphar_hat_{k+1} + dr_k X_{k+1}, X_face = omega^2 |T| r_face^2 / (r_{face+1} -
+ * r_{face-1}) xi_face.  tpmg_setup rejects profiles for which a coupling of a V-cycle
+ * level is negative (the column blocks must stay M-matrices for the line smoother's
+ * elimination), and tpmg_solve then needs params.outer Richardson or BiCGStab. */
 typedef struct {
     const double *beta_r;
     const double *alphaS_r;
@@ -150,6 +160,8 @@ typedef struct {
     const double *beta_s;
     const double *alphar_s;
     const double *alphaS_s;
+    const double *xi_r;
+    const double *xi_s;
 } tpmg_profiles;
 
 /* Builds the grid hierarchy, geometry, colouring and coefficients on the host
@@ -168,8 +180,9 @@ tpmg_status tpmg_setup_profiles(const tpmg_params *p, const tpmg_profiles *prof,
 /* The problem's operator with general (non-factorising) profiles on the finest level
  * (Sec. 2, eq. profiles; the TPMG^full storage of Sec. 4.2 for the operator only):
  * h_beta, h_alphaS [n_cells * n_r] at the cell centres and h_alphar [n_cells * (n_r + 1)]
- * at the faces (cell-major), host arrays, positive and finite; three NULLs restore the
- * factorised operator.  From then on the outer iteration -- tpmg_solve, tpmg_apply_operator,
+ * at the faces (cell-major), host arrays, positive and finite; h_xi [n_cells * (n_r + 1)]
+ * the vertical advection at the faces (finite), or NULL for none; three NULLs restore the
+ * factorised operator (h_xi is then ignored).  From then on the outer iteration -- tpmg_solve, tpmg_apply_operator,
  * the learned and batched solves -- applies this operator with per-unknown FP64
  * coefficients (edges: the mean of the two cells' alpha_S).  The V-cycle follows its
  * coefficient storage (Sec. 3.2.2, Sec. 5, Sec. 5.3):
@@ -180,7 +193,7 @@ tpmg_status tpmg_setup_profiles(const tpmg_params *p, const tpmg_profiles *prof,
  * Each coarse level takes the area-weighted mean of a general profile over the 4
  * children per vertical index.  Synchronous.  Errors: INVALID_ARG, OOM, CUDA. */
 tpmg_status tpmg_set_outer_profiles(tpmg_ctx *ctx, const double *h_beta, const double *h_alphar,
-                                    const double *h_alphaS);
+                                    const double *h_alphaS, const double *h_xi);
 
 /* y = A x on the finest level (eq. ColumnEquation: matrix-free finite-volume
  * operator).  d_x, d_y: device, n_cells*n_r doubles, must not overlap.
@@ -234,6 +247,8 @@ tpmg_status tpmg_vcycle_noalloc(tpmg_ctx *ctx, const double *d_r, double *d_z);
  * for k = 0..*iters.  Synchronises the context stream before returning.
  * Returns OK, NOT_CONVERGED (iters = max_iter), BREAKDOWN (p.Ap <= 0 or a
  * non-finite norm; the solution holds the last finite iterate), INVALID_ARG, CUDA.
+ * With vertical advection (xi in the profiles) the operator is not symmetric and CG
+ * does not apply: INVALID_ARG unless params.outer is Richardson or BiCGStab.
  * With graphs on (and no kernel class being timed) the whole solve is one graph
  * launch with the loop on the device; otherwise the host drives the loop.
  * Both run the same kernels in the same order. */
@@ -257,7 +272,8 @@ tpmg_status tpmg_solve_host(tpmg_ctx *ctx, const double *h_f, double *h_u, doubl
  * pointers are baked into the batch, which stays valid while the contexts and
  * vectors live.  A context may belong to one batch and must not run another
  * solve while its batch runs.  max_iter < 4096.
- * Errors: INVALID_ARG (NULL, repeated context, other device), OOM, CUDA. */
+ * Errors: INVALID_ARG (NULL, repeated context, other device, a context with
+ * vertical advection), OOM, CUDA. */
 typedef struct tpmg_batch tpmg_batch;
 tpmg_status tpmg_batch_create(tpmg_ctx *const *ctxs, int n, const double *const *d_f, double *const *d_u,
                               double rtol, int max_iter, tpmg_batch **out);

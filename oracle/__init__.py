@@ -77,9 +77,9 @@ def _load(path: str | None = None):
         lib.oracle_fcg.argtypes = [_P, _P, _P, _D, _I, _P, _P, _P, _P]
         lib.oracle_set_vcycle_bf16.argtypes = [_P, _I]
         lib.oracle_set_vcycle_bf16.restype = None
-        lib.oracle_set_profiles.argtypes = [_P, _P, _P, _P, _P, _P, _P]
+        lib.oracle_set_profiles.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _P]
         lib.oracle_set_profiles.restype = None
-        lib.oracle_set_outer_profiles.argtypes = [_P, _P, _P, _P]
+        lib.oracle_set_outer_profiles.argtypes = [_P, _P, _P, _P, _P]
         lib.oracle_set_outer_profiles.restype = None
         lib.oracle_apply_outer.argtypes = [_P, _P, _P]
         lib.oracle_set_vcycle_full.argtypes = [_P, _I]
@@ -94,7 +94,9 @@ def _load(path: str | None = None):
         lib.oracle_bicgstab.argtypes = [_P, _P, _P, _D, _I, _P, _P, _P]
         lib.oracle_thomas.argtypes = [_I, _P, _P, _P, _P, _P]
         lib.oracle_column_solve.argtypes = [_I, _P, _P, _P, _P]
+        lib.oracle_column_solve2.argtypes = [_I, _P, _P, _P, _P, _P]
         lib.oracle_column_couplings.argtypes = [_P, _I, _P, _P]
+        lib.oracle_column_couplings2.argtypes = [_P, _I, _P, _P, _P]
         _libs[key] = lib
         if path is None:
             _lib = lib
@@ -140,6 +142,17 @@ def column_solve(c, m, d, lib_path: str | None = None) -> np.ndarray:
     x = np.empty(n)
     if _load(lib_path).oracle_column_solve(n, _ptr(c), _ptr(m), _ptr(d), _ptr(x)) != 0:
         raise ValueError("oracle_column_solve failed")
+    return x
+
+
+def column_solve2(cd, cu, m, d, lib_path: str | None = None) -> np.ndarray:
+    """Solve the non-symmetric column block tridiag(-cd, m + cd + cu, -cu): couplings
+    of each row to the row below, cd[1..n-1], and above, cu[0..n-2]."""
+    cd, cu, m, d = (_f64(v) for v in (cd, cu, m, d))
+    n = d.shape[0]
+    x = np.empty(n)
+    if _load(lib_path).oracle_column_solve2(n, _ptr(cd), _ptr(cu), _ptr(m), _ptr(d), _ptr(x)) != 0:
+        raise ValueError("oracle_column_solve2 failed")
     return x
 
 
@@ -241,6 +254,15 @@ class Oracle:
         self._lib.oracle_column_couplings(self._h, level, _ptr(c), _ptr(m))
         return c, m
 
+    def column_couplings2(self, level: int | None = None):
+        """(cd, cu, m) [n_cells, n_r]: each row's coupling to the row below and above
+        (they differ with vertical advection) and the diagonal excess."""
+        level = self.n_levels - 1 if level is None else level
+        n = self.level_cells(level)
+        cd, cu, m = (np.empty((n, self.n_r)) for _ in range(3))
+        self._lib.oracle_column_couplings2(self._h, level, _ptr(cd), _ptr(cu), _ptr(m))
+        return cd, cu, m
+
     def smooth(self, f, u, sweeps: int = 1, direction: int = 1, level: int | None = None) -> np.ndarray:
         level = self.n_levels - 1 if level is None else level
         f = _f64(f).reshape(-1)
@@ -273,24 +295,28 @@ class Oracle:
         FP64 arithmetic) in vcycle(), pcg() and fcg()."""
         self._lib.oracle_set_vcycle_bf16(self._h, 1 if on else 0)
 
-    def set_profiles(self, beta_r=None, alphaS_r=None, alphar_r=None, beta_s=None, alphar_s=None, alphaS_s=None):
+    def set_profiles(self, beta_r=None, alphaS_r=None, alphar_r=None, beta_s=None, alphar_s=None, alphaS_s=None,
+                     xi_r=None, xi_s=None):
         """Factorised profiles alpha(r, x) = alpha^r(r) alpha^S(x) (None = 1): vertical
         factors of beta and alpha_S at the cell centres [n_r], of alpha_r at the faces
-        [n_r + 1]; horizontal factors on the finest level's cells."""
+        [n_r + 1]; horizontal factors on the finest level's cells.  The vertical advection
+        xi_r = xi^r(r) xi^S(x) (faces, cells) is absent when both factors are None."""
         arrs = [None if a is None else _f64(a).reshape(-1).copy() for a in
-                (beta_r, alphaS_r, alphar_r, beta_s, alphar_s, alphaS_s)]
+                (beta_r, alphaS_r, alphar_r, beta_s, alphar_s, alphaS_s, xi_r, xi_s)]
         self._profiles = arrs
         self._lib.oracle_set_profiles(self._h, *(_ptr(a) for a in arrs))
 
-    def set_outer_profiles(self, beta=None, alphar=None, alphaS=None):
+    def set_outer_profiles(self, beta=None, alphar=None, alphaS=None, xi=None):
         """General profiles of the problem's operator on the finest level (beta,
-        alpha_S [n_cells, n_r], alpha_r [n_cells, n_r + 1]; None clears): the outer
-        iterations apply this operator, the V-cycle keeps its own profiles."""
+        alpha_S [n_cells, n_r], alpha_r and the vertical advection xi [n_cells, n_r + 1];
+        None clears; xi None = no advection): the outer iterations apply this operator,
+        the V-cycle keeps its own profiles unless set_vcycle_full / _partial."""
         if beta is None:
             self._outer = None
-            self._lib.oracle_set_outer_profiles(self._h, None, None, None)
+            self._lib.oracle_set_outer_profiles(self._h, None, None, None, None)
             return
         self._outer = [_f64(a).reshape(-1).copy() for a in (beta, alphar, alphaS)]
+        self._outer.append(None if xi is None else _f64(xi).reshape(-1).copy())
         self._lib.oracle_set_outer_profiles(self._h, *(_ptr(a) for a in self._outer))
 
     def set_vcycle_full(self, on: bool = True):

@@ -384,16 +384,22 @@ typedef struct {
      * coarser levels the area-weighted mean over the 4 children); NULL = 1 */
     double *pr_beta, *pr_aS, *pr_ar;
     double **ps_beta, **ps_ar, **ps_aS;
+    /* vertical advection xi_r (Sec. 2, eq. HelmholtzVector; Appendix A) in factorised
+     * form: vertical factor at the faces [n_r+1], horizontal per refinement level; both
+     * NULL = no advection (a NULL factor next to a given one counts as 1) */
+    double *pr_xi;
+    double **ps_xi;
     /* general (non-factorising) profiles of the problem's operator on the finest level:
      * beta, alpha_S per unknown [n_cells][n_r], alpha_r per face [n_cells][n_r + 1];
      * NULL = the V-cycle's operator.  The outer iterations apply this operator; the
      * V-cycle keeps its (factorised) profiles: TPMG preconditioning the full operator. */
     double *pf_beta, *pf_ar, *pf_aS;
+    double *pf_xi;        /* general xi_r per face [n_cells][n_r + 1], or NULL (none)   */
     /* the same general profiles on every refinement level (coarse: area-weighted means
      * over the 4 children, per vertical index) and the switch vc_full that makes the
      * V-cycle's operators use them: 0 none (TPMG^fac, the factorised profiles), 1 all
      * three (TPMG^full), 2 alpha_r only, beta and alpha_S factorised (TPMG^partial, Sec. 5.3) */
-    double **pl_beta, **pl_ar, **pl_aS;
+    double **pl_beta, **pl_ar, **pl_aS, **pl_xi;
     int vc_full;
     /* multigrid work arrays per multigrid level (0 = coarsest)               */
     double **mg_f, **mg_u, **mg_r;
@@ -458,6 +464,38 @@ static double alphar_hat(const octx *o, const ogrid *G, int T, int face)
     return coeff(o, o->omega2 * G->area[T] * o->arv[face] * vfac(o->pr_ar, face) * hfac(o, o->ps_ar, G, T));
 }
 
+/* Vertical advection of face `face` (Appendix A, the cell integral of xi_r d_r u):
+ * X_{T,face} = omega^2 sigma_face |T| r_face^2 / (r_{face+1} - r_{face-1}) xi_{T,face},
+ * half the alphar_hat factor; row k takes it times its own thickness r_{k+1} - r_k
+ * (Reading C24).  Zero without advection. */
+static int has_xi(const octx *o) { return full_now(o) ? o->pl_xi != NULL : (o->pr_xi || o->ps_xi); }
+static double xi_hat(const octx *o, const ogrid *G, int T, int face)
+{
+    if (full_now(o)) {
+        if (!o->pl_xi) return 0.0;
+        return coeff(o, o->omega2 * G->area[T] * (0.5 * o->arv[face]) * o->pl_xi[G - o->grid][(size_t)T * (o->n_r + 1) + face]);
+    }
+    if (!o->pr_xi && !o->ps_xi) return 0.0;
+    return coeff(o, o->omega2 * G->area[T] * (0.5 * o->arv[face]) * vfac(o->pr_xi, face) * hfac(o, o->ps_xi, G, T));
+}
+
+/* The vertical couplings of row (T, k): diffusion through face k (resp. k+1) minus
+ * (plus) the centred advection across it,
+ *   down_k = alphar_hat_{T,k} - dr_k X_{T,k},   up_k = alphar_hat_{T,k+1} + dr_k X_{T,k+1},
+ * so that the row's vertical part is down_k (u_k - u_{k-1}) + up_k (u_k - u_{k+1})
+ * (eq. TridiagonalNonFactorising: b = -alphar_hat - xi_hat, c = -alphar_hat + xi_hat).
+ * Without advection both are the symmetric alphar_hat of the face. */
+static double vert_down(const octx *o, const ogrid *G, int T, int k)
+{
+    const double a = alphar_hat(o, G, T, k);
+    return has_xi(o) ? a - o->dr[k] * xi_hat(o, G, T, k) : a;
+}
+static double vert_up(const octx *o, const ogrid *G, int T, int k)
+{
+    const double a = alphar_hat(o, G, T, k + 1);
+    return has_xi(o) ? a + o->dr[k] * xi_hat(o, G, T, k + 1) : a;
+}
+
 /* Column T of the operator as a tridiagonal matrix (eq. ColumnEquation,
  * TridiagonalSystem; Reading C2): off-diagonals -alphar_hat_{T,k} (face k couples
  * levels k-1 and k), d_{TT',k} = -alphaS_hat_{TT',k}, and diagonal a_{T,k} =
@@ -467,7 +505,7 @@ static void column_matrix(const octx *o, const ogrid *G, int T, double *sub, dou
 {
     int k, e, n = o->n_r;
     for (k = 0; k < n; ++k) {
-        double lo = alphar_hat(o, G, T, k), up = alphar_hat(o, G, T, k + 1), hs = 0.0;
+        double lo = vert_down(o, G, T, k), up = vert_up(o, G, T, k), hs = 0.0;
         for (e = 0; e < 3; ++e) hs += alphaS_hat(o, G, T, e, k);
         sub[k] = -lo;
         sup[k] = -up;
@@ -489,8 +527,8 @@ static double apply_row(const octx *o, const ogrid *G, const double *u, int T, i
     int n = o->n_r, e;
     size_t i = (size_t)T * n + k;
     double s = beta_hat(o, G, T, k) * u[i];
-    if (k > 0) s += alphar_hat(o, G, T, k) * (u[i] - u[i - 1]);
-    if (k < n - 1) s += alphar_hat(o, G, T, k + 1) * (u[i] - u[i + 1]);
+    if (k > 0) s += vert_down(o, G, T, k) * (u[i] - u[i - 1]);
+    if (k < n - 1) s += vert_up(o, G, T, k) * (u[i] - u[i + 1]);
     for (e = 0; e < 3; ++e) s += alphaS_hat(o, G, T, e, k) * (u[i] - u[(size_t)G->nbr[3 * T + e] * n + k]);
     return s;
 }
@@ -512,8 +550,14 @@ static double apply_row_full(const octx *o, const ogrid *G, const double *u, int
     int n = o->n_r, e;
     size_t i = (size_t)T * n + k, fa = (size_t)T * (n + 1) + k;
     double s = G->area[T] * o->vol[k] * o->pf_beta[i] * u[i];
-    if (k > 0) s += o->omega2 * G->area[T] * o->arv[k] * o->pf_ar[fa] * (u[i] - u[i - 1]);
-    if (k < n - 1) s += o->omega2 * G->area[T] * o->arv[k + 1] * o->pf_ar[fa + 1] * (u[i] - u[i + 1]);
+    double down = o->omega2 * G->area[T] * o->arv[k] * o->pf_ar[fa];
+    double up = o->omega2 * G->area[T] * o->arv[k + 1] * o->pf_ar[fa + 1];
+    if (o->pf_xi) {   /* centred vertical advection, as in vert_down / vert_up */
+        down -= o->dr[k] * (o->omega2 * G->area[T] * (0.5 * o->arv[k]) * o->pf_xi[fa]);
+        up += o->dr[k] * (o->omega2 * G->area[T] * (0.5 * o->arv[k + 1]) * o->pf_xi[fa + 1]);
+    }
+    if (k > 0) s += down * (u[i] - u[i - 1]);
+    if (k < n - 1) s += up * (u[i] - u[i + 1]);
     for (e = 0; e < 3; ++e) {
         const int Tn = G->nbr[3 * T + e];
         const double edge = 0.5 * (o->pf_aS[i] + o->pf_aS[(size_t)Tn * n + k]);
@@ -573,7 +617,28 @@ int oracle_thomas(int n, const double *a, const double *b, const double *c, cons
  * c_k^2 / pivot_{k-1} = c_k - c_k e_{k-1} / pivot_{k-1} from the diagonal.)
  * The textbook pivot b_k - c_k^2 / pivot_{k-1} cancels catastrophically when the
  * couplings dwarf the mass term, as they do in a thin shell. */
+int oracle_column_solve2(int n, const double *cd, const double *cu, const double *m, const double *d, double *x);
+
 int oracle_column_solve(int n, const double *c, const double *m, const double *d, double *x)
+{
+    double *cu;
+    int k, st;
+    if (n < 1) return -1;
+    cu = (double *)malloc((size_t)n * sizeof(double));
+    if (!cu) return -2;
+    for (k = 0; k < n; ++k) cu[k] = k < n - 1 ? c[k + 1] : 0.0;
+    st = oracle_column_solve2(n, c, cu, m, d, x);
+    free(cu);
+    return st;
+}
+
+/* The same elimination for a column block with separate couplings of each row to the
+ * row below, cd_k >= 0 (k = 1..n-1), and to the row above, cu_k >= 0 (k = 0..n-2):
+ * A_T = tridiag(-cd, m + cd + cu, -cu), the non-symmetric block of vertical advection.
+ * Eliminating row k-1 from row k subtracts cd_k cu_{k-1} / pivot_{k-1} =
+ * cd_k - cd_k e_{k-1} / pivot_{k-1} from the diagonal, so
+ *     e_0 = m_0,   e_k = m_k + cd_k e_{k-1} / pivot_{k-1},   pivot_k = e_k + cu_k. */
+int oracle_column_solve2(int n, const double *cd, const double *cu, const double *m, const double *d, double *x)
 {
     double *piv, *y;
     int k;
@@ -583,16 +648,16 @@ int oracle_column_solve(int n, const double *c, const double *m, const double *d
     if (!piv || !y) { free(piv); free(y); return -2; }
     {
         double e = m[0];
-        piv[0] = e + (n > 1 ? c[1] : 0.0);
+        piv[0] = e + (n > 1 ? cu[0] : 0.0);
         y[0] = d[0] / piv[0];
         for (k = 1; k < n; ++k) {
-            e = m[k] + c[k] * e / piv[k - 1];
-            piv[k] = e + (k < n - 1 ? c[k + 1] : 0.0);
-            y[k] = (d[k] + c[k] * y[k - 1]) / piv[k];
+            e = m[k] + cd[k] * e / piv[k - 1];
+            piv[k] = e + (k < n - 1 ? cu[k] : 0.0);
+            y[k] = (d[k] + cd[k] * y[k - 1]) / piv[k];
         }
     }
     x[n - 1] = y[n - 1];
-    for (k = n - 2; k >= 0; --k) x[k] = y[k] + c[k + 1] / piv[k] * x[k + 1];
+    for (k = n - 2; k >= 0; --k) x[k] = y[k] + cu[k] / piv[k] * x[k + 1];
     free(piv);
     free(y);
     return 0;
@@ -608,11 +673,12 @@ static void relax_column(octx *o, int l, int T, const double *f, const double *u
     for (k = 0; k < n; ++k) {
         double hs = 0.0;
         for (e = 0; e < 3; ++e) hs += alphaS_hat(o, G, T, e, k);
-        o->col_a[k] = alphar_hat(o, G, T, k);          /* coupling to level k-1 (face k) */
+        o->col_a[k] = vert_down(o, G, T, k);            /* coupling to level k-1 */
+        o->col_c[k] = vert_up(o, G, T, k);              /* coupling to level k+1 */
         o->col_b[k] = beta_hat(o, G, T, k) + hs;        /* excess of the diagonal */
         o->col_d[k] = f[(size_t)T * n + k] - apply_row(o, G, u_in, T, k);
     }
-    oracle_column_solve(n, o->col_a, o->col_b, o->col_d, o->col_x);
+    oracle_column_solve2(n, o->col_a, o->col_c, o->col_b, o->col_d, o->col_x);
     for (k = 0; k < n; ++k) u_out[(size_t)T * n + k] = u_in[(size_t)T * n + k] + o->relax * o->col_x[k];
 }
 
@@ -773,16 +839,19 @@ static double **level_profile_cols(const octx *o, const double *fine, int m)
     return p;
 }
 
-void oracle_set_outer_profiles(void *h, const double *beta, const double *ar, const double *aS)
+/* xi [n_cells][n_r + 1] (faces), or NULL: the problem's vertical advection, with the
+ * general profiles only. */
+void oracle_set_outer_profiles(void *h, const double *beta, const double *ar, const double *aS, const double *xi)
 {
     octx *o = (octx *)h;
     const size_t n = (size_t)mg_grid(o, o->n_levels - 1)->n_cells;
-    free(o->pf_beta); free(o->pf_ar); free(o->pf_aS);
+    free(o->pf_beta); free(o->pf_ar); free(o->pf_aS); free(o->pf_xi);
     free_level_profile(o, o->pl_beta);
     free_level_profile(o, o->pl_ar);
     free_level_profile(o, o->pl_aS);
-    o->pf_beta = o->pf_ar = o->pf_aS = NULL;
-    o->pl_beta = o->pl_ar = o->pl_aS = NULL;
+    free_level_profile(o, o->pl_xi);
+    o->pf_beta = o->pf_ar = o->pf_aS = o->pf_xi = NULL;
+    o->pl_beta = o->pl_ar = o->pl_aS = o->pl_xi = NULL;
     if (!beta || !ar || !aS) return;
     o->pf_beta = copy_vec(beta, (int)(n * o->n_r));
     o->pf_ar = copy_vec(ar, (int)(n * (o->n_r + 1)));
@@ -790,6 +859,10 @@ void oracle_set_outer_profiles(void *h, const double *beta, const double *ar, co
     o->pl_beta = level_profile_cols(o, beta, o->n_r);
     o->pl_ar = level_profile_cols(o, ar, o->n_r + 1);
     o->pl_aS = level_profile_cols(o, aS, o->n_r);
+    if (xi) {
+        o->pf_xi = copy_vec(xi, (int)(n * (o->n_r + 1)));
+        o->pl_xi = level_profile_cols(o, xi, o->n_r + 1);
+    }
 }
 
 /* on != 0: the V-cycle's operators use the general profiles too (TPMG^full) */
@@ -808,21 +881,25 @@ int oracle_apply_outer(void *h, const double *x, double *y)
 
 /* Factorised profiles (NULL = 1): vertical beta^r, alpha_S^r at the n_r cell
  * centres, alpha_r^r at the n_r + 1 faces; horizontal beta^S, alpha_r^S,
- * alpha_S^S on the cells of the finest level. */
+ * alpha_S^S on the cells of the finest level; the advection xi_r^r (faces) and
+ * xi_r^S (cells), both NULL for none. */
 void oracle_set_profiles(void *h, const double *beta_r, const double *aS_r, const double *ar_r, const double *beta_s,
-                         const double *ar_s, const double *aS_s)
+                         const double *ar_s, const double *aS_s, const double *xi_r, const double *xi_s)
 {
     octx *o = (octx *)h;
-    free(o->pr_beta); free(o->pr_aS); free(o->pr_ar);
+    free(o->pr_beta); free(o->pr_aS); free(o->pr_ar); free(o->pr_xi);
     free_level_profile(o, o->ps_beta);
     free_level_profile(o, o->ps_ar);
     free_level_profile(o, o->ps_aS);
+    free_level_profile(o, o->ps_xi);
     o->pr_beta = copy_vec(beta_r, o->n_r);
     o->pr_aS = copy_vec(aS_r, o->n_r);
     o->pr_ar = copy_vec(ar_r, o->n_r + 1);
+    o->pr_xi = copy_vec(xi_r, o->n_r + 1);
     o->ps_beta = level_profile(o, beta_s);
     o->ps_ar = level_profile(o, ar_s);
     o->ps_aS = level_profile(o, aS_s);
+    o->ps_xi = level_profile(o, xi_s);
 }
 
 void oracle_destroy(void *h)
@@ -839,14 +916,16 @@ void oracle_destroy(void *h)
     free(o->mg_f); free(o->mg_u); free(o->mg_r);
     free(o->col_a); free(o->col_b); free(o->col_c); free(o->col_d); free(o->col_x);
     free(o->col_cp); free(o->col_dp);
-    free(o->pr_beta); free(o->pr_aS); free(o->pr_ar);
+    free(o->pr_beta); free(o->pr_aS); free(o->pr_ar); free(o->pr_xi);
     free_level_profile(o, o->ps_beta);
     free_level_profile(o, o->ps_ar);
     free_level_profile(o, o->ps_aS);
-    free(o->pf_beta); free(o->pf_ar); free(o->pf_aS);
+    free_level_profile(o, o->ps_xi);
+    free(o->pf_beta); free(o->pf_ar); free(o->pf_aS); free(o->pf_xi);
     free_level_profile(o, o->pl_beta);
     free_level_profile(o, o->pl_ar);
     free_level_profile(o, o->pl_aS);
+    free_level_profile(o, o->pl_xi);
     free(o);
 }
 
@@ -1035,6 +1114,27 @@ int oracle_column_couplings(void *h, int l, double *c, double *m)
             double hs = 0.0;
             for (e = 0; e < 3; ++e) hs += alphaS_hat(o, G, T, e, k);
             c[(size_t)T * n + k] = alphar_hat(o, G, T, k);
+            m[(size_t)T * n + k] = beta_hat(o, G, T, k) + hs;
+        }
+    return 0;
+}
+
+/* With vertical advection: each row's coupling to the row below (cd) and above (cu),
+ * [n_cells][n_r], and the excess m. */
+int oracle_column_couplings2(void *h, int l, double *cd, double *cu, double *m)
+{
+    octx *o = (octx *)h;
+    const ogrid *G;
+    int T, k, e, n;
+    if (l < 0 || l >= o->n_levels) return -1;
+    G = mg_grid(o, l);
+    n = o->n_r;
+    for (T = 0; T < G->n_cells; ++T)
+        for (k = 0; k < n; ++k) {
+            double hs = 0.0;
+            for (e = 0; e < 3; ++e) hs += alphaS_hat(o, G, T, e, k);
+            cd[(size_t)T * n + k] = k > 0 ? vert_down(o, G, T, k) : 0.0;
+            cu[(size_t)T * n + k] = k < n - 1 ? vert_up(o, G, T, k) : 0.0;
             m[(size_t)T * n + k] = beta_hat(o, G, T, k) + hs;
         }
     return 0;

@@ -74,7 +74,7 @@ class tpmg_params(ctypes.Structure):
 
 class tpmg_profiles(ctypes.Structure):
     _fields_ = [(name, ctypes.c_void_p) for name in
-                ("beta_r", "alphaS_r", "alphar_r", "beta_s", "alphar_s", "alphaS_s")]
+                ("beta_r", "alphaS_r", "alphar_r", "beta_s", "alphar_s", "alphaS_s", "xi_r", "xi_s")]
 
 
 class TPMGError(RuntimeError):
@@ -102,7 +102,7 @@ def load(path: str | None = None):
     lib.tpmg_setup_profiles.argtypes = [ctypes.POINTER(tpmg_params), ctypes.POINTER(tpmg_profiles), P,
                                         ctypes.POINTER(P)]
     lib.tpmg_apply_operator.argtypes = [P, P, P]
-    lib.tpmg_set_outer_profiles.argtypes = [P, P, P, P]
+    lib.tpmg_set_outer_profiles.argtypes = [P, P, P, P, P]
     lib.tpmg_vcycle.argtypes = [P, P, P]
     lib.tpmg_vcycle_noalloc.argtypes = [P, P, P]
     lib.tpmg_solve.argtypes = [P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D), P]
@@ -185,7 +185,8 @@ class Solver:
     Keyword arguments are the fields of ``tpmg_params``.  Vectors are torch
     float64 CUDA tensors with ``n_cells * n_r`` elements ([cell][k], k fastest).
     ``profiles``: optional dict of factorised profiles (the fields of
-    ``tpmg_profiles``, numpy float64 arrays; absent = 1).
+    ``tpmg_profiles``, numpy float64 arrays; absent = 1, except the vertical
+    advection xi_r, xi_s: both absent = none).
     """
 
     def __init__(self, stream=None, profiles=None, **params):
@@ -289,17 +290,20 @@ class Solver:
             out[name] = dict(launches=n.value, ms=ms.value, units=units.value, timed=timed.value)
         return out
 
-    def set_outer_profiles(self, beta=None, alphar=None, alphaS=None):
+    def set_outer_profiles(self, beta=None, alphar=None, alphaS=None, xi=None):
         """The problem's operator with general profiles on the finest level (numpy
-        arrays: beta, alphaS [n_cells, n_r], alphar [n_cells, n_r + 1]); None restores
-        the factorised operator.  The V-cycle follows its coefficient storage:
-        FACTORISED keeps the profiles of the set-up (TPMG^fac), FULL adopts all three
-        (TPMG^full), PARTIAL adopts alpha_r (TPMG^partial)."""
+        arrays: beta, alphaS [n_cells, n_r], alphar and the vertical advection xi
+        [n_cells, n_r + 1]; xi None = no advection); None restores the factorised
+        operator.  The V-cycle follows its coefficient storage: FACTORISED keeps the
+        profiles of the set-up (TPMG^fac), FULL adopts all of them (TPMG^full), PARTIAL
+        adopts alpha_r (TPMG^partial)."""
         if beta is None:
-            self._check(self._lib.tpmg_set_outer_profiles(self._h, None, None, None), "tpmg_set_outer_profiles")
+            self._check(self._lib.tpmg_set_outer_profiles(self._h, None, None, None, None), "tpmg_set_outer_profiles")
             return
         arrs = [np.ascontiguousarray(a, dtype=np.float64).reshape(-1) for a in (beta, alphar, alphaS)]
-        self._check(self._lib.tpmg_set_outer_profiles(self._h, *(a.ctypes.data for a in arrs)),
+        xa = None if xi is None else np.ascontiguousarray(xi, dtype=np.float64).reshape(-1)
+        self._check(self._lib.tpmg_set_outer_profiles(self._h, *(a.ctypes.data for a in arrs),
+                                                      None if xa is None else xa.ctypes.data),
                     "tpmg_set_outer_profiles")
 
     # --------------------------------------------------------------- compute

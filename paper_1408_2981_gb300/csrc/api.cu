@@ -80,7 +80,12 @@ struct tpmg_ctx {
     // factors of every refinement level; empty = the constant 1
     std::vector<double> pr_beta, pr_aS, pr_ar;
     std::vector<std::vector<double>> ps_beta, ps_ar, ps_aS;
+    // factorised vertical advection: xi_fac set when given; empty factor = 1
+    bool xi_fac = false;
+    std::vector<double> pr_xi;
+    std::vector<std::vector<double>> ps_xi;
     dbl4 *cfull_store = nullptr;   // the finest level's general-profile coefficients (on first use)
+    double *cvx_store = nullptr;   // the finest level's general advection X (on first use)
     double *rec = nullptr;        // coarsest-level right-hand sides being recorded
     int rec_cap = 0, rec_n = 0;
     double *d_hist = nullptr;     // [kHistCap] residual history of the device-side loop
@@ -173,21 +178,22 @@ bool validate(const tpmg_params *p, std::string &msg)
     return true;
 }
 
-Launch launch_of(const tpmg_ctx *ctx) { return Launch{ctx->issue, ctx->p.n_r, ctx->sm_count}; }
+Launch launch_of(const tpmg_ctx *ctx) { return Launch{ctx->issue, ctx->p.n_r, ctx->sm_count, ctx->vert.dr, ctx->vert.dr32}; }
 
 double vfac(const std::vector<double> &v, int k) { return v.empty() ? 1.0 : v[k]; }
 double hfac(const std::vector<std::vector<double>> &h, int ref, int T) { return h.empty() ? 1.0 : h[ref][T]; }
 
 // horizontal profile factors on every refinement level: the finest as given, each
 // coarser cell the area-weighted mean of its 4 children
-bool level_means(const HostGrid &G, int L, const double *fine, std::vector<std::vector<double>> &out)
+bool level_means(const HostGrid &G, int L, const double *fine, std::vector<std::vector<double>> &out,
+                 bool any_sign = false)
 {
     out.clear();
     if (!fine) return true;
     out.assign(L + 1, std::vector<double>());
     out[L].assign(fine, fine + G.lev[L].n);
     for (double v : out[L])
-        if (!(v > 0.0) || !std::isfinite(v)) return false;
+        if (!std::isfinite(v) || (!any_sign && !(v > 0.0))) return false;
     for (int l = L - 1; l >= 0; --l) {
         out[l].resize(G.lev[l].n);
         for (int T = 0; T < G.lev[l].n; ++T) {
@@ -203,15 +209,19 @@ bool level_means(const HostGrid &G, int L, const double *fine, std::vector<std::
     return true;
 }
 
-bool copy_vertical(const double *v, int n, std::vector<double> &out)
+bool copy_vertical(const double *v, int n, std::vector<double> &out, bool any_sign = false)
 {
     out.clear();
     if (!v) return true;
     out.assign(v, v + n);
     for (double x : out)
-        if (!(x > 0.0) || !std::isfinite(x)) return false;
+        if (!std::isfinite(x) || (!any_sign && !(x > 0.0))) return false;
     return true;
 }
+
+// The solver may run CG only on a symmetric operator: vertical advection (factorised,
+// or in the outer operator's general profiles) makes it non-symmetric.
+bool has_advection(const tpmg_ctx *ctx) { return ctx->xi_fac || (!ctx->lv.empty() && ctx->lv.back().cvx); }
 
 cudaError_t grow_events(Tracer &t, size_t pairs)
 {
@@ -1036,6 +1046,83 @@ void fp64_vertical(const tpmg_ctx *ctx, const HostLevel &H, const double *pr, st
     }
 }
 
+// Vertical advection of one level per face (Appendix A, centred): x [n][n_r + 1]
+// X_{T,face} = omega^2 sigma_face |T| r_face^2 / (r_{face+1} - r_{face-1}) xi_{T,face}
+// (half the face factor of alphar_hat), from the factorised xi with pxi == NULL,
+// otherwise from a general xi of this level [n][n_r + 1]; zero on the boundary faces.
+void fp64_advection(const tpmg_ctx *ctx, const HostLevel &H, const double *pxi, std::vector<double> &x)
+{
+    const HostGrid &G = ctx->host;
+    const int n_r = ctx->p.n_r;
+    x.assign((size_t)H.n * (n_r + 1), 0.0);
+    for (int T = 0; T < H.n; ++T) {
+        const double aX = H.area[T] * hfac(ctx->ps_xi, H.ref, T);
+        for (int k = 1; k < n_r; ++k) {
+            const size_t fi = (size_t)T * (n_r + 1) + k;
+            if (!pxi)
+                x[fi] = aX * (0.5 * G.omega2 * G.face[k] * vfac(ctx->pr_xi, k));
+            else
+                x[fi] = G.omega2 * H.area[T] * (0.5 * G.face[k]) * pxi[fi];
+        }
+    }
+}
+
+// Every row of every column must couple to its neighbours with non-negative weights
+// (down_k = cr_k - dr_k X_k, up_k = cr_{k+1} + dr_k X_{k+1}) for the excess-carried
+// elimination of the line smoother: an M-matrix column block.
+bool couplings_ok(const tpmg_ctx *ctx, int n_cells, const std::vector<double> &cr, const std::vector<double> &x)
+{
+    const int n_r = ctx->p.n_r;
+    for (int T = 0; T < n_cells; ++T)
+        for (int k = 0; k < n_r; ++k) {
+            const size_t f = (size_t)T * (n_r + 1) + k;
+            const double dr = ctx->host.dr[k];
+            if (k > 0 && !(cr[f] - dr * x[f] >= 0.0)) return false;
+            if (k < n_r - 1 && !(cr[f + 1] + dr * x[f + 1] >= 0.0)) return false;
+        }
+    return true;
+}
+
+// The vertical advection a level's V-cycle uses: its stored X (FULL: vcx; mixed: cxv in
+// BF16) or its factor |T| xi^S (area_x), from the factorised xi (pxi == NULL) or a
+// general one of this level; none when neither is given.  Checks the column blocks.
+tpmg_status upload_advection(tpmg_ctx *ctx, const HostLevel &H, LevelDev &D, const double *pxi, const double *pr)
+{
+    const tpmg_params &p = ctx->p;
+    const bool mixed = p.precision == TPMG_PREC_MIXED, stored = p.coeff_storage == TPMG_COEFF_FULL;
+    const bool on = pxi ? true : (stored && pr ? false : ctx->xi_fac);   // FULL with general profiles: their xi only
+    const size_t nn = (size_t)H.n * p.n_r;
+    D.vcx_on = D.cxv_on = false;
+    if (!on) return TPMG_OK;
+    std::vector<double> x, cr;
+    fp64_advection(ctx, H, pxi, x);
+    fp64_vertical(ctx, H, pr, cr);
+    if (!couplings_ok(ctx, H.n, cr, x))
+        return fail(ctx, TPMG_ERR_INVALID_ARG, "vertical advection too strong: a column block is no M-matrix "
+                                               "(dr |xi| > 2 alpha_r on some face)");
+    if (mixed) {
+        std::vector<unsigned short> xb(nn);
+        for (int T = 0; T < H.n; ++T)
+            for (int k = 0; k < p.n_r; ++k) xb[(size_t)T * p.n_r + k] = bf16_bits(x[(size_t)T * (p.n_r + 1) + k]);
+        if (!D.cxv) CU(dalloc(ctx, &D.cxv, nn));
+        CU(cudaMemcpyAsync(D.cxv, xb.data(), nn * sizeof(unsigned short), cudaMemcpyHostToDevice, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        D.cxv_on = true;
+    } else if (stored) {
+        if (!D.vcx) CU(dalloc(ctx, &D.vcx, x.size()));
+        CU(cudaMemcpyAsync(D.vcx, x.data(), x.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        D.vcx_on = true;
+    } else if (!D.area_x) {   // factorised or partial: xi stays factorised
+        std::vector<double> ax(H.n);
+        for (int T = 0; T < H.n; ++T) ax[T] = H.area[T] * hfac(ctx->ps_xi, H.ref, T);
+        CU(dalloc(ctx, &D.area_x, ax.size()));
+        CU(cudaMemcpyAsync(D.area_x, ax.data(), ax.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+    }
+    return TPMG_OK;
+}
+
 // General per-unknown profiles of one level from the next finer (m values per cell):
 // each coarse (cell, j) the area-weighted mean over the 4 children's (cell, j).
 std::vector<double> average_children(const HostLevel &fine, const std::vector<double> &pf, int m)
@@ -1176,6 +1263,10 @@ tpmg_status upload_level(tpmg_ctx *ctx, int l)
         if (tasks[q] >= 0) { tnb[q] = nb[tasks[q]]; tg[q] = g[tasks[q]]; }
     CU(cudaMemcpyAsync(D.task_nbr, tnb.data(), tnb.size() * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(D.task_g, tg.data(), tg.size() * sizeof(dbl4), cudaMemcpyHostToDevice, ctx->stream));
+    {
+        const tpmg_status st = upload_advection(ctx, H, D, nullptr, nullptr);
+        if (st != TPMG_OK) return st;
+    }
     if (!mixed) {
         CU(launch_twisted_factors(launch_of(ctx), D, ctx->vert));
         if (D.scan) CU(launch_thomas_factors(launch_of(ctx), D, ctx->vert));
@@ -1286,8 +1377,14 @@ tpmg_status tpmg_setup_profiles(const tpmg_params *params, const tpmg_profiles *
                 if (!(v[i] > 0.0) || !std::isfinite(v[i])) return false;
             return true;
         };
+        auto finite = [](const double *v, long n) {
+            for (long i = 0; v && i < n; ++i)
+                if (!std::isfinite(v[i])) return false;
+            return true;
+        };
         if (!ok(prof->beta_r, params->n_r) || !ok(prof->alphaS_r, params->n_r) || !ok(prof->alphar_r, params->n_r + 1) ||
-            !ok(prof->beta_s, n_fine) || !ok(prof->alphar_s, n_fine) || !ok(prof->alphaS_s, n_fine))
+            !ok(prof->beta_s, n_fine) || !ok(prof->alphar_s, n_fine) || !ok(prof->alphaS_s, n_fine) ||
+            !finite(prof->xi_r, params->n_r + 1) || !finite(prof->xi_s, n_fine))
             return TPMG_ERR_INVALID_ARG;
     }
     tpmg_ctx *ctx = new (std::nothrow) tpmg_ctx();
@@ -1311,18 +1408,26 @@ tpmg_status tpmg_setup_profiles(const tpmg_params *params, const tpmg_profiles *
             !copy_vertical(prof->alphar_r, n_r + 1, ctx->pr_ar) ||
             !level_means(ctx->host, L, prof->beta_s, ctx->ps_beta) ||
             !level_means(ctx->host, L, prof->alphar_s, ctx->ps_ar) ||
-            !level_means(ctx->host, L, prof->alphaS_s, ctx->ps_aS))
+            !level_means(ctx->host, L, prof->alphaS_s, ctx->ps_aS) ||
+            !copy_vertical(prof->xi_r, n_r + 1, ctx->pr_xi, true) ||
+            !level_means(ctx->host, L, prof->xi_s, ctx->ps_xi, true))
             return bail(TPMG_ERR_INVALID_ARG);
+        ctx->xi_fac = prof->xi_r || prof->xi_s;
     }
     // vertical factors: vol | w | hr
     {
         const HostGrid &G = ctx->host;
-        std::vector<double> hv(3 * n_r + 1);
-        double *vol = hv.data(), *w = vol + n_r, *hr = w + n_r + 1;
+        std::vector<double> hv(6 * n_r + 1);
+        double *vol = hv.data(), *w = vol + n_r, *hr = w + n_r + 1, *xm = hr + n_r, *xp = xm + n_r, *drv = xp + n_r;
         for (int k = 0; k <= n_r; ++k) w[k] = G.omega2 * G.face[k] * vfac(ctx->pr_ar, k);
+        // the factorised advection's vertical factor of face k (zero on the boundary faces)
+        auto wx = [&](int k) { return (k == 0 || k == n_r) ? 0.0 : 0.5 * G.omega2 * G.face[k] * vfac(ctx->pr_xi, k); };
         for (int k = 0; k < n_r; ++k) {
             vol[k] = G.vol[k] * vfac(ctx->pr_beta, k);
             hr[k] = G.omega2 * G.dr[k] * vfac(ctx->pr_aS, k);
+            xm[k] = G.dr[k] * wx(k);
+            xp[k] = G.dr[k] * wx(k + 1);
+            drv[k] = G.dr[k];
         }
         tpmg_status st = TPMG_OK;
         if (dalloc(ctx, &ctx->d_vert, hv.size()) != cudaSuccess) return bail(TPMG_ERR_OOM);
@@ -1334,14 +1439,22 @@ tpmg_status tpmg_setup_profiles(const tpmg_params *params, const tpmg_profiles *
         ctx->vert.vol = ctx->d_vert;
         ctx->vert.w = ctx->d_vert + n_r;
         ctx->vert.hr = ctx->d_vert + 2 * n_r + 1;
-        std::vector<float> iv(n_r);
-        for (int k = 0; k < n_r; ++k) iv[k] = (float)(1.0 / G.vol[k]);
+        ctx->vert.xm = ctx->d_vert + 3 * n_r + 1;
+        ctx->vert.xp = ctx->d_vert + 4 * n_r + 1;
+        ctx->vert.dr = ctx->d_vert + 5 * n_r + 1;
+        std::vector<float> iv(2 * n_r);
+        for (int k = 0; k < n_r; ++k) {
+            iv[k] = (float)(1.0 / G.vol[k]);
+            iv[n_r + k] = (float)G.dr[k];
+        }
         float *d_iv = nullptr;
-        if (dalloc(ctx, &d_iv, n_r) != cudaSuccess) return bail(TPMG_ERR_OOM);
-        if (cudaMemcpyAsync(d_iv, iv.data(), n_r * sizeof(float), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
+        if (dalloc(ctx, &d_iv, 2 * n_r) != cudaSuccess) return bail(TPMG_ERR_OOM);
+        if (cudaMemcpyAsync(d_iv, iv.data(), 2 * n_r * sizeof(float), cudaMemcpyHostToDevice, ctx->stream) !=
+                cudaSuccess ||
             cudaStreamSynchronize(ctx->stream) != cudaSuccess)
             return bail(TPMG_ERR_CUDA);
         ctx->vert.ivol32 = d_iv;
+        ctx->vert.dr32 = d_iv + n_r;
     }
     ctx->lv.assign(ctx->p.n_levels, LevelDev());
     for (int l = 0; l < ctx->p.n_levels; ++l) {
@@ -1377,73 +1490,110 @@ tpmg_status tpmg_apply_operator(tpmg_ctx *ctx, const double *d_x, double *d_y)
 }
 
 tpmg_status tpmg_set_outer_profiles(tpmg_ctx *ctx, const double *h_beta, const double *h_alphar,
-                                    const double *h_alphaS)
+                                    const double *h_alphaS, const double *h_xi)
 {
     if (!ctx) return TPMG_ERR_INVALID_ARG;
     LevelDev &D = ctx->lv.back();
     const HostLevel &H = ctx->host.lev[ctx->p.refinement];
-    const HostGrid &G = ctx->host;
     const int n_r = ctx->p.n_r, n = H.n;
-    CU(cudaStreamSynchronize(ctx->stream));
-    drop_graph(ctx);   // captured solves hold the operator's kernels
-    // a V-cycle that stores its stencil per unknown adopts the general profiles too
-    // (FULL: all three, TPMG^full; PARTIAL: alpha_r, TPMG^partial; coarse levels average
-    // them over the children), or goes back to the factorised ones; then its column
-    // factors are formed again
-    auto restencil = [&](const double *pb, const double *pr, const double *ps) -> tpmg_status {
-        const bool mixed = ctx->p.precision == TPMG_PREC_MIXED;
-        if (ctx->p.coeff_storage == TPMG_COEFF_FACTORISED) return TPMG_OK;
-        std::vector<double> b, r, a;
-        if (pb) { b.assign(pb, pb + (size_t)n * n_r); r.assign(pr, pr + (size_t)n * (n_r + 1)); a.assign(ps, ps + (size_t)n * n_r); }
+    const size_t nn = (size_t)n * n_r, nf = (size_t)n * (n_r + 1);
+    const bool clear = !h_beta && !h_alphar && !h_alphaS;
+    if (!clear) {
+        if (!h_beta || !h_alphar || !h_alphaS) return fail(ctx, TPMG_ERR_INVALID_ARG, "give all three profiles or none");
+        auto ok = [](const double *v, size_t m, bool any_sign) {
+            for (size_t i = 0; i < m; ++i)
+                if (!std::isfinite(v[i]) || (!any_sign && !(v[i] > 0.0))) return false;
+            return true;
+        };
+        if (!ok(h_beta, nn, false) || !ok(h_alphaS, nn, false) || !ok(h_alphar, nf, false))
+            return fail(ctx, TPMG_ERR_INVALID_ARG, "profiles must be positive and finite");
+        if (h_xi && !ok(h_xi, nf, true)) return fail(ctx, TPMG_ERR_INVALID_ARG, "xi must be finite");
+    }
+    const double *px = clear ? nullptr : h_xi;
+    // A V-cycle that stores its stencil per unknown adopts the general profiles too
+    // (FULL: all of them, advection included, TPMG^full; PARTIAL: alpha_r, with beta,
+    // alpha_S and xi factorised, TPMG^partial; coarse levels average them over the
+    // children), or goes back to the factorised ones; then its column factors are formed
+    // again.  The first pass only checks that every level's column blocks stay M-matrices,
+    // so that a rejected call changes nothing.
+    const bool stored = ctx->p.coeff_storage == TPMG_COEFF_FULL;
+    const bool mixed = ctx->p.precision == TPMG_PREC_MIXED;
+    for (int pass = 0; pass < 2 && ctx->p.coeff_storage != TPMG_COEFF_FACTORISED; ++pass) {
+        std::vector<double> b, r, a, x;
+        if (!clear) {
+            b.assign(h_beta, h_beta + nn);
+            r.assign(h_alphar, h_alphar + nf);
+            a.assign(h_alphaS, h_alphaS + nn);
+            if (px) x.assign(px, px + nf);
+        }
+        if (pass == 1) {
+            CU(cudaStreamSynchronize(ctx->stream));
+            drop_graph(ctx);   // captured solves hold the V-cycle's kernels
+        }
         for (int l = ctx->p.n_levels - 1; l >= 0; --l) {
             const HostLevel &Hl = ctx->host.lev[ctx->p.refinement - (ctx->p.n_levels - 1 - l)];
-            if (pb && l < ctx->p.n_levels - 1) {
+            if (!clear && l < ctx->p.n_levels - 1) {
                 const HostLevel &Hf = ctx->host.lev[Hl.ref + 1];
                 b = average_children(Hf, b, n_r);
                 r = average_children(Hf, r, n_r + 1);
                 a = average_children(Hf, a, n_r);
+                if (px) x = average_children(Hf, x, n_r + 1);
             }
+            const double *lb = clear ? nullptr : b.data(), *lr = clear ? nullptr : r.data();
+            const double *la = clear ? nullptr : a.data(), *lx = (stored && px) ? x.data() : nullptr;
             LevelDev &Dl = ctx->lv[l];
+            if (pass == 0) {
+                const bool on = lx ? true : (stored && !clear ? false : ctx->xi_fac);
+                if (on) {
+                    std::vector<double> xv, crv;
+                    fp64_advection(ctx, Hl, lx, xv);
+                    fp64_vertical(ctx, Hl, lr, crv);
+                    if (!couplings_ok(ctx, Hl.n, crv, xv))
+                        return fail(ctx, TPMG_ERR_INVALID_ARG, "vertical advection too strong: a column block is no "
+                                                               "M-matrix (dr |xi| > 2 alpha_r on some face)");
+                }
+                continue;
+            }
             if (mixed) {
                 std::vector<bf16x4> cp;
                 std::vector<unsigned short> cv;
-                bf16_stencil(ctx, Hl, pb ? b.data() : nullptr, pb ? r.data() : nullptr, pb ? a.data() : nullptr, cp, cv);
+                bf16_stencil(ctx, Hl, lb, lr, la, cp, cv);
                 CU(cudaMemcpyAsync(Dl.cpack, cp.data(), cp.size() * sizeof(bf16x4), cudaMemcpyHostToDevice, ctx->stream));
                 CU(cudaMemcpyAsync(Dl.cvert, cv.data(), cv.size() * sizeof(unsigned short), cudaMemcpyHostToDevice,
                                    ctx->stream));
-                CU(launch_thomas_factors32(launch_of(ctx), Dl));
                 CU(cudaStreamSynchronize(ctx->stream));   // cp, cv are local
+                const tpmg_status st = upload_advection(ctx, Hl, Dl, lx, lr);
+                if (st != TPMG_OK) return st;
+                CU(launch_thomas_factors32(launch_of(ctx), Dl));
+                CU(cudaStreamSynchronize(ctx->stream));
                 continue;
             }
             std::vector<dbl4> c;
             std::vector<double> cr;
-            fp64_vertical(ctx, Hl, pb ? r.data() : nullptr, cr);
+            fp64_vertical(ctx, Hl, lr, cr);
             CU(cudaMemcpyAsync(Dl.vcr, cr.data(), cr.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-            if (ctx->p.coeff_storage == TPMG_COEFF_FULL) {
-                fp64_horizontal(ctx, Hl, pb ? b.data() : nullptr, pb ? a.data() : nullptr, c);
+            if (stored) {
+                fp64_horizontal(ctx, Hl, lb, la, c);
                 CU(cudaMemcpyAsync(Dl.vc, c.data(), c.size() * sizeof(dbl4), cudaMemcpyHostToDevice, ctx->stream));
             }
+            CU(cudaStreamSynchronize(ctx->stream));   // c, cr are local
+            const tpmg_status st = upload_advection(ctx, Hl, Dl, lx, lr);
+            if (st != TPMG_OK) return st;
             CU(launch_twisted_factors(launch_of(ctx), Dl, ctx->vert));
             if (Dl.scan) {
                 CU(launch_thomas_factors(launch_of(ctx), Dl, ctx->vert));
             }
-            CU(cudaStreamSynchronize(ctx->stream));   // c, cr are local
+            CU(cudaStreamSynchronize(ctx->stream));
         }
-        return TPMG_OK;
-    };
-    if (!h_beta && !h_alphar && !h_alphaS) {
-        D.cfull = nullptr;   // the arrays stay allocated for a later call (freed by tpmg_destroy)
-        return restencil(nullptr, nullptr, nullptr);
     }
-    if (!h_beta || !h_alphar || !h_alphaS) return fail(ctx, TPMG_ERR_INVALID_ARG, "give all three profiles or none");
-    const size_t nn = (size_t)n * n_r, nf = (size_t)n * (n_r + 1);
-    auto ok = [](const double *v, size_t m) {
-        for (size_t i = 0; i < m; ++i)
-            if (!(v[i] > 0.0) || !std::isfinite(v[i])) return false;
-        return true;
-    };
-    if (!ok(h_beta, nn) || !ok(h_alphaS, nn) || !ok(h_alphar, nf))
-        return fail(ctx, TPMG_ERR_INVALID_ARG, "profiles must be positive and finite");
+    CU(cudaStreamSynchronize(ctx->stream));
+    drop_graph(ctx);   // captured solves hold the operator's kernels
+    if (clear) {
+        D.cfull = nullptr;   // the arrays stay allocated for a later call (freed by tpmg_destroy)
+        D.cvx = nullptr;
+        return TPMG_OK;
+    }
+    // the problem's operator per unknown in FP64 (finest level)
     std::vector<dbl4> c;
     std::vector<double> cr;
     fp64_horizontal(ctx, H, h_beta, h_alphaS, c);
@@ -1456,9 +1606,16 @@ tpmg_status tpmg_set_outer_profiles(tpmg_ctx *ctx, const double *h_beta, const d
     }
     CU(cudaMemcpyAsync(ctx->cfull_store, c.data(), nn * sizeof(dbl4), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(D.cvr, cr.data(), nf * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    std::vector<double> xo;
+    if (h_xi) {
+        fp64_advection(ctx, H, h_xi, xo);
+        if (!ctx->cvx_store) CU(dalloc(ctx, &ctx->cvx_store, nf));
+        CU(cudaMemcpyAsync(ctx->cvx_store, xo.data(), nf * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    }
     CU(cudaStreamSynchronize(ctx->stream));
     D.cfull = ctx->cfull_store;
-    return restencil(h_beta, h_alphar, h_alphaS);
+    D.cvx = h_xi ? ctx->cvx_store : nullptr;
+    return TPMG_OK;
 }
 
 tpmg_status tpmg_vcycle(tpmg_ctx *ctx, const double *d_r, double *d_z)
@@ -1521,6 +1678,8 @@ tpmg_status tpmg_solve(tpmg_ctx *ctx, const double *d_f, double *d_u, double rto
     if (!ctx || !d_f || !d_u || !iters || !rel_resid) return fail(ctx, TPMG_ERR_INVALID_ARG, "NULL argument");
     if (!(rtol >= 0.0) || max_iter < 0) return fail(ctx, TPMG_ERR_INVALID_ARG, "rtol must be >= 0, max_iter >= 0");
     if (d_f == d_u) return fail(ctx, TPMG_ERR_INVALID_ARG, "f and u must not overlap");
+    if (has_advection(ctx) && ctx->p.outer == TPMG_OUTER_CG)
+        return fail(ctx, TPMG_ERR_INVALID_ARG, "vertical advection makes the operator non-symmetric: CG does not apply (use Richardson or BiCGStab)");
     // the device-side loop cannot carry the event pairs of a timed kernel class
     if (ctx->p.outer == TPMG_OUTER_CG && ctx->p.graphs && ctx->tr.mask == 0 && max_iter < kHistCap)
         return pcg_graph(ctx, d_f, d_u, rtol, max_iter, iters, rel_resid, resid_hist);
@@ -1542,6 +1701,7 @@ tpmg_status tpmg_batch_create(tpmg_ctx *const *ctxs, int n, const double *const 
     for (int i = 0; i < n; ++i) {
         if (!ctxs[i] || !d_f[i] || !d_u[i] || d_f[i] == d_u[i] || ctxs[i]->device != dev) return TPMG_ERR_INVALID_ARG;
         if (ctxs[i]->p.outer != TPMG_OUTER_CG) return TPMG_ERR_INVALID_ARG;   // batches hold device-side CG loops
+        if (has_advection(ctxs[i])) return TPMG_ERR_INVALID_ARG;             // which need a symmetric operator
         for (int k = 0; k < i; ++k)
             if (ctxs[k] == ctxs[i]) return TPMG_ERR_INVALID_ARG;   // one problem per context
     }
@@ -1604,6 +1764,8 @@ tpmg_status tpmg_solve_host(tpmg_ctx *ctx, const double *h_f, double *h_u, doubl
 {
     if (!ctx || !h_f || !h_u || !iters || !rel_resid) return fail(ctx, TPMG_ERR_INVALID_ARG, "NULL argument");
     if (!(rtol >= 0.0) || max_iter < 0) return fail(ctx, TPMG_ERR_INVALID_ARG, "rtol must be >= 0, max_iter >= 0");
+    if (has_advection(ctx) && ctx->p.outer == TPMG_OUTER_CG)
+        return fail(ctx, TPMG_ERR_INVALID_ARG, "vertical advection makes the operator non-symmetric: CG does not apply (use Richardson or BiCGStab)");
     const size_t bytes = sizeof(double) * ctx->N;
     CU(cudaMemcpyAsync(ctx->hf, h_f, bytes, cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(ctx->hu, h_u, bytes, cudaMemcpyHostToDevice, ctx->stream));
@@ -1858,6 +2020,8 @@ tpmg_status tpmg_solve_learned(tpmg_ctx *ctx, const double *d_f, double *d_u, do
     if (!ctx || !d_f || !d_u || !iters || !rel_resid) return fail(ctx, TPMG_ERR_INVALID_ARG, "NULL argument");
     if (ctx->p.precision != TPMG_PREC_MIXED)
         return fail(ctx, TPMG_ERR_INVALID_ARG, "the learned solve needs the mixed-precision form");
+    if (has_advection(ctx))
+        return fail(ctx, TPMG_ERR_INVALID_ARG, "the learned solve runs flexible CG, which needs a symmetric operator");
     if (!(rtol >= 0.0) || max_iter < 1 || max_iter >= kHistCap)
         return fail(ctx, TPMG_ERR_INVALID_ARG, "rtol must be >= 0, max_iter in 1..4095");
     if (d_f == d_u) return fail(ctx, TPMG_ERR_INVALID_ARG, "f and u must not overlap");

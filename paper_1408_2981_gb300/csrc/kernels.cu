@@ -61,11 +61,20 @@ struct OpView {
     // alphar_hat of face k (TPMG^full and TPMG^partial)
     const dbl4 *__restrict__ c;
     const double *__restrict__ cr;
+    // vertical advection (null without): area_x [n] |T| xi^S_T with the row vectors
+    // xm, xp (factorised form), or cx [n][n_r + 1] X per face (stored, TPMG^full) with
+    // the row thickness dr
+    const double *__restrict__ area_x;
+    const double *__restrict__ xm;
+    const double *__restrict__ xp;
+    const double *__restrict__ cx;
+    const double *__restrict__ dr;
 };
 
 inline OpView make_view(const LevelDev &lv, const VertDev &v, int n_r)
 {
-    return OpView{lv.nbr, lv.g, lv.area, lv.area_r, v.vol, v.w, v.hr, n_r, lv.vc, lv.vcr};
+    return OpView{lv.nbr, lv.g, lv.area, lv.area_r, v.vol, v.w, v.hr, n_r, lv.vc, lv.vcr,
+                  lv.area_x, v.xm, v.xp, lv.vcx_on ? lv.vcx : nullptr, v.dr};
 }
 
 // Stencil form of a level's V-cycle operator: factorised profiles (TPMG^fac), alpha_r
@@ -74,8 +83,11 @@ enum { CM_FAC = 0, CM_PARTIAL = 1, CM_FULL = 2 };
 inline int stencil_form(const LevelDev &lv) { return lv.vc ? CM_FULL : (lv.vcr ? CM_PARTIAL : CM_FAC); }
 
 // Column block A_T of a level (set-up kernels): the excess m_k of row k (its diagonal
-// minus its vertical couplings) and the coupling c_k of face k (rows k-1 and k).
-// A = |T| beta^S_T, G = sum of the edge weights g_e, Ar = |T| alpha_r^S_T.
+// minus its vertical couplings) and the couplings of row k to the rows below and above,
+//   down_k = alphar_hat_k - dr_k X_k,   up_k = alphar_hat_{k+1} + dr_k X_{k+1}
+// (diffusion through the face minus / plus the centred vertical advection across it;
+// without advection both are the symmetric alphar_hat of the face).
+// A = |T| beta^S_T, G = sum of the edge weights g_e, Ar = |T| alpha_r^S_T, Ax = |T| xi^S_T.
 __device__ __forceinline__ double col_excess(const OpView &o, int T, int k, double A, double G)
 {
     if (o.c) {
@@ -84,10 +96,24 @@ __device__ __forceinline__ double col_excess(const OpView &o, int T, int k, doub
     }
     return fma(A, o.vol[k], o.hr[k] * G);
 }
-__device__ __forceinline__ double col_coupling(const OpView &o, int T, int k, double Ar)
+__device__ __forceinline__ double col_face(const OpView &o, int T, int k, double Ar)
 {
     if (o.cr) return o.cr[(size_t)T * (o.n_r + 1) + k];
     return Ar * o.w[k];
+}
+__device__ __forceinline__ double col_down(const OpView &o, int T, int k, double Ar, double Ax)
+{
+    const double a = col_face(o, T, k, Ar);
+    if (o.cx) return a - o.dr[k] * o.cx[(size_t)T * (o.n_r + 1) + k];
+    if (o.area_x) return a - Ax * o.xm[k];
+    return a;
+}
+__device__ __forceinline__ double col_up(const OpView &o, int T, int k, double Ar, double Ax)
+{
+    const double a = col_face(o, T, k + 1, Ar);
+    if (o.cx) return a + o.dr[k] * o.cx[(size_t)T * (o.n_r + 1) + k + 1];
+    if (o.area_x) return a + Ax * o.xp[k];
+    return a;
 }
 
 // (A x)_{T,k} in flux form: 13 FP64 instructions.
@@ -101,7 +127,10 @@ __device__ __forceinline__ double apply_at(const OpView &o, const double *__rest
     const double dp = k < n_r - 1 ? xc - x[i + 1] : 0.0;
     const double vert = fma(__ldg(&o.w[k + 1]), dp, __ldg(&o.w[k]) * dm);
     const double hor = fma(g.z, xc - x[nb.z * n_r + k], fma(g.y, xc - x[nb.y * n_r + k], g.x * (xc - x[nb.x * n_r + k])));
-    return fma(__ldg(&o.area_r[T]), vert, fma(__ldg(&o.area[T]) * __ldg(&o.vol[k]), xc, __ldg(&o.hr[k]) * hor));
+    const double v = fma(__ldg(&o.area_r[T]), vert, fma(__ldg(&o.area[T]) * __ldg(&o.vol[k]), xc, __ldg(&o.hr[k]) * hor));
+    if (!o.area_x) return v;
+    // centred vertical advection: + Ax (xp_k (u_k - u_{k+1}) - xm_k (u_k - u_{k-1}))
+    return fma(__ldg(&o.area_x[T]), fma(__ldg(&o.xp[k]), dp, -__ldg(&o.xm[k]) * dm), v);
 }
 
 // Row (T, k) of the problem's operator from its per-unknown coefficients (general,
@@ -109,6 +138,7 @@ __device__ __forceinline__ double apply_at(const OpView &o, const double *__rest
 struct FullView {
     const dbl4 *__restrict__ c;       // [n][n_r] {alphaS_hat 0, 1, 2, beta_hat}
     const double *__restrict__ cr;    // [n][n_r + 1] alphar_hat of face k
+    const double *__restrict__ cx;    // [n][n_r + 1] advection X of face k, or null
 };
 
 __device__ __forceinline__ double apply_full_at(const OpView &o, const FullView &fv, const double *__restrict__ x,
@@ -121,7 +151,11 @@ __device__ __forceinline__ double apply_full_at(const OpView &o, const FullView 
     const double dm = k > 0 ? xc - x[i - 1] : 0.0;
     const double dp = k < n_r - 1 ? xc - x[i + 1] : 0.0;
     const double *cr = fv.cr + (size_t)T * (n_r + 1) + k;
-    const double vert = fma(__ldg(&cr[1]), dp, __ldg(&cr[0]) * dm);
+    double vert = fma(__ldg(&cr[1]), dp, __ldg(&cr[0]) * dm);
+    if (fv.cx) {   // centred vertical advection: dr_k (X_{k+1} (u_k - u_{k+1}) - X_k (u_k - u_{k-1}))
+        const double *cx = fv.cx + (size_t)T * (n_r + 1) + k;
+        vert = fma(__ldg(&o.dr[k]), fma(__ldg(&cx[1]), dp, -__ldg(&cx[0]) * dm), vert);
+    }
     const double hor = fma(c.z, xc - x[nb.z * n_r + k], fma(c.y, xc - x[nb.y * n_r + k], c.x * (xc - x[nb.x * n_r + k])));
     return fma(c.w, xc, vert + hor);
 }
@@ -145,7 +179,8 @@ __device__ __forceinline__ double apply_partial_at(const OpView &o, const double
     const double dm = k > 0 ? xc - x[i - 1] : 0.0;
     const double dp = k < n_r - 1 ? xc - x[i + 1] : 0.0;
     const double *cr = o.cr + (size_t)T * (n_r + 1) + k;
-    const double vert = fma(__ldg(&cr[1]), dp, __ldg(&cr[0]) * dm);
+    double vert = fma(__ldg(&cr[1]), dp, __ldg(&cr[0]) * dm);
+    if (o.area_x) vert = fma(__ldg(&o.area_x[T]), fma(__ldg(&o.xp[k]), dp, -__ldg(&o.xm[k]) * dm), vert);
     const double hor = fma(g.z, xc - x[nb.z * n_r + k], fma(g.y, xc - x[nb.y * n_r + k], g.x * (xc - x[nb.x * n_r + k])));
     return vert + fma(__ldg(&o.area[T]) * __ldg(&o.vol[k]), xc, __ldg(&o.hr[k]) * hor);
 }
@@ -154,7 +189,7 @@ __device__ __forceinline__ double apply_partial_at(const OpView &o, const double
 template <int CM>
 __device__ __forceinline__ double apply_vc(const OpView &o, const double *__restrict__ x, int T, int k, int i)
 {
-    if (CM == CM_FULL) return apply_full_at(o, FullView{o.c, o.cr}, x, T, k, i);
+    if (CM == CM_FULL) return apply_full_at(o, FullView{o.c, o.cr, o.cx}, x, T, k, i);
     if (CM == CM_PARTIAL) return apply_partial_at(o, x, T, k, i);
     return apply_at(o, x, T, k, i);
 }
@@ -293,11 +328,11 @@ __global__ void k_twisted_factors(int n_tasks, OpView o, const int *__restrict__
     M[col] = M[kRelaxCols + col] = 0.0;
     if (T < 0) return;
     double *ri = rinv + (size_t)T * n;
-    const double A = o.area[T], Ar = o.area_r[T], G = o.g[T].w;
+    const double A = o.area[T], Ar = o.area_r[T], G = o.g[T].w, Ax = o.area_x ? o.area_x[T] : 0.0;
     double e = 0.0, p = 1.0;
     for (int k = 0; k < j; ++k) {
         const double m = col_excess(o, T, k, A, G);
-        const double c = col_coupling(o, T, k, Ar), cu = col_coupling(o, T, k + 1, Ar);
+        const double c = col_down(o, T, k, Ar, Ax), cu = col_up(o, T, k, Ar, Ax);
         e = k == 0 ? m : m + c * e / p;
         p = e + cu;
         const double iv = 1.0 / p;
@@ -308,7 +343,7 @@ __global__ void k_twisted_factors(int n_tasks, OpView o, const int *__restrict__
     double eb = 0.0, q = 1.0;
     for (int k = n - 1, s = 0; k > j; --k, ++s) {
         const double m = col_excess(o, T, k, A, G);
-        const double cd = col_coupling(o, T, k, Ar), cu = col_coupling(o, T, k + 1, Ar);
+        const double cd = col_down(o, T, k, Ar, Ax), cu = col_up(o, T, k, Ar, Ax);
         eb = k == n - 1 ? m : m + cu * eb / q;
         q = eb + cd;
         const double iv = 1.0 / q;
@@ -316,7 +351,7 @@ __global__ void k_twisted_factors(int n_tasks, OpView o, const int *__restrict__
         fb[base + s * 32 + col + 16] = cu * iv;
         fc[base + s * 32 + col + 16] = cd * iv;
     }
-    const double cj = col_coupling(o, T, j, Ar), cj1 = col_coupling(o, T, j + 1, Ar);
+    const double cj = col_down(o, T, j, Ar, Ax), cj1 = col_up(o, T, j, Ar, Ax);
     double gam = col_excess(o, T, j, A, G);
     if (j > 0) gam += cj * e / p;
     if (j < n - 1) gam += cj1 * eb / q;
@@ -435,11 +470,11 @@ __global__ void k_thomas_factors(OpView o, int n_cells, double *__restrict__ rin
     if (T >= n_cells) return;
     const int n = o.n_r;
     const size_t row0 = (size_t)T * n;
-    const double A = o.area[T], Ar = o.area_r[T], G = o.g[T].w;
+    const double A = o.area[T], Ar = o.area_r[T], G = o.g[T].w, Ax = o.area_x ? o.area_x[T] : 0.0;
     double e = 0.0, p = 1.0;
     for (int k = 0; k < n; ++k) {
         const double m = col_excess(o, T, k, A, G);
-        const double c = k > 0 ? col_coupling(o, T, k, Ar) : 0.0, cu = k < n - 1 ? col_coupling(o, T, k + 1, Ar) : 0.0;
+        const double c = k > 0 ? col_down(o, T, k, Ar, Ax) : 0.0, cu = k < n - 1 ? col_up(o, T, k, Ar, Ax) : 0.0;
         e = k == 0 ? m : m + c * e / p;
         p = e + cu;
         const double iv = 1.0 / p;
@@ -1002,7 +1037,7 @@ cudaError_t launch_apply(const Launch &L, const LevelDev &lv, const VertDev &v, 
 {
     const int N = lv.n * L.n_r;
     const int grid = partials ? n_part : grid_for(N, kThreads, L.sm_count);
-    const FullView fv{lv.cfull, lv.cvr};
+    const FullView fv{lv.cfull, lv.cvr, lv.cvx};
     if (lv.cfull)
         k_apply<kThreads, true><<<grid, kThreads, 0, L.s>>>(make_view(lv, v, L.n_r), fv, x, y, N, partials);
     else
@@ -1015,7 +1050,7 @@ cudaError_t launch_residual(const Launch &L, const LevelDev &lv, const VertDev &
 {
     const int N = lv.n * L.n_r;
     const int grid = partials ? n_part : grid_for(N, kThreads, L.sm_count);
-    const FullView fv{lv.cfull, lv.cvr};
+    const FullView fv{lv.cfull, lv.cvr, lv.cvx};
     if (lv.cfull)
         k_residual<kThreads, true><<<grid, kThreads, 0, L.s>>>(make_view(lv, v, L.n_r), fv, f, u, r, N, partials);
     else

@@ -33,8 +33,12 @@ __device__ __forceinline__ float bf(unsigned short h) { return __uint_as_float((
 // stored per unknown in FP32: rinv = 1 / p_k, b = c_k / p_k (b_0 = 0) and
 // g = c_{k+1} / p_k, so that A_T x = d is
 //   y_k = d_k rinv_k + b_k y_{k-1},   x_k = y_k + g_k x_{k+1}.
+// With vertical advection (cxv: X of face k in BF16, dr the row thickness) row k
+// couples downwards with c_k - dr_k X_k and upwards with c_{k+1} + dr_k X_{k+1}, in
+// place of c_k and c_{k+1}.
 __global__ void k_thomas_factors32(int n_cells, const bf16x4 *__restrict__ cpack,
-                                   const unsigned short *__restrict__ cvert, int n, float *__restrict__ rinv,
+                                   const unsigned short *__restrict__ cvert, const unsigned short *__restrict__ cxv,
+                                   const double *__restrict__ dr, int n, float *__restrict__ rinv,
                                    float *__restrict__ fb, float *__restrict__ fg)
 {
     const int T = blockIdx.x * blockDim.x + threadIdx.x;
@@ -45,9 +49,15 @@ __global__ void k_thomas_factors32(int n_cells, const bf16x4 *__restrict__ cpack
         return (double)bf(c.w) + (double)bf(c.x) + (double)bf(c.y) + (double)bf(c.z);
     };
     auto c_of = [&](int k) { return k > 0 && k < n ? (double)bf(cvert[row0 + k]) : 0.0; };
+    auto x_of = [&](int k) { return cxv && k > 0 && k < n ? (double)bf(cxv[row0 + k]) : 0.0; };
     double e = 0.0, p = 1.0;
     for (int k = 0; k < n; ++k) {
-        const double m = m_of(k), c = c_of(k), cu = c_of(k + 1);
+        const double m = m_of(k);
+        double c = c_of(k), cu = c_of(k + 1);
+        if (cxv) {
+            c -= dr[k] * x_of(k);
+            cu += dr[k] * x_of(k + 1);
+        }
         e = k == 0 ? m : m + c * e / p;
         p = e + cu;
         rinv[row0 + k] = (float)(1.0 / p);
@@ -165,7 +175,8 @@ __global__ void __launch_bounds__(256)
 template <typename TF>
 __global__ void __launch_bounds__(kThreads32)
     k_resid_restrict32(const int4 *__restrict__ nbr, const bf16x4 *__restrict__ cpack,
-                       const unsigned short *__restrict__ cvert, int n_r, const TF *__restrict__ f,
+                       const unsigned short *__restrict__ cvert, const unsigned short *__restrict__ cxv,
+                       const float *__restrict__ dr32, int n_r, const TF *__restrict__ f,
                        const float *__restrict__ u, float *__restrict__ fc, int Nc)
 {
     for (int ic = blockIdx.x * kThreads32 + threadIdx.x; ic < Nc; ic += gridDim.x * kThreads32) {
@@ -178,7 +189,12 @@ __global__ void __launch_bounds__(kThreads32)
             const bf16x4 cp = cpack[i];
             const float uc = u[i];
             const float um = k > 0 ? u[i - 1] : uc, up = k < n_r - 1 ? u[i + 1] : uc;
-            const float cl = bf(__ldg(&cvert[i])), cu = k < n_r - 1 ? bf(__ldg(&cvert[i + 1])) : 0.f;
+            float cl = bf(__ldg(&cvert[i])), cu = k < n_r - 1 ? bf(__ldg(&cvert[i + 1])) : 0.f;
+            if (cxv) {   // centred vertical advection (face k's X is zero for k = 0)
+                const float d = __ldg(&dr32[k]);
+                cl = fmaf(-d, bf(__ldg(&cxv[i])), cl);
+                if (k < n_r - 1) cu = fmaf(d, bf(__ldg(&cxv[i + 1])), cu);
+            }
             float a = bf(cp.w) * uc;
             a = fmaf(cl, uc - um, a);
             a = fmaf(cu, uc - up, a);
@@ -258,8 +274,8 @@ cudaError_t launch_resid_restrict32(const Launch &L, const LevelDev &fine, const
                                     const float *u, float *fc)
 {
     const int Nc = coarse.n * L.n_r;
-    k_resid_restrict32<TF><<<grid32(Nc, L.sm_count), kThreads32, 0, L.s>>>(fine.nbr, fine.cpack, fine.cvert, L.n_r, f,
-                                                                           u, fc, Nc);
+    k_resid_restrict32<TF><<<grid32(Nc, L.sm_count), kThreads32, 0, L.s>>>(
+        fine.nbr, fine.cpack, fine.cvert, fine.cxv_on ? fine.cxv : nullptr, L.dr32, L.n_r, f, u, fc, Nc);
     return cudaGetLastError();
 }
 
@@ -272,8 +288,8 @@ cudaError_t launch_prolong_add32(const Launch &L, const LevelDev &fine, const fl
 
 cudaError_t launch_thomas_factors32(const Launch &L, const LevelDev &lv)
 {
-    k_thomas_factors32<<<(lv.n + 127) / 128, 128, 0, L.s>>>(lv.n, lv.cpack, lv.cvert, L.n_r, lv.rinv32, lv.fb32,
-                                                            lv.fc32);
+    k_thomas_factors32<<<(lv.n + 127) / 128, 128, 0, L.s>>>(lv.n, lv.cpack, lv.cvert, lv.cxv_on ? lv.cxv : nullptr,
+                                                            L.dr, L.n_r, lv.rinv32, lv.fb32, lv.fc32);
     return cudaGetLastError();
 }
 

@@ -56,6 +56,13 @@ struct VertDev {            // vertical factors shared by every level (no vertic
     const double *w;        // [n_r+1] omega^2 sigma_k 2 r_k^2 / (r_{k+1} - r_{k-1})
     const double *hr;       // [n_r]   omega^2 (r_{k+1} - r_k)
     const float *ivol32;    // [n_r]   1 / v_k (network features of the learned form)
+    // vertical advection (factorised form): X_face = |T| xi^S_T wx_face with
+    // wx_face = omega^2 sigma r_face^2 / (r_face+1 - r_face-1) xi^r_face; row k takes
+    // xm_k = dr_k wx_k (face k) and xp_k = dr_k wx_{k+1} (face k+1)
+    const double *xm;       // [n_r]
+    const double *xp;       // [n_r]
+    const double *dr;       // [n_r]   r_{k+1} - r_k (rows of a per-face X stored per cell)
+    const float *dr32;      // [n_r]
 };
 
 // Line relaxation works on tasks of kRelaxCols columns of one colour (the
@@ -94,6 +101,16 @@ struct LevelDev {
     // PARTIAL: vcr only), the same layout as cfull / cvr
     dbl4 *vc = nullptr;
     double *vcr = nullptr;
+    // vertical advection: area_x [n] |T| xi^S_T (factorised form), or null; vcx
+    // [n][n_r+1] X per face stored per column (FULL storage), used while vcx_on;
+    // cvx [n][n_r+1] X of the outer operator's general profiles (finest level), or null
+    double *area_x = nullptr;
+    double *vcx = nullptr;
+    bool vcx_on = false;
+    double *cvx = nullptr;
+    // mixed precision: X of face k in BF16 per unknown [n][n_r], used while cxv_on
+    unsigned short *cxv = nullptr;
+    bool cxv_on = false;
     float *iarea32 = nullptr;     // [n] 1 / |T| (network features of the learned form)
     float4 *wnb32 = nullptr;      // [n] {g0, g1, g2} / (g0 + g1 + g2), 0
     int *task_cells = nullptr;    // [n_tasks][16] cell ids, -1 = padding
@@ -153,6 +170,8 @@ struct Launch {
     cudaStream_t s;
     int n_r;
     int sm_count;
+    const double *dr = nullptr;    // [n_r] r_{k+1} - r_k (mixed precision: advection rows)
+    const float *dr32 = nullptr;
 };
 
 // Right-hand side of a relaxation pass: NORMAL f + sum of all neighbours;

@@ -188,7 +188,8 @@ def balanced_flow_profiles(centres: np.ndarray, r_faces: np.ndarray, cp: float =
 
 
 def balanced_flow(centres: np.ndarray, r_faces: np.ndarray, n_freq: float, cp: float = 1005.0, rd: float = 287.0,
-                  t0: float = 273.0, g: float = 9.81, radius: float = 6.371e6) -> tuple[dict, dict, float]:
+                  t0: float = 273.0, g: float = 9.81, radius: float = 6.371e6,
+                  advection: bool = False) -> tuple[dict, dict, float]:
     """The balanced atmosphere at buoyancy frequency N (Sec. 5, after Davies 2005): with
     eps = (N / N*)^2 - 1, e_H = exp(-N^2 F(phi) / g^2), e_V = exp(-N^2 R (r - 1) / g),
     the Exner pressure pi = (eps + e_H e_V) / (1 + eps), theta = T0 / (e_H e_V),
@@ -197,7 +198,12 @@ def balanced_flow(centres: np.ndarray, r_faces: np.ndarray, n_freq: float, cp: f
     Returns (exact profiles per unknown: beta, alphaS [n, n_r] at the cell centres,
     alphar [n, n_r + 1] at the faces; the factorised approximation from
     pi^x = (eps + e_V) / (1 + eps) * e_H as tpmg_profiles fields; eps).  Every profile
-    is normalised by its value at the equator and the surface, where pi = pi^x = 1."""
+    is normalised by its value at the equator and the surface, where pi = pi^x = 1.
+    advection: also the vertical advection xi_r = Lambda rho d_r theta of eq. profiles.
+    theta = T0 / (e_H e_V) gives d_r theta = theta N^2 R / g (r in earth radii), so
+    xi_r = rho theta N^2 R / g: alpha_S's shape (normalised alike) times N^2 R / g, at the
+    faces ("xi" of the exact profiles; "xi_r", "xi_s" of the factorised ones, from
+    rho^x theta = (pi^x)^gamma)."""
     centres = np.asarray(centres, dtype=np.float64)
     r_faces = np.asarray(r_faces, dtype=np.float64)
     n_star = g / math.sqrt(cp * t0)
@@ -220,4 +226,9 @@ def balanced_flow(centres: np.ndarray, r_faces: np.ndarray, n_freq: float, cp: f
     fac = dict(alphaS_r=pv(rc) ** gamma, beta_r=pv(rc) ** (gamma - 1.0) * e_v(rc),
                alphar_r=pv(r_faces) ** gamma * (r_faces / r_faces[0]) ** 2,
                alphaS_s=e_h ** gamma, alphar_s=e_h ** gamma, beta_s=e_h ** gamma)
+    if advection:
+        k_adv = n_freq ** 2 * radius / g
+        outer["xi"] = a_f * k_adv
+        fac["xi_r"] = pv(r_faces) ** gamma * k_adv
+        fac["xi_s"] = e_h ** gamma
     return outer, fac, eps

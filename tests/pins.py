@@ -757,6 +757,74 @@ def pin_partial_profiles(ns):
     o.set_outer_profiles()
 
 
+def pin_advection(ns):
+    """Vertical advection -omega^2 xi_r d_r u (Sec. 2, eq. HelmholtzVector; Appendix A;
+    reading C24: each row averages the one-sided differences through its two faces,
+    weighted by r_face^2 and the row's own thickness).
+    * xi = 0 changes nothing, bit for bit, and a constant field has no advection.
+    * For u = r at the cell midpoints and constant xi, the discrete term of row k is
+      the trapezoid rule for the cell integral of r^2:
+      -omega^2 |T| xi (dr_k / 2) (r_k^2 + r_{k+1}^2) = -omega^2 |T| xi (v_k + dr_k^3 / 6)
+      on interior rows; the bottom row keeps the upper face's half, the top row the
+      lower face's (a closed form on a graded grid).
+    * The non-symmetric column solve equals the dense solve of the assembled block.
+    * A general xi that factorises gives the factorised operator; BiCGStab reaches the
+      dense solution of the non-symmetric operator."""
+    kw = dict(refinement=2, n_levels=2, n_r=6, grading=1.2, H=0.1, courant_c=8.0)
+    o = ns.Oracle(**kw)
+    n, N, n_r = o.level_cells(1), o.size(), o.n_r
+    vert = o.vertical()
+    r, dr, vol = vert["r"], vert["dr"], vert["vol"]
+    area = o.grid(o.refinement)["area"]
+    x = inputs.uniform_pm1(inputs.SEED_UNIFORM_SMALL + 90, N)
+    y0, ones = o.apply(x), np.ones(N)
+    o.set_profiles(xi_r=np.zeros(n_r + 1), xi_s=np.ones(n))
+    assert np.array_equal(o.apply(x), y0)
+    c = 20.0
+    o.set_profiles(xi_r=np.full(n_r + 1, c))
+    assert np.array_equal(o.apply(ones), (o.set_profiles(), o.apply(ones))[1])
+    o.set_profiles(xi_r=np.full(n_r + 1, c))
+    u = np.tile(0.5 * (r[:-1] + r[1:]), n)
+    with_xi = o.apply(u)
+    o.set_profiles()
+    D = (with_xi - o.apply(u)).reshape(n, n_r)
+    w = o.omega2 * area[:, None] * c
+    expect = -w * (vol + dr ** 3 / 6.0)[None, :]
+    expect[:, 0] = -w[:, 0] * dr[0] * r[1] ** 2 / 2.0
+    expect[:, -1] = -w[:, 0] * dr[-1] * r[-2] ** 2 / 2.0
+    scale = np.abs(o.apply(u)).reshape(n, n_r)
+    assert np.all(np.abs(D - expect) <= 1e-12 * scale), np.max(np.abs(D - expect) / scale)
+    # the column blocks and their solve
+    o.set_profiles(xi_r=1.0 + 0.5 * inputs.uniform_pm1(inputs.SEED_UNIFORM_SMALL + 91, n_r + 1),
+                   xi_s=c * (1.0 + 0.5 * inputs.uniform_pm1(inputs.SEED_UNIFORM_SMALL + 92, n)))
+    cd, cu, m = o.column_couplings2()
+    sub, diag, sup = o.column_blocks()
+    assert cd[:, 1:].min() > 0.0 and cu[:, :-1].min() > 0.0
+    assert np.abs(cu[:, :-1] - cd[:, 1:]).max() > 1e-6 * cd[:, 1:].max()   # not symmetric
+    for T in (0, 11, n - 1):
+        Ad = np.diag(m[T] + cd[T] + cu[T]) - np.diag(cd[T, 1:], -1) - np.diag(cu[T, :-1], 1)
+        Ab = np.diag(diag[T]) + np.diag(sub[T, 1:], -1) + np.diag(sup[T, :-1], 1)
+        assert np.abs(Ad - Ab).max() <= 1e-13 * np.abs(Ab).max()
+        d = inputs.uniform_pm1(inputs.SEED_UNIFORM_SMALL + 93 + T, n_r)
+        xs = ns.column_solve2(cd[T], cu[T], m[T], d)
+        xd = np.linalg.solve(Ad, d)
+        assert np.linalg.norm(xs - xd) <= 1e-12 * np.linalg.norm(xd)
+    # general xi as an outer product equals the factorised one; BiCGStab on the operator
+    prof = o._profiles
+    xi_gen = np.outer(prof[7], prof[6])
+    o.set_outer_profiles(beta=np.ones((n, n_r)), alphar=np.ones((n, n_r + 1)), alphaS=np.ones((n, n_r)), xi=xi_gen)
+    assert np.max(np.abs(o.apply_outer(x) - o.apply(x))) <= 1e-13 * np.max(np.abs(o.apply(x)))
+    o.set_outer_profiles()
+    A = o.dense_operator()
+    assert np.abs(A - A.T).max() > 1e-8 * np.abs(A).max()
+    f = inputs.uniform_pm1(inputs.SEED_UNIFORM_SMALL + 94, N)
+    res = o.bicgstab(f, rtol=1e-13, max_iter=200)
+    assert res["status"] == 0
+    ud = np.linalg.solve(A, f)
+    assert np.linalg.norm(res["u"] - ud) <= 1e-9 * np.linalg.norm(ud)
+    o.set_profiles()
+
+
 def pin_manufactured(ns):
     """Manufactured solution: f = A u*, solve to rtol 1e-12, recover u* in the
     energy norm to 1e-9 (a residual drop of 1e-12 bounds the error by cond-weighted 1e-12)."""
@@ -799,5 +867,5 @@ ALL_PINS = [
     pin_vertical_consistency, pin_thomas, pin_column_solve_exact, pin_transfers, pin_vcycle_dense, pin_preconditioner_symmetric,
     pin_invariant_subspaces, pin_pcg_dense, pin_bf16_rounding, pin_flexible_cg, pin_bf16_vcycle,
     pin_manufactured, pin_robust_convergence, pin_bicgstab, pin_profiles, pin_outer_operator,
-    pin_partial_profiles,
+    pin_partial_profiles, pin_advection,
 ]

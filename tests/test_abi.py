@@ -124,3 +124,12 @@ def test_setup_profiles_rejects_non_positive_profiles_before_touching_cuda(lib):
         assert lib.tpmg_setup_profiles(ctypes.byref(p), ctypes.byref(prof), None, ctypes.byref(h)) == \
             binding.TPMG_ERR_INVALID_ARG
         assert not h.value
+    # the vertical advection may take either sign but must be finite
+    for field, n in (("xi_r", 5), ("xi_s", 80)):
+        bad = np.ones(n)
+        bad[n // 2] = np.nan
+        prof = binding.tpmg_profiles(**{field: bad.ctypes.data})
+        h = ctypes.c_void_p()
+        assert lib.tpmg_setup_profiles(ctypes.byref(p), ctypes.byref(prof), None, ctypes.byref(h)) == \
+            binding.TPMG_ERR_INVALID_ARG
+        assert not h.value

@@ -21,15 +21,26 @@ TESTS = os.path.join(ROOT, "tests")
 MUTANTS = {
     "drop_horizontal_flux": ("for (e = 0; e < 3; ++e) s += alphaS_hat(o, G, T, e, k) * (u[i] - u[",
                              "for (e = 0; e < 3; ++e) s += 0.0 * alphaS_hat(o, G, T, e, k) * (u[i] - u["),
-    "vertical_flux_sign": ("s += alphar_hat(o, G, T, k) * (u[i] - u[i - 1]);",
-                           "s += alphar_hat(o, G, T, k) * (u[i] + u[i - 1]);"),
-    "upper_face_index": ("s += alphar_hat(o, G, T, k + 1) * (u[i] - u[i + 1]);",
-                         "s += alphar_hat(o, G, T, k) * (u[i] - u[i + 1]);"),
+    "vertical_flux_sign": ("s += vert_down(o, G, T, k) * (u[i] - u[i - 1]);",
+                           "s += vert_down(o, G, T, k) * (u[i] + u[i - 1]);"),
+    "upper_face_index": ("const double a = alphar_hat(o, G, T, k + 1);",
+                         "const double a = alphar_hat(o, G, T, k);"),
     "neighbour_slot_shift": ("(u[i] - u[(size_t)G->nbr[3 * T + e] * n + k]);",
                              "(u[i] - u[(size_t)G->nbr[3 * T + (e + 1) % 3] * n + k]);"),
-    "column_solve_excess": ("e = m[k] + c[k] * e / piv[k - 1];", "e = m[k] + c[k] / piv[k - 1];"),
-    "column_solve_back": ("x[k] = y[k] + c[k + 1] / piv[k] * x[k + 1];", "x[k] = y[k] + c[k] / piv[k] * x[k + 1];"),
-    "column_solve_forward": ("y[k] = (d[k] + c[k] * y[k - 1]) / piv[k];", "y[k] = (d[k] - c[k] * y[k - 1]) / piv[k];"),
+    "column_solve_excess": ("e = m[k] + cd[k] * e / piv[k - 1];", "e = m[k] + cd[k] / piv[k - 1];"),
+    "column_solve_back": ("x[k] = y[k] + cu[k] / piv[k] * x[k + 1];", "x[k] = y[k] + cd[k] / piv[k] * x[k + 1];"),
+    "column_solve_forward": ("y[k] = (d[k] + cd[k] * y[k - 1]) / piv[k];", "y[k] = (d[k] - cd[k] * y[k - 1]) / piv[k];"),
+    "column_solve_pivot_coupling": ("piv[k] = e + (k < n - 1 ? cu[k] : 0.0);", "piv[k] = e + (k < n - 1 ? cd[k] : 0.0);"),
+    "advection_sign": ("return has_xi(o) ? a - o->dr[k] * xi_hat(o, G, T, k) : a;",
+                       "return has_xi(o) ? a + o->dr[k] * xi_hat(o, G, T, k) : a;"),
+    "advection_one_sided": ("return has_xi(o) ? a + o->dr[k] * xi_hat(o, G, T, k + 1) : a;",
+                            "return has_xi(o) ? a + 2.0 * o->dr[k] * xi_hat(o, G, T, k + 1) : a;"),
+    "advection_without_r2": ("(0.5 * o->arv[face]) * vfac(o->pr_xi, face)",
+                             "(0.5 * o->arv[face] / (o->r[face] * o->r[face])) * vfac(o->pr_xi, face)"),
+    "advection_neighbour_thickness": ("return has_xi(o) ? a - o->dr[k] * xi_hat(o, G, T, k) : a;",
+                                      "return has_xi(o) ? a - o->dr[k > 0 ? k - 1 : k] * xi_hat(o, G, T, k) : a;"),
+    "outer_advection_sign": ("up += o->dr[k] * (o->omega2 * G->area[T] * (0.5 * o->arv[k + 1]) * o->pf_xi[fa + 1]);",
+                             "up -= o->dr[k] * (o->omega2 * G->area[T] * (0.5 * o->arv[k + 1]) * o->pf_xi[fa + 1]);"),
     "thomas_forward_index": ("dp[i] = (d[i] - a[i] * dp[i - 1]) / den;", "dp[i] = (d[i] - a[i - 1] * dp[i - 1]) / den;"),
     "thomas_backward_index": ("x[i] = dp[i] - cp[i] * x[i + 1];", "x[i] = dp[i] - cp[i + 1] * x[i + 1];"),
     "restrict_child_index": ("s += rf[(size_t)(4 * T + j) * n + k];", "s += rf[(size_t)(4 * T) * n + k];"),
@@ -45,8 +56,8 @@ MUTANTS = {
     "profile_coarse_unweighted": ("s += aj * p[l + 1][4 * T + j];", "s += p[l + 1][4 * T + j];"),
     "outer_edge_one_side": ("const double edge = 0.5 * (o->pf_aS[i] + o->pf_aS[(size_t)Tn * n + k]);",
                             "const double edge = o->pf_aS[i];"),
-    "outer_upper_face": ("o->arv[k + 1] * o->pf_ar[fa + 1] * (u[i] - u[i + 1]);",
-                         "o->arv[k + 1] * o->pf_ar[fa] * (u[i] - u[i + 1]);"),
+    "outer_upper_face": ("double up = o->omega2 * G->area[T] * o->arv[k + 1] * o->pf_ar[fa + 1];",
+                         "double up = o->omega2 * G->area[T] * o->arv[k + 1] * o->pf_ar[fa];"),
     "bicgstab_omega_sign": ("r[i] = sv[i] - omega * t[i];", "r[i] = sv[i] + omega * t[i];"),
     "bicgstab_beta_ratio": ("beta = (rho / rho_prev) * (alpha / omega);", "beta = (rho / rho_prev) * (omega / alpha);"),
     "prolong_half": ("uf[(size_t)(4 * T + j) * n + k] += uc[(size_t)T * n + k];",
@@ -86,6 +97,7 @@ DRIVER = textwrap.dedent("""
     ns = types.SimpleNamespace(Oracle=functools.partial(oracle.Oracle, lib_path=lib),
                                thomas=functools.partial(oracle.thomas, lib_path=lib),
                                column_solve=functools.partial(oracle.column_solve, lib_path=lib),
+                               column_solve2=functools.partial(oracle.column_solve2, lib_path=lib),
                                bf16=functools.partial(oracle.bf16, lib_path=lib))
     for p in pins.ALL_PINS:
         try:
