@@ -100,6 +100,13 @@ WORKLOADS = {
              "uniform[-1,1], 6 MG levels, nu 2/2/1, rtol 1e-5; buoyancy frequency N in {N*, 0.022, 0.025, "
              "0.028} 1/s; the full operator with vertical advection preconditioned by TPMG^fac, TPMG^partial, "
              "TPMG^full (FP64) and TPMG^full (mixed precision) with Richardson and BiCGStab"),
+    "balanced-flow-symmetric": dict(
+        study="balanced_flow", refinement=5, n_r=128, seed=2981011, advection=False,
+        n_freq=(None, 0.022, 0.025, 0.028),
+        text="the balanced-flow study without vertical advection (a symmetric operator, so CG applies too): "
+             "icosahedral refinement 5 x 128 levels graded 1.05 over 10 km (2.6M unknowns), omega^2/h^2=8, RHS "
+             "uniform[-1,1], 6 MG levels, nu 2/2/1, rtol 1e-5; TPMG^fac, TPMG^partial, TPMG^full (FP64) and "
+             "TPMG^full (mixed precision) with Richardson, CG and BiCGStab"),
     "batch48": dict(
         batch=48, seed=2981004,
         text="48 independent solves in one graph launch: refinement drawn from {4,5,6}, vertical levels from "
