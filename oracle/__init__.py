@@ -86,6 +86,8 @@ def _load(path: str | None = None):
         lib.oracle_set_vcycle_full.restype = None
         lib.oracle_set_vcycle_partial.argtypes = [_P, _I]
         lib.oracle_set_vcycle_partial.restype = None
+        lib.oracle_set_prolongation.argtypes = [_P, _I]
+        lib.oracle_set_prolongation.restype = None
         lib.oracle_set_coarse_solve.argtypes = [_P, COARSE_SOLVE_FN]
         lib.oracle_set_coarse_solve.restype = None
         lib.oracle_bf16.argtypes = [_D]
@@ -323,6 +325,12 @@ class Oracle:
         """The V-cycle's operators use the general profiles of set_outer_profiles
         (TPMG^full) instead of the factorised ones (TPMG^fac)."""
         self._lib.oracle_set_vcycle_full(self._h, 1 if on else 0)
+
+    def set_prolongation(self, linear: bool = True):
+        """The V-cycle's prolongation: linear interpolation with a least-squares
+        tangent-plane gradient from the 3 coarse neighbours (the paper's Sec. 5), or with
+        linear=False the piecewise-constant P = R^T.  The restriction stays the sum."""
+        self._lib.oracle_set_prolongation(self._h, 1 if linear else 0)
 
     def set_vcycle_partial(self, on: bool = True):
         """The V-cycle's operators take alpha_r from the general profiles of

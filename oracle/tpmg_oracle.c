@@ -401,6 +401,8 @@ typedef struct {
      * three (TPMG^full), 2 alpha_r only, beta and alpha_S factorised (TPMG^partial, Sec. 5.3) */
     double **pl_beta, **pl_ar, **pl_aS, **pl_xi;
     int vc_full;
+    int prolong_linear;   /* 0: P = R^T, each child takes its parent's value (Reading C5);
+                             1: linear interpolation with a tangent-plane gradient (Reading C25) */
     /* multigrid work arrays per multigrid level (0 = coarsest)               */
     double **mg_f, **mg_u, **mg_r;
     double *col_a, *col_b, *col_c, *col_d, *col_x, *col_cp, *col_dp;
@@ -735,14 +737,66 @@ static void restrict_sum(const octx *o, int l_fine, const double *rf, double *fc
         }
 }
 
+/* Linear interpolation from the coarse cell T to its children (Sec. 5 prolongates
+ * "by linear interpolation"; Reading C25): the coarse field is taken as linear in the
+ * plane tangent to the sphere at the centre c_T, with the gradient g that fits the
+ * differences to the 3 coarse neighbours in least squares,
+ *     min_g sum_e (u_e - u_T - g . d_e)^2,   d_e = (c_e - c_T) projected onto the plane,
+ * and child t takes u_T + g . d_t, d_t = (c_t - c_T) projected.  In a basis (t1, t2) of
+ * the plane, with the rows x_e = (d_e . t1, d_e . t2), the normal equations are
+ * (sum_e x_e x_e^T) g = sum_e x_e (u_e - u_T); child t's weight on u_e - u_T is therefore
+ * w_te = x_t^T (sum x x^T)^{-1} x_e. */
+static void linear_weights(const octx *o, int l_fine, int T, double w[4][3])
+{
+    const ogrid *Gf = mg_grid(o, l_fine), *Gc = mg_grid(o, l_fine - 1);
+    const vec3 c = Gc->centre[T], nrm = v_unit(c);
+    double x[3][2], m00 = 0.0, m01 = 0.0, m11 = 0.0, det;
+    vec3 d[3], t1, t2;
+    int e, j;
+    for (e = 0; e < 3; ++e) {
+        vec3 v = v_sub(Gc->centre[Gc->nbr[3 * T + e]], c);
+        d[e] = v_sub(v, v_scale(nrm, v_dot(v, nrm)));
+    }
+    t1 = v_unit(d[0]);
+    t2 = v_cross(nrm, t1);
+    for (e = 0; e < 3; ++e) {
+        x[e][0] = v_dot(d[e], t1);
+        x[e][1] = v_dot(d[e], t2);
+        m00 += x[e][0] * x[e][0];
+        m01 += x[e][0] * x[e][1];
+        m11 += x[e][1] * x[e][1];
+    }
+    det = m00 * m11 - m01 * m01;
+    for (j = 0; j < 4; ++j) {
+        vec3 v = v_sub(Gf->centre[4 * T + j], c);
+        const vec3 dt = v_sub(v, v_scale(nrm, v_dot(v, nrm)));
+        const double px = v_dot(dt, t1), py = v_dot(dt, t2);
+        /* (px, py) M^{-1}, M^{-1} = [[m11, -m01], [-m01, m00]] / det */
+        const double qx = (px * m11 - py * m01) / det, qy = (py * m00 - px * m01) / det;
+        for (e = 0; e < 3; ++e) w[j][e] = qx * x[e][0] + qy * x[e][1];
+    }
+}
+
 static void prolong_add(const octx *o, int l_fine, const double *uc, double *uf)
 {
     const ogrid *Gc = mg_grid(o, l_fine - 1);
-    int n = o->n_r, T, j, k;
-    for (T = 0; T < Gc->n_cells; ++T)
+    int n = o->n_r, T, j, k, e;
+    double w[4][3];
+    for (T = 0; T < Gc->n_cells; ++T) {
+        if (o->prolong_linear) linear_weights(o, l_fine, T, w);
         for (j = 0; j < 4; ++j)
-            for (k = 0; k < n; ++k) uf[(size_t)(4 * T + j) * n + k] += uc[(size_t)T * n + k];
+            for (k = 0; k < n; ++k) {
+                const double uT = uc[(size_t)T * n + k];
+                double s = uT;
+                if (o->prolong_linear)
+                    for (e = 0; e < 3; ++e) s += w[j][e] * (uc[(size_t)Gc->nbr[3 * T + e] * n + k] - uT);
+                uf[(size_t)(4 * T + j) * n + k] += s;
+            }
+    }
 }
+
+/* on != 0: linear prolongation (Reading C25); 0: P = R^T (Reading C5) */
+void oracle_set_prolongation(void *h, int linear) { ((octx *)h)->prolong_linear = linear != 0; }
 
 /* Algorithm 1 on multigrid level l with RHS f and initial guess u (in/out).
  * Coarsest level: nu_coarse smoother sweeps (symmetric for block-SOR). */

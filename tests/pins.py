@@ -825,6 +825,50 @@ def pin_advection(ns):
     o.set_profiles()
 
 
+def pin_linear_prolongation(ns):
+    """Linear prolongation (Sec. 5: the solution is prolongated by linear interpolation;
+    reading C25: a least-squares gradient in the tangent plane from the 3 coarse
+    neighbours).  Constants are reproduced exactly; interpolating a smooth field from
+    the coarse centres to the fine ones errs by O(h^2) (the error falls about 4x per
+    refinement) where the piecewise-constant P = R^T errs by O(h) (about 2x); the
+    V-cycle with it converges, and BiCGStab with it reaches the dense solution."""
+    o = ns.Oracle(refinement=6, n_levels=4, n_r=1, H=0.01, courant_c=8.0)
+    n1 = o.level_cells(1)
+    o.set_prolongation(True)
+    c = 0.375
+    out = o.prolong_add(np.full(n1, c), np.zeros(4 * n1), 2)
+    assert np.all(out == c)
+    a, b = np.array([0.3, -0.7, 0.5]), np.array([0.6, 0.2, -0.4])
+    F = lambda x: x @ a + 2.0 * (x @ b) ** 2 + np.sin(3.0 * x[:, 2])
+    errs = {}
+    for linear in (True, False):
+        o.set_prolongation(linear)
+        e = []
+        for lf in (1, 2, 3):
+            xc = o.grid(o.level_ref(lf - 1))["centre"]
+            xf = o.grid(o.level_ref(lf))["centre"]
+            e.append(np.max(np.abs(o.prolong_add(F(xc), np.zeros(len(xf)), lf) - F(xf))))
+        errs[linear] = e
+    lin, con = errs[True], errs[False]
+    assert all(lin[i] / lin[i + 1] > 3.3 for i in range(2)), lin
+    assert all(con[i] / con[i + 1] < 2.5 for i in range(2)), con
+    assert lin[-1] < 0.2 * con[-1]
+    # in a V-cycle (sum restriction, linear prolongation): Richardson converges, and
+    # BiCGStab reaches the dense solution
+    o = ns.Oracle(refinement=3, n_levels=3, n_r=8, grading=1.1, H=0.05, courant_c=20.0)
+    o.set_prolongation(True)
+    rho = convergence_factor(o)
+    assert rho < 0.5, rho
+    o = ns.Oracle(refinement=2, n_levels=2, n_r=6, grading=1.1, H=0.05, courant_c=20.0)
+    o.set_prolongation(True)
+    f = inputs.uniform_pm1(inputs.SEED_UNIFORM_SMALL + 95, o.size())
+    res = o.bicgstab(f, rtol=1e-12, max_iter=200)
+    assert res["status"] == 0
+    A = o.dense_operator()
+    ud = np.linalg.solve(A, f)
+    assert np.linalg.norm(res["u"] - ud) <= 1e-9 * np.linalg.norm(ud)
+
+
 def pin_manufactured(ns):
     """Manufactured solution: f = A u*, solve to rtol 1e-12, recover u* in the
     energy norm to 1e-9 (a residual drop of 1e-12 bounds the error by cond-weighted 1e-12)."""
@@ -867,5 +911,5 @@ ALL_PINS = [
     pin_vertical_consistency, pin_thomas, pin_column_solve_exact, pin_transfers, pin_vcycle_dense, pin_preconditioner_symmetric,
     pin_invariant_subspaces, pin_pcg_dense, pin_bf16_rounding, pin_flexible_cg, pin_bf16_vcycle,
     pin_manufactured, pin_robust_convergence, pin_bicgstab, pin_profiles, pin_outer_operator,
-    pin_partial_profiles, pin_advection,
+    pin_partial_profiles, pin_advection, pin_linear_prolongation,
 ]

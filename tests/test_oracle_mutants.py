@@ -70,6 +70,11 @@ MUTANTS = {
                                    "static int full_now(const octx *o) { return o->vc_full >= 1 && o->pl_beta; }"),
     "partial_keeps_factorised_alphar": ("static int general_ar_now(const octx *o) { return o->vc_full >= 1 && o->pl_ar; }",
                                         "static int general_ar_now(const octx *o) { return o->vc_full == 1 && o->pl_ar; }"),
+    "linear_parent_not_subtracted": ("s += w[j][e] * (uc[(size_t)Gc->nbr[3 * T + e] * n + k] - uT);",
+                                     "s += w[j][e] * uc[(size_t)Gc->nbr[3 * T + e] * n + k];"),
+    "linear_inverse_transposed": ("const double qx = (px * m11 - py * m01) / det",
+                                  "const double qx = (px * m00 - py * m01) / det"),
+    "linear_same_child": ("vec3 v = v_sub(Gf->centre[4 * T + j], c);", "vec3 v = v_sub(Gf->centre[4 * T], c);"),
     "bf16_truncates": ("return ldexp(rint(ldexp(m, 8)), e - 8);", "return ldexp(floor(ldexp(m, 8)), e - 8);"),
     "vertical_missing_r2": ("2.0 * o->r[k] * o->r[k] / (o->zeta[k + 1] - o->zeta[k - 1])",
                             "2.0 / (o->zeta[k + 1] - o->zeta[k - 1])"),
