@@ -82,6 +82,16 @@ enum { TPMG_OUTER_CG = 0,          /* preconditioned CG (flexible CG in the mixe
        TPMG_OUTER_RICHARDSON = 1,  /* u <- u + B (f - A u) */
        TPMG_OUTER_BICGSTAB = 2 };  /* BiCGStab, preconditioned from the right (2 V-cycles per iteration) */
 
+/* Prolongation of the V-cycle (Algorithm 1's correction u_h += P u_2h).  The restriction
+ * is always the sum over the 4 children (Sec. 5).
+ *   CONSTANT: each child takes its parent's value, P = R^T, which keeps B symmetric for CG;
+ *   LINEAR:   linear interpolation, the paper's own choice (Sec. 5): the coarse field is
+ *             linear in the plane tangent to the sphere at the parent's centre, with the
+ *             least-squares gradient of the differences to its 3 neighbours, and each child
+ *             takes its value at the child's centre.  B is then not symmetric: tpmg_solve
+ *             needs params.outer Richardson or BiCGStab. */
+enum { TPMG_PROLONG_CONSTANT = 0, TPMG_PROLONG_LINEAR = 1 };
+
 /* Cell centre used by the two-point flux of Appendix A. */
 enum { TPMG_CENTRE_CIRCUM = 0,      /* spherical circumcentre (centre chord normal to the edge) */
        TPMG_CENTRE_VERTEX_MEAN = 1 };
@@ -125,12 +135,13 @@ typedef struct {
     int    outer;        /* TPMG_OUTER_*: the outer iteration of tpmg_solve.  Richardson and
                             BiCGStab run their loop from the host (one read-back per dot product)
                             and are not available in a batch. */
+    int    prolongation; /* TPMG_PROLONG_*: the V-cycle's coarse-to-fine transfer */
 } tpmg_params;
 
 /* Fills *p with the defaults: refinement 3, n_levels 4, n_r 16, H = 10/6371,
  * grading 1, omega2 0 with courant_c 8, nu 2/2/1, block-SOR with relax 1,
  * factorised storage, circumcentres, FP64, graphs and autotuning on,
- * scan_max_cells 5120, outer CG.  Returns TPMG_ERR_INVALID_ARG if p is NULL. */
+ * scan_max_cells 5120, outer CG, constant prolongation.  Returns TPMG_ERR_INVALID_ARG if p is NULL. */
 tpmg_status tpmg_default_params(tpmg_params *p);
 
 /* Factorised profiles (Sec. 2, eq. profiles): alpha_r(r, x) = alpha_r^r(r) alpha_r^S(x),
@@ -247,8 +258,9 @@ tpmg_status tpmg_vcycle_noalloc(tpmg_ctx *ctx, const double *d_r, double *d_z);
  * for k = 0..*iters.  Synchronises the context stream before returning.
  * Returns OK, NOT_CONVERGED (iters = max_iter), BREAKDOWN (p.Ap <= 0 or a
  * non-finite norm; the solution holds the last finite iterate), INVALID_ARG, CUDA.
- * With vertical advection (xi in the profiles) the operator is not symmetric and CG
- * does not apply: INVALID_ARG unless params.outer is Richardson or BiCGStab.
+ * With vertical advection (xi in the profiles) the operator, and with linear
+ * prolongation the V-cycle, is not symmetric, and CG does not apply: INVALID_ARG unless
+ * params.outer is Richardson or BiCGStab.
  * With graphs on (and no kernel class being timed) the whole solve is one graph
  * launch with the loop on the device; otherwise the host drives the loop.
  * Both run the same kernels in the same order. */
@@ -273,7 +285,7 @@ tpmg_status tpmg_solve_host(tpmg_ctx *ctx, const double *h_f, double *h_u, doubl
  * vectors live.  A context may belong to one batch and must not run another
  * solve while its batch runs.  max_iter < 4096.
  * Errors: INVALID_ARG (NULL, repeated context, other device, a context with
- * vertical advection), OOM, CUDA. */
+ * vertical advection or linear prolongation), OOM, CUDA. */
 typedef struct tpmg_batch tpmg_batch;
 tpmg_status tpmg_batch_create(tpmg_ctx *const *ctxs, int n, const double *const *d_f, double *const *d_u,
                               double rtol, int max_iter, tpmg_batch **out);

@@ -29,6 +29,8 @@ TPMG_SMOOTH_JACOBI = 1
 TPMG_COEFF_FACTORISED = 0
 TPMG_COEFF_FULL = 1
 TPMG_COEFF_PARTIAL = 2
+TPMG_PROLONG_CONSTANT = 0
+TPMG_PROLONG_LINEAR = 1
 TPMG_CENTRE_CIRCUM = 0
 TPMG_CENTRE_VERTEX_MEAN = 1
 TPMG_PREC_FP64 = 0
@@ -69,7 +71,7 @@ class tpmg_params(ctypes.Structure):
                 ("nu_coarse", ctypes.c_int), ("smoother", ctypes.c_int), ("relax", ctypes.c_double),
                 ("coeff_storage", ctypes.c_int), ("centre", ctypes.c_int), ("precision", ctypes.c_int),
                 ("graphs", ctypes.c_int), ("autotune", ctypes.c_int), ("scan_max_cells", ctypes.c_int),
-                ("outer", ctypes.c_int)]
+                ("outer", ctypes.c_int), ("prolongation", ctypes.c_int)]
 
 
 class tpmg_profiles(ctypes.Structure):

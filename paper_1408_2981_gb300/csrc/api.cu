@@ -175,6 +175,9 @@ bool validate(const tpmg_params *p, std::string &msg)
     if (p->autotune != 0 && p->autotune != 1) { msg = "autotune must be 0 or 1"; return false; }
     if (p->scan_max_cells < 0) { msg = "scan_max_cells must be >= 0"; return false; }
     if (p->outer < TPMG_OUTER_CG || p->outer > TPMG_OUTER_BICGSTAB) { msg = "unknown outer iteration"; return false; }
+    if (p->prolongation != TPMG_PROLONG_CONSTANT && p->prolongation != TPMG_PROLONG_LINEAR) {
+        msg = "unknown prolongation"; return false;
+    }
     return true;
 }
 
@@ -219,9 +222,11 @@ bool copy_vertical(const double *v, int n, std::vector<double> &out, bool any_si
     return true;
 }
 
-// The solver may run CG only on a symmetric operator: vertical advection (factorised,
-// or in the outer operator's general profiles) makes it non-symmetric.
+// The solver may run CG only with a symmetric operator and V-cycle: vertical advection
+// (factorised, or in the outer operator's general profiles) makes the operator
+// non-symmetric, linear prolongation the V-cycle.
 bool has_advection(const tpmg_ctx *ctx) { return ctx->xi_fac || (!ctx->lv.empty() && ctx->lv.back().cvx); }
+bool nonsymmetric(const tpmg_ctx *ctx) { return has_advection(ctx) || ctx->p.prolongation == TPMG_PROLONG_LINEAR; }
 
 cudaError_t grow_events(Tracer &t, size_t pairs)
 {
@@ -287,6 +292,18 @@ tpmg_status vcycle_level(tpmg_ctx *ctx, int l, const double *f, double *u, doubl
     const double nunits = (double)lv.n * p.n_r;
     const size_t nbytes = sizeof(double) * lv.n * p.n_r;
     double *cur = u, *oth = scratch;   // Jacobi: current iterate / other buffer
+    // a coarse level adds its result into the 4 children of u_fine: fused into the pass
+    // that writes each column's final value (P = R^T), or after the level's last pass
+    // (linear prolongation, which reads the 3 neighbours' final values too)
+    const bool lin = u_fine && p.prolongation == TPMG_PROLONG_LINEAR;
+    double *const fuse = lin ? nullptr : u_fine;
+    auto prolong_linear = [&]() -> tpmg_status {
+        const LevelDev &fl = ctx->lv[l + 1];
+        const double *cc = cur;
+        LCHK(run(ctx, TPMG_K_PROLONG, (double)fl.n * p.n_r,
+                 [&] { return launch_prolong_linear(L, fl, lv, cc, u_fine); }));
+        return TPMG_OK;
+    };
     // one multicolour block-SOR pass over colour c, in place in u
     auto pass = [&](int c, int mode, double *fine) -> cudaError_t {
         const int t0 = lv.colour_task_off[c], nt = lv.colour_task_off[c + 1] - t0;
@@ -313,12 +330,16 @@ tpmg_status vcycle_level(tpmg_ctx *ctx, int l, const double *f, double *u, doubl
         for (int s = 0; s < p.nu_coarse; ++s) {
             const bool last = s == p.nu_coarse - 1;
             if (jac) {
-                LCHK(jacobi(s == 0 ? PASS_ZERO : PASS_NORMAL, last ? u_fine : nullptr));
+                LCHK(jacobi(s == 0 ? PASS_ZERO : PASS_NORMAL, last ? fuse : nullptr));
                 continue;
             }
             for (int c = 0; c < C; ++c)
-                LCHK(pass(c, s == 0 ? PASS_ZERO : PASS_NORMAL, last && c == C - 1 ? u_fine : nullptr));
-            for (int c = C - 2; c >= 0; --c) LCHK(pass(c, PASS_NORMAL, last ? u_fine : nullptr));
+                LCHK(pass(c, s == 0 ? PASS_ZERO : PASS_NORMAL, last && c == C - 1 ? fuse : nullptr));
+            for (int c = C - 2; c >= 0; --c) LCHK(pass(c, PASS_NORMAL, last ? fuse : nullptr));
+        }
+        if (lin) {
+            const tpmg_status st = prolong_linear();
+            if (st != TPMG_OK) return st;
         }
     } else {
         // pre-smoothing (forward colour order)
@@ -341,12 +362,15 @@ tpmg_status vcycle_level(tpmg_ctx *ctx, int l, const double *f, double *u, doubl
         for (int s = 0; s < p.nu_post; ++s) {
             const bool last = s == p.nu_post - 1;
             if (jac) {
-                LCHK(jacobi(PASS_NORMAL, last ? u_fine : nullptr));
+                LCHK(jacobi(PASS_NORMAL, last ? fuse : nullptr));
                 continue;
             }
-            for (int c = C - 1; c >= 0; --c) LCHK(pass(c, PASS_NORMAL, last ? u_fine : nullptr));
+            for (int c = C - 1; c >= 0; --c) LCHK(pass(c, PASS_NORMAL, last ? fuse : nullptr));
         }
-        if (p.nu_post == 0 && u_fine) {
+        if (lin) {
+            const tpmg_status st = prolong_linear();
+            if (st != TPMG_OK) return st;
+        } else if (p.nu_post == 0 && u_fine) {
             const LevelDev &fl = ctx->lv[l + 1];
             const double *cc = cur;
             LCHK(run(ctx, TPMG_K_PROLONG, (double)fl.n * p.n_r,
@@ -430,6 +454,16 @@ tpmg_status vcycle_mixed(tpmg_ctx *ctx, int l, const TF *f, float *u, float *scr
     const double nunits = (double)lv.n * p.n_r;
     const size_t nbytes = sizeof(float) * lv.n * p.n_r;
     float *cur = u, *oth = scratch;
+    // the coarse-to-fine transfer as in vcycle_level: fused into the final pass, or the
+    // linear prolongation after the level's last pass
+    const bool lin = u_fine && p.prolongation == TPMG_PROLONG_LINEAR;
+    float *const fuse = lin ? nullptr : u_fine;
+    auto prolong_linear = [&](const float *cc) -> tpmg_status {
+        const LevelDev &fl = ctx->lv[l + 1];
+        LCHK(run(ctx, TPMG_K_PROLONG, (double)fl.n * p.n_r,
+                 [&] { return launch_prolong_linear32(L, fl, lv, cc, u_fine); }));
+        return TPMG_OK;
+    };
     auto pass = [&](int c, int mode, float *fine, double *out) -> cudaError_t {
         const int t0 = lv.colour_task_off[c], nt = lv.colour_task_off[c + 1] - t0;
         const int m = (mode == PASS_ZERO && c == 0) ? PASS_RHS_ONLY : mode;
@@ -462,9 +496,9 @@ tpmg_status vcycle_mixed(tpmg_ctx *ctx, int l, const TF *f, float *u, float *scr
                 tpmg_status st = net_infer<float, float>(ctx, TPMG_NET_COARSE, lv, f, scratch);
                 if (st != TPMG_OK) return st;
                 LCHK(run(ctx, TPMG_K_RELAX, nunits, [&] {
-                    return launch_relax32<float>(L, lv, PASS_NORMAL, 0, lv.n_tasks, relax, f, scratch, u, u_fine, nullptr);
+                    return launch_relax32<float>(L, lv, PASS_NORMAL, 0, lv.n_tasks, relax, f, scratch, u, fuse, nullptr);
                 }));
-                return TPMG_OK;
+                return lin ? prolong_linear(u) : TPMG_OK;
             }
         }
         if (p.nu_coarse == 0) {
@@ -474,17 +508,17 @@ tpmg_status vcycle_mixed(tpmg_ctx *ctx, int l, const TF *f, float *u, float *scr
         for (int s = 0; s < p.nu_coarse; ++s) {
             const bool last = s == p.nu_coarse - 1;
             if (jac) {
-                LCHK(jacobi(s == 0 ? PASS_ZERO : PASS_NORMAL, last ? u_fine : nullptr, last ? z64 : nullptr));
+                LCHK(jacobi(s == 0 ? PASS_ZERO : PASS_NORMAL, last ? fuse : nullptr, last ? z64 : nullptr));
                 continue;
             }
             for (int c = 0; c < C; ++c) {
                 const bool fin = last && c == C - 1;
-                LCHK(pass(c, s == 0 ? PASS_ZERO : PASS_NORMAL, fin ? u_fine : nullptr, fin ? z64 : nullptr));
+                LCHK(pass(c, s == 0 ? PASS_ZERO : PASS_NORMAL, fin ? fuse : nullptr, fin ? z64 : nullptr));
             }
             for (int c = C - 2; c >= 0; --c)
-                LCHK(pass(c, PASS_NORMAL, last ? u_fine : nullptr, last ? z64 : nullptr));
+                LCHK(pass(c, PASS_NORMAL, last ? fuse : nullptr, last ? z64 : nullptr));
         }
-        return TPMG_OK;
+        return lin ? prolong_linear(cur) : TPMG_OK;
     }
     if (p.nu_pre == 0) LCHK(clear(cur));
     for (int s = 0; s < p.nu_pre; ++s) {
@@ -503,14 +537,18 @@ tpmg_status vcycle_mixed(tpmg_ctx *ctx, int l, const TF *f, float *u, float *scr
     for (int s = 0; s < p.nu_post; ++s) {
         const bool last = s == p.nu_post - 1;
         if (jac) {
-            LCHK(jacobi(PASS_NORMAL, last ? u_fine : nullptr, last ? z64 : nullptr));
+            LCHK(jacobi(PASS_NORMAL, last ? fuse : nullptr, last ? z64 : nullptr));
             continue;
         }
-        for (int c = C - 1; c >= 0; --c) LCHK(pass(c, PASS_NORMAL, last ? u_fine : nullptr, last ? z64 : nullptr));
+        for (int c = C - 1; c >= 0; --c) LCHK(pass(c, PASS_NORMAL, last ? fuse : nullptr, last ? z64 : nullptr));
+    }
+    if (lin) {
+        const tpmg_status st2 = prolong_linear(cur);
+        if (st2 != TPMG_OK) return st2;
     }
     if (p.nu_post == 0) {
         const float *cc = cur;
-        if (u_fine) {
+        if (fuse) {
             const LevelDev &fl = ctx->lv[l + 1];
             LCHK(run(ctx, TPMG_K_PROLONG, (double)fl.n * p.n_r,
                      [&] { return launch_prolong_add32(L, fl, cc, u_fine); }));
@@ -1123,6 +1161,52 @@ tpmg_status upload_advection(tpmg_ctx *ctx, const HostLevel &H, LevelDev &D, con
     return TPMG_OK;
 }
 
+// Weights of the linear prolongation from coarse level H to its children on level
+// Hf (Sec. 5; see TPMG_PROLONG_LINEAR): for coarse cell T with centre c and unit
+// normal n, an orthonormal basis (a, b) of the tangent plane is built from the
+// coordinate axis least aligned with n; the 3 neighbours' offsets c_e - c give rows
+// x_e = ((c_e - c).a, (c_e - c).b), the children's offsets y_j likewise, and child j's
+// weight on u_e - u_T is y_j^T (X^T X)^{-1} x_e (the least-squares gradient).
+void prolong_weights(const HostLevel &H, const HostLevel &Hf, std::vector<double> &w)
+{
+    w.assign((size_t)H.n * 12, 0.0);
+    auto cen = [](const HostLevel &L, int T) { return &L.centre[3 * (size_t)T]; };
+    for (int T = 0; T < H.n; ++T) {
+        const double *c = cen(H, T);
+        const double len = std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+        const double n[3] = {c[0] / len, c[1] / len, c[2] / len};
+        int ax = 0;
+        for (int d = 1; d < 3; ++d)
+            if (std::fabs(n[d]) < std::fabs(n[ax])) ax = d;
+        double a[3] = {0.0, 0.0, 0.0};
+        a[ax] = 1.0;
+        const double an = a[ax] * n[ax];
+        for (int d = 0; d < 3; ++d) a[d] -= an * n[d];
+        const double al = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+        for (int d = 0; d < 3; ++d) a[d] /= al;
+        const double b[3] = {n[1] * a[2] - n[2] * a[1], n[2] * a[0] - n[0] * a[2], n[0] * a[1] - n[1] * a[0]};
+        auto coords = [&](const double *p, double &x, double &y) {
+            const double d0 = p[0] - c[0], d1 = p[1] - c[1], d2 = p[2] - c[2];
+            x = d0 * a[0] + d1 * a[1] + d2 * a[2];
+            y = d0 * b[0] + d1 * b[1] + d2 * b[2];
+        };
+        double ex[3], ey[3], sxx = 0.0, sxy = 0.0, syy = 0.0;
+        for (int e = 0; e < 3; ++e) {
+            coords(cen(H, H.nbr[3 * T + e]), ex[e], ey[e]);
+            sxx += ex[e] * ex[e];
+            sxy += ex[e] * ey[e];
+            syy += ey[e] * ey[e];
+        }
+        const double det = sxx * syy - sxy * sxy;
+        for (int j = 0; j < 4; ++j) {
+            double yx, yy;
+            coords(cen(Hf, 4 * T + j), yx, yy);
+            const double gx = (syy * yx - sxy * yy) / det, gy = (sxx * yy - sxy * yx) / det;
+            for (int e = 0; e < 3; ++e) w[(size_t)T * 12 + 3 * j + e] = gx * ex[e] + gy * ey[e];
+        }
+    }
+}
+
 // General per-unknown profiles of one level from the next finer (m values per cell):
 // each coarse (cell, j) the area-weighted mean over the 4 children's (cell, j).
 std::vector<double> average_children(const HostLevel &fine, const std::vector<double> &pf, int m)
@@ -1267,6 +1351,19 @@ tpmg_status upload_level(tpmg_ctx *ctx, int l)
         const tpmg_status st = upload_advection(ctx, H, D, nullptr, nullptr);
         if (st != TPMG_OK) return st;
     }
+    std::vector<double> pw;   // linear prolongation weights, alive until the final synchronise
+    std::vector<float> pw32;
+    if (p.prolongation == TPMG_PROLONG_LINEAR && l < p.n_levels - 1) {
+        prolong_weights(H, ctx->host.lev[H.ref + 1], pw);
+        if (mixed) {
+            pw32.assign(pw.begin(), pw.end());
+            CU(dalloc(ctx, &D.plin32, pw32.size()));
+            CU(cudaMemcpyAsync(D.plin32, pw32.data(), pw32.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+        } else {
+            CU(dalloc(ctx, &D.plin, pw.size()));
+            CU(cudaMemcpyAsync(D.plin, pw.data(), pw.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        }
+    }
     if (!mixed) {
         CU(launch_twisted_factors(launch_of(ctx), D, ctx->vert));
         if (D.scan) CU(launch_thomas_factors(launch_of(ctx), D, ctx->vert));
@@ -1356,6 +1453,7 @@ tpmg_status tpmg_default_params(tpmg_params *p)
     p->autotune = 1;
     p->scan_max_cells = 5120;
     p->outer = TPMG_OUTER_CG;
+    p->prolongation = TPMG_PROLONG_CONSTANT;
     return TPMG_OK;
 }
 
@@ -1678,8 +1776,8 @@ tpmg_status tpmg_solve(tpmg_ctx *ctx, const double *d_f, double *d_u, double rto
     if (!ctx || !d_f || !d_u || !iters || !rel_resid) return fail(ctx, TPMG_ERR_INVALID_ARG, "NULL argument");
     if (!(rtol >= 0.0) || max_iter < 0) return fail(ctx, TPMG_ERR_INVALID_ARG, "rtol must be >= 0, max_iter >= 0");
     if (d_f == d_u) return fail(ctx, TPMG_ERR_INVALID_ARG, "f and u must not overlap");
-    if (has_advection(ctx) && ctx->p.outer == TPMG_OUTER_CG)
-        return fail(ctx, TPMG_ERR_INVALID_ARG, "vertical advection makes the operator non-symmetric: CG does not apply (use Richardson or BiCGStab)");
+    if (nonsymmetric(ctx) && ctx->p.outer == TPMG_OUTER_CG)
+        return fail(ctx, TPMG_ERR_INVALID_ARG, "vertical advection or linear prolongation: the operator or the V-cycle is not symmetric, so CG does not apply (use Richardson or BiCGStab)");
     // the device-side loop cannot carry the event pairs of a timed kernel class
     if (ctx->p.outer == TPMG_OUTER_CG && ctx->p.graphs && ctx->tr.mask == 0 && max_iter < kHistCap)
         return pcg_graph(ctx, d_f, d_u, rtol, max_iter, iters, rel_resid, resid_hist);
@@ -1701,7 +1799,7 @@ tpmg_status tpmg_batch_create(tpmg_ctx *const *ctxs, int n, const double *const 
     for (int i = 0; i < n; ++i) {
         if (!ctxs[i] || !d_f[i] || !d_u[i] || d_f[i] == d_u[i] || ctxs[i]->device != dev) return TPMG_ERR_INVALID_ARG;
         if (ctxs[i]->p.outer != TPMG_OUTER_CG) return TPMG_ERR_INVALID_ARG;   // batches hold device-side CG loops
-        if (has_advection(ctxs[i])) return TPMG_ERR_INVALID_ARG;             // which need a symmetric operator
+        if (nonsymmetric(ctxs[i])) return TPMG_ERR_INVALID_ARG;              // which need a symmetric A and B
         for (int k = 0; k < i; ++k)
             if (ctxs[k] == ctxs[i]) return TPMG_ERR_INVALID_ARG;   // one problem per context
     }
@@ -1764,8 +1862,8 @@ tpmg_status tpmg_solve_host(tpmg_ctx *ctx, const double *h_f, double *h_u, doubl
 {
     if (!ctx || !h_f || !h_u || !iters || !rel_resid) return fail(ctx, TPMG_ERR_INVALID_ARG, "NULL argument");
     if (!(rtol >= 0.0) || max_iter < 0) return fail(ctx, TPMG_ERR_INVALID_ARG, "rtol must be >= 0, max_iter >= 0");
-    if (has_advection(ctx) && ctx->p.outer == TPMG_OUTER_CG)
-        return fail(ctx, TPMG_ERR_INVALID_ARG, "vertical advection makes the operator non-symmetric: CG does not apply (use Richardson or BiCGStab)");
+    if (nonsymmetric(ctx) && ctx->p.outer == TPMG_OUTER_CG)
+        return fail(ctx, TPMG_ERR_INVALID_ARG, "vertical advection or linear prolongation: the operator or the V-cycle is not symmetric, so CG does not apply (use Richardson or BiCGStab)");
     const size_t bytes = sizeof(double) * ctx->N;
     CU(cudaMemcpyAsync(ctx->hf, h_f, bytes, cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(ctx->hu, h_u, bytes, cudaMemcpyHostToDevice, ctx->stream));
@@ -2020,8 +2118,9 @@ tpmg_status tpmg_solve_learned(tpmg_ctx *ctx, const double *d_f, double *d_u, do
     if (!ctx || !d_f || !d_u || !iters || !rel_resid) return fail(ctx, TPMG_ERR_INVALID_ARG, "NULL argument");
     if (ctx->p.precision != TPMG_PREC_MIXED)
         return fail(ctx, TPMG_ERR_INVALID_ARG, "the learned solve needs the mixed-precision form");
-    if (has_advection(ctx))
-        return fail(ctx, TPMG_ERR_INVALID_ARG, "the learned solve runs flexible CG, which needs a symmetric operator");
+    if (nonsymmetric(ctx))
+        return fail(ctx, TPMG_ERR_INVALID_ARG, "the learned solve runs flexible CG, which needs a symmetric operator "
+                                               "and V-cycle");
     if (!(rtol >= 0.0) || max_iter < 1 || max_iter >= kHistCap)
         return fail(ctx, TPMG_ERR_INVALID_ARG, "rtol must be >= 0, max_iter in 1..4095");
     if (d_f == d_u) return fail(ctx, TPMG_ERR_INVALID_ARG, "f and u must not overlap");

@@ -284,6 +284,27 @@ __global__ void __launch_bounds__(NT) k_resid_restrict(OpView o, const double *_
     }
 }
 
+// Linear prolongation (Sec. 5): child j of coarse cell T takes
+//   u_T + sum_e w_{T,j,e} (u_{nbr e} - u_T)
+// per vertical index, the weights those of the least-squares tangent-plane gradient
+// (set-up); one thread per fine unknown, coalesced along k.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_prolong_linear(const int4 *__restrict__ nbr_c, const double *__restrict__ w,
+                                                       const double *__restrict__ uc, double *__restrict__ u,
+                                                       int n_r, int N)
+{
+    for (int i = blockIdx.x * NT + threadIdx.x; i < N; i += gridDim.x * NT) {
+        const int t = i / n_r, k = i - t * n_r, T = t >> 2, j = t & 3;
+        const int4 nb = __ldg(&nbr_c[T]);
+        const double *wt = w + (size_t)T * 12 + 3 * j;
+        const double v = uc[(size_t)T * n_r + k];
+        double s = fma(__ldg(&wt[0]), uc[(size_t)nb.x * n_r + k] - v, v);
+        s = fma(__ldg(&wt[1]), uc[(size_t)nb.y * n_r + k] - v, s);
+        s = fma(__ldg(&wt[2]), uc[(size_t)nb.z * n_r + k] - v, s);
+        u[i] += s;
+    }
+}
+
 template <int NT>
 __global__ void __launch_bounds__(NT) k_prolong_add(const double *__restrict__ uc, double *__restrict__ u, int n_r, int N)
 {
@@ -1075,6 +1096,15 @@ cudaError_t launch_prolong_add(const Launch &L, const LevelDev &fine, const doub
 {
     const int N = fine.n * L.n_r;
     k_prolong_add<kThreads><<<grid_for(N, kThreads, L.sm_count), kThreads, 0, L.s>>>(uc, u, L.n_r, N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_linear(const Launch &L, const LevelDev &fine, const LevelDev &coarse, const double *uc,
+                                  double *u)
+{
+    const int N = fine.n * L.n_r;
+    k_prolong_linear<kThreads><<<grid_for(N, kThreads, L.sm_count), kThreads, 0, L.s>>>(coarse.nbr, coarse.plin, uc, u,
+                                                                                        L.n_r, N);
     return cudaGetLastError();
 }
 

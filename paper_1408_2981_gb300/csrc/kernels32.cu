@@ -207,6 +207,24 @@ __global__ void __launch_bounds__(kThreads32)
     }
 }
 
+// Linear prolongation in FP32 (the FP64 kernel's arithmetic on the FP32 weights).
+__global__ void __launch_bounds__(kThreads32) k_prolong_linear32(const int4 *__restrict__ nbr_c,
+                                                                 const float *__restrict__ w,
+                                                                 const float *__restrict__ uc, float *__restrict__ u,
+                                                                 int n_r, int N)
+{
+    for (int i = blockIdx.x * kThreads32 + threadIdx.x; i < N; i += gridDim.x * kThreads32) {
+        const int t = i / n_r, k = i - t * n_r, T = t >> 2, j = t & 3;
+        const int4 nb = __ldg(&nbr_c[T]);
+        const float *wt = w + (size_t)T * 12 + 3 * j;
+        const float v = uc[(size_t)T * n_r + k];
+        float s = fmaf(__ldg(&wt[0]), uc[(size_t)nb.x * n_r + k] - v, v);
+        s = fmaf(__ldg(&wt[1]), uc[(size_t)nb.y * n_r + k] - v, s);
+        s = fmaf(__ldg(&wt[2]), uc[(size_t)nb.z * n_r + k] - v, s);
+        u[i] += s;
+    }
+}
+
 __global__ void __launch_bounds__(kThreads32) k_prolong_add32(const float *__restrict__ uc, float *__restrict__ u,
                                                               int n_r, int N)
 {
@@ -283,6 +301,14 @@ cudaError_t launch_prolong_add32(const Launch &L, const LevelDev &fine, const fl
 {
     const int N = fine.n * L.n_r;
     k_prolong_add32<<<grid32(N, L.sm_count), kThreads32, 0, L.s>>>(uc, u, L.n_r, N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_linear32(const Launch &L, const LevelDev &fine, const LevelDev &coarse, const float *uc,
+                                    float *u)
+{
+    const int N = fine.n * L.n_r;
+    k_prolong_linear32<<<grid32(N, L.sm_count), kThreads32, 0, L.s>>>(coarse.nbr, coarse.plin32, uc, u, L.n_r, N);
     return cudaGetLastError();
 }
 

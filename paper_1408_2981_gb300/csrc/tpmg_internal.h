@@ -111,6 +111,10 @@ struct LevelDev {
     // mixed precision: X of face k in BF16 per unknown [n][n_r], used while cxv_on
     unsigned short *cxv = nullptr;
     bool cxv_on = false;
+    // linear prolongation to the next finer level (coarse levels only): [n][4][3] the
+    // weight of child j on (u_{nbr e} - u_T), in FP64 and FP32
+    double *plin = nullptr;
+    float *plin32 = nullptr;
     float *iarea32 = nullptr;     // [n] 1 / |T| (network features of the learned form)
     float4 *wnb32 = nullptr;      // [n] {g0, g1, g2} / (g0 + g1 + g2), 0
     int *task_cells = nullptr;    // [n_tasks][16] cell ids, -1 = padding
@@ -193,6 +197,8 @@ cudaError_t launch_resid_restrict(const Launch &L, const LevelDev &fine, const L
 cudaError_t launch_relax(const Launch &L, const LevelDev &lv, const VertDev &v, int mode, int task0, int n_tasks,
                          double relax, const double *f, const double *u_in, double *u_out, double *u_fine);
 cudaError_t launch_prolong_add(const Launch &L, const LevelDev &fine, const double *uc, double *u);
+cudaError_t launch_prolong_linear(const Launch &L, const LevelDev &fine, const LevelDev &coarse, const double *uc,
+                                  double *u);
 cudaError_t launch_twisted_factors(const Launch &L, const LevelDev &lv, const VertDev &v);
 cudaError_t launch_thomas_factors(const Launch &L, const LevelDev &lv, const VertDev &v);
 // Mixed-precision V-cycle (FP32 arithmetic, BF16 stencil).  TF is the type of
@@ -204,6 +210,8 @@ template <typename TF>
 cudaError_t launch_resid_restrict32(const Launch &L, const LevelDev &fine, const LevelDev &coarse, const TF *f,
                                     const float *u, float *fc);
 cudaError_t launch_prolong_add32(const Launch &L, const LevelDev &fine, const float *uc, float *u);
+cudaError_t launch_prolong_linear32(const Launch &L, const LevelDev &fine, const LevelDev &coarse, const float *uc,
+                                    float *u);
 cudaError_t launch_to_f64(const Launch &L, long n, const float *x, double *y);
 cudaError_t launch_thomas_factors32(const Launch &L, const LevelDev &lv);
 cudaError_t launch_dot(const Launch &L, long n, const double *a, const double *b, double *partials, int n_part);

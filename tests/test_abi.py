@@ -50,7 +50,7 @@ def test_default_params_on_host(lib):
                                  dict(n_r=0), dict(n_r=2000), dict(H=0.0), dict(grading=-1.0),
                                  dict(omega2=0.0, courant_c=0.0), dict(nu_pre=-1), dict(smoother=7),
                                  dict(relax=0.0), dict(relax=2.0), dict(centre=3), dict(coeff_storage=9),
-                                 dict(precision=9), dict(precision=1, coeff_storage=0), dict(precision=1, coeff_storage=2),
+                                 dict(precision=9), dict(precision=1, coeff_storage=0), dict(precision=1, coeff_storage=2), dict(prolongation=2),
                                  dict(refinement=9, n_levels=3, n_r=1024), dict(scan_max_cells=-1), dict(outer=3)])
 def test_setup_rejects_bad_params_before_touching_cuda(lib, bad):
     p = binding.default_params(**bad)
