@@ -107,6 +107,12 @@ WORKLOADS = {
              "icosahedral refinement 5 x 128 levels graded 1.05 over 10 km (2.6M unknowns), omega^2/h^2=8, RHS "
              "uniform[-1,1], 6 MG levels, nu 2/2/1, rtol 1e-5; TPMG^fac, TPMG^partial, TPMG^full (FP64) and "
              "TPMG^full (mixed precision) with Richardson, CG and BiCGStab"),
+    "prolongation": dict(
+        study="prolongation", seed=2981006,
+        params=dict(refinement=6, n_levels=6, n_r=64, grading=1.05, courant_c=80.0, nu_pre=2, nu_post=2, nu_coarse=1),
+        text="piecewise-constant (P = R^T) against linear prolongation (Sec. 5) on the 81920x64 grid: RHS "
+             "uniform[-1,1] (rough, so that the transfer matters), rtol 1e-5, FP64 and mixed-precision V-cycles, "
+             "Richardson and BiCGStab"),
     "batch48": dict(
         batch=48, seed=2981004,
         text="48 independent solves in one graph launch: refinement drawn from {4,5,6}, vertical levels from "
@@ -960,6 +966,46 @@ def run_balanced_flow(args, wl):
     return 0
 
 
+def run_prolongation(args, wl):
+    """Sec. 5's linear prolongation against P = R^T: iterations, time per iteration and
+    solve time with Richardson and BiCGStab (CG needs the symmetric P = R^T)."""
+    import torch
+
+    from paper_1408_2981_gb300 import binding, build as _build, inputs
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    _build.build()
+    stream = torch.cuda.current_stream()
+    l2 = torch.cuda.get_device_properties(local).L2_cache_size
+    flush = torch.empty(max(2 * l2, 256 << 20) // 4, dtype=torch.float32, device="cuda")
+    rows, launches, f = [], 0, None
+    clocks = ClockSampler(local)
+    clocks.start()
+    for prec_name, prec in (("FP64", dict()), ("mixed", dict(MIXED))):
+        for oname, outer in (("Richardson", binding.TPMG_OUTER_RICHARDSON), ("BiCGStab", binding.TPMG_OUTER_BICGSTAB)):
+            for pname, prol in (("constant", binding.TPMG_PROLONG_CONSTANT), ("linear", binding.TPMG_PROLONG_LINEAR)):
+                s = binding.Solver(stream=stream, outer=outer, prolongation=prol, **wl["params"], **prec)
+                if f is None:
+                    f = torch.from_numpy(inputs.uniform_pm1(wl["seed"], s.N)).cuda()
+                s.profile(classes=())
+                res = time_solves(s, f, max(1, min(args.steps, 10)), args.warmup, 1e-5, 200, flush, stream)
+                launches += launches_of(s)
+                ms = statistics.median(r[0] for r in res)
+                it, st = res[-1][1], res[-1][2]
+                rows.append({"precision": prec_name, "outer": oname, "prolongation": pname, "status": st, "iters": it,
+                             "t_solve_ms": ms, "t_iter_ms": ms / max(it, 1), "unknowns_per_s": s.N / (ms / 1e3)})
+                del s
+                torch.cuda.synchronize()
+    clk = clocks.stop()
+    best = min((r for r in rows if r["status"] == 0), key=lambda r: r["t_solve_ms"])
+    if rank == 0:
+        study_line(args, wl, "unknowns/sec to 1e-5 with the fastest prolongation / outer iteration / precision "
+                   "(Sec. 5 linear prolongation against P = R^T)", best["unknowns_per_s"], "unknowns/s", True,
+                   "f64 / f32+f64", {"best": best, "table": rows}, clk, launches, world)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -987,7 +1033,8 @@ def main(argv=None):
             return 0
         return run_reference(args, wl)
     if "study" in wl:
-        return run_nr_sweep(args, wl) if wl["study"] == "nr_sweep" else run_balanced_flow(args, wl)
+        return {"nr_sweep": run_nr_sweep, "balanced_flow": run_balanced_flow,
+                "prolongation": run_prolongation}[wl["study"]](args, wl)
     if "batch" in wl:
         return run_batch(args, wl)
     if "learned" in wl:
