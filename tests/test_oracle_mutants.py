@@ -6,6 +6,7 @@ and run against all pins of ``pins.py`` in a child process.  The test passes
 when some pin rejects the mutant.  The mistakes are planted in the CPU oracle
 only; nothing here touches a GPU.
 """
+import concurrent.futures
 import os
 import subprocess
 import sys
@@ -60,10 +61,8 @@ MUTANTS = {
                          "double up = o->omega2 * G->area[T] * o->arv[k + 1] * o->pf_ar[fa];"),
     "bicgstab_omega_sign": ("r[i] = sv[i] - omega * t[i];", "r[i] = sv[i] + omega * t[i];"),
     "bicgstab_beta_ratio": ("beta = (rho / rho_prev) * (alpha / omega);", "beta = (rho / rho_prev) * (omega / alpha);"),
-    "prolong_half": ("uf[(size_t)(4 * T + j) * n + k] += uc[(size_t)T * n + k];",
-                     "uf[(size_t)(4 * T + j) * n + k] += 0.5 * uc[(size_t)T * n + k];"),
-    "correction_sign": ("uf[(size_t)(4 * T + j) * n + k] += uc[(size_t)T * n + k];",
-                        "uf[(size_t)(4 * T + j) * n + k] -= uc[(size_t)T * n + k];"),
+    "prolong_half": ("double s = uT;", "double s = 0.5 * uT;"),
+    "correction_sign": ("uf[(size_t)(4 * T + j) * n + k] += s;", "uf[(size_t)(4 * T + j) * n + k] -= s;"),
     "horizontal_uses_volume": ("return coeff(o, o->omega2 * o->dr[k] * G->g[3 * T + e] * vfac(o->pr_aS, k) * edge);",
                                "return coeff(o, o->omega2 * o->vol[k] * G->g[3 * T + e] * vfac(o->pr_aS, k) * edge);"),
     "partial_takes_general_beta": ("static int full_now(const octx *o) { return o->vc_full == 1 && o->pl_beta; }",
@@ -115,15 +114,37 @@ DRIVER = textwrap.dedent("""
 """)
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_planted_mistake_fails_a_pin(name, tmp_path):
+def _run_mutant(name: str, work: str):
+    """Compile the oracle with one planted mistake and run every pin on it in a child
+    process; returns (mutation site found, return code, stdout, stderr tail)."""
     old, new = MUTANTS[name]
     src = open(oracle._SRC).read()
-    assert src.count(old) >= 1, f"mutation site for {name} not found"
-    mutated = src.replace(old, new, 1)
-    c_path = tmp_path / "mutant.c"
-    c_path.write_text(mutated)
-    lib = oracle.compile_source(str(c_path), str(tmp_path / "libmutant.so"))
+    if src.count(old) < 1:
+        return False, None, "", ""
+    d = os.path.join(work, name)
+    os.makedirs(d, exist_ok=True)
+    c_path = os.path.join(d, "mutant.c")
+    with open(c_path, "w") as fh:
+        fh.write(src.replace(old, new, 1))
+    lib = oracle.compile_source(c_path, os.path.join(d, "libmutant.so"))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     proc = subprocess.run([sys.executable, "-c", DRIVER.format(root=ROOT, tests=TESTS), lib],
-                          capture_output=True, text=True, timeout=600)
-    assert proc.returncode == 0 and "REJECTED_BY" in proc.stdout, (proc.returncode, proc.stdout, proc.stderr[-2000:])
+                          capture_output=True, text=True, timeout=600, env=env)
+    return True, proc.returncode, proc.stdout, proc.stderr[-2000:]
+
+
+@pytest.fixture(scope="module")
+def mutant_results(tmp_path_factory):
+    """All mutants, compiled and checked in parallel (independent child processes)."""
+    work = str(tmp_path_factory.mktemp("mutants"))
+    workers = max(1, min(len(MUTANTS), len(os.sched_getaffinity(0))))
+    with concurrent.futures.ThreadPoolExecutor(max_workers=workers) as ex:
+        futures = {name: ex.submit(_run_mutant, name, work) for name in MUTANTS}
+        return {name: f.result() for name, f in futures.items()}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_fails_a_pin(name, mutant_results):
+    found, rc, out, err = mutant_results[name]
+    assert found, f"mutation site for {name} not found"
+    assert rc == 0 and "REJECTED_BY" in out, (rc, out, err)
