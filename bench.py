@@ -275,11 +275,12 @@ def aggregate_value(units_per_step: float, steps: int, world: int, local_ms: flo
 
 
 # ----------------------------------------------------------------------------- oracle timing
-def oracle_inputs(wl: dict):
+def oracle_inputs(wl: dict, lib_path: str | None = None):
     import oracle
     from paper_1408_2981_gb300 import inputs
 
-    o = oracle.Oracle(**{k: v for k, v in wl["params"].items() if k not in ("precision", "coeff_storage")})
+    o = oracle.Oracle(**{k: v for k, v in wl["params"].items() if k not in ("precision", "coeff_storage")},
+                      lib_path=lib_path)
     if wl["rhs"] == "manufactured":
         g, v = o.grid(o.refinement), o.vertical()
         ustar = inputs.manufactured_solution(g["centre"], v["r"], wl["seed"])
@@ -289,7 +290,38 @@ def oracle_inputs(wl: dict):
     return o, f
 
 
-def time_oracle(wl: dict, min_seconds: float, max_solves: int, rtol: float, iters_hint: int | None = None):
+def cpu_model() -> str:
+    """The host CPU's name from /proc/cpuinfo (x86: model name; Arm: implementer and part)."""
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return "unknown"
+    for key in ("model name", "Model"):
+        for line in info:
+            if line.startswith(key):
+                return line.split(":", 1)[1].strip()
+    impl = next((l.split(":", 1)[1].strip() for l in info if l.startswith("CPU implementer")), "?")
+    part = next((l.split(":", 1)[1].strip() for l in info if l.startswith("CPU part")), "?")
+    return f"Arm implementer {impl} part {part}"
+
+
+def time_oracle_threads(wl: dict, rtol: float, iters_hint: int | None):
+    """The oracle built with OpenMP on all cores of this process's affinity mask (the
+    same results bit for bit): a bounded sample like time_oracle's, about 5 s."""
+    import oracle
+
+    lib = oracle.build_openmp()
+    if lib is None:
+        return {"unavailable": "no OpenMP compiler"}
+    cores = len(os.sched_getaffinity(0))
+    oracle.threads(cores, lib_path=lib)
+    v, sample, _ = time_oracle(wl, min_seconds=5.0, max_solves=3, rtol=rtol, iters_hint=iters_hint, lib_path=lib)
+    return {"value": v, "unit": "unknowns/s", "cores": cores, "kind": "oracle (OpenMP over columns)",
+            "cpu": cpu_model(), "sample": sample.replace("single thread", f"{cores} threads")}
+
+
+def time_oracle(wl: dict, min_seconds: float, max_solves: int, rtol: float, iters_hint: int | None = None,
+                lib_path: str | None = None):
     """Oracle solves of the workload on the host cores (setup excluded).
 
     Returns (unknowns per second of a full solve, sample text, oracle iterations).
@@ -297,7 +329,7 @@ def time_oracle(wl: dict, min_seconds: float, max_solves: int, rtol: float, iter
     one, until min_seconds).  Beyond that a bounded sample: the oracle runs one
     PCG iteration (initial residual, V-cycle, operator, update), and a full
     solve is taken as that time x the iteration count of the GPU solve."""
-    o, f = oracle_inputs(wl)
+    o, f = oracle_inputs(wl, lib_path)
     N = o.size()
     flexible = wl["params"].get("precision", 0) == 1
     if flexible:
@@ -476,10 +508,11 @@ def run_tpmg(args, wl):
     hbm = {"achieved_gbs": tot_bytes / (local_ms / 1e3) / 1e9, "peak_gbs": peaks["hbm_gbs"],
            "frac": tot_bytes / (local_ms / 1e3) / 1e9 / peaks["hbm_gbs"], "source": peaks["source"]}
 
-    cpu = None
+    cpu, cpu_threads = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v_o, sample, _ = time_oracle(wl, min_seconds=10.0, max_solves=3, rtol=args.rtol, iters_hint=iters[-1])
-        cpu = {"value": v_o, "unit": "unknowns/s", "cores": 1, "kind": "oracle", "sample": sample}
+        cpu = {"value": v_o, "unit": "unknowns/s", "cores": 1, "kind": "oracle", "sample": sample, "cpu": cpu_model()}
+        cpu_threads = time_oracle_threads(wl, args.rtol, iters[-1])
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world, "steps": args.steps,
@@ -492,6 +525,7 @@ def run_tpmg(args, wl):
                 "e2e": {"value": e2e_value, "unit": "unknowns/s", "h2d_bytes_per_step": 2 * 8 * N,
                         "d2h_bytes_per_step": 8 * N},
                 "gpu_launches": gpu_launches, "roofline": roof, "hbm": hbm, "cpu_baseline": cpu,
+                "cpu_baseline_threads": cpu_threads,
                 "clocks": clk, "iters": iters[-1], "rel_resid": rel,
                 "kernel_ms_per_step": {c: round(v, 4) for c, v in shares.items()}}
         print(json.dumps(line), flush=True)

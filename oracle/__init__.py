@@ -38,17 +38,42 @@ def build(force: bool = False) -> str:
     return compile_source(_SRC, _LIB_PATH)
 
 
+_LIB_OMP_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "liboracle_tpmg_omp.so")
+
+
+def build_openmp(force: bool = False) -> str | None:
+    """The same source compiled with OpenMP (``oracle/liboracle_tpmg_omp.so``): the
+    columns of a colour pass, the operator's rows and the transfers are shared out over
+    threads, with the same results bit for bit.  Only a baseline timing uses it.
+    None where the compiler has no OpenMP."""
+    if (not force and os.path.exists(_LIB_OMP_PATH)
+            and os.path.getmtime(_LIB_OMP_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_OMP_PATH
+    try:
+        return compile_source(_SRC, _LIB_OMP_PATH, openmp=True)
+    except (subprocess.CalledProcessError, OSError):
+        return None
+
+
 _libs: dict = {}
 
 
-def compile_source(src: str, out_path: str) -> str:
+def compile_source(src: str, out_path: str, openmp: bool = False) -> str:
     """Compile one oracle C source into a shared library at ``out_path``."""
     tmp = out_path + f".tmp{os.getpid()}"
     cmd = ["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
            src, "-o", tmp, "-lm"]
-    subprocess.run(cmd, check=True)
+    if openmp:
+        cmd.insert(1, "-fopenmp")
+    subprocess.run(cmd, check=True, stderr=subprocess.DEVNULL if openmp else None)
     os.replace(tmp, out_path)
     return out_path
+
+
+def threads(n: int = 0, lib_path: str | None = None) -> int:
+    """Threads of the parallel loops of a library built with OpenMP (1 without):
+    sets n when n > 0, returns the number in use."""
+    return int(_load(lib_path).oracle_threads(int(n)))
 
 
 def _load(path: str | None = None):
@@ -60,6 +85,8 @@ def _load(path: str | None = None):
             return _libs[key]
         lib = ctypes.CDLL(path if path else build())
         lib.oracle_create.restype = _P
+        lib.oracle_threads.argtypes = [_I]
+        lib.oracle_threads.restype = _I
         lib.oracle_create.argtypes = [_I, _I, _I, _D, _D, _D, _D, _I, _I, _I, _I, _D, _I]
         lib.oracle_destroy.argtypes = [_P]
         lib.oracle_info.argtypes = [_P, _P, _P]

@@ -30,6 +30,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ------------------------------------------------------------------------- */
 /* 3-vectors                                                                  */
@@ -405,8 +408,42 @@ typedef struct {
                              1: linear interpolation with a tangent-plane gradient (Reading C25) */
     /* multigrid work arrays per multigrid level (0 = coarsest)               */
     double **mg_f, **mg_u, **mg_r;
-    double *col_a, *col_b, *col_c, *col_d, *col_x, *col_cp, *col_dp;
+    /* column work arrays of the line relaxation, 5 n_r doubles per thread: compiled with
+     * OpenMP, the columns of one colour (and the rows of the operator and the transfers)
+     * are shared out over threads; each column's arithmetic is unchanged, so the results
+     * are the same bits as with one thread (the dot products stay sequential). */
+    double *col_ws;
+    int ws_threads;
 } octx;
+
+static int thread_id(void)
+{
+#ifdef _OPENMP
+    return omp_get_thread_num();
+#else
+    return 0;
+#endif
+}
+
+static int max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* work arrays for every thread a parallel region may use (called outside any region) */
+static int ensure_ws(octx *o)
+{
+    const int nt = max_threads();
+    if (nt <= o->ws_threads) return 0;
+    free(o->col_ws);
+    o->col_ws = (double *)calloc((size_t)nt * 5 * o->n_r, sizeof(double));
+    o->ws_threads = o->col_ws ? nt : 0;
+    return o->col_ws ? 0 : -2;
+}
 
 static const ogrid *mg_grid(const octx *o, int l) { return &o->grid[o->L - (o->n_levels - 1 - l)]; }
 
@@ -539,6 +576,7 @@ static void apply_level(octx *o, int l, const double *u, double *y)
 {
     const ogrid *G = mg_grid(o, l);
     int n = o->n_r, T, k;
+#pragma omp parallel for private(k) schedule(static)
     for (T = 0; T < G->n_cells; ++T)
         for (k = 0; k < n; ++k) y[(size_t)T * n + k] = apply_row(o, G, u, T, k);
 }
@@ -578,6 +616,7 @@ static void apply_outer(octx *o, const double *u, double *y)
         apply_level(o, lf, u, y);
         return;
     }
+#pragma omp parallel for private(k) schedule(static)
     for (T = 0; T < G->n_cells; ++T)
         for (k = 0; k < n; ++k) y[(size_t)T * n + k] = apply_row_full(o, G, u, T, k);
 }
@@ -672,16 +711,17 @@ static void relax_column(octx *o, int l, int T, const double *f, const double *u
 {
     const ogrid *G = mg_grid(o, l);
     int n = o->n_r, k, e;
+    double *a = o->col_ws + (size_t)thread_id() * 5 * n, *c = a + n, *b = c + n, *d = b + n, *x = d + n;
     for (k = 0; k < n; ++k) {
         double hs = 0.0;
         for (e = 0; e < 3; ++e) hs += alphaS_hat(o, G, T, e, k);
-        o->col_a[k] = vert_down(o, G, T, k);            /* coupling to level k-1 */
-        o->col_c[k] = vert_up(o, G, T, k);              /* coupling to level k+1 */
-        o->col_b[k] = beta_hat(o, G, T, k) + hs;        /* excess of the diagonal */
-        o->col_d[k] = f[(size_t)T * n + k] - apply_row(o, G, u_in, T, k);
+        a[k] = vert_down(o, G, T, k);            /* coupling to level k-1 */
+        c[k] = vert_up(o, G, T, k);              /* coupling to level k+1 */
+        b[k] = beta_hat(o, G, T, k) + hs;        /* excess of the diagonal */
+        d[k] = f[(size_t)T * n + k] - apply_row(o, G, u_in, T, k);
     }
-    oracle_column_solve2(n, o->col_a, o->col_c, o->col_b, o->col_d, o->col_x);
-    for (k = 0; k < n; ++k) u_out[(size_t)T * n + k] = u_in[(size_t)T * n + k] + o->relax * o->col_x[k];
+    oracle_column_solve2(n, a, c, b, d, x);
+    for (k = 0; k < n; ++k) u_out[(size_t)T * n + k] = u_in[(size_t)T * n + k] + o->relax * x[k];
 }
 
 /* Multicolour block-SOR: columns of one colour do not touch each other, so a
@@ -691,6 +731,8 @@ static void colour_pass(octx *o, int l, int c, const double *f, double *u)
 {
     const ogrid *G = mg_grid(o, l);
     int T;
+    if (ensure_ws(o)) return;
+#pragma omp parallel for schedule(static)
     for (T = 0; T < G->n_cells; ++T)
         if (G->colour[T] == c) relax_column(o, l, T, f, u, u);
 }
@@ -702,6 +744,8 @@ static void jacobi_sweep(octx *o, int l, const double *f, double *u)
     double *old = (double *)malloc(N * sizeof(double));
     int T;
     memcpy(old, u, N * sizeof(double));
+    if (ensure_ws(o)) { free(old); return; }
+#pragma omp parallel for schedule(static)
     for (T = 0; T < G->n_cells; ++T) relax_column(o, l, T, f, old, u);
     free(old);
 }
@@ -729,6 +773,7 @@ static void restrict_sum(const octx *o, int l_fine, const double *rf, double *fc
 {
     const ogrid *Gc = mg_grid(o, l_fine - 1);
     int n = o->n_r, T, j, k;
+#pragma omp parallel for private(j, k) schedule(static)
     for (T = 0; T < Gc->n_cells; ++T)
         for (k = 0; k < n; ++k) {
             double s = 0.0;
@@ -781,8 +826,9 @@ static void prolong_add(const octx *o, int l_fine, const double *uc, double *uf)
 {
     const ogrid *Gc = mg_grid(o, l_fine - 1);
     int n = o->n_r, T, j, k, e;
-    double w[4][3];
+#pragma omp parallel for private(j, k, e) schedule(static)
     for (T = 0; T < Gc->n_cells; ++T) {
+        double w[4][3];
         if (o->prolong_linear) linear_weights(o, l_fine, T, w);
         for (j = 0; j < 4; ++j)
             for (k = 0; k < n; ++k) {
@@ -793,6 +839,18 @@ static void prolong_add(const octx *o, int l_fine, const double *uc, double *uf)
                 uf[(size_t)(4 * T + j) * n + k] += s;
             }
     }
+}
+
+/* Threads of the parallel loops (the build with OpenMP; 1 otherwise): sets n when
+ * n > 0, returns the number in use. */
+int oracle_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+    return max_threads();
 }
 
 /* on != 0: linear prolongation (Reading C25); 0: P = R^T (Reading C5) */
@@ -815,6 +873,7 @@ static void vcycle_level(octx *o, int l, const double *f, double *u)
     }
     smooth(o, l, f, u, o->nu_pre, +1);                       /* pre-smoothing    */
     apply_level(o, l, u, o->mg_r[l]);                        /* residual         */
+#pragma omp parallel for schedule(static)
     for (i = 0; i < N; ++i) o->mg_r[l][i] = f[i] - o->mg_r[l][i];
     restrict_sum(o, l, o->mg_r[l], o->mg_f[l - 1]);          /* f_{l-1} = R r_l  */
     memset(o->mg_u[l - 1], 0, (size_t)mg_grid(o, l - 1)->n_cells * o->n_r * sizeof(double));
@@ -968,8 +1027,7 @@ void oracle_destroy(void *h)
     if (o->mg_f)
         for (l = 0; l < o->n_levels; ++l) { free(o->mg_f[l]); free(o->mg_u[l]); free(o->mg_r[l]); }
     free(o->mg_f); free(o->mg_u); free(o->mg_r);
-    free(o->col_a); free(o->col_b); free(o->col_c); free(o->col_d); free(o->col_x);
-    free(o->col_cp); free(o->col_dp);
+    free(o->col_ws);
     free(o->pr_beta); free(o->pr_aS); free(o->pr_ar); free(o->pr_xi);
     free_level_profile(o, o->ps_beta);
     free_level_profile(o, o->ps_ar);
@@ -1057,14 +1115,7 @@ void *oracle_create(int refinement, int n_levels, int n_r, double H, double grad
         o->mg_r[l] = (double *)calloc(N, sizeof(double));
         if (!o->mg_f[l] || !o->mg_u[l] || !o->mg_r[l]) goto fail;
     }
-    o->col_a = (double *)calloc((size_t)n_r, sizeof(double));
-    o->col_b = (double *)calloc((size_t)n_r, sizeof(double));
-    o->col_c = (double *)calloc((size_t)n_r, sizeof(double));
-    o->col_d = (double *)calloc((size_t)n_r, sizeof(double));
-    o->col_x = (double *)calloc((size_t)n_r, sizeof(double));
-    o->col_cp = (double *)calloc((size_t)n_r, sizeof(double));
-    o->col_dp = (double *)calloc((size_t)n_r, sizeof(double));
-    if (!o->col_a || !o->col_b || !o->col_c || !o->col_d || !o->col_x || !o->col_cp || !o->col_dp) goto fail;
+    if (ensure_ws(o)) goto fail;
     return o;
 fail:
     oracle_destroy(o);
