@@ -87,8 +87,8 @@ MUTANTS = {
     "colouring_ignores_colour0": ("            if (c >= 0) used[c] = 1;", "            if (c >= 1) used[c] = 1;"),
     "colouring_lowest_saturation": ("for (s = 3; s >= 0 && T < 0; --s)", "for (s = 0; s < 4 && T < 0; ++s)"),
     "grading_exponent": ("pow(grading, (double)k)", "pow(grading, (double)(k + 1))"),
-    "relaxation_ignored": ("u_in[(size_t)T * n + k] + o->relax * o->col_x[k];", "u_in[(size_t)T * n + k] + o->col_x[k];"),
-    "diag_misses_mass": ("o->col_b[k] = beta_hat(o, G, T, k) + hs;", "o->col_b[k] = hs;"),
+    "relaxation_ignored": ("u_in[(size_t)T * n + k] + o->relax * x[k];", "u_in[(size_t)T * n + k] + x[k];"),
+    "diag_misses_mass": ("b[k] = beta_hat(o, G, T, k) + hs;", "b[k] = hs;"),
     "pcg_alpha_inverted": ("alpha = rz / pq;", "alpha = pq / rz;"),
     "coarse_sweep_one_way": ("smooth(o, l, f, u, o->nu_coarse, 0);", "smooth(o, l, f, u, o->nu_coarse, +1);"),
 }
