@@ -117,6 +117,7 @@ __device__ __forceinline__ double col_up(const OpView &o, int T, int k, double A
 }
 
 // (A x)_{T,k} in flux form: 13 FP64 instructions.
+template <bool ADV = false>
 __device__ __forceinline__ double apply_at(const OpView &o, const double *__restrict__ x, int T, int k, int i)
 {
     const int n_r = o.n_r;
@@ -128,7 +129,7 @@ __device__ __forceinline__ double apply_at(const OpView &o, const double *__rest
     const double vert = fma(__ldg(&o.w[k + 1]), dp, __ldg(&o.w[k]) * dm);
     const double hor = fma(g.z, xc - x[nb.z * n_r + k], fma(g.y, xc - x[nb.y * n_r + k], g.x * (xc - x[nb.x * n_r + k])));
     const double v = fma(__ldg(&o.area_r[T]), vert, fma(__ldg(&o.area[T]) * __ldg(&o.vol[k]), xc, __ldg(&o.hr[k]) * hor));
-    if (!o.area_x) return v;
+    if (!ADV) return v;
     // centred vertical advection: + Ax (xp_k (u_k - u_{k+1}) - xm_k (u_k - u_{k-1}))
     return fma(__ldg(&o.area_x[T]), fma(__ldg(&o.xp[k]), dp, -__ldg(&o.xm[k]) * dm), v);
 }
@@ -160,16 +161,17 @@ __device__ __forceinline__ double apply_full_at(const OpView &o, const FullView 
     return fma(c.w, xc, vert + hor);
 }
 
-template <int NT, bool FULL>
+template <int NT, bool FULL, bool ADV>
 __device__ __forceinline__ double apply_any(const OpView &o, const FullView &fv, const double *__restrict__ x, int T,
                                             int k, int i)
 {
     if (FULL) return apply_full_at(o, fv, x, T, k, i);
-    return apply_at(o, x, T, k, i);
+    return apply_at<ADV>(o, x, T, k, i);
 }
 
 // Row (T, k) with the vertical couplings per face (TPMG^partial): apply_at with
 // area_r w_k replaced by the stored alphar_hat of face k.
+template <bool ADV>
 __device__ __forceinline__ double apply_partial_at(const OpView &o, const double *__restrict__ x, int T, int k, int i)
 {
     const int n_r = o.n_r;
@@ -180,28 +182,28 @@ __device__ __forceinline__ double apply_partial_at(const OpView &o, const double
     const double dp = k < n_r - 1 ? xc - x[i + 1] : 0.0;
     const double *cr = o.cr + (size_t)T * (n_r + 1) + k;
     double vert = fma(__ldg(&cr[1]), dp, __ldg(&cr[0]) * dm);
-    if (o.area_x) vert = fma(__ldg(&o.area_x[T]), fma(__ldg(&o.xp[k]), dp, -__ldg(&o.xm[k]) * dm), vert);
+    if (ADV) vert = fma(__ldg(&o.area_x[T]), fma(__ldg(&o.xp[k]), dp, -__ldg(&o.xm[k]) * dm), vert);
     const double hor = fma(g.z, xc - x[nb.z * n_r + k], fma(g.y, xc - x[nb.y * n_r + k], g.x * (xc - x[nb.x * n_r + k])));
     return vert + fma(__ldg(&o.area[T]) * __ldg(&o.vol[k]), xc, __ldg(&o.hr[k]) * hor);
 }
 
 // Row (T, k) of a level's V-cycle operator in stencil form CM.
-template <int CM>
+template <int CM, bool ADV>
 __device__ __forceinline__ double apply_vc(const OpView &o, const double *__restrict__ x, int T, int k, int i)
 {
     if (CM == CM_FULL) return apply_full_at(o, FullView{o.c, o.cr, o.cx}, x, T, k, i);
-    if (CM == CM_PARTIAL) return apply_partial_at(o, x, T, k, i);
-    return apply_at(o, x, T, k, i);
+    if (CM == CM_PARTIAL) return apply_partial_at<ADV>(o, x, T, k, i);
+    return apply_at<ADV>(o, x, T, k, i);
 }
 
-template <int NT, bool FULL = false>
+template <int NT, bool FULL, bool ADV>
 __global__ void __launch_bounds__(NT) k_apply(OpView o, FullView fv, const double *__restrict__ x,
                                               double *__restrict__ y, int N, double *__restrict__ partials)
 {
     double acc = 0.0;
     for (int i = blockIdx.x * NT + threadIdx.x; i < N; i += gridDim.x * NT) {
         const int T = i / o.n_r, k = i - T * o.n_r;
-        const double v = apply_any<NT, FULL>(o, fv, x, T, k, i);
+        const double v = apply_any<NT, FULL, ADV>(o, fv, x, T, k, i);
         y[i] = v;
         acc = fma(x[i], v, acc);
     }
@@ -217,7 +219,7 @@ __device__ __forceinline__ bool is_zero(double v) { return (__double_as_longlong
 // a warp reads exact zeros (for example a zero initial guess) A u is exactly
 // zero and the warp skips its FP64 arithmetic; the test is on bit patterns,
 // so it costs no FP64 instruction.
-template <int NT, bool FULL = false>
+template <int NT, bool FULL, bool ADV>
 __global__ void __launch_bounds__(NT) k_residual(OpView o, FullView full, const double *__restrict__ f,
                                                  const double *__restrict__ u, double *__restrict__ r, int N,
                                                  double *__restrict__ partials)
@@ -256,7 +258,7 @@ __global__ void __launch_bounds__(NT) k_residual(OpView o, FullView full, const 
             const int i = i0 + q * stride;
             if (i >= N) continue;
             double v = fv[q];
-            if (!skip) v = v - apply_any<NT, FULL>(o, full, u, T[q], k[q], i);
+            if (!skip) v = v - apply_any<NT, FULL, ADV>(o, full, u, T[q], k[q], i);
             r[i] = v;
             acc = fma(v, v, acc);
         }
@@ -268,7 +270,7 @@ __global__ void __launch_bounds__(NT) k_residual(OpView o, FullView full, const 
 }
 
 // f_c[T][k] = sum_j (f - A u)[4T + j][k]  (Algorithm 1 residual + restriction, Sec. 5)
-template <int NT, int CM>
+template <int NT, int CM, bool ADV>
 __global__ void __launch_bounds__(NT) k_resid_restrict(OpView o, const double *__restrict__ f,
                                                        const double *__restrict__ u, double *__restrict__ fc, int Nc)
 {
@@ -278,7 +280,7 @@ __global__ void __launch_bounds__(NT) k_resid_restrict(OpView o, const double *_
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int T = 4 * Tc + j, i = T * o.n_r + k;
-            s += f[i] - apply_vc<CM>(o, u, T, k, i);
+            s += f[i] - apply_vc<CM, ADV>(o, u, T, k, i);
         }
         fc[ic] = s;
     }
@@ -1059,10 +1061,13 @@ cudaError_t launch_apply(const Launch &L, const LevelDev &lv, const VertDev &v, 
     const int N = lv.n * L.n_r;
     const int grid = partials ? n_part : grid_for(N, kThreads, L.sm_count);
     const FullView fv{lv.cfull, lv.cvr, lv.cvx};
+    // ADV: the factorised operator with vertical advection (compiled out without it)
     if (lv.cfull)
-        k_apply<kThreads, true><<<grid, kThreads, 0, L.s>>>(make_view(lv, v, L.n_r), fv, x, y, N, partials);
+        k_apply<kThreads, true, false><<<grid, kThreads, 0, L.s>>>(make_view(lv, v, L.n_r), fv, x, y, N, partials);
+    else if (lv.area_x)
+        k_apply<kThreads, false, true><<<grid, kThreads, 0, L.s>>>(make_view(lv, v, L.n_r), fv, x, y, N, partials);
     else
-        k_apply<kThreads, false><<<grid, kThreads, 0, L.s>>>(make_view(lv, v, L.n_r), fv, x, y, N, partials);
+        k_apply<kThreads, false, false><<<grid, kThreads, 0, L.s>>>(make_view(lv, v, L.n_r), fv, x, y, N, partials);
     return cudaGetLastError();
 }
 
@@ -1073,9 +1078,12 @@ cudaError_t launch_residual(const Launch &L, const LevelDev &lv, const VertDev &
     const int grid = partials ? n_part : grid_for(N, kThreads, L.sm_count);
     const FullView fv{lv.cfull, lv.cvr, lv.cvx};
     if (lv.cfull)
-        k_residual<kThreads, true><<<grid, kThreads, 0, L.s>>>(make_view(lv, v, L.n_r), fv, f, u, r, N, partials);
+        k_residual<kThreads, true, false><<<grid, kThreads, 0, L.s>>>(make_view(lv, v, L.n_r), fv, f, u, r, N, partials);
+    else if (lv.area_x)
+        k_residual<kThreads, false, true><<<grid, kThreads, 0, L.s>>>(make_view(lv, v, L.n_r), fv, f, u, r, N, partials);
     else
-        k_residual<kThreads, false><<<grid, kThreads, 0, L.s>>>(make_view(lv, v, L.n_r), fv, f, u, r, N, partials);
+        k_residual<kThreads, false, false><<<grid, kThreads, 0, L.s>>>(make_view(lv, v, L.n_r), fv, f, u, r, N,
+                                                                      partials);
     return cudaGetLastError();
 }
 
@@ -1085,9 +1093,14 @@ cudaError_t launch_resid_restrict(const Launch &L, const LevelDev &fine, const L
     const int Nc = coarse.n * L.n_r, grid = grid_for(Nc, kThreads, L.sm_count);
     const OpView o = make_view(fine, v, L.n_r);
     switch (stencil_form(fine)) {
-    case CM_FULL: k_resid_restrict<kThreads, CM_FULL><<<grid, kThreads, 0, L.s>>>(o, f, u, fc, Nc); break;
-    case CM_PARTIAL: k_resid_restrict<kThreads, CM_PARTIAL><<<grid, kThreads, 0, L.s>>>(o, f, u, fc, Nc); break;
-    default: k_resid_restrict<kThreads, CM_FAC><<<grid, kThreads, 0, L.s>>>(o, f, u, fc, Nc);
+    case CM_FULL: k_resid_restrict<kThreads, CM_FULL, false><<<grid, kThreads, 0, L.s>>>(o, f, u, fc, Nc); break;
+    case CM_PARTIAL:
+        if (fine.area_x) k_resid_restrict<kThreads, CM_PARTIAL, true><<<grid, kThreads, 0, L.s>>>(o, f, u, fc, Nc);
+        else k_resid_restrict<kThreads, CM_PARTIAL, false><<<grid, kThreads, 0, L.s>>>(o, f, u, fc, Nc);
+        break;
+    default:
+        if (fine.area_x) k_resid_restrict<kThreads, CM_FAC, true><<<grid, kThreads, 0, L.s>>>(o, f, u, fc, Nc);
+        else k_resid_restrict<kThreads, CM_FAC, false><<<grid, kThreads, 0, L.s>>>(o, f, u, fc, Nc);
     }
     return cudaGetLastError();
 }
