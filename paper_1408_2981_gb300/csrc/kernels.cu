@@ -169,6 +169,33 @@ __device__ __forceinline__ double apply_any(const OpView &o, const FullView &fv,
     return apply_at<ADV>(o, x, T, k, i);
 }
 
+// Row (T, k) of the factorised operator for kernels whose warps hold consecutive rows:
+// lane l has row i and lane l + 1 row i + 1 (of the same column, or row 0 of the next,
+// whose lower difference is 0).  d = x_k - x_{k-1} is this row's lower-face difference
+// (0 for k = 0) and du = x_{k+1} - x_k, from the next lane, the upper one, so the
+// vertical fluxes stay differences of neighbouring values (the nearly singular vertical
+// mode of a column needs them) while each difference is formed once:
+//   vertical = w_k d - w_{k+1} du.
+// The horizontal part, whose couplings are only omega^2/h^2 times the mass term, is
+// summed directly: m x_k - hr_k sum_e g_e x_e with the diagonal excess
+// m = |T| v_k + hr_k G.  11 FP64 operations where apply_at takes 14.
+template <bool ADV>
+__device__ __forceinline__ double apply_at_lanes(const OpView &o, const double *__restrict__ x, int T, int k,
+                                                 double xc, double d, double du)
+{
+    const int n_r = o.n_r;
+    const int4 nb = __ldg(&o.nbr[T]);
+    const dbl4 g = o.g[T];
+    const double S = fma(g.z, x[nb.z * n_r + k], fma(g.y, x[nb.y * n_r + k], g.x * x[nb.x * n_r + k]));
+    const double hrk = __ldg(&o.hr[k]);
+    const double m = fma(__ldg(&o.area[T]), __ldg(&o.vol[k]), hrk * g.w);
+    const double vert = fma(__ldg(&o.w[k]), d, -__ldg(&o.w[k + 1]) * du);
+    const double v = fma(__ldg(&o.area_r[T]), vert, fma(m, xc, -hrk * S));
+    if (!ADV) return v;
+    // centred vertical advection: Ax (xp_k (x_k - x_{k+1}) - xm_k (x_k - x_{k-1}))
+    return fma(__ldg(&o.area_x[T]), fma(-__ldg(&o.xp[k]), du, -__ldg(&o.xm[k]) * d), v);
+}
+
 // Row (T, k) with the vertical couplings per face (TPMG^partial): apply_at with
 // area_r w_k replaced by the stored alphar_hat of face k.
 template <bool ADV>
@@ -201,11 +228,35 @@ __global__ void __launch_bounds__(NT) k_apply(OpView o, FullView fv, const doubl
                                               double *__restrict__ y, int N, double *__restrict__ partials)
 {
     double acc = 0.0;
-    for (int i = blockIdx.x * NT + threadIdx.x; i < N; i += gridDim.x * NT) {
-        const int T = i / o.n_r, k = i - T * o.n_r;
-        const double v = apply_any<NT, FULL, ADV>(o, fv, x, T, k, i);
-        y[i] = v;
-        acc = fma(x[i], v, acc);
+    if (FULL) {
+        for (int i = blockIdx.x * NT + threadIdx.x; i < N; i += gridDim.x * NT) {
+            const int T = i / o.n_r, k = i - T * o.n_r;
+            const double v = apply_any<NT, FULL, ADV>(o, fv, x, T, k, i);
+            y[i] = v;
+            acc = fma(x[i], v, acc);
+        }
+    } else {
+        // each warp takes 32 consecutive rows and writes the first 31; lane 31 only hands its
+        // lower difference to lane 30 (apply_at_lanes)
+        const int lane = threadIdx.x & 31;
+        const int stride = gridDim.x * (NT / 32) * 31;
+        for (int base = (blockIdx.x * (NT / 32) + (threadIdx.x >> 5)) * 31; base < N; base += stride) {
+            const int i = base + lane;
+            int T = 0, k = 0;
+            double xc = 0.0, d = 0.0;
+            if (i < N) {
+                T = i / o.n_r;
+                k = i - T * o.n_r;
+                xc = x[i];
+                if (k > 0) d = xc - x[i - 1];
+            }
+            const double du = __shfl_down_sync(0xffffffffu, d, 1);
+            if (lane < 31 && i < N) {
+                const double v = apply_at_lanes<ADV>(o, x, T, k, xc, d, du);
+                y[i] = v;
+                acc = fma(xc, v, acc);
+            }
+        }
     }
     if (partials) {
         acc = block_sum<NT>(acc);
@@ -274,15 +325,40 @@ template <int NT, int CM, bool ADV>
 __global__ void __launch_bounds__(NT) k_resid_restrict(OpView o, const double *__restrict__ f,
                                                        const double *__restrict__ u, double *__restrict__ fc, int Nc)
 {
-    for (int ic = blockIdx.x * NT + threadIdx.x; ic < Nc; ic += gridDim.x * NT) {
-        const int Tc = ic / o.n_r, k = ic - Tc * o.n_r;
+    if (CM != CM_FAC) {
+        for (int ic = blockIdx.x * NT + threadIdx.x; ic < Nc; ic += gridDim.x * NT) {
+            const int Tc = ic / o.n_r, k = ic - Tc * o.n_r;
+            double s = 0.0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int T = 4 * Tc + j, i = T * o.n_r + k;
+                s += f[i] - apply_vc<CM, ADV>(o, u, T, k, i);
+            }
+            fc[ic] = s;
+        }
+        return;
+    }
+    // factorised: warps of 32 consecutive coarse rows (31 written), so that lane l + 1 holds
+    // the next row of each child column as well (apply_at_lanes)
+    const int lane = threadIdx.x & 31;
+    const int stride = gridDim.x * (NT / 32) * 31;
+    for (int base = (blockIdx.x * (NT / 32) + (threadIdx.x >> 5)) * 31; base < Nc; base += stride) {
+        const int ic = base + lane;
+        const bool act = ic < Nc;
+        const int Tc = act ? ic / o.n_r : 0, k = act ? ic - Tc * o.n_r : 0;
         double s = 0.0;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int T = 4 * Tc + j, i = T * o.n_r + k;
-            s += f[i] - apply_vc<CM, ADV>(o, u, T, k, i);
+            double xc = 0.0, d = 0.0;
+            if (act) {
+                xc = u[i];
+                if (k > 0) d = xc - u[i - 1];
+            }
+            const double du = __shfl_down_sync(0xffffffffu, d, 1);
+            if (act && lane < 31) s += f[i] - apply_at_lanes<ADV>(o, u, T, k, xc, d, du);
         }
-        fc[ic] = s;
+        if (act && lane < 31) fc[ic] = s;
     }
 }
 
