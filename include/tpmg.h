@@ -136,6 +136,13 @@ typedef struct {
                             BiCGStab run their loop from the host (one read-back per dot product)
                             and are not available in a batch. */
     int    prolongation; /* TPMG_PROLONG_*: the V-cycle's coarse-to-fine transfer */
+    int    pdl;          /* 1: the kernels of the V-cycle and of the outer loop are launched with
+                            programmatic dependent launch, so each one is scheduled, and reads its
+                            set-up data, while its predecessor in the stream finishes; every kernel
+                            still waits for its predecessor's results.  The FP64 relaxation of
+                            levels above scan_max_cells (16-column twisted tasks) is launched
+                            plainly, where programmatic launch measured slower.  0: plain
+                            launches.  The results are identical. */
 } tpmg_params;
 
 /* Fills *p with the defaults: refinement 3, n_levels 4, n_r 16, H = 10/6371,
@@ -345,10 +352,12 @@ tpmg_status tpmg_profile(tpmg_ctx *ctx, unsigned class_mask);
  * launches, units = number of (cell, level) unknowns the launches processed
  * (for the algorithmic bytes / flops per launch), and -- if the class is
  * timed -- total_ms, the summed device time of the `timed` launches that carry
- * an event pair.  Launches made one by one are all timed; launches replayed
- * from a captured graph carry event-record nodes, so their pairs hold the
- * most recent replay only (timed counts one replay's launches).  The average
- * duration of a launch is total_ms / timed.  Synchronises the context stream.
+ * an event pair.  Launches made one by one are all timed, each with its own
+ * pair.  In a captured graph one pair of event-record nodes spans each run of
+ * consecutive launches of the class (so that the timing adds few nodes and
+ * keeps the kernels of a run back to back); those pairs hold the most recent
+ * replay only (timed counts one replay's launches).  The average duration of
+ * a launch is total_ms / timed.  Synchronises the context stream.
  * Any output may be NULL.  Errors: INVALID_ARG, CUDA. */
 tpmg_status tpmg_profile_read(tpmg_ctx *ctx, int kernel_class, long long *launches, double *total_ms,
                               double *units, long long *timed);

@@ -71,7 +71,7 @@ class tpmg_params(ctypes.Structure):
                 ("nu_coarse", ctypes.c_int), ("smoother", ctypes.c_int), ("relax", ctypes.c_double),
                 ("coeff_storage", ctypes.c_int), ("centre", ctypes.c_int), ("precision", ctypes.c_int),
                 ("graphs", ctypes.c_int), ("autotune", ctypes.c_int), ("scan_max_cells", ctypes.c_int),
-                ("outer", ctypes.c_int), ("prolongation", ctypes.c_int)]
+                ("outer", ctypes.c_int), ("prolongation", ctypes.c_int), ("pdl", ctypes.c_int)]
 
 
 class tpmg_profiles(ctypes.Structure):

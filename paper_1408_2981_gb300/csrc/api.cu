@@ -23,9 +23,12 @@ struct Tracer {
     unsigned mask = 0;
     long long launches[TPMG_K_COUNT] = {};
     double units[TPMG_K_COUNT] = {};
-    std::vector<cudaEvent_t> ev;   // pairs: ev[2i] before, ev[2i+1] after launch i
-    std::vector<int> cls;          // class of timed launch i
+    std::vector<cudaEvent_t> ev;   // pairs: ev[2i] before the first, ev[2i+1] after the last launch of bracket i
+    std::vector<int> cls;          // class of bracket i
+    std::vector<int> nl;           // launches in bracket i
     size_t used = 0;
+    int open = -1;                 // class of the bracket being captured, -1 if none
+    cudaStream_t open_s = nullptr; // its stream
 };
 
 // The V-cycle of tpmg_solve (r -> z on the context's own vectors) replayed
@@ -178,10 +181,14 @@ bool validate(const tpmg_params *p, std::string &msg)
     if (p->prolongation != TPMG_PROLONG_CONSTANT && p->prolongation != TPMG_PROLONG_LINEAR) {
         msg = "unknown prolongation"; return false;
     }
+    if (p->pdl != 0 && p->pdl != 1) { msg = "pdl must be 0 or 1"; return false; }
     return true;
 }
 
-Launch launch_of(const tpmg_ctx *ctx) { return Launch{ctx->issue, ctx->p.n_r, ctx->sm_count, ctx->vert.dr, ctx->vert.dr32}; }
+Launch launch_of(const tpmg_ctx *ctx)
+{
+    return Launch{ctx->issue, ctx->p.n_r, ctx->sm_count, ctx->vert.dr, ctx->vert.dr32, ctx->p.pdl == 1};
+}
 
 double vfac(const std::vector<double> &v, int k) { return v.empty() ? 1.0 : v[k]; }
 double hfac(const std::vector<std::vector<double>> &h, int ref, int T) { return h.empty() ? 1.0 : h[ref][T]; }
@@ -237,14 +244,32 @@ cudaError_t grow_events(Tracer &t, size_t pairs)
         t.ev.push_back(e);
     }
     if (t.cls.size() < pairs) t.cls.resize(pairs);
+    if (t.nl.size() < pairs) t.nl.resize(pairs);
     return cudaSuccess;
+}
+
+// Records the end of the open bracket, if any.
+cudaError_t close_bracket(tpmg_ctx *ctx)
+{
+    Tracer &t = ctx->tr;
+    if (t.open < 0) return cudaSuccess;
+    const cudaError_t e =
+        cudaEventRecordWithFlags(t.ev[2 * t.used + 1], t.open_s, ctx->capturing ? cudaEventRecordExternal : 0);
+    t.cls[t.used] = t.open;
+    ++t.used;
+    t.open = -1;
+    return e;
 }
 
 // Every device operation of the library goes through run(): it counts the
 // launch and the unknowns it processes, and brackets it with an event pair on
 // the issuing stream when its class is being timed.  While a graph is being
 // captured the pair becomes two event-record nodes of the graph, re-recorded
-// by every replay.
+// by every replay, and one pair spans each run of consecutive launches of the
+// timed class (for example all post-smoothing passes of a V-cycle): an event
+// node between two kernels costs microseconds of its own and would cut the
+// programmatic overlap of the kernels around it.  The capture closes the last
+// bracket before it ends (end_capture).
 template <class F>
 cudaError_t run(tpmg_ctx *ctx, int kclass, double units, F &&launch)
 {
@@ -252,20 +277,27 @@ cudaError_t run(tpmg_ctx *ctx, int kclass, double units, F &&launch)
     t.launches[kclass] += 1;
     t.units[kclass] += units;
     const bool timed = (t.mask >> kclass) & 1u;
-    if (timed) {
+    cudaError_t e = cudaSuccess;
+    if (t.open >= 0 && (t.open != kclass || t.open_s != ctx->issue)) e = close_bracket(ctx);
+    if (e != cudaSuccess) return e;
+    if (timed && t.open < 0) {
         if (2 * t.used + 2 > t.ev.size()) {
-            cudaError_t e = grow_events(t, t.used + 1024);
+            e = grow_events(t, t.used + 1024);
             if (e != cudaSuccess) return e;
         }
-        cudaError_t e = cudaEventRecordWithFlags(t.ev[2 * t.used], ctx->issue,
-                                                 ctx->capturing ? cudaEventRecordExternal : 0);
+        e = cudaEventRecordWithFlags(t.ev[2 * t.used], ctx->issue, ctx->capturing ? cudaEventRecordExternal : 0);
         if (e != cudaSuccess) return e;
+        t.open = kclass;
+        t.open_s = ctx->issue;
+        t.nl[t.used] = 0;
     }
-    cudaError_t e = launch();
-    if (timed && e == cudaSuccess) {
-        e = cudaEventRecordWithFlags(t.ev[2 * t.used + 1], ctx->issue, ctx->capturing ? cudaEventRecordExternal : 0);
-        t.cls[t.used] = kclass;
-        ++t.used;
+    e = launch();
+    if (timed) {
+        if (e == cudaSuccess) t.nl[t.used] += 1;
+        if (!ctx->capturing) {
+            const cudaError_t ec = close_bracket(ctx);
+            if (e == cudaSuccess) e = ec;
+        }
     }
     return e;
 }
@@ -593,7 +625,8 @@ tpmg_status vcycle_pcg(tpmg_ctx *ctx)
         CU(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
         ctx->capturing = true;
         ctx->issue = ctx->cap_stream;
-        const tpmg_status st = vcycle_fine(ctx, ctx->r, ctx->z);
+        tpmg_status st = vcycle_fine(ctx, ctx->r, ctx->z);
+        if (close_bracket(ctx) != cudaSuccess && st == TPMG_OK) st = fail(ctx, TPMG_ERR_CUDA, "event record");
         cudaGraph_t g = nullptr;
         const cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
         ctx->capturing = false;
@@ -640,6 +673,7 @@ tpmg_status capture_into(tpmg_ctx *ctx, cudaGraph_t g, const cudaGraphNode_t *de
     ctx->issue = ctx->cap_stream;
     ctx->capturing = true;
     tpmg_status st = body();
+    if (close_bracket(ctx) != cudaSuccess && st == TPMG_OK) st = fail(ctx, TPMG_ERR_CUDA, "event record");
     const cudaGraphNode_t *out = nullptr;
     size_t nout = 0;
     cudaStreamCaptureStatus cs;
@@ -1454,6 +1488,7 @@ tpmg_status tpmg_default_params(tpmg_params *p)
     p->scan_max_cells = 5120;
     p->outer = TPMG_OUTER_CG;
     p->prolongation = TPMG_PROLONG_CONSTANT;
+    p->pdl = 1;
     return TPMG_OK;
 }
 
@@ -1917,6 +1952,7 @@ tpmg_status tpmg_profile(tpmg_ctx *ctx, unsigned class_mask)
     std::fill(t.launches, t.launches + TPMG_K_COUNT, 0LL);
     std::fill(t.units, t.units + TPMG_K_COUNT, 0.0);
     t.used = 0;
+    t.open = -1;
     if (class_mask) CU(grow_events(t, 8192));   // created here, outside any timed region
     return TPMG_OK;
 }
@@ -1934,7 +1970,7 @@ tpmg_status tpmg_profile_read(tpmg_ctx *ctx, int kernel_class, long long *launch
         float m = 0.f;
         CU(cudaEventElapsedTime(&m, t.ev[2 * i], t.ev[2 * i + 1]));
         ms += m;
-        ++n;
+        n += t.nl[i];
     }
     if (launches) *launches = t.launches[kernel_class];
     if (total_ms) *total_ms = ms;

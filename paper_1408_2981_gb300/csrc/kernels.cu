@@ -227,6 +227,8 @@ template <int NT, bool FULL, bool ADV>
 __global__ void __launch_bounds__(NT) k_apply(OpView o, FullView fv, const double *__restrict__ x,
                                               double *__restrict__ y, int N, double *__restrict__ partials)
 {
+    pdl_wait();
+    pdl_trigger();
     double acc = 0.0;
     if (FULL) {
         for (int i = blockIdx.x * NT + threadIdx.x; i < N; i += gridDim.x * NT) {
@@ -275,6 +277,8 @@ __global__ void __launch_bounds__(NT) k_residual(OpView o, FullView full, const 
                                                  const double *__restrict__ u, double *__restrict__ r, int N,
                                                  double *__restrict__ partials)
 {
+    pdl_wait();
+    pdl_trigger();
     double acc = 0.0;
     const int stride = gridDim.x * NT, n_r = o.n_r;
     for (int i0 = blockIdx.x * NT + threadIdx.x; i0 < N; i0 += 2 * stride) {
@@ -325,6 +329,8 @@ template <int NT, int CM, bool ADV>
 __global__ void __launch_bounds__(NT) k_resid_restrict(OpView o, const double *__restrict__ f,
                                                        const double *__restrict__ u, double *__restrict__ fc, int Nc)
 {
+    pdl_wait();
+    pdl_trigger();
     if (CM != CM_FAC) {
         for (int ic = blockIdx.x * NT + threadIdx.x; ic < Nc; ic += gridDim.x * NT) {
             const int Tc = ic / o.n_r, k = ic - Tc * o.n_r;
@@ -371,6 +377,8 @@ __global__ void __launch_bounds__(NT) k_prolong_linear(const int4 *__restrict__ 
                                                        const double *__restrict__ uc, double *__restrict__ u,
                                                        int n_r, int N)
 {
+    pdl_wait();
+    pdl_trigger();
     for (int i = blockIdx.x * NT + threadIdx.x; i < N; i += gridDim.x * NT) {
         const int t = i / n_r, k = i - t * n_r, T = t >> 2, j = t & 3;
         const int4 nb = __ldg(&nbr_c[T]);
@@ -386,6 +394,8 @@ __global__ void __launch_bounds__(NT) k_prolong_linear(const int4 *__restrict__ 
 template <int NT>
 __global__ void __launch_bounds__(NT) k_prolong_add(const double *__restrict__ uc, double *__restrict__ u, int n_r, int N)
 {
+    pdl_wait();
+    pdl_trigger();
     for (int i = blockIdx.x * NT + threadIdx.x; i < N; i += gridDim.x * NT) {
         const int T = i / n_r, k = i - T * n_r;
         u[i] += uc[(T >> 2) * n_r + k];
@@ -600,12 +610,14 @@ __global__ void __launch_bounds__(256)
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (w >= n_slots) return;
-    const int T = __ldg(&cells[slot0 + w]);
+    // the column's cell, neighbours and couplings are set-up data: read before the wait
+    const int T = w < n_slots ? __ldg(&cells[slot0 + w]) : -1;
+    const int4 nb = MODE == PASS_RHS_ONLY || T < 0 ? make_int4(0, 0, 0, 0) : __ldg(&tnb[slot0 + w]);
+    const dbl4 g = (MODE == PASS_RHS_ONLY || HF || T < 0) ? dbl4{0.0, 0.0, 0.0, 0.0} : tg[slot0 + w];
+    pdl_wait();
+    pdl_trigger();
     if (T < 0) return;
     const int n_r = o.n_r;
-    const int4 nb = MODE == PASS_RHS_ONLY ? make_int4(0, 0, 0, 0) : __ldg(&tnb[slot0 + w]);
-    const dbl4 g = (MODE == PASS_RHS_ONLY || HF) ? dbl4{0.0, 0.0, 0.0, 0.0} : tg[slot0 + w];
     const bool n0 = MODE == PASS_NORMAL || (nb.w & 1), n1 = MODE == PASS_NORMAL || (nb.w & 2),
                n2 = MODE == PASS_NORMAL || (nb.w & 4);
     const size_t base = (size_t)T * n_r;
@@ -715,6 +727,9 @@ __global__ void __launch_bounds__(NT, STAGE ? 1 : 6)
         const int q = threadIdx.x - kRelaxCols;
         s_m[q] = __ldg(&fm[(size_t)t * 2 * kRelaxCols + q]);
     }
+    // everything above is set-up data; f and u come from earlier launches
+    pdl_wait();
+    pdl_trigger();
     __syncthreads();
     // elements per thread with loads in flight (fewer with the per-unknown stencil,
     // whose 32-byte rows take registers of their own)
@@ -834,6 +849,8 @@ __global__ void __launch_bounds__(32, 16)
         s_nb[lane] = __ldg(&tnb[q]);
         s_g[lane] = tg[q];
     }
+    pdl_wait();
+    pdl_trigger();
     __syncwarp();
     constexpr int U = 4;
     for (int e0 = lane; e0 < ne; e0 += 32 * U) {
@@ -927,6 +944,8 @@ template <int NT>
 __global__ void __launch_bounds__(NT) k_dot(const double *__restrict__ a, const double *__restrict__ b, int N,
                                             double *__restrict__ partials)
 {
+    pdl_wait();
+    pdl_trigger();
     double acc = 0.0;
     const int stride = gridDim.x * NT;
     int i = blockIdx.x * NT + threadIdx.x;
@@ -950,6 +969,8 @@ __global__ void __launch_bounds__(NT) k_axpy_pair(const Scalars *__restrict__ sc
                                                   double *__restrict__ r, int N, double *__restrict__ partials,
                                                   const double *__restrict__ z_old)
 {
+    pdl_wait();
+    pdl_trigger();
     const double alpha = sc->alpha;
     double acc = 0.0, accz = 0.0;
     const int stride = gridDim.x * NT;
@@ -993,6 +1014,8 @@ template <int NT>
 __global__ void __launch_bounds__(NT) k_xpby(const Scalars *__restrict__ sc, const double *__restrict__ z,
                                              double *__restrict__ p, int N)
 {
+    pdl_wait();
+    pdl_trigger();
     const double beta = sc->beta;
     const int stride = gridDim.x * NT;
     int i = blockIdx.x * NT + threadIdx.x;
@@ -1010,6 +1033,8 @@ __global__ void __launch_bounds__(NT) k_xpby(const Scalars *__restrict__ sc, con
 __global__ void __launch_bounds__(256) k_finish(int what, const double *__restrict__ partials, int n, Scalars *sc,
                                                 LoopCtl loop)
 {
+    pdl_wait();
+    pdl_trigger();
     double v = 0.0, v2 = 0.0;
     for (int i = threadIdx.x; i < n; i += 256) v += partials[i];
     v = block_sum<256>(v);
@@ -1112,6 +1137,8 @@ __global__ void __launch_bounds__(256) k_finish(int what, const double *__restri
 __global__ void __launch_bounds__(256) k_lincomb(long n, double a, const double *x, double b, const double *y,
                                                  double c, const double *z, double *out)
 {
+    pdl_wait();
+    pdl_trigger();
     for (long i = blockIdx.x * 256L + threadIdx.x; i < n; i += (long)gridDim.x * 256) {
         double v = a * x[i];
         if (y) v = fma(b, y[i], v);
@@ -1138,13 +1165,9 @@ cudaError_t launch_apply(const Launch &L, const LevelDev &lv, const VertDev &v, 
     const int grid = partials ? n_part : grid_for(N, kThreads, L.sm_count);
     const FullView fv{lv.cfull, lv.cvr, lv.cvx};
     // ADV: the factorised operator with vertical advection (compiled out without it)
-    if (lv.cfull)
-        k_apply<kThreads, true, false><<<grid, kThreads, 0, L.s>>>(make_view(lv, v, L.n_r), fv, x, y, N, partials);
-    else if (lv.area_x)
-        k_apply<kThreads, false, true><<<grid, kThreads, 0, L.s>>>(make_view(lv, v, L.n_r), fv, x, y, N, partials);
-    else
-        k_apply<kThreads, false, false><<<grid, kThreads, 0, L.s>>>(make_view(lv, v, L.n_r), fv, x, y, N, partials);
-    return cudaGetLastError();
+    auto kern = lv.cfull ? k_apply<kThreads, true, false>
+                         : (lv.area_x ? k_apply<kThreads, false, true> : k_apply<kThreads, false, false>);
+    return launch_k(L, kern, grid, kThreads, 0, make_view(lv, v, L.n_r), fv, x, y, N, partials);
 }
 
 cudaError_t launch_residual(const Launch &L, const LevelDev &lv, const VertDev &v, const double *f, const double *u,
@@ -1153,14 +1176,9 @@ cudaError_t launch_residual(const Launch &L, const LevelDev &lv, const VertDev &
     const int N = lv.n * L.n_r;
     const int grid = partials ? n_part : grid_for(N, kThreads, L.sm_count);
     const FullView fv{lv.cfull, lv.cvr, lv.cvx};
-    if (lv.cfull)
-        k_residual<kThreads, true, false><<<grid, kThreads, 0, L.s>>>(make_view(lv, v, L.n_r), fv, f, u, r, N, partials);
-    else if (lv.area_x)
-        k_residual<kThreads, false, true><<<grid, kThreads, 0, L.s>>>(make_view(lv, v, L.n_r), fv, f, u, r, N, partials);
-    else
-        k_residual<kThreads, false, false><<<grid, kThreads, 0, L.s>>>(make_view(lv, v, L.n_r), fv, f, u, r, N,
-                                                                      partials);
-    return cudaGetLastError();
+    auto kern = lv.cfull ? k_residual<kThreads, true, false>
+                         : (lv.area_x ? k_residual<kThreads, false, true> : k_residual<kThreads, false, false>);
+    return launch_k(L, kern, grid, kThreads, 0, make_view(lv, v, L.n_r), fv, f, u, r, N, partials);
 }
 
 cudaError_t launch_resid_restrict(const Launch &L, const LevelDev &fine, const LevelDev &coarse, const VertDev &v,
@@ -1168,33 +1186,29 @@ cudaError_t launch_resid_restrict(const Launch &L, const LevelDev &fine, const L
 {
     const int Nc = coarse.n * L.n_r, grid = grid_for(Nc, kThreads, L.sm_count);
     const OpView o = make_view(fine, v, L.n_r);
+    void (*kern)(OpView, const double *, const double *, double *, int);
     switch (stencil_form(fine)) {
-    case CM_FULL: k_resid_restrict<kThreads, CM_FULL, false><<<grid, kThreads, 0, L.s>>>(o, f, u, fc, Nc); break;
+    case CM_FULL: kern = k_resid_restrict<kThreads, CM_FULL, false>; break;
     case CM_PARTIAL:
-        if (fine.area_x) k_resid_restrict<kThreads, CM_PARTIAL, true><<<grid, kThreads, 0, L.s>>>(o, f, u, fc, Nc);
-        else k_resid_restrict<kThreads, CM_PARTIAL, false><<<grid, kThreads, 0, L.s>>>(o, f, u, fc, Nc);
+        kern = fine.area_x ? k_resid_restrict<kThreads, CM_PARTIAL, true> : k_resid_restrict<kThreads, CM_PARTIAL, false>;
         break;
-    default:
-        if (fine.area_x) k_resid_restrict<kThreads, CM_FAC, true><<<grid, kThreads, 0, L.s>>>(o, f, u, fc, Nc);
-        else k_resid_restrict<kThreads, CM_FAC, false><<<grid, kThreads, 0, L.s>>>(o, f, u, fc, Nc);
+    default: kern = fine.area_x ? k_resid_restrict<kThreads, CM_FAC, true> : k_resid_restrict<kThreads, CM_FAC, false>;
     }
-    return cudaGetLastError();
+    return launch_k(L, kern, grid, kThreads, 0, o, f, u, fc, Nc);
 }
 
 cudaError_t launch_prolong_add(const Launch &L, const LevelDev &fine, const double *uc, double *u)
 {
     const int N = fine.n * L.n_r;
-    k_prolong_add<kThreads><<<grid_for(N, kThreads, L.sm_count), kThreads, 0, L.s>>>(uc, u, L.n_r, N);
-    return cudaGetLastError();
+    return launch_k(L, k_prolong_add<kThreads>, grid_for(N, kThreads, L.sm_count), kThreads, 0, uc, u, L.n_r, N);
 }
 
 cudaError_t launch_prolong_linear(const Launch &L, const LevelDev &fine, const LevelDev &coarse, const double *uc,
                                   double *u)
 {
     const int N = fine.n * L.n_r;
-    k_prolong_linear<kThreads><<<grid_for(N, kThreads, L.sm_count), kThreads, 0, L.s>>>(coarse.nbr, coarse.plin, uc, u,
-                                                                                        L.n_r, N);
-    return cudaGetLastError();
+    return launch_k(L, k_prolong_linear<kThreads>, grid_for(N, kThreads, L.sm_count), kThreads, 0, coarse.nbr,
+                    coarse.plin, uc, u, L.n_r, N);
 }
 
 cudaError_t launch_twisted_factors(const Launch &L, const LevelDev &lv, const VertDev &v)
@@ -1215,9 +1229,8 @@ static cudaError_t relax_launch_t(const Launch &L, const LevelDev &lv, const Ver
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    kern<<<n_tasks, NT, smem, L.s>>>(make_view(lv, v, L.n_r), lv.task_cells, lv.task_nbr, lv.task_g, lv.rinv, lv.fb,
-                                     lv.fc, lv.fm, lv.steps, lv.jmid, task0, f, u_in, u_out, u_fine, relax);
-    return cudaGetLastError();
+    return launch_k(L, kern, n_tasks, NT, smem, make_view(lv, v, L.n_r), lv.task_cells, lv.task_nbr, lv.task_g,
+                    lv.rinv, lv.fb, lv.fc, lv.fm, lv.steps, lv.jmid, task0, f, u_in, u_out, u_fine, relax);
 }
 
 // Kernel choice (RELAX_*): the level's autotuned variant, or without one the
@@ -1232,10 +1245,9 @@ static cudaError_t relax_scan_r(const Launch &L, const LevelDev &lv, const VertD
     const int var = lv.relax_variant < 0 ? RELAX_CTA128 : lv.relax_variant;
     const int wpb = 1 << var;   // CTAs of 1, 2, 4 or 8 warps: the autotuner's variants, same arithmetic
     const int n_slots = n_tasks * kRelaxCols;
-    k_relax_scan<MODE, R, HF><<<(n_slots + wpb - 1) / wpb, 32 * wpb, 0, L.s>>>(
-        make_view(lv, v, L.n_r), lv.task_cells, lv.task_nbr, lv.task_g, lv.rinv1, lv.fb1, lv.fc1, task0 * kRelaxCols,
-        n_slots, f, u_in, u_out, u_fine, relax);
-    return cudaGetLastError();
+    return launch_k(L, k_relax_scan<MODE, R, HF>, (n_slots + wpb - 1) / wpb, 32 * wpb, 0, make_view(lv, v, L.n_r),
+                    lv.task_cells, lv.task_nbr, lv.task_g, lv.rinv1, lv.fb1, lv.fc1, task0 * kRelaxCols, n_slots, f,
+                    u_in, u_out, u_fine, relax);
 }
 
 template <int MODE, bool HF>
@@ -1252,18 +1264,22 @@ static cudaError_t relax_scan(const Launch &L, const LevelDev &lv, const VertDev
 }
 
 template <int MODE, bool HF>
-static cudaError_t relax_launch_hf(const Launch &L, const LevelDev &lv, const VertDev &v, int task0, int n_tasks,
+static cudaError_t relax_launch_hf(const Launch &L0, const LevelDev &lv, const VertDev &v, int task0, int n_tasks,
                                    double relax, const double *f, const double *u_in, double *u_out, double *u_fine)
 {
-    if (lv.scan) return relax_scan<MODE, HF>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
+    if (lv.scan) return relax_scan<MODE, HF>(L0, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
+    // The twisted-task kernels are launched plainly: measured on GB300, programmatic
+    // launch made the FP64 solves that use them 1-2% slower (refinement 6 x 64 and
+    // 7 x 128), while it speeds up the scan, transfer and vector kernels.
+    Launch L = L0;
+    L.pdl = false;
     const size_t tile = (((size_t)kRelaxCols * (L.n_r + 1) + 1) & ~(size_t)1) * sizeof(double);
     int var = lv.relax_variant;
     if (var < 0) var = (n_tasks >= 8 * L.sm_count && tile <= 32 * 1024) ? RELAX_WARP : RELAX_CTA128;
     if (var == RELAX_WARP && tile <= 32 * 1024) {
-        k_relax_warp<MODE, HF><<<n_tasks, 32, tile, L.s>>>(make_view(lv, v, L.n_r), lv.task_cells, lv.task_nbr,
-                                                           lv.task_g, lv.rinv, lv.fb, lv.fc, lv.fm, lv.steps, lv.jmid,
-                                                           task0, f, u_in, u_out, u_fine, relax);
-        return cudaGetLastError();
+        return launch_k(L, k_relax_warp<MODE, HF>, n_tasks, 32, tile, make_view(lv, v, L.n_r), lv.task_cells,
+                        lv.task_nbr, lv.task_g, lv.rinv, lv.fb, lv.fc, lv.fm, lv.steps, lv.jmid, task0, f, u_in, u_out,
+                        u_fine, relax);
     }
     const size_t staged = tile + (size_t)2 * lv.steps * 32 * sizeof(double);
     if (staged > 160 * 1024)
@@ -1304,38 +1320,31 @@ cudaError_t launch_relax(const Launch &L, const LevelDev &lv, const VertDev &v, 
 
 cudaError_t launch_dot(const Launch &L, long n, const double *a, const double *b, double *partials, int n_part)
 {
-    k_dot<kThreads><<<n_part, kThreads, 0, L.s>>>(a, b, (int)n, partials);
-    return cudaGetLastError();
+    return launch_k(L, k_dot<kThreads>, n_part, kThreads, 0, a, b, (int)n, partials);
 }
 
 cudaError_t launch_finish(const Launch &L, int what, const double *partials, int n_part, Scalars *sc,
                           const LoopCtl *loop)
 {
-    k_finish<<<1, 256, 0, L.s>>>(what, partials, n_part, sc, loop ? *loop : LoopCtl{0, 0.0, 0, nullptr});
-    return cudaGetLastError();
+    return launch_k(L, k_finish, 1, 256, 0, what, partials, n_part, sc, loop ? *loop : LoopCtl{0, 0.0, 0, nullptr});
 }
 
 cudaError_t launch_axpy_pair(const Launch &L, long n, const Scalars *sc, const double *p, const double *q, double *u,
                              double *r, double *partials, int n_part, const double *z_old)
 {
-    if (z_old)
-        k_axpy_pair<kThreads, true><<<n_part, kThreads, 0, L.s>>>(sc, p, q, u, r, (int)n, partials, z_old);
-    else
-        k_axpy_pair<kThreads, false><<<n_part, kThreads, 0, L.s>>>(sc, p, q, u, r, (int)n, partials, nullptr);
-    return cudaGetLastError();
+    return launch_k(L, z_old ? k_axpy_pair<kThreads, true> : k_axpy_pair<kThreads, false>, n_part, kThreads, 0, sc, p,
+                    q, u, r, (int)n, partials, z_old);
 }
 
 cudaError_t launch_lincomb(const Launch &L, long n, double a, const double *x, double b, const double *y, double c,
                            const double *z, double *out)
 {
-    k_lincomb<<<grid_for(n, 256, L.sm_count), 256, 0, L.s>>>(n, a, x, b, y, c, z, out);
-    return cudaGetLastError();
+    return launch_k(L, k_lincomb, grid_for(n, 256, L.sm_count), 256, 0, n, a, x, b, y, c, z, out);
 }
 
 cudaError_t launch_xpby(const Launch &L, long n, const Scalars *sc, const double *z, double *p)
 {
-    k_xpby<kThreads><<<grid_for(n, kThreads, L.sm_count), kThreads, 0, L.s>>>(sc, z, p, (int)n);
-    return cudaGetLastError();
+    return launch_k(L, k_xpby<kThreads>, grid_for(n, kThreads, L.sm_count), kThreads, 0, sc, z, p, (int)n);
 }
 
 }  // namespace tpmg

@@ -89,10 +89,12 @@ __global__ void __launch_bounds__(256)
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (w >= n_slots) return;
-    const int T = __ldg(&cells[slot0 + w]);
+    // the column's cell and neighbours are set-up data: read before the wait
+    const int T = w < n_slots ? __ldg(&cells[slot0 + w]) : -1;
+    const int4 nb = MODE == PASS_RHS_ONLY || T < 0 ? make_int4(0, 0, 0, 0) : __ldg(&tnb[slot0 + w]);
+    pdl_wait();
+    pdl_trigger();
     if (T < 0) return;
-    const int4 nb = MODE == PASS_RHS_ONLY ? make_int4(0, 0, 0, 0) : __ldg(&tnb[slot0 + w]);
     const bool n0 = MODE == PASS_NORMAL || (nb.w & 1), n1 = MODE == PASS_NORMAL || (nb.w & 2),
                n2 = MODE == PASS_NORMAL || (nb.w & 4);
     const size_t base = (size_t)T * n_r;
@@ -179,6 +181,8 @@ __global__ void __launch_bounds__(kThreads32)
                        const float *__restrict__ dr32, int n_r, const TF *__restrict__ f,
                        const float *__restrict__ u, float *__restrict__ fc, int Nc)
 {
+    pdl_wait();
+    pdl_trigger();
     for (int ic = blockIdx.x * kThreads32 + threadIdx.x; ic < Nc; ic += gridDim.x * kThreads32) {
         const int Tc = ic / n_r, k = ic - Tc * n_r;
         float s = 0.f;
@@ -213,6 +217,8 @@ __global__ void __launch_bounds__(kThreads32) k_prolong_linear32(const int4 *__r
                                                                  const float *__restrict__ uc, float *__restrict__ u,
                                                                  int n_r, int N)
 {
+    pdl_wait();
+    pdl_trigger();
     for (int i = blockIdx.x * kThreads32 + threadIdx.x; i < N; i += gridDim.x * kThreads32) {
         const int t = i / n_r, k = i - t * n_r, T = t >> 2, j = t & 3;
         const int4 nb = __ldg(&nbr_c[T]);
@@ -228,6 +234,8 @@ __global__ void __launch_bounds__(kThreads32) k_prolong_linear32(const int4 *__r
 __global__ void __launch_bounds__(kThreads32) k_prolong_add32(const float *__restrict__ uc, float *__restrict__ u,
                                                               int n_r, int N)
 {
+    pdl_wait();
+    pdl_trigger();
     for (int i = blockIdx.x * kThreads32 + threadIdx.x; i < N; i += gridDim.x * kThreads32) {
         const int T = i / n_r, k = i - T * n_r;
         u[i] += uc[(T >> 2) * n_r + k];
@@ -236,6 +244,8 @@ __global__ void __launch_bounds__(kThreads32) k_prolong_add32(const float *__res
 
 __global__ void __launch_bounds__(kThreads32) k_to_f64(const float *__restrict__ x, double *__restrict__ y, int N)
 {
+    pdl_wait();
+    pdl_trigger();
     for (int i = blockIdx.x * kThreads32 + threadIdx.x; i < N; i += gridDim.x * kThreads32) y[i] = (double)x[i];
 }
 
@@ -254,10 +264,9 @@ cudaError_t relax32_r(const Launch &L, const LevelDev &lv, int task0, int n_task
     const int var = lv.relax_variant < 0 ? RELAX_CTA128 : lv.relax_variant;
     const int wpb = 1 << var;
     const int n_slots = n_tasks * kRelaxCols;
-    k_relax32_scan<MODE, TF, R><<<(n_slots + wpb - 1) / wpb, 32 * wpb, 0, L.s>>>(
-        lv.task_cells, lv.task_nbr, lv.cpack, lv.rinv32, lv.fb32, lv.fc32, L.n_r, task0 * kRelaxCols, n_slots, f, u_in,
-        u_out, u_fine, out64, relax);
-    return cudaGetLastError();
+    return launch_k(L, k_relax32_scan<MODE, TF, R>, (n_slots + wpb - 1) / wpb, 32 * wpb, 0, lv.task_cells,
+                    lv.task_nbr, lv.cpack, lv.rinv32, lv.fb32, lv.fc32, L.n_r, task0 * kRelaxCols, n_slots, f, u_in,
+                    u_out, u_fine, out64, relax);
 }
 
 template <int MODE, typename TF>
@@ -292,24 +301,22 @@ cudaError_t launch_resid_restrict32(const Launch &L, const LevelDev &fine, const
                                     const float *u, float *fc)
 {
     const int Nc = coarse.n * L.n_r;
-    k_resid_restrict32<TF><<<grid32(Nc, L.sm_count), kThreads32, 0, L.s>>>(
-        fine.nbr, fine.cpack, fine.cvert, fine.cxv_on ? fine.cxv : nullptr, L.dr32, L.n_r, f, u, fc, Nc);
-    return cudaGetLastError();
+    return launch_k(L, k_resid_restrict32<TF>, grid32(Nc, L.sm_count), kThreads32, 0, fine.nbr, fine.cpack, fine.cvert,
+                    fine.cxv_on ? fine.cxv : nullptr, L.dr32, L.n_r, f, u, fc, Nc);
 }
 
 cudaError_t launch_prolong_add32(const Launch &L, const LevelDev &fine, const float *uc, float *u)
 {
     const int N = fine.n * L.n_r;
-    k_prolong_add32<<<grid32(N, L.sm_count), kThreads32, 0, L.s>>>(uc, u, L.n_r, N);
-    return cudaGetLastError();
+    return launch_k(L, k_prolong_add32, grid32(N, L.sm_count), kThreads32, 0, uc, u, L.n_r, N);
 }
 
 cudaError_t launch_prolong_linear32(const Launch &L, const LevelDev &fine, const LevelDev &coarse, const float *uc,
                                     float *u)
 {
     const int N = fine.n * L.n_r;
-    k_prolong_linear32<<<grid32(N, L.sm_count), kThreads32, 0, L.s>>>(coarse.nbr, coarse.plin32, uc, u, L.n_r, N);
-    return cudaGetLastError();
+    return launch_k(L, k_prolong_linear32, grid32(N, L.sm_count), kThreads32, 0, coarse.nbr, coarse.plin32, uc, u,
+                    L.n_r, N);
 }
 
 cudaError_t launch_thomas_factors32(const Launch &L, const LevelDev &lv)
@@ -321,8 +328,7 @@ cudaError_t launch_thomas_factors32(const Launch &L, const LevelDev &lv)
 
 cudaError_t launch_to_f64(const Launch &L, long n, const float *x, double *y)
 {
-    k_to_f64<<<grid32(n, L.sm_count), kThreads32, 0, L.s>>>(x, y, (int)n);
-    return cudaGetLastError();
+    return launch_k(L, k_to_f64, grid32(n, L.sm_count), kThreads32, 0, x, y, (int)n);
 }
 
 template cudaError_t launch_relax32<double>(const Launch &, const LevelDev &, int, int, int, float, const double *,

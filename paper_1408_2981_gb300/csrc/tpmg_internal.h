@@ -176,7 +176,41 @@ struct Launch {
     int sm_count;
     const double *dr = nullptr;    // [n_r] r_{k+1} - r_k (mixed precision: advection rows)
     const float *dr32 = nullptr;
+    bool pdl = false;              // launch with programmatic stream serialisation (launch_k)
 };
+
+#ifdef __CUDACC__
+// Programmatic dependent launch.  A kernel launched by launch_k with L.pdl set
+// may be scheduled while its predecessor in the stream is still running, so
+// that its launch and its reads of set-up data overlap the predecessor's tail.
+// Every such kernel calls pdl_wait() before it touches memory that an earlier
+// launch writes or reads; the wait returns once the predecessor has completed
+// and its writes are visible (at once for a kernel launched without the
+// attribute).  Since every kernel of the chain waits, the memory effects keep
+// the order of plain launches and the results are bit-identical.
+// pdl_trigger() lets the successor be scheduled; each kernel issues it right
+// after its wait, so at most one launch runs ahead.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(const Launch &L, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, Args... args)
+{
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = L.s;
+    cfg.attrs = at;
+    cfg.numAttrs = L.pdl ? 1 : 0;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, args...);
+    const cudaError_t last = cudaGetLastError();
+    return e != cudaSuccess ? e : last;
+}
+#endif
 
 // Right-hand side of a relaxation pass: NORMAL f + sum of all neighbours;
 // ZERO (first forward sweep from a zero guess) only neighbours of a smaller

@@ -1,0 +1,49 @@
+"""Per-class kernel timing (tpmg_profile / tpmg_profile_read) through the C ABI
+(needs a GPU).
+
+Launches made one by one each get an event pair; inside a captured graph one
+pair spans each run of consecutive launches of the timed class.  Either way
+the timing must not change a result, every launch of the class must lie in
+some pair (timed counts them), and a replayed graph's pairs hold its latest
+replay.
+"""
+import pytest
+
+from paper_1408_2981_gb300 import binding, build, inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+KW = dict(refinement=4, n_levels=5, n_r=24, grading=1.05, courant_c=30.0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+
+
+@pytest.mark.parametrize("graphs", [1, 0])
+@pytest.mark.parametrize("pdl", [1, 0])
+def test_timed_solve_is_bit_identical_and_counts_every_launch(graphs, pdl):
+    s = binding.Solver(graphs=graphs, pdl=pdl, **KW)
+    ref = binding.Solver(graphs=graphs, pdl=pdl, **KW)
+    f = torch.from_numpy(inputs.uniform_pm1(inputs.SEED_UNIFORM_SMALL + 90, s.N)).cuda()
+    u_ref = torch.zeros_like(f)
+    _, it_ref, rel_ref, _ = ref.solve(f, u_ref, rtol=1e-8, max_iter=50)
+    s.profile(classes=("relax", "restrict"))
+    for rep in range(2):
+        u = torch.zeros_like(f)
+        _, it, rel, _ = s.solve(f, u, rtol=1e-8, max_iter=50)
+        torch.cuda.synchronize()
+        assert it == it_ref and rel == rel_ref and torch.equal(u, u_ref)
+    pr = s.profile_read()
+    for cls in ("relax", "restrict"):
+        p = pr[cls]
+        assert p["launches"] > 0 and p["ms"] > 0.0
+        if graphs:
+            # the V-cycle graph's pairs hold its latest replay: one V-cycle's launches
+            assert 0 < p["timed"] < p["launches"] and p["launches"] % p["timed"] == 0
+        else:
+            assert p["timed"] == p["launches"]
+    assert pr["apply"]["timed"] == 0 and pr["apply"]["launches"] > 0
