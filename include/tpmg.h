@@ -130,8 +130,10 @@ typedef struct {
                             results are identical. */
     int    scan_max_cells; /* FP64 V-cycle: levels with at most this many cells relax one warp per
                             column with the Thomas recurrences as warp scans (short latency, more
-                            FP64 work); larger levels use the 16-column twisted-factorisation tasks.
-                            A fixed rule, so the results do not depend on timings (>= 0). */
+                            FP64 work); larger levels use the 16-column twisted-factorisation tasks,
+                            except for their colours of at most scan_max_cells / 2 cells, which
+                            are relaxed by the warp scans too.  A fixed rule, so the results do
+                            not depend on timings (>= 0). */
     int    outer;        /* TPMG_OUTER_*: the outer iteration of tpmg_solve.  Richardson and
                             BiCGStab run their loop from the host (one read-back per dot product)
                             and are not available in a batch. */

@@ -1326,7 +1326,15 @@ tpmg_status upload_level(tpmg_ctx *ctx, int l)
     }
     if (!mixed) {
         D.scan = H.n <= p.scan_max_cells;
-        if (D.scan) {
+        // on a larger level, colours of at most scan_max_cells / 2 cells are relaxed by the
+        // warp scans too: such a pass is latency-bound, and a twisted-task pass takes the
+        // time of one task's serial column solve however few tasks it has
+        D.scan_pass_tasks = -1;
+        if (!D.scan)
+            for (int c = 0; c < H.n_colours; ++c)
+                if (D.colour_cells[c] <= p.scan_max_cells / 2)
+                    D.scan_pass_tasks = std::max(D.scan_pass_tasks, D.colour_task_off[c + 1] - D.colour_task_off[c]);
+        if (D.scan || D.scan_pass_tasks >= 0) {
             CU(dalloc(ctx, &D.rinv1, nn));
             CU(dalloc(ctx, &D.fb1, nn));
             CU(dalloc(ctx, &D.fc1, nn));
@@ -1400,7 +1408,7 @@ tpmg_status upload_level(tpmg_ctx *ctx, int l)
     }
     if (!mixed) {
         CU(launch_twisted_factors(launch_of(ctx), D, ctx->vert));
-        if (D.scan) CU(launch_thomas_factors(launch_of(ctx), D, ctx->vert));
+        if (D.rinv1) CU(launch_thomas_factors(launch_of(ctx), D, ctx->vert));
     } else {
         CU(launch_thomas_factors32(launch_of(ctx), D));
     }
@@ -1713,9 +1721,7 @@ tpmg_status tpmg_set_outer_profiles(tpmg_ctx *ctx, const double *h_beta, const d
             const tpmg_status st = upload_advection(ctx, Hl, Dl, lx, lr);
             if (st != TPMG_OK) return st;
             CU(launch_twisted_factors(launch_of(ctx), Dl, ctx->vert));
-            if (Dl.scan) {
-                CU(launch_thomas_factors(launch_of(ctx), Dl, ctx->vert));
-            }
+            if (Dl.rinv1) CU(launch_thomas_factors(launch_of(ctx), Dl, ctx->vert));
             CU(cudaStreamSynchronize(ctx->stream));
         }
     }

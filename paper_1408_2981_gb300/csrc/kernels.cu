@@ -1239,10 +1239,9 @@ static cudaError_t relax_launch_t(const Launch &L, const LevelDev &lv, const Ver
 // CTA variants stage the multipliers in shared memory by cp.async when they
 // fit; a column too tall for that runs unstaged with 128 threads.
 template <int MODE, int R, bool HF>
-static cudaError_t relax_scan_r(const Launch &L, const LevelDev &lv, const VertDev &v, int task0, int n_tasks,
+static cudaError_t relax_scan_r(const Launch &L, const LevelDev &lv, const VertDev &v, int var, int task0, int n_tasks,
                                 double relax, const double *f, const double *u_in, double *u_out, double *u_fine)
 {
-    const int var = lv.relax_variant < 0 ? RELAX_CTA128 : lv.relax_variant;
     const int wpb = 1 << var;   // CTAs of 1, 2, 4 or 8 warps: the autotuner's variants, same arithmetic
     const int n_slots = n_tasks * kRelaxCols;
     return launch_k(L, k_relax_scan<MODE, R, HF>, (n_slots + wpb - 1) / wpb, 32 * wpb, 0, make_view(lv, v, L.n_r),
@@ -1251,23 +1250,30 @@ static cudaError_t relax_scan_r(const Launch &L, const LevelDev &lv, const VertD
 }
 
 template <int MODE, bool HF>
-static cudaError_t relax_scan(const Launch &L, const LevelDev &lv, const VertDev &v, int task0, int n_tasks,
+static cudaError_t relax_scan(const Launch &L, const LevelDev &lv, const VertDev &v, int var, int task0, int n_tasks,
                               double relax, const double *f, const double *u_in, double *u_out, double *u_fine)
 {
     const int n = L.n_r;
-    if (n <= 32) return relax_scan_r<MODE, 1, HF>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
-    if (n <= 64) return relax_scan_r<MODE, 2, HF>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
-    if (n <= 128) return relax_scan_r<MODE, 4, HF>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
-    if (n <= 256) return relax_scan_r<MODE, 8, HF>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
-    if (n <= 512) return relax_scan_r<MODE, 16, HF>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
-    return relax_scan_r<MODE, 32, HF>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
+    if (n <= 32) return relax_scan_r<MODE, 1, HF>(L, lv, v, var, task0, n_tasks, relax, f, u_in, u_out, u_fine);
+    if (n <= 64) return relax_scan_r<MODE, 2, HF>(L, lv, v, var, task0, n_tasks, relax, f, u_in, u_out, u_fine);
+    if (n <= 128) return relax_scan_r<MODE, 4, HF>(L, lv, v, var, task0, n_tasks, relax, f, u_in, u_out, u_fine);
+    if (n <= 256) return relax_scan_r<MODE, 8, HF>(L, lv, v, var, task0, n_tasks, relax, f, u_in, u_out, u_fine);
+    if (n <= 512) return relax_scan_r<MODE, 16, HF>(L, lv, v, var, task0, n_tasks, relax, f, u_in, u_out, u_fine);
+    return relax_scan_r<MODE, 32, HF>(L, lv, v, var, task0, n_tasks, relax, f, u_in, u_out, u_fine);
 }
 
 template <int MODE, bool HF>
 static cudaError_t relax_launch_hf(const Launch &L0, const LevelDev &lv, const VertDev &v, int task0, int n_tasks,
                                    double relax, const double *f, const double *u_in, double *u_out, double *u_fine)
 {
-    if (lv.scan) return relax_scan<MODE, HF>(L0, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
+    if (lv.scan) {
+        const int var = lv.relax_variant < 0 ? RELAX_CTA128 : lv.relax_variant;
+        return relax_scan<MODE, HF>(L0, lv, v, var, task0, n_tasks, relax, f, u_in, u_out, u_fine);
+    }
+    // a small colour of a larger level: warp scans in CTAs of 4 warps (the level's tuned
+    // variant is a twisted-task kernel's)
+    if (n_tasks <= lv.scan_pass_tasks)
+        return relax_scan<MODE, HF>(L0, lv, v, RELAX_CTA128, task0, n_tasks, relax, f, u_in, u_out, u_fine);
     // The twisted-task kernels are launched plainly: measured on GB300, programmatic
     // launch made the FP64 solves that use them 1-2% slower (refinement 6 x 64 and
     // 7 x 128), while it speeds up the scan, transfer and vector kernels.

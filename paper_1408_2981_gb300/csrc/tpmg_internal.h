@@ -129,8 +129,11 @@ struct LevelDev {
     double *rinv = nullptr, *fb = nullptr, *fc = nullptr, *fm = nullptr;
     // FP64 levels with at most params.scan_max_cells cells: relaxed one warp per column
     // (k_relax_scan) with one-directional factors per unknown [n][n_r]:
-    // rinv1 = 1 / p_k, fb1 = c_k / p_k, fc1 = c_{k+1} / p_k
+    // rinv1 = 1 / p_k, fb1 = c_k / p_k, fc1 = c_{k+1} / p_k.  On larger levels a colour
+    // pass of at most scan_pass_tasks tasks (a small colour of the colouring) is relaxed
+    // the same way, with the factors held for the whole level; -1: none
     bool scan = false;
+    int scan_pass_tasks = -1;
     double *rinv1 = nullptr, *fb1 = nullptr, *fc1 = nullptr;
     // workspaces (coarse levels; the finest level uses caller / PCG buffers)
     double *f = nullptr, *u = nullptr, *u2 = nullptr;
