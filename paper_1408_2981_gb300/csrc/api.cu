@@ -1389,6 +1389,44 @@ tpmg_status upload_level(tpmg_ctx *ctx, int l)
         if (tasks[q] >= 0) { tnb[q] = nb[tasks[q]]; tg[q] = g[tasks[q]]; }
     CU(cudaMemcpyAsync(D.task_nbr, tnb.data(), tnb.size() * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(D.task_g, tg.data(), tg.size() * sizeof(dbl4), cudaMemcpyHostToDevice, ctx->stream));
+    // the restriction's view of the coarse cells (FP64 levels with a coarser one): each
+    // coarse cell's edges to outside cells, which must be 6 (3 of the 12 child-edge
+    // sides pair up inside), else the level keeps the child-by-child kernel
+    std::vector<RestrictGeo> rg;   // alive until the final synchronise
+    if (!mixed && l > 0) {
+        const int nc = H.n / 4;
+        rg.resize(nc);
+        bool ok = true;
+        for (int Tc = 0; Tc < nc && ok; ++Tc) {
+            int xe[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            double ge[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, gx[4], A[4], Ar[4];
+            int m = 0;
+            for (int j = 0; j < 4; ++j) {
+                const int T = 4 * Tc + j;
+                const int nbT[3] = {nb[T].x, nb[T].y, nb[T].z};
+                const double gT[3] = {g[T].x, g[T].y, g[T].z};
+                gx[j] = 0.0;
+                for (int e = 0; e < 3; ++e) {
+                    if (nbT[e] / 4 == Tc) continue;
+                    if (m == 6) { ok = false; break; }
+                    xe[m] = nbT[e];
+                    ge[m++] = gT[e];
+                    gx[j] += gT[e];
+                }
+                A[j] = areaB[T];
+                Ar[j] = areaR[T];
+            }
+            ok = ok && m == 6;
+            rg[Tc] = RestrictGeo{make_int4(xe[0], xe[1], xe[2], xe[3]), make_int4(xe[4], xe[5], 0, 0),
+                                 dbl4{ge[0], ge[1], ge[2], ge[3]}, dbl4{ge[4], ge[5], 0.0, 0.0},
+                                 dbl4{gx[0], gx[1], gx[2], gx[3]}, dbl4{A[0], A[1], A[2], A[3]},
+                                 dbl4{Ar[0], Ar[1], Ar[2], Ar[3]}};
+        }
+        if (ok) {
+            CU(dalloc(ctx, &D.rgeo, (size_t)nc));
+            CU(cudaMemcpyAsync(D.rgeo, rg.data(), rg.size() * sizeof(RestrictGeo), cudaMemcpyHostToDevice, ctx->stream));
+        }
+    }
     {
         const tpmg_status st = upload_advection(ctx, H, D, nullptr, nullptr);
         if (st != TPMG_OK) return st;

@@ -48,6 +48,16 @@ bool build_host_grid(const tpmg_params &p, HostGrid &grid, std::string &err);
 struct alignas(32) dbl4 {   // four doubles, one 32-byte load
     double x, y, z, w;
 };
+// One coarse cell seen from the residual restriction of the factorised operator
+// (k_restrict_fac).  Summed over the cell's 4 children, the horizontal fluxes across
+// the 3 edges between children cancel (each edge's weight is stored once for both
+// sides), so only the 6 edges from a child to a cell outside the coarse cell remain.
+struct alignas(32) RestrictGeo {
+    int4 x0, x1;   // the outside cells of those 6 edges (x1.z = x1.w = 0, with weight 0)
+    dbl4 g0, g1;   // the edges' weights g_e (times the edge's alpha_S factor)
+    dbl4 gext;     // per child j: the sum of the weights of its outside edges
+    dbl4 A, Ar;    // per child j: |T_j| beta^S_T, |T_j| alpha_r^S_T
+};
 struct alignas(8) bf16x4 {   // four bfloat16 values (raw bits), one 8-byte load
     unsigned short x, y, z, w;
 };
@@ -134,6 +144,9 @@ struct LevelDev {
     // the same way, with the factors held for the whole level; -1: none
     bool scan = false;
     int scan_pass_tasks = -1;
+    // FP64 levels with a coarser level below them: the restriction's view of each
+    // coarse cell [n / 4], or null (then the kernel forms every child's residual)
+    RestrictGeo *rgeo = nullptr;
     double *rinv1 = nullptr, *fb1 = nullptr, *fc1 = nullptr;
     // workspaces (coarse levels; the finest level uses caller / PCG buffers)
     double *f = nullptr, *u = nullptr, *u2 = nullptr;
