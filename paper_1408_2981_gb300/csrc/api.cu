@@ -1650,6 +1650,18 @@ tpmg_status tpmg_setup_profiles(const tpmg_params *params, const tpmg_profiles *
         dalloc(ctx, &ctx->d_net_s, 3) != cudaSuccess)
         return bail(TPMG_ERR_OOM);
     if (cudaMallocHost(&ctx->h_sc, sizeof(Scalars)) != cudaSuccess) return bail(TPMG_ERR_OOM);
+    {
+        // finest level: per-row products of the outer operator's coefficients (16 bytes per
+        // unknown), allocated after everything the solver needs and only where they fit;
+        // without them the operator stays matrix-free
+        LevelDev &D = ctx->lv.back();
+        if (dalloc(ctx, &D.om, (size_t)ctx->N) != cudaSuccess || dalloc(ctx, &D.oc, (size_t)ctx->N) != cudaSuccess) {
+            (void)cudaGetLastError();   // a failed allocation leaves no sticky error
+            D.om = D.oc = nullptr;
+        } else if (launch_outer_products(launch_of(ctx), D, ctx->vert) != cudaSuccess) {
+            return bail(TPMG_ERR_CUDA);
+        }
+    }
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return bail(TPMG_ERR_CUDA);
     if (ctx->p.autotune) {
         tpmg_status st = autotune(ctx);

@@ -69,12 +69,15 @@ struct OpView {
     const double *__restrict__ xp;
     const double *__restrict__ cx;
     const double *__restrict__ dr;
+    // per-row products of the factorised coefficients (LevelDev::om, oc), or null
+    const double *__restrict__ om;
+    const double *__restrict__ oc;
 };
 
 inline OpView make_view(const LevelDev &lv, const VertDev &v, int n_r)
 {
     return OpView{lv.nbr, lv.g, lv.area, lv.area_r, v.vol, v.w, v.hr, n_r, lv.vc, lv.vcr,
-                  lv.area_x, v.xm, v.xp, lv.vcx_on ? lv.vcx : nullptr, v.dr};
+                  lv.area_x, v.xm, v.xp, lv.vcx_on ? lv.vcx : nullptr, v.dr, lv.om, lv.oc};
 }
 
 // Stencil form of a level's V-cycle operator: factorised profiles (TPMG^fac), alpha_r
@@ -237,6 +240,33 @@ __global__ void __launch_bounds__(NT) k_apply(OpView o, FullView fv, const doubl
             y[i] = v;
             acc = fma(x[i], v, acc);
         }
+    } else if (!ADV && o.om) {
+        // stored row products: the flux through the row's lower face, F_k = oc_k (x_k - x_{k-1}),
+        // is formed once and handed to the row below by a shuffle, so the vertical part is
+        // F_k - F_{k+1}; the row is om x_k - hr_k sum_e g_e x_e + F_k - F_{k+1} (8 FP64 operations)
+        const int lane = threadIdx.x & 31;
+        const int stride = gridDim.x * (NT / 32) * 31;
+        for (int base = (blockIdx.x * (NT / 32) + (threadIdx.x >> 5)) * 31; base < N; base += stride) {
+            const int i = base + lane;
+            int T = 0, k = 0;
+            double xc = 0.0, F = 0.0;
+            if (i < N) {
+                T = i / o.n_r;
+                k = i - T * o.n_r;
+                xc = x[i];
+                if (k > 0) F = __ldg(&o.oc[i]) * (xc - x[i - 1]);
+            }
+            const double Fu = __shfl_down_sync(0xffffffffu, F, 1);
+            if (lane < 31 && i < N) {
+                const int n_r = o.n_r;
+                const int4 nb = __ldg(&o.nbr[T]);
+                const dbl4 g = o.g[T];
+                const double S = fma(g.z, x[nb.z * n_r + k], fma(g.y, x[nb.y * n_r + k], g.x * x[nb.x * n_r + k]));
+                const double v = fma(__ldg(&o.om[i]), xc, fma(-__ldg(&o.hr[k]), S, F - Fu));
+                y[i] = v;
+                acc = fma(xc, v, acc);
+            }
+        }
     } else {
         // each warp takes 32 consecutive rows and writes the first 31; lane 31 only hands its
         // lower difference to lane 30 (apply_at_lanes)
@@ -267,6 +297,19 @@ __global__ void __launch_bounds__(NT) k_apply(OpView o, FullView fv, const doubl
 }
 
 __device__ __forceinline__ bool is_zero(double v) { return (__double_as_longlong(v) << 1) == 0; }
+
+// The per-row products of the factorised coefficients used by k_apply (set-up):
+// om = |T| v_k + hr_k G_T, the same expression apply_at_lanes forms per row, and
+// oc = |T| alpha_r^S w_k of the row's lower face.
+__global__ void __launch_bounds__(256) k_outer_products(OpView o, int N, double *__restrict__ om,
+                                                        double *__restrict__ oc)
+{
+    for (int i = blockIdx.x * 256 + threadIdx.x; i < N; i += gridDim.x * 256) {
+        const int T = i / o.n_r, k = i - T * o.n_r;
+        om[i] = fma(o.area[T], o.vol[k], o.hr[k] * o.g[T].w);
+        oc[i] = o.area_r[T] * o.w[k];
+    }
+}
 
 // r = f - A u with partial ||r||^2.  Where the whole stencil of every lane of
 // a warp reads exact zeros (for example a zero initial guess) A u is exactly
@@ -1269,6 +1312,13 @@ cudaError_t launch_prolong_linear(const Launch &L, const LevelDev &fine, const L
     const int N = fine.n * L.n_r;
     return launch_k(L, k_prolong_linear<kThreads>, grid_for(N, kThreads, L.sm_count), kThreads, 0, coarse.nbr,
                     coarse.plin, uc, u, L.n_r, N);
+}
+
+cudaError_t launch_outer_products(const Launch &L, const LevelDev &lv, const VertDev &v)
+{
+    const int N = lv.n * L.n_r;
+    k_outer_products<<<grid_for(N, 256, L.sm_count), 256, 0, L.s>>>(make_view(lv, v, L.n_r), N, lv.om, lv.oc);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_twisted_factors(const Launch &L, const LevelDev &lv, const VertDev &v)

@@ -144,6 +144,11 @@ struct LevelDev {
     // the same way, with the factors held for the whole level; -1: none
     bool scan = false;
     int scan_pass_tasks = -1;
+    // finest level, factorised operator without advection: per-row products of its
+    // coefficients [n][n_r], om = |T| v_k + hr_k G_T (the row's excess) and
+    // oc = |T| alpha_r^S w_k (the coupling through the row's lower face), so that the
+    // outer operator costs 8 FP64 operations a row instead of 11; null if they did not fit
+    double *om = nullptr, *oc = nullptr;
     // FP64 levels with a coarser level below them: the restriction's view of each
     // coarse cell [n / 4], or null (then the kernel forms every child's residual)
     RestrictGeo *rgeo = nullptr;
@@ -250,6 +255,7 @@ cudaError_t launch_prolong_add(const Launch &L, const LevelDev &fine, const doub
 cudaError_t launch_prolong_linear(const Launch &L, const LevelDev &fine, const LevelDev &coarse, const double *uc,
                                   double *u);
 cudaError_t launch_twisted_factors(const Launch &L, const LevelDev &lv, const VertDev &v);
+cudaError_t launch_outer_products(const Launch &L, const LevelDev &lv, const VertDev &v);
 cudaError_t launch_thomas_factors(const Launch &L, const LevelDev &lv, const VertDev &v);
 // Mixed-precision V-cycle (FP32 arithmetic, BF16 stencil).  TF is the type of
 // the right-hand side (double on the finest level, float below).
