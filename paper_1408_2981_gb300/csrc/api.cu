@@ -1958,7 +1958,8 @@ tpmg_status tpmg_solve_host(tpmg_ctx *ctx, const double *h_f, double *h_u, doubl
     const size_t bytes = sizeof(double) * ctx->N;
     CU(cudaMemcpyAsync(ctx->hf, h_f, bytes, cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(ctx->hu, h_u, bytes, cudaMemcpyHostToDevice, ctx->stream));
-    tpmg_status st = outer_host(ctx, ctx->hf, ctx->hu, rtol, max_iter, iters, rel_resid, resid_hist);
+    // the solve of tpmg_solve on the staging vectors (the device-side loop where it applies)
+    tpmg_status st = tpmg_solve(ctx, ctx->hf, ctx->hu, rtol, max_iter, iters, rel_resid, resid_hist);
     CU(cudaMemcpyAsync(h_u, ctx->hu, bytes, cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     return st;
