@@ -694,12 +694,15 @@ __global__ void k_thomas_factors(OpView o, int n_cells, double *__restrict__ rin
 }
 
 // One relaxation pass (eq. BlockJacobi) in FP64 with one warp per column, for
-// levels whose passes are latency-bound (few columns per colour): row k on
-// lane k mod 32, the Thomas recurrences y_k = t_k + fb_k y_{k-1} and
-// x_k = y_k + fc_k x_{k+1} as warp-shuffle scans of affine maps, 32 rows at a
-// time (no shared memory, no barrier, no serial chain of n_r FP64 FMAs).  The
-// right-hand side is formed exactly as in k_relax (HF: the horizontal couplings of
-// the stencil stored per unknown, TPMG^full).
+// levels whose passes are latency-bound (few columns per colour).  Lane l holds the
+// R consecutive rows l R .. l R + R - 1 (n_r <= 32 R); each Thomas recurrence,
+// y_k = t_k + fb_k y_{k-1} and then x_k = y_k + fc_k x_{k+1}, is the lane's own
+// recurrence over its rows, one warp-shuffle scan of the lanes' composite affine
+// maps, and a fix-up of each row by its prefix product and the carry from the
+// neighbouring lane: 5 + 2 + 10/R FP64 operations a row forward and 2 + 8/R back,
+// with a dependent chain of R + 6 steps each way (no shared memory, no barrier).
+// The right-hand side is formed exactly as in k_relax (HF: the horizontal
+// couplings of the stencil stored per unknown, TPMG^full).
 template <int MODE, int R, bool HF>
 __global__ void __launch_bounds__(256)
     k_relax_scan(OpView o, const int *__restrict__ cells, const int4 *__restrict__ tnb, const dbl4 *__restrict__ tg,
@@ -721,12 +724,15 @@ __global__ void __launch_bounds__(256)
     const bool n0 = MODE == PASS_NORMAL || (nb.w & 1), n1 = MODE == PASS_NORMAL || (nb.w & 2),
                n2 = MODE == PASS_NORMAL || (nb.w & 4);
     const size_t base = (size_t)T * n_r;
-    double x[R];
-    double carry = 0.0;
+    const int k0 = lane * R;   // this lane's rows k0 .. k0 + R - 1
+    // forward, y_k = t_k + b_k y_{k-1}: the lane's own recurrence Y_j from y = 0 before its
+    // first row, with the prefix products P_j = b_{k0} ... b_{k0+j}; rows past the column
+    // are the identity map (b = 1, t = 0)
+    double y[R], P[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int k = 32 * r + lane;
-        double A = 0.0, B = 0.0;
+    for (int j = 0; j < R; ++j) {
+        const int k = k0 + j;
+        double t = 0.0, b = 1.0;
         if (k < n_r) {
             const size_t i = base + k;
             double d = f[i];
@@ -741,9 +747,14 @@ __global__ void __launch_bounds__(256)
                     d = fma(__ldg(&o.hr[k]), fma(g.z, v2, fma(g.y, v1, g.x * v0)), d);
                 }
             }
-            B = d * __ldg(&rinv[i]);
-            A = __ldg(&fb[i]);
+            t = d * __ldg(&rinv[i]);
+            b = __ldg(&fb[i]);
         }
+        y[j] = j == 0 ? t : fma(b, y[j - 1], t);
+        P[j] = j == 0 ? b : P[j - 1] * b;
+    }
+    {   // inclusive scan of the lanes' maps y -> P y + Y; the carry into lane l is lane l-1's
+        double A = P[R - 1], B = y[R - 1];
 #pragma unroll
         for (int s = 1; s < 32; s <<= 1) {
             const double Ap = __shfl_up_sync(full, A, s), Bp = __shfl_up_sync(full, B, s);
@@ -752,18 +763,25 @@ __global__ void __launch_bounds__(256)
                 A *= Ap;
             }
         }
-        x[r] = fma(A, carry, B);
-        carry = __shfl_sync(full, x[r], 31);
-    }
-    carry = 0.0;
+        double cin = __shfl_up_sync(full, B, 1);
+        if (lane == 0) cin = 0.0;
 #pragma unroll
-    for (int r = R - 1; r >= 0; --r) {
-        const int k = 32 * r + lane;
-        double A = 0.0, B = 0.0;
-        if (k < n_r) {
-            A = __ldg(&fcf[base + k]);
-            B = x[r];
-        }
+        for (int j = 0; j < R; ++j) y[j] = fma(P[j], cin, y[j]);
+    }
+    // backward, x_k = y_k + c_k x_{k+1}: the lane's own recurrence X_j from x = 0 after its
+    // last row, with the suffix products Q_j = c_{k0+j} ... c_{k0+R-1}; rows past the
+    // column take c = 0 (the column's last row has c = 0 anyway)
+    double Q[R];
+#pragma unroll
+    for (int j = R - 1; j >= 0; --j) {
+        const int k = k0 + j;
+        const double c = k < n_r ? __ldg(&fcf[base + k]) : 0.0;
+        if (k >= n_r) y[j] = 0.0;
+        if (j < R - 1) y[j] = fma(c, y[j + 1], y[j]);
+        Q[j] = j == R - 1 ? c : c * Q[j + 1];
+    }
+    {   // inclusive suffix scan of the maps x -> Q x + X; the carry into lane l is lane l+1's
+        double A = Q[0], B = y[0];
 #pragma unroll
         for (int s = 1; s < 32; s <<= 1) {
             const double Ad = __shfl_down_sync(full, A, s), Bd = __shfl_down_sync(full, B, s);
@@ -772,15 +790,17 @@ __global__ void __launch_bounds__(256)
                 A *= Ad;
             }
         }
-        x[r] = fma(A, carry, B);
-        carry = __shfl_sync(full, x[r], 0);
+        double cin = __shfl_down_sync(full, B, 1);
+        if (lane == 31) cin = 0.0;
+#pragma unroll
+        for (int j = 0; j < R; ++j) y[j] = fma(Q[j], cin, y[j]);
     }
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int k = 32 * r + lane;
+    for (int j = 0; j < R; ++j) {
+        const int k = k0 + j;
         if (k >= n_r) continue;
         const size_t i = base + k;
-        double v = x[r];
+        double v = y[j];
         if (relax != 1.0) {   // from a zero guess (ZERO, RHS_ONLY) the old value is 0
             const double uo = MODE == PASS_NORMAL ? u_in[i] : 0.0;
             v = fma(relax, v - uo, uo);
