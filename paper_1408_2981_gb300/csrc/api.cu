@@ -31,6 +31,13 @@ struct Tracer {
     cudaStream_t open_s = nullptr; // its stream
 };
 
+// Launches and processed unknowns per kernel class of a captured solve: its initial
+// part and one iteration of its device-side loop.
+struct ClassCounts {
+    long long init[TPMG_K_COUNT] = {}, iter[TPMG_K_COUNT] = {};
+    double uinit[TPMG_K_COUNT] = {}, uiter[TPMG_K_COUNT] = {};
+};
+
 // The V-cycle of tpmg_solve (r -> z on the context's own vectors) replayed
 // from a captured CUDA graph, with the launch counts of one replay.
 struct GraphCache {
@@ -56,6 +63,7 @@ struct tpmg_ctx {
         int max_iter = -1;
     } sg;
     long long sg_init = 0, sg_iter = 0;   // launches of sg's initial part and of one iteration
+    ClassCounts sg_cls;                   // the same per kernel class, with the unknowns processed
     long long last_launches = 0;          // kernels executed by the last solve
     // learned form (tpmg_learned.h): attached networks (COARSE, WARM), their
     // inference workspaces, scales, the learned solve's graph and the
@@ -77,6 +85,7 @@ struct tpmg_ctx {
         int max_iter = -1;
         const tpmg_net *nets[2] = {nullptr, nullptr};
         long long init = 0, iter = 0;
+        ClassCounts cls;
     } lg;
     double *bv = nullptr, *bs = nullptr, *bz = nullptr, *bh = nullptr;   // BiCGStab's v, s, z, r^ (on first use)
     // factorised profiles (tpmg_setup_profiles): vertical factors and the horizontal
@@ -104,6 +113,7 @@ struct tpmg_ctx {
     double *hf = nullptr, *hu = nullptr;   // device staging for tpmg_solve_host
     double *partials = nullptr;
     int n_part = 0;
+    int *zflags = nullptr;        // [n_part] per-block flags of the initial guess's zero probe
     Scalars *sc = nullptr;        // device
     Scalars *h_sc = nullptr;      // pinned host mirror
     std::vector<void *> allocs;   // every device allocation, freed by tpmg_destroy
@@ -307,6 +317,20 @@ cudaError_t run(tpmg_ctx *ctx, int kclass, double units, F &&launch)
         cudaError_t e_ = (call);                                                                  \
         if (e_ != cudaSuccess) return fail(ctx, TPMG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
+
+// r = f - A u on the finest level with the partials of ||r||^2: a probe of u first (its own
+// launch), so that where the guess is exactly zero -- how a solve normally starts -- the
+// residual kernel copies f instead of loading the stencil; the result is the same either way.
+cudaError_t residual_probed(tpmg_ctx *ctx, const Launch &L, const double *f, const double *u, double *r)
+{
+    const LevelDev &fl = ctx->lv.back();
+    const long N = ctx->N;
+    cudaError_t e = run(ctx, TPMG_K_RESIDUAL, (double)N, [&] { return launch_nonzero(L, N, u, ctx->zflags, ctx->n_part); });
+    if (e != cudaSuccess) return e;
+    return run(ctx, TPMG_K_RESIDUAL, (double)N, [&] {
+        return launch_residual(L, fl, ctx->vert, f, u, r, ctx->partials, ctx->n_part, ctx->zflags);
+    });
+}
 
 // Algorithm 1 on multigrid level l: u = V-cycle(f) from a zero initial guess.
 // `scratch` is a second vector of the level size (block-Jacobi ping-pong).
@@ -702,7 +726,8 @@ tpmg_status capture_into(tpmg_ctx *ctx, cudaGraph_t g, const cudaGraphNode_t *de
 // prediction if one is attached, the stop test is relative to ||f||, and the
 // judge replaces a guess whose residual is not below ||f|| by zero.
 tpmg_status append_solve(tpmg_ctx *ctx, cudaGraph_t g, const double *f, double *u, double rtol, int max_iter,
-                         long long *init_launches = nullptr, long long *iter_launches = nullptr, bool learned = false)
+                         long long *init_launches = nullptr, long long *iter_launches = nullptr, bool learned = false,
+                         ClassCounts *cls = nullptr)
 {
     Tracer &t = ctx->tr;
     long long l0[TPMG_K_COUNT];
@@ -730,7 +755,7 @@ tpmg_status append_solve(tpmg_ctx *ctx, cudaGraph_t g, const double *f, double *
                                               fl.u2_32, nullptr, u);
             }));
         }
-        LCHK(run(ctx, TPMG_K_RESIDUAL, (double)N, [&] { return launch_residual(L, fl, ctx->vert, f, u, ctx->r, ctx->partials, np); }));
+        LCHK(residual_probed(ctx, L, f, u, ctx->r));
         if (learned) {
             LCHK(run(ctx, TPMG_K_DOT, (double)N, [&] { return launch_dot(L, N, f, f, ctx->partials + np, np); }));
             LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_LOOP_RR0F, ctx->partials, np, ctx->sc, &loop); }));
@@ -743,7 +768,13 @@ tpmg_status append_solve(tpmg_ctx *ctx, cudaGraph_t g, const double *f, double *
     });
     if (st != TPMG_OK) return st;
     long long after_init = 0;
-    for (int c = 0; c < TPMG_K_COUNT; ++c) after_init += t.launches[c] - l0[c];
+    long long l1[TPMG_K_COUNT];
+    double u1[TPMG_K_COUNT];
+    for (int c = 0; c < TPMG_K_COUNT; ++c) {
+        after_init += t.launches[c] - l0[c];
+        l1[c] = t.launches[c];
+        u1[c] = t.units[c];
+    }
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = h;
@@ -776,6 +807,13 @@ tpmg_status append_solve(tpmg_ctx *ctx, cudaGraph_t g, const double *f, double *
     for (int c = 0; c < TPMG_K_COUNT; ++c) total += t.launches[c] - l0[c];
     if (init_launches) *init_launches = after_init;
     if (iter_launches) *iter_launches = total - after_init;
+    if (cls)
+        for (int c = 0; c < TPMG_K_COUNT; ++c) {
+            cls->init[c] = l1[c] - l0[c];
+            cls->iter[c] = t.launches[c] - l1[c];
+            cls->uinit[c] = u1[c] - u0[c];
+            cls->uiter[c] = t.units[c] - u1[c];
+        }
     std::copy(l0, l0 + TPMG_K_COUNT, t.launches);
     std::copy(u0, u0 + TPMG_K_COUNT, t.units);
     return st;
@@ -807,7 +845,7 @@ tpmg_status pcg_graph(tpmg_ctx *ctx, const double *f, double *u, double rtol, in
         sg.exec = nullptr;
         cudaGraph_t g;
         CU(cudaGraphCreate(&g, 0));
-        tpmg_status st = append_solve(ctx, g, f, u, rtol, max_iter, &ctx->sg_init, &ctx->sg_iter);
+        tpmg_status st = append_solve(ctx, g, f, u, rtol, max_iter, &ctx->sg_init, &ctx->sg_iter, false, &ctx->sg_cls);
         cudaError_t e = st == TPMG_OK ? cudaGraphInstantiate(&sg.exec, g, 0) : cudaSuccess;
         cudaGraphDestroy(g);
         if (st != TPMG_OK) return st;
@@ -822,6 +860,12 @@ tpmg_status pcg_graph(tpmg_ctx *ctx, const double *f, double *u, double rtol, in
     CU(cudaStreamSynchronize(ctx->stream));
     const Scalars s = *ctx->h_sc;
     ctx->last_launches = ctx->sg_init + (long long)s.it * ctx->sg_iter;
+    // the replay's launches count like launches made one by one (tpmg_profile_read)
+    if (s.it >= 0)
+        for (int c = 0; c < TPMG_K_COUNT; ++c) {
+            ctx->tr.launches[c] += ctx->sg_cls.init[c] + (long long)s.it * ctx->sg_cls.iter[c];
+            ctx->tr.units[c] += ctx->sg_cls.uinit[c] + s.it * ctx->sg_cls.uiter[c];
+        }
     if (hist && s.it >= 0) CU(cudaMemcpy(hist, ctx->d_hist, sizeof(double) * (s.it + 1), cudaMemcpyDeviceToHost));
     return loop_result(ctx, s, rtol, max_iter, iters, rel);
 }
@@ -852,7 +896,7 @@ tpmg_status richardson(tpmg_ctx *ctx, const double *f, double *u, double rtol, i
     *rel = 1.0;
     double rr0 = 0.0;
     for (int it = 0;; ++it) {
-        LCHK(run(ctx, TPMG_K_RESIDUAL, (double)N, [&] { return launch_residual(L, fl, ctx->vert, f, u, ctx->r, ctx->partials, np); }));
+        LCHK(residual_probed(ctx, L, f, u, ctx->r));
         LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_SUM, ctx->partials, np, ctx->sc); }));
         tpmg_status st = read_scalars(ctx);
         if (st != TPMG_OK) return st;
@@ -896,7 +940,7 @@ tpmg_status bicgstab(tpmg_ctx *ctx, const double *f, double *u, double rtol, int
     double *r = ctx->r, *rh = ctx->bh, *p = ctx->pv, *v = ctx->bv, *y = ctx->z, *sv = ctx->bs, *z = ctx->bz, *t = ctx->q;
     *iters = 0;
     *rel = 1.0;
-    LCHK(run(ctx, TPMG_K_RESIDUAL, (double)N, [&] { return launch_residual(L, fl, ctx->vert, f, u, r, ctx->partials, np); }));
+    LCHK(residual_probed(ctx, L, f, u, r));
     LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_SUM, ctx->partials, np, ctx->sc); }));
     tpmg_status st = read_scalars(ctx);
     if (st != TPMG_OK) return st;
@@ -961,7 +1005,7 @@ tpmg_status pcg(tpmg_ctx *ctx, const double *f, double *u, double rtol, int max_
                                           nullptr, u);
         }));
     }
-    LCHK(run(ctx, TPMG_K_RESIDUAL, (double)N, [&] { return launch_residual(L, fl, ctx->vert, f, u, ctx->r, ctx->partials, np); }));
+    LCHK(residual_probed(ctx, L, f, u, ctx->r));
     if (learned) {
         LCHK(run(ctx, TPMG_K_DOT, (double)N, [&] { return launch_dot(L, N, f, f, ctx->partials + np, np); }));
         LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_RR0F, ctx->partials, np, ctx->sc); }));
@@ -1646,6 +1690,7 @@ tpmg_status tpmg_setup_profiles(const tpmg_params *params, const tpmg_profiles *
         dalloc(ctx, &ctx->pv, ctx->N) != cudaSuccess || dalloc(ctx, &ctx->q, ctx->N) != cudaSuccess ||
         dalloc(ctx, &ctx->hf, ctx->N) != cudaSuccess || dalloc(ctx, &ctx->hu, ctx->N) != cudaSuccess ||
         dalloc(ctx, &ctx->partials, 2 * (size_t)ctx->n_part) != cudaSuccess ||
+        dalloc(ctx, &ctx->zflags, (size_t)ctx->n_part) != cudaSuccess ||
         dalloc(ctx, &ctx->d_hist, kHistCap) != cudaSuccess || dalloc(ctx, &ctx->sc, 1) != cudaSuccess ||
         dalloc(ctx, &ctx->d_net_s, 3) != cudaSuccess)
         return bail(TPMG_ERR_OOM);
@@ -2242,7 +2287,7 @@ tpmg_status tpmg_solve_learned(tpmg_ctx *ctx, const double *d_f, double *d_u, do
         // event pairs of timed classes cannot live inside the loop body: not timed here
         const unsigned mask = ctx->tr.mask;
         ctx->tr.mask = 0;
-        tpmg_status st = append_solve(ctx, g, d_f, d_u, rtol, max_iter, &lg.init, &lg.iter, true);
+        tpmg_status st = append_solve(ctx, g, d_f, d_u, rtol, max_iter, &lg.init, &lg.iter, true, &lg.cls);
         ctx->tr.mask = mask;
         cudaError_t e = st == TPMG_OK ? cudaGraphInstantiate(&lg.exec, g, 0) : cudaSuccess;
         cudaGraphDestroy(g);
@@ -2260,6 +2305,11 @@ tpmg_status tpmg_solve_learned(tpmg_ctx *ctx, const double *d_f, double *d_u, do
     CU(cudaStreamSynchronize(ctx->stream));
     s = *ctx->h_sc;
     launches = lg.init + (long long)s.it * lg.iter;
+    if (s.it >= 0)
+        for (int c = 0; c < TPMG_K_COUNT; ++c) {
+            ctx->tr.launches[c] += lg.cls.init[c] + (long long)s.it * lg.cls.iter[c];
+            ctx->tr.units[c] += lg.cls.uinit[c] + s.it * lg.cls.uiter[c];
+        }
     it_learned = s.it;
     }
     int bits = s.info & 3;

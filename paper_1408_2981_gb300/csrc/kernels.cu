@@ -318,12 +318,29 @@ __global__ void __launch_bounds__(256) k_outer_products(OpView o, int N, double 
 template <int NT, bool FULL, bool ADV>
 __global__ void __launch_bounds__(NT) k_residual(OpView o, FullView full, const double *__restrict__ f,
                                                  const double *__restrict__ u, double *__restrict__ r, int N,
-                                                 double *__restrict__ partials)
+                                                 double *__restrict__ partials, const int *__restrict__ nz,
+                                                 int n_nz)
 {
     pdl_wait();
     pdl_trigger();
     double acc = 0.0;
     const int stride = gridDim.x * NT, n_r = o.n_r;
+    // nz: the blocks' flags of k_nonzero over u; with none set u is exactly zero, so
+    // r = f, accumulated in the same order as below (bit-identical), without the stencil's loads
+    int any = nz ? 0 : 1;
+    for (int t = threadIdx.x; t < n_nz; t += NT) any |= nz[t];
+    if (!__syncthreads_or(any)) {
+        for (int i = blockIdx.x * NT + threadIdx.x; i < N; i += stride) {
+            const double v = f[i];
+            r[i] = v;
+            acc = fma(v, v, acc);
+        }
+        if (partials) {
+            acc = block_sum<NT>(acc);
+            if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+        }
+        return;
+    }
     for (int i0 = blockIdx.x * NT + threadIdx.x; i0 < N; i0 += 2 * stride) {
         double fv[2], uc[2], um[2], up[2], u0[2], u1[2], u2[2];
         int T[2], k[2];
@@ -365,6 +382,28 @@ __global__ void __launch_bounds__(NT) k_residual(OpView o, FullView full, const 
         acc = block_sum<NT>(acc);
         if (threadIdx.x == 0) partials[blockIdx.x] = acc;
     }
+}
+
+// Per block, whether x has a nonzero element in the block's grid-stride range (a test
+// of bit patterns, no FP64 instruction): the probe of k_residual's zero-guess path.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_nonzero(const double *__restrict__ x, int N, int *__restrict__ nz)
+{
+    pdl_wait();
+    pdl_trigger();
+    int any = 0;
+    const int stride = gridDim.x * NT;
+    int i = blockIdx.x * NT + threadIdx.x;
+    for (; i + 3 * stride < N; i += 4 * stride) {
+        double v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = x[i + q * stride];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) any |= !is_zero(v[q]);
+    }
+    for (; i < N; i += stride) any |= !is_zero(x[i]);
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) nz[blockIdx.x] = any;
 }
 
 // f_c[T][k] = sum_j (f - A u)[4T + j][k]  (Algorithm 1 residual + restriction, Sec. 5)
@@ -1290,15 +1329,21 @@ cudaError_t launch_apply(const Launch &L, const LevelDev &lv, const VertDev &v, 
     return launch_k(L, kern, grid, kThreads, 0, make_view(lv, v, L.n_r), fv, x, y, N, partials);
 }
 
+cudaError_t launch_nonzero(const Launch &L, long n, const double *x, int *nz, int n_blocks)
+{
+    return launch_k(L, k_nonzero<kThreads>, n_blocks, kThreads, 0, x, (int)n, nz);
+}
+
 cudaError_t launch_residual(const Launch &L, const LevelDev &lv, const VertDev &v, const double *f, const double *u,
-                            double *r, double *partials, int n_part)
+                            double *r, double *partials, int n_part, const int *nz)
 {
     const int N = lv.n * L.n_r;
     const int grid = partials ? n_part : grid_for(N, kThreads, L.sm_count);
     const FullView fv{lv.cfull, lv.cvr, lv.cvx};
     auto kern = lv.cfull ? k_residual<kThreads, true, false>
                          : (lv.area_x ? k_residual<kThreads, false, true> : k_residual<kThreads, false, false>);
-    return launch_k(L, kern, grid, kThreads, 0, make_view(lv, v, L.n_r), fv, f, u, r, N, partials);
+    return launch_k(L, kern, grid, kThreads, 0, make_view(lv, v, L.n_r), fv, f, u, r, N, partials, nz,
+                    nz ? n_part : 0);
 }
 
 cudaError_t launch_resid_restrict(const Launch &L, const LevelDev &fine, const LevelDev &coarse, const VertDev &v,

@@ -240,8 +240,10 @@ enum PassMode { PASS_NORMAL = 0, PASS_ZERO = 1, PASS_RHS_ONLY = 2 };
 
 cudaError_t launch_apply(const Launch &L, const LevelDev &lv, const VertDev &v, const double *x, double *y,
                          double *partials, int n_part);
+// nz (optional): per-block flags of launch_nonzero over u, n_part of them
 cudaError_t launch_residual(const Launch &L, const LevelDev &lv, const VertDev &v, const double *f,
-                            const double *u, double *r, double *partials, int n_part);
+                            const double *u, double *r, double *partials, int n_part, const int *nz = nullptr);
+cudaError_t launch_nonzero(const Launch &L, long n, const double *x, int *nz, int n_blocks);
 cudaError_t launch_resid_restrict(const Launch &L, const LevelDev &fine, const LevelDev &coarse, const VertDev &v,
                                   const double *f, const double *u, double *fc);
 // One relaxation pass over tasks [task0, task0 + n_tasks) of level lv:

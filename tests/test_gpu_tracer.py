@@ -47,3 +47,25 @@ def test_timed_solve_is_bit_identical_and_counts_every_launch(graphs, pdl):
         else:
             assert p["timed"] == p["launches"]
     assert pr["apply"]["timed"] == 0 and pr["apply"]["launches"] > 0
+
+
+def test_device_loop_solve_counts_its_launches():
+    """A solve run as one graph with its loop on the device counts its kernels like
+    launches made one by one: each iteration applies one V-cycle."""
+    s = binding.Solver(graphs=1, **KW)
+    f = torch.from_numpy(inputs.uniform_pm1(inputs.SEED_UNIFORM_SMALL + 91, s.N)).cuda()
+    z = torch.empty_like(f)
+    s.profile(classes=())
+    s.vcycle(f, z)
+    per_vcycle = s.profile_read()["relax"]
+    assert per_vcycle["launches"] > 0
+    for rep in range(2):   # the capturing solve, then a replay
+        s.profile(classes=())
+        u = torch.zeros_like(f)
+        st, it, rel, _ = s.solve(f, u, rtol=1e-8, max_iter=50)
+        torch.cuda.synchronize()
+        pr = s.profile_read()
+        assert st == binding.TPMG_OK and it > 0
+        assert pr["relax"]["launches"] == it * per_vcycle["launches"]
+        assert pr["relax"]["units"] == it * per_vcycle["units"]
+        assert pr["apply"]["launches"] == it and pr["residual"]["launches"] >= 1
