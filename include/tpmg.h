@@ -279,6 +279,9 @@ tpmg_status tpmg_solve(tpmg_ctx *ctx, const double *d_f, double *d_u, double rto
 /* tpmg_solve with HOST buffers: copies h_f and the initial guess h_u to the
  * device, solves, and copies the solution back into h_u, all inside the call
  * (pinned host memory gives full copy bandwidth; pageable memory works).
+ * The solve is tpmg_solve's on the context's own staging vectors, so its
+ * device-side loop graph is captured once for them (a tpmg_solve on other
+ * vectors in between captures its own, and the next call here captures again).
  * Same arguments and returns as tpmg_solve. */
 tpmg_status tpmg_solve_host(tpmg_ctx *ctx, const double *h_f, double *h_u, double rtol, int max_iter,
                             int *iters, double *rel_resid, double *resid_hist);
