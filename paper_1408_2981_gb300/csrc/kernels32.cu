@@ -98,63 +98,131 @@ __global__ void __launch_bounds__(256)
     const bool n0 = MODE == PASS_NORMAL || (nb.w & 1), n1 = MODE == PASS_NORMAL || (nb.w & 2),
                n2 = MODE == PASS_NORMAL || (nb.w & 4);
     const size_t base = (size_t)T * n_r;
+    // CH (two rows per lane, n_r <= 64): lane l holds rows 2l and 2l + 1, each recurrence is
+    // the lane's own step, one scan of the lanes' composite affine maps and a fix-up by the
+    // prefix products -- a chain of 8 steps each way instead of 12; otherwise row k sits on
+    // lane k mod 32 and the 32-row segments are scanned one after another
+    constexpr bool CH = R == 2;
+    auto row = [&](int r) { return CH ? 2 * lane + r : 32 * r + lane; };
     float x[R];
-    // forward recurrence, segment by segment
-    float carry = 0.f;
+    if (CH) {
+        float P[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int k = 32 * r + lane;
-        float A = 0.f, B = 0.f;
-        if (k < n_r) {
-            const size_t i = base + k;
-            float d = (float)f[i];
-            if (MODE != PASS_RHS_ONLY) {
-                const bf16x4 cp = cpack[i];
-                const float v0 = n0 ? u_in[(size_t)nb.x * n_r + k] : 0.f;
-                const float v1 = n1 ? u_in[(size_t)nb.y * n_r + k] : 0.f;
-                const float v2 = n2 ? u_in[(size_t)nb.z * n_r + k] : 0.f;
-                d = fmaf(bf(cp.z), v2, fmaf(bf(cp.y), v1, fmaf(bf(cp.x), v0, d)));
+        for (int j = 0; j < R; ++j) {
+            const int k = row(j);
+            float t = 0.f, b = 1.f;
+            if (k < n_r) {
+                const size_t i = base + k;
+                float d = (float)f[i];
+                if (MODE != PASS_RHS_ONLY) {
+                    const bf16x4 cp = cpack[i];
+                    const float v0 = n0 ? u_in[(size_t)nb.x * n_r + k] : 0.f;
+                    const float v1 = n1 ? u_in[(size_t)nb.y * n_r + k] : 0.f;
+                    const float v2 = n2 ? u_in[(size_t)nb.z * n_r + k] : 0.f;
+                    d = fmaf(bf(cp.z), v2, fmaf(bf(cp.y), v1, fmaf(bf(cp.x), v0, d)));
+                }
+                t = d * __ldg(&rinv[i]);
+                b = __ldg(&fb[i]);
             }
-            B = d * __ldg(&rinv[i]);
-            A = __ldg(&fb[i]);
+            x[j] = j == 0 ? t : fmaf(b, x[j - 1], t);
+            P[j] = j == 0 ? b : P[j - 1] * b;
         }
+        {
+            float A = P[R - 1], B = x[R - 1];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const float Ap = __shfl_up_sync(full, A, o), Bp = __shfl_up_sync(full, B, o);
-            if (lane >= o) {
-                B = fmaf(A, Bp, B);
-                A *= Ap;
+            for (int o = 1; o < 32; o <<= 1) {
+                const float Ap = __shfl_up_sync(full, A, o), Bp = __shfl_up_sync(full, B, o);
+                if (lane >= o) {
+                    B = fmaf(A, Bp, B);
+                    A *= Ap;
+                }
             }
-        }
-        x[r] = fmaf(A, carry, B);
-        carry = __shfl_sync(full, x[r], 31);
-    }
-    // backward recurrence, from the top segment down
-    carry = 0.f;
+            float cin = __shfl_up_sync(full, B, 1);
+            if (lane == 0) cin = 0.f;
 #pragma unroll
-    for (int r = R - 1; r >= 0; --r) {
-        const int k = 32 * r + lane;
-        float A = 0.f, B = 0.f;
-        if (k < n_r) {
-            A = __ldg(&fg[base + k]);
-            B = x[r];
+            for (int j = 0; j < R; ++j) x[j] = fmaf(P[j], cin, x[j]);
         }
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const float Ad = __shfl_down_sync(full, A, o), Bd = __shfl_down_sync(full, B, o);
-            if (lane + o < 32) {
-                B = fmaf(A, Bd, B);
-                A *= Ad;
+        for (int j = R - 1; j >= 0; --j) {
+            const int k = row(j);
+            const float c = k < n_r ? __ldg(&fg[base + k]) : 0.f;
+            if (k >= n_r) x[j] = 0.f;
+            if (j < R - 1) x[j] = fmaf(c, x[j + 1], x[j]);
+            P[j] = j == R - 1 ? c : c * P[j + 1];
+        }
+        {
+            float A = P[0], B = x[0];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const float Ad = __shfl_down_sync(full, A, o), Bd = __shfl_down_sync(full, B, o);
+                if (lane + o < 32) {
+                    B = fmaf(A, Bd, B);
+                    A *= Ad;
+                }
             }
+            float cin = __shfl_down_sync(full, B, 1);
+            if (lane == 31) cin = 0.f;
+#pragma unroll
+            for (int j = 0; j < R; ++j) x[j] = fmaf(P[j], cin, x[j]);
         }
-        x[r] = fmaf(A, carry, B);
-        carry = __shfl_sync(full, x[r], 0);
+    } else {
+        // forward recurrence, segment by segment
+        float carry = 0.f;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int k = 32 * r + lane;
+            float A = 0.f, B = 0.f;
+            if (k < n_r) {
+                const size_t i = base + k;
+                float d = (float)f[i];
+                if (MODE != PASS_RHS_ONLY) {
+                    const bf16x4 cp = cpack[i];
+                    const float v0 = n0 ? u_in[(size_t)nb.x * n_r + k] : 0.f;
+                    const float v1 = n1 ? u_in[(size_t)nb.y * n_r + k] : 0.f;
+                    const float v2 = n2 ? u_in[(size_t)nb.z * n_r + k] : 0.f;
+                    d = fmaf(bf(cp.z), v2, fmaf(bf(cp.y), v1, fmaf(bf(cp.x), v0, d)));
+                }
+                B = d * __ldg(&rinv[i]);
+                A = __ldg(&fb[i]);
+            }
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const float Ap = __shfl_up_sync(full, A, o), Bp = __shfl_up_sync(full, B, o);
+                if (lane >= o) {
+                    B = fmaf(A, Bp, B);
+                    A *= Ap;
+                }
+            }
+            x[r] = fmaf(A, carry, B);
+            carry = __shfl_sync(full, x[r], 31);
+        }
+        // backward recurrence, from the top segment down
+        carry = 0.f;
+#pragma unroll
+        for (int r = R - 1; r >= 0; --r) {
+            const int k = 32 * r + lane;
+            float A = 0.f, B = 0.f;
+            if (k < n_r) {
+                A = __ldg(&fg[base + k]);
+                B = x[r];
+            }
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const float Ad = __shfl_down_sync(full, A, o), Bd = __shfl_down_sync(full, B, o);
+                if (lane + o < 32) {
+                    B = fmaf(A, Bd, B);
+                    A *= Ad;
+                }
+            }
+            x[r] = fmaf(A, carry, B);
+            carry = __shfl_sync(full, x[r], 0);
+        }
     }
     // write-back: relaxation weight, the double copy of the finest level's
     // result, the prolongation into the 4 children (P = R^T)
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const int k = 32 * r + lane;
+        const int k = row(r);
         if (k >= n_r) continue;
         const size_t i = base + k;
         float v = x[r];
