@@ -154,7 +154,7 @@ PER_UNIT = {
 TRAFFIC = {
     ("relax", "81920x64"): {"bytes_per_launch": 18.78e6, "file": "kernels.cu", "sha256": "76fec0af40021f71",
                             "source": "profiles/relax_dram_81920x64.md"},
-    ("relax", "327680x128-mixed"): {"bytes_per_launch": 121.78e6, "file": "kernels32.cu", "sha256": "891285587210fc5f",
+    ("relax", "327680x128-mixed"): {"bytes_per_launch": 121.59e6, "file": "kernels32.cu", "sha256": "94d0b357a1e89bcd",
                                     "source": "profiles/relax32_dram_327680x128.md"},
 }
 SM_COUNT_GB300 = 152
