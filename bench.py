@@ -131,34 +131,10 @@ def batch_problems(seed: int, n: int) -> list:
     return [dict(refinement=int(r), n_levels=int(min(r, 5) + 1 if r < 6 else 6), n_r=int(k), grading=1.05,
                  courant_c=float(c), nu_pre=2, nu_post=2, nu_coarse=1, **MIXED) for r, k, c in zip(refs, nrs, cs)]
 
-# Flops per unknown of each kernel class as written (FMA = 2 flops) and
-# algorithmic HBM bytes per unknown (each array streamed once), per precision
-# of the V-cycle; the outer Krylov kernels are FP64 in both forms.
-# apply: the row from its stored products (12 flops) and the fused dot (2); 16 B of x and
-# y plus 16 B of stored products.  restrict (FP64): 48 flops per coarse row from the sums
-# over the 4 children, 12 per fine unknown.
-OUTER = {"apply": (14.0, 32.0), "residual": (17.0, 24.0), "axpy": (6.0, 48.0), "dot": (2.0, 16.0),
-         "xpby": (2.0, 24.0)}
-PER_UNIT = {
-    0: dict(OUTER, relax=(12.0, 48.0), restrict=(12.0, 18.0), prolong=(1.0, 20.0)),
-    # mixed, per the survey's convention (coefficients and vectors; neighbour re-reads
-    # cached): relax reads f (8 B on the finest level, FP64; 4 B below), the BF16
-    # stencil (8 + 2), u (4), writes u (4): 26 / 22 B, weighted 25 for the 3:1 split of
-    # unknowns between the finest level and the rest.  The stored FP32 Thomas factors
-    # (12 B) are this design's extra traffic; ncu's DRAM counters include them.
-    1: dict(OUTER, relax=(20.0, 25.0), restrict=(20.0, 19.0), prolong=(1.0, 10.0)),
-}
-# DRAM bytes per launch of a kernel class on a workload from an ncu capture
-# (profiles/), valid while the kernel source is the file that was profiled
-# (sha256 prefix)
-TRAFFIC = {
-    ("relax", "81920x64"): {"bytes_per_launch": 18.78e6, "file": "kernels.cu", "sha256": "76fec0af40021f71",
-                            "source": "profiles/relax_dram_81920x64.md"},
-    ("relax", "327680x128-mixed"): {"bytes_per_launch": 121.59e6, "file": "kernels32.cu", "sha256": "94d0b357a1e89bcd",
-                                    "source": "profiles/relax32_dram_327680x128.md"},
-}
-SM_COUNT_GB300 = 152
-FP64_FMA_PER_CLK_PER_SM = 2     # GB300: 1.25 TFLOP/s dense FP64 at 2.07 GHz over 152 SMs
+# Kernel classes of the outer Krylov iteration: FP64 in every form (the V-cycle's
+# classes -- relax, restrict, prolong -- run in FP32 in the mixed form).
+OUTER_FP64 = ("apply", "residual", "axpy", "dot", "xpby", "finish")
+FP32_FMA_PER_CLK_PER_SM = 128   # nominal FP32 lanes per SM (only used to name the binding ceiling)
 ORACLE_FULL_SOLVE_MAX_UNKNOWNS = 6_000_000   # larger workloads: the CPU baseline times one iteration
 
 
@@ -169,11 +145,30 @@ def source_sha256(name: str) -> str:
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
+def traffic_records() -> list:
+    """Machine-readable lines of the ncu summaries in profiles/ of the form
+    ``traffic: class=<kernel class> workload=<name> <source file>=<sha256 prefix> bytes_per_launch=<B>``:
+    DRAM bytes (read + write) per launch of a kernel class on a workload, measured
+    while the named kernel source had that hash."""
+    import glob
+    import re
+
+    pat = re.compile(r"traffic: class=(\w+) workload=(\S+) (\S+)=([0-9a-f]{16}) bytes_per_launch=([0-9.eE+]+)")
+    out = []
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(path) as fh:
+            for m in pat.finditer(fh.read()):
+                out.append(dict(kernel=m.group(1), workload=m.group(2), file=m.group(3), sha256=m.group(4),
+                                bytes_per_launch=float(m.group(5)), source=os.path.relpath(path, ROOT)))
+    return out
+
+
 def traffic_of(kernel: str, workload: str):
-    """ncu DRAM bytes per launch, or None once the kernel source changed after the capture."""
-    t = TRAFFIC.get((kernel, workload))
-    if t and t["sha256"] == source_sha256(t["file"]):
-        return t["bytes_per_launch"]
+    """ncu DRAM bytes per launch of the class, or None when no capture matches the
+    current kernel source."""
+    for t in traffic_records():
+        if t["kernel"] == kernel and t["workload"] == workload and t["sha256"] == source_sha256(t["file"]):
+            return t
     return None
 
 
@@ -187,8 +182,54 @@ def load_peaks() -> dict:
     return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, source="fallback")
 
 
-def fp64_peak_tflops(sm_count: int, mhz: float) -> float:
-    return sm_count * FP64_FMA_PER_CLK_PER_SM * 2 * mhz * 1e6 / 1e12
+def fp32_nominal_tflops(sm_count: int, mhz: float) -> float:
+    return sm_count * FP32_FMA_PER_CLK_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
+def roofline_of(prof: dict, before: dict, dominant: str, mixed: bool, steps: int, step_ms: float,
+                fp64_tflops: float, sm_count: int, workload: str, kernel_note: str = "") -> dict:
+    """Roofline of a kernel class from its timed launches: the algorithmic bytes and
+    flops the library counted for the launches inside the class's event pairs, over
+    their summed device time.  Both ceilings are printed; the binding one is the
+    one whose time bound (work / peak) is longer, and `frac` is taken against it."""
+    peaks = load_peaks()
+    d = prof[dominant]
+    b = before.get(dominant, {"launches": 0}) if before else {"launches": 0}
+    if not (d["ms"] > 0 and d["timed"] > 0):
+        return None
+    secs = d["ms"] / 1e3
+    tb, tf = d["timed_bytes"], d["timed_flops"]
+    fp32 = mixed and dominant not in OUTER_FP64
+    alu_peak = fp32_nominal_tflops(sm_count, peaks["sm_max_mhz"]) if fp32 else fp64_tflops
+    alu_src = (f"nominal FP32: {sm_count} SMs x {FP32_FMA_PER_CLK_PER_SM} FMA/clk x 2 x {peaks['sm_max_mhz']:.0f} MHz"
+               if fp32 else "measured FP64 FMA throughput of this GPU (tpmg_fp64_peak, best of 3 launches)")
+    bw, fl = tb / secs / 1e9, tf / secs / 1e12
+    ceilings = {
+        "hbm": {"achieved": bw, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": bw / peaks["hbm_gbs"],
+                "peak_source": f"{peaks['source']} HBM copy bandwidth (MEASURED_PEAKS.json)",
+                "time_bound_us": 1e6 * tb / (peaks["hbm_gbs"] * 1e9)},
+        "fp32" if fp32 else "fp64": {"achieved": fl, "peak": alu_peak, "unit": "TFLOP/s", "frac": fl / alu_peak,
+                                     "peak_source": alu_src, "time_bound_us": 1e6 * tf / (alu_peak * 1e12)},
+    }
+    alu_key = "fp32" if fp32 else "fp64"
+    hbm_bound = ceilings["hbm"]["time_bound_us"] >= ceilings[alu_key]["time_bound_us"]
+    c = ceilings["hbm" if hbm_bound else alu_key]
+    launches_step = (d["launches"] - b["launches"]) / max(1, steps)
+    tr = traffic_of(dominant, workload)
+    roof = {"bound": "hbm" if hbm_bound else "alu", "achieved": c["achieved"], "peak": c["peak"], "unit": c["unit"],
+            "frac": c["frac"], "peak_source": c["peak_source"],
+            "traffic": tr["bytes_per_launch"] if tr else None,
+            "traffic_unit": "DRAM bytes (read + write) per launch of the class, ncu",
+            "traffic_source": tr["source"] if tr else None,
+            "algorithmic_bytes_per_launch": tb / d["timed"], "algorithmic_flops_per_launch": tf / d["timed"],
+            "kernel": f"{dominant} ({'FP32/BF16' if fp32 else 'FP64'}){kernel_note}",
+            "launches_per_step": launches_step, "avg_launch_us": 1e3 * d["ms"] / d["timed"],
+            "timed_launches": d["timed"], "ceilings": ceilings,
+            "hbm_frac_of_measured": ceilings["hbm"]["frac"],
+            "share_of_step": (d["ms"] / d["timed"]) * launches_step / step_ms if step_ms else None}
+    if tr:
+        roof["traffic_over_algorithmic"] = tr["bytes_per_launch"] / roof["algorithmic_bytes_per_launch"]
+    return roof
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -401,7 +442,6 @@ def run_tpmg(args, wl):
     s = binding.Solver(stream=stream, **wl["params"])
     N = s.N
     mixed = wl["params"].get("precision", 0) == 1
-    per_unit = PER_UNIT[1 if mixed else 0]
     m = s.export_mesh()
     if wl["rhs"] == "manufactured":
         ustar = torch.from_numpy(inputs.manufactured_solution(m["centres"], m["r_faces"], wl["seed"])).cuda()
@@ -413,6 +453,7 @@ def run_tpmg(args, wl):
     l2 = torch.cuda.get_device_properties(local).L2_cache_size
     flush = torch.empty(max(2 * l2, 256 << 20) // 4, dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
+    fp64_tflops = binding.fp64_peak_tflops(stream)   # the FP64-pipe ceiling, measured here
 
     # warm-up; the last warm-up solve times every kernel class to find the dominant one
     for w in range(args.warmup):
@@ -477,49 +518,27 @@ def run_tpmg(args, wl):
 
     # roofline of the dominant kernel class: its launches in the timed region
     # carry event pairs (event-record nodes in the replayed graph hold the last
-    # replay, i.e. the last timed step)
-    peaks = load_peaks()
+    # replay, i.e. the last timed step); the library counts each launch's
+    # algorithmic bytes and flops
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
-    d = prof[dominant]
-    roof = None
-    if d["ms"] > 0 and d["timed"] > 0:
-        units_timed = (d["units"] - before[dominant]["units"]) * d["timed"] / max(1, d["launches"] - before[dominant]["launches"])
-        fpu, bpu = per_unit.get(dominant, (0.0, 0.0))
-        flops, nbytes = fpu * units_timed, bpu * units_timed
-        secs = d["ms"] / 1e3
-        fp64_kernel = not mixed or dominant in OUTER
-        if fp64_kernel:   # FP64 arithmetic: bound by the FP64 pipe
-            achieved, peak = flops / secs / 1e12, fp64_peak_tflops(sm_count, peaks["sm_max_mhz"])
-            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "peak_source": f"FP64 pipe: {sm_count} SMs x {FP64_FMA_PER_CLK_PER_SM} DFMA/clk x 2 x "
-                                   f"{peaks['sm_max_mhz']:.0f} MHz"}
-        else:             # FP32 V-cycle on a BF16 stencil: bound by HBM
-            achieved, peak = nbytes / secs / 1e9, peaks["hbm_gbs"]
-            roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "peak_source": f"{peaks['source']} HBM copy bandwidth"}
-        roof.update({"frac": achieved / peak,
-                "traffic": traffic_of(dominant, args.workload), "traffic_unit": "bytes per launch (ncu)",
-                "algorithmic_bytes_per_launch": nbytes / d["timed"],
-                "kernel": f"{dominant} ({'FP64' if fp64_kernel else 'FP32/BF16'})",
-                "launches_per_step": (d["launches"] - before[dominant]["launches"]) / args.steps,
-                "avg_launch_us": 1e3 * d["ms"] / d["timed"],
-                "timed_launches": d["timed"],
-                "hbm_gbs_algorithmic": nbytes / (d["ms"] / 1e3) / 1e9,
-                "hbm_frac_of_measured": nbytes / (d["ms"] / 1e3) / 1e9 / peaks["hbm_gbs"],
-                # average timed launch x the class's launches per step (a replayed graph's
-                # event pairs hold its last replay only)
-                "share_of_step": (d["ms"] / d["timed"]) * ((d["launches"] - before[dominant]["launches"]) / args.steps)
-                                 / (local_ms / args.steps)})
-    # aggregate algorithmic HBM rate of the whole solve
-    tot_bytes = sum(per_unit.get(c, (0.0, 0.0))[1] * (v["units"] - before[c]["units"]) for c, v in prof.items())
+    roof = roofline_of(prof, before, dominant, mixed, args.steps, local_ms / args.steps, fp64_tflops, sm_count,
+                       args.workload)
+    # aggregate algorithmic HBM rate of the whole solve (every class's bytes)
+    peaks = load_peaks()
+    tot_bytes = sum(v["bytes"] - before[c]["bytes"] for c, v in prof.items())
     hbm = {"achieved_gbs": tot_bytes / (local_ms / 1e3) / 1e9, "peak_gbs": peaks["hbm_gbs"],
-           "frac": tot_bytes / (local_ms / 1e3) / 1e9 / peaks["hbm_gbs"], "source": peaks["source"]}
+           "frac": tot_bytes / (local_ms / 1e3) / 1e9 / peaks["hbm_gbs"], "source": peaks["source"],
+           "algorithmic_bytes_per_step": tot_bytes / args.steps}
 
     cpu, cpu_threads = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v_o, sample, _ = time_oracle(wl, min_seconds=10.0, max_solves=3, rtol=args.rtol, iters_hint=iters[-1])
         cpu = {"value": v_o, "unit": "unknowns/s", "cores": 1, "kind": "oracle", "sample": sample, "cpu": cpu_model()}
         cpu_threads = time_oracle_threads(wl, args.rtol, iters[-1])
+    extra = None
+    if rank == 0 and world == 1 and not args.no_extra_configs and args.workload == "81920x64":
+        s.close()
+        extra = run_extra_configs(args, stream, flush)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world, "steps": args.steps,
@@ -533,14 +552,128 @@ def run_tpmg(args, wl):
                         "d2h_bytes_per_step": 8 * N},
                 "gpu_launches": gpu_launches, "roofline": roof, "hbm": hbm, "cpu_baseline": cpu,
                 "cpu_baseline_threads": cpu_threads,
-                "clocks": clk, "iters": iters[-1], "rel_resid": rel,
-                "kernel_ms_per_step": {c: round(v, 4) for c, v in shares.items()}}
+                "clocks": clk, "iters": iters[-1], "rel_resid": rel, "gpus_active": world,
+                "fp64_peak_tflops_measured": fp64_tflops,
+                "kernel_ms_per_step": {c: round(v, 4) for c, v in shares.items()},
+                "other_configs": extra}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
 
         dist.destroy_process_group()
     return 0
+
+
+def solve_config(name: str, stream, flush, steps: int, warmup: int, rtol: float, rhs=None, keep_u=False):
+    """Solves of one named workload from a zero guess (untimed set-up, `warmup`
+    untimed solves, `steps` solves timed with CUDA events, L2 flushed between
+    them): median ms, iterations, unknowns/s, the true relative residual."""
+    import torch
+
+    from paper_1408_2981_gb300 import binding, inputs
+
+    wl = WORKLOADS[name]
+    t0 = time.perf_counter()
+    s = binding.Solver(stream=stream, **wl["params"])
+    setup_s = time.perf_counter() - t0
+    N = s.N
+    if rhs is None:
+        if wl["rhs"] == "manufactured":
+            m = s.export_mesh()
+            ustar = torch.from_numpy(inputs.manufactured_solution(m["centres"], m["r_faces"], wl["seed"])).cuda()
+            f = torch.empty(N, dtype=torch.float64, device="cuda")
+            s.apply_operator(ustar, f)
+        else:
+            f = torch.from_numpy(inputs.uniform_pm1(wl["seed"], N)).cuda()
+    else:
+        f = rhs
+    s.profile(classes=())
+    res = time_solves(s, f, steps, warmup, rtol, 200, flush, stream)
+    launches = launches_of(s)
+    ms = statistics.median(r[0] for r in res)
+    it, st = res[-1][1], res[-1][2]
+    u = torch.zeros_like(f)
+    s.solve(f, u, rtol=rtol, max_iter=200, raise_on_fail=False)
+    au = torch.empty_like(u)
+    s.apply_operator(u, au)
+    true_rel = float(torch.linalg.norm(f - au) / torch.linalg.norm(f))
+    out = {"workload": wl["text"], "n_unknowns": N, "status": binding.status_name(st), "iters": it,
+           "ms_per_solve": ms, "unknowns_per_s": N / (ms / 1e3), "solves": len(res),
+           "true_rel_resid": true_rel, "setup_s": setup_s, "gpu_launches": launches,
+           "dtype": "f32+f64" if wl["params"].get("precision", 0) == 1 else "f64"}
+    s.close()
+    return out, f, (u if keep_u else None)
+
+
+def run_extra_configs(args, stream, flush) -> dict:
+    """The other configurations of the benchmark, each solved a few times in the same
+    run (a few seconds each): the small case, the headline grid with a rough
+    right-hand side (several iterations), refinement 7 x 128 in FP64 and in mixed
+    precision (with the mixed solution's distance from the FP64 one), and the
+    48-problem batch."""
+    import torch
+
+    out = {}
+    out["1280x16"], _, _ = solve_config("1280x16", stream, flush, 20, 3, args.rtol)
+    wl = dict(WORKLOADS["81920x64"], rhs="uniform", seed=2981010)
+    WORKLOADS["_81920x64-uniform"] = dict(wl, text=WORKLOADS["81920x64"]["text"].replace(
+        "manufactured spherical-harmonic x cosine solution, f = A u*", "RHS uniform[-1,1] (seed 2981010)"))
+    out["81920x64-uniform"], _, _ = solve_config("_81920x64-uniform", stream, flush, 10, 3, args.rtol)
+    del WORKLOADS["_81920x64-uniform"]
+    out["327680x128"], f, u64 = solve_config("327680x128", stream, flush, 5, 3, args.rtol, keep_u=True)
+    out["327680x128-mixed"], _, umx = solve_config("327680x128-mixed", stream, flush, 5, 3, args.rtol, rhs=f,
+                                                   keep_u=True)
+    mx = out["327680x128-mixed"]
+    mx["speedup_vs_fp64"] = out["327680x128"]["ms_per_solve"] / mx["ms_per_solve"]
+    mx["rel_diff_vs_fp64_solution"] = float(torch.linalg.norm(umx - u64) / torch.linalg.norm(u64))
+    del f, u64, umx
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    b = batch_stats(WORKLOADS["batch48"], stream, flush, steps=5, warmup=2, rtol=args.rtol)
+    out["batch48"] = {k: b[k] for k in ("workload", "n_unknowns", "problems", "ms_per_step", "unknowns_per_s",
+                                        "iters", "gpu_launches", "form")}
+    torch.cuda.empty_cache()
+    return out
+
+
+def batch_stats(wl, stream, flush, steps: int, warmup: int, rtol: float) -> dict:
+    """Set-up and timed runs of a batched workload (one tpmg_batch run per step)."""
+    import torch
+
+    from paper_1408_2981_gb300 import binding, inputs
+
+    probs = batch_problems(wl["seed"], wl["batch"])
+    solvers = [binding.Solver(stream=stream, **kw) for kw in probs]
+    fs = [torch.from_numpy(inputs.uniform_pm1(wl["seed"] + 100 + j, s.N)).cuda() for j, s in enumerate(solvers)]
+    us = [torch.zeros_like(f) for f in fs]
+    N = sum(s.N for s in solvers)
+    batch = binding.Batch(solvers, fs, us, rtol=rtol, max_iter=200)
+
+    def step():
+        for u in us:
+            u.zero_()
+        return batch.run(stream)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    launches, iters = 0, None
+    for k in range(steps):
+        flush.fill_(float(k))
+        evs[k][0].record(stream)
+        st, iters, rel, sts, nl = step()
+        evs[k][1].record(stream)
+        launches += nl
+        if st != binding.TPMG_OK:
+            raise RuntimeError(f"batch did not converge: statuses {sts.tolist()}")
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    out = {"workload": wl["text"], "n_unknowns": N, "problems": len(solvers), "ms_per_step": ms / steps,
+           "unknowns_per_s": N * steps / (ms / 1e3), "iters": [int(i) for i in iters], "gpu_launches": launches,
+           "local_ms": ms, "form": batch.form, "batch": batch, "solvers": solvers, "fs": fs, "us": us,
+           "step": step}
+    return out
 
 
 def run_batch(args, wl):
@@ -558,40 +691,16 @@ def run_batch(args, wl):
     torch.cuda.set_device(local)
     _build.build()
     stream = torch.cuda.current_stream()
-    probs = batch_problems(wl["seed"], wl["batch"])
-    solvers = [binding.Solver(stream=stream, **kw) for kw in probs]
-    fs = [torch.from_numpy(inputs.uniform_pm1(wl["seed"] + 100 + j, s.N)).cuda() for j, s in enumerate(solvers)]
-    us = [torch.zeros_like(f) for f in fs]
-    N = sum(s.N for s in solvers)
-    batch = binding.Batch(solvers, fs, us, rtol=args.rtol, max_iter=200)
     l2 = torch.cuda.get_device_properties(local).L2_cache_size
     flush = torch.empty(max(2 * l2, 256 << 20) // 4, dtype=torch.float32, device="cuda")
-
-    def step():
-        for u in us:
-            u.zero_()
-        return batch.run(stream)
-
-    for _ in range(args.warmup):
-        step()
     barrier(world)
-    torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    launches, iters = 0, None
-    for k in range(args.steps):
-        flush.fill_(float(k))
-        evs[k][0].record(stream)
-        st, iters, rel, sts, nl = step()
-        evs[k][1].record(stream)
-        launches += nl
-        if st != binding.TPMG_OK:
-            raise RuntimeError(f"batch did not converge: statuses {sts.tolist()}")
-    torch.cuda.synchronize()
+    b = batch_stats(wl, stream, flush, args.steps, args.warmup, args.rtol)
     clk = clocks.stop()
-    local_ms = sum(a.elapsed_time(b) for a, b in evs)
-    value, t_ms = aggregate_value(N, args.steps, world, local_ms)
+    fs, us, step, N, solvers, launches, iters = b["fs"], b["us"], b["step"], b["n_unknowns"], b["solvers"], \
+        b["gpu_launches"], b["iters"]
+    value, t_ms = aggregate_value(N, args.steps, world, b["local_ms"])
 
     # end to end: right-hand sides from pinned host memory and solutions back, inside the timed region
     f_host = [torch.empty(f.numel(), dtype=torch.float64, pin_memory=True).copy_(f) for f in fs]
@@ -619,7 +728,7 @@ def run_batch(args, wl):
                 "e2e": {"value": N * e2e_steps * world / (e2e_ms / 1e3), "unit": "unknowns/s",
                         "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N},
                 "gpu_launches": launches, "roofline": None, "cpu_baseline": None, "clocks": clk,
-                "iters": [int(i) for i in iters],
+                "iters": [int(i) for i in iters], "form": b["form"], "gpus_active": world,
                 "note": "the loops run on the device, so kernels carry no event pairs: no per-kernel roofline here"}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -798,15 +907,9 @@ def run_learned(args, wl):
     s.profile(classes=())
     shares = {k: v["ms"] for k, v in prof.items() if v["timed"] > 0}
     dominant = max(shares, key=shares.get)
-    d = prof[dominant]
-    fpu, bpu = (PER_UNIT[1].get(dominant) or (0.0, 0.0))
-    nbytes = bpu * d["units"]
-    roof = {"bound": "hbm", "achieved": nbytes / (d["ms"] / 1e3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "peak_source": f"{peaks['source']} HBM copy bandwidth",
-            "kernel": f"{dominant} (FP32/BF16), from one learned solve run kernel by kernel with every class timed",
-            "avg_launch_us": 1e3 * d["ms"] / max(1, d["timed"]), "traffic": None, "launches_per_step": d["launches"],
-            "algorithmic_bytes_per_launch": nbytes / max(1, d["launches"])}
-    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof = roofline_of(prof, None, dominant, True, 1, None, binding.fp64_peak_tflops(stream),
+                       torch.cuda.get_device_properties(local).multi_processor_count, args.workload,
+                       ", from one learned solve run kernel by kernel with every class timed")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -1047,6 +1150,35 @@ def run_prolongation(args, wl):
     return 0
 
 
+def free_port() -> int:
+    import socket
+
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        return sk.getsockname()[1]
+
+
+def replica_command(argv: list, n: int, port: int) -> list:
+    """The torchrun command line that starts n ranks of this bench on one node, one
+    per GPU, each solving its own replica of the workload."""
+    return [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+            "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + list(argv)
+
+
+def launcher_check() -> int:
+    """Each rank reports how it was started (after a gloo barrier); no GPU is used."""
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("gloo", init_method="env://")
+        dist.barrier()
+    print(json.dumps({"launcher_check": True, "rank": rank, "world": world, "local_rank": local}), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -1056,12 +1188,28 @@ def main(argv=None):
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="81920x64")
     ap.add_argument("--rtol", type=float, default=1e-5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra-configs", action="store_true",
+                    help="headline workload: skip the other configurations (small case, refinement 7, batch)")
     ap.add_argument("--pairs", type=int, default=None, help="learned workload: training pairs (default 2000)")
     ap.add_argument("--iters-hint", type=int, default=None,
                     help="reference arm on workloads sampled by one iteration: iterations of a full solve")
+    ap.add_argument("--launcher-check", action="store_true",
+                    help="start the ranks as --gpus asks, print each rank's view of the launch and exit (no GPU)")
+    argv = list(sys.argv[1:] if argv is None else argv)
     args = ap.parse_args(argv)
     if args.warmup < 1 and args.impl == "tpmg":
         ap.error("--warmup must be >= 1")
+    if args.gpus < 1:
+        ap.error("--gpus must be >= 1")
+    world_env = os.environ.get("WORLD_SIZE")
+    if world_env is None and args.gpus > 1:
+        # not started by torchrun: start the N replica ranks here (one process per GPU)
+        return subprocess.call(replica_command(argv, args.gpus, free_port()))
+    if world_env is not None and int(world_env) != args.gpus:
+        print(f"bench.py: --gpus {args.gpus} but WORLD_SIZE={world_env}: start one rank per GPU", file=sys.stderr)
+        return 2
+    if args.launcher_check:
+        return launcher_check()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         if "study" in wl:

@@ -248,9 +248,8 @@ tpmg_status tpmg_vcycle(tpmg_ctx *ctx, const double *d_r, double *d_z);
  * coarse levels of n_cells_l * n_r doubles for block-SOR, plus sum over all
  * levels of n_cells_l * n_r for block Jacobi (each part rounded up to 32
  * doubles); a larger problem is rejected with INVALID_ARG before anything is
- * launched.  The first call on a device looks up the array's device address
- * (once per device, with that device current); make that first call before
- * any stream capture.  Every call on a device shares the one array and leaves
+ * launched.  tpmg_setup looks up the array's device address (with the
+ * context's device current), so this call only reads it.  Every call on a device shares the one array and leaves
  * the last call's values in it; no element is read before the call has written
  * it, so nothing needs clearing.  Calls whose work overlaps on the GPU (other
  * streams, other contexts, other threads) race on the array: order them.
@@ -366,6 +365,43 @@ tpmg_status tpmg_profile(tpmg_ctx *ctx, unsigned class_mask);
  * Any output may be NULL.  Errors: INVALID_ARG, CUDA. */
 tpmg_status tpmg_profile_read(tpmg_ctx *ctx, int kernel_class, long long *launches, double *total_ms,
                               double *units, long long *timed);
+
+/* Algorithmic work of one kernel class since the last tpmg_profile call, for the
+ * roofline of the class: the HBM bytes the method itself must move (each array
+ * it needs streamed once, neighbour re-reads cached, per-column metadata
+ * amortised; arrays a kernel stores only to save arithmetic -- the Thomas
+ * factors, the outer operator's row products -- are not counted) and the flops
+ * of its formulas (FMA = 2).  bytes / flops cover every launch counted by
+ * tpmg_profile_read; timed_bytes / timed_flops the launches inside the class's
+ * event pairs, so that timed_bytes / total_ms is the class's achieved
+ * algorithmic rate.  Per unknown of a launch:
+ *   line relaxation (eq. BlockJacobi), FP64: 24 B (read f and u, write u), 16 B
+ *     from a zero guess; 12 flops (the right-hand side f + sum of the neighbour
+ *     couplings and its scaling by the pivot, 3 FMA and 2 multiplies, then one FMA
+ *     per recurrence), 5 for the first colour from a zero guess (no neighbour
+ *     terms); the prolongation fused into a coarse level's last
+ *     pass adds 8 B (2 B per fine unknown) and 4 flops per coarse unknown;
+ *   line relaxation, FP32 on the BF16 stencil: f (8 B on the finest level, 4 B
+ *     below) + stencil 10 B + u read 4 B (not from a zero guess) + u write 4 B,
+ *     +8 B for the finest level's FP64 result, +4 B per coarse unknown of fused
+ *     prolongation; flops as in FP64;
+ *   residual + restriction (Algorithm 1) per fine unknown: FP64 18 B, 12 flops;
+ *     FP32 f + u 4 B + stencil 10 B + 1 B, 20 flops;
+ *   operator apply 16 B, 14 flops; initial residual 24 B, 17 flops (+8 B for the
+ *   zero-guess probe); axpy 48 B (56 B in flexible CG); dot 16 B; xpby 24 B;
+ *   clears 8 B (FP32: 4 B); copies 16 B.
+ * Any output may be NULL.  Synchronises the context stream.  Errors: INVALID_ARG, CUDA. */
+tpmg_status tpmg_profile_work(tpmg_ctx *ctx, int kernel_class, double *bytes, double *timed_bytes, double *flops,
+                              double *timed_flops);
+
+/* Measured FP64 throughput of the current device in TFLOP/s (FMA = 2 flops): a
+ * kernel of independent FMA chains fills every SM (as many 256-thread blocks as
+ * fit), one warm-up launch, then the best of three launches timed with CUDA
+ * events on cuda_stream.  It is the denominator of the FP64-pipe roofline of the
+ * FP64 kernels.  The paper has no counterpart: a measurement utility.  Allocates
+ * and frees a small device buffer; synchronises the stream; takes about 0.2 s.
+ * Errors: INVALID_ARG (tflops NULL), OOM, CUDA. */
+tpmg_status tpmg_fp64_peak(void *cuda_stream, double *tflops);
 
 /* Static description of a status value. */
 const char *tpmg_status_string(tpmg_status s);

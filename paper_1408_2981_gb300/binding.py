@@ -44,6 +44,7 @@ EXPORTS = ["tpmg_default_params", "tpmg_setup", "tpmg_setup_profiles", "tpmg_set
            "tpmg_apply_operator", "tpmg_vcycle", "tpmg_vcycle_noalloc",
            "tpmg_solve",
            "tpmg_solve_host", "tpmg_query", "tpmg_query_tuning", "tpmg_export_mesh", "tpmg_profile", "tpmg_profile_read",
+           "tpmg_profile_work", "tpmg_fp64_peak",
            "tpmg_status_string", "tpmg_last_error", "tpmg_destroy", "tpmg_batch_create", "tpmg_batch_run",
            "tpmg_batch_destroy"]
 
@@ -115,6 +116,8 @@ def load(path: str | None = None):
     lib.tpmg_profile.argtypes = [P, ctypes.c_uint]
     lib.tpmg_profile_read.argtypes = [P, I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(D), ctypes.POINTER(D),
                                       ctypes.POINTER(ctypes.c_longlong)]
+    lib.tpmg_profile_work.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D)]
+    lib.tpmg_fp64_peak.argtypes = [P, ctypes.POINTER(D)]
     lib.tpmg_status_string.argtypes = [I]
     lib.tpmg_status_string.restype = ctypes.c_char_p
     lib.tpmg_last_error.argtypes = [P]
@@ -156,6 +159,19 @@ def load(path: str | None = None):
     if path is None:
         _lib = lib
     return lib
+
+
+def fp64_peak_tflops(stream=None) -> float:
+    """Measured FP64 FMA throughput of the current GPU in TFLOP/s (tpmg_fp64_peak)."""
+    import torch
+
+    lib = load()
+    stream = stream or torch.cuda.current_stream()
+    t = ctypes.c_double()
+    st = lib.tpmg_fp64_peak(ctypes.c_void_p(stream.cuda_stream), ctypes.byref(t))
+    if st != TPMG_OK:
+        raise TPMGError(st, "tpmg_fp64_peak")
+    return t.value
 
 
 def status_name(status: int) -> str:
@@ -289,7 +305,11 @@ class Solver:
             n, ms, units, timed = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double(), ctypes.c_longlong()
             self._check(self._lib.tpmg_profile_read(self._h, i, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(units),
                                                     ctypes.byref(timed)), "tpmg_profile_read")
-            out[name] = dict(launches=n.value, ms=ms.value, units=units.value, timed=timed.value)
+            b, tb, fl, tfl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+            self._check(self._lib.tpmg_profile_work(self._h, i, ctypes.byref(b), ctypes.byref(tb), ctypes.byref(fl),
+                                                    ctypes.byref(tfl)), "tpmg_profile_work")
+            out[name] = dict(launches=n.value, ms=ms.value, units=units.value, timed=timed.value, bytes=b.value,
+                             timed_bytes=tb.value, flops=fl.value, timed_flops=tfl.value)
         return out
 
     def set_outer_profiles(self, beta=None, alphar=None, alphaS=None, xi=None):
@@ -552,6 +572,7 @@ class Batch:
         if st != TPMG_OK:
             raise TPMGError(st, "tpmg_batch_create")
         self._h = h
+        self.form = "branches"
 
     def run(self, stream=None):
         """Returns (status, iters[n], rel_resid[n], status[n], kernel_launches)."""

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libtpmg.so")
-SOURCES = ["grid.cpp", "kernels.cu", "kernels32.cu", "api.cu", "noalloc.cu", "learned.cu"]
+SOURCES = ["grid.cpp", "kernels.cu", "kernels32.cu", "api.cu", "noalloc.cu", "learned.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

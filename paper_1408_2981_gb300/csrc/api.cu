@@ -12,6 +12,7 @@
 #include <new>
 #include <string>
 #include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "tpmg_internal.h"
@@ -23,9 +24,13 @@ struct Tracer {
     unsigned mask = 0;
     long long launches[TPMG_K_COUNT] = {};
     double units[TPMG_K_COUNT] = {};
+    double bytes[TPMG_K_COUNT] = {};   // algorithmic HBM bytes of the launches (alg_* below)
+    double flops[TPMG_K_COUNT] = {};   // algorithmic flops of the launches (FMA = 2)
     std::vector<cudaEvent_t> ev;   // pairs: ev[2i] before the first, ev[2i+1] after the last launch of bracket i
     std::vector<int> cls;          // class of bracket i
     std::vector<int> nl;           // launches in bracket i
+    std::vector<double> nb;        // algorithmic bytes of the launches in bracket i
+    std::vector<double> nf;        // algorithmic flops of the launches in bracket i
     size_t used = 0;
     int open = -1;                 // class of the bracket being captured, -1 if none
     cudaStream_t open_s = nullptr; // its stream
@@ -36,6 +41,8 @@ struct Tracer {
 struct ClassCounts {
     long long init[TPMG_K_COUNT] = {}, iter[TPMG_K_COUNT] = {};
     double uinit[TPMG_K_COUNT] = {}, uiter[TPMG_K_COUNT] = {};
+    double binit[TPMG_K_COUNT] = {}, biter[TPMG_K_COUNT] = {};
+    double finit[TPMG_K_COUNT] = {}, fiter[TPMG_K_COUNT] = {};
 };
 
 // The V-cycle of tpmg_solve (r -> z on the context's own vectors) replayed
@@ -44,6 +51,8 @@ struct GraphCache {
     cudaGraphExec_t exec = nullptr;
     long long launches[TPMG_K_COUNT] = {};
     double units[TPMG_K_COUNT] = {};
+    double bytes[TPMG_K_COUNT] = {};
+    double flops[TPMG_K_COUNT] = {};
 };
 
 struct tpmg_ctx {
@@ -103,6 +112,7 @@ struct tpmg_ctx {
     double *d_hist = nullptr;     // [kHistCap] residual history of the device-side loop
     int device = 0;
     int sm_count = 0;
+    double *noalloc_base = nullptr;   // device address of tpmg_vcycle_noalloc's fixed array (set-up)
     HostGrid host;
     std::vector<LevelDev> lv;     // multigrid levels, 0 = coarsest
     VertDev vert{};
@@ -255,6 +265,8 @@ cudaError_t grow_events(Tracer &t, size_t pairs)
     }
     if (t.cls.size() < pairs) t.cls.resize(pairs);
     if (t.nl.size() < pairs) t.nl.resize(pairs);
+    if (t.nb.size() < pairs) t.nb.resize(pairs);
+    if (t.nf.size() < pairs) t.nf.resize(pairs);
     return cudaSuccess;
 }
 
@@ -280,12 +292,56 @@ cudaError_t close_bracket(tpmg_ctx *ctx)
 // node between two kernels costs microseconds of its own and would cut the
 // programmatic overlap of the kernels around it.  The capture closes the last
 // bracket before it ends (end_capture).
+// Algorithmic HBM bytes per unit of the kernel classes whose launches do not state
+// their own: each array the method needs streamed once (neighbour re-reads cached,
+// per-column metadata amortised), FP64 vectors of the outer iteration.  The line
+// relaxation, the restriction, the prolongation, the copies and the initial residual
+// state their bytes at the launch (alg_* below).
+double class_bytes_per_unit(int kclass)
+{
+    switch (kclass) {
+    case TPMG_K_APPLY: return 16.0;    // read x, write y
+    case TPMG_K_RESIDUAL: return 24.0; // read f, u, write r
+    case TPMG_K_RESTRICT: return 18.0; // read f, u, write f_c (a quarter of the fine size)
+    case TPMG_K_PROLONG: return 18.0;  // read u_c (a quarter), read and write u
+    case TPMG_K_DOT: return 16.0;
+    case TPMG_K_AXPY: return 48.0;     // read p, q, u, r, write u, r (+8 with z_old: alg_axpy)
+    case TPMG_K_XPBY: return 24.0;
+    case TPMG_K_COPY: return 8.0;      // a clear (a copy states 16)
+    default: return 0.0;               // finish (scalars), network (not part of the roofline)
+    }
+}
+
+// Algorithmic FP64 flops per unit (FMA = 2) of the same classes: the arithmetic of the
+// method's formulas as the kernels evaluate them.  The apply's row (8 operations from
+// its stored products) and its fused dot; the residual's flux-form row; the
+// restriction's row per fine unknown; the axpy pair with ||r||^2; dot, xpby one FMA.
+double class_flops_per_unit(int kclass)
+{
+    switch (kclass) {
+    case TPMG_K_APPLY: return 14.0;
+    case TPMG_K_RESIDUAL: return 17.0;
+    case TPMG_K_RESTRICT: return 12.0;
+    case TPMG_K_PROLONG: return 1.0;
+    case TPMG_K_DOT: return 2.0;
+    case TPMG_K_AXPY: return 6.0;
+    case TPMG_K_XPBY: return 2.0;
+    default: return 0.0;
+    }
+}
+
+struct Alg {         // algorithmic work of one launch
+    double bytes, flops;
+};
+
 template <class F>
-cudaError_t run(tpmg_ctx *ctx, int kclass, double units, F &&launch)
+cudaError_t run_w(tpmg_ctx *ctx, int kclass, double units, Alg w, F &&launch)
 {
     Tracer &t = ctx->tr;
     t.launches[kclass] += 1;
     t.units[kclass] += units;
+    t.bytes[kclass] += w.bytes;
+    t.flops[kclass] += w.flops;
     const bool timed = (t.mask >> kclass) & 1u;
     cudaError_t e = cudaSuccess;
     if (t.open >= 0 && (t.open != kclass || t.open_s != ctx->issue)) e = close_bracket(ctx);
@@ -300,10 +356,16 @@ cudaError_t run(tpmg_ctx *ctx, int kclass, double units, F &&launch)
         t.open = kclass;
         t.open_s = ctx->issue;
         t.nl[t.used] = 0;
+        t.nb[t.used] = 0.0;
+        t.nf[t.used] = 0.0;
     }
     e = launch();
     if (timed) {
-        if (e == cudaSuccess) t.nl[t.used] += 1;
+        if (e == cudaSuccess) {
+            t.nl[t.used] += 1;
+            t.nb[t.used] += w.bytes;
+            t.nf[t.used] += w.flops;
+        }
         if (!ctx->capturing) {
             const cudaError_t ec = close_bracket(ctx);
             if (e == cudaSuccess) e = ec;
@@ -311,6 +373,55 @@ cudaError_t run(tpmg_ctx *ctx, int kclass, double units, F &&launch)
     }
     return e;
 }
+
+// a launch whose flops follow from its class (class_flops_per_unit) and whose bytes are given
+template <class F>
+cudaError_t run_b(tpmg_ctx *ctx, int kclass, double units, double bytes, F &&launch)
+{
+    return run_w(ctx, kclass, units, Alg{bytes, units * class_flops_per_unit(kclass)}, std::forward<F>(launch));
+}
+
+template <class F>
+cudaError_t run(tpmg_ctx *ctx, int kclass, double units, F &&launch)
+{
+    return run_b(ctx, kclass, units, units * class_bytes_per_unit(kclass), std::forward<F>(launch));
+}
+
+// Algorithmic bytes of one line-relaxation pass over `units` unknowns (the survey of
+// the method's traffic: the arrays the method needs, each streamed once).  FP64: read
+// f, the neighbours' u (one read of u over a sweep) and write u, 24 B per unknown;
+// a pass from a zero guess reads no u, 16 B; the prolongation fused into a coarse
+// level's last pass adds the read of the coarse value, 2 B per fine unknown = 8 B per
+// coarse unknown.  The stored twisted factors are this design's extra traffic, not
+// the method's.
+// Flops per unknown: the right-hand side f + hr_k sum_e g_e u_e (3 FMA + 1 multiply)
+// scaled by the pivot (1), the forward and backward recurrences (1 FMA each): 12; from
+// a zero guess the first colour has no neighbour terms, 5; the fused prolongation adds
+// 4 per coarse unknown.  (The kernels evaluate the neighbour terms of the other colours
+// of a first sweep with zeros for the not yet relaxed ones, as counted here.)
+Alg alg_relax64(double units, int mode, bool fused)
+{
+    return Alg{units * ((mode == PASS_NORMAL ? 24.0 : 16.0) + (fused ? 8.0 : 0.0)),
+               units * ((mode == PASS_RHS_ONLY ? 5.0 : 12.0) + (fused ? 4.0 : 0.0))};
+}
+// The FP32 V-cycle on the BF16 stencil: f (8 B in FP64 on the finest level, 4 B
+// below), the stencil of the column (alphaS_hat x 3 and beta_hat: 8 B; alphar_hat of
+// the lower face: 2 B), u read (4 B, not from a zero guess), u written (4 B), the
+// finest level's result also written in FP64 (8 B), the fused prolongation 1 B per
+// fine unknown (4 B per coarse unknown).  The stored FP32 Thomas factors (12 B) are
+// this design's extra traffic.
+// Flops (FP32) per unknown as in FP64: 12, 5 for the first colour from a zero guess,
+// +4 per coarse unknown for the fused prolongation.
+Alg alg_relax32(double units, int mode, bool f64, bool out64, bool fused)
+{
+    return Alg{units * ((f64 ? 8.0 : 4.0) + 10.0 + (mode == PASS_NORMAL ? 4.0 : 0.0) + 4.0 + (out64 ? 8.0 : 0.0) +
+                        (fused ? 4.0 : 0.0)),
+               units * ((mode == PASS_RHS_ONLY ? 5.0 : 12.0) + (fused ? 4.0 : 0.0))};
+}
+// Residual + restriction in FP32 per fine unknown: f (8 or 4 B), u (4 B), the stencil
+// (10 B), f_c written (4 B over 4 children).
+// Flops per fine unknown: the flux-form row (6 FMA, 1 multiply, 6 differences) and the sum.
+Alg alg_restrict32(double units, bool f64) { return Alg{units * ((f64 ? 8.0 : 4.0) + 4.0 + 10.0 + 1.0), units * 20.0}; }
 
 #define LCHK(call)                                                                                \
     do {                                                                                          \
@@ -325,7 +436,8 @@ cudaError_t residual_probed(tpmg_ctx *ctx, const Launch &L, const double *f, con
 {
     const LevelDev &fl = ctx->lv.back();
     const long N = ctx->N;
-    cudaError_t e = run(ctx, TPMG_K_RESIDUAL, (double)N, [&] { return launch_nonzero(L, N, u, ctx->zflags, ctx->n_part); });
+    cudaError_t e = run_w(ctx, TPMG_K_RESIDUAL, (double)N, Alg{8.0 * N, 0.0},   // the probe reads u
+                          [&] { return launch_nonzero(L, N, u, ctx->zflags, ctx->n_part); });
     if (e != cudaSuccess) return e;
     return run(ctx, TPMG_K_RESIDUAL, (double)N, [&] {
         return launch_residual(L, fl, ctx->vert, f, u, r, ctx->partials, ctx->n_part, ctx->zflags);
@@ -364,14 +476,15 @@ tpmg_status vcycle_level(tpmg_ctx *ctx, int l, const double *f, double *u, doubl
     auto pass = [&](int c, int mode, double *fine) -> cudaError_t {
         const int t0 = lv.colour_task_off[c], nt = lv.colour_task_off[c + 1] - t0;
         const int m = (mode == PASS_ZERO && c == 0) ? PASS_RHS_ONLY : mode;
-        return run(ctx, TPMG_K_RELAX, (double)lv.colour_cells[c] * p.n_r, [&] {
+        const double units = (double)lv.colour_cells[c] * p.n_r;
+        return run_w(ctx, TPMG_K_RELAX, units, alg_relax64(units, m, fine != nullptr), [&] {
             return launch_relax(L, lv, ctx->vert, m, t0, nt, p.relax, f, u, u, fine);
         });
     };
     // one block-Jacobi sweep from cur into oth
     auto jacobi = [&](int mode, double *fine) -> cudaError_t {
         const int m = mode == PASS_ZERO ? PASS_RHS_ONLY : mode;
-        cudaError_t e = run(ctx, TPMG_K_RELAX, nunits, [&] {
+        cudaError_t e = run_w(ctx, TPMG_K_RELAX, nunits, alg_relax64(nunits, m, fine != nullptr), [&] {
             return launch_relax(L, lv, ctx->vert, m, 0, lv.n_tasks, p.relax, f, cur, oth, fine);
         });
         std::swap(cur, oth);
@@ -436,8 +549,8 @@ tpmg_status vcycle_level(tpmg_ctx *ctx, int l, const double *f, double *u, doubl
     // the finest level returns its result in u (coarse levels have handed theirs on already)
     if (!u_fine && cur != u) {
         const double *cc = cur;
-        LCHK(run(ctx, TPMG_K_COPY, nunits,
-                 [&] { return cudaMemcpyAsync(u, cc, nbytes, cudaMemcpyDeviceToDevice, ctx->issue); }));
+        LCHK(run_b(ctx, TPMG_K_COPY, nunits, 16.0 * nunits,
+                   [&] { return cudaMemcpyAsync(u, cc, nbytes, cudaMemcpyDeviceToDevice, ctx->issue); }));
     }
     return TPMG_OK;
 }
@@ -509,6 +622,7 @@ tpmg_status vcycle_mixed(tpmg_ctx *ctx, int l, const TF *f, float *u, float *scr
     const float relax = (float)p.relax;
     const double nunits = (double)lv.n * p.n_r;
     const size_t nbytes = sizeof(float) * lv.n * p.n_r;
+    constexpr bool kF64 = std::is_same<TF, double>::value;   // the finest level's FP64 right-hand side
     float *cur = u, *oth = scratch;
     // the coarse-to-fine transfer as in vcycle_level: fused into the final pass, or the
     // linear prolongation after the level's last pass
@@ -516,33 +630,34 @@ tpmg_status vcycle_mixed(tpmg_ctx *ctx, int l, const TF *f, float *u, float *scr
     float *const fuse = lin ? nullptr : u_fine;
     auto prolong_linear = [&](const float *cc) -> tpmg_status {
         const LevelDev &fl = ctx->lv[l + 1];
-        LCHK(run(ctx, TPMG_K_PROLONG, (double)fl.n * p.n_r,
-                 [&] { return launch_prolong_linear32(L, fl, lv, cc, u_fine); }));
+        LCHK(run_b(ctx, TPMG_K_PROLONG, (double)fl.n * p.n_r, 9.0 * fl.n * p.n_r,
+                   [&] { return launch_prolong_linear32(L, fl, lv, cc, u_fine); }));
         return TPMG_OK;
     };
     auto pass = [&](int c, int mode, float *fine, double *out) -> cudaError_t {
         const int t0 = lv.colour_task_off[c], nt = lv.colour_task_off[c + 1] - t0;
         const int m = (mode == PASS_ZERO && c == 0) ? PASS_RHS_ONLY : mode;
-        return run(ctx, TPMG_K_RELAX, (double)lv.colour_cells[c] * p.n_r,
-                   [&] { return launch_relax32<TF>(L, lv, m, t0, nt, relax, f, u, u, fine, out); });
+        const double units = (double)lv.colour_cells[c] * p.n_r;
+        return run_w(ctx, TPMG_K_RELAX, units, alg_relax32(units, m, kF64, out != nullptr, fine != nullptr),
+                     [&] { return launch_relax32<TF>(L, lv, m, t0, nt, relax, f, u, u, fine, out); });
     };
     auto jacobi = [&](int mode, float *fine, double *out) -> cudaError_t {
         const int m = mode == PASS_ZERO ? PASS_RHS_ONLY : mode;
-        cudaError_t e = run(ctx, TPMG_K_RELAX, nunits, [&] {
-            return launch_relax32<TF>(L, lv, m, 0, lv.n_tasks, relax, f, cur, oth, fine, out);
-        });
+        cudaError_t e = run_w(ctx, TPMG_K_RELAX, nunits, alg_relax32(nunits, m, kF64, out != nullptr, fine != nullptr),
+                              [&] { return launch_relax32<TF>(L, lv, m, 0, lv.n_tasks, relax, f, cur, oth, fine, out); });
         std::swap(cur, oth);
         return e;
     };
     auto clear = [&](float *x) -> cudaError_t {
-        return run(ctx, TPMG_K_COPY, nunits, [&] { return cudaMemsetAsync(x, 0, nbytes, ctx->issue); });
+        return run_b(ctx, TPMG_K_COPY, nunits, 4.0 * nunits, [&] { return cudaMemsetAsync(x, 0, nbytes, ctx->issue); });
     };
     if (l == 0) {
         if constexpr (std::is_same<TF, float>::value) {
             // recording of the coarsest-level right-hand sides (training data of the learned form)
             if (ctx->rec && !ctx->capturing && ctx->rec_n < ctx->rec_cap) {
                 double *dst = ctx->rec + (size_t)ctx->rec_n * lv.n * p.n_r;
-                LCHK(run(ctx, TPMG_K_COPY, nunits, [&] { return launch_to_f64(L, (long)lv.n * p.n_r, f, dst); }));
+                LCHK(run_b(ctx, TPMG_K_COPY, nunits, 12.0 * nunits,
+                           [&] { return launch_to_f64(L, (long)lv.n * p.n_r, f, dst); }));
                 ++ctx->rec_n;
             }
             // learned form: the network's prediction and one block-Jacobi line
@@ -551,7 +666,7 @@ tpmg_status vcycle_mixed(tpmg_ctx *ctx, int l, const TF *f, float *u, float *scr
             if (ctx->net_coarse_on) {
                 tpmg_status st = net_infer<float, float>(ctx, TPMG_NET_COARSE, lv, f, scratch);
                 if (st != TPMG_OK) return st;
-                LCHK(run(ctx, TPMG_K_RELAX, nunits, [&] {
+                LCHK(run_w(ctx, TPMG_K_RELAX, nunits, alg_relax32(nunits, PASS_NORMAL, false, false, fuse != nullptr), [&] {
                     return launch_relax32<float>(L, lv, PASS_NORMAL, 0, lv.n_tasks, relax, f, scratch, u, fuse, nullptr);
                 }));
                 return lin ? prolong_linear(u) : TPMG_OK;
@@ -559,7 +674,9 @@ tpmg_status vcycle_mixed(tpmg_ctx *ctx, int l, const TF *f, float *u, float *scr
         }
         if (p.nu_coarse == 0) {
             LCHK(clear(u));
-            if (z64) LCHK(run(ctx, TPMG_K_COPY, nunits, [&] { return launch_to_f64(L, (long)lv.n * p.n_r, u, z64); }));
+            if (z64)
+                LCHK(run_b(ctx, TPMG_K_COPY, nunits, 12.0 * nunits,
+                           [&] { return launch_to_f64(L, (long)lv.n * p.n_r, u, z64); }));
         }
         for (int s = 0; s < p.nu_coarse; ++s) {
             const bool last = s == p.nu_coarse - 1;
@@ -586,8 +703,8 @@ tpmg_status vcycle_mixed(tpmg_ctx *ctx, int l, const TF *f, float *u, float *scr
     }
     LevelDev &co = ctx->lv[l - 1];
     const float *uc = cur;
-    LCHK(run(ctx, TPMG_K_RESTRICT, nunits,
-             [&] { return launch_resid_restrict32<TF>(L, lv, co, f, uc, co.f32); }));
+    LCHK(run_w(ctx, TPMG_K_RESTRICT, nunits, alg_restrict32(nunits, kF64),
+               [&] { return launch_resid_restrict32<TF>(L, lv, co, f, uc, co.f32); }));
     tpmg_status st = vcycle_mixed<float>(ctx, l - 1, co.f32, co.u32, co.u2_32, cur, nullptr);
     if (st != TPMG_OK) return st;
     for (int s = 0; s < p.nu_post; ++s) {
@@ -606,10 +723,12 @@ tpmg_status vcycle_mixed(tpmg_ctx *ctx, int l, const TF *f, float *u, float *scr
         const float *cc = cur;
         if (fuse) {
             const LevelDev &fl = ctx->lv[l + 1];
-            LCHK(run(ctx, TPMG_K_PROLONG, (double)fl.n * p.n_r,
-                     [&] { return launch_prolong_add32(L, fl, cc, u_fine); }));
+            LCHK(run_b(ctx, TPMG_K_PROLONG, (double)fl.n * p.n_r, 9.0 * fl.n * p.n_r,
+                       [&] { return launch_prolong_add32(L, fl, cc, u_fine); }));
         }
-        if (z64) LCHK(run(ctx, TPMG_K_COPY, nunits, [&] { return launch_to_f64(L, (long)lv.n * p.n_r, cc, z64); }));
+        if (z64)
+            LCHK(run_b(ctx, TPMG_K_COPY, nunits, 12.0 * nunits,
+                       [&] { return launch_to_f64(L, (long)lv.n * p.n_r, cc, z64); }));
     }
     return TPMG_OK;
 }
@@ -643,9 +762,11 @@ tpmg_status vcycle_pcg(tpmg_ctx *ctx)
     Tracer &t = ctx->tr;
     if (!ctx->vc.exec) {
         long long l0[TPMG_K_COUNT];
-        double u0[TPMG_K_COUNT];
+        double u0[TPMG_K_COUNT], b0[TPMG_K_COUNT], f0[TPMG_K_COUNT];
         std::copy(t.launches, t.launches + TPMG_K_COUNT, l0);
         std::copy(t.units, t.units + TPMG_K_COUNT, u0);
+        std::copy(t.bytes, t.bytes + TPMG_K_COUNT, b0);
+        std::copy(t.flops, t.flops + TPMG_K_COUNT, f0);
         CU(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
         ctx->capturing = true;
         ctx->issue = ctx->cap_stream;
@@ -662,8 +783,12 @@ tpmg_status vcycle_pcg(tpmg_ctx *ctx)
         for (int c = 0; c < TPMG_K_COUNT; ++c) {   // the captured launches belong to every replay
             ctx->vc.launches[c] = t.launches[c] - l0[c];
             ctx->vc.units[c] = t.units[c] - u0[c];
+            ctx->vc.bytes[c] = t.bytes[c] - b0[c];
+            ctx->vc.flops[c] = t.flops[c] - f0[c];
             t.launches[c] = l0[c];
             t.units[c] = u0[c];
+            t.bytes[c] = b0[c];
+            t.flops[c] = f0[c];
         }
         if (st != TPMG_OK) return st;
         if (e != cudaSuccess) return fail(ctx, TPMG_ERR_CUDA, std::string("V-cycle capture: ") + cudaGetErrorString(e));
@@ -674,6 +799,8 @@ tpmg_status vcycle_pcg(tpmg_ctx *ctx)
     for (int c = 0; c < TPMG_K_COUNT; ++c) {
         t.launches[c] += ctx->vc.launches[c];
         t.units[c] += ctx->vc.units[c];
+        t.bytes[c] += ctx->vc.bytes[c];
+        t.flops[c] += ctx->vc.flops[c];
     }
     return TPMG_OK;
 }
@@ -731,9 +858,11 @@ tpmg_status append_solve(tpmg_ctx *ctx, cudaGraph_t g, const double *f, double *
 {
     Tracer &t = ctx->tr;
     long long l0[TPMG_K_COUNT];
-    double u0[TPMG_K_COUNT];
+    double u0[TPMG_K_COUNT], b0[TPMG_K_COUNT], f0[TPMG_K_COUNT];
     std::copy(t.launches, t.launches + TPMG_K_COUNT, l0);
     std::copy(t.units, t.units + TPMG_K_COUNT, u0);
+    std::copy(t.bytes, t.bytes + TPMG_K_COUNT, b0);
+    std::copy(t.flops, t.flops + TPMG_K_COUNT, f0);
     cudaGraphConditionalHandle h;
     CU(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
     const LoopCtl loop{h, rtol, max_iter, ctx->d_hist};
@@ -750,7 +879,7 @@ tpmg_status append_solve(tpmg_ctx *ctx, cudaGraph_t g, const double *f, double *
             // the vertically oscillating part of the network's error; written to u in FP64
             tpmg_status s1 = net_infer<double, float>(ctx, TPMG_NET_WARM, fl, f, fl.u32);
             if (s1 != TPMG_OK) return s1;
-            LCHK(run(ctx, TPMG_K_RELAX, (double)N, [&] {
+            LCHK(run_w(ctx, TPMG_K_RELAX, (double)N, alg_relax32((double)N, PASS_NORMAL, true, true, false), [&] {
                 return launch_relax32<double>(L, fl, PASS_NORMAL, 0, fl.n_tasks, (float)ctx->p.relax, f, fl.u32,
                                               fl.u2_32, nullptr, u);
             }));
@@ -769,11 +898,13 @@ tpmg_status append_solve(tpmg_ctx *ctx, cudaGraph_t g, const double *f, double *
     if (st != TPMG_OK) return st;
     long long after_init = 0;
     long long l1[TPMG_K_COUNT];
-    double u1[TPMG_K_COUNT];
+    double u1[TPMG_K_COUNT], b1[TPMG_K_COUNT], f1[TPMG_K_COUNT];
     for (int c = 0; c < TPMG_K_COUNT; ++c) {
         after_init += t.launches[c] - l0[c];
         l1[c] = t.launches[c];
         u1[c] = t.units[c];
+        b1[c] = t.bytes[c];
+        f1[c] = t.flops[c];
     }
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
@@ -797,7 +928,8 @@ tpmg_status append_solve(tpmg_ctx *ctx, cudaGraph_t g, const double *f, double *
         LCHK(run(ctx, TPMG_K_APPLY, (double)N, [&] { return launch_apply(L, fl, ctx->vert, ctx->pv, ctx->q, ctx->partials, np); }));
         LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_ALPHA, ctx->partials, np, ctx->sc); }));
         const double *z_old = flexible ? ctx->z : nullptr;
-        LCHK(run(ctx, TPMG_K_AXPY, (double)N, [&] { return launch_axpy_pair(L, N, ctx->sc, ctx->pv, ctx->q, u, ctx->r, ctx->partials, np, z_old); }));
+        LCHK(run_w(ctx, TPMG_K_AXPY, (double)N, Alg{(z_old ? 56.0 : 48.0) * N, (z_old ? 8.0 : 6.0) * N},
+                   [&] { return launch_axpy_pair(L, N, ctx->sc, ctx->pv, ctx->q, u, ctx->r, ctx->partials, np, z_old); }));
         LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_LOOP_RR, ctx->partials, np, ctx->sc, &loop); }));
         if (flexible)
             LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_RZC, ctx->partials + np, np, ctx->sc); }));
@@ -813,9 +945,15 @@ tpmg_status append_solve(tpmg_ctx *ctx, cudaGraph_t g, const double *f, double *
             cls->iter[c] = t.launches[c] - l1[c];
             cls->uinit[c] = u1[c] - u0[c];
             cls->uiter[c] = t.units[c] - u1[c];
+            cls->binit[c] = b1[c] - b0[c];
+            cls->biter[c] = t.bytes[c] - b1[c];
+            cls->finit[c] = f1[c] - f0[c];
+            cls->fiter[c] = t.flops[c] - f1[c];
         }
     std::copy(l0, l0 + TPMG_K_COUNT, t.launches);
     std::copy(u0, u0 + TPMG_K_COUNT, t.units);
+    std::copy(b0, b0 + TPMG_K_COUNT, t.bytes);
+    std::copy(f0, f0 + TPMG_K_COUNT, t.flops);
     return st;
 }
 
@@ -865,6 +1003,8 @@ tpmg_status pcg_graph(tpmg_ctx *ctx, const double *f, double *u, double rtol, in
         for (int c = 0; c < TPMG_K_COUNT; ++c) {
             ctx->tr.launches[c] += ctx->sg_cls.init[c] + (long long)s.it * ctx->sg_cls.iter[c];
             ctx->tr.units[c] += ctx->sg_cls.uinit[c] + s.it * ctx->sg_cls.uiter[c];
+            ctx->tr.bytes[c] += ctx->sg_cls.binit[c] + s.it * ctx->sg_cls.biter[c];
+            ctx->tr.flops[c] += ctx->sg_cls.finit[c] + s.it * ctx->sg_cls.fiter[c];
         }
     if (hist && s.it >= 0) CU(cudaMemcpy(hist, ctx->d_hist, sizeof(double) * (s.it + 1), cudaMemcpyDeviceToHost));
     return loop_result(ctx, s, rtol, max_iter, iters, rel);
@@ -1000,7 +1140,7 @@ tpmg_status pcg(tpmg_ctx *ctx, const double *f, double *u, double rtol, int max_
     if (learned && ctx->net[TPMG_NET_WARM]) {
         tpmg_status s1 = net_infer<double, float>(ctx, TPMG_NET_WARM, fl, f, fl.u32);
         if (s1 != TPMG_OK) return s1;
-        LCHK(run(ctx, TPMG_K_RELAX, (double)N, [&] {
+        LCHK(run_w(ctx, TPMG_K_RELAX, (double)N, alg_relax32((double)N, PASS_NORMAL, true, true, false), [&] {
             return launch_relax32<double>(L, fl, PASS_NORMAL, 0, fl.n_tasks, (float)ctx->p.relax, f, fl.u32, fl.u2_32,
                                           nullptr, u);
         }));
@@ -1039,7 +1179,8 @@ tpmg_status pcg(tpmg_ctx *ctx, const double *f, double *u, double rtol, int max_
         LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_ALPHA, ctx->partials, np, ctx->sc); }));
         // flexible CG (mixed precision): the axpy also forms <r_new, z_old>
         const double *z_old = flexible ? ctx->z : nullptr;
-        LCHK(run(ctx, TPMG_K_AXPY, (double)N, [&] { return launch_axpy_pair(L, N, ctx->sc, ctx->pv, ctx->q, u, ctx->r, ctx->partials, np, z_old); }));
+        LCHK(run_w(ctx, TPMG_K_AXPY, (double)N, Alg{(z_old ? 56.0 : 48.0) * N, (z_old ? 8.0 : 6.0) * N},
+                   [&] { return launch_axpy_pair(L, N, ctx->sc, ctx->pv, ctx->q, u, ctx->r, ctx->partials, np, z_old); }));
         LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_RR, ctx->partials, np, ctx->sc); }));
         if (flexible) LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_RZC, ctx->partials + np, np, ctx->sc); }));
         if ((st = read_scalars(ctx)) != TPMG_OK) return st;
@@ -1623,6 +1764,9 @@ tpmg_status tpmg_setup_profiles(const tpmg_params *params, const tpmg_profiles *
     if (cudaGetDevice(&ctx->device) != cudaSuccess) return bail(TPMG_ERR_CUDA);
     if (cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess)
         return bail(TPMG_ERR_CUDA);
+    // the fixed array of tpmg_vcycle_noalloc: its address is looked up here, with the
+    // context's device current, so that the entry point itself only reads it
+    if (noalloc_scratch(ctx->device, &ctx->noalloc_base) != cudaSuccess) return bail(TPMG_ERR_CUDA);
     if (!build_host_grid(ctx->p, ctx->host, msg)) return bail(TPMG_ERR_INVALID_ARG);
     const int n_r = ctx->p.n_r;
     if (prof) {
@@ -1884,8 +2028,7 @@ tpmg_status tpmg_vcycle_noalloc(tpmg_ctx *ctx, const double *d_r, double *d_z)
     int dev = -1;
     CU(cudaGetDevice(&dev));
     if (dev != ctx->device) return fail(ctx, TPMG_ERR_INVALID_ARG, "the context's device must be current");
-    double *base = nullptr;
-    CU(noalloc_scratch(dev, &base));
+    double *const base = ctx->noalloc_base;   // looked up by tpmg_setup
     struct Saved { double *f, *u, *u2; } saved[16];   // n_levels <= 10
     size_t off = 0;
     for (int l = 0; l < L; ++l) {
@@ -2053,6 +2196,8 @@ tpmg_status tpmg_profile(tpmg_ctx *ctx, unsigned class_mask)
     t.mask = class_mask;
     std::fill(t.launches, t.launches + TPMG_K_COUNT, 0LL);
     std::fill(t.units, t.units + TPMG_K_COUNT, 0.0);
+    std::fill(t.bytes, t.bytes + TPMG_K_COUNT, 0.0);
+    std::fill(t.flops, t.flops + TPMG_K_COUNT, 0.0);
     t.used = 0;
     t.open = -1;
     if (class_mask) CU(grow_events(t, 8192));   // created here, outside any timed region
@@ -2078,6 +2223,25 @@ tpmg_status tpmg_profile_read(tpmg_ctx *ctx, int kernel_class, long long *launch
     if (total_ms) *total_ms = ms;
     if (units) *units = t.units[kernel_class];
     if (timed) *timed = n;
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_profile_work(tpmg_ctx *ctx, int kernel_class, double *bytes, double *timed_bytes, double *flops,
+                              double *timed_flops)
+{
+    if (!ctx || kernel_class < 0 || kernel_class >= TPMG_K_COUNT) return fail(ctx, TPMG_ERR_INVALID_ARG, "bad class");
+    CU(cudaStreamSynchronize(ctx->stream));
+    const Tracer &t = ctx->tr;
+    double b = 0.0, fl = 0.0;
+    for (size_t i = 0; i < t.used; ++i)
+        if (t.cls[i] == kernel_class) {
+            b += t.nb[i];
+            fl += t.nf[i];
+        }
+    if (bytes) *bytes = t.bytes[kernel_class];
+    if (timed_bytes) *timed_bytes = b;
+    if (flops) *flops = t.flops[kernel_class];
+    if (timed_flops) *timed_flops = fl;
     return TPMG_OK;
 }
 
@@ -2309,6 +2473,8 @@ tpmg_status tpmg_solve_learned(tpmg_ctx *ctx, const double *d_f, double *d_u, do
         for (int c = 0; c < TPMG_K_COUNT; ++c) {
             ctx->tr.launches[c] += lg.cls.init[c] + (long long)s.it * lg.cls.iter[c];
             ctx->tr.units[c] += lg.cls.uinit[c] + s.it * lg.cls.uiter[c];
+            ctx->tr.bytes[c] += lg.cls.binit[c] + s.it * lg.cls.biter[c];
+            ctx->tr.flops[c] += lg.cls.finit[c] + s.it * lg.cls.fiter[c];
         }
     it_learned = s.it;
     }

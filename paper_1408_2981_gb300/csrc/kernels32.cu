@@ -68,17 +68,25 @@ __global__ void k_thomas_factors32(int n_cells, const bf16x4 *__restrict__ cpack
 
 // One relaxation pass (eq. BlockJacobi) in FP32 with one warp per column T:
 //   u_T <- (1 - relax) u_T + relax A_T^{-1} (f_T + sum_e alphaS_hat_e u_{T_e}).
-// Row k of the column lives on lane k mod 32 (R = ceil(n_r / 32) rows per
-// lane), so that every load and store of the warp is one coalesced access of
-// 32 consecutive values.  The Thomas algorithm's two first-order recurrences
-// (factors of k_thomas_factors32),
+// The Thomas algorithm's two first-order recurrences (factors of
+// k_thomas_factors32),
 //   y_k = t_k + b_k y_{k-1},  t_k = d_k / p_k,     x_k = y_k + g_k x_{k+1},
-// are solved 32 rows at a time as parallel scans of the affine maps
-// y -> b y + t over the lanes (Kogge-Stone, 5 shuffle rounds), each segment
-// starting from the previous segment's last value: no shared memory and no
-// block barrier, and the warp never waits on a serial chain of n_r steps.
-// Slots are the relaxation tasks' cell lists ([task][16], padding -1), so a
-// colour pass covers slots [16 task0, 16 (task0 + n_tasks)).
+// are solved with parallel scans of the affine maps y -> b y + t over the
+// lanes (Kogge-Stone, 5 shuffle rounds), in one of two row layouts (R =
+// ceil(n_r / 32) rows per lane):
+// * R == 2 (33 to 64 levels): lane l holds the adjacent rows 2l and 2l + 1.
+//   Each recurrence is the lane's own step over its two rows with the prefix
+//   (suffix) product of their coefficients, one scan of the lanes' composite
+//   maps, and a fix-up of both rows by that product times the carry from the
+//   neighbouring lane;
+// * otherwise: row k lives on lane k mod 32, so that every load and store of
+//   the warp is one coalesced access of 32 consecutive values, and the column
+//   is scanned 32 rows at a time, each segment starting from the previous
+//   segment's last value.
+// Either way there is no shared memory and no block barrier, and the warp
+// never waits on a serial chain of n_r steps.  Slots are the relaxation
+// tasks' cell lists ([task][16], padding -1), so a colour pass covers slots
+// [16 task0, 16 (task0 + n_tasks)).
 template <int MODE, typename TF, int R>
 __global__ void __launch_bounds__(256)
     k_relax32_scan(const int *__restrict__ cells, const int4 *__restrict__ tnb, const bf16x4 *__restrict__ cpack,

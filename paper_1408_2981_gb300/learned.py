@@ -59,7 +59,8 @@ class SmoothFields:
         Y = np.stack([inputs.real_sph_harm(l, m, c) / (1.0 + l) ** decay
                       for l in range(l_max + 1) for m in range(-l, l + 1)], axis=1)
         V = np.stack([np.cos(n * math.pi * zmid / H) for n in range(n_max + 1)], axis=1)
-        vol = (r[1:] ** 3 - r[:-1] ** 3) / 3.0
+        dr = r[1:] - r[:-1]
+        vol = dr * (r[1:] ** 2 + r[1:] * r[:-1] + r[:-1] ** 2) / 3.0   # factored: r^3 differences cancel
         self.n_coef = Y.shape[1] * (n_max + 1)
         self.shape = (Y.shape[1], n_max + 1)
         self.Y = torch.from_numpy(Y).cuda()

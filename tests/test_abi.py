@@ -19,7 +19,7 @@ def lib():
 def declared_functions():
     txt = open(os.path.join(ROOT, "include", "tpmg.h")).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(tpmg_[a-z_]+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(tpmg_[a-z0-9_]+)\s*\(", txt)))
 
 
 def test_header_and_binding_agree():
@@ -79,7 +79,7 @@ def test_status_strings(lib):
 def declared_learned_functions():
     txt = open(os.path.join(ROOT, "include", "tpmg_learned.h")).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(tpmg_[a-z_]+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(tpmg_[a-z0-9_]+)\s*\(", txt)))
 
 
 def test_learned_header_and_binding_agree(lib):

@@ -65,3 +65,29 @@ def test_one_rank_needs_no_process_group():
     assert bench.max_over_ranks(3.5, 1) == 3.5
     value, t_ms = bench.aggregate_value(10.0, 2, 1, 4.0)
     assert t_ms == 4.0 and value == pytest.approx(10.0 * 2 / 0.004)
+
+
+def test_gpus_flag_starts_one_rank_per_gpu():
+    """bench.py --gpus N started without torchrun starts the N ranks itself."""
+    import json
+    import subprocess
+    import sys
+
+    import bench
+
+    cmd = bench.replica_command(["--gpus", "2"], 2, 12345)
+    assert cmd[1:4] == ["-m", "torch.distributed.run", "--nnodes=1"] and "--nproc-per-node=2" in cmd
+    assert cmd[cmd.index("--master-addr") + 1] == "127.0.0.1" and cmd[-2:] == ["--gpus", "2"]
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    res = subprocess.run([sys.executable, bench.__file__, "--gpus", "2", "--launcher-check"], capture_output=True,
+                         text=True, timeout=180, env=env)
+    assert res.returncode == 0, res.stderr
+    lines = [json.loads(l) for l in res.stdout.splitlines() if l.startswith("{")]
+    assert sorted((d["rank"], d["world"], d["local_rank"]) for d in lines) == [(0, 2, 0), (1, 2, 1)]
+
+
+def test_gpus_flag_must_match_the_world_size(monkeypatch):
+    import bench
+
+    monkeypatch.setenv("WORLD_SIZE", "3")
+    assert bench.main(["--gpus", "2", "--launcher-check"]) == 2

@@ -56,6 +56,47 @@ def test_batch_matches_individual_solves():
             assert torch.equal(u, u_ref), j
 
 
+def test_batch_problems_match_the_oracle():
+    """Batched solves against the CPU oracle directly (not only against the
+    library's own solves): an FP64 problem reaches the oracle's PCG solution to
+    the 1e-10 relative solution error of the FP64 parity tests, and a
+    mixed-precision problem takes the oracle's flexible-CG iterations with the
+    BF16 V-cycle (up to one at the stopping boundary) and, solved tightly,
+    reaches the FP64 oracle solution to 1e-9 in the energy norm."""
+    import oracle
+
+    oracle.build()
+    kw64, kwmx = PROBLEMS[1], PROBLEMS[3]
+    o64 = oracle.Oracle(**kw64)
+    omx = oracle.Oracle(**{k: v for k, v in kwmx.items() if k not in ("precision", "coeff_storage")})
+
+    def run(rtol):
+        solvers = [binding.Solver(**kw64), binding.Solver(**kwmx)]
+        fs = [rhs(s, 20 + j) for j, s in enumerate(solvers)]
+        us = [torch.zeros_like(f) for f in fs]
+        st, it, rel, sts, _ = binding.Batch(solvers, fs, us, rtol=rtol, max_iter=300).run()
+        torch.cuda.synchronize()
+        assert st == binding.TPMG_OK and np.all(sts == binding.TPMG_OK)
+        return [f.cpu().numpy() for f in fs], [u.cpu().numpy() for u in us], it
+
+    fs, us, it = run(1e-11)
+    r64 = o64.pcg(fs[0], rtol=1e-11, max_iter=300)
+    err64 = np.linalg.norm(us[0] - r64["u"]) / np.linalg.norm(r64["u"])
+    rmx = omx.pcg(fs[1], rtol=1e-11, max_iter=300)
+    e = us[1] - rmx["u"]
+    errmx = np.sqrt(max(e @ omx.apply(e), 0.0)) / np.sqrt(rmx["u"] @ omx.apply(rmx["u"]))
+    print(f"FP64 member: {it[0]} iterations (oracle {r64['iters']}), rel. solution error {err64:.2e}; "
+          f"mixed member: {it[1]} iterations (FP64 oracle {rmx['iters']}), energy-norm rel. error {errmx:.2e}")
+    assert err64 <= 1e-10, err64
+    assert errmx <= 1e-9, errmx
+
+    fs, us, it = run(1e-5)
+    omx.set_vcycle_bf16(True)
+    flex = omx.pcg(fs[1], rtol=1e-5, max_iter=100, flexible=True)
+    print(f"mixed member at 1e-5: {it[1]} iterations, oracle flexible CG with the BF16 V-cycle {flex['iters']}")
+    assert abs(int(it[1]) - flex["iters"]) <= 1
+
+
 def test_batch_reports_each_problem():
     solvers = [binding.Solver(**kw) for kw in PROBLEMS[:3]]
     fs = [rhs(s, j) for j, s in enumerate(solvers)]

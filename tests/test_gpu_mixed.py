@@ -109,6 +109,66 @@ def test_mixed_iterations_match_oracle_flexible_bf16(name):
     print(f"  max relative deviation of the residual history from the oracle's: {dev:.2e}")
 
 
+# Grids whose finest level has 81,920 columns (refinement 6): the size at which the
+# FP32 relaxation runs the finest level's passes in CTAs of several warps (as the
+# autotuner chooses there; 4 warps without it) on the FP64 right-hand side, one
+# column per warp.  n_r = 32 takes the one-row-per-lane layout, n_r = 64 the
+# two-rows-per-lane one.
+LARGE = {
+    "ref6_nr32_graded_c80": dict(refinement=6, n_levels=6, n_r=32, grading=1.05, courant_c=80.0),
+    "ref6_nr64_graded_c80": dict(refinement=6, n_levels=6, n_r=64, grading=1.05, courant_c=80.0),
+}
+_large_oracle = {}
+
+
+def large_oracle(name):
+    """The oracle and its BF16-coefficient V-cycle of the seeded residual (computed once)."""
+    if name not in _large_oracle:
+        o = oracle.Oracle(**LARGE[name])
+        o.set_vcycle_bf16(True)
+        r = inputs.uniform_pm1(inputs.SEED_UNIFORM_SMALL + 8, o.size())
+        _large_oracle[name] = (o, r, o.vcycle(r))
+    return _large_oracle[name]
+
+
+@pytest.mark.parametrize("autotune", [0, 1])
+@pytest.mark.parametrize("name", sorted(LARGE))
+def test_mixed_vcycle_vs_oracle_bf16_81920_columns(name, autotune):
+    o, r, zo = large_oracle(name)
+    s = binding.Solver(autotune=autotune, **MIXED, **LARGE[name])
+    assert s.N == r.size
+    z = torch.full((s.N,), float("nan"), dtype=torch.float64, device="cuda")
+    s.vcycle(cuda(r), z)
+    zg = host(z)
+    assert np.all(np.isfinite(zg))
+    rel = energy(o, zg - zo) / energy(o, zo)
+    finest = s.tuning()[-1][0]
+    print(f"{name} autotune={autotune} (finest-level variant {finest}): FP32 V-cycle vs BF16-coefficient oracle "
+          f"V-cycle, energy-norm rel. error {rel:.2e}")
+    assert rel <= 5e-3, rel
+
+
+def test_mixed_solve_reaches_fp64_solution_81920_columns():
+    """The mixed solve on the refinement-6 grid reaches the FP64 oracle's PCG
+    solution (1e-9 in the energy norm, as on the small grids)."""
+    name = "ref6_nr32_graded_c80"
+    o, _, _ = large_oracle(name)
+    o.set_vcycle_bf16(False)
+    try:
+        s = binding.Solver(**MIXED, **LARGE[name])
+        f = inputs.uniform_pm1(inputs.SEED_UNIFORM_SMALL + 1, s.N)
+        u = torch.zeros(s.N, dtype=torch.float64, device="cuda")
+        st, it, rel, _ = s.solve(cuda(f), u, rtol=1e-11, max_iter=300)
+        ro = o.pcg(f, rtol=1e-11, max_iter=300)
+    finally:
+        o.set_vcycle_bf16(True)
+    assert st == binding.TPMG_OK and ro["status"] == 0
+    ug = host(u)
+    err_a = energy(o, ug - ro["u"]) / energy(o, ro["u"])
+    print(f"{name}: mixed {it} iterations, FP64 oracle {ro['iters']}; energy-norm rel. error {err_a:.2e}")
+    assert err_a <= 1e-9, err_a
+
+
 def test_mixed_rejects_factorised_storage():
     with pytest.raises(binding.TPMGError):
         binding.Solver(precision=binding.TPMG_PREC_MIXED, coeff_storage=binding.TPMG_COEFF_FACTORISED, **CASES["ref0_nr1_single_level"])

@@ -5,11 +5,12 @@ device memory once their own run has started: a host model that owns the
 device through its own memory pool, or code that cannot afford the device
 synchronisation a cudaMalloc / cudaFree may cause.  It takes the coarse-level
 work vectors from a fixed device array built into the library instead.  Its
-result must be the V-cycle of tpmg_vcycle.  The check uses the V-cycle
-tolerance of the parity tests: 1e-11 relative in the energy norm and 1e-7 in
-the 2-norm.  Two calls in a row, with different right-hand sides and a second
-context sharing the array, show that values left in the array by a previous
-call do not leak into the next result.
+result must be the V-cycle of tpmg_vcycle bit for bit: both launch the same
+kernels in the same order on the same data, and only the addresses of the
+work vectors differ, so any difference would be a wrong offset into the
+array or a value left over from an earlier call.  Two calls in a row, with
+different right-hand sides and a second context sharing the array, show that
+values left in the array by a previous call do not leak into the next result.
 
 This file is collected last on purpose, so a run that stops at its first
 failure has already run every other test.
@@ -44,11 +45,12 @@ def energy_rel(s, e, z):
     return (torch.dot(e, ae).abs().sqrt() / torch.dot(z, az).sqrt()).item()
 
 
-def check_close(s, z_new, z_ref):
+def check_equal(s, z_new, z_ref):
     assert torch.isfinite(z_new).all()
-    e = z_new - z_ref
-    assert energy_rel(s, e, z_ref) <= 1e-11
-    assert torch.linalg.norm(e).item() <= 1e-7 * torch.linalg.norm(z_ref).item()
+    if not torch.equal(z_new, z_ref):
+        e = z_new - z_ref
+        pytest.fail(f"fixed-scratch V-cycle differs from tpmg_vcycle: energy-norm rel. {energy_rel(s, e, z_ref):.3e}, "
+                    f"2-norm rel. {(torch.linalg.norm(e) / torch.linalg.norm(z_ref)).item():.3e}")
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
@@ -67,12 +69,12 @@ def test_vcycle_noalloc_matches_vcycle_twice(name):
         z_other = torch.empty_like(r_other)
         other.vcycle_noalloc(r_other, z_other)
         torch.cuda.synchronize()
-        check_close(s, z_new, z_ref)
+        check_equal(s, z_new, z_ref)
         assert torch.equal(r, r_copy)   # the input is not modified
     z_o_ref = torch.empty_like(r_other)
     other.vcycle(r_other, z_o_ref)
     torch.cuda.synchronize()
-    check_close(other, z_other, z_o_ref)
+    check_equal(other, z_other, z_o_ref)
 
 
 def test_vcycle_noalloc_rejects_problems_beyond_the_array():
