@@ -536,6 +536,7 @@ def run_tpmg(args, wl):
         cpu = {"value": v_o, "unit": "unknowns/s", "cores": 1, "kind": "oracle", "sample": sample, "cpu": cpu_model()}
         cpu_threads = time_oracle_threads(wl, args.rtol, iters[-1])
     extra = None
+    tuning = [["warp", "cta64", "cta128", "cta256"][v] if v >= 0 else "heuristic" for v, _ in s.tuning()]
     if rank == 0 and world == 1 and not args.no_extra_configs and args.workload == "81920x64":
         s.close()
         extra = run_extra_configs(args, stream, flush)
@@ -546,8 +547,7 @@ def run_tpmg(args, wl):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
                 "config": {"workload": wl["text"], "n_unknowns": N, "parallelism": f"replicas{world}",
                            "l2": "flushed between steps (write of 2x L2 outside the timed events)",
-                           "relax_kernel_per_level": [["warp", "cta64", "cta128", "cta256"][v] if v >= 0 else "heuristic"
-                                                      for v, _ in s.tuning()]},
+                           "relax_kernel_per_level": tuning},
                 "e2e": {"value": e2e_value, "unit": "unknowns/s", "h2d_bytes_per_step": 2 * 8 * N,
                         "d2h_bytes_per_step": 8 * N},
                 "gpu_launches": gpu_launches, "roofline": roof, "hbm": hbm, "cpu_baseline": cpu,

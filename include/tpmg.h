@@ -145,12 +145,16 @@ typedef struct {
                             levels above scan_max_cells (16-column twisted tasks) is launched
                             plainly, where programmatic launch measured slower.  0: plain
                             launches.  The results are identical. */
+    int    relax_variant;/* -1: the autotuner's (or the heuristic's) relaxation kernel per level;
+                            0..4 (mixed precision 0..3): that variant of tpmg_query_tuning on every
+                            level, where it applies.  The results are identical. */
 } tpmg_params;
 
 /* Fills *p with the defaults: refinement 3, n_levels 4, n_r 16, H = 10/6371,
  * grading 1, omega2 0 with courant_c 8, nu 2/2/1, block-SOR with relax 1,
  * factorised storage, circumcentres, FP64, graphs and autotuning on,
- * scan_max_cells 5120, outer CG, constant prolongation.  Returns TPMG_ERR_INVALID_ARG if p is NULL. */
+ * scan_max_cells 5120, outer CG, constant prolongation, programmatic launch, relax_variant -1.
+ * Returns TPMG_ERR_INVALID_ARG if p is NULL. */
 tpmg_status tpmg_default_params(tpmg_params *p);
 
 /* Factorised profiles (Sec. 2, eq. profiles): alpha_r(r, x) = alpha_r^r(r) alpha_r^S(x),
@@ -285,18 +289,36 @@ tpmg_status tpmg_solve(tpmg_ctx *ctx, const double *d_f, double *d_u, double rto
 tpmg_status tpmg_solve_host(tpmg_ctx *ctx, const double *h_f, double *h_u, double rtol, int max_iter,
                             int *iters, double *rel_resid, double *resid_hist);
 
-/* Many independent solves in one graph launch (the batched form).  A batch
- * holds one PCG solve (tpmg_solve's algorithm and arithmetic, rtol, max_iter)
- * for each of n contexts -- of any sizes and parameters, on the current
- * device -- with the loop of each solve on the device: the whole batch is a
- * single CUDA graph in which every problem is an independent branch, so the
- * problems' kernels overlap.  d_f[i], d_u[i]: device vectors of ctxs[i] as in
+/* Many independent solves in one graph launch (the batched form, Sec. 5's
+ * method applied to many problems at once; the paper has no batching layer).
+ * A batch holds one PCG solve (tpmg_solve's algorithm and arithmetic, rtol,
+ * max_iter) for each of n (context, right-hand side) pairs -- of any sizes and
+ * parameters, on the current device -- with the loop of every solve on the
+ * device, in one CUDA graph.  d_f[i], d_u[i]: device vectors of ctxs[i] as in
  * tpmg_solve (d_u[i] = initial guess, overwritten by the solution); the
  * pointers are baked into the batch, which stays valid while the contexts and
- * vectors live.  A context may belong to one batch and must not run another
- * solve while its batch runs.  max_iter < 4096.
- * Errors: INVALID_ARG (NULL, repeated context, other device, a context with
- * vertical advection or linear prolongation), OOM, CUDA. */
+ * vectors live.  Every problem's solution, iterations and residuals are those
+ * of its own tpmg_solve, bit for bit.  max_iter < 4096.  Two forms:
+ *   TPMG_BATCH_WORKLIST, built when every context is a mixed-precision CG
+ *   context with constant prolongation, no vertical advection, the factorised
+ *   outer operator (no tpmg_set_outer_profiles) and nu_pre, nu_post,
+ *   nu_coarse >= 1: the members' V-cycles are merged into one schedule of
+ *   steps (aligned at the coarsest level: the same phase, level counted from
+ *   the coarsest, and pass of that level), and each step is one launch per
+ *   kernel class whose work list holds that step's pass of every member (a
+ *   member, its level, colour and column range); the outer FP64 kernels run
+ *   every member's blocks in one launch each.  A context may appear several
+ *   times (several right-hand sides on one operator): its grid, stencil and
+ *   factors are shared and the batch allocates each member's work vectors
+ *   (about 48 bytes per unknown).  The relaxation launches' CTA shapes (1, 2,
+ *   4 or 8 warps) are timed at creation and the fastest kept (same arithmetic).
+ *   TPMG_BATCH_BRANCHES otherwise: each problem is an independent branch of
+ *   the graph (the contexts' own device-side solves); a context may appear
+ *   once, and must not run another solve while its batch runs.
+ * Errors: INVALID_ARG (NULL, a repeated context outside the work-list form,
+ * aliased vectors, other device, a context with vertical advection or linear
+ * prolongation), OOM, CUDA. */
+enum { TPMG_BATCH_BRANCHES = 0, TPMG_BATCH_WORKLIST = 1 };
 typedef struct tpmg_batch tpmg_batch;
 tpmg_status tpmg_batch_create(tpmg_ctx *const *ctxs, int n, const double *const *d_f, double *const *d_u,
                               double rtol, int max_iter, tpmg_batch **out);
@@ -308,6 +330,9 @@ tpmg_status tpmg_batch_create(tpmg_ctx *const *ctxs, int n, const double *const 
 tpmg_status tpmg_batch_run(tpmg_batch *b, void *cuda_stream, int *iters, double *rel_resid, int *status,
                            long long *kernel_launches);
 
+/* The form tpmg_batch_create built (TPMG_BATCH_*), or -1 for NULL. */
+int tpmg_batch_form(const tpmg_batch *b);
+
 /* Releases the batch (not the contexts).  NULL is ignored. */
 void tpmg_batch_destroy(tpmg_batch *b);
 
@@ -318,9 +343,11 @@ tpmg_status tpmg_query(const tpmg_ctx *ctx, int level, int *n_cells, int *n_r, d
 
 /* The autotuner's choice on multigrid level `level`: variant = relaxation kernel
  * (FP64: 0 one warp per 16-column task, 1/2/3 one CTA of 64/128/256 threads per
- * task; mixed precision: one warp per column in CTAs of 1/2/4/8 warps; -1
- * heuristic: not tuned) and us[4] = measured microseconds of the level's
- * largest colour pass with each variant.  Any output may be NULL.
+ * task, 4 warp-specialised CTAs -- two warps gathering the next task while one
+ * solves the current one -- over strided tasks; mixed precision: one warp per
+ * column in CTAs of 1/2/4/8 warps; -1 heuristic: not tuned) and us[5] =
+ * measured microseconds of the level's largest colour pass with each variant
+ * (us[4] = 0 in mixed precision).  Any output may be NULL.
  * Errors: INVALID_ARG. */
 tpmg_status tpmg_query_tuning(const tpmg_ctx *ctx, int level, int *variant, float *us);
 

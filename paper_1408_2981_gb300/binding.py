@@ -46,7 +46,10 @@ EXPORTS = ["tpmg_default_params", "tpmg_setup", "tpmg_setup_profiles", "tpmg_set
            "tpmg_solve_host", "tpmg_query", "tpmg_query_tuning", "tpmg_export_mesh", "tpmg_profile", "tpmg_profile_read",
            "tpmg_profile_work", "tpmg_fp64_peak",
            "tpmg_status_string", "tpmg_last_error", "tpmg_destroy", "tpmg_batch_create", "tpmg_batch_run",
-           "tpmg_batch_destroy"]
+           "tpmg_batch_form", "tpmg_batch_destroy"]
+
+TPMG_BATCH_BRANCHES = 0
+TPMG_BATCH_WORKLIST = 1
 
 # every entry point declared in include/tpmg_learned.h
 EXPORTS_LEARNED = ["tpmg_net_create", "tpmg_net_n_params", "tpmg_net_set_params", "tpmg_net_get_params",
@@ -72,7 +75,8 @@ class tpmg_params(ctypes.Structure):
                 ("nu_coarse", ctypes.c_int), ("smoother", ctypes.c_int), ("relax", ctypes.c_double),
                 ("coeff_storage", ctypes.c_int), ("centre", ctypes.c_int), ("precision", ctypes.c_int),
                 ("graphs", ctypes.c_int), ("autotune", ctypes.c_int), ("scan_max_cells", ctypes.c_int),
-                ("outer", ctypes.c_int), ("prolongation", ctypes.c_int), ("pdl", ctypes.c_int)]
+                ("outer", ctypes.c_int), ("prolongation", ctypes.c_int), ("pdl", ctypes.c_int),
+                ("relax_variant", ctypes.c_int)]
 
 
 class tpmg_profiles(ctypes.Structure):
@@ -126,6 +130,8 @@ def load(path: str | None = None):
     lib.tpmg_destroy.restype = None
     lib.tpmg_batch_create.argtypes = [P, I, P, P, D, I, ctypes.POINTER(P)]
     lib.tpmg_batch_run.argtypes = [P, P, P, P, P, ctypes.POINTER(ctypes.c_longlong)]
+    lib.tpmg_batch_form.argtypes = [P]
+    lib.tpmg_batch_form.restype = I
     lib.tpmg_batch_destroy.argtypes = [P]
     lib.tpmg_batch_destroy.restype = None
     L, F, LL = ctypes.c_long, ctypes.c_float, ctypes.c_longlong
@@ -273,7 +279,7 @@ class Solver:
         out = []
         for level in range(self.n_levels):
             v = ctypes.c_int()
-            us = np.zeros(4, dtype=np.float32)
+            us = np.zeros(5, dtype=np.float32)
             st = self._lib.tpmg_query_tuning(self._h, level, ctypes.byref(v), us.ctypes.data)
             if st != TPMG_OK:
                 raise TPMGError(st, "tpmg_query_tuning")
@@ -550,11 +556,14 @@ class Net:
 
 
 class Batch:
-    """tpmg_batch: one PCG solve per Solver in one graph launch.
+    """tpmg_batch: one PCG solve per (Solver, right-hand side) in one graph launch.
 
     ``solvers``, ``fs``, ``us``: equal-length lists; fs[i], us[i] are float64 CUDA
     tensors of solvers[i] (us[i] = initial guess, overwritten by the solution).
-    The tensors must stay alive while the batch is used.
+    A Solver may appear several times (several right-hand sides on one operator)
+    when the batch takes the work-list form (``form == "worklist"``: every Solver
+    mixed precision with the defaults of the CG path).  The tensors must stay
+    alive while the batch is used.
     """
 
     def __init__(self, solvers, fs, us, rtol: float = 1e-5, max_iter: int = 100):
@@ -572,7 +581,7 @@ class Batch:
         if st != TPMG_OK:
             raise TPMGError(st, "tpmg_batch_create")
         self._h = h
-        self.form = "branches"
+        self.form = {TPMG_BATCH_BRANCHES: "branches", TPMG_BATCH_WORKLIST: "worklist"}[self._lib.tpmg_batch_form(h)]
 
     def run(self, stream=None):
         """Returns (status, iters[n], rel_resid[n], status[n], kernel_launches)."""

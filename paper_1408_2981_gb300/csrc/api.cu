@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstdint>
@@ -120,6 +122,9 @@ struct tpmg_ctx {
     long N = 0;                   // fine-level unknowns
     // PCG vectors (fine level)
     double *r = nullptr, *z = nullptr, *pv = nullptr, *q = nullptr;
+    // mixed precision: r in FP32, written by every kernel that writes r (initial residual,
+    // axpy, the learned solve's judge), read by the finest level of the V-cycle of r
+    float *r32 = nullptr;
     double *hf = nullptr, *hu = nullptr;   // device staging for tpmg_solve_host
     double *partials = nullptr;
     int n_part = 0;
@@ -130,12 +135,38 @@ struct tpmg_ctx {
     std::string err;
 };
 
+// One launch of the work-list form's schedule: a kernel class and its items.
+struct BatchLaunch {
+    int kind = 0;            // 0 relaxation, 1 residual + restriction
+    int mode = 0;            // PASS_* (relaxation)
+    bool f64 = false;        // right-hand side in FP64 (a member's finest level)
+    int n_r_max = 0;         // rows-per-lane class of the items' columns
+    int args = 0;            // index of the launch's work list (tpmg_batch::rargs or cargs)
+    int count = 0;           // its items
+    long total = 0;          // warps (relaxation) or positions (restriction) of the launch
+    int wpb = 4;             // warps per CTA of a relaxation launch (tuned)
+    float us[4] = {};        // tuner timings for 1 / 2 / 4 / 8 warps per CTA
+};
+
 struct tpmg_batch {
     std::vector<tpmg_ctx *> ctx;
     std::vector<long long> init_launches, iter_launches;   // per problem
     double rtol = 0.0;
     int max_iter = 0;
     cudaGraphExec_t exec = nullptr;
+    // work-list form (TPMG_BATCH_WORKLIST): one graph whose launches each cover one step
+    // of every member's V-cycle or outer iteration; members may share a context
+    int form = TPMG_BATCH_BRANCHES;
+    int n_part = 0;
+    BatchMemberDev *d_mem = nullptr;       // [M]
+    int *d_active = nullptr, *d_go = nullptr;   // [M]
+    Scalars *h_sc = nullptr;                // [M] pinned host mirror of the members' scalars
+    std::vector<Scalars *> d_sc;            // [M] device
+    std::vector<BatchLaunch> launches;      // the V-cycle's launches in order
+    std::vector<RelaxBatchArgs> rargs;      // their work lists (kernel parameters)
+    std::vector<RestrictBatchArgs> cargs;
+    long long wl_init = 0, wl_iter = 0;     // launches of the initial part and of one iteration
+    std::vector<void *> allocs;             // device allocations of the work-list form
 };
 
 namespace {
@@ -202,6 +233,11 @@ bool validate(const tpmg_params *p, std::string &msg)
         msg = "unknown prolongation"; return false;
     }
     if (p->pdl != 0 && p->pdl != 1) { msg = "pdl must be 0 or 1"; return false; }
+    if (p->relax_variant < -1 ||
+        p->relax_variant >= (p->precision == TPMG_PREC_MIXED ? kRelaxVariants32 : (int)RELAX_VARIANTS)) {
+        msg = "relax_variant must be -1 or a relaxation kernel variant";
+        return false;
+    }
     return true;
 }
 
@@ -436,11 +472,12 @@ cudaError_t residual_probed(tpmg_ctx *ctx, const Launch &L, const double *f, con
 {
     const LevelDev &fl = ctx->lv.back();
     const long N = ctx->N;
+    float *const r32 = r == ctx->r ? ctx->r32 : nullptr;   // the context's r keeps its FP32 copy in step
     cudaError_t e = run_w(ctx, TPMG_K_RESIDUAL, (double)N, Alg{8.0 * N, 0.0},   // the probe reads u
                           [&] { return launch_nonzero(L, N, u, ctx->zflags, ctx->n_part); });
     if (e != cudaSuccess) return e;
-    return run(ctx, TPMG_K_RESIDUAL, (double)N, [&] {
-        return launch_residual(L, fl, ctx->vert, f, u, r, ctx->partials, ctx->n_part, ctx->zflags);
+    return run_b(ctx, TPMG_K_RESIDUAL, (double)N, (r32 ? 28.0 : 24.0) * N, [&] {
+        return launch_residual(L, fl, ctx->vert, f, u, r, ctx->partials, ctx->n_part, ctx->zflags, r32);
     });
 }
 
@@ -654,7 +691,7 @@ tpmg_status vcycle_mixed(tpmg_ctx *ctx, int l, const TF *f, float *u, float *scr
     if (l == 0) {
         if constexpr (std::is_same<TF, float>::value) {
             // recording of the coarsest-level right-hand sides (training data of the learned form)
-            if (ctx->rec && !ctx->capturing && ctx->rec_n < ctx->rec_cap) {
+            if (ctx->rec && !ctx->capturing && ctx->rec_n < ctx->rec_cap && ctx->p.n_levels > 1) {
                 double *dst = ctx->rec + (size_t)ctx->rec_n * lv.n * p.n_r;
                 LCHK(run_b(ctx, TPMG_K_COPY, nunits, 12.0 * nunits,
                            [&] { return launch_to_f64(L, (long)lv.n * p.n_r, f, dst); }));
@@ -663,7 +700,7 @@ tpmg_status vcycle_mixed(tpmg_ctx *ctx, int l, const TF *f, float *u, float *scr
             // learned form: the network's prediction and one block-Jacobi line
             // relaxation from it replace the coarsest-level solve; the relaxation
             // pass adds the result into u_fine (prolongation)
-            if (ctx->net_coarse_on) {
+            if (ctx->net_coarse_on && ctx->p.n_levels > 1) {
                 tpmg_status st = net_infer<float, float>(ctx, TPMG_NET_COARSE, lv, f, scratch);
                 if (st != TPMG_OK) return st;
                 LCHK(run_w(ctx, TPMG_K_RELAX, nunits, alg_relax32(nunits, PASS_NORMAL, false, false, fuse != nullptr), [&] {
@@ -737,7 +774,12 @@ tpmg_status vcycle_fine(tpmg_ctx *ctx, const double *r, double *z)
 {
     const int l = ctx->p.n_levels - 1;
     LevelDev &fl = ctx->lv[l];
-    if (ctx->p.precision == TPMG_PREC_MIXED) return vcycle_mixed<double>(ctx, l, r, fl.u32, fl.u2_32, nullptr, z);
+    if (ctx->p.precision == TPMG_PREC_MIXED) {
+        // the V-cycle of the context's own residual reads its FP32 copy: the same values
+        // the passes would round r to, in half the bytes
+        if (r == ctx->r && ctx->r32) return vcycle_mixed<float>(ctx, l, ctx->r32, fl.u32, fl.u2_32, nullptr, z);
+        return vcycle_mixed<double>(ctx, l, r, fl.u32, fl.u2_32, nullptr, z);
+    }
     return vcycle_level(ctx, l, r, z, fl.u2, nullptr);
 }
 
@@ -888,7 +930,7 @@ tpmg_status append_solve(tpmg_ctx *ctx, cudaGraph_t g, const double *f, double *
         if (learned) {
             LCHK(run(ctx, TPMG_K_DOT, (double)N, [&] { return launch_dot(L, N, f, f, ctx->partials + np, np); }));
             LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_LOOP_RR0F, ctx->partials, np, ctx->sc, &loop); }));
-            LCHK(run(ctx, TPMG_K_COPY, (double)N, [&] { return launch_judge_reset(L, ctx->sc, N, f, u, ctx->r); }));
+            LCHK(run(ctx, TPMG_K_COPY, (double)N, [&] { return launch_judge_reset(L, ctx->sc, N, f, u, ctx->r, ctx->r32); }));
         } else {
             LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_LOOP_RR0, ctx->partials, np, ctx->sc, &loop); }));
         }
@@ -928,8 +970,11 @@ tpmg_status append_solve(tpmg_ctx *ctx, cudaGraph_t g, const double *f, double *
         LCHK(run(ctx, TPMG_K_APPLY, (double)N, [&] { return launch_apply(L, fl, ctx->vert, ctx->pv, ctx->q, ctx->partials, np); }));
         LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_ALPHA, ctx->partials, np, ctx->sc); }));
         const double *z_old = flexible ? ctx->z : nullptr;
-        LCHK(run_w(ctx, TPMG_K_AXPY, (double)N, Alg{(z_old ? 56.0 : 48.0) * N, (z_old ? 8.0 : 6.0) * N},
-                   [&] { return launch_axpy_pair(L, N, ctx->sc, ctx->pv, ctx->q, u, ctx->r, ctx->partials, np, z_old); }));
+        LCHK(run_w(ctx, TPMG_K_AXPY, (double)N,
+                   Alg{((z_old ? 56.0 : 48.0) + (ctx->r32 ? 4.0 : 0.0)) * N, (z_old ? 8.0 : 6.0) * N}, [&] {
+                       return launch_axpy_pair(L, N, ctx->sc, ctx->pv, ctx->q, u, ctx->r, ctx->partials, np, z_old,
+                                               ctx->r32);
+                   }));
         LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_LOOP_RR, ctx->partials, np, ctx->sc, &loop); }));
         if (flexible)
             LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_RZC, ctx->partials + np, np, ctx->sc); }));
@@ -1149,7 +1194,7 @@ tpmg_status pcg(tpmg_ctx *ctx, const double *f, double *u, double rtol, int max_
     if (learned) {
         LCHK(run(ctx, TPMG_K_DOT, (double)N, [&] { return launch_dot(L, N, f, f, ctx->partials + np, np); }));
         LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_RR0F, ctx->partials, np, ctx->sc); }));
-        LCHK(run(ctx, TPMG_K_COPY, (double)N, [&] { return launch_judge_reset(L, ctx->sc, N, f, u, ctx->r); }));
+        LCHK(run(ctx, TPMG_K_COPY, (double)N, [&] { return launch_judge_reset(L, ctx->sc, N, f, u, ctx->r, ctx->r32); }));
     } else {
         LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_RR0, ctx->partials, np, ctx->sc); }));
     }
@@ -1179,8 +1224,11 @@ tpmg_status pcg(tpmg_ctx *ctx, const double *f, double *u, double rtol, int max_
         LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_ALPHA, ctx->partials, np, ctx->sc); }));
         // flexible CG (mixed precision): the axpy also forms <r_new, z_old>
         const double *z_old = flexible ? ctx->z : nullptr;
-        LCHK(run_w(ctx, TPMG_K_AXPY, (double)N, Alg{(z_old ? 56.0 : 48.0) * N, (z_old ? 8.0 : 6.0) * N},
-                   [&] { return launch_axpy_pair(L, N, ctx->sc, ctx->pv, ctx->q, u, ctx->r, ctx->partials, np, z_old); }));
+        LCHK(run_w(ctx, TPMG_K_AXPY, (double)N,
+                   Alg{((z_old ? 56.0 : 48.0) + (ctx->r32 ? 4.0 : 0.0)) * N, (z_old ? 8.0 : 6.0) * N}, [&] {
+                       return launch_axpy_pair(L, N, ctx->sc, ctx->pv, ctx->q, u, ctx->r, ctx->partials, np, z_old,
+                                               ctx->r32);
+                   }));
         LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_RR, ctx->partials, np, ctx->sc); }));
         if (flexible) LCHK(run(ctx, TPMG_K_FINISH, 1.0, [&] { return launch_finish(L, FIN_RZC, ctx->partials + np, np, ctx->sc); }));
         if ((st = read_scalars(ctx)) != TPMG_OK) return st;
@@ -1362,6 +1410,8 @@ tpmg_status upload_advection(tpmg_ctx *ctx, const HostLevel &H, LevelDev &D, con
         for (int T = 0; T < H.n; ++T)
             for (int k = 0; k < p.n_r; ++k) xb[(size_t)T * p.n_r + k] = bf16_bits(x[(size_t)T * (p.n_r + 1) + k]);
         if (!D.cxv) CU(dalloc(ctx, &D.cxv, nn));
+        if (!D.fb32) CU(dalloc(ctx, &D.fb32, nn));   // the column blocks' multipliers, stored with advection
+        if (!D.fc32) CU(dalloc(ctx, &D.fc32, nn));
         CU(cudaMemcpyAsync(D.cxv, xb.data(), nn * sizeof(unsigned short), cudaMemcpyHostToDevice, ctx->stream));
         CU(cudaStreamSynchronize(ctx->stream));
         D.cxv_on = true;
@@ -1540,10 +1590,9 @@ tpmg_status upload_level(tpmg_ctx *ctx, int l)
         std::vector<unsigned short> cv;
         bf16_stencil(ctx, H, nullptr, nullptr, nullptr, cp, cv);
         CU(dalloc(ctx, &D.cpack, nn));
-        CU(dalloc(ctx, &D.cvert, nn));
+        CU(dalloc(ctx, &D.cvert, nn + 1));   // + a zero coupling after the last column (face n_r)
+        CU(cudaMemsetAsync(D.cvert + nn, 0, sizeof(unsigned short), ctx->stream));
         CU(dalloc(ctx, &D.rinv32, nn));
-        CU(dalloc(ctx, &D.fb32, nn));
-        CU(dalloc(ctx, &D.fc32, nn));
         CU(dalloc(ctx, &D.u32, nn));
         CU(dalloc(ctx, &D.u2_32, nn));
         if (l < p.n_levels - 1) CU(dalloc(ctx, &D.f32, nn));
@@ -1668,7 +1717,7 @@ tpmg_status autotune(tpmg_ctx *ctx)
         };
         float best = 0.f;
         int best_var = RELAX_CTA128;
-        for (int var = 0; var < RELAX_VARIANTS && st == TPMG_OK; ++var) {
+        for (int var = 0; var < (mixed ? kRelaxVariants32 : RELAX_VARIANTS) && st == TPMG_OK; ++var) {
             D.relax_variant = var;
             cudaError_t e = pass();
             if (e == cudaSuccess) e = cudaEventRecord(a, ctx->stream);
@@ -1688,6 +1737,422 @@ tpmg_status autotune(tpmg_ctx *ctx)
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
+    return st;
+}
+
+// ---- the work-list form of the batch ------------------------------------------
+
+// One step of a member's mixed-precision V-cycle, generated in the order vcycle_mixed
+// issues it.  Buffers of a level: 0 = u32, 1 = u2_32 (block Jacobi's second buffer).
+struct VOp {
+    int kind = 0;            // 0 relaxation pass, 1 residual + restriction (lvl -> lvl - 1)
+    int phase = 0;           // 0 pre-smoothing (and restriction), 1 coarsest level, 2 post-smoothing
+    int lvl = 0;             // multigrid level, 0 = coarsest
+    int idx = 0;             // position among the same (phase, lvl, kind)
+    int mode = PASS_NORMAL, task0 = 0, n_tasks = 0;
+    int uin = 0, uout = 0;   // relaxation: buffers read and written; restriction: uin = the iterate
+    int fine_buf = -1;       // fused prolongation into this buffer of level lvl + 1, or none
+    bool out64 = false;      // writes the member's FP64 result z
+};
+
+// The member's V-cycle (Algorithm 1, mixed precision, P = R^T fused), as vcycle_mixed.
+void member_ops(const tpmg_ctx *ctx, int l, bool finest, int fine_cur, std::vector<VOp> &ops)
+{
+    const tpmg_params &p = ctx->p;
+    const LevelDev &lv = ctx->lv[l];
+    const int C = lv.n_colours;
+    const bool jac = p.smoother == TPMG_SMOOTH_JACOBI;
+    const int fuse = finest ? -1 : fine_cur;
+    int cur = 0, oth = 1;
+    int counter[3] = {0, 0, 0};
+    auto relax = [&](int phase, int mode, int c, int in, int out, int fine, bool o64) {
+        VOp o;
+        o.kind = 0;
+        o.phase = phase;
+        o.lvl = l;
+        o.idx = counter[phase]++;
+        o.mode = mode;
+        if (c < 0) {
+            o.task0 = 0;
+            o.n_tasks = lv.n_tasks;
+        } else {
+            o.task0 = lv.colour_task_off[c];
+            o.n_tasks = lv.colour_task_off[c + 1] - o.task0;
+        }
+        o.uin = in;
+        o.uout = out;
+        o.fine_buf = fine;
+        o.out64 = o64;
+        if (o.n_tasks > 0) ops.push_back(o);
+    };
+    auto colour_mode = [](int sweep, int c) { return sweep == 0 ? (c == 0 ? PASS_RHS_ONLY : PASS_ZERO) : PASS_NORMAL; };
+    if (l == 0) {
+        for (int s = 0; s < p.nu_coarse; ++s) {
+            const bool last = s == p.nu_coarse - 1;
+            if (jac) {
+                relax(1, s == 0 ? PASS_RHS_ONLY : PASS_NORMAL, -1, cur, oth, last ? fuse : -1, last && finest);
+                std::swap(cur, oth);
+                continue;
+            }
+            for (int c = 0; c < C; ++c) {
+                const bool fin = last && c == C - 1;
+                relax(1, colour_mode(s, c), c, 0, 0, fin ? fuse : -1, fin && finest);
+            }
+            for (int c = C - 2; c >= 0; --c) relax(1, PASS_NORMAL, c, 0, 0, last ? fuse : -1, last && finest);
+        }
+        return;
+    }
+    for (int s = 0; s < p.nu_pre; ++s) {
+        if (jac) {
+            relax(0, s == 0 ? PASS_RHS_ONLY : PASS_NORMAL, -1, cur, oth, -1, false);
+            std::swap(cur, oth);
+            continue;
+        }
+        for (int c = 0; c < C; ++c) relax(0, colour_mode(s, c), c, 0, 0, -1, false);
+    }
+    VOp r;
+    r.kind = 1;
+    r.phase = 0;
+    r.lvl = l;
+    r.uin = cur;
+    ops.push_back(r);
+    member_ops(ctx, l - 1, false, cur, ops);
+    for (int s = 0; s < p.nu_post; ++s) {
+        const bool last = s == p.nu_post - 1;
+        if (jac) {
+            relax(2, PASS_NORMAL, -1, cur, oth, last ? fuse : -1, last && finest);
+            std::swap(cur, oth);
+            continue;
+        }
+        for (int c = C - 1; c >= 0; --c) relax(2, PASS_NORMAL, c, 0, 0, last ? fuse : -1, last && finest);
+    }
+}
+
+// Position of an op in the merged schedule: pre-smoothing and restriction from the
+// finest level down, the coarsest level, post-smoothing from the coarsest level up;
+// levels are counted from the coarsest, so that the members' small coarse passes
+// fall into the same steps.  Every member's own order is kept.
+std::array<int, 4> op_key(const VOp &o)
+{
+    if (o.phase == 0) return {0, -o.lvl, o.kind, o.idx};
+    if (o.phase == 1) return {1, 0, 0, o.idx};
+    return {2, o.lvl, 0, o.idx};
+}
+
+int rows_class(int n_r)
+{
+    int c = 32;
+    while (c < n_r && c < 1024) c *= 2;
+    return c;
+}
+
+bool worklist_member_ok(const tpmg_ctx *c)
+{
+    const tpmg_params &p = c->p;
+    return p.precision == TPMG_PREC_MIXED && p.outer == TPMG_OUTER_CG && p.prolongation == TPMG_PROLONG_CONSTANT &&
+           !has_advection(c) && !c->lv.back().cfull && p.nu_pre >= 1 && p.nu_post >= 1 && p.nu_coarse >= 1;
+}
+
+template <typename T>
+cudaError_t balloc(tpmg_batch *b, T **ptr, size_t count)
+{
+    void *q = nullptr;
+    const cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) return e;
+    b->allocs.push_back(q);
+    *ptr = static_cast<T *>(q);
+    return cudaSuccess;
+}
+
+// The batch's V-cycle for every active member: the schedule's launches in order.
+cudaError_t batch_vcycle(const tpmg_batch *b, const Launch &L)
+{
+    for (const BatchLaunch &bl : b->launches) {
+        cudaError_t e;
+        if (bl.kind == 0) {
+            const RelaxBatchArgs &a = b->rargs[bl.args];
+            e = bl.f64 ? launch_relax32_batch<double>(L, bl.mode, bl.n_r_max, a, bl.total, bl.wpb, b->d_active)
+                       : launch_relax32_batch<float>(L, bl.mode, bl.n_r_max, a, bl.total, bl.wpb, b->d_active);
+        } else {
+            const RestrictBatchArgs &a = b->cargs[bl.args];
+            e = bl.f64 ? launch_restrict32_batch<double>(L, a, bl.total, b->d_active)
+                       : launch_restrict32_batch<float>(L, a, bl.total, b->d_active);
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Builds the work-list form of a batch whose members all pass worklist_member_ok.
+tpmg_status build_worklist(tpmg_batch *b, tpmg_ctx *const *ctxs, int M, const double *const *d_f, double *const *d_u,
+                           cudaStream_t s)
+{
+    const int n_part = ctxs[0]->n_part;
+    for (int m = 0; m < M; ++m)
+        if (ctxs[m]->n_part != n_part) return TPMG_ERR_INVALID_ARG;
+    b->form = TPMG_BATCH_WORKLIST;
+    b->n_part = n_part;
+    // the members' work vectors: outer FP64 r, z, p, q and every level's FP32 iterate
+    // (and block Jacobi's second buffer), the coarse levels' FP32 right-hand sides
+    std::vector<BatchMemberDev> mem(M);
+    std::vector<std::vector<float *>> u32(M), u2(M), f32(M);
+    b->d_sc.assign(M, nullptr);
+    for (int m = 0; m < M; ++m) {
+        const tpmg_ctx *c = ctxs[m];
+        const LevelDev &fl = c->lv.back();
+        const long N = c->N;
+        const int n_r = c->p.n_r, L = c->p.n_levels;
+        BatchMemberDev &x = mem[m];
+        x = BatchMemberDev{fl.nbr, fl.g, fl.area, fl.area_r, fl.om, fl.oc, c->vert.vol, c->vert.w, c->vert.hr, n_r,
+                           (int)N, d_f[m], d_u[m]};
+        if (balloc(b, &x.r, N) != cudaSuccess || balloc(b, &x.r32, N) != cudaSuccess || balloc(b, &x.z, N) != cudaSuccess ||
+            balloc(b, &x.p, N) != cudaSuccess ||
+            balloc(b, &x.q, N) != cudaSuccess || balloc(b, &x.partials, 2 * (size_t)n_part) != cudaSuccess ||
+            balloc(b, &x.zflags, (size_t)n_part) != cudaSuccess || balloc(b, &b->d_sc[m], 1) != cudaSuccess ||
+            balloc(b, &x.hist, kHistCap) != cudaSuccess)
+            return TPMG_ERR_OOM;
+        x.sc = b->d_sc[m];
+        x.rtol = b->rtol;
+        x.max_iter = b->max_iter;
+        const bool jac = c->p.smoother == TPMG_SMOOTH_JACOBI;
+        u32[m].assign(L, nullptr);
+        u2[m].assign(L, nullptr);
+        f32[m].assign(L, nullptr);
+        for (int l = 0; l < L; ++l) {
+            const size_t n = (size_t)c->lv[l].n * n_r;
+            if (balloc(b, &u32[m][l], n) != cudaSuccess || (jac && balloc(b, &u2[m][l], n) != cudaSuccess) ||
+                (l < L - 1 && balloc(b, &f32[m][l], n) != cudaSuccess))
+                return TPMG_ERR_OOM;
+            if (cudaMemsetAsync(u32[m][l], 0, n * sizeof(float), s) != cudaSuccess ||
+                (jac && cudaMemsetAsync(u2[m][l], 0, n * sizeof(float), s) != cudaSuccess) ||
+                (l < L - 1 && cudaMemsetAsync(f32[m][l], 0, n * sizeof(float), s) != cudaSuccess))
+                return TPMG_ERR_CUDA;
+        }
+        if (cudaMemsetAsync(x.r, 0, N * sizeof(double), s) != cudaSuccess ||
+            cudaMemsetAsync(x.z, 0, N * sizeof(double), s) != cudaSuccess)
+            return TPMG_ERR_CUDA;
+    }
+    // the merged schedule: every member's ops under their keys, steps in key order,
+    // each step split into launches by kernel class
+    struct Tagged {
+        std::array<int, 4> key;
+        int member;
+        VOp op;
+    };
+    std::vector<Tagged> all;
+    for (int m = 0; m < M; ++m) {
+        std::vector<VOp> ops;
+        const tpmg_ctx *c = ctxs[m];
+        member_ops(c, c->p.n_levels - 1, true, -1, ops);
+        for (const VOp &o : ops) all.push_back(Tagged{op_key(o), m, o});
+    }
+    std::stable_sort(all.begin(), all.end(), [](const Tagged &a, const Tagged &b2) { return a.key < b2.key; });
+    for (size_t i0 = 0; i0 < all.size();) {
+        size_t i1 = i0;
+        while (i1 < all.size() && all[i1].key == all[i0].key) ++i1;
+        // launch classes of the step: (kind, mode, f64, rows class)
+        std::vector<std::array<int, 4>> classes;
+        for (size_t i = i0; i < i1; ++i) {
+            const Tagged &t = all[i];
+            const tpmg_ctx *c = ctxs[t.member];
+            const bool f64 = false;   // the finest level reads the member's FP32 copy of r
+            const std::array<int, 4> cl{t.op.kind, t.op.kind == 0 ? t.op.mode : 0, f64 ? 1 : 0,
+                                        t.op.kind == 0 ? rows_class(c->p.n_r) : 0};
+            if (std::find(classes.begin(), classes.end(), cl) == classes.end()) classes.push_back(cl);
+        }
+        for (const auto &cl : classes) {
+            BatchLaunch bl;
+            bl.kind = cl[0];
+            bl.mode = cl[1];
+            bl.f64 = cl[2] != 0;
+            bl.n_r_max = cl[3];
+            // a new work list for the launch
+            auto open = [&]() {
+                bl.count = 0;
+                bl.total = 0;
+                if (bl.kind == 0) {
+                    bl.args = (int)b->rargs.size();
+                    b->rargs.emplace_back();
+                    std::memset(&b->rargs.back(), 0, sizeof(RelaxBatchArgs));
+                } else {
+                    bl.args = (int)b->cargs.size();
+                    b->cargs.emplace_back();
+                    std::memset(&b->cargs.back(), 0, sizeof(RestrictBatchArgs));
+                }
+            };
+            auto flush = [&]() {
+                if (bl.count > 0) b->launches.push_back(bl);
+                open();
+            };
+            open();
+            for (size_t i = i0; i < i1; ++i) {
+                const Tagged &t = all[i];
+                const tpmg_ctx *c = ctxs[t.member];
+                const bool f64 = false;
+                const std::array<int, 4> tc{t.op.kind, t.op.kind == 0 ? t.op.mode : 0, f64 ? 1 : 0,
+                                            t.op.kind == 0 ? rows_class(c->p.n_r) : 0};
+                if (tc != cl) continue;
+                if (bl.count == kBatchItems) flush();
+                const int m = t.member, l = t.op.lvl, n_r = c->p.n_r;
+                const LevelDev &lv = c->lv[l];
+                auto buf = [&](int lvl, int id) { return id == 0 ? u32[m][lvl] : u2[m][lvl]; };
+                const bool finest = l == c->p.n_levels - 1;
+                const void *f = finest ? (const void *)mem[m].r32 : (const void *)f32[m][l];
+                if (bl.kind == 0) {
+                    BatchRelaxItem it{lv.task_cells, lv.task_nbr, lv.cpack, lv.cvert, lv.rinv32, f,
+                                      buf(l, t.op.uin), buf(l, t.op.uout),
+                                      t.op.fine_buf >= 0 ? buf(l + 1, t.op.fine_buf) : nullptr,
+                                      t.op.out64 ? mem[m].z : nullptr, n_r, t.op.task0 * kRelaxCols,
+                                      t.op.n_tasks * kRelaxCols, m, (float)c->p.relax};
+                    RelaxBatchArgs &a = b->rargs[bl.args];
+                    a.off[bl.count] = (int)bl.total;
+                    a.items[bl.count] = it;
+                    a.n_items = bl.count + 1;
+                    bl.total += it.n_slots;
+                } else {
+                    const int Nc = c->lv[l - 1].n * n_r;
+                    BatchRestrictItem it{lv.nbr, lv.cpack, lv.cvert, f, buf(l, t.op.uin), f32[m][l - 1], n_r, Nc, m};
+                    RestrictBatchArgs &a = b->cargs[bl.args];
+                    a.off[bl.count] = (int)bl.total;
+                    a.items[bl.count] = it;
+                    a.n_items = bl.count + 1;
+                    bl.total += (Nc + 31) & ~31;
+                }
+                ++bl.count;
+            }
+            if (bl.count > 0) b->launches.push_back(bl);   // the last list (an empty one stays unused)
+        }
+        i0 = i1;
+    }
+    for (const BatchLaunch &bl : b->launches)
+        if (bl.total > INT32_MAX / 2) return TPMG_ERR_INVALID_ARG;   // positions are 32-bit in the kernels
+    if (balloc(b, &b->d_mem, M) != cudaSuccess || balloc(b, &b->d_active, M) != cudaSuccess ||
+        balloc(b, &b->d_go, M) != cudaSuccess)
+        return TPMG_ERR_OOM;
+    if (cudaMallocHost(&b->h_sc, sizeof(Scalars) * M) != cudaSuccess) return TPMG_ERR_OOM;
+    if (cudaMemcpyAsync(b->d_mem, mem.data(), sizeof(BatchMemberDev) * M, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(b->d_active, 1, sizeof(int) * M, s) != cudaSuccess ||
+        cudaMemsetAsync(b->d_go, 0, sizeof(int) * M, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+        return TPMG_ERR_CUDA;
+    // tuner: CTAs of 1, 2, 4 or 8 warps for each relaxation launch of more than a wave of
+    // warps, timed on the batch's zeroed work vectors (every variant is the same arithmetic)
+    const int sm = ctxs[0]->sm_count;
+    const Launch L0{s, 0, sm, nullptr, nullptr, false};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return TPMG_ERR_CUDA;
+    tpmg_status st = TPMG_OK;
+    for (BatchLaunch &bl : b->launches) {
+        if (bl.kind != 0 || bl.total < 2L * 32 * sm) continue;
+        float best = 0.f;
+        for (int v = 0; v < 4 && st == TPMG_OK; ++v) {
+            BatchLaunch t = bl;
+            t.wpb = 1 << v;
+            auto go = [&]() {
+                const RelaxBatchArgs &a = b->rargs[t.args];
+                return t.f64 ? launch_relax32_batch<double>(L0, t.mode, t.n_r_max, a, t.total, t.wpb, b->d_active)
+                             : launch_relax32_batch<float>(L0, t.mode, t.n_r_max, a, t.total, t.wpb, b->d_active);
+            };
+            float ms = 0.f;
+            if (go() != cudaSuccess || cudaEventRecord(e0, s) != cudaSuccess) st = TPMG_ERR_CUDA;
+            for (int k = 0; k < 3 && st == TPMG_OK; ++k)
+                if (go() != cudaSuccess) st = TPMG_ERR_CUDA;
+            if (st == TPMG_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                                  cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                st = TPMG_ERR_CUDA;
+            bl.us[v] = 1e3f * ms / 3.f;
+            if (st == TPMG_OK && (best == 0.f || bl.us[v] < best)) {
+                best = bl.us[v];
+                bl.wpb = t.wpb;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != TPMG_OK) return st;
+    // the work vectors again as at creation (the tuner wrote into them)
+    for (int m = 0; m < M; ++m)
+        for (size_t l = 0; l < u32[m].size(); ++l) {
+            const size_t n = (size_t)ctxs[m]->lv[l].n * ctxs[m]->p.n_r;
+            if (cudaMemsetAsync(u32[m][l], 0, n * sizeof(float), s) != cudaSuccess ||
+                (u2[m][l] && cudaMemsetAsync(u2[m][l], 0, n * sizeof(float), s) != cudaSuccess) ||
+                (f32[m][l] && cudaMemsetAsync(f32[m][l], 0, n * sizeof(float), s) != cudaSuccess))
+                return TPMG_ERR_CUDA;
+        }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return TPMG_ERR_CUDA;
+    // the graph: the members' initial residuals and first decisions, then a conditional
+    // WHILE node whose body is one iteration of every active member
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return TPMG_ERR_CUDA;
+    const Launch L{cs, 0, sm, nullptr, nullptr, ctxs[0]->p.pdl != 0};
+    cudaGraph_t g = nullptr;
+    cudaGraphConditionalHandle h = 0;
+    auto capture = [&](cudaGraph_t into, const cudaGraphNode_t *deps, size_t nd, std::vector<cudaGraphNode_t> *leaves,
+                       auto &&body) -> tpmg_status {
+        if (cudaStreamBeginCaptureToGraph(cs, into, deps, nullptr, nd, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return TPMG_ERR_CUDA;
+        const cudaError_t eb = body();
+        const cudaGraphNode_t *out = nullptr;
+        size_t nout = 0;
+        cudaStreamCaptureStatus csx;
+        const cudaError_t ei = cudaStreamGetCaptureInfo(cs, &csx, nullptr, nullptr, &out, nullptr, &nout);
+        if (leaves && ei == cudaSuccess) leaves->assign(out, out + nout);
+        cudaGraph_t gout = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(cs, &gout);
+        return (eb == cudaSuccess && ei == cudaSuccess && ee == cudaSuccess) ? TPMG_OK : TPMG_ERR_CUDA;
+    };
+    long long n_init = 0, n_iter = 0;
+    auto counted = [](long long &n, cudaError_t e) {
+        ++n;
+        return e;
+    };
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) st = TPMG_ERR_CUDA;
+    if (st == TPMG_OK && cudaGraphConditionalHandleCreate(&h, g, 0, 0) != cudaSuccess) st = TPMG_ERR_CUDA;
+    std::vector<cudaGraphNode_t> leaves;
+    if (st == TPMG_OK)
+        st = capture(g, nullptr, 0, &leaves, [&]() -> cudaError_t {
+            cudaError_t e = cudaMemsetAsync(b->d_active, 1, sizeof(int) * M, cs);
+            if (e == cudaSuccess) e = counted(n_init, launch_outer_batch(L, BATCH_NONZERO, b->d_mem, M, n_part, b->d_active));
+            if (e == cudaSuccess) e = counted(n_init, launch_outer_batch(L, BATCH_RESIDUAL, b->d_mem, M, n_part, b->d_active));
+            if (e == cudaSuccess)
+                e = counted(n_init, launch_finish_batch(L, FIN_LOOP_RR0, b->d_mem, M, n_part, b->d_active, b->d_go, 0));
+            if (e == cudaSuccess) e = counted(n_init, launch_outer_batch(L, BATCH_CLEAR_P, b->d_mem, M, n_part, b->d_active));
+            if (e == cudaSuccess) e = counted(n_init, launch_batch_continue(L, M, b->d_go, b->d_active, h));
+            return e;
+        });
+    cudaGraphNode_t node = nullptr;
+    cudaGraphNodeParams cp = {};
+    if (st == TPMG_OK) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        if (cudaGraphAddNode(&node, g, leaves.data(), nullptr, leaves.size(), &cp) != cudaSuccess) st = TPMG_ERR_CUDA;
+    }
+    if (st == TPMG_OK)
+        st = capture(cp.conditional.phGraph_out[0], nullptr, 0, nullptr, [&]() -> cudaError_t {
+            cudaError_t e = batch_vcycle(b, L);
+            n_iter += (long long)b->launches.size();
+            if (e == cudaSuccess) e = counted(n_iter, launch_outer_batch(L, BATCH_DOT_RZ, b->d_mem, M, n_part, b->d_active));
+            if (e == cudaSuccess)
+                e = counted(n_iter, launch_finish_batch(L, FIN_LOOP_BETA_PR, b->d_mem, M, n_part, b->d_active, b->d_go, 0));
+            if (e == cudaSuccess) e = counted(n_iter, launch_outer_batch(L, BATCH_XPBY, b->d_mem, M, n_part, b->d_active));
+            if (e == cudaSuccess) e = counted(n_iter, launch_outer_batch(L, BATCH_APPLY, b->d_mem, M, n_part, b->d_active));
+            if (e == cudaSuccess)
+                e = counted(n_iter, launch_finish_batch(L, FIN_ALPHA, b->d_mem, M, n_part, b->d_active, b->d_go, 0));
+            if (e == cudaSuccess) e = counted(n_iter, launch_outer_batch(L, BATCH_AXPY, b->d_mem, M, n_part, b->d_active));
+            if (e == cudaSuccess)
+                e = counted(n_iter, launch_finish_batch(L, FIN_LOOP_RR, b->d_mem, M, n_part, b->d_active, b->d_go, 0));
+            if (e == cudaSuccess)
+                e = counted(n_iter,
+                            launch_finish_batch(L, FIN_RZC, b->d_mem, M, n_part, b->d_active, b->d_go, n_part));
+            if (e == cudaSuccess) e = counted(n_iter, launch_batch_continue(L, M, b->d_go, b->d_active, h));
+            return e;
+        });
+    if (st == TPMG_OK && cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) st = TPMG_ERR_CUDA;
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    b->wl_init = n_init;
+    b->wl_iter = n_iter;
     return st;
 }
 
@@ -1720,6 +2185,7 @@ tpmg_status tpmg_default_params(tpmg_params *p)
     p->outer = TPMG_OUTER_CG;
     p->prolongation = TPMG_PROLONG_CONSTANT;
     p->pdl = 1;
+    p->relax_variant = -1;
     return TPMG_OK;
 }
 
@@ -1836,7 +2302,8 @@ tpmg_status tpmg_setup_profiles(const tpmg_params *params, const tpmg_profiles *
         dalloc(ctx, &ctx->partials, 2 * (size_t)ctx->n_part) != cudaSuccess ||
         dalloc(ctx, &ctx->zflags, (size_t)ctx->n_part) != cudaSuccess ||
         dalloc(ctx, &ctx->d_hist, kHistCap) != cudaSuccess || dalloc(ctx, &ctx->sc, 1) != cudaSuccess ||
-        dalloc(ctx, &ctx->d_net_s, 3) != cudaSuccess)
+        dalloc(ctx, &ctx->d_net_s, 3) != cudaSuccess ||
+        (ctx->p.precision == TPMG_PREC_MIXED && dalloc(ctx, &ctx->r32, ctx->N) != cudaSuccess))
         return bail(TPMG_ERR_OOM);
     if (cudaMallocHost(&ctx->h_sc, sizeof(Scalars)) != cudaSuccess) return bail(TPMG_ERR_OOM);
     {
@@ -1852,7 +2319,9 @@ tpmg_status tpmg_setup_profiles(const tpmg_params *params, const tpmg_profiles *
         }
     }
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return bail(TPMG_ERR_CUDA);
-    if (ctx->p.autotune) {
+    if (ctx->p.relax_variant >= 0) {
+        for (LevelDev &D : ctx->lv) D.relax_variant = ctx->p.relax_variant;
+    } else if (ctx->p.autotune) {
         tpmg_status st = autotune(ctx);
         if (st != TPMG_OK) return bail(st);
     }
@@ -2075,13 +2544,18 @@ tpmg_status tpmg_batch_create(tpmg_ctx *const *ctxs, int n, const double *const 
     if (!(rtol >= 0.0) || max_iter < 0 || max_iter >= kHistCap) return TPMG_ERR_INVALID_ARG;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return TPMG_ERR_CUDA;
+    bool worklist = true, repeated = false;
     for (int i = 0; i < n; ++i) {
         if (!ctxs[i] || !d_f[i] || !d_u[i] || d_f[i] == d_u[i] || ctxs[i]->device != dev) return TPMG_ERR_INVALID_ARG;
         if (ctxs[i]->p.outer != TPMG_OUTER_CG) return TPMG_ERR_INVALID_ARG;   // batches hold device-side CG loops
         if (nonsymmetric(ctxs[i])) return TPMG_ERR_INVALID_ARG;              // which need a symmetric A and B
-        for (int k = 0; k < i; ++k)
-            if (ctxs[k] == ctxs[i]) return TPMG_ERR_INVALID_ARG;   // one problem per context
+        worklist = worklist && worklist_member_ok(ctxs[i]);
+        for (int k = 0; k < i; ++k) {
+            if (ctxs[k] == ctxs[i]) repeated = true;
+            if (d_u[k] == d_u[i] || d_u[k] == d_f[i] || d_f[k] == d_u[i]) return TPMG_ERR_INVALID_ARG;   // aliased
+        }
     }
+    if (repeated && !worklist) return TPMG_ERR_INVALID_ARG;   // a branch holds its context's own solve
     tpmg_batch *b = new (std::nothrow) tpmg_batch();
     if (!b) return TPMG_ERR_OOM;
     b->ctx.assign(ctxs, ctxs + n);
@@ -2089,6 +2563,16 @@ tpmg_status tpmg_batch_create(tpmg_ctx *const *ctxs, int n, const double *const 
     b->iter_launches.assign(n, 0);
     b->rtol = rtol;
     b->max_iter = max_iter;
+    if (worklist) {
+        const tpmg_status st = build_worklist(b, ctxs, n, d_f, d_u, ctxs[0]->stream);
+        if (st != TPMG_OK) {
+            (void)cudaGetLastError();
+            tpmg_batch_destroy(b);
+            return st;
+        }
+        *out = b;
+        return TPMG_OK;
+    }
     cudaGraph_t g;
     if (cudaGraphCreate(&g, 0) != cudaSuccess) {
         delete b;
@@ -2113,6 +2597,24 @@ tpmg_status tpmg_batch_run(tpmg_batch *b, void *cuda_stream, int *iters, double 
     if (!b || !iters || !rel_resid) return TPMG_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     if (cudaGraphLaunch(b->exec, s) != cudaSuccess) return TPMG_ERR_CUDA;
+    if (b->form == TPMG_BATCH_WORKLIST) {
+        const int M = (int)b->ctx.size();
+        for (int m = 0; m < M; ++m)
+            if (cudaMemcpyAsync(b->h_sc + m, b->d_sc[m], sizeof(Scalars), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+                return TPMG_ERR_CUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return TPMG_ERR_CUDA;
+        tpmg_status first = TPMG_OK;
+        int it_max = 0;
+        for (int m = 0; m < M; ++m) {
+            const tpmg_status st = loop_result(b->ctx[m], b->h_sc[m], b->rtol, b->max_iter, &iters[m], &rel_resid[m]);
+            if (status) status[m] = st;
+            if (st != TPMG_OK && first == TPMG_OK) first = st;
+            it_max = std::max(it_max, iters[m]);
+        }
+        // the batch's loop runs as long as its longest member
+        if (kernel_launches) *kernel_launches = b->wl_init + (long long)it_max * b->wl_iter;
+        return first;
+    }
     for (tpmg_ctx *c : b->ctx)
         if (cudaMemcpyAsync(c->h_sc, c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s) != cudaSuccess)
             return TPMG_ERR_CUDA;
@@ -2129,10 +2631,15 @@ tpmg_status tpmg_batch_run(tpmg_batch *b, void *cuda_stream, int *iters, double 
     return first;
 }
 
+int tpmg_batch_form(const tpmg_batch *b) { return b ? b->form : -1; }
+
 void tpmg_batch_destroy(tpmg_batch *b)
 {
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (!b->allocs.empty() || b->h_sc) cudaDeviceSynchronize();   // no member's kernel still reads them
+    for (void *q : b->allocs) cudaFree(q);
+    if (b->h_sc) cudaFreeHost(b->h_sc);
     delete b;
 }
 

@@ -22,6 +22,8 @@
 // u_T') directly (no residual, no cancellation).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "tpmg_internal.h"
 
 namespace tpmg {
@@ -226,15 +228,17 @@ __device__ __forceinline__ double apply_vc(const OpView &o, const double *__rest
     return apply_at<ADV>(o, x, T, k, i);
 }
 
+// The kernels below take the block index and the grid size as arguments of their
+// bodies (bid, nblk), so that the batched form runs the same code as block bid of
+// a launch of nblk blocks for each member: same partition, same partial sums.
 template <int NT, bool FULL, bool ADV>
-__global__ void __launch_bounds__(NT) k_apply(OpView o, FullView fv, const double *__restrict__ x,
-                                              double *__restrict__ y, int N, double *__restrict__ partials)
+__device__ __forceinline__ void apply_body(const OpView &o, const FullView &fv, const double *__restrict__ x,
+                                           double *__restrict__ y, int N, double *__restrict__ partials, int bid,
+                                           int nblk)
 {
-    pdl_wait();
-    pdl_trigger();
     double acc = 0.0;
     if (FULL) {
-        for (int i = blockIdx.x * NT + threadIdx.x; i < N; i += gridDim.x * NT) {
+        for (int i = bid * NT + threadIdx.x; i < N; i += nblk * NT) {
             const int T = i / o.n_r, k = i - T * o.n_r;
             const double v = apply_any<NT, FULL, ADV>(o, fv, x, T, k, i);
             y[i] = v;
@@ -245,8 +249,8 @@ __global__ void __launch_bounds__(NT) k_apply(OpView o, FullView fv, const doubl
         // is formed once and handed to the row below by a shuffle, so the vertical part is
         // F_k - F_{k+1}; the row is om x_k - hr_k sum_e g_e x_e + F_k - F_{k+1} (8 FP64 operations)
         const int lane = threadIdx.x & 31;
-        const int stride = gridDim.x * (NT / 32) * 31;
-        for (int base = (blockIdx.x * (NT / 32) + (threadIdx.x >> 5)) * 31; base < N; base += stride) {
+        const int stride = nblk * (NT / 32) * 31;
+        for (int base = (bid * (NT / 32) + (threadIdx.x >> 5)) * 31; base < N; base += stride) {
             const int i = base + lane;
             int T = 0, k = 0;
             double xc = 0.0, F = 0.0;
@@ -271,8 +275,8 @@ __global__ void __launch_bounds__(NT) k_apply(OpView o, FullView fv, const doubl
         // each warp takes 32 consecutive rows and writes the first 31; lane 31 only hands its
         // lower difference to lane 30 (apply_at_lanes)
         const int lane = threadIdx.x & 31;
-        const int stride = gridDim.x * (NT / 32) * 31;
-        for (int base = (blockIdx.x * (NT / 32) + (threadIdx.x >> 5)) * 31; base < N; base += stride) {
+        const int stride = nblk * (NT / 32) * 31;
+        for (int base = (bid * (NT / 32) + (threadIdx.x >> 5)) * 31; base < N; base += stride) {
             const int i = base + lane;
             int T = 0, k = 0;
             double xc = 0.0, d = 0.0;
@@ -292,8 +296,17 @@ __global__ void __launch_bounds__(NT) k_apply(OpView o, FullView fv, const doubl
     }
     if (partials) {
         acc = block_sum<NT>(acc);
-        if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+        if (threadIdx.x == 0) partials[bid] = acc;
     }
+}
+
+template <int NT, bool FULL, bool ADV>
+__global__ void __launch_bounds__(NT) k_apply(OpView o, FullView fv, const double *__restrict__ x,
+                                              double *__restrict__ y, int N, double *__restrict__ partials)
+{
+    pdl_wait();
+    pdl_trigger();
+    apply_body<NT, FULL, ADV>(o, fv, x, y, N, partials, blockIdx.x, gridDim.x);
 }
 
 __device__ __forceinline__ bool is_zero(double v) { return (__double_as_longlong(v) << 1) == 0; }
@@ -316,32 +329,31 @@ __global__ void __launch_bounds__(256) k_outer_products(OpView o, int N, double 
 // zero and the warp skips its FP64 arithmetic; the test is on bit patterns,
 // so it costs no FP64 instruction.
 template <int NT, bool FULL, bool ADV>
-__global__ void __launch_bounds__(NT) k_residual(OpView o, FullView full, const double *__restrict__ f,
-                                                 const double *__restrict__ u, double *__restrict__ r, int N,
-                                                 double *__restrict__ partials, const int *__restrict__ nz,
-                                                 int n_nz)
+__device__ __forceinline__ void residual_body(const OpView &o, const FullView &full, const double *__restrict__ f,
+                                              const double *__restrict__ u, double *__restrict__ r, int N,
+                                              double *__restrict__ partials, const int *__restrict__ nz, int n_nz,
+                                              int bid, int nblk, float *__restrict__ r32)
 {
-    pdl_wait();
-    pdl_trigger();
     double acc = 0.0;
-    const int stride = gridDim.x * NT, n_r = o.n_r;
+    const int stride = nblk * NT, n_r = o.n_r;
     // nz: the blocks' flags of k_nonzero over u; with none set u is exactly zero, so
     // r = f, accumulated in the same order as below (bit-identical), without the stencil's loads
     int any = nz ? 0 : 1;
     for (int t = threadIdx.x; t < n_nz; t += NT) any |= nz[t];
     if (!__syncthreads_or(any)) {
-        for (int i = blockIdx.x * NT + threadIdx.x; i < N; i += stride) {
+        for (int i = bid * NT + threadIdx.x; i < N; i += stride) {
             const double v = f[i];
             r[i] = v;
+            if (r32) r32[i] = (float)v;
             acc = fma(v, v, acc);
         }
         if (partials) {
             acc = block_sum<NT>(acc);
-            if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+            if (threadIdx.x == 0) partials[bid] = acc;
         }
         return;
     }
-    for (int i0 = blockIdx.x * NT + threadIdx.x; i0 < N; i0 += 2 * stride) {
+    for (int i0 = bid * NT + threadIdx.x; i0 < N; i0 += 2 * stride) {
         double fv[2], uc[2], um[2], up[2], u0[2], u1[2], u2[2];
         int T[2], k[2];
 #pragma unroll
@@ -375,25 +387,36 @@ __global__ void __launch_bounds__(NT) k_residual(OpView o, FullView full, const 
             double v = fv[q];
             if (!skip) v = v - apply_any<NT, FULL, ADV>(o, full, u, T[q], k[q], i);
             r[i] = v;
+            if (r32) r32[i] = (float)v;
             acc = fma(v, v, acc);
         }
     }
     if (partials) {
         acc = block_sum<NT>(acc);
-        if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+        if (threadIdx.x == 0) partials[bid] = acc;
     }
+}
+
+template <int NT, bool FULL, bool ADV>
+__global__ void __launch_bounds__(NT) k_residual(OpView o, FullView full, const double *__restrict__ f,
+                                                 const double *__restrict__ u, double *__restrict__ r, int N,
+                                                 double *__restrict__ partials, const int *__restrict__ nz,
+                                                 int n_nz, float *__restrict__ r32)
+{
+    pdl_wait();
+    pdl_trigger();
+    residual_body<NT, FULL, ADV>(o, full, f, u, r, N, partials, nz, n_nz, blockIdx.x, gridDim.x, r32);
 }
 
 // Per block, whether x has a nonzero element in the block's grid-stride range (a test
 // of bit patterns, no FP64 instruction): the probe of k_residual's zero-guess path.
 template <int NT>
-__global__ void __launch_bounds__(NT) k_nonzero(const double *__restrict__ x, int N, int *__restrict__ nz)
+__device__ __forceinline__ void nonzero_body(const double *__restrict__ x, int N, int *__restrict__ nz, int bid,
+                                             int nblk)
 {
-    pdl_wait();
-    pdl_trigger();
     int any = 0;
-    const int stride = gridDim.x * NT;
-    int i = blockIdx.x * NT + threadIdx.x;
+    const int stride = nblk * NT;
+    int i = bid * NT + threadIdx.x;
     for (; i + 3 * stride < N; i += 4 * stride) {
         double v[4];
 #pragma unroll
@@ -403,7 +426,15 @@ __global__ void __launch_bounds__(NT) k_nonzero(const double *__restrict__ x, in
     }
     for (; i < N; i += stride) any |= !is_zero(x[i]);
     any = __syncthreads_or(any);
-    if (threadIdx.x == 0) nz[blockIdx.x] = any;
+    if (threadIdx.x == 0) nz[bid] = any;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_nonzero(const double *__restrict__ x, int N, int *__restrict__ nz)
+{
+    pdl_wait();
+    pdl_trigger();
+    nonzero_body<NT>(x, N, nz, blockIdx.x, gridDim.x);
 }
 
 // f_c[T][k] = sum_j (f - A u)[4T + j][k]  (Algorithm 1 residual + restriction, Sec. 5)
@@ -1095,19 +1126,169 @@ __global__ void __launch_bounds__(32, 16)
     }
 }
 
+// Named CTA barriers (ids 1..15; 0 is __syncthreads) for the warp-specialised pass below.
+__device__ __forceinline__ void bar_sync(int id, int n) { asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(n) : "memory"); }
+__device__ __forceinline__ void bar_arrive(int id, int n)
+{
+    asm volatile("bar.arrive %0, %1;\n" ::"r"(id), "r"(n) : "memory");
+}
+
+constexpr int kPipeThreads = 96;   // two gathering warps and one solving warp
+
+// The same relaxation pass with warp specialisation, for passes of many tasks: each
+// CTA takes the tasks blockIdx.x, blockIdx.x + gridDim.x, ... of the pass.  Warps 0
+// and 1 (the producers) gather the right-hand side t = (f + hr sum_e g_e u_e) / pivot
+// of task i + 1 into one of two shared tiles while warp 2 (the consumer) runs the
+// twisted solve of task i on the other tile and writes it back, so that the load
+// latency and FP64 work of the gathers overlap the serial chain of the solves on the
+// SM's FP64 units.  Hand-over by named barriers: FULL[b] (ids 1, 2) -- tile b holds a
+// gathered task; EMPTY[b] (ids 3, 4) -- the consumer is done with tile b.  Every warp
+// runs the same number of tasks; producers wait on EMPTY[b] only from their third
+// task on, and the consumer arrives on EMPTY[b] only where a later task waits on it,
+// so every phase of every barrier completes.  The arithmetic of each column is that
+// of k_relax_warp (same gather, same twisted_solve, same write-back).
+template <int MODE, bool HF>
+__global__ void __launch_bounds__(kPipeThreads, 5)
+    k_relax_pc(OpView o, const int *__restrict__ cells, const int4 *__restrict__ tnb, const dbl4 *__restrict__ tg,
+               const double *__restrict__ rinv, const double *__restrict__ fb, const double *__restrict__ fcf,
+               const double *__restrict__ fm, int S, int j, int task0, int n_tasks, const double *__restrict__ f,
+               const double *u_in, double *u_out, double *__restrict__ u_fine, double relax)
+{
+    extern __shared__ double smem[];   // two tiles [16][n_r + 1]
+    __shared__ int s_cell[2][kRelaxCols];
+    __shared__ int4 s_nb[2][kRelaxCols];
+    __shared__ dbl4 s_g[2][kRelaxCols];
+    __shared__ double s_m[2][2 * kRelaxCols];
+    const int n_r = o.n_r, ld = n_r + 1, ne = kRelaxCols * n_r;
+    const int tsz = (kRelaxCols * ld + 1) & ~1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int count = (n_tasks - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;   // >= 1: grid <= n_tasks
+    pdl_wait();
+    pdl_trigger();
+    if (warp < 2) {
+        const int pt = threadIdx.x;   // 0..63
+        for (int it = 0; it < count; ++it) {
+            const int b = it & 1, t = task0 + blockIdx.x + it * gridDim.x;
+            if (it >= 2) bar_sync(3 + b, kPipeThreads);   // the consumer is done with tile b
+            if (pt < kRelaxCols) {
+                const int q = t * kRelaxCols + pt;
+                s_cell[b][pt] = __ldg(&cells[q]);
+                s_nb[b][pt] = __ldg(&tnb[q]);
+                s_g[b][pt] = tg[q];
+            } else if (pt < 3 * kRelaxCols) {
+                s_m[b][pt - kRelaxCols] = __ldg(&fm[(size_t)t * 2 * kRelaxCols + pt - kRelaxCols]);
+            }
+            bar_sync(5, 64);   // the task's cells and couplings, for both producer warps
+            double *tile = smem + b * tsz;
+            constexpr int U = 8;
+            for (int e0 = pt; e0 < ne; e0 += 64 * U) {
+                double fv[U], iv[U], v0[U], v1[U], v2[U];
+                dbl4 cs[U];
+                int col[U], kk[U];
+#pragma unroll
+                for (int q = 0; q < U; ++q) {
+                    const int e = e0 + 64 * q;
+                    col[q] = -1;
+                    kk[q] = 0;
+                    fv[q] = iv[q] = v0[q] = v1[q] = v2[q] = 0.0;
+                    if (HF) cs[q] = dbl4{0.0, 0.0, 0.0, 0.0};
+                    if (e < ne) {
+                        const int c = e / n_r, k = e - c * n_r;
+                        col[q] = c;
+                        kk[q] = k;
+                        const int T = s_cell[b][c];
+                        if (T >= 0) {
+                            fv[q] = f[T * n_r + k];
+                            iv[q] = __ldg(&rinv[T * n_r + k]);
+                            if (MODE != PASS_RHS_ONLY) {
+                                const int4 nb = s_nb[b][c];
+                                if (MODE == PASS_NORMAL || (nb.w & 1)) v0[q] = u_in[nb.x * n_r + k];
+                                if (MODE == PASS_NORMAL || (nb.w & 2)) v1[q] = u_in[nb.y * n_r + k];
+                                if (MODE == PASS_NORMAL || (nb.w & 4)) v2[q] = u_in[nb.z * n_r + k];
+                                if (HF) cs[q] = o.c[T * n_r + k];
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < U; ++q) {
+                    if (col[q] < 0) continue;
+                    double d = fv[q];
+                    if (MODE != PASS_RHS_ONLY) {
+                        if (HF) {
+                            d = fma(cs[q].z, v2[q], fma(cs[q].y, v1[q], fma(cs[q].x, v0[q], d)));
+                        } else {
+                            const dbl4 g = s_g[b][col[q]];
+                            d = fma(__ldg(&o.hr[kk[q]]), fma(g.z, v2[q], fma(g.y, v1[q], g.x * v0[q])), d);
+                        }
+                    }
+                    tile[col[q] * ld + kk[q]] = d * iv[q];
+                }
+            }
+            __threadfence_block();
+            bar_arrive(1 + b, kPipeThreads);   // tile b is full
+        }
+    } else {
+        for (int it = 0; it < count; ++it) {
+            const int b = it & 1, t = task0 + blockIdx.x + it * gridDim.x;
+            bar_sync(1 + b, kPipeThreads);
+            double *tile = smem + b * tsz;
+            const size_t fbase = (size_t)t * S * 32 + lane;
+            twisted_solve<4>(fb + fbase, fcf + fbase, s_m[b], tile + (lane & (kRelaxCols - 1)) * ld, n_r, j, lane);
+            __syncwarp();
+            constexpr int W = 2;
+            for (int e0 = lane; e0 < ne; e0 += 32 * W) {
+                double x[W], uo[W], uf[W][4];
+                int idx[W], fi[W];
+#pragma unroll
+                for (int q = 0; q < W; ++q) {
+                    const int e = e0 + 32 * q;
+                    idx[q] = -1;
+                    if (e >= ne) continue;
+                    const int c = e / n_r, k = e - c * n_r;
+                    const int T = s_cell[b][c];
+                    if (T < 0) continue;
+                    idx[q] = T * n_r + k;
+                    fi[q] = 4 * T * n_r + k;
+                    x[q] = tile[c * ld + k];
+                    uo[q] = (MODE == PASS_NORMAL && relax != 1.0) ? u_in[idx[q]] : 0.0;
+                    if (u_fine) {
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) uf[q][h] = u_fine[fi[q] + h * n_r];
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < W; ++q) {
+                    if (idx[q] < 0) continue;
+                    double v = x[q];
+                    if (relax != 1.0) v = fma(relax, v - uo[q], uo[q]);
+                    u_out[idx[q]] = v;
+                    if (u_fine) {
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) u_fine[fi[q] + h * n_r] = uf[q][h] + v;
+                    }
+                }
+            }
+            if (it + 2 < count) {   // a later task of the producers waits for tile b
+                __syncwarp();
+                __threadfence_block();
+                bar_arrive(3 + b, kPipeThreads);
+            }
+        }
+    }
+}
+
 // The vector kernels below are HBM-bound: each thread keeps the loads of 4
 // grid-stride iterations in flight, and the grid holds 8 blocks per SM.
 
 // partial <a, b>
 template <int NT>
-__global__ void __launch_bounds__(NT) k_dot(const double *__restrict__ a, const double *__restrict__ b, int N,
-                                            double *__restrict__ partials)
+__device__ __forceinline__ void dot_body(const double *__restrict__ a, const double *__restrict__ b, int N,
+                                         double *__restrict__ partials, int bid, int nblk)
 {
-    pdl_wait();
-    pdl_trigger();
     double acc = 0.0;
-    const int stride = gridDim.x * NT;
-    int i = blockIdx.x * NT + threadIdx.x;
+    const int stride = nblk * NT;
+    int i = bid * NT + threadIdx.x;
     for (; i + 3 * stride < N; i += 4 * stride) {
         double x[4], y[4];
 #pragma unroll
@@ -1117,23 +1298,31 @@ __global__ void __launch_bounds__(NT) k_dot(const double *__restrict__ a, const 
     }
     for (; i < N; i += stride) acc = fma(a[i], b[i], acc);
     acc = block_sum<NT>(acc);
-    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+    if (threadIdx.x == 0) partials[bid] = acc;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_dot(const double *__restrict__ a, const double *__restrict__ b, int N,
+                                            double *__restrict__ partials)
+{
+    pdl_wait();
+    pdl_trigger();
+    dot_body<NT>(a, b, N, partials, blockIdx.x, gridDim.x);
 }
 
 // u += alpha p; r -= alpha q; partial ||r||^2.  With z_old (flexible CG) also
 // the partial <r_new, z_old> of the Polak-Ribiere coefficient, in partials[gridDim.x + block].
 template <int NT, bool CROSS>
-__global__ void __launch_bounds__(NT) k_axpy_pair(const Scalars *__restrict__ sc, const double *__restrict__ p,
-                                                  const double *__restrict__ q, double *__restrict__ u,
-                                                  double *__restrict__ r, int N, double *__restrict__ partials,
-                                                  const double *__restrict__ z_old)
+__device__ __forceinline__ void axpy_pair_body(const Scalars *__restrict__ sc, const double *__restrict__ p,
+                                               const double *__restrict__ q, double *__restrict__ u,
+                                               double *__restrict__ r, int N, double *__restrict__ partials,
+                                               const double *__restrict__ z_old, int bid, int nblk,
+                                               float *__restrict__ r32)
 {
-    pdl_wait();
-    pdl_trigger();
     const double alpha = sc->alpha;
     double acc = 0.0, accz = 0.0;
-    const int stride = gridDim.x * NT;
-    int i = blockIdx.x * NT + threadIdx.x;
+    const int stride = nblk * NT;
+    int i = bid * NT + threadIdx.x;
     for (; i + 3 * stride < N; i += 4 * stride) {
         double pv[4], qv[4], uv[4], rv[4], zv[4];
 #pragma unroll
@@ -1148,6 +1337,7 @@ __global__ void __launch_bounds__(NT) k_axpy_pair(const Scalars *__restrict__ sc
             u[j] = fma(alpha, pv[k], uv[k]);
             const double x = fma(-alpha, qv[k], rv[k]);
             r[j] = x;
+            if (r32) r32[j] = (float)x;
             acc = fma(x, x, acc);
             if (CROSS) accz = fma(x, zv[k], accz);
         }
@@ -1156,28 +1346,38 @@ __global__ void __launch_bounds__(NT) k_axpy_pair(const Scalars *__restrict__ sc
         u[i] = fma(alpha, p[i], u[i]);
         const double x = fma(-alpha, q[i], r[i]);
         r[i] = x;
+        if (r32) r32[i] = (float)x;
         acc = fma(x, x, acc);
         if (CROSS) accz = fma(x, z_old[i], accz);
     }
     acc = block_sum<NT>(acc);
-    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+    if (threadIdx.x == 0) partials[bid] = acc;
     if (CROSS) {
         __syncthreads();   // block_sum's shared scratch is reused
         accz = block_sum<NT>(accz);
-        if (threadIdx.x == 0) partials[gridDim.x + blockIdx.x] = accz;
+        if (threadIdx.x == 0) partials[nblk + bid] = accz;
     }
+}
+
+template <int NT, bool CROSS>
+__global__ void __launch_bounds__(NT) k_axpy_pair(const Scalars *__restrict__ sc, const double *__restrict__ p,
+                                                  const double *__restrict__ q, double *__restrict__ u,
+                                                  double *__restrict__ r, int N, double *__restrict__ partials,
+                                                  const double *__restrict__ z_old, float *__restrict__ r32)
+{
+    pdl_wait();
+    pdl_trigger();
+    axpy_pair_body<NT, CROSS>(sc, p, q, u, r, N, partials, z_old, blockIdx.x, gridDim.x, r32);
 }
 
 // p = z + beta p
 template <int NT>
-__global__ void __launch_bounds__(NT) k_xpby(const Scalars *__restrict__ sc, const double *__restrict__ z,
-                                             double *__restrict__ p, int N)
+__device__ __forceinline__ void xpby_body(const Scalars *__restrict__ sc, const double *__restrict__ z,
+                                          double *__restrict__ p, int N, int bid, int nblk)
 {
-    pdl_wait();
-    pdl_trigger();
     const double beta = sc->beta;
-    const int stride = gridDim.x * NT;
-    int i = blockIdx.x * NT + threadIdx.x;
+    const int stride = nblk * NT;
+    int i = bid * NT + threadIdx.x;
     for (; i + 3 * stride < N; i += 4 * stride) {
         double zv[4], pv[4];
 #pragma unroll
@@ -1188,12 +1388,29 @@ __global__ void __launch_bounds__(NT) k_xpby(const Scalars *__restrict__ sc, con
     for (; i < N; i += stride) p[i] = fma(beta, p[i], z[i]);
 }
 
-// Deterministic reduction of the block partials (fixed order) and the PCG scalar step.
-__global__ void __launch_bounds__(256) k_finish(int what, const double *__restrict__ partials, int n, Scalars *sc,
-                                                LoopCtl loop)
+template <int NT>
+__global__ void __launch_bounds__(NT) k_xpby(const Scalars *__restrict__ sc, const double *__restrict__ z,
+                                             double *__restrict__ p, int N)
 {
     pdl_wait();
     pdl_trigger();
+    xpby_body<NT>(sc, z, p, N, blockIdx.x, gridDim.x);
+}
+
+// The decision of a device-side loop: the loop's conditional handle, or, for a member
+// of a batched solve (loop.go set), the member's flag, which the batch's loop reads.
+__device__ __forceinline__ void set_loop(const LoopCtl &loop, bool go)
+{
+    if (loop.go)
+        *loop.go = go ? 1 : 0;
+    else
+        cudaGraphSetConditional(loop.cond, go ? 1u : 0u);
+}
+
+// Deterministic reduction of the block partials (fixed order) and the PCG scalar step.
+__device__ __forceinline__ void finish_body(int what, const double *__restrict__ partials, int n, Scalars *sc,
+                                            const LoopCtl &loop)
+{
     double v = 0.0, v2 = 0.0;
     for (int i = threadIdx.x; i < n; i += 256) v += partials[i];
     v = block_sum<256>(v);
@@ -1250,7 +1467,7 @@ __global__ void __launch_bounds__(256) k_finish(int what, const double *__restri
         sc->it = 0;
         sc->flag = isfinite(v) ? 0 : 2;
         if (loop.hist) loop.hist[0] = 1.0;
-        cudaGraphSetConditional(loop.cond, (isfinite(v) && v > 0.0 && loop.max_iter > 0) ? 1u : 0u);
+        set_loop(loop, isfinite(v) && v > 0.0 && loop.max_iter > 0);
         break;
     }
     case FIN_RR0F:
@@ -1267,7 +1484,7 @@ __global__ void __launch_bounds__(256) k_finish(int what, const double *__restri
         const double rel = v2 > 0.0 ? sqrt(rr / v2) : 0.0;
         if (what == FIN_LOOP_RR0F) {
             if (loop.hist) loop.hist[0] = rel;
-            cudaGraphSetConditional(loop.cond, (isfinite(rr) && rr > 0.0 && !(rel <= loop.rtol) && loop.max_iter > 0) ? 1u : 0u);
+            set_loop(loop, isfinite(rr) && rr > 0.0 && !(rel <= loop.rtol) && loop.max_iter > 0);
         }
         break;
     }
@@ -1285,12 +1502,89 @@ __global__ void __launch_bounds__(256) k_finish(int what, const double *__restri
         const double rel = sqrt(v / sc->rr0);
         if (loop.hist) loop.hist[it] = rel;
         const bool go = sc->flag == 0 && !(rel <= loop.rtol) && it < loop.max_iter;
-        cudaGraphSetConditional(loop.cond, go ? 1u : 0u);
+        set_loop(loop, go);
         break;
     }
     default:
         break;
     }
+}
+
+__global__ void __launch_bounds__(256) k_finish(int what, const double *__restrict__ partials, int n, Scalars *sc,
+                                                LoopCtl loop)
+{
+    pdl_wait();
+    pdl_trigger();
+    finish_body(what, partials, n, sc, loop);
+}
+
+// ---- batched form: the outer FP64 kernels over the members of a batch -----------
+__device__ __forceinline__ OpView batch_view(const BatchMemberDev &m)
+{
+    return OpView{m.nbr,   m.g,     m.area,  m.area_r, m.vol,   m.w,   m.hr,  m.n_r, nullptr,
+                  nullptr, nullptr, nullptr, nullptr,  nullptr, nullptr, m.om, m.oc};
+}
+
+// Member m's block b of n_part is virtual block m n_part + b; each CTA runs virtual
+// blocks blockIdx.x, blockIdx.x + gridDim.x, ... with the body of the member's own
+// kernel, so every member gets the partition (and the partial sums) of its own solve.
+template <int NT, int WHAT>
+__global__ void __launch_bounds__(NT) k_outer_batch(const BatchMemberDev *__restrict__ mem, int M, int n_part,
+                                                    const int *__restrict__ active)
+{
+    pdl_wait();
+    pdl_trigger();
+    const int nv = M * n_part;
+    for (int vb = blockIdx.x; vb < nv; vb += gridDim.x) {
+        const int m = vb / n_part, b = vb - m * n_part;
+        if (!active[m]) continue;   // the same for every thread of the block
+        const BatchMemberDev &x = mem[m];
+        if (WHAT == BATCH_NONZERO) nonzero_body<NT>(x.u, x.N, x.zflags, b, n_part);
+        if (WHAT == BATCH_RESIDUAL)
+            residual_body<NT, false, false>(batch_view(x), FullView{}, x.f, x.u, x.r, x.N, x.partials, x.zflags, n_part,
+                                            b, n_part, x.r32);
+        if (WHAT == BATCH_DOT_RZ) dot_body<NT>(x.r, x.z, x.N, x.partials, b, n_part);
+        if (WHAT == BATCH_XPBY) xpby_body<NT>(x.sc, x.z, x.p, x.N, b, n_part);
+        if (WHAT == BATCH_APPLY)
+            apply_body<NT, false, false>(batch_view(x), FullView{}, x.p, x.q, x.N, x.partials, b, n_part);
+        if (WHAT == BATCH_AXPY)
+            axpy_pair_body<NT, true>(x.sc, x.p, x.q, x.u, x.r, x.N, x.partials, x.z, b, n_part, x.r32);
+        if (WHAT == BATCH_CLEAR_P)
+            for (int i = b * NT + threadIdx.x; i < x.N; i += n_part * NT) x.p[i] = 0.0;
+        __syncthreads();   // the next virtual block reuses block_sum's shared scratch
+    }
+}
+
+// The members' finishes, one block each: member m's k_finish with its loop decision
+// written to go[m] (active members only).
+__global__ void __launch_bounds__(256) k_finish_batch(int what, const BatchMemberDev *__restrict__ mem, int n_part,
+                                                      int offset, const int *__restrict__ active, int *go)
+{
+    pdl_wait();
+    pdl_trigger();
+    const int m = blockIdx.x;
+    if (!active[m]) return;
+    const BatchMemberDev &x = mem[m];
+    LoopCtl loop{0, x.rtol, x.max_iter, x.hist};
+    loop.go = go + m;
+    finish_body(what, x.partials + offset, n_part, x.sc, loop);
+}
+
+// The end of a batched iteration: the members whose finish decided to go on stay
+// active; the batch's loop continues while any member is active.
+__global__ void __launch_bounds__(256) k_batch_continue(int M, const int *__restrict__ go, int *active,
+                                                        cudaGraphConditionalHandle cond)
+{
+    pdl_wait();
+    pdl_trigger();
+    int any = 0;
+    for (int m = threadIdx.x; m < M; m += 256) {
+        const int g = go[m];
+        active[m] = g;
+        any |= g;
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) cudaGraphSetConditional(cond, any ? 1u : 0u);
 }
 
 __global__ void __launch_bounds__(256) k_lincomb(long n, double a, const double *x, double b, const double *y,
@@ -1335,7 +1629,7 @@ cudaError_t launch_nonzero(const Launch &L, long n, const double *x, int *nz, in
 }
 
 cudaError_t launch_residual(const Launch &L, const LevelDev &lv, const VertDev &v, const double *f, const double *u,
-                            double *r, double *partials, int n_part, const int *nz)
+                            double *r, double *partials, int n_part, const int *nz, float *r32)
 {
     const int N = lv.n * L.n_r;
     const int grid = partials ? n_part : grid_for(N, kThreads, L.sm_count);
@@ -1343,7 +1637,7 @@ cudaError_t launch_residual(const Launch &L, const LevelDev &lv, const VertDev &
     auto kern = lv.cfull ? k_residual<kThreads, true, false>
                          : (lv.area_x ? k_residual<kThreads, false, true> : k_residual<kThreads, false, false>);
     return launch_k(L, kern, grid, kThreads, 0, make_view(lv, v, L.n_r), fv, f, u, r, N, partials, nz,
-                    nz ? n_part : 0);
+                    nz ? n_part : 0, r32);
 }
 
 cudaError_t launch_resid_restrict(const Launch &L, const LevelDev &fine, const LevelDev &coarse, const VertDev &v,
@@ -1457,6 +1751,21 @@ static cudaError_t relax_launch_hf(const Launch &L0, const LevelDev &lv, const V
     const size_t tile = (((size_t)kRelaxCols * (L.n_r + 1) + 1) & ~(size_t)1) * sizeof(double);
     int var = lv.relax_variant;
     if (var < 0) var = (n_tasks >= 8 * L.sm_count && tile <= 32 * 1024) ? RELAX_WARP : RELAX_CTA128;
+    if (var == RELAX_PIPE && 2 * tile <= 64 * 1024) {
+        auto kern = k_relax_pc<MODE, HF>;
+        const size_t smem = 2 * tile;
+        if (smem > 48 * 1024) {
+            const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        int per_sm = 0;   // resident CTAs per SM: one wave of CTAs walks all tasks
+        const cudaError_t eo = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPipeThreads, smem);
+        if (eo != cudaSuccess) return eo;
+        const int grid = std::min(n_tasks, std::max(per_sm, 1) * L.sm_count);
+        return launch_k(L, kern, grid, kPipeThreads, smem, make_view(lv, v, L.n_r), lv.task_cells, lv.task_nbr,
+                        lv.task_g, lv.rinv, lv.fb, lv.fc, lv.fm, lv.steps, lv.jmid, task0, n_tasks, f, u_in, u_out,
+                        u_fine, relax);
+    }
     if (var == RELAX_WARP && tile <= 32 * 1024) {
         return launch_k(L, k_relax_warp<MODE, HF>, n_tasks, 32, tile, make_view(lv, v, L.n_r), lv.task_cells,
                         lv.task_nbr, lv.task_g, lv.rinv, lv.fb, lv.fc, lv.fm, lv.steps, lv.jmid, task0, f, u_in, u_out,
@@ -1511,10 +1820,39 @@ cudaError_t launch_finish(const Launch &L, int what, const double *partials, int
 }
 
 cudaError_t launch_axpy_pair(const Launch &L, long n, const Scalars *sc, const double *p, const double *q, double *u,
-                             double *r, double *partials, int n_part, const double *z_old)
+                             double *r, double *partials, int n_part, const double *z_old, float *r32)
 {
     return launch_k(L, z_old ? k_axpy_pair<kThreads, true> : k_axpy_pair<kThreads, false>, n_part, kThreads, 0, sc, p,
-                    q, u, r, (int)n, partials, z_old);
+                    q, u, r, (int)n, partials, z_old, r32);
+}
+
+cudaError_t launch_outer_batch(const Launch &L, int what, const BatchMemberDev *mem, int M, int n_part,
+                               const int *active)
+{
+    if (M <= 0) return cudaSuccess;
+    const int grid = 2 * 8 * L.sm_count;   // 2 x 8 CTAs per SM, each over M n_part / grid virtual blocks
+    switch (what) {
+    case BATCH_NONZERO: return launch_k(L, k_outer_batch<kThreads, BATCH_NONZERO>, grid, kThreads, 0, mem, M, n_part, active);
+    case BATCH_RESIDUAL: return launch_k(L, k_outer_batch<kThreads, BATCH_RESIDUAL>, grid, kThreads, 0, mem, M, n_part, active);
+    case BATCH_DOT_RZ: return launch_k(L, k_outer_batch<kThreads, BATCH_DOT_RZ>, grid, kThreads, 0, mem, M, n_part, active);
+    case BATCH_XPBY: return launch_k(L, k_outer_batch<kThreads, BATCH_XPBY>, grid, kThreads, 0, mem, M, n_part, active);
+    case BATCH_APPLY: return launch_k(L, k_outer_batch<kThreads, BATCH_APPLY>, grid, kThreads, 0, mem, M, n_part, active);
+    case BATCH_AXPY: return launch_k(L, k_outer_batch<kThreads, BATCH_AXPY>, grid, kThreads, 0, mem, M, n_part, active);
+    case BATCH_CLEAR_P: return launch_k(L, k_outer_batch<kThreads, BATCH_CLEAR_P>, grid, kThreads, 0, mem, M, n_part, active);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_finish_batch(const Launch &L, int what, const BatchMemberDev *mem, int M, int n_part,
+                                const int *active, int *go, int partial_offset)
+{
+    if (M <= 0) return cudaSuccess;
+    return launch_k(L, k_finish_batch, M, 256, 0, what, mem, n_part, partial_offset, active, go);
+}
+
+cudaError_t launch_batch_continue(const Launch &L, int M, const int *go, int *active, cudaGraphConditionalHandle cond)
+{
+    return launch_k(L, k_batch_continue, 1, 256, 0, M, go, active, cond);
 }
 
 cudaError_t launch_lincomb(const Launch &L, long n, double a, const double *x, double b, const double *y, double c,

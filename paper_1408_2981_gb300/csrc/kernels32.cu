@@ -8,10 +8,14 @@
 // 2-byte array (the upper face of k is the lower face of k+1).  Each edge
 // coupling is rounded once and used by both of its cells, so the BF16
 // operator is symmetric and still maps constants to beta_hat.  The column
-// blocks' Thomas factors are computed once per level in FP64 from those
-// coefficients (excess-carried pivots) and stored per unknown in FP32.  The
-// outer Krylov vectors stay in FP64: the finest level reads its right-hand
-// side as double and writes its result as double.
+// blocks' Thomas pivots are computed once per level in FP64 from those
+// coefficients (excess-carried pivots) and their reciprocals stored per
+// unknown in FP32; the two multipliers of a row are formed in the pass as the
+// BF16 couplings times that reciprocal (stored as well only with vertical
+// advection, whose couplings differ from alphar_hat).  The outer Krylov
+// vectors stay in FP64: the finest level reads the outer residual in FP32 (a
+// copy written by the kernel that forms it, or the FP64 vector itself) and
+// writes its result as double.
 #include <cuda_runtime.h>
 
 #include "tpmg_internal.h"
@@ -30,12 +34,13 @@ __device__ __forceinline__ float bf(unsigned short h) { return __uint_as_float((
 // m_k = beta_hat + sum_e alphaS_hat_e, couplings c_k = alphar_hat of face k
 // (c_0 = c_{n} = 0) -- from the bottom row upwards:
 //   e_0 = m_0,  e_k = m_k + c_k e_{k-1} / p_{k-1},  p_k = e_k + c_{k+1},
-// stored per unknown in FP32: rinv = 1 / p_k, b = c_k / p_k (b_0 = 0) and
-// g = c_{k+1} / p_k, so that A_T x = d is
+// stored per unknown in FP32: rinv = 1 / p_k, and, where fb / fg are given (vertical
+// advection), b = c_k / p_k (b_0 = 0) and g = c_{k+1} / p_k, so that A_T x = d is
 //   y_k = d_k rinv_k + b_k y_{k-1},   x_k = y_k + g_k x_{k+1}.
-// With vertical advection (cxv: X of face k in BF16, dr the row thickness) row k
-// couples downwards with c_k - dr_k X_k and upwards with c_{k+1} + dr_k X_{k+1}, in
-// place of c_k and c_{k+1}.
+// Without advection the relaxation forms b = c_k rinv_k and g = c_{k+1} rinv_k
+// itself from the BF16 couplings (exact in FP32).  With vertical advection (cxv: X
+// of face k in BF16, dr the row thickness) row k couples downwards with
+// c_k - dr_k X_k and upwards with c_{k+1} + dr_k X_{k+1}, in place of c_k and c_{k+1}.
 __global__ void k_thomas_factors32(int n_cells, const bf16x4 *__restrict__ cpack,
                                    const unsigned short *__restrict__ cvert, const unsigned short *__restrict__ cxv,
                                    const double *__restrict__ dr, int n, float *__restrict__ rinv,
@@ -61,8 +66,8 @@ __global__ void k_thomas_factors32(int n_cells, const bf16x4 *__restrict__ cpack
         e = k == 0 ? m : m + c * e / p;
         p = e + cu;
         rinv[row0 + k] = (float)(1.0 / p);
-        fb[row0 + k] = (float)(c / p);
-        fg[row0 + k] = (float)(cu / p);
+        if (fb) fb[row0 + k] = (float)(c / p);
+        if (fg) fg[row0 + k] = (float)(cu / p);
     }
 }
 
@@ -87,22 +92,18 @@ __global__ void k_thomas_factors32(int n_cells, const bf16x4 *__restrict__ cpack
 // never waits on a serial chain of n_r steps.  Slots are the relaxation
 // tasks' cell lists ([task][16], padding -1), so a colour pass covers slots
 // [16 task0, 16 (task0 + n_tasks)).
-template <int MODE, typename TF, int R>
-__global__ void __launch_bounds__(256)
-    k_relax32_scan(const int *__restrict__ cells, const int4 *__restrict__ tnb, const bf16x4 *__restrict__ cpack,
-                   const float *__restrict__ rinv, const float *__restrict__ fb, const float *__restrict__ fg,
-                   int n_r, int slot0, int n_slots, const TF *__restrict__ f, const float *u_in, float *u_out,
-                   float *__restrict__ u_fine, double *__restrict__ out64, float relax)
+// The column T (neighbour record nb) of one pass, by one warp (the body of
+// k_relax32_scan, shared with the batched form).
+template <int MODE, typename TF, int R, bool SF>
+__device__ __forceinline__ void relax32_column(const bf16x4 *__restrict__ cpack,
+                                               const unsigned short *__restrict__ cvert,
+                                               const float *__restrict__ rinv, const float *__restrict__ fb,
+                                               const float *__restrict__ fg, int n_r,
+                                               const TF *__restrict__ f, const float *u_in, float *u_out,
+                                               float *__restrict__ u_fine, double *__restrict__ out64, float relax,
+                                               int T, int4 nb, int lane)
 {
     const unsigned full = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    // the column's cell and neighbours are set-up data: read before the wait
-    const int T = w < n_slots ? __ldg(&cells[slot0 + w]) : -1;
-    const int4 nb = MODE == PASS_RHS_ONLY || T < 0 ? make_int4(0, 0, 0, 0) : __ldg(&tnb[slot0 + w]);
-    pdl_wait();
-    pdl_trigger();
-    if (T < 0) return;
     const bool n0 = MODE == PASS_NORMAL || (nb.w & 1), n1 = MODE == PASS_NORMAL || (nb.w & 2),
                n2 = MODE == PASS_NORMAL || (nb.w & 4);
     const size_t base = (size_t)T * n_r;
@@ -112,13 +113,20 @@ __global__ void __launch_bounds__(256)
     // lane k mod 32 and the 32-row segments are scanned one after another
     constexpr bool CH = R == 2;
     auto row = [&](int r) { return CH ? 2 * lane + r : 32 * r + lane; };
-    float x[R];
+    // the multipliers of row k: c_k rinv_k below and c_{k+1} rinv_k above (SF: the
+    // stored ones, with advection).  Face 0 of every column stores the coupling 0 (no
+    // flux through the bottom), which is also face n_r of the column before, and one
+    // zero element follows the level's last column, so both loads are unconditional.
+    auto below = [&](int k, size_t i, float ri) { return SF ? __ldg(&fb[i]) : bf(__ldg(&cvert[i])) * ri; };
+    auto above = [&](int k, size_t i, float ri) { return SF ? __ldg(&fg[i]) : bf(__ldg(&cvert[i + 1])) * ri; };
+    float x[R], ri[R];
     if (CH) {
         float P[R];
 #pragma unroll
         for (int j = 0; j < R; ++j) {
             const int k = row(j);
             float t = 0.f, b = 1.f;
+            ri[j] = 0.f;
             if (k < n_r) {
                 const size_t i = base + k;
                 float d = (float)f[i];
@@ -129,8 +137,9 @@ __global__ void __launch_bounds__(256)
                     const float v2 = n2 ? u_in[(size_t)nb.z * n_r + k] : 0.f;
                     d = fmaf(bf(cp.z), v2, fmaf(bf(cp.y), v1, fmaf(bf(cp.x), v0, d)));
                 }
-                t = d * __ldg(&rinv[i]);
-                b = __ldg(&fb[i]);
+                ri[j] = __ldg(&rinv[i]);
+                t = d * ri[j];
+                b = below(k, i, ri[j]);
             }
             x[j] = j == 0 ? t : fmaf(b, x[j - 1], t);
             P[j] = j == 0 ? b : P[j - 1] * b;
@@ -153,7 +162,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int j = R - 1; j >= 0; --j) {
             const int k = row(j);
-            const float c = k < n_r ? __ldg(&fg[base + k]) : 0.f;
+            const float c = k < n_r ? above(k, base + k, ri[j]) : 0.f;
             if (k >= n_r) x[j] = 0.f;
             if (j < R - 1) x[j] = fmaf(c, x[j + 1], x[j]);
             P[j] = j == R - 1 ? c : c * P[j + 1];
@@ -180,6 +189,7 @@ __global__ void __launch_bounds__(256)
         for (int r = 0; r < R; ++r) {
             const int k = 32 * r + lane;
             float A = 0.f, B = 0.f;
+            ri[r] = 0.f;
             if (k < n_r) {
                 const size_t i = base + k;
                 float d = (float)f[i];
@@ -190,8 +200,9 @@ __global__ void __launch_bounds__(256)
                     const float v2 = n2 ? u_in[(size_t)nb.z * n_r + k] : 0.f;
                     d = fmaf(bf(cp.z), v2, fmaf(bf(cp.y), v1, fmaf(bf(cp.x), v0, d)));
                 }
-                B = d * __ldg(&rinv[i]);
-                A = __ldg(&fb[i]);
+                ri[r] = __ldg(&rinv[i]);
+                B = d * ri[r];
+                A = below(k, i, ri[r]);
             }
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -211,7 +222,7 @@ __global__ void __launch_bounds__(256)
             const int k = 32 * r + lane;
             float A = 0.f, B = 0.f;
             if (k < n_r) {
-                A = __ldg(&fg[base + k]);
+                A = above(k, base + k, ri[r]);
                 B = x[r];
             }
 #pragma unroll
@@ -248,18 +259,77 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+template <int MODE, typename TF, int R, bool SF>
+__global__ void __launch_bounds__(256)
+    k_relax32_scan(const int *__restrict__ cells, const int4 *__restrict__ tnb, const bf16x4 *__restrict__ cpack,
+                   const unsigned short *__restrict__ cvert, const float *__restrict__ rinv,
+                   const float *__restrict__ fb, const float *__restrict__ fg, int n_r, int slot0, int n_slots,
+                   const TF *__restrict__ f, const float *u_in, float *u_out, float *__restrict__ u_fine,
+                   double *__restrict__ out64, float relax)
+{
+    const int lane = threadIdx.x & 31;
+    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    // the column's cell and neighbours are set-up data: read before the wait
+    const int T = w < n_slots ? __ldg(&cells[slot0 + w]) : -1;
+    const int4 nb = MODE == PASS_RHS_ONLY || T < 0 ? make_int4(0, 0, 0, 0) : __ldg(&tnb[slot0 + w]);
+    pdl_wait();
+    pdl_trigger();
+    if (T < 0) return;
+    relax32_column<MODE, TF, R, SF>(cpack, cvert, rinv, fb, fg, n_r, f, u_in, u_out, u_fine, out64, relax, T, nb,
+                                    lane);
+}
+
+// Index of the work-list item of a warp-uniform position x: the last item whose first
+// position off[it] (ascending, off[0] = 0) is <= x.  A binary search over the launch's
+// parameter block: every lane of the warp reads the same entries (broadcast from the
+// constant cache), with no global-memory round trip before the column's own loads.
+__device__ __forceinline__ int batch_item(const int *off, int n_items, int x)
+{
+    int lo = 0, hi = n_items - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= x)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// One pass of the batched form: the columns of several members' colour passes of one
+// mode, right-hand-side type and rows-per-lane class in one launch.  Warp w relaxes
+// slot w - woff[it] of item it, with that item's level data and vectors, exactly as
+// k_relax32_scan does for the item's own pass; members whose loop has stopped
+// (active == 0) are skipped.
+template <int MODE, typename TF, int R>
+__global__ void __launch_bounds__(256) k_relax32_batch(const __grid_constant__ RelaxBatchArgs a,
+                                                       const int *__restrict__ active)
+{
+    const int lane = threadIdx.x & 31;
+    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int it = batch_item(a.off, a.n_items, w);
+    const BatchRelaxItem &I = a.items[it];
+    const int ws = w - a.off[it];
+    const int T = ws < I.n_slots ? __ldg(&I.cells[I.slot0 + ws]) : -1;
+    const int4 nb = MODE == PASS_RHS_ONLY || T < 0 ? make_int4(0, 0, 0, 0) : __ldg(&I.tnb[I.slot0 + ws]);
+    pdl_wait();
+    pdl_trigger();
+    if (T < 0 || !active[I.member]) return;
+    relax32_column<MODE, TF, R, false>(I.cpack, I.cvert, I.rinv, nullptr, nullptr, I.n_r,
+                                       static_cast<const TF *>(I.f), I.u_in, I.u_out, I.u_fine, I.out64, I.relax, T,
+                                       nb, lane);
+}
+
 // f_c[T][k] = sum_j (f - A u)[4T + j][k] in FP32 with the BF16 stencil, the row
 // in the flux form of Appendix A (Algorithm 1 residual + restriction).
 template <typename TF>
-__global__ void __launch_bounds__(kThreads32)
-    k_resid_restrict32(const int4 *__restrict__ nbr, const bf16x4 *__restrict__ cpack,
-                       const unsigned short *__restrict__ cvert, const unsigned short *__restrict__ cxv,
-                       const float *__restrict__ dr32, int n_r, const TF *__restrict__ f,
-                       const float *__restrict__ u, float *__restrict__ fc, int Nc)
+__device__ __forceinline__ void restrict32_row(const int4 *__restrict__ nbr, const bf16x4 *__restrict__ cpack,
+                                               const unsigned short *__restrict__ cvert,
+                                               const unsigned short *__restrict__ cxv, const float *__restrict__ dr32,
+                                               int n_r, const TF *__restrict__ f, const float *__restrict__ u,
+                                               float *__restrict__ fc, int ic)
 {
-    pdl_wait();
-    pdl_trigger();
-    for (int ic = blockIdx.x * kThreads32 + threadIdx.x; ic < Nc; ic += gridDim.x * kThreads32) {
+    {
         const int Tc = ic / n_r, k = ic - Tc * n_r;
         float s = 0.f;
 #pragma unroll
@@ -284,6 +354,40 @@ __global__ void __launch_bounds__(kThreads32)
             s += (float)f[i] - a;
         }
         fc[ic] = s;
+    }
+}
+
+template <typename TF>
+__global__ void __launch_bounds__(kThreads32)
+    k_resid_restrict32(const int4 *__restrict__ nbr, const bf16x4 *__restrict__ cpack,
+                       const unsigned short *__restrict__ cvert, const unsigned short *__restrict__ cxv,
+                       const float *__restrict__ dr32, int n_r, const TF *__restrict__ f,
+                       const float *__restrict__ u, float *__restrict__ fc, int Nc)
+{
+    pdl_wait();
+    pdl_trigger();
+    for (int ic = blockIdx.x * kThreads32 + threadIdx.x; ic < Nc; ic += gridDim.x * kThreads32)
+        restrict32_row<TF>(nbr, cpack, cvert, cxv, dr32, n_r, f, u, fc, ic);
+}
+
+// Residual + restriction of the batched form: the coarse rows of several members'
+// restrictions in one launch.  Each item's rows occupy a range of the launch's
+// positions starting at roff[it], a multiple of 32, so that a warp's positions belong
+// to one item; position x is coarse row x - roff[it] of that item.
+template <typename TF>
+__global__ void __launch_bounds__(kThreads32) k_restrict32_batch(const __grid_constant__ RestrictBatchArgs a,
+                                                                 int total, const int *__restrict__ active)
+{
+    pdl_wait();
+    pdl_trigger();
+    const int lane = threadIdx.x & 31;
+    for (int x0 = (blockIdx.x * kThreads32 + threadIdx.x) & ~31; x0 < total; x0 += gridDim.x * kThreads32) {
+        const int it = batch_item(a.off, a.n_items, x0);
+        const BatchRestrictItem &I = a.items[it];
+        const int ic = x0 + lane - a.off[it];
+        if (ic < I.Nc && active[I.member])
+            restrict32_row<TF>(I.nbr, I.cpack, I.cvert, nullptr, nullptr, I.n_r, static_cast<const TF *>(I.f), I.u,
+                               I.fc, ic);
     }
 }
 
@@ -340,9 +444,11 @@ cudaError_t relax32_r(const Launch &L, const LevelDev &lv, int task0, int n_task
     const int var = lv.relax_variant < 0 ? RELAX_CTA128 : lv.relax_variant;
     const int wpb = 1 << var;
     const int n_slots = n_tasks * kRelaxCols;
-    return launch_k(L, k_relax32_scan<MODE, TF, R>, (n_slots + wpb - 1) / wpb, 32 * wpb, 0, lv.task_cells,
-                    lv.task_nbr, lv.cpack, lv.rinv32, lv.fb32, lv.fc32, L.n_r, task0 * kRelaxCols, n_slots, f, u_in,
-                    u_out, u_fine, out64, relax);
+    // the stored multipliers only with vertical advection (their couplings are not alphar_hat)
+    auto kern = lv.cxv_on ? k_relax32_scan<MODE, TF, R, true> : k_relax32_scan<MODE, TF, R, false>;
+    return launch_k(L, kern, (n_slots + wpb - 1) / wpb, 32 * wpb, 0, lv.task_cells, lv.task_nbr, lv.cpack, lv.cvert,
+                    lv.rinv32, lv.fb32, lv.fc32, L.n_r, task0 * kRelaxCols, n_slots, f, u_in, u_out, u_fine, out64,
+                    relax);
 }
 
 template <int MODE, typename TF>
@@ -381,6 +487,42 @@ cudaError_t launch_resid_restrict32(const Launch &L, const LevelDev &fine, const
                     fine.cxv_on ? fine.cxv : nullptr, L.dr32, L.n_r, f, u, fc, Nc);
 }
 
+template <int MODE, typename TF>
+cudaError_t relax32_batch_t(const Launch &L, int n_r_max, const RelaxBatchArgs &a, long total_warps, int wpb,
+                            const int *active)
+{
+    const unsigned grid = (unsigned)((total_warps + wpb - 1) / wpb);
+    const int nt = 32 * wpb;
+    // the items of a launch share the rows-per-lane class of their column height
+    if (n_r_max <= 32) return launch_k(L, k_relax32_batch<MODE, TF, 1>, grid, nt, 0, a, active);
+    if (n_r_max <= 64) return launch_k(L, k_relax32_batch<MODE, TF, 2>, grid, nt, 0, a, active);
+    if (n_r_max <= 128) return launch_k(L, k_relax32_batch<MODE, TF, 4>, grid, nt, 0, a, active);
+    if (n_r_max <= 256) return launch_k(L, k_relax32_batch<MODE, TF, 8>, grid, nt, 0, a, active);
+    if (n_r_max <= 512) return launch_k(L, k_relax32_batch<MODE, TF, 16>, grid, nt, 0, a, active);
+    return launch_k(L, k_relax32_batch<MODE, TF, 32>, grid, nt, 0, a, active);
+}
+
+template <typename TF>
+cudaError_t launch_relax32_batch(const Launch &L, int mode, int n_r_max, const RelaxBatchArgs &a, long total_warps,
+                                 int wpb, const int *active)
+{
+    if (a.n_items <= 0 || total_warps <= 0) return cudaSuccess;
+    if (a.n_items > kBatchItems || (wpb != 1 && wpb != 2 && wpb != 4 && wpb != 8)) return cudaErrorInvalidValue;
+    switch (mode) {
+    case PASS_ZERO: return relax32_batch_t<PASS_ZERO, TF>(L, n_r_max, a, total_warps, wpb, active);
+    case PASS_RHS_ONLY: return relax32_batch_t<PASS_RHS_ONLY, TF>(L, n_r_max, a, total_warps, wpb, active);
+    default: return relax32_batch_t<PASS_NORMAL, TF>(L, n_r_max, a, total_warps, wpb, active);
+    }
+}
+
+template <typename TF>
+cudaError_t launch_restrict32_batch(const Launch &L, const RestrictBatchArgs &a, long total, const int *active)
+{
+    if (a.n_items <= 0 || total <= 0) return cudaSuccess;
+    if (a.n_items > kBatchItems) return cudaErrorInvalidValue;
+    return launch_k(L, k_restrict32_batch<TF>, grid32(total, L.sm_count), kThreads32, 0, a, (int)total, active);
+}
+
 cudaError_t launch_prolong_add32(const Launch &L, const LevelDev &fine, const float *uc, float *u)
 {
     const int N = fine.n * L.n_r;
@@ -398,7 +540,8 @@ cudaError_t launch_prolong_linear32(const Launch &L, const LevelDev &fine, const
 cudaError_t launch_thomas_factors32(const Launch &L, const LevelDev &lv)
 {
     k_thomas_factors32<<<(lv.n + 127) / 128, 128, 0, L.s>>>(lv.n, lv.cpack, lv.cvert, lv.cxv_on ? lv.cxv : nullptr,
-                                                            L.dr, L.n_r, lv.rinv32, lv.fb32, lv.fc32);
+                                                            L.dr, L.n_r, lv.rinv32, lv.cxv_on ? lv.fb32 : nullptr,
+                                                            lv.cxv_on ? lv.fc32 : nullptr);
     return cudaGetLastError();
 }
 
@@ -411,6 +554,12 @@ template cudaError_t launch_relax32<double>(const Launch &, const LevelDev &, in
                                             const float *, float *, float *, double *);
 template cudaError_t launch_relax32<float>(const Launch &, const LevelDev &, int, int, int, float, const float *,
                                            const float *, float *, float *, double *);
+template cudaError_t launch_relax32_batch<double>(const Launch &, int, int, const RelaxBatchArgs &, long, int,
+                                                  const int *);
+template cudaError_t launch_relax32_batch<float>(const Launch &, int, int, const RelaxBatchArgs &, long, int,
+                                                 const int *);
+template cudaError_t launch_restrict32_batch<double>(const Launch &, const RestrictBatchArgs &, long, const int *);
+template cudaError_t launch_restrict32_batch<float>(const Launch &, const RestrictBatchArgs &, long, const int *);
 template cudaError_t launch_resid_restrict32<double>(const Launch &, const LevelDev &, const LevelDev &,
                                                      const double *, const float *, float *);
 template cudaError_t launch_resid_restrict32<float>(const Launch &, const LevelDev &, const LevelDev &, const float *,

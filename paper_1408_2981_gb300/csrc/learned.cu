@@ -308,12 +308,13 @@ __global__ void k_net_output(const float *__restrict__ y, long n, const double *
 
 // judge of the initial guess: if the finish kernel rejected it, u = 0 and r = f
 __global__ void k_judge_reset(const Scalars *__restrict__ sc, long n, const double *__restrict__ f,
-                              double *__restrict__ u, double *__restrict__ r)
+                              double *__restrict__ u, double *__restrict__ r, float *__restrict__ r32)
 {
     if (!(sc->info & 2)) return;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
         u[i] = 0.0;
         r[i] = f[i];
+        if (r32) r32[i] = (float)f[i];
     }
 }
 
@@ -589,9 +590,10 @@ cudaError_t launch_net_output(const Launch &L, const float *y, long n, const dou
     return cudaGetLastError();
 }
 
-cudaError_t launch_judge_reset(const Launch &L, const Scalars *sc, long n, const double *f, double *u, double *r)
+cudaError_t launch_judge_reset(const Launch &L, const Scalars *sc, long n, const double *f, double *u, double *r,
+                               float *r32)
 {
-    k_judge_reset<<<grid_1d(n, 256, L.sm_count), 256, 0, L.s>>>(sc, n, f, u, r);
+    k_judge_reset<<<grid_1d(n, 256, L.sm_count), 256, 0, L.s>>>(sc, n, f, u, r, r32);
     return cudaGetLastError();
 }
 

@@ -84,9 +84,13 @@ struct VertDev {            // vertical factors shared by every level (no vertic
 constexpr int kRelaxCols = 16;
 
 // Kernel variants of a relaxation pass (chosen per level by the autotuner).
-// FP64: one warp per 16-column task, or one CTA of 64 / 128 / 256 threads per
-// task.  FP32: one warp per column in CTAs of 1 / 2 / 4 / 8 warps.
-enum RelaxVariant { RELAX_WARP = 0, RELAX_CTA64 = 1, RELAX_CTA128 = 2, RELAX_CTA256 = 3, RELAX_VARIANTS = 4 };
+// FP64: one warp per 16-column task, one CTA of 64 / 128 / 256 threads per task,
+// or warp-specialised CTAs (two gathering warps, one solving warp) over strided
+// tasks.  FP32: one warp per column in CTAs of 1 / 2 / 4 / 8 warps (the first
+// four variants).
+enum RelaxVariant { RELAX_WARP = 0, RELAX_CTA64 = 1, RELAX_CTA128 = 2, RELAX_CTA256 = 3, RELAX_PIPE = 4,
+                    RELAX_VARIANTS = 5 };
+constexpr int kRelaxVariants32 = 4;
 
 struct LevelDev {
     int n = 0;              // cells
@@ -158,9 +162,12 @@ struct LevelDev {
     // mixed-precision form: the stencil stored per unknown in BF16 (full
     // storage, Sec. 4.2) and FP32 work vectors on every level
     bf16x4 *cpack = nullptr;        // [n][n_r] {alphaS_hat e = 0, 1, 2, beta_hat}
-    unsigned short *cvert = nullptr;   // [n][n_r] alphar_hat of face k (coupling to level k-1)
+    unsigned short *cvert = nullptr;   // [n][n_r] alphar_hat of face k (coupling to level k-1; 0 for k = 0),
+                                       // followed by one 0 (face n_r of the last column)
     // Thomas factors of the BF16 column blocks in FP32, per unknown [n][n_r] (bottom-up
-    // elimination): rinv32 = 1 / p_k, fb32 = c_k / p_k, fc32 = c_{k+1} / p_k
+    // elimination): rinv32 = 1 / p_k; with vertical advection also the multipliers
+    // fb32 = c_k / p_k, fc32 = c_{k+1} / p_k (allocated with the advection; without it
+    // the relaxation forms them from cvert and rinv32)
     float *rinv32 = nullptr, *fb32 = nullptr, *fc32 = nullptr;
     float *f32 = nullptr, *u32 = nullptr, *u2_32 = nullptr;
 };
@@ -188,6 +195,68 @@ struct LoopCtl {
     double rtol;                       // stop when sqrt(||r||^2 / ||r_0||^2) <= rtol (as the host loop)
     int max_iter;
     double *hist;                      // [max_iter + 1] ||r_k|| / ||r_0|| (device), or NULL
+    int *go = nullptr;                 // member of a batched solve: the decision goes here, not to cond
+};
+
+// ---------------------------------------------------------------------------
+// Batched form (tpmg_batch with the work-list schedule): one launch per step of the
+// V-cycle covers that step's passes of every member, each pass an item of the
+// launch's work list; the outer Krylov kernels loop over the members' virtual blocks.
+// ---------------------------------------------------------------------------
+constexpr int kBatchItems = 64;   // items per launch (two ballots of the lanes' entries)
+
+struct BatchRelaxItem {     // one member's colour pass (or Jacobi sweep) of the FP32 V-cycle
+    const int *cells;       // the level's task cell lists; the pass covers slots [slot0, slot0 + n_slots)
+    const int4 *tnb;
+    const bf16x4 *cpack;
+    const unsigned short *cvert;
+    const float *rinv;
+    const void *f;          // double (the member's finest level) or float
+    const float *u_in;
+    float *u_out, *u_fine;  // u_fine: the next finer level's iterate (fused prolongation), or null
+    double *out64;          // the member's z on its finest level's last pass, or null
+    int n_r, slot0, n_slots, member;
+    float relax;
+};
+
+struct BatchRestrictItem {  // one member's FP32 residual + restriction
+    const int4 *nbr;
+    const bf16x4 *cpack;
+    const unsigned short *cvert;
+    const void *f;          // double (finest level) or float
+    const float *u;
+    float *fc;
+    int n_r, Nc, member;
+};
+
+// The work list of one launch, passed by value as the kernel's parameter (about 7 KB,
+// read through the constant cache): items [n_items] with their first warps / positions.
+struct RelaxBatchArgs {
+    int n_items;
+    int off[kBatchItems];   // first warp of each item (ascending, off[0] = 0)
+    BatchRelaxItem items[kBatchItems];
+};
+struct RestrictBatchArgs {
+    int n_items;
+    int off[kBatchItems];   // first position of each item (multiples of 32, ascending, off[0] = 0)
+    BatchRestrictItem items[kBatchItems];
+};
+
+struct BatchMemberDev {     // one member's outer FP64 iteration (finest level, factorised operator)
+    const int4 *nbr;
+    const dbl4 *g;
+    const double *area, *area_r, *om, *oc;
+    const double *vol, *w, *hr;
+    int n_r, N;
+    const double *f;
+    double *u, *r, *z, *p, *q;
+    float *r32;             // r in FP32: the right-hand side of the finest level's V-cycle passes
+    double *partials;       // [2 n_part]
+    int *zflags;            // [n_part]
+    Scalars *sc;
+    double *hist;           // [kHistCap]
+    double rtol;
+    int max_iter;
 };
 
 // kernels.cu launchers ------------------------------------------------------
@@ -241,8 +310,10 @@ enum PassMode { PASS_NORMAL = 0, PASS_ZERO = 1, PASS_RHS_ONLY = 2 };
 cudaError_t launch_apply(const Launch &L, const LevelDev &lv, const VertDev &v, const double *x, double *y,
                          double *partials, int n_part);
 // nz (optional): per-block flags of launch_nonzero over u, n_part of them
+// r32 (optional): r also in FP32 (the mixed V-cycle's copy of the outer residual)
 cudaError_t launch_residual(const Launch &L, const LevelDev &lv, const VertDev &v, const double *f,
-                            const double *u, double *r, double *partials, int n_part, const int *nz = nullptr);
+                            const double *u, double *r, double *partials, int n_part, const int *nz = nullptr,
+                            float *r32 = nullptr);
 cudaError_t launch_nonzero(const Launch &L, long n, const double *x, int *nz, int n_blocks);
 cudaError_t launch_resid_restrict(const Launch &L, const LevelDev &fine, const LevelDev &coarse, const VertDev &v,
                                   const double *f, const double *u, double *fc);
@@ -277,11 +348,31 @@ cudaError_t launch_finish(const Launch &L, int what, const double *partials, int
                           const LoopCtl *loop = nullptr);
 // z_old != NULL (flexible CG): also partials of <r_new, z_old> in partials[n_part..2 n_part)
 cudaError_t launch_axpy_pair(const Launch &L, long n, const Scalars *sc, const double *p, const double *q, double *u,
-                             double *r, double *partials, int n_part, const double *z_old);
+                             double *r, double *partials, int n_part, const double *z_old, float *r32 = nullptr);
 cudaError_t launch_xpby(const Launch &L, long n, const Scalars *sc, const double *z, double *p);
 // out = a x + b y + c z (y, z nullable: terms dropped); out may alias x, y or z elementwise
 cudaError_t launch_lincomb(const Launch &L, long n, double a, const double *x, double b, const double *y, double c,
                            const double *z, double *out);
+
+// Batched form.  Relaxation: one launch per (mode, right-hand-side type, rows per lane)
+// over args.n_items <= kBatchItems items, total_warps the sum of their slots, wpb warps
+// per CTA.  Restriction: total the end of the last item's range of positions.
+template <typename TF>
+cudaError_t launch_relax32_batch(const Launch &L, int mode, int n_r_max, const RelaxBatchArgs &args, long total_warps,
+                                 int wpb, const int *active);
+template <typename TF>
+cudaError_t launch_restrict32_batch(const Launch &L, const RestrictBatchArgs &args, long total, const int *active);
+// The outer kernels over the M members (each member's n_part virtual blocks, skipped
+// where active[m] == 0).  what: BATCH_* below; finish: FIN_* with the members' loop
+// decisions written to go[m].
+enum BatchOuter { BATCH_NONZERO = 0, BATCH_RESIDUAL = 1, BATCH_DOT_RZ = 2, BATCH_XPBY = 3, BATCH_APPLY = 4,
+                  BATCH_AXPY = 5, BATCH_CLEAR_P = 6 };
+cudaError_t launch_outer_batch(const Launch &L, int what, const BatchMemberDev *mem, int M, int n_part,
+                               const int *active);
+cudaError_t launch_finish_batch(const Launch &L, int what, const BatchMemberDev *mem, int M, int n_part,
+                                const int *active, int *go, int partial_offset);
+// active[m] = go[m] for every member, and the batch loop's condition = any member active
+cudaError_t launch_batch_continue(const Launch &L, int M, const int *go, int *active, cudaGraphConditionalHandle cond);
 
 // noalloc.cu: device address of the fixed scratch array of
 // tpmg_vcycle_noalloc on `device`, which must be the current device (looked
@@ -325,7 +416,8 @@ cudaError_t launch_net_features(const Launch &L, const LevelDev &lv, const float
 cudaError_t launch_net_targets(const Launch &L, const double *u, const int *cells, long rows, const double *s, float *t);
 template <typename TO>
 cudaError_t launch_net_output(const Launch &L, const float *y, long n, const double *s, TO *u);
-cudaError_t launch_judge_reset(const Launch &L, const Scalars *sc, long n, const double *f, double *u, double *r);
+cudaError_t launch_judge_reset(const Launch &L, const Scalars *sc, long n, const double *f, double *u, double *r,
+                               float *r32 = nullptr);
 cudaError_t launch_to_f32(const Launch &L, long n, const double *x, float *y);
 
 }  // namespace tpmg

@@ -51,7 +51,8 @@ def test_default_params_on_host(lib):
                                  dict(omega2=0.0, courant_c=0.0), dict(nu_pre=-1), dict(smoother=7),
                                  dict(relax=0.0), dict(relax=2.0), dict(centre=3), dict(coeff_storage=9),
                                  dict(precision=9), dict(precision=1, coeff_storage=0), dict(precision=1, coeff_storage=2), dict(prolongation=2),
-                                 dict(refinement=9, n_levels=3, n_r=1024), dict(scan_max_cells=-1), dict(outer=3)])
+                                 dict(refinement=9, n_levels=3, n_r=1024), dict(scan_max_cells=-1), dict(outer=3),
+                                 dict(relax_variant=-2), dict(relax_variant=5), dict(relax_variant=4, precision=1, coeff_storage=1)])
 def test_setup_rejects_bad_params_before_touching_cuda(lib, bad):
     p = binding.default_params(**bad)
     h = ctypes.c_void_p()

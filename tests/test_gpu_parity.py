@@ -263,3 +263,56 @@ def test_graph_replay_matches_direct_launches():
     assert len(set(its)) == 1
     for o in outs[1:]:
         np.testing.assert_array_equal(o, outs[0])
+
+
+# The FP64 relaxation kernels of the twisted 16-column tasks (tpmg_query_tuning's
+# variants 0-4, forced with relax_variant) perform the same arithmetic per column, so
+# whole solves agree bit for bit.  The cases put each kernel through its paths: a
+# finest level of 2548 tasks per colour, so the warp-specialised CTAs (variant 4) walk
+# several tasks each and reuse both tiles; twisted tasks on every level
+# (scan_max_cells = 0), so the fused prolongation and the small coarse passes run
+# through each variant; block Jacobi with a relaxation weight; the stencil stored per
+# unknown (TPMG^full); a column of 160 levels.
+VARIANT_CASES = {
+    "ref6_nr16_many_tasks": dict(refinement=6, n_levels=2, n_r=16, grading=1.05, courant_c=80.0),
+    "ref4_nr24_twisted_everywhere_jacobi": dict(refinement=4, n_levels=5, n_r=24, grading=1.05, courant_c=30.0,
+                                                smoother=1, relax=0.7, scan_max_cells=0),
+    "ref5_nr40_full_storage": dict(refinement=5, n_levels=3, n_r=40, courant_c=20.0, coeff_storage=1,
+                                   scan_max_cells=0),
+    "ref3_nr160_tall": dict(refinement=3, n_levels=3, n_r=160, grading=1.02, courant_c=8.0, scan_max_cells=0),
+}
+
+
+@pytest.mark.parametrize("name", sorted(VARIANT_CASES))
+def test_relaxation_variants_give_identical_results(name):
+    kw = VARIANT_CASES[name]
+    outs = []
+    for variant in range(5):
+        s = binding.Solver(relax_variant=variant, **kw)
+        assert all(v == variant for v, _ in s.tuning())
+        f = torch.from_numpy(inputs.uniform_pm1(inputs.SEED_UNIFORM_SMALL + 60, s.N)).cuda()
+        u = torch.zeros_like(f)
+        st, it, rel, _ = s.solve(f, u, rtol=1e-8, max_iter=200)
+        z = torch.empty_like(f)
+        s.vcycle(f, z)
+        torch.cuda.synchronize()
+        outs.append((st, it, rel, u.cpu().numpy(), z.cpu().numpy()))
+        s.close()
+    for v in range(1, 5):
+        assert outs[v][:3] == outs[0][:3], (v, outs[v][:3], outs[0][:3])
+        np.testing.assert_array_equal(outs[v][3], outs[0][3])
+        np.testing.assert_array_equal(outs[v][4], outs[0][4])
+
+
+def test_warp_specialised_relaxation_vs_oracle():
+    """The V-cycle with the warp-specialised twisted passes on every level against the
+    oracle's V-cycle (the V-cycle bound of this file)."""
+    kw = VARIANT_CASES["ref4_nr24_twisted_everywhere_jacobi"]
+    s, o = binding.Solver(relax_variant=4, **kw), oracle_for(kw)
+    r = inputs.uniform_pm1(inputs.SEED_UNIFORM_SMALL + 61, s.N)
+    z = torch.full((s.N,), float("nan"), dtype=torch.float64, device="cuda")
+    s.vcycle(cuda(r), z)
+    zg, zo = host(z), o.vcycle(r)
+    e = zg - zo
+    rel_a = np.sqrt(e @ o.apply(e)) / np.sqrt(zo @ o.apply(zo))
+    assert rel_a <= 1e-11, rel_a
