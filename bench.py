@@ -1168,14 +1168,18 @@ def replica_command(argv: list, n: int, port: int) -> list:
 def launcher_check() -> int:
     """Each rank reports how it was started (after a gloo barrier); no GPU is used."""
     world, rank, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
+    line = json.dumps({"launcher_check": True, "rank": rank, "world": world, "local_rank": local})
+    if world <= 1:
+        print(line, flush=True)
+        return 0
+    import torch.distributed as dist
 
-        dist.init_process_group("gloo", init_method="env://")
+    dist.init_process_group("gloo", init_method="env://")
+    for r in range(world):   # one rank at a time, so that the lines do not interleave
+        if r == rank:
+            print(line, flush=True)
         dist.barrier()
-    print(json.dumps({"launcher_check": True, "rank": rank, "world": world, "local_rank": local}), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    dist.destroy_process_group()
     return 0
 
 
