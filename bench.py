@@ -758,6 +758,9 @@ def run_learned(args, wl):
     cfg = dict(wl["learned"])
     if args.pairs:
         cfg["pairs"] = args.pairs
+    if args.levels:   # a shallower hierarchy: the coarsest level is then horizontally coupled
+        wl = dict(wl, params=dict(wl["params"], n_levels=args.levels),
+                  text=wl["text"] + f"; {args.levels} multigrid levels")
     seed = wl["seed"] + 7919 * rank
     t_setup = time.perf_counter()
     data_solver = binding.Solver(stream=stream, graphs=0, **wl["params"])
@@ -1195,6 +1198,9 @@ def main(argv=None):
     ap.add_argument("--no-extra-configs", action="store_true",
                     help="headline workload: skip the other configurations (small case, refinement 7, batch)")
     ap.add_argument("--pairs", type=int, default=None, help="learned workload: training pairs (default 2000)")
+    ap.add_argument("--levels", type=int, default=None,
+                    help="learned workload: multigrid levels (default 6; the coarse network replaces the coarsest "
+                         "level's solve)")
     ap.add_argument("--iters-hint", type=int, default=None,
                     help="reference arm on workloads sampled by one iteration: iterations of a full solve")
     ap.add_argument("--launcher-check", action="store_true",

@@ -147,7 +147,8 @@ typedef struct {
                             launches.  The results are identical. */
     int    relax_variant;/* -1: the autotuner's (or the heuristic's) relaxation kernel per level;
                             0..4 (mixed precision 0..3): that variant of tpmg_query_tuning on every
-                            level, where it applies.  The results are identical. */
+                            level (variant 4 on a warp-scan level: its default CTA shape).  The
+                            results are identical. */
 } tpmg_params;
 
 /* Fills *p with the defaults: refinement 3, n_levels 4, n_r 16, H = 10/6371,
@@ -318,10 +319,19 @@ tpmg_status tpmg_solve_host(tpmg_ctx *ctx, const double *h_f, double *h_u, doubl
  * Errors: INVALID_ARG (NULL, a repeated context outside the work-list form,
  * aliased vectors, other device, a context with vertical advection or linear
  * prolongation), OOM, CUDA. */
-enum { TPMG_BATCH_BRANCHES = 0, TPMG_BATCH_WORKLIST = 1 };
+enum { TPMG_BATCH_AUTO = -1, TPMG_BATCH_BRANCHES = 0, TPMG_BATCH_WORKLIST = 1 };
 typedef struct tpmg_batch tpmg_batch;
 tpmg_status tpmg_batch_create(tpmg_ctx *const *ctxs, int n, const double *const *d_f, double *const *d_u,
                               double rtol, int max_iter, tpmg_batch **out);
+
+/* tpmg_batch_create with the form chosen by the caller: form TPMG_BATCH_AUTO (the
+ * rule of tpmg_batch_create), TPMG_BATCH_BRANCHES, or TPMG_BATCH_WORKLIST
+ * (INVALID_ARG if a member does not qualify); groups = the work-list form's number
+ * of root branches, each a work-list schedule over a share of the members of about
+ * equal size (0: the default; at most n).  Results are those of tpmg_batch_create
+ * bit for bit whatever the form and the groups.  Errors as tpmg_batch_create. */
+tpmg_status tpmg_batch_create_ex(tpmg_ctx *const *ctxs, int n, const double *const *d_f, double *const *d_u,
+                                 double rtol, int max_iter, int form, int groups, tpmg_batch **out);
 
 /* Runs the batch on cuda_stream and waits for it.  iters[i], rel_resid[i]
  * (host, n entries) as tpmg_solve; status (nullable, n entries) per problem;
@@ -343,11 +353,13 @@ tpmg_status tpmg_query(const tpmg_ctx *ctx, int level, int *n_cells, int *n_r, d
 
 /* The autotuner's choice on multigrid level `level`: variant = relaxation kernel
  * (FP64: 0 one warp per 16-column task, 1/2/3 one CTA of 64/128/256 threads per
- * task, 4 warp-specialised CTAs -- two warps gathering the next task while one
- * solves the current one -- over strided tasks; mixed precision: one warp per
+ * task, 4 one warp per task with twice the loads in flight (8 elements per lane
+ * in the gather, the solve's multipliers 8 steps ahead); mixed precision: one warp per
  * column in CTAs of 1/2/4/8 warps; -1 heuristic: not tuned) and us[5] =
  * measured microseconds of the level's largest colour pass with each variant
- * (us[4] = 0 in mixed precision).  Any output may be NULL.
+ * (us[4] = 0 where only four apply: mixed precision, and FP64 levels relaxed by
+ * the warp scans, whose variants 0..3 are CTAs of 1/2/4/8 warps).  Any output
+ * may be NULL.
  * Errors: INVALID_ARG. */
 tpmg_status tpmg_query_tuning(const tpmg_ctx *ctx, int level, int *variant, float *us);
 
@@ -421,12 +433,13 @@ tpmg_status tpmg_profile_read(tpmg_ctx *ctx, int kernel_class, long long *launch
 tpmg_status tpmg_profile_work(tpmg_ctx *ctx, int kernel_class, double *bytes, double *timed_bytes, double *flops,
                               double *timed_flops);
 
-/* Measured FP64 throughput of the current device in TFLOP/s (FMA = 2 flops): a
- * kernel of independent FMA chains fills every SM (as many 256-thread blocks as
- * fit), one warm-up launch, then the best of three launches timed with CUDA
- * events on cuda_stream.  It is the denominator of the FP64-pipe roofline of the
- * FP64 kernels.  The paper has no counterpart: a measurement utility.  Allocates
- * and frees a small device buffer; synchronises the stream; takes about 0.2 s.
+/* Measured FP64 throughput of the current device in TFLOP/s (FMA = 2 flops):
+ * kernels of 2, 4 or 8 independent FMA chains per thread on every SM, with 1, 2,
+ * 4 or the most resident 256-thread blocks per SM; per configuration one warm-up
+ * launch and three launches timed with CUDA events on cuda_stream; the best rate
+ * of all.  It is the denominator of the FP64-pipe roofline of the FP64 kernels.
+ * The paper has no counterpart: a measurement utility.  Allocates and frees a
+ * small device buffer; synchronises the stream; takes about 0.5 s.
  * Errors: INVALID_ARG (tflops NULL), OOM, CUDA. */
 tpmg_status tpmg_fp64_peak(void *cuda_stream, double *tflops);
 

@@ -46,8 +46,9 @@ EXPORTS = ["tpmg_default_params", "tpmg_setup", "tpmg_setup_profiles", "tpmg_set
            "tpmg_solve_host", "tpmg_query", "tpmg_query_tuning", "tpmg_export_mesh", "tpmg_profile", "tpmg_profile_read",
            "tpmg_profile_work", "tpmg_fp64_peak",
            "tpmg_status_string", "tpmg_last_error", "tpmg_destroy", "tpmg_batch_create", "tpmg_batch_run",
-           "tpmg_batch_form", "tpmg_batch_destroy"]
+           "tpmg_batch_create_ex", "tpmg_batch_form", "tpmg_batch_destroy"]
 
+TPMG_BATCH_AUTO = -1
 TPMG_BATCH_BRANCHES = 0
 TPMG_BATCH_WORKLIST = 1
 
@@ -130,6 +131,7 @@ def load(path: str | None = None):
     lib.tpmg_destroy.restype = None
     lib.tpmg_batch_create.argtypes = [P, I, P, P, D, I, ctypes.POINTER(P)]
     lib.tpmg_batch_run.argtypes = [P, P, P, P, P, ctypes.POINTER(ctypes.c_longlong)]
+    lib.tpmg_batch_create_ex.argtypes = [P, I, P, P, D, I, I, I, ctypes.POINTER(P)]
     lib.tpmg_batch_form.argtypes = [P]
     lib.tpmg_batch_form.restype = I
     lib.tpmg_batch_destroy.argtypes = [P]
@@ -566,7 +568,7 @@ class Batch:
     alive while the batch is used.
     """
 
-    def __init__(self, solvers, fs, us, rtol: float = 1e-5, max_iter: int = 100):
+    def __init__(self, solvers, fs, us, rtol: float = 1e-5, max_iter: int = 100, form: str = "auto", groups: int = 0):
         if not (len(solvers) == len(fs) == len(us)) or not solvers:
             raise ValueError("solvers, fs and us must be non-empty lists of equal length")
         self._lib = load()
@@ -577,7 +579,8 @@ class Batch:
         fp = (ctypes.c_void_p * n)(*[s._vec(f, "f") for s, f in zip(solvers, fs)])
         up = (ctypes.c_void_p * n)(*[s._vec(u, "u") for s, u in zip(solvers, us)])
         h = ctypes.c_void_p()
-        st = self._lib.tpmg_batch_create(ctxs, n, fp, up, rtol, max_iter, ctypes.byref(h))
+        fcode = {"auto": TPMG_BATCH_AUTO, "branches": TPMG_BATCH_BRANCHES, "worklist": TPMG_BATCH_WORKLIST}[form]
+        st = self._lib.tpmg_batch_create_ex(ctxs, n, fp, up, rtol, max_iter, fcode, groups, ctypes.byref(h))
         if st != TPMG_OK:
             raise TPMGError(st, "tpmg_batch_create")
         self._h = h

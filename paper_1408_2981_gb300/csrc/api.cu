@@ -158,14 +158,21 @@ struct tpmg_batch {
     // of every member's V-cycle or outer iteration; members may share a context
     int form = TPMG_BATCH_BRANCHES;
     int n_part = 0;
-    BatchMemberDev *d_mem = nullptr;       // [M]
-    int *d_active = nullptr, *d_go = nullptr;   // [M]
     Scalars *h_sc = nullptr;                // [M] pinned host mirror of the members' scalars
     std::vector<Scalars *> d_sc;            // [M] device
-    std::vector<BatchLaunch> launches;      // the V-cycle's launches in order
-    std::vector<RelaxBatchArgs> rargs;      // their work lists (kernel parameters)
-    std::vector<RestrictBatchArgs> cargs;
-    long long wl_init = 0, wl_iter = 0;     // launches of the initial part and of one iteration
+    // The members are split into groups of about equal work; each group is one work-list
+    // schedule with its own loop, a root branch of the graph, so that the groups drift
+    // apart and one group's FP64-bound outer operator overlaps another's HBM-bound V-cycle.
+    struct Group {
+        std::vector<int> members;           // batch members, in the group's order
+        BatchMemberDev *d_mem = nullptr;    // [members]
+        int *d_active = nullptr, *d_go = nullptr;
+        std::vector<BatchLaunch> launches;  // the group's V-cycle launches in order
+        std::vector<RelaxBatchArgs> rargs;  // their work lists (kernel parameters)
+        std::vector<RestrictBatchArgs> cargs;
+        long long init = 0, iter = 0;       // launches of the initial part and of one iteration
+    };
+    std::vector<Group> groups;
     std::vector<void *> allocs;             // device allocations of the work-list form
 };
 
@@ -1717,7 +1724,9 @@ tpmg_status autotune(tpmg_ctx *ctx)
         };
         float best = 0.f;
         int best_var = RELAX_CTA128;
-        for (int var = 0; var < (mixed ? kRelaxVariants32 : RELAX_VARIANTS) && st == TPMG_OK; ++var) {
+        // the warp-scan levels (FP32, and FP64 levels of at most scan_max_cells) have four CTA shapes
+        const int n_var = (mixed || D.scan) ? kRelaxVariants32 : (int)RELAX_VARIANTS;
+        for (int var = 0; var < n_var && st == TPMG_OK; ++var) {
             D.relax_variant = var;
             cudaError_t e = pass();
             if (e == cudaSuccess) e = cudaEventRecord(a, ctx->stream);
@@ -1864,36 +1873,38 @@ cudaError_t balloc(tpmg_batch *b, T **ptr, size_t count)
     return cudaSuccess;
 }
 
-// The batch's V-cycle for every active member: the schedule's launches in order.
-cudaError_t batch_vcycle(const tpmg_batch *b, const Launch &L)
+// A group's V-cycle for every active member: the schedule's launches in order.
+cudaError_t batch_vcycle(const tpmg_batch::Group &G, const Launch &L)
 {
-    for (const BatchLaunch &bl : b->launches) {
+    for (const BatchLaunch &bl : G.launches) {
         cudaError_t e;
         if (bl.kind == 0) {
-            const RelaxBatchArgs &a = b->rargs[bl.args];
-            e = bl.f64 ? launch_relax32_batch<double>(L, bl.mode, bl.n_r_max, a, bl.total, bl.wpb, b->d_active)
-                       : launch_relax32_batch<float>(L, bl.mode, bl.n_r_max, a, bl.total, bl.wpb, b->d_active);
+            const RelaxBatchArgs &a = G.rargs[bl.args];
+            e = bl.f64 ? launch_relax32_batch<double>(L, bl.mode, bl.n_r_max, a, bl.total, bl.wpb, G.d_active)
+                       : launch_relax32_batch<float>(L, bl.mode, bl.n_r_max, a, bl.total, bl.wpb, G.d_active);
         } else {
-            const RestrictBatchArgs &a = b->cargs[bl.args];
-            e = bl.f64 ? launch_restrict32_batch<double>(L, a, bl.total, b->d_active)
-                       : launch_restrict32_batch<float>(L, a, bl.total, b->d_active);
+            const RestrictBatchArgs &a = G.cargs[bl.args];
+            e = bl.f64 ? launch_restrict32_batch<double>(L, a, bl.total, G.d_active)
+                       : launch_restrict32_batch<float>(L, a, bl.total, G.d_active);
         }
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
+constexpr int kBatchGroups = 4;   // root branches of a work-list batch (fewer for small batches)
+
 // Builds the work-list form of a batch whose members all pass worklist_member_ok.
 tpmg_status build_worklist(tpmg_batch *b, tpmg_ctx *const *ctxs, int M, const double *const *d_f, double *const *d_u,
-                           cudaStream_t s)
+                           cudaStream_t s, int groups)
 {
     const int n_part = ctxs[0]->n_part;
     for (int m = 0; m < M; ++m)
         if (ctxs[m]->n_part != n_part) return TPMG_ERR_INVALID_ARG;
     b->form = TPMG_BATCH_WORKLIST;
     b->n_part = n_part;
-    // the members' work vectors: outer FP64 r, z, p, q and every level's FP32 iterate
-    // (and block Jacobi's second buffer), the coarse levels' FP32 right-hand sides
+    // the members' work vectors: outer FP64 r, z, p, q (r also in FP32) and every level's
+    // FP32 iterate (and block Jacobi's second buffer), the coarse levels' FP32 right-hand sides
     std::vector<BatchMemberDev> mem(M);
     std::vector<std::vector<float *>> u32(M), u2(M), f32(M);
     b->d_sc.assign(M, nullptr);
@@ -1923,172 +1934,194 @@ tpmg_status build_worklist(tpmg_batch *b, tpmg_ctx *const *ctxs, int M, const do
             if (balloc(b, &u32[m][l], n) != cudaSuccess || (jac && balloc(b, &u2[m][l], n) != cudaSuccess) ||
                 (l < L - 1 && balloc(b, &f32[m][l], n) != cudaSuccess))
                 return TPMG_ERR_OOM;
-            if (cudaMemsetAsync(u32[m][l], 0, n * sizeof(float), s) != cudaSuccess ||
-                (jac && cudaMemsetAsync(u2[m][l], 0, n * sizeof(float), s) != cudaSuccess) ||
-                (l < L - 1 && cudaMemsetAsync(f32[m][l], 0, n * sizeof(float), s) != cudaSuccess))
-                return TPMG_ERR_CUDA;
         }
-        if (cudaMemsetAsync(x.r, 0, N * sizeof(double), s) != cudaSuccess ||
-            cudaMemsetAsync(x.z, 0, N * sizeof(double), s) != cudaSuccess)
-            return TPMG_ERR_CUDA;
     }
-    // the merged schedule: every member's ops under their keys, steps in key order,
-    // each step split into launches by kernel class
+    auto clear_work = [&]() -> bool {   // every work vector zero (at creation, and after the tuner)
+        for (int m = 0; m < M; ++m) {
+            const long N = ctxs[m]->N;
+            if (cudaMemsetAsync(mem[m].r, 0, N * sizeof(double), s) != cudaSuccess ||
+                cudaMemsetAsync(mem[m].r32, 0, N * sizeof(float), s) != cudaSuccess ||
+                cudaMemsetAsync(mem[m].z, 0, N * sizeof(double), s) != cudaSuccess)
+                return false;
+            for (size_t l = 0; l < u32[m].size(); ++l) {
+                const size_t n = (size_t)ctxs[m]->lv[l].n * ctxs[m]->p.n_r;
+                if (cudaMemsetAsync(u32[m][l], 0, n * sizeof(float), s) != cudaSuccess ||
+                    (u2[m][l] && cudaMemsetAsync(u2[m][l], 0, n * sizeof(float), s) != cudaSuccess) ||
+                    (f32[m][l] && cudaMemsetAsync(f32[m][l], 0, n * sizeof(float), s) != cudaSuccess))
+                    return false;
+            }
+        }
+        return cudaStreamSynchronize(s) == cudaSuccess;
+    };
+    if (!clear_work()) return TPMG_ERR_CUDA;
+    // groups of about equal work: members by decreasing size, each to the lightest group
+    const int G = groups > 0 ? std::min(groups, M) : std::max(1, std::min(M / 2, kBatchGroups));
+    b->groups.assign(G, tpmg_batch::Group{});
+    {
+        std::vector<int> order(M);
+        for (int m = 0; m < M; ++m) order[m] = m;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int c2) { return ctxs[a]->N > ctxs[c2]->N; });
+        std::vector<double> load(G, 0.0);
+        for (int m : order) {
+            const int g = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            b->groups[g].members.push_back(m);
+            load[g] += (double)ctxs[m]->N;
+        }
+        for (auto &grp : b->groups) std::sort(grp.members.begin(), grp.members.end());   // the caller's order
+    }
+    // each group's merged schedule: its members' ops under their keys, steps in key order,
+    // each step split into launches by kernel class; item member = index within the group
     struct Tagged {
         std::array<int, 4> key;
-        int member;
+        int member;   // within the group
         VOp op;
     };
-    std::vector<Tagged> all;
-    for (int m = 0; m < M; ++m) {
-        std::vector<VOp> ops;
-        const tpmg_ctx *c = ctxs[m];
-        member_ops(c, c->p.n_levels - 1, true, -1, ops);
-        for (const VOp &o : ops) all.push_back(Tagged{op_key(o), m, o});
-    }
-    std::stable_sort(all.begin(), all.end(), [](const Tagged &a, const Tagged &b2) { return a.key < b2.key; });
-    for (size_t i0 = 0; i0 < all.size();) {
-        size_t i1 = i0;
-        while (i1 < all.size() && all[i1].key == all[i0].key) ++i1;
-        // launch classes of the step: (kind, mode, f64, rows class)
-        std::vector<std::array<int, 4>> classes;
-        for (size_t i = i0; i < i1; ++i) {
-            const Tagged &t = all[i];
-            const tpmg_ctx *c = ctxs[t.member];
-            const bool f64 = false;   // the finest level reads the member's FP32 copy of r
-            const std::array<int, 4> cl{t.op.kind, t.op.kind == 0 ? t.op.mode : 0, f64 ? 1 : 0,
-                                        t.op.kind == 0 ? rows_class(c->p.n_r) : 0};
-            if (std::find(classes.begin(), classes.end(), cl) == classes.end()) classes.push_back(cl);
+    for (tpmg_batch::Group &grp : b->groups) {
+        const int Mg = (int)grp.members.size();
+        std::vector<Tagged> all;
+        for (int j = 0; j < Mg; ++j) {
+            std::vector<VOp> ops;
+            const tpmg_ctx *c = ctxs[grp.members[j]];
+            member_ops(c, c->p.n_levels - 1, true, -1, ops);
+            for (const VOp &o : ops) all.push_back(Tagged{op_key(o), j, o});
         }
-        for (const auto &cl : classes) {
-            BatchLaunch bl;
-            bl.kind = cl[0];
-            bl.mode = cl[1];
-            bl.f64 = cl[2] != 0;
-            bl.n_r_max = cl[3];
-            // a new work list for the launch
-            auto open = [&]() {
-                bl.count = 0;
-                bl.total = 0;
-                if (bl.kind == 0) {
-                    bl.args = (int)b->rargs.size();
-                    b->rargs.emplace_back();
-                    std::memset(&b->rargs.back(), 0, sizeof(RelaxBatchArgs));
-                } else {
-                    bl.args = (int)b->cargs.size();
-                    b->cargs.emplace_back();
-                    std::memset(&b->cargs.back(), 0, sizeof(RestrictBatchArgs));
-                }
+        std::stable_sort(all.begin(), all.end(), [](const Tagged &a, const Tagged &b2) { return a.key < b2.key; });
+        for (size_t i0 = 0; i0 < all.size();) {
+            size_t i1 = i0;
+            while (i1 < all.size() && all[i1].key == all[i0].key) ++i1;
+            // launch classes of the step: (kind, mode, rows class); every member's finest level
+            // reads its FP32 copy of r, so all right-hand sides are FP32
+            auto class_of = [&](const Tagged &t) {
+                const tpmg_ctx *c = ctxs[grp.members[t.member]];
+                return std::array<int, 3>{t.op.kind, t.op.kind == 0 ? t.op.mode : 0,
+                                          t.op.kind == 0 ? rows_class(c->p.n_r) : 0};
             };
-            auto flush = [&]() {
-                if (bl.count > 0) b->launches.push_back(bl);
-                open();
-            };
-            open();
+            std::vector<std::array<int, 3>> classes;
             for (size_t i = i0; i < i1; ++i) {
-                const Tagged &t = all[i];
-                const tpmg_ctx *c = ctxs[t.member];
-                const bool f64 = false;
-                const std::array<int, 4> tc{t.op.kind, t.op.kind == 0 ? t.op.mode : 0, f64 ? 1 : 0,
-                                            t.op.kind == 0 ? rows_class(c->p.n_r) : 0};
-                if (tc != cl) continue;
-                if (bl.count == kBatchItems) flush();
-                const int m = t.member, l = t.op.lvl, n_r = c->p.n_r;
-                const LevelDev &lv = c->lv[l];
-                auto buf = [&](int lvl, int id) { return id == 0 ? u32[m][lvl] : u2[m][lvl]; };
-                const bool finest = l == c->p.n_levels - 1;
-                const void *f = finest ? (const void *)mem[m].r32 : (const void *)f32[m][l];
-                if (bl.kind == 0) {
-                    BatchRelaxItem it{lv.task_cells, lv.task_nbr, lv.cpack, lv.cvert, lv.rinv32, f,
-                                      buf(l, t.op.uin), buf(l, t.op.uout),
-                                      t.op.fine_buf >= 0 ? buf(l + 1, t.op.fine_buf) : nullptr,
-                                      t.op.out64 ? mem[m].z : nullptr, n_r, t.op.task0 * kRelaxCols,
-                                      t.op.n_tasks * kRelaxCols, m, (float)c->p.relax};
-                    RelaxBatchArgs &a = b->rargs[bl.args];
-                    a.off[bl.count] = (int)bl.total;
-                    a.items[bl.count] = it;
-                    a.n_items = bl.count + 1;
-                    bl.total += it.n_slots;
-                } else {
-                    const int Nc = c->lv[l - 1].n * n_r;
-                    BatchRestrictItem it{lv.nbr, lv.cpack, lv.cvert, f, buf(l, t.op.uin), f32[m][l - 1], n_r, Nc, m};
-                    RestrictBatchArgs &a = b->cargs[bl.args];
-                    a.off[bl.count] = (int)bl.total;
-                    a.items[bl.count] = it;
-                    a.n_items = bl.count + 1;
-                    bl.total += (Nc + 31) & ~31;
-                }
-                ++bl.count;
+                const auto cl = class_of(all[i]);
+                if (std::find(classes.begin(), classes.end(), cl) == classes.end()) classes.push_back(cl);
             }
-            if (bl.count > 0) b->launches.push_back(bl);   // the last list (an empty one stays unused)
+            for (const auto &cl : classes) {
+                BatchLaunch bl;
+                bl.kind = cl[0];
+                bl.mode = cl[1];
+                bl.f64 = false;
+                bl.n_r_max = cl[2];
+                auto open = [&]() {   // a new work list for the launch
+                    bl.count = 0;
+                    bl.total = 0;
+                    if (bl.kind == 0) {
+                        bl.args = (int)grp.rargs.size();
+                        grp.rargs.emplace_back();
+                        std::memset(&grp.rargs.back(), 0, sizeof(RelaxBatchArgs));
+                    } else {
+                        bl.args = (int)grp.cargs.size();
+                        grp.cargs.emplace_back();
+                        std::memset(&grp.cargs.back(), 0, sizeof(RestrictBatchArgs));
+                    }
+                };
+                open();
+                for (size_t i = i0; i < i1; ++i) {
+                    const Tagged &t = all[i];
+                    if (class_of(t) != cl) continue;
+                    if (bl.count == kBatchItems) {
+                        grp.launches.push_back(bl);
+                        open();
+                    }
+                    const int m = grp.members[t.member], l = t.op.lvl;
+                    const tpmg_ctx *c = ctxs[m];
+                    const int n_r = c->p.n_r;
+                    const LevelDev &lv = c->lv[l];
+                    auto buf = [&](int lvl, int id) { return id == 0 ? u32[m][lvl] : u2[m][lvl]; };
+                    const bool finest = l == c->p.n_levels - 1;
+                    const void *f = finest ? (const void *)mem[m].r32 : (const void *)f32[m][l];
+                    if (bl.kind == 0) {
+                        BatchRelaxItem it{lv.task_cells, lv.task_nbr, lv.cpack, lv.cvert, lv.rinv32, f,
+                                          buf(l, t.op.uin), buf(l, t.op.uout),
+                                          t.op.fine_buf >= 0 ? buf(l + 1, t.op.fine_buf) : nullptr,
+                                          t.op.out64 ? mem[m].z : nullptr, n_r, t.op.task0 * kRelaxCols,
+                                          t.op.n_tasks * kRelaxCols, t.member, (float)c->p.relax};
+                        RelaxBatchArgs &a = grp.rargs[bl.args];
+                        a.off[bl.count] = (int)bl.total;
+                        a.items[bl.count] = it;
+                        a.n_items = bl.count + 1;
+                        bl.total += it.n_slots;
+                    } else {
+                        const int Nc = c->lv[l - 1].n * n_r;
+                        BatchRestrictItem it{lv.nbr, lv.cpack, lv.cvert, f, buf(l, t.op.uin), f32[m][l - 1], n_r, Nc,
+                                             t.member};
+                        RestrictBatchArgs &a = grp.cargs[bl.args];
+                        a.off[bl.count] = (int)bl.total;
+                        a.items[bl.count] = it;
+                        a.n_items = bl.count + 1;
+                        bl.total += (Nc + 31) & ~31;
+                    }
+                    ++bl.count;
+                }
+                if (bl.count > 0) grp.launches.push_back(bl);   // (an empty last list stays unused)
+            }
+            i0 = i1;
         }
-        i0 = i1;
+        for (const BatchLaunch &bl : grp.launches)
+            if (bl.total > INT32_MAX / 2) return TPMG_ERR_INVALID_ARG;   // positions are 32-bit in the kernels
+        std::vector<BatchMemberDev> gm(Mg);
+        for (int j = 0; j < Mg; ++j) gm[j] = mem[grp.members[j]];
+        if (balloc(b, &grp.d_mem, Mg) != cudaSuccess || balloc(b, &grp.d_active, Mg) != cudaSuccess ||
+            balloc(b, &grp.d_go, Mg) != cudaSuccess)
+            return TPMG_ERR_OOM;
+        if (cudaMemcpyAsync(grp.d_mem, gm.data(), sizeof(BatchMemberDev) * Mg, cudaMemcpyHostToDevice, s) !=
+                cudaSuccess ||
+            cudaMemsetAsync(grp.d_active, 1, sizeof(int) * Mg, s) != cudaSuccess ||
+            cudaMemsetAsync(grp.d_go, 0, sizeof(int) * Mg, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+            return TPMG_ERR_CUDA;
     }
-    for (const BatchLaunch &bl : b->launches)
-        if (bl.total > INT32_MAX / 2) return TPMG_ERR_INVALID_ARG;   // positions are 32-bit in the kernels
-    if (balloc(b, &b->d_mem, M) != cudaSuccess || balloc(b, &b->d_active, M) != cudaSuccess ||
-        balloc(b, &b->d_go, M) != cudaSuccess)
-        return TPMG_ERR_OOM;
     if (cudaMallocHost(&b->h_sc, sizeof(Scalars) * M) != cudaSuccess) return TPMG_ERR_OOM;
-    if (cudaMemcpyAsync(b->d_mem, mem.data(), sizeof(BatchMemberDev) * M, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemsetAsync(b->d_active, 1, sizeof(int) * M, s) != cudaSuccess ||
-        cudaMemsetAsync(b->d_go, 0, sizeof(int) * M, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
-        return TPMG_ERR_CUDA;
-    // tuner: CTAs of 1, 2, 4 or 8 warps for each relaxation launch of more than a wave of
-    // warps, timed on the batch's zeroed work vectors (every variant is the same arithmetic)
+    // tuner: CTAs of 1, 2, 4 or 8 warps for each relaxation launch of more than two waves
+    // of warps, timed on the batch's zeroed work vectors (every variant is the same arithmetic)
     const int sm = ctxs[0]->sm_count;
     const Launch L0{s, 0, sm, nullptr, nullptr, false};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return TPMG_ERR_CUDA;
     tpmg_status st = TPMG_OK;
-    for (BatchLaunch &bl : b->launches) {
-        if (bl.kind != 0 || bl.total < 2L * 32 * sm) continue;
-        float best = 0.f;
-        for (int v = 0; v < 4 && st == TPMG_OK; ++v) {
-            BatchLaunch t = bl;
-            t.wpb = 1 << v;
-            auto go = [&]() {
-                const RelaxBatchArgs &a = b->rargs[t.args];
-                return t.f64 ? launch_relax32_batch<double>(L0, t.mode, t.n_r_max, a, t.total, t.wpb, b->d_active)
-                             : launch_relax32_batch<float>(L0, t.mode, t.n_r_max, a, t.total, t.wpb, b->d_active);
-            };
-            float ms = 0.f;
-            if (go() != cudaSuccess || cudaEventRecord(e0, s) != cudaSuccess) st = TPMG_ERR_CUDA;
-            for (int k = 0; k < 3 && st == TPMG_OK; ++k)
-                if (go() != cudaSuccess) st = TPMG_ERR_CUDA;
-            if (st == TPMG_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-                                  cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-                st = TPMG_ERR_CUDA;
-            bl.us[v] = 1e3f * ms / 3.f;
-            if (st == TPMG_OK && (best == 0.f || bl.us[v] < best)) {
-                best = bl.us[v];
-                bl.wpb = t.wpb;
+    for (tpmg_batch::Group &grp : b->groups)
+        for (BatchLaunch &bl : grp.launches) {
+            if (bl.kind != 0 || bl.total < 2L * 32 * sm) continue;
+            float best = 0.f;
+            for (int v = 0; v < 4 && st == TPMG_OK; ++v) {
+                BatchLaunch t = bl;
+                t.wpb = 1 << v;
+                auto go = [&]() {
+                    return launch_relax32_batch<float>(L0, t.mode, t.n_r_max, grp.rargs[t.args], t.total, t.wpb,
+                                                       grp.d_active);
+                };
+                float ms = 0.f;
+                if (go() != cudaSuccess || cudaEventRecord(e0, s) != cudaSuccess) st = TPMG_ERR_CUDA;
+                for (int k = 0; k < 3 && st == TPMG_OK; ++k)
+                    if (go() != cudaSuccess) st = TPMG_ERR_CUDA;
+                if (st == TPMG_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                                      cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                    st = TPMG_ERR_CUDA;
+                bl.us[v] = 1e3f * ms / 3.f;
+                if (st == TPMG_OK && (best == 0.f || bl.us[v] < best)) {
+                    best = bl.us[v];
+                    bl.wpb = t.wpb;
+                }
             }
         }
-    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != TPMG_OK) return st;
-    // the work vectors again as at creation (the tuner wrote into them)
-    for (int m = 0; m < M; ++m)
-        for (size_t l = 0; l < u32[m].size(); ++l) {
-            const size_t n = (size_t)ctxs[m]->lv[l].n * ctxs[m]->p.n_r;
-            if (cudaMemsetAsync(u32[m][l], 0, n * sizeof(float), s) != cudaSuccess ||
-                (u2[m][l] && cudaMemsetAsync(u2[m][l], 0, n * sizeof(float), s) != cudaSuccess) ||
-                (f32[m][l] && cudaMemsetAsync(f32[m][l], 0, n * sizeof(float), s) != cudaSuccess))
-                return TPMG_ERR_CUDA;
-        }
-    if (cudaStreamSynchronize(s) != cudaSuccess) return TPMG_ERR_CUDA;
-    // the graph: the members' initial residuals and first decisions, then a conditional
-    // WHILE node whose body is one iteration of every active member
+    if (!clear_work()) return TPMG_ERR_CUDA;   // the tuner wrote into them
+    // the graph: per group a root branch -- its members' initial residuals and first
+    // decisions, then a conditional WHILE node whose body is one iteration of every
+    // active member of the group
     cudaStream_t cs = nullptr;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return TPMG_ERR_CUDA;
     const Launch L{cs, 0, sm, nullptr, nullptr, ctxs[0]->p.pdl != 0};
     cudaGraph_t g = nullptr;
-    cudaGraphConditionalHandle h = 0;
-    auto capture = [&](cudaGraph_t into, const cudaGraphNode_t *deps, size_t nd, std::vector<cudaGraphNode_t> *leaves,
-                       auto &&body) -> tpmg_status {
-        if (cudaStreamBeginCaptureToGraph(cs, into, deps, nullptr, nd, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    auto capture = [&](cudaGraph_t into, std::vector<cudaGraphNode_t> *leaves, auto &&body) -> tpmg_status {
+        if (cudaStreamBeginCaptureToGraph(cs, into, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+            cudaSuccess)
             return TPMG_ERR_CUDA;
         const cudaError_t eb = body();
         const cudaGraphNode_t *out = nullptr;
@@ -2100,59 +2133,63 @@ tpmg_status build_worklist(tpmg_batch *b, tpmg_ctx *const *ctxs, int M, const do
         const cudaError_t ee = cudaStreamEndCapture(cs, &gout);
         return (eb == cudaSuccess && ei == cudaSuccess && ee == cudaSuccess) ? TPMG_OK : TPMG_ERR_CUDA;
     };
-    long long n_init = 0, n_iter = 0;
     auto counted = [](long long &n, cudaError_t e) {
         ++n;
         return e;
     };
     if (cudaGraphCreate(&g, 0) != cudaSuccess) st = TPMG_ERR_CUDA;
-    if (st == TPMG_OK && cudaGraphConditionalHandleCreate(&h, g, 0, 0) != cudaSuccess) st = TPMG_ERR_CUDA;
-    std::vector<cudaGraphNode_t> leaves;
-    if (st == TPMG_OK)
-        st = capture(g, nullptr, 0, &leaves, [&]() -> cudaError_t {
-            cudaError_t e = cudaMemsetAsync(b->d_active, 1, sizeof(int) * M, cs);
-            if (e == cudaSuccess) e = counted(n_init, launch_outer_batch(L, BATCH_NONZERO, b->d_mem, M, n_part, b->d_active));
-            if (e == cudaSuccess) e = counted(n_init, launch_outer_batch(L, BATCH_RESIDUAL, b->d_mem, M, n_part, b->d_active));
-            if (e == cudaSuccess)
-                e = counted(n_init, launch_finish_batch(L, FIN_LOOP_RR0, b->d_mem, M, n_part, b->d_active, b->d_go, 0));
-            if (e == cudaSuccess) e = counted(n_init, launch_outer_batch(L, BATCH_CLEAR_P, b->d_mem, M, n_part, b->d_active));
-            if (e == cudaSuccess) e = counted(n_init, launch_batch_continue(L, M, b->d_go, b->d_active, h));
+    for (tpmg_batch::Group &grp : b->groups) {
+        if (st != TPMG_OK) break;
+        const int Mg = (int)grp.members.size();
+        BatchMemberDev *dm = grp.d_mem;
+        int *act = grp.d_active, *go = grp.d_go;
+        cudaGraphConditionalHandle h = 0;
+        if (cudaGraphConditionalHandleCreate(&h, g, 0, 0) != cudaSuccess) {
+            st = TPMG_ERR_CUDA;
+            break;
+        }
+        std::vector<cudaGraphNode_t> leaves;
+        long long &n_init = grp.init, &n_iter = grp.iter;
+        st = capture(g, &leaves, [&]() -> cudaError_t {
+            cudaError_t e = cudaMemsetAsync(act, 1, sizeof(int) * Mg, cs);
+            if (e == cudaSuccess) e = counted(n_init, launch_outer_batch(L, BATCH_NONZERO, dm, Mg, n_part, act));
+            if (e == cudaSuccess) e = counted(n_init, launch_outer_batch(L, BATCH_RESIDUAL, dm, Mg, n_part, act));
+            if (e == cudaSuccess) e = counted(n_init, launch_finish_batch(L, FIN_LOOP_RR0, dm, Mg, n_part, act, go, 0));
+            if (e == cudaSuccess) e = counted(n_init, launch_outer_batch(L, BATCH_CLEAR_P, dm, Mg, n_part, act));
+            if (e == cudaSuccess) e = counted(n_init, launch_batch_continue(L, Mg, go, act, h));
             return e;
         });
-    cudaGraphNode_t node = nullptr;
-    cudaGraphNodeParams cp = {};
-    if (st == TPMG_OK) {
+        if (st != TPMG_OK) break;
+        cudaGraphNode_t node = nullptr;
+        cudaGraphNodeParams cp = {};
         cp.type = cudaGraphNodeTypeConditional;
         cp.conditional.handle = h;
         cp.conditional.type = cudaGraphCondTypeWhile;
         cp.conditional.size = 1;
-        if (cudaGraphAddNode(&node, g, leaves.data(), nullptr, leaves.size(), &cp) != cudaSuccess) st = TPMG_ERR_CUDA;
-    }
-    if (st == TPMG_OK)
-        st = capture(cp.conditional.phGraph_out[0], nullptr, 0, nullptr, [&]() -> cudaError_t {
-            cudaError_t e = batch_vcycle(b, L);
-            n_iter += (long long)b->launches.size();
-            if (e == cudaSuccess) e = counted(n_iter, launch_outer_batch(L, BATCH_DOT_RZ, b->d_mem, M, n_part, b->d_active));
+        if (cudaGraphAddNode(&node, g, leaves.data(), nullptr, leaves.size(), &cp) != cudaSuccess) {
+            st = TPMG_ERR_CUDA;
+            break;
+        }
+        st = capture(cp.conditional.phGraph_out[0], nullptr, [&]() -> cudaError_t {
+            cudaError_t e = batch_vcycle(grp, L);
+            n_iter += (long long)grp.launches.size();
+            if (e == cudaSuccess) e = counted(n_iter, launch_outer_batch(L, BATCH_DOT_RZ, dm, Mg, n_part, act));
             if (e == cudaSuccess)
-                e = counted(n_iter, launch_finish_batch(L, FIN_LOOP_BETA_PR, b->d_mem, M, n_part, b->d_active, b->d_go, 0));
-            if (e == cudaSuccess) e = counted(n_iter, launch_outer_batch(L, BATCH_XPBY, b->d_mem, M, n_part, b->d_active));
-            if (e == cudaSuccess) e = counted(n_iter, launch_outer_batch(L, BATCH_APPLY, b->d_mem, M, n_part, b->d_active));
+                e = counted(n_iter, launch_finish_batch(L, FIN_LOOP_BETA_PR, dm, Mg, n_part, act, go, 0));
+            if (e == cudaSuccess) e = counted(n_iter, launch_outer_batch(L, BATCH_XPBY, dm, Mg, n_part, act));
+            if (e == cudaSuccess) e = counted(n_iter, launch_outer_batch(L, BATCH_APPLY, dm, Mg, n_part, act));
+            if (e == cudaSuccess) e = counted(n_iter, launch_finish_batch(L, FIN_ALPHA, dm, Mg, n_part, act, go, 0));
+            if (e == cudaSuccess) e = counted(n_iter, launch_outer_batch(L, BATCH_AXPY, dm, Mg, n_part, act));
+            if (e == cudaSuccess) e = counted(n_iter, launch_finish_batch(L, FIN_LOOP_RR, dm, Mg, n_part, act, go, 0));
             if (e == cudaSuccess)
-                e = counted(n_iter, launch_finish_batch(L, FIN_ALPHA, b->d_mem, M, n_part, b->d_active, b->d_go, 0));
-            if (e == cudaSuccess) e = counted(n_iter, launch_outer_batch(L, BATCH_AXPY, b->d_mem, M, n_part, b->d_active));
-            if (e == cudaSuccess)
-                e = counted(n_iter, launch_finish_batch(L, FIN_LOOP_RR, b->d_mem, M, n_part, b->d_active, b->d_go, 0));
-            if (e == cudaSuccess)
-                e = counted(n_iter,
-                            launch_finish_batch(L, FIN_RZC, b->d_mem, M, n_part, b->d_active, b->d_go, n_part));
-            if (e == cudaSuccess) e = counted(n_iter, launch_batch_continue(L, M, b->d_go, b->d_active, h));
+                e = counted(n_iter, launch_finish_batch(L, FIN_RZC, dm, Mg, n_part, act, go, n_part));
+            if (e == cudaSuccess) e = counted(n_iter, launch_batch_continue(L, Mg, go, act, h));
             return e;
         });
+    }
     if (st == TPMG_OK && cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) st = TPMG_ERR_CUDA;
     if (g) cudaGraphDestroy(g);
     cudaStreamDestroy(cs);
-    b->wl_init = n_init;
-    b->wl_iter = n_iter;
     return st;
 }
 
@@ -2540,7 +2577,15 @@ tpmg_status tpmg_solve(tpmg_ctx *ctx, const double *d_f, double *d_u, double rto
 tpmg_status tpmg_batch_create(tpmg_ctx *const *ctxs, int n, const double *const *d_f, double *const *d_u, double rtol,
                               int max_iter, tpmg_batch **out)
 {
+    return tpmg_batch_create_ex(ctxs, n, d_f, d_u, rtol, max_iter, TPMG_BATCH_AUTO, 0, out);
+}
+
+tpmg_status tpmg_batch_create_ex(tpmg_ctx *const *ctxs, int n, const double *const *d_f, double *const *d_u,
+                                 double rtol, int max_iter, int form, int groups, tpmg_batch **out)
+{
     if (!out || !ctxs || !d_f || !d_u || n < 1) return TPMG_ERR_INVALID_ARG;
+    if (form != TPMG_BATCH_AUTO && form != TPMG_BATCH_BRANCHES && form != TPMG_BATCH_WORKLIST) return TPMG_ERR_INVALID_ARG;
+    if (groups < 0 || groups > n) return TPMG_ERR_INVALID_ARG;
     if (!(rtol >= 0.0) || max_iter < 0 || max_iter >= kHistCap) return TPMG_ERR_INVALID_ARG;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return TPMG_ERR_CUDA;
@@ -2555,6 +2600,8 @@ tpmg_status tpmg_batch_create(tpmg_ctx *const *ctxs, int n, const double *const 
             if (d_u[k] == d_u[i] || d_u[k] == d_f[i] || d_f[k] == d_u[i]) return TPMG_ERR_INVALID_ARG;   // aliased
         }
     }
+    if (form == TPMG_BATCH_WORKLIST && !worklist) return TPMG_ERR_INVALID_ARG;   // a member does not qualify
+    if (form == TPMG_BATCH_BRANCHES) worklist = false;
     if (repeated && !worklist) return TPMG_ERR_INVALID_ARG;   // a branch holds its context's own solve
     tpmg_batch *b = new (std::nothrow) tpmg_batch();
     if (!b) return TPMG_ERR_OOM;
@@ -2564,7 +2611,7 @@ tpmg_status tpmg_batch_create(tpmg_ctx *const *ctxs, int n, const double *const 
     b->rtol = rtol;
     b->max_iter = max_iter;
     if (worklist) {
-        const tpmg_status st = build_worklist(b, ctxs, n, d_f, d_u, ctxs[0]->stream);
+        const tpmg_status st = build_worklist(b, ctxs, n, d_f, d_u, ctxs[0]->stream, groups);
         if (st != TPMG_OK) {
             (void)cudaGetLastError();
             tpmg_batch_destroy(b);
@@ -2604,15 +2651,19 @@ tpmg_status tpmg_batch_run(tpmg_batch *b, void *cuda_stream, int *iters, double 
                 return TPMG_ERR_CUDA;
         if (cudaStreamSynchronize(s) != cudaSuccess) return TPMG_ERR_CUDA;
         tpmg_status first = TPMG_OK;
-        int it_max = 0;
         for (int m = 0; m < M; ++m) {
             const tpmg_status st = loop_result(b->ctx[m], b->h_sc[m], b->rtol, b->max_iter, &iters[m], &rel_resid[m]);
             if (status) status[m] = st;
             if (st != TPMG_OK && first == TPMG_OK) first = st;
-            it_max = std::max(it_max, iters[m]);
         }
-        // the batch's loop runs as long as its longest member
-        if (kernel_launches) *kernel_launches = b->wl_init + (long long)it_max * b->wl_iter;
+        // each group's loop runs as long as its longest member
+        long long launches = 0;
+        for (const tpmg_batch::Group &grp : b->groups) {
+            int it_max = 0;
+            for (int m : grp.members) it_max = std::max(it_max, iters[m]);
+            launches += grp.init + (long long)it_max * grp.iter;
+        }
+        if (kernel_launches) *kernel_launches = launches;
         return first;
     }
     for (tpmg_ctx *c : b->ctx)

@@ -1017,9 +1017,11 @@ __global__ void __launch_bounds__(NT, STAGE ? 1 : 6)
 // 16 columns, so the serial phases of the tasks resident on an SM overlap
 // with the gather and write-back phases of others and keep its four FP64
 // units busy.  One warp per CTA spreads the tasks evenly over the SMs and
-// their sub-partitions.
-template <int MODE, bool HF>
-__global__ void __launch_bounds__(32, 16)
+// their sub-partitions.  DEEP: twice the loads in flight -- 8 elements per
+// lane in the gather, the solve's multipliers 8 steps ahead, 4 elements in
+// the write-back -- for more registers per warp (fewer resident warps).
+template <int MODE, bool HF, bool DEEP>
+__global__ void __launch_bounds__(32, DEEP ? 12 : 16)
     k_relax_warp(OpView o, const int *__restrict__ cells, const int4 *__restrict__ tnb, const dbl4 *__restrict__ tg,
                  const double *__restrict__ rinv, const double *__restrict__ fb, const double *__restrict__ fcf,
                  const double *__restrict__ fm, int S, int j, int task0, const double *__restrict__ f,
@@ -1042,7 +1044,7 @@ __global__ void __launch_bounds__(32, 16)
     pdl_wait();
     pdl_trigger();
     __syncwarp();
-    constexpr int U = 4;
+    constexpr int U = DEEP ? 8 : 4;
     for (int e0 = lane; e0 < ne; e0 += 32 * U) {
         double fv[U], iv[U], v0[U], v1[U], v2[U];
         dbl4 cs[U];
@@ -1089,9 +1091,9 @@ __global__ void __launch_bounds__(32, 16)
     }
     __syncwarp();
     const size_t fbase = (size_t)t * S * 32 + lane;
-    twisted_solve<4>(fb + fbase, fcf + fbase, s_m, tile + (lane & (kRelaxCols - 1)) * ld, n_r, j, lane);
+    twisted_solve<DEEP ? 8 : 4>(fb + fbase, fcf + fbase, s_m, tile + (lane & (kRelaxCols - 1)) * ld, n_r, j, lane);
     __syncwarp();
-    constexpr int W = 2;
+    constexpr int W = DEEP ? 4 : 2;
     for (int e0 = lane; e0 < ne; e0 += 32 * W) {
         double x[W], uo[W], uf[W][4];
         int idx[W], fi[W];
@@ -1121,158 +1123,6 @@ __global__ void __launch_bounds__(32, 16)
             if (u_fine) {
 #pragma unroll
                 for (int h = 0; h < 4; ++h) u_fine[fi[q] + h * n_r] = uf[q][h] + v;
-            }
-        }
-    }
-}
-
-// Named CTA barriers (ids 1..15; 0 is __syncthreads) for the warp-specialised pass below.
-__device__ __forceinline__ void bar_sync(int id, int n) { asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(n) : "memory"); }
-__device__ __forceinline__ void bar_arrive(int id, int n)
-{
-    asm volatile("bar.arrive %0, %1;\n" ::"r"(id), "r"(n) : "memory");
-}
-
-constexpr int kPipeThreads = 96;   // two gathering warps and one solving warp
-
-// The same relaxation pass with warp specialisation, for passes of many tasks: each
-// CTA takes the tasks blockIdx.x, blockIdx.x + gridDim.x, ... of the pass.  Warps 0
-// and 1 (the producers) gather the right-hand side t = (f + hr sum_e g_e u_e) / pivot
-// of task i + 1 into one of two shared tiles while warp 2 (the consumer) runs the
-// twisted solve of task i on the other tile and writes it back, so that the load
-// latency and FP64 work of the gathers overlap the serial chain of the solves on the
-// SM's FP64 units.  Hand-over by named barriers: FULL[b] (ids 1, 2) -- tile b holds a
-// gathered task; EMPTY[b] (ids 3, 4) -- the consumer is done with tile b.  Every warp
-// runs the same number of tasks; producers wait on EMPTY[b] only from their third
-// task on, and the consumer arrives on EMPTY[b] only where a later task waits on it,
-// so every phase of every barrier completes.  The arithmetic of each column is that
-// of k_relax_warp (same gather, same twisted_solve, same write-back).
-template <int MODE, bool HF>
-__global__ void __launch_bounds__(kPipeThreads, 5)
-    k_relax_pc(OpView o, const int *__restrict__ cells, const int4 *__restrict__ tnb, const dbl4 *__restrict__ tg,
-               const double *__restrict__ rinv, const double *__restrict__ fb, const double *__restrict__ fcf,
-               const double *__restrict__ fm, int S, int j, int task0, int n_tasks, const double *__restrict__ f,
-               const double *u_in, double *u_out, double *__restrict__ u_fine, double relax)
-{
-    extern __shared__ double smem[];   // two tiles [16][n_r + 1]
-    __shared__ int s_cell[2][kRelaxCols];
-    __shared__ int4 s_nb[2][kRelaxCols];
-    __shared__ dbl4 s_g[2][kRelaxCols];
-    __shared__ double s_m[2][2 * kRelaxCols];
-    const int n_r = o.n_r, ld = n_r + 1, ne = kRelaxCols * n_r;
-    const int tsz = (kRelaxCols * ld + 1) & ~1;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int count = (n_tasks - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;   // >= 1: grid <= n_tasks
-    pdl_wait();
-    pdl_trigger();
-    if (warp < 2) {
-        const int pt = threadIdx.x;   // 0..63
-        for (int it = 0; it < count; ++it) {
-            const int b = it & 1, t = task0 + blockIdx.x + it * gridDim.x;
-            if (it >= 2) bar_sync(3 + b, kPipeThreads);   // the consumer is done with tile b
-            if (pt < kRelaxCols) {
-                const int q = t * kRelaxCols + pt;
-                s_cell[b][pt] = __ldg(&cells[q]);
-                s_nb[b][pt] = __ldg(&tnb[q]);
-                s_g[b][pt] = tg[q];
-            } else if (pt < 3 * kRelaxCols) {
-                s_m[b][pt - kRelaxCols] = __ldg(&fm[(size_t)t * 2 * kRelaxCols + pt - kRelaxCols]);
-            }
-            bar_sync(5, 64);   // the task's cells and couplings, for both producer warps
-            double *tile = smem + b * tsz;
-            constexpr int U = 8;
-            for (int e0 = pt; e0 < ne; e0 += 64 * U) {
-                double fv[U], iv[U], v0[U], v1[U], v2[U];
-                dbl4 cs[U];
-                int col[U], kk[U];
-#pragma unroll
-                for (int q = 0; q < U; ++q) {
-                    const int e = e0 + 64 * q;
-                    col[q] = -1;
-                    kk[q] = 0;
-                    fv[q] = iv[q] = v0[q] = v1[q] = v2[q] = 0.0;
-                    if (HF) cs[q] = dbl4{0.0, 0.0, 0.0, 0.0};
-                    if (e < ne) {
-                        const int c = e / n_r, k = e - c * n_r;
-                        col[q] = c;
-                        kk[q] = k;
-                        const int T = s_cell[b][c];
-                        if (T >= 0) {
-                            fv[q] = f[T * n_r + k];
-                            iv[q] = __ldg(&rinv[T * n_r + k]);
-                            if (MODE != PASS_RHS_ONLY) {
-                                const int4 nb = s_nb[b][c];
-                                if (MODE == PASS_NORMAL || (nb.w & 1)) v0[q] = u_in[nb.x * n_r + k];
-                                if (MODE == PASS_NORMAL || (nb.w & 2)) v1[q] = u_in[nb.y * n_r + k];
-                                if (MODE == PASS_NORMAL || (nb.w & 4)) v2[q] = u_in[nb.z * n_r + k];
-                                if (HF) cs[q] = o.c[T * n_r + k];
-                            }
-                        }
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < U; ++q) {
-                    if (col[q] < 0) continue;
-                    double d = fv[q];
-                    if (MODE != PASS_RHS_ONLY) {
-                        if (HF) {
-                            d = fma(cs[q].z, v2[q], fma(cs[q].y, v1[q], fma(cs[q].x, v0[q], d)));
-                        } else {
-                            const dbl4 g = s_g[b][col[q]];
-                            d = fma(__ldg(&o.hr[kk[q]]), fma(g.z, v2[q], fma(g.y, v1[q], g.x * v0[q])), d);
-                        }
-                    }
-                    tile[col[q] * ld + kk[q]] = d * iv[q];
-                }
-            }
-            __threadfence_block();
-            bar_arrive(1 + b, kPipeThreads);   // tile b is full
-        }
-    } else {
-        for (int it = 0; it < count; ++it) {
-            const int b = it & 1, t = task0 + blockIdx.x + it * gridDim.x;
-            bar_sync(1 + b, kPipeThreads);
-            double *tile = smem + b * tsz;
-            const size_t fbase = (size_t)t * S * 32 + lane;
-            twisted_solve<4>(fb + fbase, fcf + fbase, s_m[b], tile + (lane & (kRelaxCols - 1)) * ld, n_r, j, lane);
-            __syncwarp();
-            constexpr int W = 2;
-            for (int e0 = lane; e0 < ne; e0 += 32 * W) {
-                double x[W], uo[W], uf[W][4];
-                int idx[W], fi[W];
-#pragma unroll
-                for (int q = 0; q < W; ++q) {
-                    const int e = e0 + 32 * q;
-                    idx[q] = -1;
-                    if (e >= ne) continue;
-                    const int c = e / n_r, k = e - c * n_r;
-                    const int T = s_cell[b][c];
-                    if (T < 0) continue;
-                    idx[q] = T * n_r + k;
-                    fi[q] = 4 * T * n_r + k;
-                    x[q] = tile[c * ld + k];
-                    uo[q] = (MODE == PASS_NORMAL && relax != 1.0) ? u_in[idx[q]] : 0.0;
-                    if (u_fine) {
-#pragma unroll
-                        for (int h = 0; h < 4; ++h) uf[q][h] = u_fine[fi[q] + h * n_r];
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < W; ++q) {
-                    if (idx[q] < 0) continue;
-                    double v = x[q];
-                    if (relax != 1.0) v = fma(relax, v - uo[q], uo[q]);
-                    u_out[idx[q]] = v;
-                    if (u_fine) {
-#pragma unroll
-                        for (int h = 0; h < 4; ++h) u_fine[fi[q] + h * n_r] = uf[q][h] + v;
-                    }
-                }
-            }
-            if (it + 2 < count) {   // a later task of the producers waits for tile b
-                __syncwarp();
-                __threadfence_block();
-                bar_arrive(3 + b, kPipeThreads);
             }
         }
     }
@@ -1735,8 +1585,8 @@ template <int MODE, bool HF>
 static cudaError_t relax_launch_hf(const Launch &L0, const LevelDev &lv, const VertDev &v, int task0, int n_tasks,
                                    double relax, const double *f, const double *u_in, double *u_out, double *u_fine)
 {
-    if (lv.scan) {
-        const int var = lv.relax_variant < 0 ? RELAX_CTA128 : lv.relax_variant;
+    if (lv.scan) {   // CTAs of 1, 2, 4 or 8 warps (variants 0..3; the warp-specialised variant 4 is for tasks)
+        const int var = (lv.relax_variant < 0 || lv.relax_variant > RELAX_CTA256) ? RELAX_CTA128 : lv.relax_variant;
         return relax_scan<MODE, HF>(L0, lv, v, var, task0, n_tasks, relax, f, u_in, u_out, u_fine);
     }
     // a small colour of a larger level: warp scans in CTAs of 4 warps (the level's tuned
@@ -1751,25 +1601,10 @@ static cudaError_t relax_launch_hf(const Launch &L0, const LevelDev &lv, const V
     const size_t tile = (((size_t)kRelaxCols * (L.n_r + 1) + 1) & ~(size_t)1) * sizeof(double);
     int var = lv.relax_variant;
     if (var < 0) var = (n_tasks >= 8 * L.sm_count && tile <= 32 * 1024) ? RELAX_WARP : RELAX_CTA128;
-    if (var == RELAX_PIPE && 2 * tile <= 64 * 1024) {
-        auto kern = k_relax_pc<MODE, HF>;
-        const size_t smem = 2 * tile;
-        if (smem > 48 * 1024) {
-            const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-        }
-        int per_sm = 0;   // resident CTAs per SM: one wave of CTAs walks all tasks
-        const cudaError_t eo = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPipeThreads, smem);
-        if (eo != cudaSuccess) return eo;
-        const int grid = std::min(n_tasks, std::max(per_sm, 1) * L.sm_count);
-        return launch_k(L, kern, grid, kPipeThreads, smem, make_view(lv, v, L.n_r), lv.task_cells, lv.task_nbr,
-                        lv.task_g, lv.rinv, lv.fb, lv.fc, lv.fm, lv.steps, lv.jmid, task0, n_tasks, f, u_in, u_out,
-                        u_fine, relax);
-    }
-    if (var == RELAX_WARP && tile <= 32 * 1024) {
-        return launch_k(L, k_relax_warp<MODE, HF>, n_tasks, 32, tile, make_view(lv, v, L.n_r), lv.task_cells,
-                        lv.task_nbr, lv.task_g, lv.rinv, lv.fb, lv.fc, lv.fm, lv.steps, lv.jmid, task0, f, u_in, u_out,
-                        u_fine, relax);
+    if ((var == RELAX_WARP || var == RELAX_WARP_DEEP) && tile <= 32 * 1024) {
+        auto kern = var == RELAX_WARP_DEEP ? k_relax_warp<MODE, HF, true> : k_relax_warp<MODE, HF, false>;
+        return launch_k(L, kern, n_tasks, 32, tile, make_view(lv, v, L.n_r), lv.task_cells, lv.task_nbr, lv.task_g,
+                        lv.rinv, lv.fb, lv.fc, lv.fm, lv.steps, lv.jmid, task0, f, u_in, u_out, u_fine, relax);
     }
     const size_t staged = tile + (size_t)2 * lv.steps * 32 * sizeof(double);
     if (staged > 160 * 1024)

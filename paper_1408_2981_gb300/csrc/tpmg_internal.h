@@ -85,10 +85,9 @@ constexpr int kRelaxCols = 16;
 
 // Kernel variants of a relaxation pass (chosen per level by the autotuner).
 // FP64: one warp per 16-column task, one CTA of 64 / 128 / 256 threads per task,
-// or warp-specialised CTAs (two gathering warps, one solving warp) over strided
-// tasks.  FP32: one warp per column in CTAs of 1 / 2 / 4 / 8 warps (the first
-// four variants).
-enum RelaxVariant { RELAX_WARP = 0, RELAX_CTA64 = 1, RELAX_CTA128 = 2, RELAX_CTA256 = 3, RELAX_PIPE = 4,
+// or one warp per task with twice the loads in flight.  FP32: one warp per column
+// in CTAs of 1 / 2 / 4 / 8 warps (the first four variants).
+enum RelaxVariant { RELAX_WARP = 0, RELAX_CTA64 = 1, RELAX_CTA128 = 2, RELAX_CTA256 = 3, RELAX_WARP_DEEP = 4,
                     RELAX_VARIANTS = 5 };
 constexpr int kRelaxVariants32 = 4;
 

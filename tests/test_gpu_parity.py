@@ -268,8 +268,7 @@ def test_graph_replay_matches_direct_launches():
 # The FP64 relaxation kernels of the twisted 16-column tasks (tpmg_query_tuning's
 # variants 0-4, forced with relax_variant) perform the same arithmetic per column, so
 # whole solves agree bit for bit.  The cases put each kernel through its paths: a
-# finest level of 2548 tasks per colour, so the warp-specialised CTAs (variant 4) walk
-# several tasks each and reuse both tiles; twisted tasks on every level
+# finest level of 2548 tasks per colour; twisted tasks on every level
 # (scan_max_cells = 0), so the fused prolongation and the small coarse passes run
 # through each variant; block Jacobi with a relaxation weight; the stencil stored per
 # unknown (TPMG^full); a column of 160 levels.
@@ -304,9 +303,9 @@ def test_relaxation_variants_give_identical_results(name):
         np.testing.assert_array_equal(outs[v][4], outs[0][4])
 
 
-def test_warp_specialised_relaxation_vs_oracle():
-    """The V-cycle with the warp-specialised twisted passes on every level against the
-    oracle's V-cycle (the V-cycle bound of this file)."""
+def test_deep_warp_relaxation_vs_oracle():
+    """The V-cycle with the deeply pipelined one-warp twisted passes (variant 4) on
+    every level against the oracle's V-cycle (the V-cycle bound of this file)."""
     kw = VARIANT_CASES["ref4_nr24_twisted_everywhere_jacobi"]
     s, o = binding.Solver(relax_variant=4, **kw), oracle_for(kw)
     r = inputs.uniform_pm1(inputs.SEED_UNIFORM_SMALL + 61, s.N)
