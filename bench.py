@@ -153,13 +153,17 @@ def traffic_records() -> list:
     import glob
     import re
 
-    pat = re.compile(r"traffic: class=(\w+) workload=(\S+) (\S+)=([0-9a-f]{16}) bytes_per_launch=([0-9.eE+]+)")
+    pat = re.compile(r"traffic: class=(\w+) workload=(\S+) (\S+)=([0-9a-f]{16}) bytes_per_launch=([0-9.eE+]+)"
+                     r"(?: algorithmic_per_launch=([0-9.eE+]+))?(?: scope=(\S+))?")
     out = []
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         with open(path) as fh:
             for m in pat.finditer(fh.read()):
                 out.append(dict(kernel=m.group(1), workload=m.group(2), file=m.group(3), sha256=m.group(4),
-                                bytes_per_launch=float(m.group(5)), source=os.path.relpath(path, ROOT)))
+                                bytes_per_launch=float(m.group(5)),
+                                algorithmic_per_launch=float(m.group(6)) if m.group(6) else None,
+                                scope=(m.group(7) or "").replace("-", " ") or None,
+                                source=os.path.relpath(path, ROOT)))
     return out
 
 
@@ -219,7 +223,9 @@ def roofline_of(prof: dict, before: dict, dominant: str, mixed: bool, steps: int
     roof = {"bound": "hbm" if hbm_bound else "alu", "achieved": c["achieved"], "peak": c["peak"], "unit": c["unit"],
             "frac": c["frac"], "peak_source": c["peak_source"],
             "traffic": tr["bytes_per_launch"] if tr else None,
-            "traffic_unit": "DRAM bytes (read + write) per launch of the class, ncu",
+            "traffic_unit": "DRAM bytes (read + write) per launch, ncu, of the launches in traffic_scope",
+            "traffic_scope": (tr["scope"] or "every launch of the class") if tr else None,
+            "traffic_algorithmic_bytes": tr["algorithmic_per_launch"] if tr else None,
             "traffic_source": tr["source"] if tr else None,
             "algorithmic_bytes_per_launch": tb / d["timed"], "algorithmic_flops_per_launch": tf / d["timed"],
             "kernel": f"{dominant} ({'FP32/BF16' if fp32 else 'FP64'}){kernel_note}",
@@ -228,7 +234,8 @@ def roofline_of(prof: dict, before: dict, dominant: str, mixed: bool, steps: int
             "hbm_frac_of_measured": ceilings["hbm"]["frac"],
             "share_of_step": (d["ms"] / d["timed"]) * launches_step / step_ms if step_ms else None}
     if tr:
-        roof["traffic_over_algorithmic"] = tr["bytes_per_launch"] / roof["algorithmic_bytes_per_launch"]
+        alg = tr["algorithmic_per_launch"] or roof["algorithmic_bytes_per_launch"]
+        roof["traffic_over_algorithmic"] = tr["bytes_per_launch"] / alg
     return roof
 
 
@@ -629,25 +636,32 @@ def run_extra_configs(args, stream, flush) -> dict:
     del f, u64, umx
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
-    b = batch_stats(WORKLOADS["batch48"], stream, flush, steps=5, warmup=2, rtol=args.rtol)
+    b, wlist = batch_both(WORKLOADS["batch48"], stream, flush, steps=5, warmup=2, rtol=args.rtol)
     out["batch48"] = {k: b[k] for k in ("workload", "n_unknowns", "problems", "ms_per_step", "unknowns_per_s",
                                         "iters", "gpu_launches", "form")}
+    out["batch48"]["other_form"] = wlist
+    del b
     torch.cuda.empty_cache()
     return out
 
 
-def batch_stats(wl, stream, flush, steps: int, warmup: int, rtol: float) -> dict:
-    """Set-up and timed runs of a batched workload (one tpmg_batch run per step)."""
+def batch_stats(wl, stream, flush, steps: int, warmup: int, rtol: float, form: str = "auto", groups: int = 0,
+                problems=None) -> dict:
+    """Set-up and timed runs of a batched workload (one tpmg_batch run per step).
+    problems: (solvers, fs, us) to reuse, else created from the workload."""
     import torch
 
     from paper_1408_2981_gb300 import binding, inputs
 
-    probs = batch_problems(wl["seed"], wl["batch"])
-    solvers = [binding.Solver(stream=stream, **kw) for kw in probs]
-    fs = [torch.from_numpy(inputs.uniform_pm1(wl["seed"] + 100 + j, s.N)).cuda() for j, s in enumerate(solvers)]
-    us = [torch.zeros_like(f) for f in fs]
+    if problems is None:
+        probs = batch_problems(wl["seed"], wl["batch"])
+        solvers = [binding.Solver(stream=stream, **kw) for kw in probs]
+        fs = [torch.from_numpy(inputs.uniform_pm1(wl["seed"] + 100 + j, s.N)).cuda() for j, s in enumerate(solvers)]
+        us = [torch.zeros_like(f) for f in fs]
+    else:
+        solvers, fs, us = problems
     N = sum(s.N for s in solvers)
-    batch = binding.Batch(solvers, fs, us, rtol=rtol, max_iter=200)
+    batch = binding.Batch(solvers, fs, us, rtol=rtol, max_iter=200, form=form, groups=groups)
 
     def step():
         for u in us:
@@ -671,9 +685,26 @@ def batch_stats(wl, stream, flush, steps: int, warmup: int, rtol: float) -> dict
     ms = sum(a.elapsed_time(b) for a, b in evs)
     out = {"workload": wl["text"], "n_unknowns": N, "problems": len(solvers), "ms_per_step": ms / steps,
            "unknowns_per_s": N * steps / (ms / 1e3), "iters": [int(i) for i in iters], "gpu_launches": launches,
-           "local_ms": ms, "form": batch.form, "batch": batch, "solvers": solvers, "fs": fs, "us": us,
-           "step": step}
+           "local_ms": ms, "form": batch.form, "groups": groups, "batch": batch, "solvers": solvers, "fs": fs,
+           "us": us, "step": step}
     return out
+
+
+BATCH_WORKLIST_GROUPS = 16   # the work-list form's root branches in the batch lines (measured best of 1..48)
+
+
+def batch_both(wl, stream, flush, steps: int, warmup: int, rtol: float) -> tuple:
+    """The batch in its automatic form, then in the work-list form on the same problems."""
+    import torch
+
+    a = batch_stats(wl, stream, flush, steps, warmup, rtol)   # stays open for the caller (end-to-end runs)
+    torch.cuda.synchronize()
+    w = batch_stats(wl, stream, flush, steps, warmup, rtol, form="worklist", groups=BATCH_WORKLIST_GROUPS,
+                    problems=(a["solvers"], a["fs"], a["us"]))
+    w["batch"].close()
+    torch.cuda.synchronize()
+    other = {k: w[k] for k in ("form", "groups", "ms_per_step", "unknowns_per_s", "gpu_launches")}
+    return a, other
 
 
 def run_batch(args, wl):
@@ -696,7 +727,7 @@ def run_batch(args, wl):
     barrier(world)
     clocks = ClockSampler(local)
     clocks.start()
-    b = batch_stats(wl, stream, flush, args.steps, args.warmup, args.rtol)
+    b, wlist = batch_both(wl, stream, flush, args.steps, args.warmup, args.rtol)
     clk = clocks.stop()
     fs, us, step, N, solvers, launches, iters = b["fs"], b["us"], b["step"], b["n_unknowns"], b["solvers"], \
         b["gpu_launches"], b["iters"]
@@ -728,7 +759,7 @@ def run_batch(args, wl):
                 "e2e": {"value": N * e2e_steps * world / (e2e_ms / 1e3), "unit": "unknowns/s",
                         "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N},
                 "gpu_launches": launches, "roofline": None, "cpu_baseline": None, "clocks": clk,
-                "iters": [int(i) for i in iters], "form": b["form"], "gpus_active": world,
+                "iters": [int(i) for i in iters], "form": b["form"], "other_form": wlist, "gpus_active": world,
                 "note": "the loops run on the device, so kernels carry no event pairs: no per-kernel roofline here"}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -299,8 +299,10 @@ tpmg_status tpmg_solve_host(tpmg_ctx *ctx, const double *h_f, double *h_u, doubl
  * tpmg_solve (d_u[i] = initial guess, overwritten by the solution); the
  * pointers are baked into the batch, which stays valid while the contexts and
  * vectors live.  Every problem's solution, iterations and residuals are those
- * of its own tpmg_solve, bit for bit.  max_iter < 4096.  Two forms:
- *   TPMG_BATCH_WORKLIST, built when every context is a mixed-precision CG
+ * of its own tpmg_solve, bit for bit.  max_iter < 4096.  Two forms (this
+ * call builds the work-list form when a context appears more than once, the
+ * branch form otherwise; tpmg_batch_create_ex chooses explicitly):
+ *   TPMG_BATCH_WORKLIST, possible when every context is a mixed-precision CG
  *   context with constant prolongation, no vertical advection, the factorised
  *   outer operator (no tpmg_set_outer_profiles) and nu_pre, nu_post,
  *   nu_coarse >= 1: the members' V-cycles are merged into one schedule of
@@ -313,9 +315,12 @@ tpmg_status tpmg_solve_host(tpmg_ctx *ctx, const double *h_f, double *h_u, doubl
  *   factors are shared and the batch allocates each member's work vectors
  *   (about 48 bytes per unknown).  The relaxation launches' CTA shapes (1, 2,
  *   4 or 8 warps) are timed at creation and the fastest kept (same arithmetic).
- *   TPMG_BATCH_BRANCHES otherwise: each problem is an independent branch of
- *   the graph (the contexts' own device-side solves); a context may appear
- *   once, and must not run another solve while its batch runs.
+ *   TPMG_BATCH_BRANCHES: each problem is an independent branch of the graph
+ *   (the contexts' own device-side solves), any context kind; a context may
+ *   appear once, and must not run another solve while its batch runs.  On 48
+ *   distinct mixed-precision problems it measured faster than the work list
+ *   (the problems' graphs overlap freely; the work list's launches carry an
+ *   item lookup and a member flag on their critical path).
  * Errors: INVALID_ARG (NULL, a repeated context outside the work-list form,
  * aliased vectors, other device, a context with vertical advection or linear
  * prolongation), OOM, CUDA. */

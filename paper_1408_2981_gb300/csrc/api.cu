@@ -2602,7 +2602,11 @@ tpmg_status tpmg_batch_create_ex(tpmg_ctx *const *ctxs, int n, const double *con
     }
     if (form == TPMG_BATCH_WORKLIST && !worklist) return TPMG_ERR_INVALID_ARG;   // a member does not qualify
     if (form == TPMG_BATCH_BRANCHES) worklist = false;
-    if (repeated && !worklist) return TPMG_ERR_INVALID_ARG;   // a branch holds its context's own solve
+    // automatic: branches where every problem has its own context (measured faster on the
+    // 48-problem workload: the problems' graphs overlap freely), the work list where a
+    // context carries several right-hand sides (a branch holds its context's own solve)
+    if (form == TPMG_BATCH_AUTO && !repeated) worklist = false;
+    if (repeated && !worklist) return TPMG_ERR_INVALID_ARG;
     tpmg_batch *b = new (std::nothrow) tpmg_batch();
     if (!b) return TPMG_ERR_OOM;
     b->ctx.assign(ctxs, ctxs + n);

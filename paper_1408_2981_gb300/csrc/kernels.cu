@@ -798,6 +798,11 @@ __global__ void __launch_bounds__(256)
     // forward, y_k = t_k + b_k y_{k-1}: the lane's own recurrence Y_j from y = 0 before its
     // first row, with the prefix products P_j = b_{k0} ... b_{k0+j}; rows past the column
     // are the identity map (b = 1, t = 0)
+    // the backward recurrence's coefficients, loaded with the forward ones so that a pass
+    // has one round trip to memory on its critical path
+    double cf[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) cf[j] = k0 + j < n_r ? __ldg(&fcf[base + k0 + j]) : 0.0;
     double y[R], P[R];
 #pragma unroll
     for (int j = 0; j < R; ++j) {
@@ -845,7 +850,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int j = R - 1; j >= 0; --j) {
         const int k = k0 + j;
-        const double c = k < n_r ? __ldg(&fcf[base + k]) : 0.0;
+        const double c = cf[j];
         if (k >= n_r) y[j] = 0.0;
         if (j < R - 1) y[j] = fma(c, y[j + 1], y[j]);
         Q[j] = j == R - 1 ? c : c * Q[j + 1];

@@ -118,7 +118,14 @@ __device__ __forceinline__ void relax32_column(const bf16x4 *__restrict__ cpack,
     // flux through the bottom), which is also face n_r of the column before, and one
     // zero element follows the level's last column, so both loads are unconditional.
     auto below = [&](int k, size_t i, float ri) { return SF ? __ldg(&fb[i]) : bf(__ldg(&cvert[i])) * ri; };
-    auto above = [&](int k, size_t i, float ri) { return SF ? __ldg(&fg[i]) : bf(__ldg(&cvert[i + 1])) * ri; };
+    // the coupling above row k (or its stored multiplier): with at most two rows per lane
+    // loaded with the forward pass's operands, so that the pass has one round trip to
+    // memory on its critical path; with more rows per lane in the backward pass (the
+    // registers would cost resident warps on the HBM-bound large levels)
+    constexpr bool PF = R <= 2;
+    auto above_load = [&](size_t i) { return SF ? __ldg(&fg[i]) : bf(__ldg(&cvert[i + 1])); };
+    auto above = [&](float cu, float ri) { return SF ? cu : cu * ri; };
+    float cu[R];
     float x[R], ri[R];
     if (CH) {
         float P[R];
@@ -126,7 +133,7 @@ __device__ __forceinline__ void relax32_column(const bf16x4 *__restrict__ cpack,
         for (int j = 0; j < R; ++j) {
             const int k = row(j);
             float t = 0.f, b = 1.f;
-            ri[j] = 0.f;
+            ri[j] = cu[j] = 0.f;
             if (k < n_r) {
                 const size_t i = base + k;
                 float d = (float)f[i];
@@ -138,6 +145,7 @@ __device__ __forceinline__ void relax32_column(const bf16x4 *__restrict__ cpack,
                     d = fmaf(bf(cp.z), v2, fmaf(bf(cp.y), v1, fmaf(bf(cp.x), v0, d)));
                 }
                 ri[j] = __ldg(&rinv[i]);
+                cu[j] = above_load(i);
                 t = d * ri[j];
                 b = below(k, i, ri[j]);
             }
@@ -162,7 +170,7 @@ __device__ __forceinline__ void relax32_column(const bf16x4 *__restrict__ cpack,
 #pragma unroll
         for (int j = R - 1; j >= 0; --j) {
             const int k = row(j);
-            const float c = k < n_r ? above(k, base + k, ri[j]) : 0.f;
+            const float c = k < n_r ? above(cu[j], ri[j]) : 0.f;
             if (k >= n_r) x[j] = 0.f;
             if (j < R - 1) x[j] = fmaf(c, x[j + 1], x[j]);
             P[j] = j == R - 1 ? c : c * P[j + 1];
@@ -189,7 +197,7 @@ __device__ __forceinline__ void relax32_column(const bf16x4 *__restrict__ cpack,
         for (int r = 0; r < R; ++r) {
             const int k = 32 * r + lane;
             float A = 0.f, B = 0.f;
-            ri[r] = 0.f;
+            ri[r] = cu[r] = 0.f;
             if (k < n_r) {
                 const size_t i = base + k;
                 float d = (float)f[i];
@@ -201,6 +209,7 @@ __device__ __forceinline__ void relax32_column(const bf16x4 *__restrict__ cpack,
                     d = fmaf(bf(cp.z), v2, fmaf(bf(cp.y), v1, fmaf(bf(cp.x), v0, d)));
                 }
                 ri[r] = __ldg(&rinv[i]);
+                if (PF) cu[r] = above_load(i);
                 B = d * ri[r];
                 A = below(k, i, ri[r]);
             }
@@ -222,7 +231,7 @@ __device__ __forceinline__ void relax32_column(const bf16x4 *__restrict__ cpack,
             const int k = 32 * r + lane;
             float A = 0.f, B = 0.f;
             if (k < n_r) {
-                A = above(k, base + k, ri[r]);
+                A = above(PF ? cu[r] : above_load(base + k), ri[r]);
                 B = x[r];
             }
 #pragma unroll
@@ -301,8 +310,8 @@ __device__ __forceinline__ int batch_item(const int *off, int n_items, int x)
 // slot w - woff[it] of item it, with that item's level data and vectors, exactly as
 // k_relax32_scan does for the item's own pass; members whose loop has stopped
 // (active == 0) are skipped.
-template <int MODE, typename TF, int R>
-__global__ void __launch_bounds__(256) k_relax32_batch(const __grid_constant__ RelaxBatchArgs a,
+template <int MODE, typename TF, int R, int CAP>
+__global__ void __launch_bounds__(256) k_relax32_batch(const __grid_constant__ RelaxBatchArgsT<CAP> a,
                                                        const int *__restrict__ active)
 {
     const int lane = threadIdx.x & 31;
@@ -374,8 +383,8 @@ __global__ void __launch_bounds__(kThreads32)
 // restrictions in one launch.  Each item's rows occupy a range of the launch's
 // positions starting at roff[it], a multiple of 32, so that a warp's positions belong
 // to one item; position x is coarse row x - roff[it] of that item.
-template <typename TF>
-__global__ void __launch_bounds__(kThreads32) k_restrict32_batch(const __grid_constant__ RestrictBatchArgs a,
+template <typename TF, int CAP>
+__global__ void __launch_bounds__(kThreads32) k_restrict32_batch(const __grid_constant__ RestrictBatchArgsT<CAP> a,
                                                                  int total, const int *__restrict__ active)
 {
     pdl_wait();
@@ -487,19 +496,53 @@ cudaError_t launch_resid_restrict32(const Launch &L, const LevelDev &fine, const
                     fine.cxv_on ? fine.cxv : nullptr, L.dr32, L.n_r, f, u, fc, Nc);
 }
 
+// The launch's items in a parameter block of capacity CAP (>= the item count).
+template <int CAP>
+RelaxBatchArgsT<CAP> shrink_relax(const RelaxBatchArgs &a)
+{
+    RelaxBatchArgsT<CAP> s{};
+    s.n_items = a.n_items;
+    for (int i = 0; i < a.n_items && i < CAP; ++i) {
+        s.off[i] = a.off[i];
+        s.items[i] = a.items[i];
+    }
+    return s;
+}
+template <int CAP>
+RestrictBatchArgsT<CAP> shrink_restrict(const RestrictBatchArgs &a)
+{
+    RestrictBatchArgsT<CAP> s{};
+    s.n_items = a.n_items;
+    for (int i = 0; i < a.n_items && i < CAP; ++i) {
+        s.off[i] = a.off[i];
+        s.items[i] = a.items[i];
+    }
+    return s;
+}
+
+template <int MODE, typename TF, int CAP>
+cudaError_t relax32_batch_c(const Launch &L, int n_r_max, const RelaxBatchArgs &big, unsigned grid, int nt,
+                            const int *active)
+{
+    const RelaxBatchArgsT<CAP> a = shrink_relax<CAP>(big);
+    // the items of a launch share the rows-per-lane class of their column height
+    if (n_r_max <= 32) return launch_k(L, k_relax32_batch<MODE, TF, 1, CAP>, grid, nt, 0, a, active);
+    if (n_r_max <= 64) return launch_k(L, k_relax32_batch<MODE, TF, 2, CAP>, grid, nt, 0, a, active);
+    if (n_r_max <= 128) return launch_k(L, k_relax32_batch<MODE, TF, 4, CAP>, grid, nt, 0, a, active);
+    if (n_r_max <= 256) return launch_k(L, k_relax32_batch<MODE, TF, 8, CAP>, grid, nt, 0, a, active);
+    if (n_r_max <= 512) return launch_k(L, k_relax32_batch<MODE, TF, 16, CAP>, grid, nt, 0, a, active);
+    return launch_k(L, k_relax32_batch<MODE, TF, 32, CAP>, grid, nt, 0, a, active);
+}
+
 template <int MODE, typename TF>
 cudaError_t relax32_batch_t(const Launch &L, int n_r_max, const RelaxBatchArgs &a, long total_warps, int wpb,
                             const int *active)
 {
     const unsigned grid = (unsigned)((total_warps + wpb - 1) / wpb);
     const int nt = 32 * wpb;
-    // the items of a launch share the rows-per-lane class of their column height
-    if (n_r_max <= 32) return launch_k(L, k_relax32_batch<MODE, TF, 1>, grid, nt, 0, a, active);
-    if (n_r_max <= 64) return launch_k(L, k_relax32_batch<MODE, TF, 2>, grid, nt, 0, a, active);
-    if (n_r_max <= 128) return launch_k(L, k_relax32_batch<MODE, TF, 4>, grid, nt, 0, a, active);
-    if (n_r_max <= 256) return launch_k(L, k_relax32_batch<MODE, TF, 8>, grid, nt, 0, a, active);
-    if (n_r_max <= 512) return launch_k(L, k_relax32_batch<MODE, TF, 16>, grid, nt, 0, a, active);
-    return launch_k(L, k_relax32_batch<MODE, TF, 32>, grid, nt, 0, a, active);
+    if (a.n_items <= 2) return relax32_batch_c<MODE, TF, 2>(L, n_r_max, a, grid, nt, active);
+    if (a.n_items <= 8) return relax32_batch_c<MODE, TF, 8>(L, n_r_max, a, grid, nt, active);
+    return relax32_batch_c<MODE, TF, kBatchItems>(L, n_r_max, a, grid, nt, active);
 }
 
 template <typename TF>
@@ -520,7 +563,12 @@ cudaError_t launch_restrict32_batch(const Launch &L, const RestrictBatchArgs &a,
 {
     if (a.n_items <= 0 || total <= 0) return cudaSuccess;
     if (a.n_items > kBatchItems) return cudaErrorInvalidValue;
-    return launch_k(L, k_restrict32_batch<TF>, grid32(total, L.sm_count), kThreads32, 0, a, (int)total, active);
+    const int grid = grid32(total, L.sm_count);
+    if (a.n_items <= 2)
+        return launch_k(L, k_restrict32_batch<TF, 2>, grid, kThreads32, 0, shrink_restrict<2>(a), (int)total, active);
+    if (a.n_items <= 8)
+        return launch_k(L, k_restrict32_batch<TF, 8>, grid, kThreads32, 0, shrink_restrict<8>(a), (int)total, active);
+    return launch_k(L, k_restrict32_batch<TF, kBatchItems>, grid, kThreads32, 0, a, (int)total, active);
 }
 
 cudaError_t launch_prolong_add32(const Launch &L, const LevelDev &fine, const float *uc, float *u)

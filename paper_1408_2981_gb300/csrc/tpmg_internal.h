@@ -228,18 +228,24 @@ struct BatchRestrictItem {  // one member's FP32 residual + restriction
     int n_r, Nc, member;
 };
 
-// The work list of one launch, passed by value as the kernel's parameter (about 7 KB,
-// read through the constant cache): items [n_items] with their first warps / positions.
-struct RelaxBatchArgs {
+// The work list of one launch, passed by value as the kernel's parameter (read through
+// the constant cache): items [n_items] with their first warps / positions.  CAP is the
+// capacity of the launch's parameter block: the smallest of 2, 8 and kBatchItems that
+// holds its items, since a launch's cost grows with the size of its parameters.
+template <int CAP>
+struct RelaxBatchArgsT {
     int n_items;
-    int off[kBatchItems];   // first warp of each item (ascending, off[0] = 0)
-    BatchRelaxItem items[kBatchItems];
+    int off[CAP];           // first warp of each item (ascending, off[0] = 0)
+    BatchRelaxItem items[CAP];
 };
-struct RestrictBatchArgs {
+template <int CAP>
+struct RestrictBatchArgsT {
     int n_items;
-    int off[kBatchItems];   // first position of each item (multiples of 32, ascending, off[0] = 0)
-    BatchRestrictItem items[kBatchItems];
+    int off[CAP];           // first position of each item (multiples of 32, ascending, off[0] = 0)
+    BatchRestrictItem items[CAP];
 };
+using RelaxBatchArgs = RelaxBatchArgsT<kBatchItems>;
+using RestrictBatchArgs = RestrictBatchArgsT<kBatchItems>;
 
 struct BatchMemberDev {     // one member's outer FP64 iteration (finest level, factorised operator)
     const int4 *nbr;

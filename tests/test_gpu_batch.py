@@ -187,11 +187,12 @@ def own_solve(kw, f, rtol, max_iter=100):
     return st, it, rel, u
 
 
-def test_worklist_batch_matches_individual_solves():
+@pytest.mark.parametrize("groups", [1, 0, 6])   # all members in one schedule, the default, one each
+def test_worklist_batch_matches_individual_solves(groups):
     solvers = [binding.Solver(**kw) for kw in WORKLIST]
     fs = [rhs(s, 30 + j) for j, s in enumerate(solvers)]
     us = [torch.zeros_like(f) for f in fs]
-    b = binding.Batch(solvers, fs, us, rtol=1e-6, max_iter=100)
+    b = binding.Batch(solvers, fs, us, rtol=1e-6, max_iter=100, form="worklist", groups=groups)
     assert b.form == "worklist"
     for rep in range(2):   # a second run from zero guesses repeats the first
         for u in us:
@@ -215,7 +216,7 @@ def test_worklist_batch_many_right_hand_sides_on_one_operator():
     fs = [rhs(s, 40 + j) for j, s in enumerate(solvers)]
     us = [torch.zeros_like(f) for f in fs]
     b = binding.Batch(solvers, fs, us, rtol=1e-7, max_iter=100)
-    assert b.form == "worklist"
+    assert b.form == "worklist"   # a repeated context takes the work list automatically
     st, it, rel, sts, _ = b.run()
     torch.cuda.synchronize()
     assert st == binding.TPMG_OK
@@ -231,7 +232,7 @@ def test_worklist_batch_reports_each_problem():
     fs = [rhs(s, j) for j, s in enumerate(solvers)]
     fs[1] = torch.zeros_like(fs[1])          # zero right-hand side: done in 0 iterations
     us = [torch.zeros_like(f) for f in fs]
-    b = binding.Batch(solvers, fs, us, rtol=1e-12, max_iter=3)
+    b = binding.Batch(solvers, fs, us, rtol=1e-12, max_iter=3, form="worklist", groups=2)
     assert b.form == "worklist"
     st, it, rel, sts, _ = b.run()
     assert sts[1] == binding.TPMG_OK and it[1] == 0 and rel[1] == 0.0
@@ -257,7 +258,7 @@ def test_worklist_batch_member_matches_the_oracle():
     for rtol in (1e-11, 1e-5):
         fs = [rhs(a, 50), rhs(c, 51)]
         us = [torch.zeros_like(f) for f in fs]
-        st, it, rel, sts, _ = binding.Batch([a, c], fs, us, rtol=rtol, max_iter=300).run()
+        st, it, rel, sts, _ = binding.Batch([a, c], fs, us, rtol=rtol, max_iter=300, form="worklist").run()
         torch.cuda.synchronize()
         assert sts[0] == binding.TPMG_OK
         f0, u0 = fs[0].cpu().numpy(), us[0].cpu().numpy()
@@ -276,10 +277,15 @@ def test_worklist_batch_member_matches_the_oracle():
 
 
 def test_batch_form_follows_the_members():
-    mixed = binding.Solver(**WORKLIST[2])
+    mixed, mixed2 = binding.Solver(**WORKLIST[2]), binding.Solver(**WORKLIST[1])
     fp64 = binding.Solver(**PROBLEMS[0])
-    f1, f2 = rhs(mixed, 0), rhs(fp64, 0)
-    assert binding.Batch([mixed, fp64], [f1, f2], [torch.zeros_like(f1), torch.zeros_like(f2)]).form == "branches"
+    f1, f2, f3 = rhs(mixed, 0), rhs(fp64, 0), rhs(mixed2, 0)
+    z = torch.zeros_like
+    assert binding.Batch([mixed, fp64], [f1, f2], [z(f1), z(f2)]).form == "branches"
+    assert binding.Batch([mixed, mixed2], [f1, f3], [z(f1), z(f3)]).form == "branches"   # distinct contexts
+    assert binding.Batch([mixed, mixed2], [f1, f3], [z(f1), z(f3)], form="worklist").form == "worklist"
+    with pytest.raises(binding.TPMGError):   # an FP64 member cannot join the work list
+        binding.Batch([mixed, fp64], [f1, f2], [z(f1), z(f2)], form="worklist")
     u1, u2 = torch.zeros_like(f1), torch.zeros_like(f1)
     with pytest.raises(binding.TPMGError) as exc:   # two members writing one solution vector
         binding.Batch([mixed, mixed], [f1, f1.clone()], [u1, u1])
