@@ -543,7 +543,7 @@ def run_tpmg(args, wl):
         cpu = {"value": v_o, "unit": "unknowns/s", "cores": 1, "kind": "oracle", "sample": sample, "cpu": cpu_model()}
         cpu_threads = time_oracle_threads(wl, args.rtol, iters[-1])
     extra = None
-    tuning = [["warp", "cta64", "cta128", "cta256"][v] if v >= 0 else "heuristic" for v, _ in s.tuning()]
+    tuning = [["warp", "cta64", "cta128", "cta256", "warp-deep"][v] if v >= 0 else "heuristic" for v, _ in s.tuning()]
     if rank == 0 and world == 1 and not args.no_extra_configs and args.workload == "81920x64":
         s.close()
         extra = run_extra_configs(args, stream, flush)

@@ -149,12 +149,21 @@ typedef struct {
                             0..4 (mixed precision 0..3): that variant of tpmg_query_tuning on every
                             level (variant 4 on a warp-scan level: its default CTA shape).  The
                             results are identical. */
+    int    scaled_rhs;   /* FP64 V-cycle, factorised stencil: 1 (default) the levels relaxed by
+                            twisted tasks keep their horizontal couplings divided by the pivots,
+                            hr_k g_e / p_k, per unknown (24 bytes), and the relaxation writes
+                            f / p_k once per colour and visit of a level, so that a pass forms its
+                            right-hand side in 3 FP64 operations a row instead of 5 (allocated
+                            only where they fit; otherwise the factorised form).  0: the
+                            factorised form.  Equal in exact arithmetic; the rounding differs by
+                            a few ulp of the right-hand side. */
 } tpmg_params;
 
 /* Fills *p with the defaults: refinement 3, n_levels 4, n_r 16, H = 10/6371,
  * grading 1, omega2 0 with courant_c 8, nu 2/2/1, block-SOR with relax 1,
  * factorised storage, circumcentres, FP64, graphs and autotuning on,
- * scan_max_cells 5120, outer CG, constant prolongation, programmatic launch, relax_variant -1.
+ * scan_max_cells 5120, outer CG, constant prolongation, programmatic launch, relax_variant -1,
+ * scaled_rhs 1.
  * Returns TPMG_ERR_INVALID_ARG if p is NULL. */
 tpmg_status tpmg_default_params(tpmg_params *p);
 
@@ -240,8 +249,9 @@ tpmg_status tpmg_vcycle(tpmg_ctx *ctx, const double *d_r, double *d_z);
  * the device memory through its own pool and forbids other allocations once
  * its time loop runs, or code for which the device synchronisation that
  * cudaMalloc / cudaFree can cause is not acceptable.  This call allocates
- * nothing: the work vectors of the coarse levels (and the second buffer of the
- * block-Jacobi smoother) come from one fixed device array built into the
+ * nothing: the work vectors of the coarse levels (the second buffer of the
+ * block-Jacobi smoother, and the f / pivot vectors of levels relaxed with
+ * scaled couplings, params.scaled_rhs) come from one fixed device array built into the
  * library, of TPMG_VCYCLE_NOALLOC_MAX_DOUBLES doubles, which every GPU that
  * loads the library holds until the process exits.  The context itself still
  * comes from tpmg_setup, and this call neither reads nor writes the context's
@@ -251,8 +261,9 @@ tpmg_status tpmg_vcycle(tpmg_ctx *ctx, const double *d_r, double *d_z);
  * d_r, d_z: device, n_cells*n_r doubles, must not overlap; d_r is not modified.
  * FP64 contexts only (TPMG_ERR_INVALID_ARG otherwise).  The context's device must be current.  Scratch needed: 2 * sum over the
  * coarse levels of n_cells_l * n_r doubles for block-SOR, plus sum over all
- * levels of n_cells_l * n_r for block Jacobi (each part rounded up to 32
- * doubles); a larger problem is rejected with INVALID_ARG before anything is
+ * levels of n_cells_l * n_r for block Jacobi, plus n_cells_l * n_r for every
+ * level relaxed with scaled couplings (each part rounded up to 32 doubles); a
+ * larger problem is rejected with INVALID_ARG before anything is
  * launched.  tpmg_setup looks up the array's device address (with the
  * context's device current), so this call only reads it.  Every call on a device shares the one array and leaves
  * the last call's values in it; no element is read before the call has written

@@ -77,7 +77,7 @@ class tpmg_params(ctypes.Structure):
                 ("coeff_storage", ctypes.c_int), ("centre", ctypes.c_int), ("precision", ctypes.c_int),
                 ("graphs", ctypes.c_int), ("autotune", ctypes.c_int), ("scan_max_cells", ctypes.c_int),
                 ("outer", ctypes.c_int), ("prolongation", ctypes.c_int), ("pdl", ctypes.c_int),
-                ("relax_variant", ctypes.c_int)]
+                ("relax_variant", ctypes.c_int), ("scaled_rhs", ctypes.c_int)]
 
 
 class tpmg_profiles(ctypes.Structure):

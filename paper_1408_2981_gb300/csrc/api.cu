@@ -245,6 +245,7 @@ bool validate(const tpmg_params *p, std::string &msg)
         msg = "relax_variant must be -1 or a relaxation kernel variant";
         return false;
     }
+    if (p->scaled_rhs != 0 && p->scaled_rhs != 1) { msg = "scaled_rhs must be 0 or 1"; return false; }
     return true;
 }
 
@@ -516,20 +517,33 @@ tpmg_status vcycle_level(tpmg_ctx *ctx, int l, const double *f, double *u, doubl
                  [&] { return launch_prolong_linear(L, fl, lv, cc, u_fine); }));
         return TPMG_OK;
     };
+    // scaled couplings: the first pass over a colour in this visit of the level writes
+    // its columns' f / pivot into lv.ft, the later passes read it (bit c: colour c;
+    // bit 63: the whole level, block Jacobi)
+    unsigned long long ft_seen = 0;
+    auto ft_mode = [&](int c) {
+        if (!lv.cs || !lv.ft) return 0;
+        const unsigned long long bit = 1ull << c;
+        const int m = (ft_seen & bit) ? 2 : 1;
+        ft_seen |= bit;
+        return m;
+    };
     // one multicolour block-SOR pass over colour c, in place in u
     auto pass = [&](int c, int mode, double *fine) -> cudaError_t {
         const int t0 = lv.colour_task_off[c], nt = lv.colour_task_off[c + 1] - t0;
         const int m = (mode == PASS_ZERO && c == 0) ? PASS_RHS_ONLY : mode;
         const double units = (double)lv.colour_cells[c] * p.n_r;
+        const int ftm = ft_mode(c);
         return run_w(ctx, TPMG_K_RELAX, units, alg_relax64(units, m, fine != nullptr), [&] {
-            return launch_relax(L, lv, ctx->vert, m, t0, nt, p.relax, f, u, u, fine);
+            return launch_relax(L, lv, ctx->vert, m, t0, nt, p.relax, f, u, u, fine, ftm);
         });
     };
     // one block-Jacobi sweep from cur into oth
     auto jacobi = [&](int mode, double *fine) -> cudaError_t {
         const int m = mode == PASS_ZERO ? PASS_RHS_ONLY : mode;
+        const int ftm = ft_mode(63);
         cudaError_t e = run_w(ctx, TPMG_K_RELAX, nunits, alg_relax64(nunits, m, fine != nullptr), [&] {
-            return launch_relax(L, lv, ctx->vert, m, 0, lv.n_tasks, p.relax, f, cur, oth, fine);
+            return launch_relax(L, lv, ctx->vert, m, 0, lv.n_tasks, p.relax, f, cur, oth, fine, ftm);
         });
         std::swap(cur, oth);
         return e;
@@ -1720,7 +1734,7 @@ tpmg_status autotune(tpmg_ctx *ctx)
         const int t0 = D.colour_task_off[c], nt = D.colour_task_off[c + 1] - t0;
         auto pass = [&]() {
             return mixed ? launch_relax32<float>(L, D, PASS_NORMAL, t0, nt, 1.f, D.u2_32, D.u32, D.u32, nullptr, nullptr)
-                         : launch_relax(L, D, ctx->vert, PASS_NORMAL, t0, nt, 1.0, D.u2, D.u2, D.u2, nullptr);
+                         : launch_relax(L, D, ctx->vert, PASS_NORMAL, t0, nt, 1.0, D.u2, D.u2, D.u2, nullptr, 2);
         };
         float best = 0.f;
         int best_var = RELAX_CTA128;
@@ -2223,6 +2237,7 @@ tpmg_status tpmg_default_params(tpmg_params *p)
     p->prolongation = TPMG_PROLONG_CONSTANT;
     p->pdl = 1;
     p->relax_variant = -1;
+    p->scaled_rhs = 1;
     return TPMG_OK;
 }
 
@@ -2354,6 +2369,19 @@ tpmg_status tpmg_setup_profiles(const tpmg_params *params, const tpmg_profiles *
         } else if (launch_outer_products(launch_of(ctx), D, ctx->vert) != cudaSuccess) {
             return bail(TPMG_ERR_CUDA);
         }
+    }
+    // levels relaxed by twisted tasks (FP64, factorised stencil): the scaled couplings
+    // (24 bytes per unknown) and the work vector of f / pivot, where they fit
+    for (LevelDev &D : ctx->lv) {
+        if (ctx->p.precision != TPMG_PREC_FP64 || !ctx->p.scaled_rhs) break;
+        if (D.scan || D.vc || D.n_colours > 63) continue;
+        const size_t nn = (size_t)D.n * n_r;
+        if (dalloc(ctx, &D.cs, 3 * nn) != cudaSuccess || dalloc(ctx, &D.ft, nn) != cudaSuccess) {
+            (void)cudaGetLastError();
+            D.cs = D.ft = nullptr;
+            continue;
+        }
+        if (launch_scaled_couplings(launch_of(ctx), D, ctx->vert) != cudaSuccess) return bail(TPMG_ERR_CUDA);
     }
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return bail(TPMG_ERR_CUDA);
     if (ctx->p.relax_variant >= 0) {
@@ -2524,7 +2552,10 @@ tpmg_status tpmg_vcycle_noalloc(tpmg_ctx *ctx, const double *d_r, double *d_z)
     const bool jac = ctx->p.smoother == TPMG_SMOOTH_JACOBI;
     auto padded = [&](int l) { return ((size_t)ctx->lv[l].n * ctx->p.n_r + 31) & ~(size_t)31; };
     size_t need = 0;
-    for (int l = 0; l < L; ++l) need += (l < L - 1 ? 2 : 0) * padded(l) + (jac ? padded(l) : 0);
+    // f, u of the coarse levels; block Jacobi's second buffer; f / pivot where the level
+    // relaxes with scaled couplings
+    for (int l = 0; l < L; ++l)
+        need += (l < L - 1 ? 2 : 0) * padded(l) + (jac ? padded(l) : 0) + (ctx->lv[l].ft ? padded(l) : 0);
     if (need > (size_t)TPMG_VCYCLE_NOALLOC_MAX_DOUBLES) {
         char msg[160];
         std::snprintf(msg, sizeof msg, "problem needs %zu doubles of scratch; the fixed array holds %u", need,
@@ -2535,22 +2566,24 @@ tpmg_status tpmg_vcycle_noalloc(tpmg_ctx *ctx, const double *d_r, double *d_z)
     CU(cudaGetDevice(&dev));
     if (dev != ctx->device) return fail(ctx, TPMG_ERR_INVALID_ARG, "the context's device must be current");
     double *const base = ctx->noalloc_base;   // looked up by tpmg_setup
-    struct Saved { double *f, *u, *u2; } saved[16];   // n_levels <= 10
+    struct Saved { double *f, *u, *u2, *ft; } saved[16];   // n_levels <= 10
     size_t off = 0;
     for (int l = 0; l < L; ++l) {
         LevelDev &D = ctx->lv[l];
-        saved[l] = Saved{D.f, D.u, D.u2};
+        saved[l] = Saved{D.f, D.u, D.u2, D.ft};
         if (l < L - 1) {
             D.f = base + off; off += padded(l);
             D.u = base + off; off += padded(l);
         }
         if (jac) { D.u2 = base + off; off += padded(l); }
+        if (D.ft) { D.ft = base + off; off += padded(l); }
     }
     const tpmg_status st = vcycle_fine(ctx, d_r, d_z);
     for (int l = 0; l < L; ++l) {
         ctx->lv[l].f = saved[l].f;
         ctx->lv[l].u = saved[l].u;
         ctx->lv[l].u2 = saved[l].u2;
+        ctx->lv[l].ft = saved[l].ft;
     }
     return st;
 }

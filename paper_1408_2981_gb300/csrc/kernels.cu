@@ -640,6 +640,22 @@ __global__ void k_twisted_factors(int n_tasks, OpView o, const int *__restrict__
     M[kRelaxCols + col] = cj1 * ig;
 }
 
+// Scaled couplings of the twisted relaxation (set-up, after k_twisted_factors): three
+// planes of n n_r doubles, cs_e [T][k] = hr_k g_e(T) rinv [T][k] (e = 0, 1, 2).
+__global__ void k_scaled_couplings(OpView o, long nn, const double *__restrict__ rinv, double *__restrict__ cs)
+{
+    const int n_r = o.n_r;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < nn; i += (long)gridDim.x * blockDim.x) {
+        const long T = i / n_r;
+        const int k = (int)(i - T * n_r);
+        const dbl4 g = o.g[T];
+        const double h = o.hr[k], iv = rinv[i];
+        cs[i] = (h * g.x) * iv;
+        cs[nn + i] = (h * g.y) * iv;
+        cs[2 * nn + i] = (h * g.z) * iv;
+    }
+}
+
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
     const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
@@ -719,6 +735,90 @@ __device__ __forceinline__ void twisted_solve(const double *B, const double *C, 
             }
 #pragma unroll
             for (int q = 0; q < P; ++q) { cc[q] = cn[q]; yy[q] = yn[q]; }
+        }
+    }
+}
+
+// Right-hand-side forms of a twisted relaxation pass (phase A), per row k of a
+// column T with the neighbours' iterates u_e and pivot p_k:
+//   SK_FAC           t = (f + hr_k sum_e g_e u_e) / p_k    (factorised couplings)
+//   SK_FULL          t = (f + sum_e c_e u_e) / p_k         (stencil stored per unknown)
+//   SK_SCALED_FIRST  t = f / p_k + sum_e cs_e u_e, also writing f / p_k to ft
+//   SK_SCALED        t = ft + sum_e cs_e u_e
+// with the scaled couplings cs_e = hr_k g_e / p_k stored per unknown.  The same
+// value in exact arithmetic; the scaled forms take 3 FP64 operations a row instead
+// of 5 once the colour's ft is written (by its first pass in a visit of the level).
+enum RhsForm { SK_FAC = 0, SK_FULL = 1, SK_SCALED_FIRST = 2, SK_SCALED = 3 };
+
+// Phase A for the elements e = tid, tid + NTH, ... of the task's [16][n_r] block:
+// t into the shared tile [16][n_r + 1], U elements' loads in flight per thread.
+// Padding columns (cell -1) get t = 0.  SK_SCALED reads ft through f.
+template <int MODE, int SK, int U, int NTH>
+__device__ __forceinline__ void gather_rhs(const OpView &o, const int *s_cell, const int4 *s_nb, const dbl4 *s_g,
+                                           const double *__restrict__ rinv, const double *__restrict__ csc,
+                                           size_t plane, const double *__restrict__ f, const double *u_in,
+                                           double *__restrict__ ft_out, double *tile, int tid)
+{
+    const int n_r = o.n_r, ld = n_r + 1, ne = kRelaxCols * n_r;
+    for (int e0 = tid; e0 < ne; e0 += NTH * U) {
+        double fv[U], iv[U], v0[U], v1[U], v2[U];
+        dbl4 cs[U];   // SK_FULL: the stored stencil; scaled forms: the scaled couplings in x, y, z
+        int col[U], kk[U], gi[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int e = e0 + NTH * q;
+            col[q] = -1;
+            kk[q] = 0;
+            gi[q] = -1;
+            fv[q] = iv[q] = v0[q] = v1[q] = v2[q] = 0.0;
+            if (SK != SK_FAC) cs[q] = dbl4{0.0, 0.0, 0.0, 0.0};
+            if (e < ne) {
+                const int c = e / n_r, k = e - c * n_r;
+                col[q] = c;
+                kk[q] = k;
+                const int T = s_cell[c];
+                if (T >= 0) {
+                    const int i = T * n_r + k;
+                    gi[q] = i;
+                    fv[q] = f[i];
+                    if (SK != SK_SCALED) iv[q] = __ldg(&rinv[i]);
+                    if (MODE != PASS_RHS_ONLY) {
+                        const int4 nb = s_nb[c];
+                        if (MODE == PASS_NORMAL || (nb.w & 1)) v0[q] = u_in[nb.x * n_r + k];
+                        if (MODE == PASS_NORMAL || (nb.w & 2)) v1[q] = u_in[nb.y * n_r + k];
+                        if (MODE == PASS_NORMAL || (nb.w & 4)) v2[q] = u_in[nb.z * n_r + k];
+                        if (SK == SK_FULL) cs[q] = o.c[i];
+                        if (SK >= SK_SCALED_FIRST) {
+                            cs[q].x = __ldg(&csc[i]);
+                            cs[q].y = __ldg(&csc[plane + i]);
+                            cs[q].z = __ldg(&csc[2 * plane + i]);
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            if (col[q] < 0) continue;
+            double d = fv[q];
+            if (SK >= SK_SCALED_FIRST) {
+                if (SK == SK_SCALED_FIRST) {
+                    d = fv[q] * iv[q];
+                    if (ft_out && gi[q] >= 0) ft_out[gi[q]] = d;
+                }
+                if (MODE != PASS_RHS_ONLY) d = fma(cs[q].z, v2[q], fma(cs[q].y, v1[q], fma(cs[q].x, v0[q], d)));
+                tile[col[q] * ld + kk[q]] = d;
+            } else {
+                if (MODE != PASS_RHS_ONLY) {
+                    if (SK == SK_FULL) {
+                        d = fma(cs[q].z, v2[q], fma(cs[q].y, v1[q], fma(cs[q].x, v0[q], d)));
+                    } else {
+                        const dbl4 g = s_g[col[q]];
+                        d = fma(__ldg(&o.hr[kk[q]]), fma(g.z, v2[q], fma(g.y, v1[q], g.x * v0[q])), d);
+                    }
+                }
+                tile[col[q] * ld + kk[q]] = d * iv[q];
+            }
         }
     }
 }
@@ -889,12 +989,13 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-template <int MODE, bool STAGE, int NT, bool HF>
+template <int MODE, bool STAGE, int NT, int SK>
 __global__ void __launch_bounds__(NT, STAGE ? 1 : 6)
     k_relax(OpView o, const int *__restrict__ cells, const int4 *__restrict__ tnb, const dbl4 *__restrict__ tg,
             const double *__restrict__ rinv, const double *__restrict__ fb, const double *__restrict__ fcf,
             const double *__restrict__ fm, int S, int j, int task0, const double *__restrict__ f, const double *u_in,
-            double *u_out, double *__restrict__ u_fine, double relax)
+            double *u_out, double *__restrict__ u_fine, double relax, const double *__restrict__ csc, size_t plane,
+            double *__restrict__ ft_out)
 {
     extern __shared__ double smem[];
     __shared__ int s_cell[kRelaxCols];
@@ -926,53 +1027,10 @@ __global__ void __launch_bounds__(NT, STAGE ? 1 : 6)
     pdl_wait();
     pdl_trigger();
     __syncthreads();
-    // elements per thread with loads in flight (fewer with the per-unknown stencil,
-    // whose 32-byte rows take registers of their own)
-    constexpr int U = HF ? (STAGE ? 4 : 2) : (STAGE ? 8 : 4);
-    for (int e0 = threadIdx.x; e0 < ne; e0 += NT * U) {
-        double fv[U], iv[U], v0[U], v1[U], v2[U];
-        dbl4 cs[U];
-        int col[U], kk[U];
-#pragma unroll
-        for (int q = 0; q < U; ++q) {
-            const int e = e0 + NT * q;
-            col[q] = -1;
-            kk[q] = 0;
-            fv[q] = iv[q] = v0[q] = v1[q] = v2[q] = 0.0;
-            if (HF) cs[q] = dbl4{0.0, 0.0, 0.0, 0.0};
-            if (e < ne) {
-                const int c = e / n_r, k = e - c * n_r;
-                col[q] = c;
-                kk[q] = k;
-                const int T = s_cell[c];
-                if (T >= 0) {
-                    fv[q] = f[T * n_r + k];
-                    iv[q] = __ldg(&rinv[T * n_r + k]);
-                    if (MODE != PASS_RHS_ONLY) {
-                        const int4 nb = s_nb[c];
-                        if (MODE == PASS_NORMAL || (nb.w & 1)) v0[q] = u_in[nb.x * n_r + k];
-                        if (MODE == PASS_NORMAL || (nb.w & 2)) v1[q] = u_in[nb.y * n_r + k];
-                        if (MODE == PASS_NORMAL || (nb.w & 4)) v2[q] = u_in[nb.z * n_r + k];
-                        if (HF) cs[q] = o.c[T * n_r + k];
-                    }
-                }
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < U; ++q) {
-            if (col[q] < 0) continue;
-            double d = fv[q];
-            if (MODE != PASS_RHS_ONLY) {
-                if (HF) {
-                    d = fma(cs[q].z, v2[q], fma(cs[q].y, v1[q], fma(cs[q].x, v0[q], d)));
-                } else {
-                    const dbl4 g = s_g[col[q]];
-                    d = fma(__ldg(&o.hr[kk[q]]), fma(g.z, v2[q], fma(g.y, v1[q], g.x * v0[q])), d);
-                }
-            }
-            tile[col[q] * ld + kk[q]] = d * iv[q];
-        }
-    }
+    // elements per thread with loads in flight (fewer with couplings per unknown,
+    // whose rows take registers of their own)
+    constexpr int U = SK != SK_FAC ? (STAGE ? 4 : 2) : (STAGE ? 8 : 4);
+    gather_rhs<MODE, SK, U, NT>(o, s_cell, s_nb, s_g, rinv, csc, plane, f, u_in, ft_out, tile, threadIdx.x);
     if (STAGE) cp_async_wait_all();
     __syncthreads();
     if ((threadIdx.x >> 5) == (int)(blockIdx.x % (NT / 32))) {
@@ -1025,12 +1083,13 @@ __global__ void __launch_bounds__(NT, STAGE ? 1 : 6)
 // their sub-partitions.  DEEP: twice the loads in flight -- 8 elements per
 // lane in the gather, the solve's multipliers 8 steps ahead, 4 elements in
 // the write-back -- for more registers per warp (fewer resident warps).
-template <int MODE, bool HF, bool DEEP>
+template <int MODE, int SK, bool DEEP>
 __global__ void __launch_bounds__(32, DEEP ? 12 : 16)
     k_relax_warp(OpView o, const int *__restrict__ cells, const int4 *__restrict__ tnb, const dbl4 *__restrict__ tg,
                  const double *__restrict__ rinv, const double *__restrict__ fb, const double *__restrict__ fcf,
                  const double *__restrict__ fm, int S, int j, int task0, const double *__restrict__ f,
-                 const double *u_in, double *u_out, double *__restrict__ u_fine, double relax)
+                 const double *u_in, double *u_out, double *__restrict__ u_fine, double relax,
+                 const double *__restrict__ csc, size_t plane, double *__restrict__ ft_out)
 {
     extern __shared__ double tile[];
     __shared__ int s_cell[kRelaxCols];
@@ -1050,50 +1109,7 @@ __global__ void __launch_bounds__(32, DEEP ? 12 : 16)
     pdl_trigger();
     __syncwarp();
     constexpr int U = DEEP ? 8 : 4;
-    for (int e0 = lane; e0 < ne; e0 += 32 * U) {
-        double fv[U], iv[U], v0[U], v1[U], v2[U];
-        dbl4 cs[U];
-        int col[U], kk[U];
-#pragma unroll
-        for (int q = 0; q < U; ++q) {
-            const int e = e0 + 32 * q;
-            col[q] = -1;
-            kk[q] = 0;
-            fv[q] = iv[q] = v0[q] = v1[q] = v2[q] = 0.0;
-            if (HF) cs[q] = dbl4{0.0, 0.0, 0.0, 0.0};
-            if (e < ne) {
-                const int c = e / n_r, k = e - c * n_r;
-                col[q] = c;
-                kk[q] = k;
-                const int T = s_cell[c];
-                if (T >= 0) {
-                    fv[q] = f[T * n_r + k];
-                    iv[q] = __ldg(&rinv[T * n_r + k]);
-                    if (MODE != PASS_RHS_ONLY) {
-                        const int4 nb = s_nb[c];
-                        if (MODE == PASS_NORMAL || (nb.w & 1)) v0[q] = u_in[nb.x * n_r + k];
-                        if (MODE == PASS_NORMAL || (nb.w & 2)) v1[q] = u_in[nb.y * n_r + k];
-                        if (MODE == PASS_NORMAL || (nb.w & 4)) v2[q] = u_in[nb.z * n_r + k];
-                        if (HF) cs[q] = o.c[T * n_r + k];
-                    }
-                }
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < U; ++q) {
-            if (col[q] < 0) continue;
-            double d = fv[q];
-            if (MODE != PASS_RHS_ONLY) {
-                if (HF) {
-                    d = fma(cs[q].z, v2[q], fma(cs[q].y, v1[q], fma(cs[q].x, v0[q], d)));
-                } else {
-                    const dbl4 g = s_g[col[q]];
-                    d = fma(__ldg(&o.hr[kk[q]]), fma(g.z, v2[q], fma(g.y, v1[q], g.x * v0[q])), d);
-                }
-            }
-            tile[col[q] * ld + kk[q]] = d * iv[q];
-        }
-    }
+    gather_rhs<MODE, SK, U, 32>(o, s_cell, s_nb, s_g, rinv, csc, plane, f, u_in, ft_out, tile, lane);
     __syncwarp();
     const size_t fbase = (size_t)t * S * 32 + lane;
     twisted_solve<DEEP ? 8 : 4>(fb + fbase, fcf + fbase, s_m, tile + (lane & (kRelaxCols - 1)) * ld, n_r, j, lane);
@@ -1540,21 +1556,32 @@ cudaError_t launch_twisted_factors(const Launch &L, const LevelDev &lv, const Ve
     const int n = lv.n_tasks * kRelaxCols;
     k_twisted_factors<<<(n + 127) / 128, 128, 0, L.s>>>(lv.n_tasks, make_view(lv, v, L.n_r), lv.task_cells, lv.steps,
                                                          lv.jmid, lv.rinv, lv.fb, lv.fc, lv.fm);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && lv.cs) e = launch_scaled_couplings(L, lv, v);
+    return e;
+}
+
+cudaError_t launch_scaled_couplings(const Launch &L, const LevelDev &lv, const VertDev &v)
+{
+    if (!lv.cs) return cudaSuccess;
+    const long nn = (long)lv.n * L.n_r;
+    k_scaled_couplings<<<grid_for(nn, 256, L.sm_count), 256, 0, L.s>>>(make_view(lv, v, L.n_r), nn, lv.rinv, lv.cs);
     return cudaGetLastError();
 }
 
-template <int MODE, bool STAGE, int NT, bool HF>
+template <int MODE, bool STAGE, int NT, int SK>
 static cudaError_t relax_launch_t(const Launch &L, const LevelDev &lv, const VertDev &v, int task0, int n_tasks,
                                   double relax, const double *f, const double *u_in, double *u_out, double *u_fine,
                                   size_t smem)
 {
-    auto kern = k_relax<MODE, STAGE, NT, HF>;
+    auto kern = k_relax<MODE, STAGE, NT, SK>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     return launch_k(L, kern, n_tasks, NT, smem, make_view(lv, v, L.n_r), lv.task_cells, lv.task_nbr, lv.task_g,
-                    lv.rinv, lv.fb, lv.fc, lv.fm, lv.steps, lv.jmid, task0, f, u_in, u_out, u_fine, relax);
+                    lv.rinv, lv.fb, lv.fc, lv.fm, lv.steps, lv.jmid, task0, f, u_in, u_out, u_fine, relax,
+                    (const double *)lv.cs, (size_t)lv.n * L.n_r, SK == SK_SCALED_FIRST ? lv.ft : (double *)nullptr);
 }
 
 // Kernel choice (RELAX_*): the level's autotuned variant, or without one the
@@ -1586,16 +1613,17 @@ static cudaError_t relax_scan(const Launch &L, const LevelDev &lv, const VertDev
     return relax_scan_r<MODE, 32, HF>(L, lv, v, var, task0, n_tasks, relax, f, u_in, u_out, u_fine);
 }
 
-template <int MODE, bool HF>
-static cudaError_t relax_launch_hf(const Launch &L0, const LevelDev &lv, const VertDev &v, int task0, int n_tasks,
+template <int MODE, int SK>
+static cudaError_t relax_launch_sk(const Launch &L0, const LevelDev &lv, const VertDev &v, int task0, int n_tasks,
                                    double relax, const double *f, const double *u_in, double *u_out, double *u_fine)
 {
-    if (lv.scan) {   // CTAs of 1, 2, 4 or 8 warps (variants 0..3; the warp-specialised variant 4 is for tasks)
+    constexpr bool HF = SK == SK_FULL;
+    if (lv.scan) {   // CTAs of 1, 2, 4 or 8 warps (variants 0..3; the deep-pipeline variant 4 is for tasks)
         const int var = (lv.relax_variant < 0 || lv.relax_variant > RELAX_CTA256) ? RELAX_CTA128 : lv.relax_variant;
         return relax_scan<MODE, HF>(L0, lv, v, var, task0, n_tasks, relax, f, u_in, u_out, u_fine);
     }
     // a small colour of a larger level: warp scans in CTAs of 4 warps (the level's tuned
-    // variant is a twisted-task kernel's)
+    // variant is a twisted-task kernel's); they form their right-hand side from f
     if (n_tasks <= lv.scan_pass_tasks)
         return relax_scan<MODE, HF>(L0, lv, v, RELAX_CTA128, task0, n_tasks, relax, f, u_in, u_out, u_fine);
     // The twisted-task kernels are launched plainly: measured on GB300, programmatic
@@ -1603,33 +1631,43 @@ static cudaError_t relax_launch_hf(const Launch &L0, const LevelDev &lv, const V
     // 7 x 128), while it speeds up the scan, transfer and vector kernels.
     Launch L = L0;
     L.pdl = false;
+    const double *rhs = SK == SK_SCALED ? lv.ft : f;   // the scaled form reads f / pivot
     const size_t tile = (((size_t)kRelaxCols * (L.n_r + 1) + 1) & ~(size_t)1) * sizeof(double);
     int var = lv.relax_variant;
     if (var < 0) var = (n_tasks >= 8 * L.sm_count && tile <= 32 * 1024) ? RELAX_WARP : RELAX_CTA128;
     if ((var == RELAX_WARP || var == RELAX_WARP_DEEP) && tile <= 32 * 1024) {
-        auto kern = var == RELAX_WARP_DEEP ? k_relax_warp<MODE, HF, true> : k_relax_warp<MODE, HF, false>;
+        auto kern = var == RELAX_WARP_DEEP ? k_relax_warp<MODE, SK, true> : k_relax_warp<MODE, SK, false>;
         return launch_k(L, kern, n_tasks, 32, tile, make_view(lv, v, L.n_r), lv.task_cells, lv.task_nbr, lv.task_g,
-                        lv.rinv, lv.fb, lv.fc, lv.fm, lv.steps, lv.jmid, task0, f, u_in, u_out, u_fine, relax);
+                        lv.rinv, lv.fb, lv.fc, lv.fm, lv.steps, lv.jmid, task0, rhs, u_in, u_out, u_fine, relax,
+                        (const double *)lv.cs, (size_t)lv.n * L.n_r,
+                        SK == SK_SCALED_FIRST ? lv.ft : (double *)nullptr);
     }
     const size_t staged = tile + (size_t)2 * lv.steps * 32 * sizeof(double);
     if (staged > 160 * 1024)
-        return relax_launch_t<MODE, false, 128, HF>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine, tile);
+        return relax_launch_t<MODE, false, 128, SK>(L, lv, v, task0, n_tasks, relax, rhs, u_in, u_out, u_fine, tile);
     if (var == RELAX_CTA64)
-        return relax_launch_t<MODE, true, 64, HF>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine, staged);
+        return relax_launch_t<MODE, true, 64, SK>(L, lv, v, task0, n_tasks, relax, rhs, u_in, u_out, u_fine, staged);
     if (var == RELAX_CTA256)
-        return relax_launch_t<MODE, true, 256, HF>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine, staged);
-    return relax_launch_t<MODE, true, 128, HF>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine, staged);
+        return relax_launch_t<MODE, true, 256, SK>(L, lv, v, task0, n_tasks, relax, rhs, u_in, u_out, u_fine, staged);
+    return relax_launch_t<MODE, true, 128, SK>(L, lv, v, task0, n_tasks, relax, rhs, u_in, u_out, u_fine, staged);
 }
 
-// HF: the level's stencil is stored per unknown (TPMG^full), and the right-hand
-// side's horizontal couplings come from it.
+// The right-hand-side form of a pass: the stored stencil (TPMG^full) where the level
+// has one; otherwise, with the level's scaled couplings, SK_SCALED_FIRST for the first
+// pass over a colour in a visit of the level (ft_mode 1) and SK_SCALED after it
+// (ft_mode 2); else the factorised couplings.
 template <int MODE>
 static cudaError_t relax_launch(const Launch &L, const LevelDev &lv, const VertDev &v, int task0, int n_tasks,
-                                double relax, const double *f, const double *u_in, double *u_out, double *u_fine)
+                                double relax, const double *f, const double *u_in, double *u_out, double *u_fine,
+                                int ft_mode)
 {
     if (n_tasks <= 0) return cudaSuccess;
-    if (lv.vc) return relax_launch_hf<MODE, true>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
-    return relax_launch_hf<MODE, false>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
+    if (lv.vc) return relax_launch_sk<MODE, SK_FULL>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
+    if (lv.cs && lv.ft && ft_mode == 1)
+        return relax_launch_sk<MODE, SK_SCALED_FIRST>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
+    if (lv.cs && lv.ft && ft_mode == 2)
+        return relax_launch_sk<MODE, SK_SCALED>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
+    return relax_launch_sk<MODE, SK_FAC>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
 }
 
 cudaError_t launch_thomas_factors(const Launch &L, const LevelDev &lv, const VertDev &v)
@@ -1639,12 +1677,14 @@ cudaError_t launch_thomas_factors(const Launch &L, const LevelDev &lv, const Ver
 }
 
 cudaError_t launch_relax(const Launch &L, const LevelDev &lv, const VertDev &v, int mode, int task0, int n_tasks,
-                         double relax, const double *f, const double *u_in, double *u_out, double *u_fine)
+                         double relax, const double *f, const double *u_in, double *u_out, double *u_fine,
+                         int ft_mode)
 {
     switch (mode) {
-    case PASS_ZERO: return relax_launch<PASS_ZERO>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
-    case PASS_RHS_ONLY: return relax_launch<PASS_RHS_ONLY>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
-    default: return relax_launch<PASS_NORMAL>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine);
+    case PASS_ZERO: return relax_launch<PASS_ZERO>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine, ft_mode);
+    case PASS_RHS_ONLY:
+        return relax_launch<PASS_RHS_ONLY>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine, ft_mode);
+    default: return relax_launch<PASS_NORMAL>(L, lv, v, task0, n_tasks, relax, f, u_in, u_out, u_fine, ft_mode);
     }
 }
 

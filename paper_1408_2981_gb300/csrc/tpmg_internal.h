@@ -156,6 +156,11 @@ struct LevelDev {
     // coarse cell [n / 4], or null (then the kernel forms every child's residual)
     RestrictGeo *rgeo = nullptr;
     double *rinv1 = nullptr, *fb1 = nullptr, *fc1 = nullptr;
+    // FP64 levels relaxed by twisted tasks, factorised stencil (params.scaled_rhs, where
+    // they fit): the horizontal couplings scaled by the pivots, three planes [3][n][n_r]
+    // cs_e = hr_k g_e rinv, and the work vector ft [n][n_r] = f rinv, written by the
+    // first pass over each colour in a visit of the level and read by the later ones
+    double *cs = nullptr, *ft = nullptr;
     // workspaces (coarse levels; the finest level uses caller / PCG buffers)
     double *f = nullptr, *u = nullptr, *u2 = nullptr;
     // mixed-precision form: the stencil stored per unknown in BF16 (full
@@ -327,8 +332,14 @@ cudaError_t launch_resid_restrict(const Launch &L, const LevelDev &fine, const L
 // If u_fine is not NULL the new values are also added to the 4 children of
 // each cell in u_fine (prolongation P = R^T of Algorithm 1, fused into the
 // last pass that writes a colour).
+// ft_mode (levels with scaled couplings): 1 the pass is the first over its columns in
+// this visit of the level and writes their f / pivot into lv.ft; 2 it reads lv.ft;
+// 0 the factorised form.  Colours relaxed by the warp scans always read f.
 cudaError_t launch_relax(const Launch &L, const LevelDev &lv, const VertDev &v, int mode, int task0, int n_tasks,
-                         double relax, const double *f, const double *u_in, double *u_out, double *u_fine);
+                         double relax, const double *f, const double *u_in, double *u_out, double *u_fine,
+                         int ft_mode = 0);
+// cs of a level from its pivots (rinv): after launch_twisted_factors, which also calls it
+cudaError_t launch_scaled_couplings(const Launch &L, const LevelDev &lv, const VertDev &v);
 cudaError_t launch_prolong_add(const Launch &L, const LevelDev &fine, const double *uc, double *u);
 cudaError_t launch_prolong_linear(const Launch &L, const LevelDev &fine, const LevelDev &coarse, const double *uc,
                                   double *u);

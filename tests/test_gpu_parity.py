@@ -35,11 +35,23 @@ CASES = {
     # (140 and 66 cells), which take the warp scans; the 320- and 80-cell levels all scans
     "ref4_nr24_small_colours_scanned": dict(refinement=4, n_levels=4, n_r=24, grading=1.05, courant_c=30.0,
                                             scan_max_cells=640),
+    # every level in twisted tasks: the right-hand side from the scaled couplings (f / pivot
+    # written by each colour's first pass in a visit), and the factorised form beside it
+    "ref3_nr16_twisted_scaled": dict(refinement=3, n_levels=4, n_r=16, courant_c=8.0, nu_pre=1, nu_post=1,
+                                     nu_coarse=1, scan_max_cells=0),
+    "ref3_nr16_twisted_factorised": dict(refinement=3, n_levels=4, n_r=16, courant_c=8.0, nu_pre=1, nu_post=1,
+                                         nu_coarse=1, scan_max_cells=0, scaled_rhs=0),
+    # no pre-smoothing: each colour's first pass of a visit is a post-smoothing pass
+    "ref2_nr7_twisted_no_presmoothing": dict(refinement=2, n_levels=3, n_r=7, grading=1.1, courant_c=80.0, nu_pre=0,
+                                             nu_post=2, scan_max_cells=0),
+    "ref1_nr33_twisted_jacobi": dict(refinement=1, n_levels=2, n_r=33, courant_c=20.0, smoother=1, relax=0.6,
+                                     nu_pre=1, nu_post=1, nu_coarse=2, scan_max_cells=0),
 }
 
 
 def oracle_for(kw):
-    kw = {k: v for k, v in kw.items() if k != "scan_max_cells"}   # a kernel choice, not part of the method
+    # kernel choices, not part of the method
+    kw = {k: v for k, v in kw.items() if k not in ("scan_max_cells", "scaled_rhs")}
     if "centre" in kw:
         kw["centre_kind"] = kw.pop("centre")
     return oracle.Oracle(**kw)

@@ -28,6 +28,11 @@ CASES = {
     "mcsor_ref4_nr24_graded": dict(refinement=4, n_levels=5, n_r=24, grading=1.05, courant_c=30.0),
     "jacobi_ref1_nr33": dict(refinement=1, n_levels=2, n_r=33, courant_c=20.0, smoother=1, relax=0.6, nu_pre=1,
                              nu_post=1, nu_coarse=2),
+    # twisted tasks on every level: the f / pivot work vectors come from the array too
+    "mcsor_ref3_nr16_twisted": dict(refinement=3, n_levels=4, n_r=16, courant_c=8.0, nu_pre=1, nu_post=1,
+                                    nu_coarse=1, scan_max_cells=0),
+    "jacobi_ref2_nr16_twisted": dict(refinement=2, n_levels=3, n_r=16, courant_c=8.0, smoother=1, relax=0.7,
+                                     scan_max_cells=0),
 }
 
 
