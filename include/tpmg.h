@@ -369,8 +369,8 @@ tpmg_status tpmg_query(const tpmg_ctx *ctx, int level, int *n_cells, int *n_r, d
 
 /* The autotuner's choice on multigrid level `level`: variant = relaxation kernel
  * (FP64: 0 one warp per 16-column task, 1/2/3 one CTA of 64/128/256 threads per
- * task, 4 one warp per task with twice the loads in flight (8 elements per lane
- * in the gather, the solve's multipliers 8 steps ahead); mixed precision: one warp per
+ * task, 4 one warp per task with 6 elements per lane in flight in the gather
+ * instead of 4); mixed precision: one warp per
  * column in CTAs of 1/2/4/8 warps; -1 heuristic: not tuned) and us[5] =
  * measured microseconds of the level's largest colour pass with each variant
  * (us[4] = 0 where only four apply: mixed precision, and FP64 levels relaxed by

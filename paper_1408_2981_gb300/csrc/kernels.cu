@@ -1080,11 +1080,11 @@ __global__ void __launch_bounds__(NT, STAGE ? 1 : 6)
 // 16 columns, so the serial phases of the tasks resident on an SM overlap
 // with the gather and write-back phases of others and keep its four FP64
 // units busy.  One warp per CTA spreads the tasks evenly over the SMs and
-// their sub-partitions.  DEEP: twice the loads in flight -- 8 elements per
-// lane in the gather, the solve's multipliers 8 steps ahead, 4 elements in
-// the write-back -- for more registers per warp (fewer resident warps).
+// their sub-partitions.  DEEP: 6 elements per lane in flight in the gather
+// instead of 4 -- fewer rounds of load latency, which bound a warp's gather --
+// for more registers per warp.
 template <int MODE, int SK, bool DEEP>
-__global__ void __launch_bounds__(32, DEEP ? 12 : 16)
+__global__ void __launch_bounds__(32, 16)
     k_relax_warp(OpView o, const int *__restrict__ cells, const int4 *__restrict__ tnb, const dbl4 *__restrict__ tg,
                  const double *__restrict__ rinv, const double *__restrict__ fb, const double *__restrict__ fcf,
                  const double *__restrict__ fm, int S, int j, int task0, const double *__restrict__ f,
@@ -1108,13 +1108,13 @@ __global__ void __launch_bounds__(32, DEEP ? 12 : 16)
     pdl_wait();
     pdl_trigger();
     __syncwarp();
-    constexpr int U = DEEP ? 8 : 4;
+    constexpr int U = DEEP ? 6 : 4;
     gather_rhs<MODE, SK, U, 32>(o, s_cell, s_nb, s_g, rinv, csc, plane, f, u_in, ft_out, tile, lane);
     __syncwarp();
     const size_t fbase = (size_t)t * S * 32 + lane;
-    twisted_solve<DEEP ? 8 : 4>(fb + fbase, fcf + fbase, s_m, tile + (lane & (kRelaxCols - 1)) * ld, n_r, j, lane);
+    twisted_solve<4>(fb + fbase, fcf + fbase, s_m, tile + (lane & (kRelaxCols - 1)) * ld, n_r, j, lane);
     __syncwarp();
-    constexpr int W = DEEP ? 4 : 2;
+    constexpr int W = 2;
     for (int e0 = lane; e0 < ne; e0 += 32 * W) {
         double x[W], uo[W], uf[W][4];
         int idx[W], fi[W];

@@ -85,7 +85,7 @@ constexpr int kRelaxCols = 16;
 
 // Kernel variants of a relaxation pass (chosen per level by the autotuner).
 // FP64: one warp per 16-column task, one CTA of 64 / 128 / 256 threads per task,
-// or one warp per task with twice the loads in flight.  FP32: one warp per column
+// or one warp per task with 6 elements per lane in flight in the gather instead of 4.  FP32: one warp per column
 // in CTAs of 1 / 2 / 4 / 8 warps (the first four variants).
 enum RelaxVariant { RELAX_WARP = 0, RELAX_CTA64 = 1, RELAX_CTA128 = 2, RELAX_CTA256 = 3, RELAX_WARP_DEEP = 4,
                     RELAX_VARIANTS = 5 };

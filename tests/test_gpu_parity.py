@@ -316,8 +316,8 @@ def test_relaxation_variants_give_identical_results(name):
 
 
 def test_deep_warp_relaxation_vs_oracle():
-    """The V-cycle with the deeply pipelined one-warp twisted passes (variant 4) on
-    every level against the oracle's V-cycle (the V-cycle bound of this file)."""
+    """The V-cycle with the wide-gather one-warp twisted passes (variant 4) on every
+    level against the oracle's V-cycle (the V-cycle bound of this file)."""
     kw = VARIANT_CASES["ref4_nr24_twisted_everywhere_jacobi"]
     s, o = binding.Solver(relax_variant=4, **kw), oracle_for(kw)
     r = inputs.uniform_pm1(inputs.SEED_UNIFORM_SMALL + 61, s.N)
