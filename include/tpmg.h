@@ -157,13 +157,18 @@ typedef struct {
                             only where they fit; otherwise the factorised form).  0: the
                             factorised form.  Equal in exact arithmetic; the rounding differs by
                             a few ulp of the right-hand side. */
+    int    net_tcgen05;  /* learned form (tpmg_learned.h), hidden width 64 and n_r a multiple of 16
+                            up to 128: 1 (default) the network runs as one tcgen05 kernel (MMAs
+                            from shared memory into tensor memory), 0 as one mma.sync kernel.
+                            Both round inputs and activations to bfloat16 and accumulate in FP32;
+                            the accumulation order differs. */
 } tpmg_params;
 
 /* Fills *p with the defaults: refinement 3, n_levels 4, n_r 16, H = 10/6371,
  * grading 1, omega2 0 with courant_c 8, nu 2/2/1, block-SOR with relax 1,
  * factorised storage, circumcentres, FP64, graphs and autotuning on,
  * scan_max_cells 5120, outer CG, constant prolongation, programmatic launch, relax_variant -1,
- * scaled_rhs 1.
+ * scaled_rhs 1, net_tcgen05 1.
  * Returns TPMG_ERR_INVALID_ARG if p is NULL. */
 tpmg_status tpmg_default_params(tpmg_params *p);
 

@@ -144,9 +144,19 @@ tpmg_status tpmg_vcycle_learned(tpmg_ctx *ctx, const double *d_r, double *d_z);
  * the line relaxation that follows there.  Inside the solve the network runs as
  * one fused tensor-core kernel when its hidden width is 64 and n_r is a
  * multiple of 8 (inputs and activations rounded to bfloat16, FP32
- * accumulation); otherwise layer by layer with FP32 activations.
+ * accumulation): on tcgen05 with FP32 accumulators in tensor memory when n_r
+ * is a multiple of 16 up to 128 and params.net_tcgen05 is set (the default),
+ * else with mma.sync; otherwise layer by layer with FP32 activations.
  * Asynchronous.  Errors: INVALID_ARG (also: no network in `role`), CUDA. */
 tpmg_status tpmg_net_predict(tpmg_ctx *ctx, int role, const double *d_f, double *d_u);
+
+/* *flag = 1 if, since tpmg_setup, a network kernel on the tcgen05 tensor cores
+ * (params.net_tcgen05) gave up waiting for its matrix multiplies, else 0.  Such
+ * a kernel writes NaN over the outputs it could not compute, so that the
+ * judge of the warm start and the breakdown test of the solve reject them.
+ * Not part of the paper: a health check of this implementation.  Waits for
+ * the context's stream.  Errors: INVALID_ARG, CUDA. */
+tpmg_status tpmg_net_fault(tpmg_ctx *ctx, int *flag);
 
 /* Bits of *info of tpmg_solve_learned. */
 enum { TPMG_LEARNED_WARM_USED = 1,      /* the network's initial guess was kept */

@@ -56,7 +56,8 @@ TPMG_BATCH_WORKLIST = 1
 EXPORTS_LEARNED = ["tpmg_net_create", "tpmg_net_n_params", "tpmg_net_set_params", "tpmg_net_get_params",
                    "tpmg_net_forward", "tpmg_net_gradients", "tpmg_net_train_step", "tpmg_net_last_error",
                    "tpmg_net_destroy", "tpmg_net_features", "tpmg_net_targets", "tpmg_record_coarse",
-                   "tpmg_record_count", "tpmg_coarse_solve", "tpmg_attach_net", "tpmg_net_predict", "tpmg_vcycle_learned",
+                   "tpmg_record_count", "tpmg_coarse_solve", "tpmg_attach_net", "tpmg_net_predict", "tpmg_net_fault",
+                   "tpmg_vcycle_learned",
                    "tpmg_solve_learned"]
 
 TPMG_NET_COARSE = 0
@@ -77,7 +78,8 @@ class tpmg_params(ctypes.Structure):
                 ("coeff_storage", ctypes.c_int), ("centre", ctypes.c_int), ("precision", ctypes.c_int),
                 ("graphs", ctypes.c_int), ("autotune", ctypes.c_int), ("scan_max_cells", ctypes.c_int),
                 ("outer", ctypes.c_int), ("prolongation", ctypes.c_int), ("pdl", ctypes.c_int),
-                ("relax_variant", ctypes.c_int), ("scaled_rhs", ctypes.c_int)]
+                ("relax_variant", ctypes.c_int), ("scaled_rhs", ctypes.c_int),
+                ("net_tcgen05", ctypes.c_int)]
 
 
 class tpmg_profiles(ctypes.Structure):
@@ -157,6 +159,7 @@ def load(path: str | None = None):
     lib.tpmg_attach_net.argtypes = [P, I, P]
     lib.tpmg_vcycle_learned.argtypes = [P, P, P]
     lib.tpmg_net_predict.argtypes = [P, I, P, P]
+    lib.tpmg_net_fault.argtypes = [P, ctypes.POINTER(I)]
     lib.tpmg_solve_learned.argtypes = [P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(I),
                                        ctypes.POINTER(I), ctypes.POINTER(LL)]
     no_status = ("tpmg_destroy", "tpmg_status_string", "tpmg_last_error", "tpmg_batch_destroy", "tpmg_net_n_params",
@@ -449,6 +452,12 @@ class Solver:
         level = 0 if role == TPMG_NET_COARSE else self.n_levels - 1
         self._check(self._lib.tpmg_net_predict(self._h, role, self._level_vec(f, level, "f"),
                                                self._level_vec(u, level, "u")), "tpmg_net_predict")
+
+    def net_fault(self) -> bool:
+        """True if a tcgen05 network kernel of this context gave up waiting (outputs NaN)."""
+        flag = ctypes.c_int()
+        self._check(self._lib.tpmg_net_fault(self._h, ctypes.byref(flag)), "tpmg_net_fault")
+        return bool(flag.value)
 
     def vcycle_learned(self, r, z):
         """z = B r with the attached COARSE network as the coarsest-level solve."""

@@ -82,11 +82,13 @@ struct tpmg_ctx {
     tpmg_net *net[2] = {nullptr, nullptr};
     struct NetWs {
         float *p = nullptr, *x = nullptr, *h0 = nullptr, *h1 = nullptr, *y = nullptr;
+        uint16_t *xt = nullptr;   // the tcgen05 kernel's inputs, bfloat16 in its tile layout
         long rows = 0;
     } nws[2];
     float *net_p = nullptr;       // point values of tpmg_net_features / tpmg_net_targets
     long net_p_cap = 0;
     double *d_net_s = nullptr;    // [2] feature scales s (COARSE, WARM)
+    int *d_net_err = nullptr;     // set by the tcgen05 network kernel if a CTA gave up waiting
     bool net_coarse_on = false;   // the V-cycle being issued uses the COARSE network
     struct {
         cudaGraphExec_t exec = nullptr;
@@ -246,6 +248,7 @@ bool validate(const tpmg_params *p, std::string &msg)
         return false;
     }
     if (p->scaled_rhs != 0 && p->scaled_rhs != 1) { msg = "scaled_rhs must be 0 or 1"; return false; }
+    if (p->net_tcgen05 != 0 && p->net_tcgen05 != 1) { msg = "net_tcgen05 must be 0 or 1"; return false; }
     return true;
 }
 
@@ -647,8 +650,14 @@ tpmg_status net_infer(tpmg_ctx *ctx, int role, const LevelDev &lv, const TF *f, 
         return launch_net_prepare<TF>(L, lv, ctx->vert, f, w.p, ctx->partials, ctx->n_part);
     }));
     LCHK(run(ctx, TPMG_K_NET, 1.0, [&] { return launch_net_scale_finish(L, lv, ctx->partials, ctx->n_part, s); }));
+    if (ctx->p.net_tcgen05 && net_tc_ok(v) && w.xt) {   // the whole network on tcgen05
+        LCHK(run(ctx, TPMG_K_NET, nunits, [&] { return launch_net_features_tiled(L, lv, w.p, rows, s, w.xt); }));
+        LCHK(run(ctx, TPMG_K_NET, nunits,
+                 [&] { return launch_net_tc<TO>(L, v, w.xt, rows, s, u_out, ctx->d_net_err); }));
+        return TPMG_OK;
+    }
     LCHK(run(ctx, TPMG_K_NET, nunits, [&] { return launch_net_features(L, lv, w.p, nullptr, rows, s, w.x); }));
-    if (net_fused_ok(v)) {   // one tensor-core kernel for the whole network
+    if (net_fused_ok(v)) {   // one tensor-core kernel for the whole network (mma.sync)
         LCHK(run(ctx, TPMG_K_NET, nunits, [&] { return launch_net_fused<TO>(L, v, w.x, rows, s, u_out); }));
         return TPMG_OK;
     }
@@ -2238,6 +2247,7 @@ tpmg_status tpmg_default_params(tpmg_params *p)
     p->pdl = 1;
     p->relax_variant = -1;
     p->scaled_rhs = 1;
+    p->net_tcgen05 = 1;
     return TPMG_OK;
 }
 
@@ -2354,7 +2364,7 @@ tpmg_status tpmg_setup_profiles(const tpmg_params *params, const tpmg_profiles *
         dalloc(ctx, &ctx->partials, 2 * (size_t)ctx->n_part) != cudaSuccess ||
         dalloc(ctx, &ctx->zflags, (size_t)ctx->n_part) != cudaSuccess ||
         dalloc(ctx, &ctx->d_hist, kHistCap) != cudaSuccess || dalloc(ctx, &ctx->sc, 1) != cudaSuccess ||
-        dalloc(ctx, &ctx->d_net_s, 3) != cudaSuccess ||
+        dalloc(ctx, &ctx->d_net_s, 3) != cudaSuccess || dalloc(ctx, &ctx->d_net_err, 1) != cudaSuccess ||
         (ctx->p.precision == TPMG_PREC_MIXED && dalloc(ctx, &ctx->r32, ctx->N) != cudaSuccess))
         return bail(TPMG_ERR_OOM);
     if (cudaMallocHost(&ctx->h_sc, sizeof(Scalars)) != cudaSuccess) return bail(TPMG_ERR_OOM);
@@ -2959,6 +2969,16 @@ tpmg_status tpmg_coarse_solve(tpmg_ctx *ctx, const double *d_f0, double *d_u0, i
     return TPMG_OK;
 }
 
+tpmg_status tpmg_net_fault(tpmg_ctx *ctx, int *flag)
+{
+    if (!ctx || !flag) return fail(ctx, TPMG_ERR_INVALID_ARG, "NULL argument");
+    int h = 0;
+    CU(cudaMemcpyAsync(&h, ctx->d_net_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    *flag = h != 0;
+    return TPMG_OK;
+}
+
 tpmg_status tpmg_net_predict(tpmg_ctx *ctx, int role, const double *d_f, double *d_u)
 {
     if (!ctx || !d_f || !d_u) return fail(ctx, TPMG_ERR_INVALID_ARG, "NULL argument");
@@ -2996,6 +3016,7 @@ tpmg_status tpmg_attach_net(tpmg_ctx *ctx, int role, tpmg_net *net)
             const size_t nr = (size_t)ctx->p.n_r;
             CU(dalloc(ctx, &w.p, (size_t)rows * nr));
             CU(dalloc(ctx, &w.x, (size_t)rows * 2 * nr));
+            CU(dalloc(ctx, &w.xt, net_tc_input_elems(rows, ctx->p.n_r)));
             CU(dalloc(ctx, &w.h0, (size_t)rows * h));
             CU(dalloc(ctx, &w.h1, (size_t)rows * h));
             CU(dalloc(ctx, &w.y, (size_t)rows * nr));

@@ -472,6 +472,363 @@ __global__ void __launch_bounds__(32 * kFusedWarps) k_mlp_fused(const float *__r
     }
 }
 
+// ---- fused inference on the 5th-generation tensor cores (tcgen05) ----------
+//
+// The network for tiles of 128 columns per CTA on tcgen05.mma (kind::f16:
+// bfloat16 operands in shared memory, FP32 accumulators in tensor memory).
+// Per layer one thread issues the chain of MMAs D[128 x N] = A[128 x K] W^T
+// (K / 16 instructions) and tcgen05.commit signals their completion on an
+// mbarrier; then every warp reads 32 rows of D from tensor memory
+// (tcgen05.ld), adds the bias, applies ReLU and rounds to bfloat16 into the
+// next layer's A tile in shared memory, and the last layer scales its D and
+// writes the output.  The operands use the K-major layout without swizzle:
+// core matrices of 8 rows x 16 bytes (row stride 16 B), adjacent along K at
+// 128 bytes (the descriptor's leading byte offset) and 8-row groups at
+// K * 16 bytes (its stride byte offset).  The rounding is that of
+// k_mlp_fused: inputs and hidden activations in bfloat16, FP32 accumulation
+// (in the tensor cores' order).  Every mbarrier wait is bounded: a CTA that
+// gives up writes NaN over the outputs it has not written, sets *err, frees
+// its tensor memory and returns.
+constexpr int kTcRows = 128;        // rows (grid columns) per tile = the MMA's M
+constexpr int kTcThreads = 256;     // 8 warps: warp w reads TMEM lanes 32 (w % 4) + 0..31, column half w / 4
+constexpr uint32_t kTcCols = 128;   // tensor-memory columns allocated (>= 64 and >= n_r)
+constexpr long kTcSpin = 1L << 22;  // mbarrier polls before a CTA gives up
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// byte offset of element (r, k) of a K-major tile with K columns (no swizzle)
+__device__ __forceinline__ uint32_t kmajor_off(int r, int k, int K)
+{
+    return (uint32_t)((r >> 3) * (K * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// shared-memory matrix descriptor: start address, leading and stride byte
+// offsets (in 16-byte units), descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: D in FP32, A and B bfloat16, both K-major, N x M = n x 128
+__device__ __forceinline__ uint32_t umma_idesc(int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, int accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+// generic-proxy writes of shared memory made visible to the tensor cores' (async proxy) reads
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, int count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(mbar), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+
+// wait until the phase with the given parity has completed; false after kTcSpin polls
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
+{
+    for (long i = 0; i < kTcSpin; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// 8 consecutive FP32 columns of this thread's tensor-memory lane
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8])
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// weights W [N][K] (bfloat16, row-major) into the K-major tile
+__device__ __forceinline__ void tc_stage_w(const uint16_t *__restrict__ g, uint8_t *dst, int N, int K)
+{
+    const int cpr = K / 8;
+    for (int i = threadIdx.x; i < N * cpr; i += kTcThreads) {
+        const int n = i / cpr, c = i - n * cpr;
+        const uint4 val = __ldg(reinterpret_cast<const uint4 *>(g + (size_t)n * K + c * 8));
+        *reinterpret_cast<uint4 *>(dst + kmajor_off(n, c * 8, K)) = val;
+    }
+}
+
+// one layer's MMA chain D = A W^T over K (issued by one thread) and its commit
+__device__ __forceinline__ void tc_layer(uint32_t d_tmem, uint32_t a_s, uint32_t w_s, int K, int N, uint32_t mbar)
+{
+    const uint32_t idesc = umma_idesc(N);
+    for (int k = 0; k < K; k += 16)
+        umma_bf16(d_tmem, umma_desc(a_s + k * 16, 128, K * 16), umma_desc(w_s + k * 16, 128, K * 16), idesc, k > 0);
+    umma_commit(mbar);
+}
+
+// hidden epilogue: this thread's row, its 32 of the 64 columns: bias, ReLU, bfloat16 into H
+__device__ __forceinline__ void tc_epi_hidden(uint32_t t_row, int row, int half, const float *bias, uint8_t *ht)
+{
+#pragma unroll
+    for (int c0 = 0; c0 < 32; c0 += 8) {
+        const int col = half * 32 + c0;
+        float d[8];
+        tmem_ld8(t_row + col, d);
+        uint4 p;
+        p.x = pack_bf16(fmaxf(d[0] + bias[col + 0], 0.f), fmaxf(d[1] + bias[col + 1], 0.f));
+        p.y = pack_bf16(fmaxf(d[2] + bias[col + 2], 0.f), fmaxf(d[3] + bias[col + 3], 0.f));
+        p.z = pack_bf16(fmaxf(d[4] + bias[col + 4], 0.f), fmaxf(d[5] + bias[col + 5], 0.f));
+        p.w = pack_bf16(fmaxf(d[6] + bias[col + 6], 0.f), fmaxf(d[7] + bias[col + 7], 0.f));
+        *reinterpret_cast<uint4 *>(ht + kmajor_off(row, col, kFusedH)) = p;
+    }
+}
+
+__device__ __forceinline__ void tc_store8(float *o, const float v[8])
+{
+    reinterpret_cast<float4 *>(o)[0] = make_float4(v[0], v[1], v[2], v[3]);
+    reinterpret_cast<float4 *>(o)[1] = make_float4(v[4], v[5], v[6], v[7]);
+}
+__device__ __forceinline__ void tc_store8(double *o, const float v[8])
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i) reinterpret_cast<double2 *>(o)[i] = make_double2(v[2 * i], v[2 * i + 1]);
+}
+
+// mbarrier arrival that also expects `bytes` of asynchronous copies in this phase
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+// one bulk copy global -> shared memory, completed on the mbarrier (16-byte aligned, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
+}
+
+// The network's inputs (those of k_net_features, over every column of the level)
+// rounded to bfloat16 and written in the A-tile layout of k_mlp_tc: tile t of 128
+// rows at t * 128 * 2 n_r elements, K-major without swizzle; rows past `rows` are
+// zero.  A warp's 32 chunks of 8 inputs are 8 rows x 4 chunks, so that each row's
+// loads are 128 contiguous bytes and each 8 lanes store 128 contiguous bytes.
+__global__ void __launch_bounds__(256) k_net_features_tiled(const float *__restrict__ p, const int4 *__restrict__ nbr,
+                                                            const float4 *__restrict__ wnb, long rows, int n_r,
+                                                            const double *__restrict__ s, uint16_t *__restrict__ Xt)
+{
+    const double sv = *s;
+    const float inv = sv > 0.0 ? (float)(1.0 / sv) : 0.f;
+    const int K1 = 2 * n_r, cpr = K1 / 8, nb = cpr / 4, half = n_r / 8;
+    const long per_tile = (long)kTcRows * cpr, n_tiles = (rows + kTcRows - 1) / kTcRows;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n_tiles * per_tile;
+         i += (long)gridDim.x * blockDim.x) {
+        const long t = i / per_tile;
+        const int w = (int)(i - t * per_tile), l = w & 31, blk = w >> 5, g = blk / nb, cb = blk - g * nb;
+        const int r = g * 8 + (l & 7), c = cb * 4 + (l >> 3);
+        const long j = t * kTcRows + r;
+        float x[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) x[q] = 0.f;
+        if (j < rows) {
+            const int T = (int)j;
+            if (c < half) {
+                const float *src = p + (size_t)T * n_r + 8 * c;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) x[q] = src[q] * inv;
+            } else {
+                const int k0 = 8 * (c - half);
+                const int4 nb4 = nbr[T];
+                const float4 wv = wnb[T];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int k = k0 + q;
+                    const float mean = fmaf(wv.z, p[nb4.z * n_r + k], fmaf(wv.y, p[nb4.y * n_r + k], wv.x * p[nb4.x * n_r + k]));
+                    x[q] = mean * inv;
+                }
+            }
+        }
+        uint4 o;
+        o.x = pack_bf16(x[0], x[1]);
+        o.y = pack_bf16(x[2], x[3]);
+        o.z = pack_bf16(x[4], x[5]);
+        o.w = pack_bf16(x[6], x[7]);
+        *reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(Xt) + t * ((long)kTcRows * K1 * 2) +
+                                   kmajor_off(r, 8 * c, K1)) = o;
+    }
+}
+
+// The network on tcgen05 for the A tiles of k_net_features_tiled.  Each CTA walks its
+// tiles with two A buffers: while one tile's four layers run, one thread's bulk copy
+// brings the next tile's inputs into the other buffer (completion on that buffer's
+// mbarrier).
+template <typename TO>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_mlp_tc(const uint16_t *__restrict__ Xt, long rows, int n_r, NetView v, const double *__restrict__ s,
+             TO *__restrict__ out, int *__restrict__ err)
+{
+    extern __shared__ __align__(128) uint8_t tsm[];
+    const int K1 = 2 * n_r, H = kFusedH;
+    const uint32_t a_bytes = (uint32_t)kTcRows * K1 * 2;
+    uint8_t *w1 = tsm;                      // [H][K1]
+    uint8_t *w2 = w1 + H * K1 * 2;          // [H][H]
+    uint8_t *w3 = w2 + H * H * 2;           // [H][H]
+    uint8_t *w4 = w3 + H * H * 2;           // [n_r][H]
+    uint8_t *at = w4 + n_r * H * 2;         // two A tiles [128][K1]
+    uint8_t *ht = at + 2 * a_bytes;         // hidden tile [128][H]
+    float *sb = reinterpret_cast<float *>(ht + kTcRows * H * 2);   // b_1 | b_2 | b_3 | b_4
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sb + 3 * H + n_r);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(tslot + 2);      // [0] MMAs, [1], [2] the A buffers' loads
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t mb = smem_u32(mbar), mb_ld0 = smem_u32(mbar + 1), mb_ld1 = smem_u32(mbar + 2);
+    const uint32_t a_s0 = smem_u32(at), a_s1 = smem_u32(at + a_bytes);
+    const long n_tiles = (rows + kTcRows - 1) / kTcRows;
+    if (tid == 0) {
+        mbar_init(mb, 1);
+        mbar_init(mb_ld0, 1);
+        mbar_init(mb_ld1, 1);
+    }
+    __syncthreads();
+    long tile = blockIdx.x;
+    if (tid == 0 && tile < n_tiles) {   // the first tile's inputs, while the weights are staged
+        mbar_expect_tx(mb_ld0, a_bytes);
+        bulk_g2s(a_s0, reinterpret_cast<const uint8_t *>(Xt) + tile * a_bytes, a_bytes, mb_ld0);
+    }
+    tc_stage_w(v.w[0], w1, H, K1);
+    tc_stage_w(v.w[1], w2, H, H);
+    tc_stage_w(v.w[2], w3, H, H);
+    tc_stage_w(v.w[3], w4, n_r, H);
+    for (int i = tid; i < H; i += kTcThreads) {
+        sb[i] = v.b[0][i];
+        sb[H + i] = v.b[1][i];
+        sb[2 * H + i] = v.b[2][i];
+    }
+    for (int i = tid; i < n_r; i += kTcThreads) sb[3 * H + i] = v.b[3][i];
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                     "r"(kTcCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const int q = warp & 3, half = warp >> 2, row = q * 32 + lane;
+    const uint32_t t_row = tmem + ((uint32_t)(q * 32) << 16);   // this warp's lane quarter
+    const uint32_t h_s = smem_u32(ht);
+    const uint32_t w1_s = smem_u32(w1), w2_s = smem_u32(w2), w3_s = smem_u32(w3), w4_s = smem_u32(w4);
+    const float sv = (float)*s;
+    // per A buffer: its load phase parity and whether a copy into it is in flight (bits 0, 1)
+    uint32_t phase = 0, ld_phase = 0, pending = tile < n_tiles ? 1u : 0u;
+    bool failed = false;
+    for (int it = 0; tile < n_tiles; ++it, tile += gridDim.x) {
+        const int b = it & 1;
+        const uint32_t mb_cur = b ? mb_ld1 : mb_ld0, mb_oth = b ? mb_ld0 : mb_ld1;
+        const long next = tile + gridDim.x;
+        if (tid == 0 && next < n_tiles) {   // the next tile's inputs into the other buffer (its MMAs are done)
+            mbar_expect_tx(mb_oth, a_bytes);
+            bulk_g2s(b ? a_s0 : a_s1, reinterpret_cast<const uint8_t *>(Xt) + next * a_bytes, a_bytes, mb_oth);
+        }
+        if (next < n_tiles) pending |= 1u << (b ^ 1);
+        bool ok = __syncthreads_and(mbar_wait(mb_cur, (ld_phase >> b) & 1u)) != 0;
+        if (ok) {
+            ld_phase ^= 1u << b;
+            pending &= ~(1u << b);
+        }
+        const long r0 = tile * kTcRows;
+#pragma unroll 1
+        for (int l = 0; l < 4 && ok; ++l) {
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                if (l == 0) tc_layer(tmem, b ? a_s1 : a_s0, w1_s, K1, H, mb);
+                else tc_layer(tmem, h_s, l == 1 ? w2_s : (l == 2 ? w3_s : w4_s), H, l == 3 ? n_r : H, mb);
+            }
+            ok = __syncthreads_and(mbar_wait(mb, phase)) != 0;
+            if (!ok) break;
+            phase ^= 1;
+            tc_fence_after();
+            if (l < 3) {
+                tc_epi_hidden(t_row, row, half, sb + l * H, ht);
+            } else {
+                const long gr = r0 + row;
+                const int per = n_r / 2;
+                for (int c0 = 0; c0 < per; c0 += 8) {
+                    const int col = half * per + c0;
+                    float d[8];
+                    tmem_ld8(t_row + col, d);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) d[i] = sv * (d[i] + sb[3 * H + col + i]);
+                    if (gr < rows) tc_store8(out + gr * n_r + col, d);
+                }
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+        if (!ok) {
+            failed = true;
+            break;
+        }
+    }
+    if (failed) {   // the outputs of this CTA's remaining tiles are not valid
+        for (; tile < n_tiles; tile += gridDim.x)
+            for (long i = tid; i < (long)kTcRows * n_r; i += kTcThreads) {
+                const long gr = tile * kTcRows + i / n_r;
+                if (gr < rows) out[gr * n_r + i % n_r] = (TO)NAN;
+            }
+        if (tid == 0) {
+            atomicExch(err, 1);
+            // let the copies and MMAs still in flight finish (bounded) before the memory is released
+            if (pending & 1u) (void)mbar_wait(mb_ld0, ld_phase & 1u);
+            if (pending & 2u) (void)mbar_wait(mb_ld1, (ld_phase >> 1) & 1u);
+            (void)mbar_wait(mb, phase);
+        }
+        __syncthreads();
+    }
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTcCols) : "memory");
+    }
+}
+
+size_t tc_smem_bytes(int n_r)
+{
+    const size_t K1 = 2 * (size_t)n_r, H = kFusedH;
+    const size_t b = H * K1 * 2 + 2 * H * H * 2 + (size_t)n_r * H * 2 + 2 * kTcRows * K1 * 2 + kTcRows * H * 2 +
+                     (3 * H + (size_t)n_r) * 4 + 32;
+    // at least 116 KB: one CTA per SM, so that its tensor-memory allocation never waits for another's
+    return std::max<size_t>(b, 116 * 1024);
+}
+
 size_t fused_smem_bytes(int n_r)
 {
     const size_t ld1 = (size_t)n_r + 4, ldh = kFusedH / 2 + 4;
@@ -528,6 +885,37 @@ cudaError_t launch_net_layer(cudaStream_t s, const NetView &v, int l, const floa
     if (l < 3)
         return gemm<false, true, uint16_t, EPI_BIAS_RELU>(s, (int)rows, out, in, 1, x, in, v.w[l], in, y, out, v.b[l]);
     return gemm<false, true, uint16_t, EPI_BIAS>(s, (int)rows, out, in, 1, x, in, v.w[l], in, y, out, v.b[l]);
+}
+
+bool net_tc_ok(const NetView &v)
+{
+    const int n_r = v.sizes[4];
+    return v.sizes[1] == kFusedH && v.sizes[2] == kFusedH && v.sizes[3] == kFusedH && v.sizes[0] == 2 * n_r &&
+           n_r % 16 == 0 && n_r >= 16 && n_r <= (int)kTcCols && tc_smem_bytes(n_r) <= 227 * 1024;
+}
+
+size_t net_tc_input_elems(long rows, int n_r) { return (size_t)((rows + kTcRows - 1) / kTcRows) * kTcRows * 2 * n_r; }
+
+cudaError_t launch_net_features_tiled(const Launch &L, const LevelDev &lv, const float *p, long rows,
+                                      const double *s, uint16_t *Xt)
+{
+    const long chunks = (long)net_tc_input_elems(rows, L.n_r) / 8;
+    k_net_features_tiled<<<grid_1d(chunks, 256, L.sm_count), 256, 0, L.s>>>(p, lv.nbr, lv.wnb32, rows, L.n_r, s, Xt);
+    return cudaGetLastError();
+}
+
+template <typename TO>
+cudaError_t launch_net_tc(const Launch &L, const NetView &v, const uint16_t *Xt, long rows, const double *s, TO *out,
+                          int *err)
+{
+    const int n_r = v.sizes[4];
+    const size_t smem = tc_smem_bytes(n_r);
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_tc<TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const long tiles = (rows + kTcRows - 1) / kTcRows;
+    const int grid = (int)std::max<long>(1, std::min<long>(tiles, (long)std::max(L.sm_count, 1)));
+    k_mlp_tc<TO><<<grid, kTcThreads, smem, L.s>>>(Xt, rows, n_r, v, s, out, err);
+    return cudaGetLastError();
 }
 
 bool net_fused_ok(const NetView &v)
@@ -607,6 +995,10 @@ template cudaError_t launch_net_prepare<float>(const Launch &, const LevelDev &,
                                                double *, int);
 template cudaError_t launch_net_prepare<double>(const Launch &, const LevelDev &, const VertDev &, const double *,
                                                 float *, double *, int);
+template cudaError_t launch_net_tc<float>(const Launch &, const NetView &, const uint16_t *, long, const double *,
+                                          float *, int *);
+template cudaError_t launch_net_tc<double>(const Launch &, const NetView &, const uint16_t *, long, const double *,
+                                           double *, int *);
 template cudaError_t launch_net_fused<float>(const Launch &, const NetView &, const float *, long, const double *, float *);
 template cudaError_t launch_net_fused<double>(const Launch &, const NetView &, const float *, long, const double *,
                                               double *);

@@ -419,6 +419,17 @@ cudaError_t launch_net_layer(cudaStream_t s, const NetView &v, int l, const floa
 // the whole network in one tensor-core kernel (hidden width 64, n_r % 8 == 0):
 // out [rows][n_r] = s * network(X), activations rounded to bfloat16 between layers
 bool net_fused_ok(const NetView &v);
+// the same network on tcgen05 (tiles of 128 columns, FP32 accumulators in tensor memory;
+// n_r a multiple of 16, at most 128), from the inputs of launch_net_features_tiled
+// (bfloat16 in the kernel's tile layout, net_tc_input_elems of them); *err set if a
+// CTA gave up waiting (its outputs NaN)
+bool net_tc_ok(const NetView &v);
+size_t net_tc_input_elems(long rows, int n_r);
+cudaError_t launch_net_features_tiled(const Launch &L, const LevelDev &lv, const float *p, long rows,
+                                      const double *s, uint16_t *Xt);
+template <typename TO>
+cudaError_t launch_net_tc(const Launch &L, const NetView &v, const uint16_t *Xt, long rows, const double *s, TO *out,
+                          int *err);
 template <typename TO>
 cudaError_t launch_net_fused(const Launch &L, const NetView &v, const float *X, long rows, const double *s, TO *out);
 // p = f / (|T| v_k) in FP32 (level size) and partials [n_part] of sum p^2; the finish writes s

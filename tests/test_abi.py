@@ -53,7 +53,7 @@ def test_default_params_on_host(lib):
                                  dict(precision=9), dict(precision=1, coeff_storage=0), dict(precision=1, coeff_storage=2), dict(prolongation=2),
                                  dict(refinement=9, n_levels=3, n_r=1024), dict(scan_max_cells=-1), dict(outer=3),
                                  dict(relax_variant=-2), dict(relax_variant=5), dict(relax_variant=4, precision=1, coeff_storage=1),
-                                 dict(scaled_rhs=2), dict(scaled_rhs=-1)])
+                                 dict(scaled_rhs=2), dict(scaled_rhs=-1), dict(net_tcgen05=2)])
 def test_setup_rejects_bad_params_before_touching_cuda(lib, bad):
     p = binding.default_params(**bad)
     h = ctypes.c_void_p()

@@ -187,6 +187,35 @@ def test_network_prediction_matches_the_oracle(hidden):
         s.attach_net(role, None)
 
 
+@pytest.mark.parametrize("n_r", [16, 32, 64, 128])
+def test_tcgen05_network_matches_the_mma_sync_kernel(n_r):
+    """The network on tcgen05 (tiles of 128 columns, accumulators in tensor memory)
+    against the mma.sync kernel: the same bfloat16 roundings of inputs and
+    activations, FP32 accumulation in another order, so values agree up to an
+    occasional rounding boundary crossed differently.  Level 0 has 320 columns
+    (a ragged third tile), the finest 5120; the kernel reports no timeout."""
+    kw = dict(refinement=4, n_levels=3, n_r=n_r, grading=1.05, courant_c=8.0, **MIXED)
+    tc, ms = binding.Solver(net_tcgen05=1, **kw), binding.Solver(net_tcgen05=0, **kw)
+    net, _ = random_net(n_r, 64, seed=inputs.SEED_LEARNED + 90 + n_r)
+    for role, level in ((binding.TPMG_NET_COARSE, 0), (binding.TPMG_NET_WARM, kw["n_levels"] - 1)):
+        n = tc.query(level)[0] * n_r
+        f = torch.from_numpy(inputs.uniform_pm1(inputs.SEED_LEARNED + 91 + level, n)).cuda()
+        outs = []
+        for s in (tc, ms):
+            s.attach_net(role, net)
+            u = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+            s.net_predict(role, f, u)
+            torch.cuda.synchronize()
+            outs.append(u.cpu().numpy())
+            s.attach_net(role, None)
+        a, b = outs
+        assert np.all(np.isfinite(a))
+        scale = np.max(np.abs(b))
+        assert np.max(np.abs(a - b)) <= 2e-2 * scale, (role, np.max(np.abs(a - b)) / scale)
+        assert np.mean(np.abs(a - b)) <= 1e-3 * np.mean(np.abs(b)), (role, np.mean(np.abs(a - b)))
+    assert not tc.net_fault()
+
+
 def _smooth_rhs(s, seed):
     fields = learned.SmoothFields(s, l_max=8)
     return fields, fields.field(seed)
