@@ -324,11 +324,12 @@ __global__ void __launch_bounds__(256) k_outer_products(OpView o, int N, double 
     }
 }
 
-// r = f - A u with partial ||r||^2.  Where the whole stencil of every lane of
-// a warp reads exact zeros (for example a zero initial guess) A u is exactly
-// zero and the warp skips its FP64 arithmetic; the test is on bit patterns,
-// so it costs no FP64 instruction.
-template <int NT, bool FULL, bool ADV>
+// r = f - A u with partial ||r||^2.  With the stored row products (the finest
+// level of the factorised operator) the rows are formed as in k_apply; otherwise in
+// flux form, where a warp whose stencil reads exact zeros on every lane (A u exactly
+// zero) skips its FP64 arithmetic -- the test is on bit patterns, so it costs no FP64
+// instruction.  Either way a guess that k_nonzero found to be zero is not read at all.
+template <int NT, bool FULL, bool ADV, bool R32>
 __device__ __forceinline__ void residual_body(const OpView &o, const FullView &full, const double *__restrict__ f,
                                               const double *__restrict__ u, double *__restrict__ r, int N,
                                               double *__restrict__ partials, const int *__restrict__ nz, int n_nz,
@@ -340,11 +341,50 @@ __device__ __forceinline__ void residual_body(const OpView &o, const FullView &f
     // r = f, accumulated in the same order as below (bit-identical), without the stencil's loads
     int any = nz ? 0 : 1;
     for (int t = threadIdx.x; t < n_nz; t += NT) any |= nz[t];
-    if (!__syncthreads_or(any)) {
+    const bool copy = !__syncthreads_or(any);
+    if (!FULL && !ADV && o.om) {
+        // the stored row products (as k_apply): each warp takes 32 consecutive rows and
+        // writes the first 31; the flux through a row's lower face, F_k = oc_k (u_k - u_{k-1}),
+        // is formed once and handed to the row below by a shuffle, and
+        // r = f - (om u_k - hr_k sum_e g_e u_e + F_k - F_{k+1}): 10 FP64 operations a row
+        // with the partial sum of r^2, where the flux form takes 16
+        const int lane = threadIdx.x & 31;
+        const int wstride = nblk * (NT / 32) * 31;
+        for (int base = (bid * (NT / 32) + (threadIdx.x >> 5)) * 31; base < N; base += wstride) {
+            const int i = base + lane;
+            int T = 0, k = 0;
+            double xc = 0.0, F = 0.0;
+            if (i < N && !copy) {
+                T = i / n_r;
+                k = i - T * n_r;
+                xc = u[i];
+                if (k > 0) F = __ldg(&o.oc[i]) * (xc - u[i - 1]);
+            }
+            const double Fu = __shfl_down_sync(0xffffffffu, F, 1);
+            if (lane < 31 && i < N) {
+                double v = f[i];
+                if (!copy) {
+                    const int4 nb = __ldg(&o.nbr[T]);
+                    const dbl4 g = o.g[T];
+                    const double S = fma(g.z, u[nb.z * n_r + k], fma(g.y, u[nb.y * n_r + k], g.x * u[nb.x * n_r + k]));
+                    v -= fma(__ldg(&o.om[i]), xc, fma(-__ldg(&o.hr[k]), S, F - Fu));
+                }
+                r[i] = v;
+                if (R32) r32[i] = (float)v;
+                acc = fma(v, v, acc);
+            }
+        }
+        if (partials) {
+            acc = block_sum<NT>(acc);
+            if (threadIdx.x == 0) partials[bid] = acc;
+        }
+        return;
+    }
+    if (copy) {
         for (int i = bid * NT + threadIdx.x; i < N; i += stride) {
             const double v = f[i];
             r[i] = v;
-            if (r32) r32[i] = (float)v;
+            if (R32) r32[i] = (float)v;
             acc = fma(v, v, acc);
         }
         if (partials) {
@@ -387,7 +427,7 @@ __device__ __forceinline__ void residual_body(const OpView &o, const FullView &f
             double v = fv[q];
             if (!skip) v = v - apply_any<NT, FULL, ADV>(o, full, u, T[q], k[q], i);
             r[i] = v;
-            if (r32) r32[i] = (float)v;
+            if (R32) r32[i] = (float)v;
             acc = fma(v, v, acc);
         }
     }
@@ -397,7 +437,10 @@ __device__ __forceinline__ void residual_body(const OpView &o, const FullView &f
     }
 }
 
-template <int NT, bool FULL, bool ADV>
+// R32: r is also written in FP32 (the mixed V-cycle's copy).  A compile-time choice:
+// the double -> float conversion runs on the FP64 pipe, and a kernel that only skips
+// its store at run time may still issue it.
+template <int NT, bool FULL, bool ADV, bool R32>
 __global__ void __launch_bounds__(NT) k_residual(OpView o, FullView full, const double *__restrict__ f,
                                                  const double *__restrict__ u, double *__restrict__ r, int N,
                                                  double *__restrict__ partials, const int *__restrict__ nz,
@@ -405,7 +448,7 @@ __global__ void __launch_bounds__(NT) k_residual(OpView o, FullView full, const 
 {
     pdl_wait();
     pdl_trigger();
-    residual_body<NT, FULL, ADV>(o, full, f, u, r, N, partials, nz, n_nz, blockIdx.x, gridDim.x, r32);
+    residual_body<NT, FULL, ADV, R32>(o, full, f, u, r, N, partials, nz, n_nz, blockIdx.x, gridDim.x, r32);
 }
 
 // Per block, whether x has a nonzero element in the block's grid-stride range (a test
@@ -1183,7 +1226,7 @@ __global__ void __launch_bounds__(NT) k_dot(const double *__restrict__ a, const 
 
 // u += alpha p; r -= alpha q; partial ||r||^2.  With z_old (flexible CG) also
 // the partial <r_new, z_old> of the Polak-Ribiere coefficient, in partials[gridDim.x + block].
-template <int NT, bool CROSS>
+template <int NT, bool CROSS, bool R32>
 __device__ __forceinline__ void axpy_pair_body(const Scalars *__restrict__ sc, const double *__restrict__ p,
                                                const double *__restrict__ q, double *__restrict__ u,
                                                double *__restrict__ r, int N, double *__restrict__ partials,
@@ -1208,7 +1251,7 @@ __device__ __forceinline__ void axpy_pair_body(const Scalars *__restrict__ sc, c
             u[j] = fma(alpha, pv[k], uv[k]);
             const double x = fma(-alpha, qv[k], rv[k]);
             r[j] = x;
-            if (r32) r32[j] = (float)x;
+            if (R32) r32[j] = (float)x;
             acc = fma(x, x, acc);
             if (CROSS) accz = fma(x, zv[k], accz);
         }
@@ -1217,7 +1260,7 @@ __device__ __forceinline__ void axpy_pair_body(const Scalars *__restrict__ sc, c
         u[i] = fma(alpha, p[i], u[i]);
         const double x = fma(-alpha, q[i], r[i]);
         r[i] = x;
-        if (r32) r32[i] = (float)x;
+        if (R32) r32[i] = (float)x;
         acc = fma(x, x, acc);
         if (CROSS) accz = fma(x, z_old[i], accz);
     }
@@ -1230,7 +1273,7 @@ __device__ __forceinline__ void axpy_pair_body(const Scalars *__restrict__ sc, c
     }
 }
 
-template <int NT, bool CROSS>
+template <int NT, bool CROSS, bool R32>
 __global__ void __launch_bounds__(NT) k_axpy_pair(const Scalars *__restrict__ sc, const double *__restrict__ p,
                                                   const double *__restrict__ q, double *__restrict__ u,
                                                   double *__restrict__ r, int N, double *__restrict__ partials,
@@ -1238,7 +1281,7 @@ __global__ void __launch_bounds__(NT) k_axpy_pair(const Scalars *__restrict__ sc
 {
     pdl_wait();
     pdl_trigger();
-    axpy_pair_body<NT, CROSS>(sc, p, q, u, r, N, partials, z_old, blockIdx.x, gridDim.x, r32);
+    axpy_pair_body<NT, CROSS, R32>(sc, p, q, u, r, N, partials, z_old, blockIdx.x, gridDim.x, r32);
 }
 
 // p = z + beta p
@@ -1412,14 +1455,14 @@ __global__ void __launch_bounds__(NT) k_outer_batch(const BatchMemberDev *__rest
         const BatchMemberDev &x = mem[m];
         if (WHAT == BATCH_NONZERO) nonzero_body<NT>(x.u, x.N, x.zflags, b, n_part);
         if (WHAT == BATCH_RESIDUAL)
-            residual_body<NT, false, false>(batch_view(x), FullView{}, x.f, x.u, x.r, x.N, x.partials, x.zflags, n_part,
+            residual_body<NT, false, false, true>(batch_view(x), FullView{}, x.f, x.u, x.r, x.N, x.partials, x.zflags, n_part,
                                             b, n_part, x.r32);
         if (WHAT == BATCH_DOT_RZ) dot_body<NT>(x.r, x.z, x.N, x.partials, b, n_part);
         if (WHAT == BATCH_XPBY) xpby_body<NT>(x.sc, x.z, x.p, x.N, b, n_part);
         if (WHAT == BATCH_APPLY)
             apply_body<NT, false, false>(batch_view(x), FullView{}, x.p, x.q, x.N, x.partials, b, n_part);
         if (WHAT == BATCH_AXPY)
-            axpy_pair_body<NT, true>(x.sc, x.p, x.q, x.u, x.r, x.N, x.partials, x.z, b, n_part, x.r32);
+            axpy_pair_body<NT, true, true>(x.sc, x.p, x.q, x.u, x.r, x.N, x.partials, x.z, b, n_part, x.r32);
         if (WHAT == BATCH_CLEAR_P)
             for (int i = b * NT + threadIdx.x; i < x.N; i += n_part * NT) x.p[i] = 0.0;
         __syncthreads();   // the next virtual block reuses block_sum's shared scratch
@@ -1505,8 +1548,12 @@ cudaError_t launch_residual(const Launch &L, const LevelDev &lv, const VertDev &
     const int N = lv.n * L.n_r;
     const int grid = partials ? n_part : grid_for(N, kThreads, L.sm_count);
     const FullView fv{lv.cfull, lv.cvr, lv.cvx};
-    auto kern = lv.cfull ? k_residual<kThreads, true, false>
-                         : (lv.area_x ? k_residual<kThreads, false, true> : k_residual<kThreads, false, false>);
+    auto kern = r32 ? (lv.cfull ? k_residual<kThreads, true, false, true>
+                                : (lv.area_x ? k_residual<kThreads, false, true, true>
+                                             : k_residual<kThreads, false, false, true>))
+                    : (lv.cfull ? k_residual<kThreads, true, false, false>
+                                : (lv.area_x ? k_residual<kThreads, false, true, false>
+                                             : k_residual<kThreads, false, false, false>));
     return launch_k(L, kern, grid, kThreads, 0, make_view(lv, v, L.n_r), fv, f, u, r, N, partials, nz,
                     nz ? n_part : 0, r32);
 }
@@ -1702,7 +1749,9 @@ cudaError_t launch_finish(const Launch &L, int what, const double *partials, int
 cudaError_t launch_axpy_pair(const Launch &L, long n, const Scalars *sc, const double *p, const double *q, double *u,
                              double *r, double *partials, int n_part, const double *z_old, float *r32)
 {
-    return launch_k(L, z_old ? k_axpy_pair<kThreads, true> : k_axpy_pair<kThreads, false>, n_part, kThreads, 0, sc, p,
+    auto kern = r32 ? (z_old ? k_axpy_pair<kThreads, true, true> : k_axpy_pair<kThreads, false, true>)
+                    : (z_old ? k_axpy_pair<kThreads, true, false> : k_axpy_pair<kThreads, false, false>);
+    return launch_k(L, kern, n_part, kThreads, 0, sc, p,
                     q, u, r, (int)n, partials, z_old, r32);
 }
 
