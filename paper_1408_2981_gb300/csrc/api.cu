@@ -1937,7 +1937,7 @@ tpmg_status build_worklist(tpmg_batch *b, tpmg_ctx *const *ctxs, int M, const do
         const long N = c->N;
         const int n_r = c->p.n_r, L = c->p.n_levels;
         BatchMemberDev &x = mem[m];
-        x = BatchMemberDev{fl.nbr, fl.g, fl.area, fl.area_r, fl.om, fl.oc, c->vert.vol, c->vert.w, c->vert.hr, n_r,
+        x = BatchMemberDev{fl.nbr, fl.g, fl.area, fl.area_r, fl.om, fl.oc, fl.ocs, c->vert.vol, c->vert.w, c->vert.hr, n_r,
                            (int)N, d_f[m], d_u[m]};
         if (balloc(b, &x.r, N) != cudaSuccess || balloc(b, &x.r32, N) != cudaSuccess || balloc(b, &x.z, N) != cudaSuccess ||
             balloc(b, &x.p, N) != cudaSuccess ||
@@ -2376,8 +2376,12 @@ tpmg_status tpmg_setup_profiles(const tpmg_params *params, const tpmg_profiles *
         if (dalloc(ctx, &D.om, (size_t)ctx->N) != cudaSuccess || dalloc(ctx, &D.oc, (size_t)ctx->N) != cudaSuccess) {
             (void)cudaGetLastError();   // a failed allocation leaves no sticky error
             D.om = D.oc = nullptr;
-        } else if (launch_outer_products(launch_of(ctx), D, ctx->vert) != cudaSuccess) {
-            return bail(TPMG_ERR_CUDA);
+        } else {
+            if (dalloc(ctx, &D.ocs, 3 * (size_t)ctx->N) != cudaSuccess) {   // 24 more bytes per unknown
+                (void)cudaGetLastError();
+                D.ocs = nullptr;
+            }
+            if (launch_outer_products(launch_of(ctx), D, ctx->vert) != cudaSuccess) return bail(TPMG_ERR_CUDA);
         }
     }
     // levels relaxed by twisted tasks (FP64, factorised stencil): the scaled couplings

@@ -74,12 +74,15 @@ struct OpView {
     // per-row products of the factorised coefficients (LevelDev::om, oc), or null
     const double *__restrict__ om;
     const double *__restrict__ oc;
+    // with them, the horizontal couplings per unknown, three planes [3][n n_r] hr_k g_e
+    // (LevelDev::ocs), or null
+    const double *__restrict__ ocs;
 };
 
 inline OpView make_view(const LevelDev &lv, const VertDev &v, int n_r)
 {
     return OpView{lv.nbr, lv.g, lv.area, lv.area_r, v.vol, v.w, v.hr, n_r, lv.vc, lv.vcr,
-                  lv.area_x, v.xm, v.xp, lv.vcx_on ? lv.vcx : nullptr, v.dr, lv.om, lv.oc};
+                  lv.area_x, v.xm, v.xp, lv.vcx_on ? lv.vcx : nullptr, v.dr, lv.om, lv.oc, lv.ocs};
 }
 
 // Stencil form of a level's V-cycle operator: factorised profiles (TPMG^fac), alpha_r
@@ -228,6 +231,23 @@ __device__ __forceinline__ double apply_vc(const OpView &o, const double *__rest
     return apply_at<ADV>(o, x, T, k, i);
 }
 
+// -hr_k sum_e g_e x_e + rest for row (T, k) = i of the finest level's outer operator:
+// from the couplings per unknown, three FMAs (hr_k g_e stored: LevelDev::ocs), else
+// from the factorised couplings, four operations.
+__device__ __forceinline__ double outer_horizontal(const OpView &o, const double *__restrict__ x, int T, int k, int i,
+                                                   int N, double rest)
+{
+    const int n_r = o.n_r;
+    const int4 nb = __ldg(&o.nbr[T]);
+    if (o.ocs) {
+        const double c0 = __ldg(&o.ocs[i]), c1 = __ldg(&o.ocs[(size_t)N + i]), c2 = __ldg(&o.ocs[2 * (size_t)N + i]);
+        return fma(-c2, x[nb.z * n_r + k], fma(-c1, x[nb.y * n_r + k], fma(-c0, x[nb.x * n_r + k], rest)));
+    }
+    const dbl4 g = o.g[T];
+    const double S = fma(g.z, x[nb.z * n_r + k], fma(g.y, x[nb.y * n_r + k], g.x * x[nb.x * n_r + k]));
+    return fma(-__ldg(&o.hr[k]), S, rest);
+}
+
 // The kernels below take the block index and the grid size as arguments of their
 // bodies (bid, nblk), so that the batched form runs the same code as block bid of
 // a launch of nblk blocks for each member: same partition, same partial sums.
@@ -262,11 +282,7 @@ __device__ __forceinline__ void apply_body(const OpView &o, const FullView &fv, 
             }
             const double Fu = __shfl_down_sync(0xffffffffu, F, 1);
             if (lane < 31 && i < N) {
-                const int n_r = o.n_r;
-                const int4 nb = __ldg(&o.nbr[T]);
-                const dbl4 g = o.g[T];
-                const double S = fma(g.z, x[nb.z * n_r + k], fma(g.y, x[nb.y * n_r + k], g.x * x[nb.x * n_r + k]));
-                const double v = fma(__ldg(&o.om[i]), xc, fma(-__ldg(&o.hr[k]), S, F - Fu));
+                const double v = fma(__ldg(&o.om[i]), xc, outer_horizontal(o, x, T, k, i, N, F - Fu));
                 y[i] = v;
                 acc = fma(xc, v, acc);
             }
@@ -315,12 +331,18 @@ __device__ __forceinline__ bool is_zero(double v) { return (__double_as_longlong
 // om = |T| v_k + hr_k G_T, the same expression apply_at_lanes forms per row, and
 // oc = |T| alpha_r^S w_k of the row's lower face.
 __global__ void __launch_bounds__(256) k_outer_products(OpView o, int N, double *__restrict__ om,
-                                                        double *__restrict__ oc)
+                                                        double *__restrict__ oc, double *__restrict__ ocs)
 {
     for (int i = blockIdx.x * 256 + threadIdx.x; i < N; i += gridDim.x * 256) {
         const int T = i / o.n_r, k = i - T * o.n_r;
         om[i] = fma(o.area[T], o.vol[k], o.hr[k] * o.g[T].w);
         oc[i] = o.area_r[T] * o.w[k];
+        if (ocs) {
+            const dbl4 g = o.g[T];
+            ocs[i] = o.hr[k] * g.x;
+            ocs[(size_t)N + i] = o.hr[k] * g.y;
+            ocs[2 * (size_t)N + i] = o.hr[k] * g.z;
+        }
     }
 }
 
@@ -363,12 +385,7 @@ __device__ __forceinline__ void residual_body(const OpView &o, const FullView &f
             const double Fu = __shfl_down_sync(0xffffffffu, F, 1);
             if (lane < 31 && i < N) {
                 double v = f[i];
-                if (!copy) {
-                    const int4 nb = __ldg(&o.nbr[T]);
-                    const dbl4 g = o.g[T];
-                    const double S = fma(g.z, u[nb.z * n_r + k], fma(g.y, u[nb.y * n_r + k], g.x * u[nb.x * n_r + k]));
-                    v -= fma(__ldg(&o.om[i]), xc, fma(-__ldg(&o.hr[k]), S, F - Fu));
-                }
+                if (!copy) v -= fma(__ldg(&o.om[i]), xc, outer_horizontal(o, u, T, k, i, N, F - Fu));
                 r[i] = v;
                 if (R32) r32[i] = (float)v;
                 acc = fma(v, v, acc);
@@ -1436,7 +1453,7 @@ __global__ void __launch_bounds__(256) k_finish(int what, const double *__restri
 __device__ __forceinline__ OpView batch_view(const BatchMemberDev &m)
 {
     return OpView{m.nbr,   m.g,     m.area,  m.area_r, m.vol,   m.w,   m.hr,  m.n_r, nullptr,
-                  nullptr, nullptr, nullptr, nullptr,  nullptr, nullptr, m.om, m.oc};
+                  nullptr, nullptr, nullptr, nullptr,  nullptr, nullptr, m.om, m.oc, m.ocs};
 }
 
 // Member m's block b of n_part is virtual block m n_part + b; each CTA runs virtual
@@ -1594,7 +1611,7 @@ cudaError_t launch_prolong_linear(const Launch &L, const LevelDev &fine, const L
 cudaError_t launch_outer_products(const Launch &L, const LevelDev &lv, const VertDev &v)
 {
     const int N = lv.n * L.n_r;
-    k_outer_products<<<grid_for(N, 256, L.sm_count), 256, 0, L.s>>>(make_view(lv, v, L.n_r), N, lv.om, lv.oc);
+    k_outer_products<<<grid_for(N, 256, L.sm_count), 256, 0, L.s>>>(make_view(lv, v, L.n_r), N, lv.om, lv.oc, lv.ocs);
     return cudaGetLastError();
 }
 

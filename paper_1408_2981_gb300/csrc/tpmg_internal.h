@@ -152,6 +152,9 @@ struct LevelDev {
     // oc = |T| alpha_r^S w_k (the coupling through the row's lower face), so that the
     // outer operator costs 8 FP64 operations a row instead of 11; null if they did not fit
     double *om = nullptr, *oc = nullptr;
+    // with them where they fit, the horizontal couplings per unknown, three planes [3][n][n_r]
+    // ocs_e = hr_k g_e, so that the outer operator's horizontal part costs 3 FMAs a row
+    double *ocs = nullptr;
     // FP64 levels with a coarser level below them: the restriction's view of each
     // coarse cell [n / 4], or null (then the kernel forms every child's residual)
     RestrictGeo *rgeo = nullptr;
@@ -255,7 +258,7 @@ using RestrictBatchArgs = RestrictBatchArgsT<kBatchItems>;
 struct BatchMemberDev {     // one member's outer FP64 iteration (finest level, factorised operator)
     const int4 *nbr;
     const dbl4 *g;
-    const double *area, *area_r, *om, *oc;
+    const double *area, *area_r, *om, *oc, *ocs;
     const double *vol, *w, *hr;
     int n_r, N;
     const double *f;

@@ -46,9 +46,12 @@ def energy(o, e):
     return math.sqrt(max(float(e @ o.apply(e)), 0.0))
 
 
+@pytest.mark.parametrize("scan", [5120, 0], ids=["scan", "twisted"])
 @pytest.mark.parametrize("prof_fn", [lambda o: random_profiles(o, 500), flow_profiles], ids=["random", "balanced_flow"])
-def test_apply_and_vcycle_parity(prof_fn):
-    s, o = pair(prof_fn)
+def test_apply_and_vcycle_parity(prof_fn, scan):
+    # scan 0: twisted tasks on every level, whose right-hand side comes from the couplings
+    # scaled by the pivots of the profiles' column blocks
+    s, o = pair(prof_fn, scan_max_cells=scan)
     x = inputs.uniform_pm1(inputs.SEED_UNIFORM_SMALL + 50, s.N)
     y = torch.empty(s.N, dtype=torch.float64, device="cuda")
     s.apply_operator(torch.from_numpy(x).cuda(), y)
