@@ -1234,6 +1234,9 @@ def main(argv=None):
                          "level's solve)")
     ap.add_argument("--iters-hint", type=int, default=None,
                     help="reference arm on workloads sampled by one iteration: iterations of a full solve")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="single-problem workloads: the fixed kernel heuristic instead of the autotuner (for "
+                         "ncu launch lists, under which the autotuner's timings are distorted)")
     ap.add_argument("--launcher-check", action="store_true",
                     help="start the ranks as --gpus asks, print each rank's view of the launch and exit (no GPU)")
     argv = list(sys.argv[1:] if argv is None else argv)
@@ -1269,6 +1272,8 @@ def main(argv=None):
         return run_batch(args, wl)
     if "learned" in wl:
         return run_learned(args, wl)
+    if args.no_autotune:
+        wl = dict(wl, params=dict(wl["params"], autotune=0))
     return run_tpmg(args, wl)
 
 
