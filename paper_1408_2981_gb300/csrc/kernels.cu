@@ -1143,8 +1143,13 @@ __global__ void __launch_bounds__(NT, STAGE ? 1 : 6)
 // their sub-partitions.  DEEP: 6 elements per lane in flight in the gather
 // instead of 4 -- fewer rounds of load latency, which bound a warp's gather --
 // for more registers per warp.
+// Registers are capped (without DEEP: 20 resident one-warp CTAs per SM, 5 warps per
+// sub-partition, at most 96 registers) so that
+// a finest-level pass of up to 3040 tasks fits in one wave: with 102 registers the first sweep's
+// ZERO pass held 4 warps per SM sub-partition instead of 5 and ran its last 105 tasks as a
+// second wave (73 us against 44 us for a NORMAL pass).
 template <int MODE, int SK, bool DEEP>
-__global__ void __launch_bounds__(32, 16)
+__global__ void __launch_bounds__(32, DEEP ? 16 : 20)
     k_relax_warp(OpView o, const int *__restrict__ cells, const int4 *__restrict__ tnb, const dbl4 *__restrict__ tg,
                  const double *__restrict__ rinv, const double *__restrict__ fb, const double *__restrict__ fcf,
                  const double *__restrict__ fm, int S, int j, int task0, const double *__restrict__ f,
