@@ -457,8 +457,11 @@ __device__ __forceinline__ void residual_body(const OpView &o, const FullView &f
 // R32: r is also written in FP32 (the mixed V-cycle's copy).  A compile-time choice:
 // the double -> float conversion runs on the FP64 pipe, and a kernel that only skips
 // its store at run time may still issue it.
+// 8 blocks of NT threads per SM (at most 32 registers): the n_part = 8 x SMs blocks of the
+// reductions in one wave (40 registers left a second, partial wave: 0.88 against 0.85 ms at
+// 41.9 M unknowns)
 template <int NT, bool FULL, bool ADV, bool R32>
-__global__ void __launch_bounds__(NT) k_residual(OpView o, FullView full, const double *__restrict__ f,
+__global__ void __launch_bounds__(NT, 8) k_residual(OpView o, FullView full, const double *__restrict__ f,
                                                  const double *__restrict__ u, double *__restrict__ r, int N,
                                                  double *__restrict__ partials, const int *__restrict__ nz,
                                                  int n_nz, float *__restrict__ r32)
@@ -1586,8 +1589,7 @@ cudaError_t launch_resid_restrict(const Launch &L, const LevelDev &fine, const L
     const int Nc = coarse.n * L.n_r, grid = grid_for(Nc, kThreads, L.sm_count);
     if (fine.rgeo && stencil_form(fine) == CM_FAC && !fine.area_x)
         return launch_k(L, k_restrict_fac<kThreads>, grid, kThreads, 0, (const RestrictGeo *)fine.rgeo, v.vol, v.w, v.hr,
-                        f, u, fc, L.n_r, Nc);
-    const OpView o = make_view(fine, v, L.n_r);
+                        f, u, fc, L.n_r, Nc);    const OpView o = make_view(fine, v, L.n_r);
     void (*kern)(OpView, const double *, const double *, double *, int);
     switch (stencil_form(fine)) {
     case CM_FULL: kern = k_resid_restrict<kThreads, CM_FULL, false>; break;
