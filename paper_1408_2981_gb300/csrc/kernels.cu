@@ -372,11 +372,33 @@ __device__ __forceinline__ void residual_body(const OpView &o, const FullView &f
         // with the partial sum of r^2, where the flux form takes 16
         const int lane = threadIdx.x & 31;
         const int wstride = nblk * (NT / 32) * 31;
-        for (int base = (bid * (NT / 32) + (threadIdx.x >> 5)) * 31; base < N; base += wstride) {
+        const int base0 = (bid * (NT / 32) + (threadIdx.x >> 5)) * 31;
+        if (copy) {
+            // a zero guess: r = f over the same rows, accumulated in the same order as below,
+            // with four rows' loads in flight per thread
+            for (int base = base0; base < N; base += 4 * wstride) {
+                double v[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int i = base + q * wstride + lane;
+                    v[q] = (lane < 31 && i < N) ? f[i] : 0.0;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int i = base + q * wstride + lane;
+                    if (lane < 31 && i < N) {
+                        r[i] = v[q];
+                        if (R32) r32[i] = (float)v[q];
+                        acc = fma(v[q], v[q], acc);
+                    }
+                }
+            }
+        }
+        for (int base = copy ? N : base0; base < N; base += wstride) {
             const int i = base + lane;
             int T = 0, k = 0;
             double xc = 0.0, F = 0.0;
-            if (i < N && !copy) {
+            if (i < N) {
                 T = i / n_r;
                 k = i - T * n_r;
                 xc = u[i];
@@ -384,8 +406,7 @@ __device__ __forceinline__ void residual_body(const OpView &o, const FullView &f
             }
             const double Fu = __shfl_down_sync(0xffffffffu, F, 1);
             if (lane < 31 && i < N) {
-                double v = f[i];
-                if (!copy) v -= fma(__ldg(&o.om[i]), xc, outer_horizontal(o, u, T, k, i, N, F - Fu));
+                const double v = f[i] - fma(__ldg(&o.om[i]), xc, outer_horizontal(o, u, T, k, i, N, F - Fu));
                 r[i] = v;
                 if (R32) r32[i] = (float)v;
                 acc = fma(v, v, acc);
