@@ -638,7 +638,7 @@ unsigned short bf16_bits(double x)
 // The network attached in `role` on level lv: u_out = s network(features(f))
 // for every column of the level (scale, features, four layers, output).
 template <typename TF, typename TO>
-tpmg_status net_infer(tpmg_ctx *ctx, int role, const LevelDev &lv, const TF *f, TO *u_out)
+tpmg_status net_infer(tpmg_ctx *ctx, int role, const LevelDev &lv, const TF *f, TO *u_out, float *f32 = nullptr)
 {
     const Launch L = launch_of(ctx);
     const NetView v = net_view(ctx->net[role]);
@@ -647,7 +647,7 @@ tpmg_status net_infer(tpmg_ctx *ctx, int role, const LevelDev &lv, const TF *f, 
     const long rows = lv.n;
     const double nunits = (double)lv.n * ctx->p.n_r;
     LCHK(run(ctx, TPMG_K_NET, nunits, [&] {
-        return launch_net_prepare<TF>(L, lv, ctx->vert, f, w.p, ctx->partials, ctx->n_part);
+        return launch_net_prepare<TF>(L, lv, ctx->vert, f, w.p, ctx->partials, ctx->n_part, f32);
     }));
     LCHK(run(ctx, TPMG_K_NET, 1.0, [&] { return launch_net_scale_finish(L, lv, ctx->partials, ctx->n_part, s); }));
     if (ctx->p.net_tcgen05 && net_tc_ok(v) && w.xt) {   // the whole network on tcgen05
@@ -669,6 +669,28 @@ tpmg_status net_infer(tpmg_ctx *ctx, int role, const LevelDev &lv, const TF *f, 
         in = out;
     }
     LCHK(run(ctx, TPMG_K_NET, nunits, [&] { return launch_net_output<TO>(L, w.y, rows * ctx->p.n_r, s, u_out); }));
+    return TPMG_OK;
+}
+
+// The learned solve's initial guess: the WARM network's prediction, then one block-Jacobi
+// line relaxation (eq. BlockJacobi, the V-cycle's smoother in FP32) from it on the finest
+// level, which removes the vertically oscillating part of the network's error; written to
+// u in FP64.  The network's first kernel converts f to FP32 anyway, and stores it in the
+// FP32 copy of r (free until the initial residual is formed), so that the relaxation reads
+// f in FP32 instead of converting every double again on the FP64 pipe.
+tpmg_status warm_start(tpmg_ctx *ctx, const Launch &L, const double *f, double *u)
+{
+    LevelDev &fl = ctx->lv[ctx->p.n_levels - 1];
+    const long N = ctx->N;
+    float *const f32 = ctx->r32;
+    const tpmg_status s1 = net_infer<double, float>(ctx, TPMG_NET_WARM, fl, f, fl.u32, f32);
+    if (s1 != TPMG_OK) return s1;
+    LCHK(run_w(ctx, TPMG_K_RELAX, (double)N, alg_relax32((double)N, PASS_NORMAL, !f32, true, false), [&] {
+        return f32 ? launch_relax32<float>(L, fl, PASS_NORMAL, 0, fl.n_tasks, (float)ctx->p.relax, f32, fl.u32,
+                                           fl.u2_32, nullptr, u)
+                   : launch_relax32<double>(L, fl, PASS_NORMAL, 0, fl.n_tasks, (float)ctx->p.relax, f, fl.u32,
+                                            fl.u2_32, nullptr, u);
+    }));
     return TPMG_OK;
 }
 
@@ -945,16 +967,9 @@ tpmg_status append_solve(tpmg_ctx *ctx, cudaGraph_t g, const double *f, double *
     std::vector<cudaGraphNode_t> leaves;
     tpmg_status st = capture_into(ctx, g, nullptr, 0, &leaves, [&]() -> tpmg_status {
         const Launch L = launch_of(ctx);
-        if (learned && ctx->net[TPMG_NET_WARM]) {
-            // the network's guess, then one block-Jacobi line relaxation (eq. BlockJacobi,
-            // the V-cycle's smoother in FP32) from it on the finest level, which removes
-            // the vertically oscillating part of the network's error; written to u in FP64
-            tpmg_status s1 = net_infer<double, float>(ctx, TPMG_NET_WARM, fl, f, fl.u32);
+        if (learned && ctx->net[TPMG_NET_WARM]) {   // the network's guess and one relaxation
+            const tpmg_status s1 = warm_start(ctx, L, f, u);
             if (s1 != TPMG_OK) return s1;
-            LCHK(run_w(ctx, TPMG_K_RELAX, (double)N, alg_relax32((double)N, PASS_NORMAL, true, true, false), [&] {
-                return launch_relax32<double>(L, fl, PASS_NORMAL, 0, fl.n_tasks, (float)ctx->p.relax, f, fl.u32,
-                                              fl.u2_32, nullptr, u);
-            }));
         }
         LCHK(residual_probed(ctx, L, f, u, ctx->r));
         if (learned) {
@@ -1212,13 +1227,9 @@ tpmg_status pcg(tpmg_ctx *ctx, const double *f, double *u, double rtol, int max_
     const bool flexible = ctx->p.precision == TPMG_PREC_MIXED || learned;
     *iters = 0;
     *rel = 1.0;
-    if (learned && ctx->net[TPMG_NET_WARM]) {
-        tpmg_status s1 = net_infer<double, float>(ctx, TPMG_NET_WARM, fl, f, fl.u32);
+    if (learned && ctx->net[TPMG_NET_WARM]) {   // the network's guess and one relaxation
+        const tpmg_status s1 = warm_start(ctx, L, f, u);
         if (s1 != TPMG_OK) return s1;
-        LCHK(run_w(ctx, TPMG_K_RELAX, (double)N, alg_relax32((double)N, PASS_NORMAL, true, true, false), [&] {
-            return launch_relax32<double>(L, fl, PASS_NORMAL, 0, fl.n_tasks, (float)ctx->p.relax, f, fl.u32, fl.u2_32,
-                                          nullptr, u);
-        }));
     }
     LCHK(residual_probed(ctx, L, f, u, ctx->r));
     if (learned) {

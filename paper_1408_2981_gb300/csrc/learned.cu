@@ -238,14 +238,17 @@ __global__ void k_round_bf16(long n, const float *__restrict__ w, uint16_t *__re
 template <typename TF>
 __global__ void __launch_bounds__(256) k_net_prepare(const TF *__restrict__ f, const float *__restrict__ iarea,
                                                      const float *__restrict__ ivol, long N, int n_r,
-                                                     float *__restrict__ p, double *__restrict__ partials)
+                                                     float *__restrict__ p, double *__restrict__ partials,
+                                                     float *__restrict__ f32)
 {
     float acc = 0.f;
     // 32-bit indices: a level holds fewer than 2^31 unknowns (checked at set-up)
     for (int i = blockIdx.x * 256 + threadIdx.x; i < (int)N; i += gridDim.x * 256) {
         const int T = i / n_r;
         const int k = i - T * n_r;
-        const float v = (float)f[i] * iarea[T] * ivol[k];
+        const float fi = (float)f[i];
+        if (f32) f32[i] = fi;
+        const float v = fi * iarea[T] * ivol[k];
         p[i] = v;
         acc = fmaf(v, v, acc);
     }
@@ -942,10 +945,10 @@ cudaError_t launch_net_fused(const Launch &L, const NetView &v, const float *X, 
 
 template <typename TF>
 cudaError_t launch_net_prepare(const Launch &L, const LevelDev &lv, const VertDev &vert, const TF *f, float *p,
-                               double *partials, int n_part)
+                               double *partials, int n_part, float *f32)
 {
     const long N = (long)lv.n * L.n_r;
-    k_net_prepare<TF><<<n_part, 256, 0, L.s>>>(f, lv.iarea32, vert.ivol32, N, L.n_r, p, partials);
+    k_net_prepare<TF><<<n_part, 256, 0, L.s>>>(f, lv.iarea32, vert.ivol32, N, L.n_r, p, partials, f32);
     return cudaGetLastError();
 }
 
@@ -992,9 +995,9 @@ cudaError_t launch_to_f32(const Launch &L, long n, const double *x, float *y)
 }
 
 template cudaError_t launch_net_prepare<float>(const Launch &, const LevelDev &, const VertDev &, const float *, float *,
-                                               double *, int);
+                                               double *, int, float *);
 template cudaError_t launch_net_prepare<double>(const Launch &, const LevelDev &, const VertDev &, const double *,
-                                                float *, double *, int);
+                                                float *, double *, int, float *);
 template cudaError_t launch_net_tc<float>(const Launch &, const NetView &, const uint16_t *, long, const double *,
                                           float *, int *);
 template cudaError_t launch_net_tc<double>(const Launch &, const NetView &, const uint16_t *, long, const double *,

@@ -435,10 +435,11 @@ cudaError_t launch_net_tc(const Launch &L, const NetView &v, const uint16_t *Xt,
                           int *err);
 template <typename TO>
 cudaError_t launch_net_fused(const Launch &L, const NetView &v, const float *X, long rows, const double *s, TO *out);
-// p = f / (|T| v_k) in FP32 (level size) and partials [n_part] of sum p^2; the finish writes s
+// p = f / (|T| v_k) in FP32 (level size) and partials [n_part] of sum p^2; the finish writes s.
+// f32 (optional): f in FP32 as well (the conversion the kernel makes anyway)
 template <typename TF>
 cudaError_t launch_net_prepare(const Launch &L, const LevelDev &lv, const VertDev &vert, const TF *f, float *p,
-                               double *partials, int n_part);
+                               double *partials, int n_part, float *f32 = nullptr);
 cudaError_t launch_net_scale_finish(const Launch &L, const LevelDev &lv, const double *partials, int n_part, double *s);
 // X [rows][2 n_r] network inputs from the point values p of the level (cells NULL: rows 0..rows-1)
 cudaError_t launch_net_features(const Launch &L, const LevelDev &lv, const float *p, const int *cells, long rows,
