@@ -306,6 +306,28 @@ tpmg_status tpmg_solve(tpmg_ctx *ctx, const double *d_f, double *d_u, double rto
 tpmg_status tpmg_solve_host(tpmg_ctx *ctx, const double *h_f, double *h_u, double rtol, int max_iter,
                             int *iters, double *rel_resid, double *resid_hist);
 
+/* n solves with HOST buffers, one after another, with the copies overlapped
+ * (tpmg_solve's PCG of Sec. 5 for each right-hand side in turn; the paper has no
+ * host-transfer layer).  System j solves A u_j = f_j: h_f[j] (N doubles, read)
+ * and h_u[j] (N doubles, receives the solution; with guess = 1 it also holds the
+ * initial guess, with guess = 0 the guess is zero and nothing is copied in for
+ * it).  While system j is solved on the device, system j + 1's inputs are copied
+ * to the device and system j - 1's solution back to the host, on two copy
+ * streams of the context, through two staging slots (2 N doubles of device
+ * memory allocated on the first call, kept with the context; one cached solve
+ * graph per slot).  Each system's solution, iterations and residual are those
+ * of tpmg_solve on the same vectors, bit for bit.  The overlap needs page-locked
+ * host memory (cudaHostAlloc, cudaHostRegister); pageable arrays give the same
+ * results with the copies serialised by CUDA.  The h_f[j] may repeat; no h_u[j]
+ * may overlap another system's h_f or h_u (INVALID_ARG, nothing launched).
+ * iters[n], rel_resid[n]: per system, as tpmg_solve; status[n] (or NULL): each
+ * system's tpmg_solve status.  A system that ends NOT_CONVERGED or BREAKDOWN
+ * does not stop the others; the call returns the first such status, or OK.  A
+ * CUDA error stops the call (later systems are not solved, their outputs are
+ * unset).  Nothing of the call is in flight when it returns. */
+tpmg_status tpmg_solve_host_many(tpmg_ctx *ctx, int n, const double *const *h_f, double *const *h_u, int guess,
+                                 double rtol, int max_iter, int *iters, double *rel_resid, int *status);
+
 /* Many independent solves in one graph launch (the batched form, Sec. 5's
  * method applied to many problems at once; the paper has no batching layer).
  * A batch holds one PCG solve (tpmg_solve's algorithm and arithmetic, rtol,

@@ -43,7 +43,7 @@ TPMG_OUTER_BICGSTAB = 2
 EXPORTS = ["tpmg_default_params", "tpmg_setup", "tpmg_setup_profiles", "tpmg_set_outer_profiles",
            "tpmg_apply_operator", "tpmg_vcycle", "tpmg_vcycle_noalloc",
            "tpmg_solve",
-           "tpmg_solve_host", "tpmg_query", "tpmg_query_tuning", "tpmg_export_mesh", "tpmg_profile", "tpmg_profile_read",
+           "tpmg_solve_host", "tpmg_solve_host_many", "tpmg_query", "tpmg_query_tuning", "tpmg_export_mesh", "tpmg_profile", "tpmg_profile_read",
            "tpmg_profile_work", "tpmg_fp64_peak",
            "tpmg_status_string", "tpmg_last_error", "tpmg_destroy", "tpmg_batch_create", "tpmg_batch_run",
            "tpmg_batch_create_ex", "tpmg_batch_form", "tpmg_batch_destroy"]
@@ -117,6 +117,7 @@ def load(path: str | None = None):
     lib.tpmg_vcycle_noalloc.argtypes = [P, P, P]
     lib.tpmg_solve.argtypes = [P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D), P]
     lib.tpmg_solve_host.argtypes = [P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D), P]
+    lib.tpmg_solve_host_many.argtypes = [P, I, P, P, I, D, I, P, P, P]
     lib.tpmg_query.argtypes = [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(I)]
     lib.tpmg_export_mesh.argtypes = [P, I, P, P, P, P, P, P]
     lib.tpmg_query_tuning.argtypes = [P, I, ctypes.POINTER(I), P]
@@ -378,6 +379,30 @@ class Solver:
         if raise_on_fail and st != TPMG_OK:
             self._check(st, "tpmg_solve_host")
         return st, it.value, rel.value
+
+    def solve_host_many(self, fs, us, guess: bool = False, rtol: float = 1e-5, max_iter: int = 100,
+                        raise_on_fail: bool = True):
+        """Solves A u_j = f_j for host arrays fs[j], us[j] (us[j] receives the solution, and
+        holds the initial guess when guess is true), with the copies of the neighbouring
+        systems overlapping each solve.  Returns (status, iters[n], rel_resid[n], status[n])."""
+        n = len(fs)
+        if len(us) != n:
+            raise ValueError("fs and us must have the same length")
+        for j in range(n):
+            for a, name in ((fs[j], f"fs[{j}]"), (us[j], f"us[{j}]")):
+                if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+                        and a.size == self.N):
+                    raise ValueError(f"{name} must be a contiguous float64 array of {self.N} elements")
+        pf = (ctypes.c_void_p * max(n, 1))(*[a.ctypes.data for a in fs])
+        pu = (ctypes.c_void_p * max(n, 1))(*[a.ctypes.data for a in us])
+        it = np.zeros(max(n, 1), dtype=np.int32)
+        rel = np.zeros(max(n, 1))
+        sts = np.zeros(max(n, 1), dtype=np.int32)
+        st = self._lib.tpmg_solve_host_many(self._h, n, pf, pu, 1 if guess else 0, rtol, max_iter, it.ctypes.data,
+                                            rel.ctypes.data, sts.ctypes.data)
+        if raise_on_fail and st != TPMG_OK:
+            self._check(st, "tpmg_solve_host_many")
+        return st, it[:n].copy(), rel[:n].copy(), sts[:n].copy()
 
 
     # --------------------------------------------------------------- learned form

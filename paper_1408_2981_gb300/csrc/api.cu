@@ -65,16 +65,19 @@ struct tpmg_ctx {
     cudaStream_t cap_stream = nullptr;  // private stream on which graphs are captured
     bool capturing = false;
     GraphCache vc;
-    // whole solve as one graph (device-side loop), cached for one argument set
-    struct {
+    // whole solve as one graph (device-side loop), cached for the two argument sets used
+    // last (two, so that the pipelined host solves alternate between their staging slots)
+    struct SolveGraph {
         cudaGraphExec_t exec = nullptr;
         const double *f = nullptr;
         double *u = nullptr;
         double rtol = 0.0;
         int max_iter = -1;
-    } sg;
-    long long sg_init = 0, sg_iter = 0;   // launches of sg's initial part and of one iteration
-    ClassCounts sg_cls;                   // the same per kernel class, with the unknowns processed
+        long long init = 0, iter = 0;   // launches of the initial part and of one iteration
+        ClassCounts cls;                // the same per kernel class, with the unknowns processed
+        unsigned long long used = 0;    // last use, for replacing the older entry
+    } sg[2];
+    unsigned long long sg_clock = 0;
     long long last_launches = 0;          // kernels executed by the last solve
     // learned form (tpmg_learned.h): attached networks (COARSE, WARM), their
     // inference workspaces, scales, the learned solve's graph and the
@@ -128,6 +131,11 @@ struct tpmg_ctx {
     // axpy, the learned solve's judge), read by the finest level of the V-cycle of r
     float *r32 = nullptr;
     double *hf = nullptr, *hu = nullptr;   // device staging for tpmg_solve_host
+    // tpmg_solve_host_many (on first use): its second staging slot, the streams of its
+    // copies in and out, and its events (per slot: inputs copied, solved, solution copied out)
+    double *hf2 = nullptr, *hu2 = nullptr;
+    cudaStream_t xin = nullptr, xout = nullptr;
+    cudaEvent_t xev_in[2] = {}, xev_solved[2] = {}, xev_out[2] = {};
     double *partials = nullptr;
     int n_part = 0;
     int *zflags = nullptr;        // [n_part] per-block flags of the initial guess's zero probe
@@ -839,9 +847,10 @@ void drop_graph(tpmg_ctx *ctx)
 {
     if (ctx->vc.exec) cudaGraphExecDestroy(ctx->vc.exec);
     ctx->vc = GraphCache{};
-    if (ctx->sg.exec) cudaGraphExecDestroy(ctx->sg.exec);
-    ctx->sg.exec = nullptr;
-    ctx->sg.max_iter = -1;
+    for (auto &e : ctx->sg) {
+        if (e.exec) cudaGraphExecDestroy(e.exec);
+        e = tpmg_ctx::SolveGraph{};
+    }
     if (ctx->lg.exec) cudaGraphExecDestroy(ctx->lg.exec);
     ctx->lg.exec = nullptr;
     ctx->lg.max_iter = -1;
@@ -1067,34 +1076,44 @@ tpmg_status loop_result(tpmg_ctx *ctx, const Scalars &s, double rtol, int max_it
 tpmg_status pcg_graph(tpmg_ctx *ctx, const double *f, double *u, double rtol, int max_iter, int *iters, double *rel,
                       double *hist)
 {
-    auto &sg = ctx->sg;
-    if (!sg.exec || sg.f != f || sg.u != u || sg.rtol != rtol || sg.max_iter != max_iter) {
+    auto hit = [&](const tpmg_ctx::SolveGraph &e) {
+        return e.exec && e.f == f && e.u == u && e.rtol == rtol && e.max_iter == max_iter;
+    };
+    tpmg_ctx::SolveGraph *slot = hit(ctx->sg[0]) ? &ctx->sg[0] : hit(ctx->sg[1]) ? &ctx->sg[1] : nullptr;
+    if (!slot) {
+        slot = ctx->sg[0].used <= ctx->sg[1].used ? &ctx->sg[0] : &ctx->sg[1];
+        auto &sg = *slot;
         if (sg.exec) cudaGraphExecDestroy(sg.exec);
-        sg.exec = nullptr;
+        sg = tpmg_ctx::SolveGraph{};
         cudaGraph_t g;
         CU(cudaGraphCreate(&g, 0));
-        tpmg_status st = append_solve(ctx, g, f, u, rtol, max_iter, &ctx->sg_init, &ctx->sg_iter, false, &ctx->sg_cls);
+        tpmg_status st = append_solve(ctx, g, f, u, rtol, max_iter, &sg.init, &sg.iter, false, &sg.cls);
         cudaError_t e = st == TPMG_OK ? cudaGraphInstantiate(&sg.exec, g, 0) : cudaSuccess;
         cudaGraphDestroy(g);
         if (st != TPMG_OK) return st;
-        if (e != cudaSuccess) return fail(ctx, TPMG_ERR_CUDA, std::string("solve graph: ") + cudaGetErrorString(e));
+        if (e != cudaSuccess) {
+            sg.exec = nullptr;
+            return fail(ctx, TPMG_ERR_CUDA, std::string("solve graph: ") + cudaGetErrorString(e));
+        }
         sg.f = f;
         sg.u = u;
         sg.rtol = rtol;
         sg.max_iter = max_iter;
     }
+    auto &sg = *slot;
+    sg.used = ++ctx->sg_clock;
     CU(cudaGraphLaunch(sg.exec, ctx->stream));
     CU(cudaMemcpyAsync(ctx->h_sc, ctx->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     const Scalars s = *ctx->h_sc;
-    ctx->last_launches = ctx->sg_init + (long long)s.it * ctx->sg_iter;
+    ctx->last_launches = sg.init + (long long)s.it * sg.iter;
     // the replay's launches count like launches made one by one (tpmg_profile_read)
     if (s.it >= 0)
         for (int c = 0; c < TPMG_K_COUNT; ++c) {
-            ctx->tr.launches[c] += ctx->sg_cls.init[c] + (long long)s.it * ctx->sg_cls.iter[c];
-            ctx->tr.units[c] += ctx->sg_cls.uinit[c] + s.it * ctx->sg_cls.uiter[c];
-            ctx->tr.bytes[c] += ctx->sg_cls.binit[c] + s.it * ctx->sg_cls.biter[c];
-            ctx->tr.flops[c] += ctx->sg_cls.finit[c] + s.it * ctx->sg_cls.fiter[c];
+            ctx->tr.launches[c] += sg.cls.init[c] + (long long)s.it * sg.cls.iter[c];
+            ctx->tr.units[c] += sg.cls.uinit[c] + s.it * sg.cls.uiter[c];
+            ctx->tr.bytes[c] += sg.cls.binit[c] + s.it * sg.cls.biter[c];
+            ctx->tr.flops[c] += sg.cls.finit[c] + s.it * sg.cls.fiter[c];
         }
     if (hist && s.it >= 0) CU(cudaMemcpy(hist, ctx->d_hist, sizeof(double) * (s.it + 1), cudaMemcpyDeviceToHost));
     return loop_result(ctx, s, rtol, max_iter, iters, rel);
@@ -2773,6 +2792,97 @@ tpmg_status tpmg_solve_host(tpmg_ctx *ctx, const double *h_f, double *h_u, doubl
     return st;
 }
 
+// tpmg_solve_host for a sequence of right-hand sides, with the copies of one system
+// overlapping the solves of its neighbours.  Two staging slots alternate: system j is
+// solved in slot j % 2 while the copy-in stream fills the other slot with system j + 1's
+// inputs and the copy-out stream drains system j - 1's solution from it.  Every solve is
+// tpmg_solve's on one slot's vectors (one cached graph per slot), and the events order
+// each slot's uses: inputs copied -> solved -> solution copied out -> next inputs.
+tpmg_status tpmg_solve_host_many(tpmg_ctx *ctx, int n, const double *const *h_f, double *const *h_u, int guess,
+                                 double rtol, int max_iter, int *iters, double *rel_resid, int *status)
+{
+    if (!ctx) return TPMG_ERR_INVALID_ARG;
+    if (n < 0 || (n > 0 && (!h_f || !h_u || !iters || !rel_resid)))
+        return fail(ctx, TPMG_ERR_INVALID_ARG, "n < 0 or NULL array");
+    if (guess != 0 && guess != 1) return fail(ctx, TPMG_ERR_INVALID_ARG, "guess must be 0 or 1");
+    if (!(rtol >= 0.0) || max_iter < 0) return fail(ctx, TPMG_ERR_INVALID_ARG, "rtol must be >= 0, max_iter >= 0");
+    if (nonsymmetric(ctx) && ctx->p.outer == TPMG_OUTER_CG)
+        return fail(ctx, TPMG_ERR_INVALID_ARG, "vertical advection or linear prolongation: the operator or the V-cycle is not symmetric, so CG does not apply (use Richardson or BiCGStab)");
+    // a solution is copied out while later systems' inputs are copied in, so no solution
+    // array may overlap another system's arrays
+    auto overlap = [&](const double *a, const double *b) { return a < b + ctx->N && b < a + ctx->N; };
+    for (int j = 0; j < n; ++j) {
+        if (!h_f[j] || !h_u[j]) return fail(ctx, TPMG_ERR_INVALID_ARG, "NULL right-hand side or solution");
+        for (int k = 0; k < n; ++k)
+            if (k != j && (overlap(h_u[k], h_u[j]) || overlap(h_u[k], h_f[j])))
+                return fail(ctx, TPMG_ERR_INVALID_ARG, "a solution array overlaps another system's arrays");
+    }
+    if (n == 0) return TPMG_OK;
+    if (!ctx->hf2) {
+        if (dalloc(ctx, &ctx->hf2, ctx->N) != cudaSuccess || dalloc(ctx, &ctx->hu2, ctx->N) != cudaSuccess)
+            return fail(ctx, TPMG_ERR_OOM, "second staging slot");
+    }
+    if (!ctx->xin) {
+        CU(cudaStreamCreateWithFlags(&ctx->xin, cudaStreamNonBlocking));
+        CU(cudaStreamCreateWithFlags(&ctx->xout, cudaStreamNonBlocking));
+        for (int i = 0; i < 2; ++i) {
+            CU(cudaEventCreateWithFlags(&ctx->xev_in[i], cudaEventDisableTiming));
+            CU(cudaEventCreateWithFlags(&ctx->xev_solved[i], cudaEventDisableTiming));
+            CU(cudaEventCreateWithFlags(&ctx->xev_out[i], cudaEventDisableTiming));
+        }
+    }
+    double *F[2] = {ctx->hf, ctx->hf2}, *U[2] = {ctx->hu, ctx->hu2};
+    const size_t bytes = sizeof(double) * ctx->N;
+    // the streams start behind all work already on the context's stream; a slot's events
+    // are recorded afresh on every use, so no wait below sees an earlier call's record
+    CU(cudaEventRecord(ctx->xev_solved[0], ctx->stream));
+    CU(cudaEventRecord(ctx->xev_solved[1], ctx->stream));
+    CU(cudaEventRecord(ctx->xev_out[0], ctx->stream));
+    CU(cudaEventRecord(ctx->xev_out[1], ctx->stream));
+    // system j's inputs into slot j % 2, once the slot's previous system is solved and
+    // its solution copied out
+    auto copy_in = [&](int j) -> cudaError_t {
+        const int sl = j & 1;
+        cudaError_t e = cudaStreamWaitEvent(ctx->xin, ctx->xev_solved[sl], 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->xin, ctx->xev_out[sl], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(F[sl], h_f[j], bytes, cudaMemcpyHostToDevice, ctx->xin);
+        if (e == cudaSuccess && guess) e = cudaMemcpyAsync(U[sl], h_u[j], bytes, cudaMemcpyHostToDevice, ctx->xin);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->xev_in[sl], ctx->xin);
+        return e;
+    };
+    auto body = [&]() -> tpmg_status {
+        tpmg_status first = TPMG_OK;
+        CU(copy_in(0));
+        for (int j = 0; j < n; ++j) {
+            const int sl = j & 1;
+            if (j + 1 < n) CU(copy_in(j + 1));
+            CU(cudaStreamWaitEvent(ctx->stream, ctx->xev_in[sl], 0));
+            if (!guess) {
+                CU(cudaStreamWaitEvent(ctx->stream, ctx->xev_out[sl], 0));
+                CU(cudaMemsetAsync(U[sl], 0, bytes, ctx->stream));
+            }
+            const tpmg_status st = tpmg_solve(ctx, F[sl], U[sl], rtol, max_iter, &iters[j], &rel_resid[j], nullptr);
+            if (status) status[j] = st;
+            if (st != TPMG_OK && st != TPMG_ERR_NOT_CONVERGED && st != TPMG_ERR_BREAKDOWN) return st;
+            if (st != TPMG_OK && first == TPMG_OK) first = st;
+            CU(cudaEventRecord(ctx->xev_solved[sl], ctx->stream));
+            CU(cudaStreamWaitEvent(ctx->xout, ctx->xev_solved[sl], 0));
+            CU(cudaMemcpyAsync(h_u[j], U[sl], bytes, cudaMemcpyDeviceToHost, ctx->xout));
+            CU(cudaEventRecord(ctx->xev_out[sl], ctx->xout));
+        }
+        return first;
+    };
+    tpmg_status st = body();
+    // nothing of the call is in flight when it returns, whatever failed
+    const cudaError_t e1 = cudaStreamSynchronize(ctx->xin), e2 = cudaStreamSynchronize(ctx->xout),
+                      e3 = cudaStreamSynchronize(ctx->stream);
+    if (st == TPMG_OK || st == TPMG_ERR_NOT_CONVERGED || st == TPMG_ERR_BREAKDOWN) {
+        const cudaError_t e = e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3;
+        if (e != cudaSuccess) return fail(ctx, TPMG_ERR_CUDA, std::string("host solves: ") + cudaGetErrorString(e));
+    }
+    return st;
+}
+
 tpmg_status tpmg_query(const tpmg_ctx *ctx, int level, int *n_cells, int *n_r, double *omega2, int *n_colours)
 {
     if (!ctx || level < 0 || level >= ctx->p.n_levels) return TPMG_ERR_INVALID_ARG;
@@ -3142,6 +3252,14 @@ void tpmg_destroy(tpmg_ctx *ctx)
     cudaStreamSynchronize(ctx->stream);
     drop_graph(ctx);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    for (cudaStream_t x : {ctx->xin, ctx->xout})
+        if (x) {
+            cudaStreamSynchronize(x);
+            cudaStreamDestroy(x);
+        }
+    for (int i = 0; i < 2; ++i)
+        for (cudaEvent_t e : {ctx->xev_in[i], ctx->xev_solved[i], ctx->xev_out[i]})
+            if (e) cudaEventDestroy(e);
     for (void *p : ctx->allocs) cudaFree(p);
     if (ctx->h_sc) cudaFreeHost(ctx->h_sc);
     for (cudaEvent_t e : ctx->tr.ev) cudaEventDestroy(e);
