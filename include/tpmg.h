@@ -31,8 +31,9 @@
  * is allocated by tpmg_setup and released by tpmg_destroy.
  *
  * All device work is ordered on the stream given to tpmg_setup.
- * tpmg_apply_operator and tpmg_vcycle are asynchronous; tpmg_solve and
- * tpmg_solve_host return after the solve has finished.
+ * tpmg_apply_operator and tpmg_vcycle are asynchronous; tpmg_solve,
+ * tpmg_solve_host and tpmg_solve_host_many return after their solves have
+ * finished.
  *
  * Errors are returned as tpmg_status values; no C++ exception crosses this
  * interface.  A context is not thread-safe: one thread at a time per context.
@@ -321,10 +322,13 @@ tpmg_status tpmg_solve_host(tpmg_ctx *ctx, const double *h_f, double *h_u, doubl
  * results with the copies serialised by CUDA.  The h_f[j] may repeat; no h_u[j]
  * may overlap another system's h_f or h_u (INVALID_ARG, nothing launched).
  * iters[n], rel_resid[n]: per system, as tpmg_solve; status[n] (or NULL): each
- * system's tpmg_solve status.  A system that ends NOT_CONVERGED or BREAKDOWN
- * does not stop the others; the call returns the first such status, or OK.  A
- * CUDA error stops the call (later systems are not solved, their outputs are
- * unset).  Nothing of the call is in flight when it returns. */
+ * system's tpmg_solve status.  Where tpmg_solve runs its loop on the device
+ * (CG, graphs on, no kernel class timed, max_iter < 4096), all n solves are
+ * enqueued back to back and their results read after the last one; otherwise
+ * each returns before the next is enqueued.  A system that ends NOT_CONVERGED
+ * or BREAKDOWN does not stop the others; the call returns the first such
+ * status, or OK.  A CUDA error stops the call (the outputs of systems not yet
+ * reported are unset).  Nothing of the call is in flight when it returns. */
 tpmg_status tpmg_solve_host_many(tpmg_ctx *ctx, int n, const double *const *h_f, double *const *h_u, int guess,
                                  double rtol, int max_iter, int *iters, double *rel_resid, int *status);
 

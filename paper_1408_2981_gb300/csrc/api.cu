@@ -136,6 +136,8 @@ struct tpmg_ctx {
     double *hf2 = nullptr, *hu2 = nullptr;
     cudaStream_t xin = nullptr, xout = nullptr;
     cudaEvent_t xev_in[2] = {}, xev_solved[2] = {}, xev_out[2] = {};
+    Scalars *h_many = nullptr;   // pinned: each system's scalars, read after the last solve
+    int h_many_cap = 0;
     double *partials = nullptr;
     int n_part = 0;
     int *zflags = nullptr;        // [n_part] per-block flags of the initial guess's zero probe
@@ -1072,9 +1074,13 @@ tpmg_status loop_result(tpmg_ctx *ctx, const Scalars &s, double rtol, int max_it
 }
 
 // tpmg_solve with the loop on the device: one graph launch per solve (the
-// graph is captured once per argument set), one read-back at the end.
-tpmg_status pcg_graph(tpmg_ctx *ctx, const double *f, double *u, double rtol, int max_iter, int *iters, double *rel,
-                      double *hist)
+// graph is captured once per argument set), one read-back at the end.  In two
+// parts, so that several solves can be enqueued before their results are read:
+// pcg_graph_launch enqueues the solve and the copy of its scalars into *h_out;
+// pcg_graph_result turns those scalars, once the stream has reached them, into
+// the solve's results (and counts its launches).
+tpmg_status pcg_graph_launch(tpmg_ctx *ctx, const double *f, double *u, double rtol, int max_iter, Scalars *h_out,
+                             const tpmg_ctx::SolveGraph **used)
 {
     auto hit = [&](const tpmg_ctx::SolveGraph &e) {
         return e.exec && e.f == f && e.u == u && e.rtol == rtol && e.max_iter == max_iter;
@@ -1100,12 +1106,16 @@ tpmg_status pcg_graph(tpmg_ctx *ctx, const double *f, double *u, double rtol, in
         sg.rtol = rtol;
         sg.max_iter = max_iter;
     }
-    auto &sg = *slot;
-    sg.used = ++ctx->sg_clock;
-    CU(cudaGraphLaunch(sg.exec, ctx->stream));
-    CU(cudaMemcpyAsync(ctx->h_sc, ctx->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->stream));
-    CU(cudaStreamSynchronize(ctx->stream));
-    const Scalars s = *ctx->h_sc;
+    slot->used = ++ctx->sg_clock;
+    CU(cudaGraphLaunch(slot->exec, ctx->stream));
+    CU(cudaMemcpyAsync(h_out, ctx->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->stream));
+    *used = slot;
+    return TPMG_OK;
+}
+
+tpmg_status pcg_graph_result(tpmg_ctx *ctx, const Scalars &s, const tpmg_ctx::SolveGraph &sg, double rtol,
+                             int max_iter, int *iters, double *rel)
+{
     ctx->last_launches = sg.init + (long long)s.it * sg.iter;
     // the replay's launches count like launches made one by one (tpmg_profile_read)
     if (s.it >= 0)
@@ -1115,8 +1125,19 @@ tpmg_status pcg_graph(tpmg_ctx *ctx, const double *f, double *u, double rtol, in
             ctx->tr.bytes[c] += sg.cls.binit[c] + s.it * sg.cls.biter[c];
             ctx->tr.flops[c] += sg.cls.finit[c] + s.it * sg.cls.fiter[c];
         }
-    if (hist && s.it >= 0) CU(cudaMemcpy(hist, ctx->d_hist, sizeof(double) * (s.it + 1), cudaMemcpyDeviceToHost));
     return loop_result(ctx, s, rtol, max_iter, iters, rel);
+}
+
+tpmg_status pcg_graph(tpmg_ctx *ctx, const double *f, double *u, double rtol, int max_iter, int *iters, double *rel,
+                      double *hist)
+{
+    const tpmg_ctx::SolveGraph *sg = nullptr;
+    const tpmg_status st = pcg_graph_launch(ctx, f, u, rtol, max_iter, ctx->h_sc, &sg);
+    if (st != TPMG_OK) return st;
+    CU(cudaStreamSynchronize(ctx->stream));
+    const Scalars s = *ctx->h_sc;
+    if (hist && s.it >= 0) CU(cudaMemcpy(hist, ctx->d_hist, sizeof(double) * (s.it + 1), cudaMemcpyDeviceToHost));
+    return pcg_graph_result(ctx, s, *sg, rtol, max_iter, iters, rel);
 }
 
 // The sum of a dot product on the host (block partials, fixed-order finish, one read-back).
@@ -2850,6 +2871,19 @@ tpmg_status tpmg_solve_host_many(tpmg_ctx *ctx, int n, const double *const *h_f,
         if (e == cudaSuccess) e = cudaEventRecord(ctx->xev_in[sl], ctx->xin);
         return e;
     };
+    // with the loop on the device every solve is enqueued at once and its scalars read
+    // after the last one, so the solves follow each other on the GPU without waiting for
+    // the host; otherwise each tpmg_solve returns before the next system is enqueued
+    const bool device_loop =
+        ctx->p.outer == TPMG_OUTER_CG && ctx->p.graphs && ctx->tr.mask == 0 && max_iter < kHistCap;
+    if (device_loop && ctx->h_many_cap < n) {
+        if (ctx->h_many) CU(cudaFreeHost(ctx->h_many));
+        ctx->h_many = nullptr;
+        ctx->h_many_cap = 0;
+        CU(cudaMallocHost(&ctx->h_many, sizeof(Scalars) * (size_t)n));
+        ctx->h_many_cap = n;
+    }
+    std::vector<const tpmg_ctx::SolveGraph *> graph(device_loop ? n : 0, nullptr);
     auto body = [&]() -> tpmg_status {
         tpmg_status first = TPMG_OK;
         CU(copy_in(0));
@@ -2861,14 +2895,28 @@ tpmg_status tpmg_solve_host_many(tpmg_ctx *ctx, int n, const double *const *h_f,
                 CU(cudaStreamWaitEvent(ctx->stream, ctx->xev_out[sl], 0));
                 CU(cudaMemsetAsync(U[sl], 0, bytes, ctx->stream));
             }
-            const tpmg_status st = tpmg_solve(ctx, F[sl], U[sl], rtol, max_iter, &iters[j], &rel_resid[j], nullptr);
-            if (status) status[j] = st;
-            if (st != TPMG_OK && st != TPMG_ERR_NOT_CONVERGED && st != TPMG_ERR_BREAKDOWN) return st;
-            if (st != TPMG_OK && first == TPMG_OK) first = st;
+            if (device_loop) {
+                const tpmg_status st = pcg_graph_launch(ctx, F[sl], U[sl], rtol, max_iter, ctx->h_many + j, &graph[j]);
+                if (st != TPMG_OK) return st;
+            } else {
+                const tpmg_status st = tpmg_solve(ctx, F[sl], U[sl], rtol, max_iter, &iters[j], &rel_resid[j], nullptr);
+                if (status) status[j] = st;
+                if (st != TPMG_OK && st != TPMG_ERR_NOT_CONVERGED && st != TPMG_ERR_BREAKDOWN) return st;
+                if (st != TPMG_OK && first == TPMG_OK) first = st;
+            }
             CU(cudaEventRecord(ctx->xev_solved[sl], ctx->stream));
             CU(cudaStreamWaitEvent(ctx->xout, ctx->xev_solved[sl], 0));
             CU(cudaMemcpyAsync(h_u[j], U[sl], bytes, cudaMemcpyDeviceToHost, ctx->xout));
             CU(cudaEventRecord(ctx->xev_out[sl], ctx->xout));
+        }
+        if (device_loop) {
+            CU(cudaStreamSynchronize(ctx->stream));
+            for (int j = 0; j < n; ++j) {
+                const tpmg_status st =
+                    pcg_graph_result(ctx, ctx->h_many[j], *graph[j], rtol, max_iter, &iters[j], &rel_resid[j]);
+                if (status) status[j] = st;
+                if (st != TPMG_OK && first == TPMG_OK) first = st;
+            }
         }
         return first;
     };
@@ -3262,6 +3310,7 @@ void tpmg_destroy(tpmg_ctx *ctx)
             if (e) cudaEventDestroy(e);
     for (void *p : ctx->allocs) cudaFree(p);
     if (ctx->h_sc) cudaFreeHost(ctx->h_sc);
+    if (ctx->h_many) cudaFreeHost(ctx->h_many);
     for (cudaEvent_t e : ctx->tr.ev) cudaEventDestroy(e);
     delete ctx;
 }

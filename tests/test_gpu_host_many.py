@@ -132,3 +132,17 @@ def test_device_solves_in_between_keep_their_graphs():
             np.testing.assert_array_equal(us[j], ref[j][3])
         st, it, rel, u = device_solve(s, fs[1], np.zeros(s.N), 1e-8, 100)
         np.testing.assert_array_equal(u, ref[1][3])
+
+
+def test_host_driven_loop_gives_the_same_results():
+    """Without graphs each system's solve returns before the next is enqueued; the
+    results are those of the same context's device solves."""
+    s = binding.Solver(graphs=0, **FP64)
+    fs = [rhs(s, j) for j in range(3)]
+    us = [np.zeros(s.N) for _ in fs]
+    st, it, rel, sts = s.solve_host_many(fs, us, rtol=1e-8)
+    assert st == binding.TPMG_OK
+    for j in range(3):
+        st2, it2, rel2, u2 = device_solve(s, fs[j], np.zeros(s.N), 1e-8, 100)
+        assert (it2, rel2) == (it[j], rel[j])
+        np.testing.assert_array_equal(us[j], u2)
