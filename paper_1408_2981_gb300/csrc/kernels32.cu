@@ -268,84 +268,108 @@ __device__ __forceinline__ void relax32_column(const bf16x4 *__restrict__ cpack,
     }
 }
 
-// The same pass for columns of exactly 128 rows without vertical advection, in the
-// row-chunk layout with 4 rows per lane (lane l: rows 4l .. 4l + 3) and every array
-// moved in pieces of 16 bytes or more: f, 1/pivot, u and the neighbours' u as one
-// float4 (f in FP64 as two double2), the lane's 4 stencil records as two 16-byte
-// loads, its 4 lower-face couplings as one 8-byte load.  The upper face of row 4l + 3
-// is the next lane's first lower face (a shuffle; 0 above the top row).  Each
-// recurrence is the lane's own 4 steps, one scan of the lanes' composite maps and a
-// fix-up, as in the two-rows-per-lane layout; the arithmetic per row is the same as
-// there, so the pass gives the same values as the segmented layout up to the
-// order of the scan's roundings.
-__host__ __device__ inline bool relax32_v4_ok(int n_r, bool advection, const void *cpack, const void *cvert,
-                                              const void *rinv, const void *f, const void *u_in, const void *u_out,
-                                              const void *u_fine, const void *out64)
+// The same pass for columns of exactly 32 R rows (R = 2: 64, R = 4: 128) without
+// vertical advection, in the row-chunk layout (lane l: rows R l .. R l + R - 1) with
+// every array moved in pieces of 4 to 32 bytes: f, 1/pivot, u and the neighbours' u
+// as one float2 / float4 per lane (f in FP64 as R / 2 double2), the lane's R stencil
+// records as R / 2 loads of 16 bytes, its R lower-face couplings as one 4- or 8-byte
+// load.  The upper face of row R l + R - 1 is the next lane's first lower face (a
+// shuffle; 0 above the top row).  Each recurrence is the lane's own R steps, one scan
+// of the lanes' composite maps and a fix-up, with the arithmetic per row of the
+// other layouts, so the pass differs from them only in the order of the scan's
+// roundings.
+__host__ __device__ inline bool relax32_vec_ok(int R, int n_r, bool advection, const void *cpack, const void *cvert,
+                                               const void *rinv, const void *f, const void *u_in, const void *u_out,
+                                               const void *u_fine, const void *out64)
 {
     // every array on a 16-byte boundary (the couplings on 8); null pointers are unused
     const uintptr_t a = (uintptr_t)cpack | (uintptr_t)rinv | (uintptr_t)f | (uintptr_t)u_in | (uintptr_t)u_out |
                         (uintptr_t)u_fine | (uintptr_t)out64;
-    return n_r == 128 && !advection && (a & 15) == 0 && ((uintptr_t)cvert & 7) == 0;
+    return (R == 2 || R == 4) && n_r == 32 * R && !advection && (a & 15) == 0 && ((uintptr_t)cvert & 7) == 0;
 }
 
 __device__ __forceinline__ float bf_lo(unsigned w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf_hi(unsigned w) { return __uint_as_float(w & 0xffff0000u); }
 
-template <int MODE, typename TF>
-__device__ __forceinline__ void relax32_column_v4(const bf16x4 *__restrict__ cpack,
-                                                  const unsigned short *__restrict__ cvert,
-                                                  const float *__restrict__ rinv, const TF *__restrict__ f,
-                                                  const float *u_in, float *u_out, float *__restrict__ u_fine,
-                                                  double *__restrict__ out64, float relax, int T, int4 nb, int lane)
+// R consecutive floats starting at p (8- or 16-byte aligned) into v[0 .. R-1]
+template <int R, bool LDG>
+__device__ __forceinline__ void load_rows(const float *p, float *v)
 {
-    constexpr int n_r = 128;
+    if constexpr (R == 2) {
+        const float2 t = LDG ? __ldg(reinterpret_cast<const float2 *>(p)) : *reinterpret_cast<const float2 *>(p);
+        v[0] = t.x, v[1] = t.y;
+    } else {
+        const float4 t = LDG ? __ldg(reinterpret_cast<const float4 *>(p)) : *reinterpret_cast<const float4 *>(p);
+        v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+    }
+}
+
+template <int MODE, typename TF, int R>
+__device__ __forceinline__ void relax32_column_vec(const bf16x4 *__restrict__ cpack,
+                                                   const unsigned short *__restrict__ cvert,
+                                                   const float *__restrict__ rinv, const TF *__restrict__ f,
+                                                   const float *u_in, float *u_out, float *__restrict__ u_fine,
+                                                   double *__restrict__ out64, float relax, int T, int4 nb, int lane)
+{
+    static_assert(R == 2 || R == 4, "16-byte layout: 2 or 4 rows per lane");
+    constexpr int n_r = 32 * R;
     const unsigned full = 0xffffffffu;
     const bool n0 = MODE == PASS_NORMAL || (nb.w & 1), n1 = MODE == PASS_NORMAL || (nb.w & 2),
                n2 = MODE == PASS_NORMAL || (nb.w & 4);
-    const int k0 = 4 * lane;
+    const int k0 = R * lane;
     const size_t i0 = (size_t)T * n_r + k0;
-    float d[4];
+    float d[R];
     if constexpr (sizeof(TF) == 4) {
-        const float4 f4 = __ldg(reinterpret_cast<const float4 *>(f + i0));
-        d[0] = f4.x, d[1] = f4.y, d[2] = f4.z, d[3] = f4.w;
+        load_rows<R, true>(reinterpret_cast<const float *>(f) + i0, d);
     } else {
-        const double2 fa = __ldg(reinterpret_cast<const double2 *>(f + i0));
-        const double2 fc = __ldg(reinterpret_cast<const double2 *>(f + i0 + 2));
-        d[0] = (float)fa.x, d[1] = (float)fa.y, d[2] = (float)fc.x, d[3] = (float)fc.y;
+#pragma unroll
+        for (int h = 0; h < R / 2; ++h) {
+            const double2 t = __ldg(reinterpret_cast<const double2 *>(f + i0) + h);
+            d[2 * h] = (float)t.x, d[2 * h + 1] = (float)t.y;
+        }
     }
     if (MODE != PASS_RHS_ONLY) {
-        // stencil records of rows k0 .. k0 + 3: {alphaS_hat 0, 1, 2, beta_hat} in 8 bytes each
-        const uint4 sa = __ldg(reinterpret_cast<const uint4 *>(cpack + i0));
-        const uint4 sb = __ldg(reinterpret_cast<const uint4 *>(cpack + i0 + 2));
-        const unsigned lo[4] = {sa.x, sa.z, sb.x, sb.z}, hi[4] = {sa.y, sa.w, sb.y, sb.w};
-        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 v0 = n0 ? *reinterpret_cast<const float4 *>(u_in + (size_t)nb.x * n_r + k0) : z4;
-        const float4 v1 = n1 ? *reinterpret_cast<const float4 *>(u_in + (size_t)nb.y * n_r + k0) : z4;
-        const float4 v2 = n2 ? *reinterpret_cast<const float4 *>(u_in + (size_t)nb.z * n_r + k0) : z4;
-        const float a0[4] = {v0.x, v0.y, v0.z, v0.w}, a1[4] = {v1.x, v1.y, v1.z, v1.w},
-                    a2[4] = {v2.x, v2.y, v2.z, v2.w};
+        // stencil records of rows k0 .. k0 + R - 1: {alphaS_hat 0, 1, 2, beta_hat} in 8 bytes each,
+        // as 32-bit words: lo = alphaS_hat 0 | 1, hi = alphaS_hat 2 | beta_hat
+        unsigned lo[R], hi[R];
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int h = 0; h < R / 2; ++h) {
+            const uint4 w = __ldg(reinterpret_cast<const uint4 *>(cpack + i0) + h);
+            lo[2 * h] = w.x, hi[2 * h] = w.y, lo[2 * h + 1] = w.z, hi[2 * h + 1] = w.w;
+        }
+        float a0[R], a1[R], a2[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) a0[j] = a1[j] = a2[j] = 0.f;
+        if (n0) load_rows<R, false>(u_in + (size_t)nb.x * n_r + k0, a0);
+        if (n1) load_rows<R, false>(u_in + (size_t)nb.y * n_r + k0, a1);
+        if (n2) load_rows<R, false>(u_in + (size_t)nb.z * n_r + k0, a2);
+#pragma unroll
+        for (int j = 0; j < R; ++j)
             d[j] = fmaf(bf_lo(hi[j]), a2[j], fmaf(bf_hi(lo[j]), a1[j], fmaf(bf_lo(lo[j]), a0[j], d[j])));
     }
-    const float4 r4 = __ldg(reinterpret_cast<const float4 *>(rinv + i0));
-    const float ri[4] = {r4.x, r4.y, r4.z, r4.w};
+    float ri[R];
+    load_rows<R, true>(rinv + i0, ri);
     // lower-face couplings c_k of the lane's rows; c_{k+1} above them
-    const uint2 cw = __ldg(reinterpret_cast<const uint2 *>(cvert + i0));
-    const float cb[4] = {bf_lo(cw.x), bf_hi(cw.x), bf_lo(cw.y), bf_hi(cw.y)};
-    float c4 = __shfl_down_sync(full, cb[0], 1);
-    if (lane == 31) c4 = 0.f;
-    const float ca[4] = {cb[1], cb[2], cb[3], c4};
-    float x[4], P[4];
+    float cb[R];
+    if constexpr (R == 2) {
+        const unsigned w = __ldg(reinterpret_cast<const unsigned *>(cvert + i0));
+        cb[0] = bf_lo(w), cb[1] = bf_hi(w);
+    } else {
+        const uint2 w = __ldg(reinterpret_cast<const uint2 *>(cvert + i0));
+        cb[0] = bf_lo(w.x), cb[1] = bf_hi(w.x), cb[2] = bf_lo(w.y), cb[3] = bf_hi(w.y);
+    }
+    float ctop = __shfl_down_sync(full, cb[0], 1);
+    if (lane == 31) ctop = 0.f;
+    float x[R], P[R];
     // y_k = d_k / p_k + (c_k / p_k) y_{k-1}
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < R; ++j) {
         const float t = d[j] * ri[j], b = cb[j] * ri[j];
         x[j] = j == 0 ? t : fmaf(b, x[j - 1], t);
         P[j] = j == 0 ? b : P[j - 1] * b;
     }
     {
-        float A = P[3], B = x[3];
+        float A = P[R - 1], B = x[R - 1];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const float Ap = __shfl_up_sync(full, A, o), Bp = __shfl_up_sync(full, B, o);
@@ -357,14 +381,14 @@ __device__ __forceinline__ void relax32_column_v4(const bf16x4 *__restrict__ cpa
         float cin = __shfl_up_sync(full, B, 1);
         if (lane == 0) cin = 0.f;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) x[j] = fmaf(P[j], cin, x[j]);
+        for (int j = 0; j < R; ++j) x[j] = fmaf(P[j], cin, x[j]);
     }
     // x_k = y_k + (c_{k+1} / p_k) x_{k+1}
 #pragma unroll
-    for (int j = 3; j >= 0; --j) {
-        const float c = ca[j] * ri[j];
-        if (j < 3) x[j] = fmaf(c, x[j + 1], x[j]);
-        P[j] = j == 3 ? c : c * P[j + 1];
+    for (int j = R - 1; j >= 0; --j) {
+        const float c = (j < R - 1 ? cb[j + 1] : ctop) * ri[j];
+        if (j < R - 1) x[j] = fmaf(c, x[j + 1], x[j]);
+        P[j] = j == R - 1 ? c : c * P[j + 1];
     }
     {
         float A = P[0], B = x[0];
@@ -379,37 +403,44 @@ __device__ __forceinline__ void relax32_column_v4(const bf16x4 *__restrict__ cpa
         float cin = __shfl_down_sync(full, B, 1);
         if (lane == 31) cin = 0.f;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) x[j] = fmaf(P[j], cin, x[j]);
+        for (int j = 0; j < R; ++j) x[j] = fmaf(P[j], cin, x[j]);
     }
     // write-back: relaxation weight, the double copy of the finest level's result, the
     // prolongation into the 4 children (P = R^T)
     if (relax != 1.f) {   // from a zero guess (ZERO, RHS_ONLY) the old value is 0
-        float uo[4] = {0.f, 0.f, 0.f, 0.f};
-        if (MODE == PASS_NORMAL) {
-            const float4 o4 = *reinterpret_cast<const float4 *>(u_in + i0);
-            uo[0] = o4.x, uo[1] = o4.y, uo[2] = o4.z, uo[3] = o4.w;
-        }
+        float uo[R];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) x[j] = fmaf(relax, x[j] - uo[j], uo[j]);
+        for (int j = 0; j < R; ++j) uo[j] = 0.f;
+        if (MODE == PASS_NORMAL) load_rows<R, false>(u_in + i0, uo);
+#pragma unroll
+        for (int j = 0; j < R; ++j) x[j] = fmaf(relax, x[j] - uo[j], uo[j]);
     }
-    *reinterpret_cast<float4 *>(u_out + i0) = make_float4(x[0], x[1], x[2], x[3]);
+    auto store_rows = [&](float *p, const float *v) {
+        if constexpr (R == 2)
+            *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+        else
+            *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    };
+    store_rows(u_out + i0, x);
     if (out64) {
-        reinterpret_cast<double2 *>(out64 + i0)[0] = make_double2((double)x[0], (double)x[1]);
-        reinterpret_cast<double2 *>(out64 + i0)[1] = make_double2((double)x[2], (double)x[3]);
+#pragma unroll
+        for (int h = 0; h < R / 2; ++h)
+            reinterpret_cast<double2 *>(out64 + i0)[h] = make_double2((double)x[2 * h], (double)x[2 * h + 1]);
     }
     if (u_fine) {
         const size_t fi = (size_t)4 * T * n_r + k0;
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
-            float4 *q = reinterpret_cast<float4 *>(u_fine + fi + (size_t)h * n_r);
-            float4 v = *q;
-            v.x += x[0], v.y += x[1], v.z += x[2], v.w += x[3];
-            *q = v;
+            float v[R];
+            load_rows<R, false>(u_fine + fi + (size_t)h * n_r, v);
+#pragma unroll
+            for (int j = 0; j < R; ++j) v[j] += x[j];
+            store_rows(u_fine + fi + (size_t)h * n_r, v);
         }
     }
 }
 
-template <int MODE, typename TF, int R, bool SF, bool V4 = false>
+template <int MODE, typename TF, int R, bool SF, bool VEC = false>
 __global__ void __launch_bounds__(256)
     k_relax32_scan(const int *__restrict__ cells, const int4 *__restrict__ tnb, const bf16x4 *__restrict__ cpack,
                    const unsigned short *__restrict__ cvert, const float *__restrict__ rinv,
@@ -425,8 +456,8 @@ __global__ void __launch_bounds__(256)
     pdl_wait();
     pdl_trigger();
     if (T < 0) return;
-    if constexpr (V4)
-        relax32_column_v4<MODE, TF>(cpack, cvert, rinv, f, u_in, u_out, u_fine, out64, relax, T, nb, lane);
+    if constexpr (VEC)
+        relax32_column_vec<MODE, TF, R>(cpack, cvert, rinv, f, u_in, u_out, u_fine, out64, relax, T, nb, lane);
     else
         relax32_column<MODE, TF, R, SF>(cpack, cvert, rinv, fb, fg, n_r, f, u_in, u_out, u_fine, out64, relax, T, nb,
                                         lane);
@@ -469,13 +500,16 @@ __global__ void __launch_bounds__(256) k_relax32_batch(const __grid_constant__ R
     pdl_trigger();
     if (T < 0 || !active[I.member]) return;
     // the layout the member's own pass takes (the same rounding as its single solve)
-    if (R == 4 && relax32_v4_ok(I.n_r, false, I.cpack, I.cvert, I.rinv, I.f, I.u_in, I.u_out, I.u_fine, I.out64))
-        relax32_column_v4<MODE, TF>(I.cpack, I.cvert, I.rinv, static_cast<const TF *>(I.f), I.u_in, I.u_out,
-                                    I.u_fine, I.out64, I.relax, T, nb, lane);
-    else
-        relax32_column<MODE, TF, R, false>(I.cpack, I.cvert, I.rinv, nullptr, nullptr, I.n_r,
-                                           static_cast<const TF *>(I.f), I.u_in, I.u_out, I.u_fine, I.out64, I.relax,
-                                           T, nb, lane);
+    if constexpr (R == 2 || R == 4) {
+        if (relax32_vec_ok(R, I.n_r, false, I.cpack, I.cvert, I.rinv, I.f, I.u_in, I.u_out, I.u_fine, I.out64)) {
+            relax32_column_vec<MODE, TF, R>(I.cpack, I.cvert, I.rinv, static_cast<const TF *>(I.f), I.u_in, I.u_out,
+                                            I.u_fine, I.out64, I.relax, T, nb, lane);
+            return;
+        }
+    }
+    relax32_column<MODE, TF, R, false>(I.cpack, I.cvert, I.rinv, nullptr, nullptr, I.n_r,
+                                       static_cast<const TF *>(I.f), I.u_in, I.u_out, I.u_fine, I.out64, I.relax, T,
+                                       nb, lane);
 }
 
 // f_c[T][k] = sum_j (f - A u)[4T + j][k] in FP32 with the BF16 stencil, the row
@@ -604,9 +638,10 @@ cudaError_t relax32_r(const Launch &L, const LevelDev &lv, int task0, int n_task
     const int n_slots = n_tasks * kRelaxCols;
     // the stored multipliers only with vertical advection (their couplings are not alphar_hat)
     auto kern = lv.cxv_on ? k_relax32_scan<MODE, TF, R, true> : k_relax32_scan<MODE, TF, R, false>;
-    // columns of exactly 128 rows: 4 rows per lane with 16-byte accesses
-    if (R == 4 && relax32_v4_ok(L.n_r, lv.cxv_on, lv.cpack, lv.cvert, lv.rinv32, f, u_in, u_out, u_fine, out64))
-        kern = k_relax32_scan<MODE, TF, 4, false, true>;
+    // columns of exactly 64 or 128 rows: 2 or 4 rows per lane with 8- and 16-byte accesses
+    if constexpr (R == 2 || R == 4)
+        if (relax32_vec_ok(R, L.n_r, lv.cxv_on, lv.cpack, lv.cvert, lv.rinv32, f, u_in, u_out, u_fine, out64))
+            kern = k_relax32_scan<MODE, TF, R, false, true>;
     return launch_k(L, kern, (n_slots + wpb - 1) / wpb, 32 * wpb, 0, lv.task_cells, lv.task_nbr, lv.cpack, lv.cvert,
                     lv.rinv32, lv.fb32, lv.fc32, L.n_r, task0 * kRelaxCols, n_slots, f, u_in, u_out, u_fine, out64,
                     relax);
