@@ -441,7 +441,7 @@ __device__ __forceinline__ void relax32_column_vec(const bf16x4 *__restrict__ cp
 }
 
 template <int MODE, typename TF, int R, bool SF, bool VEC = false>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, VEC ? 8 : 1)
     k_relax32_scan(const int *__restrict__ cells, const int4 *__restrict__ tnb, const bf16x4 *__restrict__ cpack,
                    const unsigned short *__restrict__ cvert, const float *__restrict__ rinv,
                    const float *__restrict__ fb, const float *__restrict__ fg, int n_r, int slot0, int n_slots,
