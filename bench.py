@@ -507,7 +507,8 @@ def run_tpmg(args, wl):
     # pinned host memory, their solutions read back into pinned host memory, every copy
     # inside the timed call (tpmg_solve_host_many overlaps step j's solve with the copies
     # of steps j - 1 and j + 1; the guess is zero, so only f is copied in)
-    e2e_steps = max(1, min(args.steps, 10))
+    # every timed step, each with its own pinned solution array, up to 2 GB of them
+    e2e_steps = max(1, min(args.steps, (2 << 30) // (8 * N)))
     f_host = torch.empty(N, dtype=torch.float64, pin_memory=True)
     f_host.copy_(f)
     u_hosts = [torch.zeros(N, dtype=torch.float64, pin_memory=True) for _ in range(e2e_steps)]
