@@ -562,6 +562,90 @@ __global__ void __launch_bounds__(kThreads32)
         restrict32_row<TF>(nbr, cpack, cvert, cxv, dr32, n_r, f, u, fc, ic);
 }
 
+// The same residual + restriction for columns of exactly 32 R rows (R = 2: 64, R = 4:
+// 128) without vertical advection: one warp per coarse column, lane l forming the
+// coarse rows R l .. R l + R - 1, every array moved R rows at a time (f, u, the
+// neighbours' u and f_c as one float2 / float4 per lane, f in FP64 as R / 2 double2,
+// the stencil as R / 2 loads of 16 bytes, the lower-face couplings as 4 or 8 bytes).
+// The rows just below and above a lane's rows, and the coupling above its last row,
+// come from the neighbouring lanes by shuffles.  Each row's operations and their
+// order are those of restrict32_row, so the results are the same bit for bit.
+template <typename TF, int R>
+__global__ void __launch_bounds__(kThreads32)
+    k_resid_restrict32_vec(const int4 *__restrict__ nbr, const bf16x4 *__restrict__ cpack,
+                           const unsigned short *__restrict__ cvert, const TF *__restrict__ f,
+                           const float *__restrict__ u, float *__restrict__ fc, int n_coarse)
+{
+    constexpr int n_r = 32 * R;
+    const unsigned full = 0xffffffffu;
+    pdl_wait();
+    pdl_trigger();
+    const int lane = threadIdx.x & 31, k0 = R * lane;
+    const int w0 = blockIdx.x * (kThreads32 >> 5) + (threadIdx.x >> 5), nw = gridDim.x * (kThreads32 >> 5);
+    for (int Tc = w0; Tc < n_coarse; Tc += nw) {
+        float s[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) s[j] = 0.f;
+#pragma unroll
+        for (int jc = 0; jc < 4; ++jc) {
+            const int T = 4 * Tc + jc;
+            const size_t i0 = (size_t)T * n_r + k0;
+            const int4 nb = __ldg(&nbr[T]);
+            unsigned lo[R], hi[R];
+#pragma unroll
+            for (int h = 0; h < R / 2; ++h) {
+                const uint4 q = __ldg(reinterpret_cast<const uint4 *>(cpack + i0) + h);
+                lo[2 * h] = q.x, hi[2 * h] = q.y, lo[2 * h + 1] = q.z, hi[2 * h + 1] = q.w;
+            }
+            float uc[R], v0[R], v1[R], v2[R], cl[R], fr[R];
+            load_rows<R, true>(u + i0, uc);
+            load_rows<R, true>(u + (size_t)nb.x * n_r + k0, v0);
+            load_rows<R, true>(u + (size_t)nb.y * n_r + k0, v1);
+            load_rows<R, true>(u + (size_t)nb.z * n_r + k0, v2);
+            if constexpr (R == 2) {
+                const unsigned q = __ldg(reinterpret_cast<const unsigned *>(cvert + i0));
+                cl[0] = bf_lo(q), cl[1] = bf_hi(q);
+            } else {
+                const uint2 q = __ldg(reinterpret_cast<const uint2 *>(cvert + i0));
+                cl[0] = bf_lo(q.x), cl[1] = bf_hi(q.x), cl[2] = bf_lo(q.y), cl[3] = bf_hi(q.y);
+            }
+            if constexpr (sizeof(TF) == 4) {
+                load_rows<R, true>(reinterpret_cast<const float *>(f) + i0, fr);
+            } else {
+#pragma unroll
+                for (int h = 0; h < R / 2; ++h) {
+                    const double2 t = __ldg(reinterpret_cast<const double2 *>(f + i0) + h);
+                    fr[2 * h] = (float)t.x, fr[2 * h + 1] = (float)t.y;
+                }
+            }
+            // the row below the lane's first (u of the column's row 0 itself at k = 0), the row
+            // above its last (the top row itself at k = n_r - 1) and the coupling above its last
+            // row (0 at the top face)
+            float ubelow = __shfl_up_sync(full, uc[R - 1], 1), uabove = __shfl_down_sync(full, uc[0], 1),
+                  ctop = __shfl_down_sync(full, cl[0], 1);
+            if (lane == 0) ubelow = uc[0];
+            if (lane == 31) uabove = uc[R - 1], ctop = 0.f;
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const float um = j > 0 ? uc[j - 1] : ubelow, up = j < R - 1 ? uc[j + 1] : uabove;
+                const float cu = j < R - 1 ? cl[j + 1] : ctop;
+                float a = bf_hi(hi[j]) * uc[j];
+                a = fmaf(cl[j], uc[j] - um, a);
+                a = fmaf(cu, uc[j] - up, a);
+                a = fmaf(bf_lo(lo[j]), uc[j] - v0[j], a);
+                a = fmaf(bf_hi(lo[j]), uc[j] - v1[j], a);
+                a = fmaf(bf_lo(hi[j]), uc[j] - v2[j], a);
+                s[j] += fr[j] - a;
+            }
+        }
+        float *out = fc + (size_t)Tc * n_r + k0;
+        if constexpr (R == 2)
+            *reinterpret_cast<float2 *>(out) = make_float2(s[0], s[1]);
+        else
+            *reinterpret_cast<float4 *>(out) = make_float4(s[0], s[1], s[2], s[3]);
+    }
+}
+
 // Residual + restriction of the batched form: the coarse rows of several members'
 // restrictions in one launch.  Each item's rows occupy a range of the launch's
 // positions starting at roff[it], a multiple of 32, so that a warp's positions belong
@@ -679,6 +763,15 @@ cudaError_t launch_resid_restrict32(const Launch &L, const LevelDev &fine, const
                                     const float *u, float *fc)
 {
     const int Nc = coarse.n * L.n_r;
+    // columns of exactly 64 or 128 rows without advection: one warp per coarse column
+    // with 8- and 16-byte accesses (the same arithmetic)
+    const int grid_w = grid32((long)coarse.n * 32, L.sm_count);
+    if (relax32_vec_ok(2, L.n_r, fine.cxv_on, fine.cpack, fine.cvert, nullptr, f, u, fc, nullptr, nullptr))
+        return launch_k(L, k_resid_restrict32_vec<TF, 2>, grid_w, kThreads32, 0, fine.nbr, fine.cpack, fine.cvert, f,
+                        u, fc, coarse.n);
+    if (relax32_vec_ok(4, L.n_r, fine.cxv_on, fine.cpack, fine.cvert, nullptr, f, u, fc, nullptr, nullptr))
+        return launch_k(L, k_resid_restrict32_vec<TF, 4>, grid_w, kThreads32, 0, fine.nbr, fine.cpack, fine.cvert, f,
+                        u, fc, coarse.n);
     return launch_k(L, k_resid_restrict32<TF>, grid32(Nc, L.sm_count), kThreads32, 0, fine.nbr, fine.cpack, fine.cvert,
                     fine.cxv_on ? fine.cxv : nullptr, L.dr32, L.n_r, f, u, fc, Nc);
 }
