@@ -69,6 +69,10 @@ def test_null_arguments_are_rejected(lib):
     assert lib.tpmg_solve(None, None, None, 1e-5, 10, ctypes.byref(it), ctypes.byref(rel), None) == \
         binding.TPMG_ERR_INVALID_ARG
     assert lib.tpmg_query(None, 0, None, None, None, None) == binding.TPMG_ERR_INVALID_ARG
+    assert lib.tpmg_solve_host(None, None, None, 1e-5, 10, ctypes.byref(it), ctypes.byref(rel), None) == \
+        binding.TPMG_ERR_INVALID_ARG
+    assert lib.tpmg_solve_host_many(None, 0, None, None, 0, 1e-5, 10, None, None, None) == \
+        binding.TPMG_ERR_INVALID_ARG
     lib.tpmg_destroy(None)
 
 
