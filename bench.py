@@ -574,6 +574,9 @@ def run_tpmg(args, wl):
                         "iters": [int(i) for i in e2e_iters],
                         "call": "tpmg_solve_host_many (pinned host f in, u out; copies of neighbouring steps "
                                 "overlap each solve)",
+                        "note": "host clock around one call; its solves run without the roofline's CUDA-event "
+                                "brackets and without an L2 flush between steps, which the device-timed value "
+                                "carries, so it can exceed value",
                         "per_call": {"value": pc_value, "unit": "unknowns/s", "h2d_bytes_per_step": 2 * 8 * N,
                                      "d2h_bytes_per_step": 8 * N, "ms": pc_ms,
                                      "call": "tpmg_solve_host once per step (f and the guess in, u out)"}},
