@@ -32,6 +32,13 @@ CASES = {
     "ref3_nr128_graded_c80": dict(refinement=3, n_levels=4, n_r=128, grading=1.02, courant_c=80.0),
     "ref3_nr128_graded_c8": dict(refinement=3, n_levels=4, n_r=128, grading=1.02, courant_c=8.0),
     "ref2_nr100_graded_c8": dict(refinement=2, n_levels=3, n_r=100, grading=1.03, courant_c=8.0),
+    # weighted block-Jacobi (relax != 1, a second buffer) in the wide-access layouts
+    "ref2_nr64_jacobi": dict(refinement=2, n_levels=3, n_r=64, courant_c=20.0, smoother=1, relax=0.6, nu_pre=1,
+                             nu_post=1, nu_coarse=2),
+    "ref2_nr128_jacobi_relax07": dict(refinement=2, n_levels=3, n_r=128, grading=1.02, courant_c=8.0, smoother=1,
+                                      relax=0.7, nu_pre=2, nu_post=2, nu_coarse=2),
+    "ref2_nr128_sor_relax08": dict(refinement=2, n_levels=3, n_r=128, courant_c=8.0, relax=0.8, nu_pre=1,
+                                   nu_post=1, nu_coarse=1),
 }
 
 
