@@ -2839,17 +2839,30 @@ tpmg_status tpmg_solve_host_many(tpmg_ctx *ctx, int n, const double *const *h_f,
                 return fail(ctx, TPMG_ERR_INVALID_ARG, "a solution array overlaps another system's arrays");
     }
     if (n == 0) return TPMG_OK;
-    if (!ctx->hf2) {
-        if (dalloc(ctx, &ctx->hf2, ctx->N) != cudaSuccess || dalloc(ctx, &ctx->hu2, ctx->N) != cudaSuccess)
+    if (!ctx->hu2) {   // hu2 is set last: a failed first attempt is retried whole
+        if (!ctx->hf2 && dalloc(ctx, &ctx->hf2, ctx->N) != cudaSuccess)
             return fail(ctx, TPMG_ERR_OOM, "second staging slot");
+        if (dalloc(ctx, &ctx->hu2, ctx->N) != cudaSuccess) return fail(ctx, TPMG_ERR_OOM, "second staging slot");
     }
-    if (!ctx->xin) {
-        CU(cudaStreamCreateWithFlags(&ctx->xin, cudaStreamNonBlocking));
-        CU(cudaStreamCreateWithFlags(&ctx->xout, cudaStreamNonBlocking));
+    if (!ctx->xout) {   // the streams and events, kept only once all of them exist
+        cudaStream_t in = nullptr, out = nullptr;
+        cudaEvent_t ev[6] = {};
+        cudaError_t e = cudaStreamCreateWithFlags(&in, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&out, cudaStreamNonBlocking);
+        for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            for (cudaEvent_t x : ev)
+                if (x) cudaEventDestroy(x);
+            if (in) cudaStreamDestroy(in);
+            if (out) cudaStreamDestroy(out);
+            return fail(ctx, TPMG_ERR_CUDA, std::string("host solves: ") + cudaGetErrorString(e));
+        }
+        ctx->xin = in;
+        ctx->xout = out;
         for (int i = 0; i < 2; ++i) {
-            CU(cudaEventCreateWithFlags(&ctx->xev_in[i], cudaEventDisableTiming));
-            CU(cudaEventCreateWithFlags(&ctx->xev_solved[i], cudaEventDisableTiming));
-            CU(cudaEventCreateWithFlags(&ctx->xev_out[i], cudaEventDisableTiming));
+            ctx->xev_in[i] = ev[i];
+            ctx->xev_solved[i] = ev[2 + i];
+            ctx->xev_out[i] = ev[4 + i];
         }
     }
     double *F[2] = {ctx->hf, ctx->hf2}, *U[2] = {ctx->hu, ctx->hu2};
